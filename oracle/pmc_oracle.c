@@ -1,0 +1,670 @@
+/*
+ * pmc_oracle.c -- CPU FP64 oracle of Progressive Material Caching.
+ *
+ * TEST INFRASTRUCTURE ONLY (see pmc_oracle.h).  Written for clarity, not speed:
+ * one shading point at a time, one node at a time, one table slot at a time.
+ */
+#include "pmc_oracle.h"
+
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+/* ========================================================================== */
+/* Published mixers                                                           */
+/* ========================================================================== */
+
+/* MurmurHash3 fmix32 (Appleby, public domain): xor-shift / multiply avalanche. */
+uint32_t orc_fmix32(uint32_t h) {
+    h ^= h >> 16;
+    h *= 0x85EBCA6Bu;
+    h ^= h >> 13;
+    h *= 0xC2B2AE35u;
+    h ^= h >> 16;
+    return h;
+}
+
+/* MurmurHash3 fmix64 (Appleby, public domain). */
+uint64_t orc_fmix64(uint64_t k) {
+    k ^= k >> 33;
+    k *= 0xFF51AFD7ED558CCDull;
+    k ^= k >> 33;
+    k *= 0xC4CEB9FE1A85EC53ull;
+    k ^= k >> 33;
+    return k;
+}
+
+/* Output function of SplitMix64 (Steele, Lea & Flood 2014). */
+uint64_t orc_splitmix64_mix(uint64_t z) {
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+/* ========================================================================== */
+/* Node primitives (the paper leaves them to the renderer; defined here)      */
+/* ========================================================================== */
+
+/* Integer lattice hash: the three primes of Teschner et al. 2003 ("Optimized
+ * spatial hashing for collision detection of deformable objects") combined by
+ * xor, then the MurmurHash3 32-bit finaliser.  Arithmetic is modulo 2^32;
+ * negative lattice indices wrap as two's complement. */
+uint32_t orc_lattice_hash(int64_t i, int64_t j, uint32_t seed) {
+    uint32_t ui = (uint32_t)i;
+    uint32_t uj = (uint32_t)j;
+    uint32_t h = (ui * 73856093u) ^ (uj * 19349663u) ^ (seed * 83492791u);
+    return orc_fmix32(h);
+}
+
+/* Perlin's improved-noise interpolant 6t^5 - 15t^4 + 10t^3 (Perlin 2002). */
+double orc_fade(double t) {
+    return 6.0 * pow(t, 5) - 15.0 * pow(t, 4) + 10.0 * pow(t, 3);
+}
+
+/* The 8 unit gradients at multiples of 45 degrees, selected by hash & 7. */
+static void gradient(int64_t i, int64_t j, uint32_t seed, double* gx, double* gy) {
+    uint32_t k = orc_lattice_hash(i, j, seed) & 7u;
+    double ang = (double)k * (M_PI / 4.0);
+    *gx = cos(ang);
+    *gy = sin(ang);
+    /* cos/sin of multiples of pi/4 are 0, +-1 or +-sqrt(1/2); snap the zeros
+     * and ones that cos/sin return with a last-bit error. */
+    if (fabs(*gx) < 1e-12) *gx = 0.0;
+    if (fabs(*gy) < 1e-12) *gy = 0.0;
+    if (fabs(fabs(*gx) - 1.0) < 1e-12) *gx = *gx > 0 ? 1.0 : -1.0;
+    if (fabs(fabs(*gy) - 1.0) < 1e-12) *gy = *gy > 0 ? 1.0 : -1.0;
+}
+
+static double lerp(double a, double b, double t) { return a + (b - a) * t; }
+
+/* 2-D gradient noise (Perlin 1985/2002): a gradient at every lattice point,
+ * dotted with the offset to the sample, blended with the quintic fade. */
+double orc_perlin(double x, double y, uint32_t seed) {
+    double fx0 = floor(x), fy0 = floor(y);
+    int64_t ix = (int64_t)fx0, iy = (int64_t)fy0;
+    double fx = x - fx0, fy = y - fy0;
+    double d[2][2];
+    for (int cy = 0; cy < 2; ++cy) {
+        for (int cx = 0; cx < 2; ++cx) {
+            double gx, gy;
+            gradient(ix + cx, iy + cy, seed, &gx, &gy);
+            d[cy][cx] = gx * (fx - cx) + gy * (fy - cy);
+        }
+    }
+    double su = orc_fade(fx), sv = orc_fade(fy);
+    return lerp(lerp(d[0][0], d[0][1], su), lerp(d[1][0], d[1][1], su), sv);
+}
+
+static double clamp01(double x) { return x < 0.0 ? 0.0 : (x > 1.0 ? 1.0 : x); }
+
+/* Fractal Brownian motion: octave k samples noise at frequency scale*lac^k with
+ * weight gain^k and seed + k; the weighted sum is normalised by the sum of the
+ * weights and mapped to 0.5 + f, clamped to [0, 1]. */
+double orc_fbm(double x, double y, double scale, int octaves, double lacunarity,
+               double gain, uint32_t seed) {
+    double sum = 0.0, norm = 0.0;
+    for (int k = 0; k < octaves; ++k) {
+        double freq = scale * pow(lacunarity, k);
+        double amp = pow(gain, k);
+        sum += amp * orc_perlin(x * freq, y * freq, seed + (uint32_t)k);
+        norm += amp;
+    }
+    return clamp01(0.5 + sum / norm);
+}
+
+/* Worley (1996) F1: distance to the nearest feature point, one feature point
+ * per unit cell at cell + 0.25 + 0.5 * (16-bit fractions of the cell hash).
+ * The 0.25 margin makes the 3x3 neighbourhood exact: a point outside it is at
+ * least 1.25 away, the own cell's point at most sqrt(2) * 0.75 ~ 1.06. */
+double orc_voronoi_f1(double x, double y, uint32_t seed) {
+    double fx0 = floor(x), fy0 = floor(y);
+    int64_t ix = (int64_t)fx0, iy = (int64_t)fy0;
+    double fx = x - fx0, fy = y - fy0;
+    double best = INFINITY;
+    for (int b = -1; b <= 1; ++b) {
+        for (int a = -1; a <= 1; ++a) {
+            uint32_t h = orc_lattice_hash(ix + a, iy + b, seed);
+            double ox = a + 0.25 + 0.5 * ((double)(h & 0xFFFFu) / 65536.0);
+            double oy = b + 0.25 + 0.5 * ((double)(h >> 16) / 65536.0);
+            double d2 = (ox - fx) * (ox - fx) + (oy - fy) * (oy - fy);
+            if (d2 < best) best = d2;
+        }
+    }
+    return sqrt(best);
+}
+
+void orc_eval_node(const orc_node* nd, const double* a, const double* b, const double* c,
+                   const double sp[8], double out[3]) {
+    const float* p = nd->fp;
+    switch (nd->op) {
+    case ORC_UV:
+        out[0] = sp[0]; out[1] = sp[1]; out[2] = 0.0;
+        return;
+    case ORC_POSITION:
+        out[0] = sp[2]; out[1] = sp[3]; out[2] = sp[4];
+        return;
+    case ORC_NORMAL:
+        out[0] = sp[5]; out[1] = sp[6]; out[2] = sp[7];
+        return;
+    case ORC_CONST:
+        out[0] = p[0]; out[1] = p[1]; out[2] = p[2];
+        return;
+    case ORC_UV_AFFINE: /* [x'; y'] = [p0 p1; p2 p3] [x; y] + [p4; p5]; not clamped */
+        out[0] = (double)p[0] * a[0] + (double)p[1] * a[1] + (double)p[4];
+        out[1] = (double)p[2] * a[0] + (double)p[3] * a[1] + (double)p[5];
+        out[2] = 0.0;
+        return;
+    case ORC_FBM: {
+        double s = orc_fbm(a[0], a[1], p[0], nd->ip[0], p[1], p[2], (uint32_t)nd->ip[1]);
+        out[0] = out[1] = out[2] = s;
+        return;
+    }
+    case ORC_VORONOI: {
+        double s = clamp01(orc_voronoi_f1(a[0] * p[0], a[1] * p[0], (uint32_t)nd->ip[1]));
+        out[0] = out[1] = out[2] = s;
+        return;
+    }
+    case ORC_CHECKER: {
+        int64_t k = (int64_t)floor(a[0] * p[0]) + (int64_t)floor(a[1] * p[0]);
+        const float* col = (k & 1) ? &p[4] : &p[1];
+        for (int i = 0; i < 3; ++i) out[i] = clamp01(col[i]);
+        return;
+    }
+    case ORC_RAMP: {
+        int ns = nd->ip[0];
+        double t = clamp01(a[0]);
+        double res[3];
+        if (t <= p[0]) {
+            for (int i = 0; i < 3; ++i) res[i] = p[4 + i];
+        } else if (t >= p[ns - 1]) {
+            for (int i = 0; i < 3; ++i) res[i] = p[4 + 3 * (ns - 1) + i];
+        } else {
+            for (int k = 0; k + 1 < ns; ++k) {
+                if (t < p[k + 1]) {
+                    double w = (t - p[k]) / ((double)p[k + 1] - (double)p[k]);
+                    for (int i = 0; i < 3; ++i)
+                        res[i] = lerp(p[4 + 3 * k + i], p[4 + 3 * (k + 1) + i], w);
+                    break;
+                }
+            }
+        }
+        for (int i = 0; i < 3; ++i) out[i] = clamp01(res[i]);
+        return;
+    }
+    case ORC_MIX: {
+        double f = clamp01(c ? c[0] : (double)p[0]);
+        for (int i = 0; i < 3; ++i) out[i] = clamp01(lerp(a[i], b[i], f));
+        return;
+    }
+    case ORC_ADD:
+        for (int i = 0; i < 3; ++i) out[i] = clamp01(a[i] + b[i]);
+        return;
+    case ORC_MUL:
+        for (int i = 0; i < 3; ++i) out[i] = clamp01(a[i] * b[i]);
+        return;
+    case ORC_POW:
+        for (int i = 0; i < 3; ++i) {
+            double x = a[i] > 0.0 ? a[i] : 0.0;
+            out[i] = clamp01(pow(x, (double)p[0]));
+        }
+        return;
+    case ORC_FACING: {
+        double s = clamp01(fabs(a[0] * p[0] + a[1] * p[1] + a[2] * p[2]));
+        out[0] = out[1] = out[2] = s;
+        return;
+    }
+    default:
+        out[0] = out[1] = out[2] = 0.0;
+        return;
+    }
+}
+
+/* ========================================================================== */
+/* Descriptor and hashes                                                      */
+/* ========================================================================== */
+
+/* Texel index on a virtual texture of 2^level texels per axis (Sec. 3.1):
+ * clamp u to [0, 1] (NaN to 0), then floor(u * 2^level), with u = 1 mapped to
+ * the last texel. */
+uint32_t orc_texel(float u, uint32_t level) {
+    double x = (double)u;
+    if (!(x >= 0.0)) x = 0.0;
+    if (x > 1.0) x = 1.0;
+    double r = ldexp(1.0, (int)level);
+    double t = floor(x * r);
+    if (t > r - 1.0) t = r - 1.0;
+    return (uint32_t)t;
+}
+
+/* Descriptor (Sec. 3.1): material ID, node ID (index in the network as given),
+ * mip level lambda, texel indices, packed as
+ * mat<<48 | node<<32 | level<<26 | iu<<13 | iv. */
+uint64_t orc_key(uint32_t mat, uint32_t node, uint32_t level, float u, float v) {
+    uint64_t iu = orc_texel(u, level), iv = orc_texel(v, level);
+    return ((uint64_t)mat << 48) | ((uint64_t)node << 32) | ((uint64_t)level << 26) |
+           (iu << 13) | iv;
+}
+
+/* Hash of Alg. 1 (cell selection): SplitMix64 output function of the key. */
+uint64_t orc_hash1(uint64_t key) { return orc_splitmix64_mix(key); }
+
+/* Hash2 of Alg. 1 (entry check): upper 32 bits of fmix64(key xor golden gamma);
+ * 0 is reserved for an empty entry and maps to 1. */
+uint32_t orc_hash2(uint64_t key) {
+    uint32_t h = (uint32_t)(orc_fmix64(key ^ 0x9E3779B97F4A7C15ull) >> 32);
+    return h == 0 ? 1u : h;
+}
+
+/* ========================================================================== */
+/* Network analysis (Sec. 3)                                                  */
+/* ========================================================================== */
+
+static int n_required_inputs(uint32_t op, int* optional) {
+    *optional = 0;
+    switch (op) {
+    case ORC_UV: case ORC_POSITION: case ORC_NORMAL: case ORC_CONST:
+        return 0;
+    case ORC_UV_AFFINE: case ORC_FBM: case ORC_VORONOI: case ORC_CHECKER:
+    case ORC_RAMP: case ORC_POW: case ORC_FACING:
+        return 1;
+    case ORC_MIX:
+        *optional = 1;
+        return 2;
+    case ORC_ADD: case ORC_MUL:
+        return 2;
+    default:
+        return -1;
+    }
+}
+
+int orc_validate(const orc_node* nodes, uint32_t n) {
+    if (n == 0 || n > 65535u) return ORC_ERR_ARG;
+    for (uint32_t i = 0; i < n; ++i) {
+        const orc_node* nd = &nodes[i];
+        int opt;
+        int req = n_required_inputs(nd->op, &opt);
+        if (req < 0) return ORC_ERR_ARG;
+        for (int k = 0; k < 4; ++k) {
+            int32_t x = nd->in[k];
+            if (k < req) {
+                if (x < 0 || (uint32_t)x >= i) return ORC_ERR_ARG;
+            } else if (k < req + opt) {
+                if (x < -1 || (x >= 0 && (uint32_t)x >= i)) return ORC_ERR_ARG;
+            } else if (x != -1) {
+                return ORC_ERR_ARG;
+            }
+        }
+        if (nd->op == ORC_FBM && (nd->ip[0] < 1 || nd->ip[0] > 16)) return ORC_ERR_ARG;
+        if (nd->op == ORC_RAMP) {
+            int ns = nd->ip[0];
+            if (ns < 2 || ns > 4) return ORC_ERR_ARG;
+            for (int k = 0; k < ns; ++k) {
+                if (!(nd->fp[k] >= 0.0f && nd->fp[k] <= 1.0f)) return ORC_ERR_ARG;
+                if (k > 0 && nd->fp[k] < nd->fp[k - 1]) return ORC_ERR_ARG;
+            }
+        }
+        if (nd->op == ORC_POW && !(nd->fp[0] > 0.0f)) return ORC_ERR_ARG;
+    }
+    return ORC_OK;
+}
+
+static int is_input_op(uint32_t op) {
+    return op == ORC_UV || op == ORC_POSITION || op == ORC_NORMAL || op == ORC_CONST;
+}
+
+/* Marks the sub-graph of node r (r and everything it reads) in mark[]. */
+static void mark_subgraph(const orc_node* nodes, uint32_t r, uint8_t* mark) {
+    mark[r] = 1;
+    for (int32_t i = (int32_t)r; i >= 0; --i) {
+        if (!mark[i]) continue;
+        for (int k = 0; k < 4; ++k)
+            if (nodes[i].in[k] >= 0) mark[nodes[i].in[k]] = 1;
+    }
+}
+
+/* Dependence classes and cacheable roots.
+ *   class(UV input) = UV; class(position, normal) = SP; class(const) = CONST;
+ *   any other node takes the highest class of its inputs (CONST < UV < SP).
+ * A node is a cacheable root when it is reachable from the output, has class
+ * UV, is not the bare UV input, is the output or feeds some SP-class node
+ * ("the highest possible level", Sec. 3), and its sub-graph holds at least
+ * min_root_nodes nodes that are not inputs or constants. */
+int orc_analyze(const orc_node* nodes, uint32_t n, uint32_t min_root_nodes,
+                int32_t* cls, uint8_t* is_root, uint32_t* n_roots) {
+    if (orc_validate(nodes, n) != ORC_OK) return ORC_ERR_ARG;
+    for (uint32_t i = 0; i < n; ++i) {
+        const orc_node* nd = &nodes[i];
+        int c;
+        if (nd->op == ORC_UV) c = ORC_CLS_UV;
+        else if (nd->op == ORC_POSITION || nd->op == ORC_NORMAL) c = ORC_CLS_SP;
+        else if (nd->op == ORC_CONST) c = ORC_CLS_CONST;
+        else {
+            c = ORC_CLS_CONST;
+            for (int k = 0; k < 4; ++k)
+                if (nd->in[k] >= 0 && cls[nd->in[k]] > c) c = cls[nd->in[k]];
+        }
+        cls[i] = c;
+    }
+    uint8_t* reach = (uint8_t*)calloc(n, 1);
+    uint8_t* feeds_sp = (uint8_t*)calloc(n, 1);
+    uint8_t* mark = (uint8_t*)malloc(n);
+    mark_subgraph(nodes, n - 1, reach);
+    for (uint32_t i = 0; i < n; ++i) {
+        if (!reach[i] || cls[i] != ORC_CLS_SP) continue;
+        for (int k = 0; k < 4; ++k)
+            if (nodes[i].in[k] >= 0) feeds_sp[nodes[i].in[k]] = 1;
+    }
+    uint32_t nr = 0;
+    for (uint32_t i = 0; i < n; ++i) {
+        is_root[i] = 0;
+        if (!reach[i] || cls[i] != ORC_CLS_UV || nodes[i].op == ORC_UV) continue;
+        if (!(i == n - 1 || feeds_sp[i])) continue;
+        memset(mark, 0, n);
+        mark_subgraph(nodes, i, mark);
+        uint32_t work = 0;
+        for (uint32_t j = 0; j <= i; ++j)
+            if (mark[j] && !is_input_op(nodes[j].op)) ++work;
+        if (work < min_root_nodes) continue;
+        is_root[i] = 1;
+        ++nr;
+    }
+    *n_roots = nr;
+    free(reach);
+    free(feeds_sp);
+    free(mark);
+    return ORC_OK;
+}
+
+static const double* input_value(const orc_node* nd, int k, const double* val) {
+    return nd->in[k] >= 0 ? &val[3 * nd->in[k]] : NULL;
+}
+
+int orc_eval_point_nocache(const orc_node* nodes, uint32_t n, const double sp[8],
+                           double rgb[3]) {
+    if (orc_validate(nodes, n) != ORC_OK) return ORC_ERR_ARG;
+    double* val = (double*)calloc(3 * (size_t)n, sizeof(double));
+    uint8_t* reach = (uint8_t*)calloc(n, 1);
+    mark_subgraph(nodes, n - 1, reach);
+    for (uint32_t i = 0; i < n; ++i) {
+        if (!reach[i]) continue;
+        orc_eval_node(&nodes[i], input_value(&nodes[i], 0, val), input_value(&nodes[i], 1, val),
+                      input_value(&nodes[i], 2, val), sp, &val[3 * i]);
+    }
+    for (int k = 0; k < 3; ++k) rgb[k] = val[3 * (n - 1) + k];
+    free(val);
+    free(reach);
+    return ORC_OK;
+}
+
+/* ========================================================================== */
+/* Progressive cache: sequential emulation of the bulk-synchronous update      */
+/* ========================================================================== */
+
+typedef struct {
+    orc_node* nodes;
+    uint32_t n;
+    uint8_t* is_root;
+    uint32_t n_roots;
+    uint32_t* roots; /* ascending node IDs */
+} orc_mat;
+
+struct orc_cache {
+    uint64_t n_cells;
+    uint32_t n_entries;
+    uint32_t level;
+    uint32_t min_root_nodes;
+    int off;
+    uint32_t* h2;  /* n_cells * n_entries, 0 = empty */
+    float* rgb;    /* 3 per slot */
+    orc_mat* mats;
+    uint32_t n_mats;
+    orc_hash_override_fn hook;
+    uint64_t stats[ORC_NSTATS];
+};
+
+orc_cache* orc_cache_new(uint64_t n_cells, uint32_t n_entries, uint32_t level,
+                         uint32_t min_root_nodes, int cache_off) {
+    if (level > 13) return NULL;
+    orc_cache* c = (orc_cache*)calloc(1, sizeof(orc_cache));
+    c->n_cells = n_cells;
+    c->n_entries = n_entries;
+    c->level = level;
+    c->min_root_nodes = min_root_nodes;
+    c->off = cache_off || n_cells == 0 || n_entries == 0;
+    size_t slots = c->off ? 0 : (size_t)n_cells * n_entries;
+    c->h2 = (uint32_t*)calloc(slots ? slots : 1, sizeof(uint32_t));
+    c->rgb = (float*)calloc(slots ? 3 * slots : 1, sizeof(float));
+    return c;
+}
+
+static void free_mats(orc_cache* c) {
+    for (uint32_t m = 0; m < c->n_mats; ++m) {
+        free(c->mats[m].nodes);
+        free(c->mats[m].is_root);
+        free(c->mats[m].roots);
+    }
+    free(c->mats);
+    c->mats = NULL;
+    c->n_mats = 0;
+}
+
+void orc_cache_free(orc_cache* c) {
+    if (!c) return;
+    free_mats(c);
+    free(c->h2);
+    free(c->rgb);
+    free(c);
+}
+
+int orc_cache_set_materials(orc_cache* c, uint32_t n_mats, const orc_node* const* mat_nodes,
+                            const uint32_t* n_nodes) {
+    if (n_mats > 65536u) return ORC_ERR_ARG;
+    free_mats(c);
+    c->mats = (orc_mat*)calloc(n_mats ? n_mats : 1, sizeof(orc_mat));
+    c->n_mats = n_mats;
+    for (uint32_t m = 0; m < n_mats; ++m) {
+        uint32_t n = n_nodes[m];
+        orc_mat* M = &c->mats[m];
+        if (orc_validate(mat_nodes[m], n) != ORC_OK) {
+            free_mats(c);
+            return ORC_ERR_ARG;
+        }
+        M->n = n;
+        M->nodes = (orc_node*)malloc(n * sizeof(orc_node));
+        memcpy(M->nodes, mat_nodes[m], n * sizeof(orc_node));
+        M->is_root = (uint8_t*)calloc(n, 1);
+        int32_t* cls = (int32_t*)malloc(n * sizeof(int32_t));
+        orc_analyze(M->nodes, n, c->min_root_nodes, cls, M->is_root, &M->n_roots);
+        free(cls);
+        M->roots = (uint32_t*)malloc((M->n_roots ? M->n_roots : 1) * sizeof(uint32_t));
+        uint32_t r = 0;
+        for (uint32_t i = 0; i < n; ++i)
+            if (M->is_root[i]) M->roots[r++] = i;
+    }
+    return ORC_OK;
+}
+
+void orc_cache_set_hash_override(orc_cache* c, orc_hash_override_fn fn) { c->hook = fn; }
+
+void orc_cache_reset(orc_cache* c) {
+    size_t slots = c->off ? 0 : (size_t)c->n_cells * c->n_entries;
+    if (slots) {
+        memset(c->h2, 0, slots * sizeof(uint32_t));
+        memset(c->rgb, 0, 3 * slots * sizeof(float));
+    }
+    memset(c->stats, 0, sizeof(c->stats));
+}
+
+uint32_t orc_cache_n_roots(const orc_cache* c, uint32_t mat) {
+    return mat < c->n_mats ? c->mats[mat].n_roots : 0;
+}
+
+void orc_cache_roots(const orc_cache* c, uint32_t mat, uint32_t* out) {
+    if (mat >= c->n_mats) return;
+    for (uint32_t r = 0; r < c->mats[mat].n_roots; ++r) out[r] = c->mats[mat].roots[r];
+}
+
+static void cell_and_check(const orc_cache* c, uint64_t key, uint64_t* cell, uint32_t* h2) {
+    if (c->hook) {
+        c->hook(key, c->n_cells, cell, h2);
+        return;
+    }
+    *cell = orc_hash1(key) % c->n_cells;
+    *h2 = orc_hash2(key);
+}
+
+/* Scan of one cell as in Alg. 1: the first entry whose stored hash equals h2
+ * (found) or is 0 (empty).  Returns 1 = found, 0 = empty, -1 = cell full;
+ * *slot receives the entry index. */
+static int scan_cell(const orc_cache* c, uint64_t cell, uint32_t h2, uint64_t* slot) {
+    for (uint32_t i = 0; i < c->n_entries; ++i) {
+        uint64_t s = cell * c->n_entries + i;
+        if (c->h2[s] == h2) { *slot = s; return 1; }
+        if (c->h2[s] == 0) { *slot = s; return 0; }
+    }
+    return -1;
+}
+
+typedef struct {
+    uint64_t cell;
+    uint32_t h2;
+    float rgb[3];
+} orc_candidate;
+
+int orc_run_batch(orc_cache* c, uint64_t n, const float* u, const float* v,
+                  const uint32_t* mat, const float* px, const float* py, const float* pz,
+                  const float* nx, const float* ny, const float* nz, double* rgb,
+                  uint16_t* hits, uint32_t* evaluated, uint64_t* probe_key,
+                  uint64_t* probe_cell, uint32_t* probe_h2, uint8_t* probe_hit) {
+    int status = ORC_OK;
+    uint32_t max_n = 1;
+    for (uint32_t m = 0; m < c->n_mats; ++m)
+        if (c->mats[m].n > max_n) max_n = c->mats[m].n;
+    double* val = (double*)malloc(3 * (size_t)max_n * sizeof(double));
+    uint8_t* hit = (uint8_t*)malloc(max_n);
+    double* hitval = (double*)malloc(3 * (size_t)max_n * sizeof(double));
+    uint8_t* needed = (uint8_t*)malloc(max_n);
+    uint64_t* rcell = (uint64_t*)malloc((size_t)max_n * sizeof(uint64_t));
+    uint32_t* rh2 = (uint32_t*)malloc((size_t)max_n * sizeof(uint32_t));
+    size_t cand_cap = 1024, n_cand = 0;
+    orc_candidate* cand = (orc_candidate*)malloc(cand_cap * sizeof(orc_candidate));
+    uint64_t probe = 0;
+
+    /* Phase L and evaluation: every point sees the table as it was when the
+     * batch started. */
+    for (uint64_t i = 0; i < n; ++i) {
+        if (mat[i] >= c->n_mats) {
+            status = ORC_ERR_BADMAT;
+            rgb[i] = rgb[n + i] = rgb[2 * n + i] = 0.0;
+            if (hits) hits[i] = 0;
+            if (evaluated) evaluated[i] = 0;
+            continue;
+        }
+        const orc_mat* M = &c->mats[mat[i]];
+        const double sp[8] = {u[i], v[i], px[i], py[i], pz[i], nx[i], ny[i], nz[i]};
+        uint32_t n_hit = 0;
+        memset(hit, 0, M->n);
+        for (uint32_t r = 0; r < M->n_roots; ++r) {
+            uint32_t node = M->roots[r];
+            if (c->off) continue;
+            uint64_t key = orc_key(mat[i], node, c->level, u[i], v[i]);
+            uint64_t cell, slot;
+            uint32_t h2;
+            cell_and_check(c, key, &cell, &h2);
+            rcell[node] = cell;
+            rh2[node] = h2;
+            int found = scan_cell(c, cell, h2, &slot) == 1;
+            c->stats[0]++;
+            if (found) {
+                hit[node] = 1;
+                for (int k = 0; k < 3; ++k) hitval[3 * node + k] = (double)c->rgb[3 * slot + k];
+                c->stats[1]++;
+                n_hit++;
+            } else {
+                c->stats[2]++;
+            }
+            if (probe_key) probe_key[probe] = key;
+            if (probe_cell) probe_cell[probe] = cell;
+            if (probe_h2) probe_h2[probe] = h2;
+            if (probe_hit) probe_hit[probe] = (uint8_t)found;
+            probe++;
+        }
+        /* Needed set: the output is needed; a needed node that is not a hit
+         * root needs its inputs (reverse storage order = reverse topological). */
+        memset(needed, 0, M->n);
+        needed[M->n - 1] = 1;
+        for (int32_t j = (int32_t)M->n - 1; j >= 0; --j) {
+            if (!needed[j] || hit[j]) continue;
+            for (int k = 0; k < 4; ++k)
+                if (M->nodes[j].in[k] >= 0) needed[M->nodes[j].in[k]] = 1;
+        }
+        /* Evaluation in storage order: hit roots take their cached value. */
+        uint32_t n_eval = 0;
+        for (uint32_t j = 0; j < M->n; ++j) {
+            if (!needed[j]) continue;
+            if (hit[j]) {
+                for (int k = 0; k < 3; ++k) val[3 * j + k] = hitval[3 * j + k];
+                continue;
+            }
+            const orc_node* nd = &M->nodes[j];
+            orc_eval_node(nd, input_value(nd, 0, val), input_value(nd, 1, val),
+                          input_value(nd, 2, val), sp, &val[3 * j]);
+            n_eval++;
+            if (!c->off && M->is_root[j]) {
+                /* A missed root that was evaluated becomes an insert candidate
+                 * carrying its own value rounded to FP32 (Sec. 3). */
+                if (n_cand == cand_cap) {
+                    cand_cap *= 2;
+                    cand = (orc_candidate*)realloc(cand, cand_cap * sizeof(orc_candidate));
+                }
+                cand[n_cand].cell = rcell[j];
+                cand[n_cand].h2 = rh2[j];
+                for (int k = 0; k < 3; ++k) cand[n_cand].rgb[k] = (float)val[3 * j + k];
+                n_cand++;
+            }
+        }
+        c->stats[7] += n_eval;
+        for (int k = 0; k < 3; ++k) rgb[(size_t)k * n + i] = val[3 * (M->n - 1) + k];
+        if (hits) hits[i] = (uint16_t)n_hit;
+        if (evaluated) evaluated[i] = n_eval;
+    }
+
+    /* Phase I: candidates were produced in ascending (point index, node ID)
+     * order; insert them one at a time in that order (Alg. 1 serialised: the
+     * CAS on an empty entry always succeeds; the first value is kept). */
+    c->stats[3] += n_cand;
+    for (size_t q = 0; q < n_cand; ++q) {
+        uint64_t slot;
+        int r = scan_cell(c, cand[q].cell, cand[q].h2, &slot);
+        if (r == 1) {
+            c->stats[5]++;
+        } else if (r == 0) {
+            c->h2[slot] = cand[q].h2;
+            for (int k = 0; k < 3; ++k) c->rgb[3 * slot + k] = cand[q].rgb[k];
+            c->stats[4]++;
+        } else {
+            c->stats[6]++;
+        }
+    }
+    c->stats[8]++;
+    free(val);
+    free(hit);
+    free(hitval);
+    free(needed);
+    free(rcell);
+    free(rh2);
+    free(cand);
+    return status;
+}
+
+void orc_cache_table(const orc_cache* c, uint32_t* h2, float* rgb) {
+    size_t slots = c->off ? 0 : (size_t)c->n_cells * c->n_entries;
+    if (slots) {
+        memcpy(h2, c->h2, slots * sizeof(uint32_t));
+        memcpy(rgb, c->rgb, 3 * slots * sizeof(float));
+    }
+}
+
+void orc_cache_stats(const orc_cache* c, uint64_t out[ORC_NSTATS]) {
+    memcpy(out, c->stats, sizeof(c->stats));
+}

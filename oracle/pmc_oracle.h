@@ -1,0 +1,162 @@
+/*
+ * pmc_oracle.h -- CPU FP64 oracle of Progressive Material Caching
+ * (Fujieda & Harada, SIGGRAPH Asia 2022 Technical Communications).
+ *
+ * TEST INFRASTRUCTURE ONLY.  This is the plain, slow, sequential statement of
+ * what the GPU path computes.  Only the test suite, the smoke check and the
+ * benchmark's CPU-baseline leg may load it.  It shares no code, header, table
+ * or constant with the CUDA library: every definition here is written again
+ * from the paper and from the published descriptions of the primitives.
+ *
+ * What it follows:
+ *   - Sec. 2: a material is a node network evaluated node by node in storage
+ *     order (the "stack machine" form);
+ *   - Sec. 3: cacheable nodes are the highest nodes whose sub-graph depends on
+ *     no shading-point information other than UV; on a hit the sub-graph is
+ *     skipped, on a miss it is evaluated and its value is stored;
+ *   - Sec. 3.1 and Eq. 1: the descriptor is (material ID, node ID, mip level,
+ *     texel indices) with a virtual texture of 2^lambda texels per axis;
+ *   - Sec. 3.2 and Fig. 3: a fixed table of N_c cells x N_e entries, cell =
+ *     Hash(desc) mod N_c, entry verified by Hash2(desc), first value kept;
+ *   - Algorithm 1: an entry is taken at the first slot whose stored hash is
+ *     either Hash2(desc) or 0.
+ *
+ * Readings where the paper is silent (each listed in the design notes):
+ *   hash pair = SplitMix64 finalizer / MurmurHash3 fmix64 (Sec. 3.2 names
+ *   none); Hash2 == 0 is remapped to 1 because 0 marks an empty entry
+ *   (Alg. 1); the entry loop runs i = 0 .. N_e-1; a batch of shading points
+ *   sees only entries inserted by earlier batches and inserts in ascending
+ *   (point index, node ID) order (a serialisation of the concurrent CAS of
+ *   Alg. 1); the stored value is the inserting point's own value rounded to
+ *   FP32.
+ */
+#ifndef PMC_ORACLE_H
+#define PMC_ORACLE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* One node of a material network (binary layout of the IR format).
+ * in[k] is the index of an earlier node or -1; ip/fp are integer and float
+ * parameters whose meaning depends on op. */
+typedef struct {
+    uint32_t op;
+    int32_t in[4];
+    int32_t ip[4];
+    float fp[16];
+} orc_node;
+
+/* Node operators.  The numbering is part of the IR format. */
+enum {
+    ORC_UV = 0,        /* (u, v, 0)                                    */
+    ORC_POSITION = 1,  /* (px, py, pz)         shading-point dependent */
+    ORC_NORMAL = 2,    /* (nx, ny, nz)         shading-point dependent */
+    ORC_CONST = 3,     /* (fp0, fp1, fp2)                              */
+    ORC_UV_AFFINE = 4, /* 2-D affine map of in0.xy                     */
+    ORC_FBM = 5,       /* fractal sum of 2-D gradient noise            */
+    ORC_VORONOI = 6,   /* Worley F1 distance                           */
+    ORC_CHECKER = 7,   /* two-colour checkerboard                      */
+    ORC_RAMP = 8,      /* colour ramp of 2..4 stops                    */
+    ORC_MIX = 9,       /* a + (b - a) f                                */
+    ORC_ADD = 10,      /* a + b                                        */
+    ORC_MUL = 11,      /* a * b                                        */
+    ORC_POW = 12,      /* max(a,0)^e                                   */
+    ORC_FACING = 13,   /* |dot(in0, d)|                                */
+    ORC_NUM_OPS = 14
+};
+
+/* Dependence classes (Sec. 3): CONST < UV < SP. */
+enum { ORC_CLS_CONST = 0, ORC_CLS_UV = 1, ORC_CLS_SP = 2 };
+
+/* Status codes. */
+enum {
+    ORC_OK = 0,
+    ORC_ERR_ARG = 1,     /* malformed network or argument */
+    ORC_ERR_BADMAT = 2,  /* a shading point names a material that does not exist */
+};
+
+/* ---- published mixers ---------------------------------------------------- */
+uint32_t orc_fmix32(uint32_t h);          /* MurmurHash3 32-bit finaliser     */
+uint64_t orc_fmix64(uint64_t k);          /* MurmurHash3 64-bit finaliser     */
+uint64_t orc_splitmix64_mix(uint64_t z);  /* SplitMix64 output function       */
+
+/* ---- node primitives ------------------------------------------------------ */
+uint32_t orc_lattice_hash(int64_t i, int64_t j, uint32_t seed);
+double orc_fade(double t);
+double orc_perlin(double x, double y, uint32_t seed);
+double orc_fbm(double x, double y, double scale, int octaves, double lacunarity,
+               double gain, uint32_t seed);
+double orc_voronoi_f1(double x, double y, uint32_t seed);
+/* Evaluate one node given its input values (3 doubles each, NULL if unused)
+ * and the shading point sp = (u, v, px, py, pz, nx, ny, nz). */
+void orc_eval_node(const orc_node* nd, const double* a, const double* b, const double* c,
+                   const double sp[8], double out[3]);
+
+/* ---- descriptor and hashes (Sec. 3.1, Eq. 1, Sec. 3.2) -------------------- */
+uint32_t orc_texel(float u, uint32_t level);
+uint64_t orc_key(uint32_t mat, uint32_t node, uint32_t level, float u, float v);
+uint64_t orc_hash1(uint64_t key);
+uint32_t orc_hash2(uint64_t key);
+
+/* ---- network analysis (Sec. 3) ------------------------------------------- */
+/* Validates the network and fills cls[n] (ORC_CLS_*), is_root[n] (0/1).
+ * Returns ORC_OK or ORC_ERR_ARG. */
+int orc_validate(const orc_node* nodes, uint32_t n);
+int orc_analyze(const orc_node* nodes, uint32_t n, uint32_t min_root_nodes,
+                int32_t* cls, uint8_t* is_root, uint32_t* n_roots);
+
+/* ---- single shading point, no cache -------------------------------------- */
+/* Plain evaluation of every node reachable from the output. */
+int orc_eval_point_nocache(const orc_node* nodes, uint32_t n, const double sp[8],
+                           double rgb[3]);
+
+/* ---- progressive cache ----------------------------------------------------- */
+typedef struct orc_cache orc_cache;
+
+/* Optional test hook: replaces Hash/Hash2 for a descriptor. */
+typedef void (*orc_hash_override_fn)(uint64_t key, uint64_t n_cells, uint64_t* cell,
+                                     uint32_t* h2);
+
+/* n_cells == 0 or cache_off != 0 gives plain evaluation (no lookups, no inserts). */
+orc_cache* orc_cache_new(uint64_t n_cells, uint32_t n_entries, uint32_t level,
+                         uint32_t min_root_nodes, int cache_off);
+void orc_cache_free(orc_cache* c);
+/* Copies the networks in (mat_nodes[m] points at n_nodes[m] nodes). */
+int orc_cache_set_materials(orc_cache* c, uint32_t n_mats, const orc_node* const* mat_nodes,
+                            const uint32_t* n_nodes);
+void orc_cache_set_hash_override(orc_cache* c, orc_hash_override_fn fn);
+void orc_cache_reset(orc_cache* c);
+uint32_t orc_cache_n_roots(const orc_cache* c, uint32_t mat);
+/* Root node IDs of a material in ascending order (n_roots entries). */
+void orc_cache_roots(const orc_cache* c, uint32_t mat, uint32_t* out);
+
+/* One progressive pass over n shading points (SoA, FP32 as stored on the GPU).
+ * Outputs: rgb (3*n doubles, SoA r[n] g[n] b[n]); hits (n), may be NULL;
+ * evaluated (n; nodes evaluated per point), may be NULL;
+ * probe_* arrays (sum over points of the point's root count, point-major,
+ * roots in ascending node ID), each may be NULL.
+ * Returns ORC_OK, or ORC_ERR_BADMAT if some mat[i] >= n_mats (those points
+ * get rgb 0, hits 0 and no probes). */
+int orc_run_batch(orc_cache* c, uint64_t n, const float* u, const float* v,
+                  const uint32_t* mat, const float* px, const float* py, const float* pz,
+                  const float* nx, const float* ny, const float* nz, double* rgb,
+                  uint16_t* hits, uint32_t* evaluated, uint64_t* probe_key,
+                  uint64_t* probe_cell, uint32_t* probe_h2, uint8_t* probe_hit);
+
+/* Table contents: h2[N_c*N_e], rgb[3*N_c*N_e] (slot-major r,g,b). */
+void orc_cache_table(const orc_cache* c, uint32_t* h2, float* rgb);
+
+/* Counters, in this order:
+ * 0 lookups, 1 hits, 2 misses, 3 candidates, 4 inserted, 5 dropped_dup,
+ * 6 dropped_full, 7 nodes_evaluated, 8 batches. */
+#define ORC_NSTATS 9
+void orc_cache_stats(const orc_cache* c, uint64_t out[ORC_NSTATS]);
+
+#ifdef __cplusplus
+}
+#endif
+#endif
