@@ -1,0 +1,395 @@
+#!/usr/bin/env python3
+"""Throughput of the progressive material cache on one GB300 (shading points / s).
+
+Workload (one "step"): one progressive frame of 1920x1080 pixels x 16 samples, run as
+16 passes (pmc_eval_batch calls) of 2,073,600 shading points each against a table of
+2^24 slots (2^21 cells x 8 entries, 16 B each) that starts empty; 64 generated
+material networks of 20-200 nodes (20 % shading-point dependent), materials per 8x8
+tile from a Zipf(1.1) law, UV affine per tile with per-sample jitter.  Inputs (1.2 GB
+of points) are resident in HBM and larger than L2; the table is 256 MB.
+
+The JSON line reports the cached throughput (value), the same frame with the cache
+off (uncached), the cached throughput through the host-buffer entry point with the
+copies inside the timed region (e2e), the roofline of the dominant kernel from
+CUDA events on the library's stream, and the CPU oracle on a bounded sample.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2305_07238_gb300 import workload as W  # noqa: E402
+
+METRIC = "shading points/sec (progressive material cache, cached)"
+UNIT = "points/s"
+WIDTH, HEIGHT, SPP = 1920, 1080, 16
+N_MATS, NODES_LO, NODES_HI, SP_FRAC = 64, 20, 200, 0.2
+N_CELLS, N_ENTRIES, LEVEL = 1 << 21, 8, 10
+SAMPLE_ROWS = (0, 40)            # CPU-oracle sample: 40 full-width rows, all 16 passes
+REF_ROWS = (0, 16)               # reference arm: 16 full-width rows per step, all 16 passes
+# ncu capture of k_eval / k_lookup on the same workload (profiles/): DRAM bytes per launch
+NCU_TRAFFIC = {"eval": None, "lookup": None}
+
+FP32_LANES_PER_SM = 128          # Blackwell SM: 4 partitions x 32 FP32 lanes
+N_SMS = 152
+
+
+def workload(seed=0):
+    mats = W.random_materials(N_MATS, NODES_LO, NODES_HI, SP_FRAC, seed=seed)
+    frame = W.Frame(W.FrameSpec(width=WIDTH, height=HEIGHT, n_mats=N_MATS, seed=seed))
+    return mats, frame
+
+
+def config_dict(extra=None):
+    d = {"workload": f"frame {WIDTH}x{HEIGHT}x{SPP}spp, 16 passes of {WIDTH * HEIGHT} points, "
+                     f"{N_MATS} materials {NODES_LO}-{NODES_HI} nodes ({int(SP_FRAC * 100)}% SP), "
+                     f"table {N_CELLS}x{N_ENTRIES} slots (256 MB), Zipf 1.1, lambda {LEVEL}",
+         "points_per_step": WIDTH * HEIGHT * SPP, "batch": WIDTH * HEIGHT, "passes_per_step": SPP,
+         "n_cells": N_CELLS, "n_entries": N_ENTRIES, "uv_level": LEVEL,
+         "l2": "inputs larger than L2 (1.2 GB points + 256 MB table per step)"}
+    if extra:
+        d.update(extra)
+    return d
+
+
+# --------------------------------------------------------------------------------------
+# clocks sampled during the timed region
+# --------------------------------------------------------------------------------------
+class ClockSampler:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index=0):
+        self.index = index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.QUERY}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, ValueError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        self.lines = []
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                out, _ = self.proc.communicate()
+            self.lines = [ln for ln in out.splitlines() if ln.strip()]
+
+    def summary(self):
+        sm, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in getattr(self, "lines", []):
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = max(mx, float(f[2]))
+            except ValueError:
+                continue
+            for name, val in zip(names, f[5:9]):
+                if val.lower() == "active":
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# --------------------------------------------------------------------------------------
+# our arm
+# --------------------------------------------------------------------------------------
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), float(p.get("sm_max_mhz", 2070.0)), "measured"
+    return 6800.0, 2070.0, "fallback"
+
+
+def run_frame(cache, dev_passes, outs, hits, stream):
+    cache.reset(stream)
+    for p in range(SPP):
+        cache.eval_batch(dev_passes[p], outs, hits, stream)
+
+
+def timed_steps(torch, cache, dev_passes, outs, hits, steps, dist_barrier):
+    stream = torch.cuda.current_stream()
+    dist_barrier()
+    torch.cuda.synchronize()
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    for _ in range(steps):
+        run_frame(cache, dev_passes, outs, hits, stream)
+    t1.record(stream)
+    torch.cuda.synchronize()
+    dist_barrier()
+    return t0.elapsed_time(t1) / 1000.0
+
+
+def ours(args, rank, world, local_rank, dist):
+    import torch
+    from paper_2305_07238_gb300 import build as B
+    from paper_2305_07238_gb300 import pmc as P
+
+    B.build()
+    torch.cuda.set_device(local_rank)
+    dev = f"cuda:{local_rank}"
+    barrier = (lambda: dist.barrier()) if dist is not None else (lambda: None)
+
+    mats, frame = workload(seed=rank)
+    passes_host = [frame.points(p) for p in range(SPP)]
+    dev_passes = [P.points_to_device(h, dev) for h in passes_host]
+    n = WIDTH * HEIGHT
+    outs = torch.empty((3, n), dtype=torch.float32, device=dev)
+    hits = torch.empty(n, dtype=torch.int16, device=dev)
+
+    cached = P.Cache(mats, N_CELLS, N_ENTRIES, uv_level=LEVEL, device=local_rank)
+    uncached = P.Cache(mats, N_CELLS, N_ENTRIES, uv_level=LEVEL, flags=P.PMC_CACHE_OFF, device=local_rank)
+
+    # ---- cached, device-resident inputs ---------------------------------------------
+    for _ in range(args.warmup):
+        run_frame(cached, dev_passes, outs, hits, None)
+    cached.sync()
+    s0 = cached.stats()
+    cached.read_timing()
+    cached.set_timing(True)
+    with ClockSampler(local_rank) as clk:
+        secs = timed_steps(torch, cached, dev_passes, outs, hits, args.steps, barrier)
+    cached.set_timing(False)
+    timing = cached.read_timing()
+    s1 = cached.stats()
+    # the timed steps each start from an empty table, so per-step counters repeat
+    pts_total = n * SPP * args.steps
+    secs_max = secs
+    if dist is not None:
+        t = torch.tensor([secs], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        secs_max = float(t.item())
+    value = pts_total * world / secs_max
+    # counters: read directly after the last timed step (reset() zeroes them per frame)
+    frame_stats = s1
+
+    # ---- uncached --------------------------------------------------------------------
+    for _ in range(max(1, args.warmup)):
+        run_frame(uncached, dev_passes, outs, hits, None)
+    uncached.sync()
+    usecs = timed_steps(torch, uncached, dev_passes, outs, hits, args.steps, barrier)
+    if dist is not None:
+        t = torch.tensor([usecs], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        usecs = float(t.item())
+    u_value = pts_total * world / usecs
+
+    # ---- end to end through the host-buffer entry point --------------------------------
+    e2e = e2e_run(torch, P, mats, passes_host, args, local_rank, barrier, dist, dev)
+
+    # ---- roofline of the dominant kernel ------------------------------------------------
+    hbm_peak, sm_mhz_max, peak_kind = peaks()
+    ms = timing["ms"]
+    per_launch_ms = {k: v / max(1, timing["batches"]) for k, v in ms.items()}
+    fp32_peak = N_SMS * FP32_LANES_PER_SM * 2 * sm_mhz_max * 1e6 / 1e12   # TFLOP/s
+    flops_per_frame = frame_stats["flops"]
+    eval_tflops = flops_per_frame * args.steps / (ms["eval"] / 1e3) / 1e12 if ms["eval"] else 0.0
+    look_bytes_frame = (8 * n * SPP                               # u, v of every point
+                        + 16 * frame_stats["slots_probed"]        # slots examined
+                        + 16 * frame_stats["lookups"])            # one 16-B record per probe
+    look_gbs = look_bytes_frame * args.steps / (ms["lookup"] / 1e3) / 1e9 if ms["lookup"] else 0.0
+    kernels = {
+        "eval": {"bound": "alu", "achieved": round(eval_tflops, 3), "peak": round(fp32_peak, 2),
+                 "unit": "TFLOP/s", "frac": round(eval_tflops / fp32_peak, 4),
+                 "ms_per_launch": round(per_launch_ms["eval"], 4), "traffic": NCU_TRAFFIC["eval"]},
+        "lookup": {"bound": "hbm", "achieved": round(look_gbs, 1), "peak": hbm_peak, "unit": "GB/s",
+                   "frac": round(look_gbs / hbm_peak, 4), "ms_per_launch": round(per_launch_ms["lookup"], 4),
+                   "traffic": NCU_TRAFFIC["lookup"]},
+    }
+    dominant = max(("eval", "lookup"), key=lambda k: ms[k])
+    roof = dict(kernels[dominant])
+    roof["kernel"] = "k_eval" if dominant == "eval" else "k_lookup"
+    roof["peak_kind"] = f"{'FP32 lanes x 2 x max SM clock' if dominant == 'eval' else peak_kind + ' HBM copy'}"
+
+    line = {
+        "metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": round(secs_max / args.steps * 1e3, 3), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": config_dict({"parallelism": f"replicas x{world}" if world > 1 else "single GPU"}),
+        "uncached": {"value": round(u_value, 1), "unit": UNIT,
+                     "ms_per_step": round(usecs / args.steps * 1e3, 3),
+                     "speedup_cached_over_uncached": round(value / u_value, 3)},
+        "hit_rate": round(frame_stats["hits"] / max(1, frame_stats["lookups"]), 4),
+        "table": {k: frame_stats[k] for k in ("lookups", "hits", "inserted", "dropped_dup", "dropped_full")},
+        "phase_ms_per_step": {k: round(v / args.steps, 3) for k, v in ms.items()},
+        "roofline": roof,
+        "kernels": kernels,
+        "e2e": e2e,
+        "gpu_launches": int(timing["launches"]),
+        "clocks": clk.summary(),
+    }
+    if rank == 0 and not args.no_cpu_baseline:
+        line["cpu_baseline"], line["max_abs_err_vs_fp64"] = cpu_baseline(P, torch, mats, frame, dev)
+    return line
+
+
+def e2e_run(torch, P, mats, passes_host, args, local_rank, barrier, dist, dev):
+    """Same frame through pmc_eval_batch_host from pinned host buffers: the H2D copy of
+    each pass's points and the D2H copy of its colours and hit counts are timed."""
+    n = WIDTH * HEIGHT
+    pinned = []
+    for h in passes_host:
+        d = {}
+        for k in W.POINT_FIELDS:
+            t = torch.from_numpy(h[k].view(np.int32) if k == "mat" else h[k]).pin_memory()
+            d[k] = t.numpy().view(np.uint32) if k == "mat" else t.numpy()
+        pinned.append(d)
+    rgb_t = torch.empty(3 * n, dtype=torch.float32).pin_memory()
+    hits_t = torch.empty(n, dtype=torch.int16).pin_memory()
+    rgb, hits = rgb_t.numpy(), hits_t.numpy().view(np.uint16)
+    cache = P.Cache(mats, N_CELLS, N_ENTRIES, uv_level=LEVEL, device=local_rank)
+
+    def frame_host():
+        cache.reset()
+        for p in range(SPP):
+            cache.eval_batch_host(pinned[p], rgb, hits)
+
+    for _ in range(max(1, args.warmup)):
+        frame_host()
+    barrier()
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    for _ in range(args.steps):
+        frame_host()
+    torch.cuda.synchronize()
+    secs = time.perf_counter() - t
+    barrier()
+    if dist is not None:
+        tt = torch.tensor([secs], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        secs = float(tt.item())
+    world = dist.get_world_size() if dist is not None else 1
+    cache.close()
+    return {"value": round(n * SPP * args.steps * world / secs, 1), "unit": UNIT,
+            "h2d_bytes_per_step": int(SPP * n * 36), "d2h_bytes_per_step": int(SPP * n * (12 + 2))}
+
+
+def cpu_baseline(P, torch, mats, frame, dev):
+    """The FP64 oracle, single-threaded, on the first SAMPLE_ROWS rows of all 16 passes
+    (same table geometry); the CUDA path runs the same sample for the error figure."""
+    from oracle import oracle as O
+    ref = O.Cache(mats, N_CELLS, N_ENTRIES, level=LEVEL)
+    gpu = P.Cache(mats, N_CELLS, N_ENTRIES, uv_level=LEVEL)
+    npts, secs, err = 0, 0.0, 0.0
+    for p in range(SPP):
+        part = frame.points(p, rows=SAMPLE_ROWS)
+        t = time.perf_counter()
+        r = ref.run_batch(part)
+        secs += time.perf_counter() - t
+        npts += len(part["u"])
+        d = P.points_to_device(part, dev)
+        rgb = torch.empty((3, len(part["u"])), dtype=torch.float32, device=dev)
+        gpu.eval_batch(d, rgb)
+        gpu.sync()
+        err = max(err, float(np.abs(rgb.cpu().numpy() - r["rgb"]).max()))
+    gpu.close()
+    rows = SAMPLE_ROWS[1] - SAMPLE_ROWS[0]
+    return ({"value": round(npts / secs, 1), "unit": UNIT, "cores": 1, "kind": "oracle",
+             "sample": f"rows {SAMPLE_ROWS[0]}-{SAMPLE_ROWS[1]} of all {SPP} passes "
+                       f"({rows * WIDTH} points/pass, {npts} points, {secs:.1f} s), same table size"},
+            err)
+
+
+# --------------------------------------------------------------------------------------
+# reference arm: the CPU oracle as it stands
+# --------------------------------------------------------------------------------------
+def reference(args):
+    from oracle import oracle as O
+    mats, frame = workload(seed=0)
+    passes = [frame.points(p, rows=REF_ROWS) for p in range(SPP)]
+    ref = O.Cache(mats, N_CELLS, N_ENTRIES, level=LEVEL)
+
+    def step():
+        ref.reset()
+        for p in range(SPP):
+            ref.run_batch(passes[p])
+
+    for _ in range(args.warmup):
+        step()
+    t = time.perf_counter()
+    for _ in range(args.steps):
+        step()
+    secs = time.perf_counter() - t
+    npts = sum(len(p["u"]) for p in passes) * args.steps
+    value = npts / secs
+    rows = REF_ROWS[1] - REF_ROWS[0]
+    sample = (f"rows {REF_ROWS[0]}-{REF_ROWS[1]} of all {SPP} passes per step "
+              f"({rows * WIDTH} points/pass), same materials and table size")
+    return {"impl": "reference", "metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(secs / args.steps * 1e3, 3), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": config_dict({"parallelism": "single CPU thread"}),
+            "cpu_baseline": {"value": round(value, 1), "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": round(value, 1), "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+
+    if args.impl == "reference":
+        if rank == 0:
+            print(json.dumps(reference(args)), flush=True)
+        return 0
+
+    dist = None
+    if world > 1:
+        import torch
+        import torch.distributed as tdist
+        torch.cuda.set_device(local_rank)
+        tdist.init_process_group("nccl", device_id=torch.device(f"cuda:{local_rank}"))
+        dist = tdist
+    line = ours(args, rank, world, local_rank, dist)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,248 @@
+/*
+ * pmc.h -- C ABI of the GB300 (sm_103a) Progressive Material Caching library.
+ *
+ * The library evaluates node-based material networks for wavefronts of shading
+ * points and caches the outputs of cacheable nodes in a fixed-size hash table
+ * (Fujieda & Harada, "Progressive Material Caching", SIGGRAPH Asia 2022 Technical
+ * Communications):
+ *   - Sec. 2: a material network is serialised into a linear program that a GPU
+ *     interpreter runs in storage order;
+ *   - Sec. 3: cacheable nodes are the highest nodes whose sub-graph depends on no
+ *     shading-point information other than UV; a hit skips the sub-graph, a miss
+ *     evaluates it and stores the value;
+ *   - Sec. 3.1, Eq. 1: descriptor = (material ID, node ID, mip level, texel indices);
+ *   - Sec. 3.2, Fig. 3: N_c cells x N_e entries, cell = Hash(desc) mod N_c, entry
+ *     checked by Hash2(desc), first inserted value kept;
+ *   - Alg. 1: an entry is taken at the first slot whose stored hash is Hash2(desc)
+ *     or 0.  This library resolves concurrent inserts deterministically: a batch
+ *     looks up against the table as it was when the batch started, then inserts
+ *     its misses in ascending (point index, node ID) order, which it realises with
+ *     rounds of atomicMin on a per-cell claim word.
+ *
+ * Conventions for every entry point:
+ *   - All pointers to shading points and outputs are DEVICE pointers owned by the
+ *     caller unless the name ends in _host.  The library never frees them.
+ *   - The library owns the table, the compiled programs and all scratch memory.
+ *   - Work is enqueued on the caller's CUDA stream (a cudaStream_t passed as void*;
+ *     NULL = legacy default stream).  Argument errors are returned synchronously
+ *     and enqueue nothing.  A CUDA launch error is recorded in the cache object and
+ *     returned by this and every later call (PMC_ERR_CUDA, sticky).
+ *   - Errors found on the device (a material ID out of range) are folded into the
+ *     next pmc_sync / pmc_stats call.
+ *   - A cache object is not thread-safe; distinct cache objects are independent.
+ *   - The first pmc_eval_batch with a given batch size allocates scratch; later
+ *     calls of the same or smaller size allocate nothing.
+ */
+#ifndef PMC_H
+#define PMC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    PMC_OK = 0,
+    PMC_ERR_INVALID_ARG = 1, /* malformed argument, network or shading point     */
+    PMC_ERR_OOM = 2,         /* device or host allocation failed                  */
+    PMC_ERR_CUDA = 3,        /* a CUDA call failed (sticky in the cache object)   */
+    PMC_ERR_TIMEOUT = 4,     /* a bounded device wait ran out                     */
+    PMC_ERR_UNSUPPORTED = 5  /* feature or size outside what this build supports */
+} pmc_status;
+
+/* Opaque cache object: compiled networks, the table and scratch; library-owned. */
+typedef struct pmc_cache pmc_cache;
+
+/* ---- material networks (Sec. 2, Fig. 2) -------------------------------------
+ * A material is an array of nodes in topological order: in[k] names an earlier
+ * node (0 <= in[k] < own index) or is -1.  The last node is the material output.
+ * The node ID used in descriptors is the node's index in this array, as given
+ * (Sec. 3.1), independent of any optimisation the library applies.
+ * Every node value is 3 floats; single-valued nodes repeat their value.  All
+ * outputs except UV, POSITION, NORMAL, CONST and UV_AFFINE are clamped to [0,1].
+ *
+ *  op              inputs          parameters
+ *  PMC_OP_UV        -              -                     (u, v, 0)
+ *  PMC_OP_POSITION  -              -                     (px, py, pz)
+ *  PMC_OP_NORMAL    -              -                     (nx, ny, nz)
+ *  PMC_OP_CONST     -              fp[0..2]              (fp0, fp1, fp2)
+ *  PMC_OP_UV_AFFINE in0            fp[0..5]              (fp0 x + fp1 y + fp4, fp2 x + fp3 y + fp5, 0)
+ *  PMC_OP_FBM       in0 (x, y)     fp0 scale, fp1 lacunarity, fp2 gain, ip0 octaves (1..16), ip1 seed
+ *                                  0.5 + sum_k gain^k noise(scale lac^k (x,y); seed+k) / sum_k gain^k
+ *  PMC_OP_VORONOI   in0 (x, y)     fp0 scale, ip1 seed   Worley F1 at scale (x, y)
+ *  PMC_OP_CHECKER   in0 (x, y)     fp0 scale, fp1..3 colour A, fp4..6 colour B
+ *                                  A if floor(x s) + floor(y s) is even, else B
+ *  PMC_OP_RAMP      in0 (x)        ip0 stops (2..4), fp0..3 positions (ascending, in [0,1]),
+ *                                  fp4.. colours (3 per stop); piecewise linear, constant outside
+ *  PMC_OP_MIX       in0 a, in1 b, in2 f (optional; fp0 if -1)   a + (b - a) clamp(f.x, 0, 1)
+ *  PMC_OP_ADD       in0, in1       -                     a + b
+ *  PMC_OP_MUL       in0, in1       -                     a * b
+ *  PMC_OP_POW       in0            fp0 exponent (> 0)    max(a, 0)^fp0
+ *  PMC_OP_FACING    in0            fp0..2 direction      |dot(a, d)|
+ */
+enum {
+    PMC_OP_UV = 0,
+    PMC_OP_POSITION = 1,
+    PMC_OP_NORMAL = 2,
+    PMC_OP_CONST = 3,
+    PMC_OP_UV_AFFINE = 4,
+    PMC_OP_FBM = 5,
+    PMC_OP_VORONOI = 6,
+    PMC_OP_CHECKER = 7,
+    PMC_OP_RAMP = 8,
+    PMC_OP_MIX = 9,
+    PMC_OP_ADD = 10,
+    PMC_OP_MUL = 11,
+    PMC_OP_POW = 12,
+    PMC_OP_FACING = 13,
+    PMC_NUM_OPS = 14
+};
+
+typedef struct {
+    uint32_t op;
+    int32_t in[4];
+    int32_t ip[4];
+    float fp[16];
+} pmc_node; /* 100 bytes, host memory */
+
+typedef struct {
+    uint32_t n_nodes;      /* 1 .. 65535 */
+    const pmc_node* nodes; /* host memory, copied by pmc_create_cache */
+} pmc_material;
+
+/* ---- cache description (Sec. 3.2, Fig. 3, Alg. 1 inputs N_c and N_e) --------- */
+#define PMC_CACHE_OFF 0x1u        /* evaluate every node, no lookups, no inserts   */
+#define PMC_SORT_BY_MATERIAL 0x2u /* accepted; shading points are always grouped
+                                     by material inside the library               */
+#define PMC_DEBUG_CHECKS 0x4u     /* extra device-side bounds checks               */
+
+typedef struct {
+    uint64_t n_cells;        /* N_c >= 1, < 2^32                                  */
+    uint32_t n_entries;      /* N_e, 1 .. 32; a slot is 16 bytes {hash2, r, g, b} */
+    uint32_t uv_level;       /* lambda of Eq. 1: 2^lambda texels per axis, 0 .. 13 */
+    uint32_t flags;          /* PMC_CACHE_OFF | PMC_DEBUG_CHECKS                   */
+    uint32_t min_root_nodes; /* a cacheable node's sub-graph must hold at least this
+                                many non-input nodes (0 is read as 2)              */
+    int device;              /* CUDA device ordinal                                */
+} pmc_cache_desc;
+
+/* ---- shading points: structure of arrays, n entries each, DEVICE memory ----- */
+typedef struct {
+    const float* u;
+    const float* v;
+    const uint32_t* mat; /* material index < n_mats */
+    const float* px;
+    const float* py;
+    const float* pz;
+    const float* nx;
+    const float* ny;
+    const float* nz;
+    uint64_t n; /* 0 .. 2^28 */
+} pmc_points;
+
+/* Cumulative counters since creation or pmc_reset. */
+typedef struct {
+    uint64_t lookups;         /* (point, cacheable node) probes                     */
+    uint64_t hits;
+    uint64_t misses;
+    uint64_t candidates;      /* evaluated cacheable nodes offered for insertion     */
+    uint64_t inserted;        /* = occupied slots (nothing is ever evicted)          */
+    uint64_t dropped_dup;     /* an entry with the same (cell, hash2) was present    */
+    uint64_t dropped_full;    /* the cell had no empty entry                         */
+    uint64_t nodes_evaluated; /* node instructions executed, summed over points      */
+    uint64_t batches;
+    uint64_t flops;           /* FP32 operations of the executed nodes (FMA = 2)     */
+    uint64_t slots_probed;    /* table slots examined by lookups                     */
+    uint64_t points;
+    uint64_t bad_points;      /* points whose material index was out of range        */
+} pmc_stats_t;
+
+/* Compiles the networks (cacheable-node analysis, constant folding, serialisation;
+ * Sec. 2 and 3), uploads them to `desc->device` and allocates a zeroed table of
+ * n_cells * n_entries 16-byte slots.  Returns PMC_ERR_INVALID_ARG for a malformed
+ * network or description, PMC_ERR_OOM if the table does not fit. */
+pmc_status pmc_create_cache(const pmc_cache_desc* desc, const pmc_material* mats,
+                            uint32_t n_mats, pmc_cache** out);
+
+/* One progressive pass (Sec. 3; Alg. 1 for the inserts) over `pts->n` shading points:
+ * lookup of every cacheable node of every point against the table as it was when
+ * the call was made, evaluation of the nodes still needed, deterministic insert of
+ * the evaluated cacheable nodes.  out_rgb: DEVICE, 3*n floats, planar (r[0..n),
+ * g[0..n), b[0..n)).  out_hits: DEVICE, n uint16 (cacheable nodes found in the
+ * table per point, the Fig. 1d quantity) or NULL.  Asynchronous on `stream`. */
+pmc_status pmc_eval_batch(pmc_cache* cache, const pmc_points* pts, float* out_rgb,
+                          uint16_t* out_hits, void* stream);
+
+/* Same pass with HOST buffers: copies the points in, runs pmc_eval_batch, copies
+ * rgb (and hits if non-NULL) out and waits for `stream`.  Pinned host memory gives
+ * the fastest copies; pageable memory works. */
+pmc_status pmc_eval_batch_host(pmc_cache* cache, const pmc_points* host_pts,
+                               float* host_rgb, uint16_t* host_hits, void* stream);
+
+/* Waits for the last stream used with this cache and reports device-side errors
+ * (PMC_ERR_INVALID_ARG for out-of-range material indices). */
+pmc_status pmc_sync(pmc_cache* cache);
+
+/* Synchronises (as pmc_sync) and copies the counters to `out` (host). */
+pmc_status pmc_stats(pmc_cache* cache, pmc_stats_t* out);
+
+/* Synchronises and copies the table to `host_dst`: n_cells * n_entries slots of
+ * 16 bytes {uint32 hash2 (0 = empty); float r, g, b}.  `bytes` must be at least
+ * that size. */
+pmc_status pmc_table_dump(pmc_cache* cache, void* host_dst, size_t bytes);
+
+/* Synchronises and copies, for the last batch, one 64-bit mask per point (host
+ * memory, n entries, original point order): bit r set when the point's r-th
+ * cacheable node (ascending node ID, r < 64) was found in the table. */
+pmc_status pmc_last_hit_masks(pmc_cache* cache, uint64_t* host_dst, uint64_t n);
+
+/* Empties the table and clears the counters (enqueued on `stream`). */
+pmc_status pmc_reset(pmc_cache* cache, void* stream);
+
+/* Frees everything the cache owns (synchronises first).  NULL is ignored. */
+void pmc_destroy_cache(pmc_cache* cache);
+
+/* Cacheable nodes of a material (ascending node IDs, up to `cap` written) and the
+ * size of its compiled program.  Any output pointer may be NULL. */
+pmc_status pmc_material_info(const pmc_cache* cache, uint32_t mat, uint32_t* n_roots,
+                             uint32_t* roots, uint32_t cap, uint32_t* n_instr,
+                             uint32_t* n_slots);
+
+/* Host-only: compiles one network as pmc_create_cache would (Sec. 2, Sec. 3) and
+ * reports its cacheable nodes (ascending node IDs, up to `cap`), program length
+ * and live-value slots.  Needs no GPU.  Any output pointer may be NULL. */
+pmc_status pmc_analyze_material(const pmc_material* mat, uint32_t min_root_nodes,
+                                uint32_t* n_roots, uint32_t* roots, uint32_t cap,
+                                uint32_t* n_instr, uint32_t* n_slots);
+
+/* Descriptor and table addressing for n (material, node, u, v) tuples, all DEVICE
+ * arrays: key = mat<<48 | node<<32 | level<<26 | iu<<13 | iv with
+ * iu = min(floor(clamp(u,0,1) 2^level), 2^level - 1) (Sec. 3.1, Eq. 1);
+ * cell = Hash(key) mod n_cells, h2 = Hash2(key) (0 remapped to 1) (Alg. 1).
+ * Hash is the SplitMix64 output function, Hash2 the upper half of MurmurHash3's
+ * fmix64 of key xor 0x9E3779B97F4A7C15.  Asynchronous on `stream`. */
+pmc_status pmc_compute_keys(const uint32_t* mat, const uint32_t* node, const float* u,
+                            const float* v, uint64_t n, uint32_t level, uint64_t n_cells,
+                            uint64_t* key, uint64_t* cell, uint32_t* h2, void* stream);
+
+/* Per-phase device timing of later batches, measured with CUDA events recorded on
+ * each batch's stream: 0 = grouping by material (histogram, scan, scatter),
+ * 1 = lookup, 2 = evaluation, 3 = insert rounds, 4 = bookkeeping.  Timing adds two
+ * event records per phase and is off by default. */
+pmc_status pmc_set_timing(pmc_cache* cache, int enable);
+
+/* Synchronises, then returns the milliseconds per phase summed over the batches
+ * enqueued since the last read (ms[5], host), the number of kernels the library
+ * launched in that time and the number of batches; clears the accumulators. */
+pmc_status pmc_read_timing(pmc_cache* cache, double* ms, uint64_t* kernel_launches,
+                           uint64_t* batches);
+
+/* Human-readable name of a status code (static storage). */
+const char* pmc_status_str(pmc_status s);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

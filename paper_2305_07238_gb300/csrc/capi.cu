@@ -1,0 +1,550 @@
+// capi.cu -- the extern "C" entry points declared in include/pmc.h.
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "pmc_internal.h"
+
+using namespace pmc;
+
+struct pmc_cache {
+    pmc_cache_desc desc{};
+    int use_cache = 1;
+    uint32_t n_mats = 0;
+    uint32_t max_roots = 0;
+    uint32_t max_slots = 0;
+    int num_sms = 0;
+    std::vector<MatInfo> mat_info;
+    std::vector<uint32_t> roots;
+    uint32_t prog_len = 0;
+    // device-resident, owned
+    MatInfo* d_mats = nullptr;
+    uint4* d_prog = nullptr;
+    float* d_params = nullptr;
+    uint32_t* d_roots = nullptr;
+    uint4* d_table = nullptr;
+    unsigned long long* d_claims = nullptr;
+    Control* d_ctl = nullptr;
+    unsigned long long* d_stats = nullptr;
+    // per-batch scratch, grown on demand
+    uint64_t cap_points = 0;
+    uint64_t cap_probes = 0;
+    uint32_t* d_seg = nullptr;      // counts | seg_start | probe_base | item_base | cursor
+    float* d_sorted = nullptr;      // 8 planes of cap_points
+    uint32_t* d_sidx = nullptr;
+    float4* d_probes = nullptr;
+    Candidate* d_cands = nullptr;
+    uint32_t* d_lists = nullptr;    // 3 lists of cap_probes
+    // staging for the host-buffer entry point
+    uint64_t cap_host = 0;
+    float* d_hpts = nullptr;        // 8 float planes + 1 uint32 plane
+    float* d_hrgb = nullptr;
+    uint16_t* d_hhits = nullptr;
+    // state
+    cudaStream_t last_stream = nullptr;
+    pmc_status sticky = PMC_OK;
+    uint32_t epoch_host = 0;
+    uint64_t last_n = 0;
+    // timing
+    bool timing = false;
+    std::vector<cudaEvent_t> events;   // (PH_COUNT + 1) per timed batch, in order
+    size_t events_used = 0;
+    uint64_t launches = 0;
+    uint64_t timed_batches = 0;
+};
+
+namespace {
+
+struct DeviceGuard {
+    int prev = -1;
+    bool ok = true;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        if (prev != dev) ok = cudaSetDevice(dev) == cudaSuccess;
+    }
+    ~DeviceGuard() {
+        int cur;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+template <class T>
+pmc_status dalloc(T** p, size_t count) {
+    *p = nullptr;
+    if (count == 0) count = 1;
+    if (cudaMalloc((void**)p, count * sizeof(T)) != cudaSuccess) {
+        cudaGetLastError();
+        *p = nullptr;
+        return PMC_ERR_OOM;
+    }
+    return PMC_OK;
+}
+
+template <class T>
+void dfree(T** p) {
+    if (*p) cudaFree(*p);
+    *p = nullptr;
+}
+
+pmc_status cuda_fail(pmc_cache* c, cudaError_t e) {
+    if (e == cudaSuccess) return PMC_OK;
+    fprintf(stderr, "pmc: CUDA error %d (%s)\n", (int)e, cudaGetErrorString(e));
+    if (c) c->sticky = PMC_ERR_CUDA;
+    return PMC_ERR_CUDA;
+}
+
+void free_scratch(pmc_cache* c) {
+    dfree(&c->d_seg);
+    dfree(&c->d_sorted);
+    dfree(&c->d_sidx);
+    dfree(&c->d_probes);
+    dfree(&c->d_cands);
+    dfree(&c->d_lists);
+    c->cap_points = c->cap_probes = 0;
+}
+
+pmc_status ensure_scratch(pmc_cache* c, uint64_t n) {
+    uint64_t need_probes = c->use_cache ? n * (uint64_t)c->max_roots : 0;
+    if (c->d_seg && n <= c->cap_points && need_probes <= c->cap_probes) return PMC_OK;
+    if (c->last_stream || c->d_seg) cudaDeviceSynchronize();
+    free_scratch(c);
+    uint64_t cap = n > 0 ? n : 1;
+    uint64_t pcap = need_probes > 0 ? need_probes : 1;
+    if (pcap > 0xFFFFFFFFull) return PMC_ERR_UNSUPPORTED;
+    pmc_status s;
+    if ((s = dalloc(&c->d_seg, 5 * ((size_t)c->n_mats + 1))) != PMC_OK) return s;
+    if ((s = dalloc(&c->d_sorted, 8 * (size_t)cap)) != PMC_OK) return s;
+    if ((s = dalloc(&c->d_sidx, (size_t)cap)) != PMC_OK) return s;
+    if ((s = dalloc(&c->d_probes, (size_t)pcap)) != PMC_OK) return s;
+    if ((s = dalloc(&c->d_cands, (size_t)pcap)) != PMC_OK) return s;
+    if ((s = dalloc(&c->d_lists, 3 * (size_t)pcap)) != PMC_OK) return s;
+    c->cap_points = cap;
+    c->cap_probes = pcap;
+    return PMC_OK;
+}
+
+pmc_status fold_device_errors(pmc_cache* c) {
+    uint32_t err = 0;
+    cudaError_t e = cudaMemcpy(&err, &c->d_ctl->err, sizeof(err), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(c, e);
+    if (err) {
+        uint32_t zero = 0;
+        cudaMemcpy(&c->d_ctl->err, &zero, sizeof(zero), cudaMemcpyHostToDevice);
+    }
+    if (err & (ERR_INSERT | ERR_BOUNDS)) {
+        fprintf(stderr, "pmc: internal device check failed (flags %u)\n", err);
+        return PMC_ERR_CUDA;
+    }
+    if (err & ERR_BAD_MAT) return PMC_ERR_INVALID_ARG;
+    return PMC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* pmc_status_str(pmc_status s) {
+    switch (s) {
+    case PMC_OK: return "ok";
+    case PMC_ERR_INVALID_ARG: return "invalid argument";
+    case PMC_ERR_OOM: return "out of memory";
+    case PMC_ERR_CUDA: return "CUDA error";
+    case PMC_ERR_TIMEOUT: return "device wait timed out";
+    case PMC_ERR_UNSUPPORTED: return "unsupported";
+    default: return "unknown status";
+    }
+}
+
+void pmc_destroy_cache(pmc_cache* c) {
+    if (!c) return;
+    {
+        DeviceGuard g(c->desc.device);
+        cudaDeviceSynchronize();
+        for (cudaEvent_t e : c->events) cudaEventDestroy(e);
+        c->events.clear();
+        free_scratch(c);
+        dfree(&c->d_mats);
+        dfree(&c->d_prog);
+        dfree(&c->d_params);
+        dfree(&c->d_roots);
+        dfree(&c->d_table);
+        dfree(&c->d_claims);
+        dfree(&c->d_ctl);
+        dfree(&c->d_stats);
+        dfree(&c->d_hpts);
+        dfree(&c->d_hrgb);
+        dfree(&c->d_hhits);
+    }
+    delete c;
+}
+
+pmc_status pmc_create_cache(const pmc_cache_desc* desc, const pmc_material* mats, uint32_t n_mats,
+                            pmc_cache** out) {
+    if (!desc || !out || (n_mats && !mats)) return PMC_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (n_mats == 0 || n_mats > 65536u) return PMC_ERR_INVALID_ARG;
+    if (desc->uv_level > 13) return PMC_ERR_INVALID_ARG;
+    const bool off = (desc->flags & PMC_CACHE_OFF) != 0;
+    if (!off) {
+        if (desc->n_cells == 0 || desc->n_cells > 0xFFFFFFFFull) return PMC_ERR_INVALID_ARG;
+        if (desc->n_entries == 0 || desc->n_entries > MAX_ENTRIES) return PMC_ERR_INVALID_ARG;
+    }
+    uint32_t min_root = desc->min_root_nodes ? desc->min_root_nodes : 2u;
+
+    pmc_cache* c = new (std::nothrow) pmc_cache();
+    if (!c) return PMC_ERR_OOM;
+    c->desc = *desc;
+    c->desc.min_root_nodes = min_root;
+    c->use_cache = off ? 0 : 1;
+    c->n_mats = n_mats;
+
+    std::vector<uint4> prog;
+    std::vector<float> params;
+    for (uint32_t m = 0; m < n_mats; ++m) {
+        CompiledMaterial cm;
+        const char* why = "";
+        if (!mats[m].nodes || !compile_material(mats[m].nodes, mats[m].n_nodes, min_root, &cm, &why)) {
+            fprintf(stderr, "pmc: material %u rejected: %s\n", m, why);
+            delete c;
+            return PMC_ERR_INVALID_ARG;
+        }
+        MatInfo mi{};
+        mi.prog_start = (uint32_t)prog.size();
+        mi.prog_len = (uint32_t)cm.prog.size();
+        mi.root_base = (uint32_t)c->roots.size();
+        mi.n_roots = (uint32_t)cm.roots.size();
+        mi.out_slot = cm.out_slot;
+        mi.n_slots = cm.n_slots;
+        mi.n_nodes = cm.n_nodes;
+        const uint32_t pbase = (uint32_t)params.size();
+        for (uint4 ins : cm.prog) {
+            if ((ins.x & 0xFFu) != OP_ROOT_BEGIN) ins.w += pbase;
+            prog.push_back(ins);
+        }
+        params.insert(params.end(), cm.params.begin(), cm.params.end());
+        c->roots.insert(c->roots.end(), cm.roots.begin(), cm.roots.end());
+        c->mat_info.push_back(mi);
+        c->max_roots = std::max(c->max_roots, mi.n_roots);
+        c->max_slots = std::max(c->max_slots, mi.n_slots);
+    }
+    c->prog_len = (uint32_t)prog.size();
+    if (eval_smem_bytes(c->max_slots) > 200u * 1024u) {
+        fprintf(stderr, "pmc: a material needs %u live values; this build supports %zu\n",
+                c->max_slots, (size_t)(200u * 1024u) / eval_smem_bytes(1));
+        delete c;
+        return PMC_ERR_UNSUPPORTED;
+    }
+
+    DeviceGuard g(desc->device);
+    if (!g.ok) { delete c; return PMC_ERR_INVALID_ARG; }
+    cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, desc->device);
+    if (c->num_sms <= 0) c->num_sms = 1;
+    pmc_status s = PMC_OK;
+    const uint64_t slots = c->use_cache ? desc->n_cells * desc->n_entries : 0;
+    const uint64_t cells = c->use_cache ? desc->n_cells : 0;
+    if ((s = dalloc(&c->d_mats, n_mats)) != PMC_OK ||
+        (s = dalloc(&c->d_prog, prog.size())) != PMC_OK ||
+        (s = dalloc(&c->d_params, params.size())) != PMC_OK ||
+        (s = dalloc(&c->d_roots, c->roots.size())) != PMC_OK ||
+        (s = dalloc(&c->d_table, slots)) != PMC_OK ||
+        (s = dalloc(&c->d_claims, cells)) != PMC_OK ||
+        (s = dalloc(&c->d_ctl, 1)) != PMC_OK ||
+        (s = dalloc(&c->d_stats, ST_COUNT)) != PMC_OK) {
+        pmc_destroy_cache(c);
+        return s;
+    }
+    cudaError_t e = cudaSuccess;
+    if (e == cudaSuccess) e = cudaMemcpy(c->d_mats, c->mat_info.data(), n_mats * sizeof(MatInfo), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && !prog.empty()) e = cudaMemcpy(c->d_prog, prog.data(), prog.size() * sizeof(uint4), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && !params.empty()) e = cudaMemcpy(c->d_params, params.data(), params.size() * sizeof(float), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && !c->roots.empty()) e = cudaMemcpy(c->d_roots, c->roots.data(), c->roots.size() * sizeof(uint32_t), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = launch_reset(c->d_table, slots, c->d_claims, cells, c->d_ctl, c->d_stats, 0);
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) {
+        cuda_fail(nullptr, e);
+        pmc_destroy_cache(c);
+        return PMC_ERR_CUDA;
+    }
+    *out = c;
+    return PMC_OK;
+}
+
+pmc_status pmc_eval_batch(pmc_cache* c, const pmc_points* pts, float* out_rgb, uint16_t* out_hits,
+                          void* stream) {
+    if (!c || !pts) return PMC_ERR_INVALID_ARG;
+    if (c->sticky != PMC_OK) return c->sticky;
+    const uint64_t n = pts->n;
+    if (n >= MAX_POINTS) return PMC_ERR_UNSUPPORTED;
+    if (n > 0 && (!pts->u || !pts->v || !pts->mat || !pts->px || !pts->py || !pts->pz || !pts->nx ||
+                  !pts->ny || !pts->nz || !out_rgb))
+        return PMC_ERR_INVALID_ARG;
+    DeviceGuard g(c->desc.device);
+    if (!g.ok) return PMC_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    pmc_status st = ensure_scratch(c, n);
+    if (st != PMC_OK) return st;
+    const uint32_t ne = c->desc.n_entries;
+    if (c->use_cache && c->epoch_host + 2 * (ne + 1) > EPOCH_MAX) {
+        // claim words carry a 20-bit epoch; restart it before it runs out
+        cudaError_t e = cudaMemsetAsync(c->d_claims, 0xFF, c->desc.n_cells * sizeof(unsigned long long), s);
+        if (e == cudaSuccess) e = cudaMemsetAsync(&c->d_ctl->epoch, 0, sizeof(uint32_t), s);
+        if (e != cudaSuccess) return cuda_fail(c, e);
+        c->epoch_host = 0;
+    }
+    BatchArgs a{};
+    a.u = pts->u; a.v = pts->v; a.mat = pts->mat;
+    a.px = pts->px; a.py = pts->py; a.pz = pts->pz;
+    a.nx = pts->nx; a.ny = pts->ny; a.nz = pts->nz;
+    a.n = (uint32_t)n;
+    a.out_rgb = out_rgb; a.out_hits = out_hits;
+    a.mats = c->d_mats; a.n_mats = c->n_mats;
+    a.prog = c->d_prog; a.params = c->d_params; a.roots = c->d_roots;
+    a.max_slots = c->max_slots ? c->max_slots : 1;
+    const size_t M1 = (size_t)c->n_mats + 1;
+    a.counts = c->d_seg; a.seg_start = c->d_seg + M1; a.probe_base = c->d_seg + 2 * M1;
+    a.item_base = c->d_seg + 3 * M1; a.cursor = c->d_seg + 4 * M1;
+    const size_t P = c->cap_points;
+    a.su = c->d_sorted; a.sv = c->d_sorted + P; a.spx = c->d_sorted + 2 * P; a.spy = c->d_sorted + 3 * P;
+    a.spz = c->d_sorted + 4 * P; a.snx = c->d_sorted + 5 * P; a.sny = c->d_sorted + 6 * P;
+    a.snz = c->d_sorted + 7 * P; a.sidx = c->d_sidx;
+    a.table = c->d_table; a.claims = c->d_claims;
+    a.n_cells = c->use_cache ? c->desc.n_cells : 1; a.n_entries = c->use_cache ? ne : 1;
+    a.level = c->desc.uv_level;
+    const uint64_t nc = a.n_cells;
+    a.cells_pow2_mask = (nc > 1 && (nc & (nc - 1)) == 0) ? (uint32_t)(nc - 1) : 0u;
+    a.use_cache = c->use_cache; a.debug = (c->desc.flags & PMC_DEBUG_CHECKS) != 0;
+    a.probes = c->d_probes; a.probe_cap = (uint32_t)c->cap_probes;
+    a.cands = c->d_cands;
+    a.lists[0] = c->d_lists; a.lists[1] = c->d_lists + c->cap_probes; a.lists[2] = c->d_lists + 2 * c->cap_probes;
+    a.ctl = c->d_ctl; a.stats = c->d_stats;
+    cudaEvent_t* ev = nullptr;
+    if (c->timing) {
+        while (c->events.size() < c->events_used + PH_COUNT + 1) {
+            cudaEvent_t x;
+            cudaError_t ce = cudaEventCreate(&x);
+            if (ce != cudaSuccess) return cuda_fail(c, ce);
+            c->events.push_back(x);
+        }
+        ev = c->events.data() + c->events_used;
+        c->events_used += PH_COUNT + 1;
+        c->timed_batches++;
+    }
+    cudaError_t e = launch_batch(a, s, c->num_sms, ev, &c->launches);
+    if (e != cudaSuccess) return cuda_fail(c, e);
+    if (c->use_cache) c->epoch_host += ne + 1;
+    c->last_stream = s;
+    c->last_n = n;
+    return PMC_OK;
+}
+
+pmc_status pmc_eval_batch_host(pmc_cache* c, const pmc_points* hp, float* host_rgb, uint16_t* host_hits,
+                               void* stream) {
+    if (!c || !hp) return PMC_ERR_INVALID_ARG;
+    if (c->sticky != PMC_OK) return c->sticky;
+    const uint64_t n = hp->n;
+    if (n >= MAX_POINTS) return PMC_ERR_UNSUPPORTED;
+    if (n > 0 && (!hp->u || !hp->v || !hp->mat || !hp->px || !hp->py || !hp->pz || !hp->nx || !hp->ny ||
+                  !hp->nz || !host_rgb))
+        return PMC_ERR_INVALID_ARG;
+    DeviceGuard g(c->desc.device);
+    if (!g.ok) return PMC_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (n > c->cap_host) {
+        if (c->last_stream || c->d_hpts) cudaDeviceSynchronize();
+        dfree(&c->d_hpts);
+        dfree(&c->d_hrgb);
+        dfree(&c->d_hhits);
+        c->cap_host = 0;
+        pmc_status st;
+        if ((st = dalloc(&c->d_hpts, 9 * (size_t)n)) != PMC_OK) return st;
+        if ((st = dalloc(&c->d_hrgb, 3 * (size_t)n)) != PMC_OK) return st;
+        if ((st = dalloc(&c->d_hhits, (size_t)n)) != PMC_OK) return st;
+        c->cap_host = n;
+    }
+    const size_t C = c->cap_host;
+    float* d = c->d_hpts;
+    const void* src[9] = {hp->u, hp->v, hp->mat, hp->px, hp->py, hp->pz, hp->nx, hp->ny, hp->nz};
+    cudaError_t e = cudaSuccess;
+    for (int k = 0; k < 9 && e == cudaSuccess && n; ++k)
+        e = cudaMemcpyAsync(d + k * C, src[k], n * 4, cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return cuda_fail(c, e);
+    pmc_points dp{d, d + C, (const uint32_t*)(d + 2 * C), d + 3 * C, d + 4 * C, d + 5 * C,
+                  d + 6 * C, d + 7 * C, d + 8 * C, n};
+    pmc_status st = pmc_eval_batch(c, &dp, c->d_hrgb, host_hits ? c->d_hhits : nullptr, stream);
+    if (st != PMC_OK) return st;
+    for (int k = 0; k < 3 && e == cudaSuccess && n; ++k)
+        e = cudaMemcpyAsync(host_rgb + k * n, c->d_hrgb + k * n, n * 4, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess && host_hits && n)
+        e = cudaMemcpyAsync(host_hits, c->d_hhits, n * 2, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(c, e);
+    return fold_device_errors(c);
+}
+
+pmc_status pmc_sync(pmc_cache* c) {
+    if (!c) return PMC_ERR_INVALID_ARG;
+    if (c->sticky != PMC_OK) return c->sticky;
+    DeviceGuard g(c->desc.device);
+    cudaError_t e = cudaStreamSynchronize(c->last_stream);
+    if (e != cudaSuccess) return cuda_fail(c, e);
+    return fold_device_errors(c);
+}
+
+pmc_status pmc_stats(pmc_cache* c, pmc_stats_t* out) {
+    if (!c || !out) return PMC_ERR_INVALID_ARG;
+    pmc_status st = pmc_sync(c);
+    unsigned long long v[ST_COUNT];
+    DeviceGuard g(c->desc.device);
+    cudaError_t e = cudaMemcpy(v, c->d_stats, sizeof(v), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(c, e);
+    out->lookups = v[ST_LOOKUPS];
+    out->hits = v[ST_HITS];
+    out->misses = v[ST_MISSES];
+    out->candidates = v[ST_CANDIDATES];
+    out->inserted = v[ST_INSERTED];
+    out->dropped_dup = v[ST_DUP];
+    out->dropped_full = v[ST_FULL];
+    out->nodes_evaluated = v[ST_NODES];
+    out->batches = v[ST_BATCHES];
+    out->flops = v[ST_FLOPS];
+    out->slots_probed = v[ST_SLOTS];
+    out->points = v[ST_POINTS];
+    out->bad_points = v[ST_BAD];
+    return st;
+}
+
+pmc_status pmc_table_dump(pmc_cache* c, void* host_dst, size_t bytes) {
+    if (!c || !host_dst) return PMC_ERR_INVALID_ARG;
+    const size_t need = c->use_cache ? (size_t)c->desc.n_cells * c->desc.n_entries * 16u : 0;
+    if (bytes < need) return PMC_ERR_INVALID_ARG;
+    pmc_status st = pmc_sync(c);
+    if (st == PMC_ERR_CUDA) return st;
+    DeviceGuard g(c->desc.device);
+    if (need) {
+        cudaError_t e = cudaMemcpy(host_dst, c->d_table, need, cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) return cuda_fail(c, e);
+    }
+    return st;
+}
+
+pmc_status pmc_last_hit_masks(pmc_cache* c, uint64_t* host_dst, uint64_t n) {
+    if (!c || (n && !host_dst)) return PMC_ERR_INVALID_ARG;
+    if (n != c->last_n) return PMC_ERR_INVALID_ARG;
+    pmc_status st = pmc_sync(c);
+    if (st == PMC_ERR_CUDA) return st;
+    std::memset(host_dst, 0, n * sizeof(uint64_t));
+    if (!c->use_cache || n == 0) return st;
+    DeviceGuard g(c->desc.device);
+    const size_t M1 = (size_t)c->n_mats + 1;
+    std::vector<uint32_t> seg(5 * M1);
+    std::vector<uint32_t> sidx(n);
+    uint32_t total = 0;
+    cudaError_t e = cudaMemcpy(seg.data(), c->d_seg, seg.size() * 4, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemcpy(sidx.data(), c->d_sidx, n * 4, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemcpy(&total, &c->d_ctl->total_probes, 4, cudaMemcpyDeviceToHost);
+    std::vector<float4> probes(total ? total : 1);
+    if (e == cudaSuccess && total) e = cudaMemcpy(probes.data(), c->d_probes, (size_t)total * 16, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(c, e);
+    const uint32_t* counts = seg.data();
+    const uint32_t* seg_start = seg.data() + M1;
+    const uint32_t* pbase = seg.data() + 2 * M1;
+    for (uint32_t m = 0; m < c->n_mats; ++m) {
+        const uint32_t cnt = counts[m], K = std::min<uint32_t>(c->mat_info[m].n_roots, 64u);
+        for (uint32_t j = 0; j < cnt; ++j) {
+            uint32_t orig = sidx[seg_start[m] + j];
+            uint64_t mask = 0;
+            for (uint32_t r = 0; r < K; ++r) {
+                float w = probes[(size_t)pbase[m] + (size_t)r * cnt + j].w;
+                uint32_t bits;
+                std::memcpy(&bits, &w, 4);
+                if (bits == 1u) mask |= 1ull << r;
+            }
+            if (orig < n) host_dst[orig] = mask;
+        }
+    }
+    return st;
+}
+
+pmc_status pmc_reset(pmc_cache* c, void* stream) {
+    if (!c) return PMC_ERR_INVALID_ARG;
+    if (c->sticky != PMC_OK) return c->sticky;
+    DeviceGuard g(c->desc.device);
+    const uint64_t slots = c->use_cache ? c->desc.n_cells * c->desc.n_entries : 0;
+    const uint64_t cells = c->use_cache ? c->desc.n_cells : 0;
+    cudaError_t e = launch_reset(c->d_table, slots, c->d_claims, cells, c->d_ctl, c->d_stats,
+                                 (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(c, e);
+    c->epoch_host = 0;
+    c->last_stream = (cudaStream_t)stream;
+    return PMC_OK;
+}
+
+pmc_status pmc_set_timing(pmc_cache* c, int enable) {
+    if (!c) return PMC_ERR_INVALID_ARG;
+    c->timing = enable != 0;
+    return PMC_OK;
+}
+
+pmc_status pmc_read_timing(pmc_cache* c, double* ms, uint64_t* kernel_launches, uint64_t* batches) {
+    if (!c) return PMC_ERR_INVALID_ARG;
+    pmc_status st = pmc_sync(c);
+    if (st == PMC_ERR_CUDA) return st;
+    DeviceGuard g(c->desc.device);
+    double acc[PH_COUNT] = {0, 0, 0, 0, 0};
+    for (size_t b = 0; b + PH_COUNT + 1 <= c->events_used; b += PH_COUNT + 1) {
+        for (int k = 0; k < PH_COUNT; ++k) {
+            float t = 0.0f;
+            cudaError_t e = cudaEventElapsedTime(&t, c->events[b + k], c->events[b + k + 1]);
+            if (e != cudaSuccess) return cuda_fail(c, e);
+            acc[k] += t;
+        }
+    }
+    if (ms)
+        for (int k = 0; k < PH_COUNT; ++k) ms[k] = acc[k];
+    if (kernel_launches) *kernel_launches = c->launches;
+    if (batches) *batches = c->timed_batches;
+    c->events_used = 0;
+    c->launches = 0;
+    c->timed_batches = 0;
+    return st;
+}
+
+pmc_status pmc_material_info(const pmc_cache* c, uint32_t mat, uint32_t* n_roots, uint32_t* roots,
+                             uint32_t cap, uint32_t* n_instr, uint32_t* n_slots) {
+    if (!c || mat >= c->n_mats) return PMC_ERR_INVALID_ARG;
+    const MatInfo& mi = c->mat_info[mat];
+    if (n_roots) *n_roots = mi.n_roots;
+    if (roots)
+        for (uint32_t r = 0; r < mi.n_roots && r < cap; ++r) roots[r] = c->roots[mi.root_base + r];
+    if (n_instr) *n_instr = mi.prog_len;
+    if (n_slots) *n_slots = mi.n_slots;
+    return PMC_OK;
+}
+
+pmc_status pmc_analyze_material(const pmc_material* mat, uint32_t min_root_nodes, uint32_t* n_roots,
+                                uint32_t* roots, uint32_t cap, uint32_t* n_instr, uint32_t* n_slots) {
+    if (!mat || !mat->nodes) return PMC_ERR_INVALID_ARG;
+    CompiledMaterial cm;
+    const char* why = "";
+    if (!compile_material(mat->nodes, mat->n_nodes, min_root_nodes ? min_root_nodes : 2u, &cm, &why))
+        return PMC_ERR_INVALID_ARG;
+    if (n_roots) *n_roots = (uint32_t)cm.roots.size();
+    if (roots)
+        for (size_t r = 0; r < cm.roots.size() && r < cap; ++r) roots[r] = cm.roots[r];
+    if (n_instr) *n_instr = (uint32_t)cm.prog.size();
+    if (n_slots) *n_slots = cm.n_slots;
+    return PMC_OK;
+}
+
+pmc_status pmc_compute_keys(const uint32_t* mat, const uint32_t* node, const float* u, const float* v,
+                            uint64_t n, uint32_t level, uint64_t n_cells, uint64_t* key, uint64_t* cell,
+                            uint32_t* h2, void* stream) {
+    if (level > 13 || n_cells == 0) return PMC_ERR_INVALID_ARG;
+    if (n && (!mat || !node || !u || !v || !key || !cell || !h2)) return PMC_ERR_INVALID_ARG;
+    cudaError_t e = launch_keys(mat, node, u, v, n, level, n_cells, key, cell, h2, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(nullptr, e);
+    return PMC_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,136 @@
+// pmc_internal.h -- data layouts shared by the library's host compiler, kernels and
+// C-ABI layer.  Not installed; the public interface is include/pmc.h.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+#include <vector>
+
+#include "pmc.h"
+
+namespace pmc {
+
+// ---- compiled program ----------------------------------------------------------------
+// A material is serialised (Sec. 2) into a linear program of 16-byte instructions run
+// by one warp-uniform interpreter.  Node values live in per-lane "slots" (a register
+// file in shared memory) assigned by linear-scan allocation.
+//
+//   x: op (bits 0-7) | flags (8-15) | cost in FP32 flops (16-31)
+//   y: out slot (0-15) | in0 slot (16-31)         ROOT_BEGIN: out slot | root ordinal
+//   z: in1 slot (0-15) | in2 slot (16-31)         ROOT_BEGIN: node ID
+//   w: offset of the node's parameters in the parameter pool
+//                                                 ROOT_BEGIN: number of instructions
+//                                                 that follow up to the root itself
+//
+// A cacheable node r with the nodes only it needs (its exclusive sub-graph) forms a
+// contiguous block: ROOT_BEGIN(r), the exclusive nodes, then r flagged FLAG_ROOT.  A
+// lane whose lookup hit takes the cached value at ROOT_BEGIN and skips the block.
+constexpr uint32_t OP_ROOT_BEGIN = 32;
+constexpr uint32_t FLAG_ROOT = 1;
+
+struct MatInfo {
+    uint32_t prog_start;  // first instruction in the program pool
+    uint32_t prog_len;
+    uint32_t root_base;   // first entry in the root-node table
+    uint32_t n_roots;
+    uint32_t out_slot;    // slot holding the material output after the program
+    uint32_t n_slots;
+    uint32_t n_nodes;
+    uint32_t pad;
+};
+
+struct CompiledMaterial {
+    std::vector<uint4> prog;
+    std::vector<float> params;     // parameter offsets in prog are relative to this
+    std::vector<uint32_t> roots;   // node IDs of cacheable nodes, ascending
+    uint32_t out_slot = 0;
+    uint32_t n_slots = 0;
+    uint32_t n_nodes = 0;
+};
+
+// Compiles one network.  Returns false (with a reason) for a malformed network.
+bool compile_material(const pmc_node* nodes, uint32_t n, uint32_t min_root_nodes,
+                      CompiledMaterial* out, const char** why);
+
+// FP32 flops of one executed node (FMA counted as 2), from the device formulas.
+uint32_t node_cost(const pmc_node& nd);
+
+// ---- insert candidates -----------------------------------------------------------------
+struct __align__(16) Candidate {
+    unsigned long long prio;  // (point index << 16) | node ID: the sequential order
+    uint32_t cell;
+    uint32_t h2;
+    float r, g, b;
+    uint32_t target;          // slot index chosen in the current round
+};
+static_assert(sizeof(Candidate) == 32, "candidate is one 32-byte sector");
+
+constexpr uint32_t MAX_ENTRIES = 32;
+constexpr uint32_t EPOCH_BITS = 20;
+constexpr uint32_t EPOCH_MAX = (1u << EPOCH_BITS) - 1;
+constexpr uint64_t MAX_POINTS = 1ull << 28;
+
+// Device-side control block of one cache object.
+struct Control {
+    uint32_t n_items;           // warp work items of the current batch
+    uint32_t total_probes;
+    uint32_t n_cand;            // candidates emitted by the evaluation
+    uint32_t epoch;             // claim epoch of round 0 of the current batch
+    uint32_t err;               // ERR_* bits
+    uint32_t pad[3];
+    uint32_t mid_count[MAX_ENTRIES + 2];
+    uint32_t out_count[MAX_ENTRIES + 2];
+};
+
+constexpr uint32_t ERR_BAD_MAT = 1;
+constexpr uint32_t ERR_INSERT = 2;
+constexpr uint32_t ERR_BOUNDS = 4;
+
+// Counter indices in the device stats array.
+enum {
+    ST_LOOKUPS = 0, ST_HITS, ST_MISSES, ST_CANDIDATES, ST_INSERTED, ST_DUP, ST_FULL,
+    ST_NODES, ST_BATCHES, ST_FLOPS, ST_SLOTS, ST_POINTS, ST_BAD, ST_COUNT = 16
+};
+
+// Everything a batch's kernels need, by value.
+struct BatchArgs {
+    // inputs (caller-owned device SoA)
+    const float* u; const float* v; const uint32_t* mat;
+    const float* px; const float* py; const float* pz;
+    const float* nx; const float* ny; const float* nz;
+    uint32_t n;
+    // outputs
+    float* out_rgb; uint16_t* out_hits;
+    // materials
+    const MatInfo* mats; uint32_t n_mats;
+    const uint4* prog; const float* params; const uint32_t* roots;
+    uint32_t max_slots;
+    // sort / segments
+    uint32_t* counts; uint32_t* seg_start; uint32_t* probe_base; uint32_t* item_base;
+    uint32_t* cursor;
+    float* su; float* sv; float* spx; float* spy; float* spz;
+    float* snx; float* sny; float* snz; uint32_t* sidx;
+    // cache
+    uint4* table; unsigned long long* claims;
+    uint64_t n_cells; uint32_t n_entries; uint32_t level; uint32_t cells_pow2_mask;
+    int use_cache; int debug;
+    float4* probes; uint32_t probe_cap;
+    Candidate* cands; uint32_t* lists[3];
+    Control* ctl; unsigned long long* stats;
+};
+
+// Phases timed by the optional CUDA events of a batch.
+enum { PH_SORT = 0, PH_LOOKUP, PH_EVAL, PH_INSERT, PH_FINISH, PH_COUNT };
+
+// Launch sequence of one batch (kernels.cu).  `ev`, if not null, holds PH_COUNT + 1
+// events recorded on `s` at the phase boundaries; `*launches` counts kernel launches.
+cudaError_t launch_batch(const BatchArgs& a, cudaStream_t s, int num_sms, cudaEvent_t* ev,
+                         uint64_t* launches);
+cudaError_t launch_reset(uint4* table, size_t slots, unsigned long long* claims, size_t cells,
+                         Control* ctl, unsigned long long* stats, cudaStream_t s);
+cudaError_t launch_keys(const uint32_t* mat, const uint32_t* node, const float* u,
+                        const float* v, uint64_t n, uint32_t level, uint64_t n_cells,
+                        uint64_t* key, uint64_t* cell, uint32_t* h2, cudaStream_t s);
+size_t eval_smem_bytes(uint32_t max_slots);
+
+}  // namespace pmc

@@ -1,0 +1,267 @@
+"""Thin ctypes binding of libpmc.so (include/pmc.h): argument marshalling only.
+
+Every step of the pass runs in the library's CUDA kernels.  Device buffers are torch
+tensors (PyTorch supplies device memory and streams); host buffers are numpy arrays.
+Loading fails loudly when the library has not been built: there is no fallback path.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from .workload import NODE_DTYPE, POINT_FIELDS
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_build", "libpmc.so")
+
+PMC_OK, PMC_ERR_INVALID_ARG, PMC_ERR_OOM, PMC_ERR_CUDA, PMC_ERR_TIMEOUT, PMC_ERR_UNSUPPORTED = range(6)
+PMC_CACHE_OFF = 0x1
+PMC_SORT_BY_MATERIAL = 0x2
+PMC_DEBUG_CHECKS = 0x4
+
+EXPORTED = (
+    "pmc_create_cache", "pmc_eval_batch", "pmc_eval_batch_host", "pmc_sync", "pmc_stats",
+    "pmc_table_dump", "pmc_last_hit_masks", "pmc_reset", "pmc_destroy_cache",
+    "pmc_material_info", "pmc_analyze_material", "pmc_compute_keys", "pmc_set_timing",
+    "pmc_read_timing", "pmc_status_str",
+)
+PHASES = ("sort", "lookup", "eval", "insert", "finish")
+
+
+class PmcError(RuntimeError):
+    def __init__(self, status, what):
+        super().__init__(f"{what}: {status_str(status)} ({status})")
+        self.status = status
+
+
+class _Node(C.Structure):
+    _fields_ = [("op", C.c_uint32), ("inp", C.c_int32 * 4), ("ip", C.c_int32 * 4), ("fp", C.c_float * 16)]
+
+
+class _Material(C.Structure):
+    _fields_ = [("n_nodes", C.c_uint32), ("nodes", C.c_void_p)]
+
+
+class _Desc(C.Structure):
+    _fields_ = [("n_cells", C.c_uint64), ("n_entries", C.c_uint32), ("uv_level", C.c_uint32),
+                ("flags", C.c_uint32), ("min_root_nodes", C.c_uint32), ("device", C.c_int)]
+
+
+class _Points(C.Structure):
+    _fields_ = [(k, C.c_void_p) for k in POINT_FIELDS] + [("n", C.c_uint64)]
+
+
+STAT_FIELDS = ("lookups", "hits", "misses", "candidates", "inserted", "dropped_dup", "dropped_full",
+               "nodes_evaluated", "batches", "flops", "slots_probed", "points", "bad_points")
+
+
+class _Stats(C.Structure):
+    _fields_ = [(k, C.c_uint64) for k in STAT_FIELDS]
+
+
+assert C.sizeof(_Node) == NODE_DTYPE.itemsize == 100
+
+_lib = None
+
+
+def load():
+    """Loads libpmc.so; raises if it was not built (call __graft_entry__.build())."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"libpmc.so is not built ({LIB_PATH}); run paper_2305_07238_gb300.build.build()")
+    L = C.CDLL(LIB_PATH)
+    vp, u32, u64, st = C.c_void_p, C.c_uint32, C.c_uint64, C.c_int
+    L.pmc_create_cache.argtypes = [vp, vp, u32, vp]
+    L.pmc_create_cache.restype = st
+    L.pmc_eval_batch.argtypes = [vp, vp, vp, vp, vp]
+    L.pmc_eval_batch.restype = st
+    L.pmc_eval_batch_host.argtypes = [vp, vp, vp, vp, vp]
+    L.pmc_eval_batch_host.restype = st
+    L.pmc_sync.argtypes = [vp]
+    L.pmc_sync.restype = st
+    L.pmc_stats.argtypes = [vp, vp]
+    L.pmc_stats.restype = st
+    L.pmc_table_dump.argtypes = [vp, vp, C.c_size_t]
+    L.pmc_table_dump.restype = st
+    L.pmc_last_hit_masks.argtypes = [vp, vp, u64]
+    L.pmc_last_hit_masks.restype = st
+    L.pmc_reset.argtypes = [vp, vp]
+    L.pmc_reset.restype = st
+    L.pmc_destroy_cache.argtypes = [vp]
+    L.pmc_destroy_cache.restype = None
+    L.pmc_material_info.argtypes = [vp, u32, vp, vp, u32, vp, vp]
+    L.pmc_material_info.restype = st
+    L.pmc_analyze_material.argtypes = [vp, u32, vp, vp, u32, vp, vp]
+    L.pmc_analyze_material.restype = st
+    L.pmc_compute_keys.argtypes = [vp, vp, vp, vp, u64, u32, u64, vp, vp, vp, vp]
+    L.pmc_compute_keys.restype = st
+    L.pmc_set_timing.argtypes = [vp, C.c_int]
+    L.pmc_set_timing.restype = st
+    L.pmc_read_timing.argtypes = [vp, vp, vp, vp]
+    L.pmc_read_timing.restype = st
+    L.pmc_status_str.argtypes = [st]
+    L.pmc_status_str.restype = C.c_char_p
+    _lib = L
+    return L
+
+
+def status_str(s: int) -> str:
+    try:
+        return load().pmc_status_str(s).decode()
+    except Exception:  # library missing: still report the number
+        return f"status {s}"
+
+
+def _check(s, what):
+    if s != PMC_OK:
+        raise PmcError(s, what)
+
+
+def _stream_handle(stream):
+    if stream is None:
+        import torch
+        return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, int):
+        return C.c_void_p(stream)
+    return C.c_void_p(stream.cuda_stream)
+
+
+def _dptr(t):
+    return None if t is None else C.c_void_p(t.data_ptr())
+
+
+def points_to_device(pts: dict, device="cuda"):
+    """Copies a host point batch (numpy SoA) into torch device tensors."""
+    import torch
+    out = {}
+    for k in POINT_FIELDS:
+        a = np.ascontiguousarray(pts[k])
+        t = torch.from_numpy(a.view(np.int32) if k == "mat" else a)
+        out[k] = t.to(device)
+    return out
+
+
+class Cache:
+    """A cache object of libpmc: compiled materials + a table of n_cells x n_entries slots."""
+
+    def __init__(self, materials, n_cells, n_entries, uv_level=10, flags=0, min_root_nodes=2, device=0):
+        L = load()
+        self._mats = [np.ascontiguousarray(m, dtype=NODE_DTYPE) for m in materials]
+        arr = (_Material * len(self._mats))()
+        for i, m in enumerate(self._mats):
+            arr[i].n_nodes = len(m)
+            arr[i].nodes = m.ctypes.data
+        desc = _Desc(n_cells, n_entries, uv_level, flags, min_root_nodes, device)
+        h = C.c_void_p()
+        _check(L.pmc_create_cache(C.byref(desc), arr, len(self._mats), C.byref(h)), "pmc_create_cache")
+        self._h = h
+        self.n_cells, self.n_entries, self.uv_level = n_cells, n_entries, uv_level
+        self.flags, self.device = flags, device
+        self.n_mats = len(self._mats)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().pmc_destroy_cache(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def cache_off(self):
+        return bool(self.flags & PMC_CACHE_OFF)
+
+    # ---- the pass --------------------------------------------------------------------
+    def eval_batch(self, pts, out_rgb, out_hits=None, stream=None):
+        """pts: dict of device tensors (float32; mat int32/uint32); out_rgb: float32 (3, n)
+        device tensor; out_hits: int16/uint16 (n,) device tensor or None."""
+        n = int(pts["u"].numel())
+        p = _Points(*[_dptr(pts[k]) for k in POINT_FIELDS], n)
+        _check(load().pmc_eval_batch(self._h, C.byref(p), _dptr(out_rgb), _dptr(out_hits),
+                                     _stream_handle(stream)), "pmc_eval_batch")
+
+    def eval_batch_host(self, pts: dict, out_rgb: np.ndarray, out_hits: np.ndarray | None = None,
+                        stream=None):
+        """Host buffers in and out; returns once the results are in out_rgb/out_hits."""
+        arrs = [np.ascontiguousarray(pts[k]) for k in POINT_FIELDS]
+        n = len(arrs[0])
+        p = _Points(*[a.ctypes.data for a in arrs], n)
+        _check(load().pmc_eval_batch_host(self._h, C.byref(p), out_rgb.ctypes.data,
+                                          None if out_hits is None else out_hits.ctypes.data,
+                                          _stream_handle(stream)), "pmc_eval_batch_host")
+
+    def sync(self):
+        _check(load().pmc_sync(self._h), "pmc_sync")
+
+    def reset(self, stream=None):
+        _check(load().pmc_reset(self._h, _stream_handle(stream)), "pmc_reset")
+
+    # ---- inspection ------------------------------------------------------------------
+    def stats(self, check=True) -> dict:
+        s = _Stats()
+        rc = load().pmc_stats(self._h, C.byref(s))
+        if check:
+            _check(rc, "pmc_stats")
+        return {k: int(getattr(s, k)) for k in STAT_FIELDS}
+
+    def table(self):
+        """(h2 uint32[slots], rgb float32[slots, 3]) copied from the device."""
+        slots = 0 if self.cache_off else self.n_cells * self.n_entries
+        buf = np.zeros((max(slots, 1), 4), dtype=np.uint32)
+        _check(load().pmc_table_dump(self._h, buf.ctypes.data, buf.nbytes), "pmc_table_dump")
+        buf = buf[:slots]
+        return buf[:, 0].copy(), buf[:, 1:].view(np.float32).copy()
+
+    def last_hit_masks(self, n: int) -> np.ndarray:
+        out = np.zeros(max(n, 1), dtype=np.uint64)
+        _check(load().pmc_last_hit_masks(self._h, out.ctypes.data, n), "pmc_last_hit_masks")
+        return out[:n]
+
+    def set_timing(self, on: bool):
+        _check(load().pmc_set_timing(self._h, int(bool(on))), "pmc_set_timing")
+
+    def read_timing(self) -> dict:
+        """Per-phase milliseconds (CUDA events) since the last read, kernel launches, batches."""
+        ms = np.zeros(len(PHASES), dtype=np.float64)
+        nl, nb = C.c_uint64(), C.c_uint64()
+        _check(load().pmc_read_timing(self._h, ms.ctypes.data, C.byref(nl), C.byref(nb)), "pmc_read_timing")
+        return {"ms": dict(zip(PHASES, ms.tolist())), "launches": nl.value, "batches": nb.value}
+
+    def material_info(self, m: int) -> dict:
+        nr, ni, ns = C.c_uint32(), C.c_uint32(), C.c_uint32()
+        roots = np.zeros(65536, dtype=np.uint32)
+        _check(load().pmc_material_info(self._h, m, C.byref(nr), roots.ctypes.data, 65536,
+                                        C.byref(ni), C.byref(ns)), "pmc_material_info")
+        return {"roots": roots[: nr.value].copy(), "n_instr": ni.value, "n_slots": ns.value}
+
+
+def analyze_material(nodes, min_root_nodes=2) -> dict:
+    """Host-only compile of one network: cacheable nodes, program length, slots."""
+    m = np.ascontiguousarray(nodes, dtype=NODE_DTYPE)
+    mat = _Material(len(m), m.ctypes.data)
+    nr, ni, ns = C.c_uint32(), C.c_uint32(), C.c_uint32()
+    roots = np.zeros(65536, dtype=np.uint32)
+    _check(load().pmc_analyze_material(C.byref(mat), min_root_nodes, C.byref(nr), roots.ctypes.data, 65536,
+                                       C.byref(ni), C.byref(ns)), "pmc_analyze_material")
+    return {"roots": roots[: nr.value].copy(), "n_instr": ni.value, "n_slots": ns.value}
+
+
+def compute_keys(mat, node, u, v, level, n_cells, stream=None):
+    """Descriptor, cell and hash2 for device tensors mat/node (int32), u/v (float32)."""
+    import torch
+    n = int(u.numel())
+    dev = u.device
+    key = torch.empty(n, dtype=torch.int64, device=dev)
+    cell = torch.empty(n, dtype=torch.int64, device=dev)
+    h2 = torch.empty(n, dtype=torch.int32, device=dev)
+    _check(load().pmc_compute_keys(_dptr(mat), _dptr(node), _dptr(u), _dptr(v), n, level, n_cells,
+                                   _dptr(key), _dptr(cell), _dptr(h2), _stream_handle(stream)),
+           "pmc_compute_keys")
+    return key, cell, h2

@@ -1,0 +1,251 @@
+"""GPU parity: the CUDA path (through the C ABI) against the CPU FP64 oracle.
+
+Bit-exact: descriptors, cells, hash2, hit/miss of every (point, cacheable node), table
+hash2 per slot, counters.  Floating point: every output and table value within max-abs
+1e-4 of the FP64 oracle (FP32 evaluation of bounded networks; see the design notes for
+the derivation of the tolerance).
+"""
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2305_07238_gb300 import workload as W
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-4
+EXACT_STATS = ("lookups", "hits", "misses", "candidates", "inserted", "dropped_dup", "dropped_full")
+
+
+@pytest.fixture(scope="module")
+def P():
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2305_07238_gb300 import pmc
+    assert torch.cuda.is_available(), "GPU tests need CUDA"
+    return pmc
+
+
+def _run_gpu(cache, P, part):
+    n = len(part["u"])
+    d = P.points_to_device(part)
+    rgb = torch.full((3, max(n, 1)), -7.0, dtype=torch.float32, device="cuda")[:, :n]
+    rgb = rgb.contiguous()
+    hits = torch.full((max(n, 1),), -1, dtype=torch.int16, device="cuda")[:n]
+    cache.eval_batch(d, rgb, hits)
+    cache.sync()
+    return rgb.cpu().numpy(), hits.cpu().numpy().astype(np.uint16)
+
+
+def _oracle_masks(ref, part, r):
+    n = len(part["u"])
+    masks = np.zeros(n, dtype=np.uint64)
+    k = 0
+    for i in range(n):
+        m = int(part["mat"][i])
+        nr = ref.n_roots(m) if m < len(ref._mats) else 0
+        for j in range(nr):
+            if r["hit"][k + j] and j < 64:
+                masks[i] |= np.uint64(1) << np.uint64(j)
+        k += nr
+    return masks
+
+
+def _compare_pass(gpu, ref, P, part, check_masks=True):
+    g_rgb, g_hits = _run_gpu(gpu, P, part)
+    r = ref.run_batch(part, probes=check_masks)
+    err = float(np.abs(g_rgb - r["rgb"]).max()) if len(part["u"]) else 0.0
+    assert err <= TOL, f"max-abs error {err}"
+    assert np.array_equal(g_hits, r["hits"])
+    if check_masks and not ref.off:
+        assert np.array_equal(gpu.last_hit_masks(len(part["u"])), _oracle_masks(ref, part, r))
+    gs, rs = gpu.stats(), ref.stats()
+    for k in EXACT_STATS:
+        assert gs[k] == rs[k], (k, gs[k], rs[k])
+    return err
+
+
+def _compare_tables(gpu, ref):
+    gh, gv = gpu.table()
+    rh, rv = ref.table()
+    assert np.array_equal(gh, rh)
+    occ = rh != 0
+    if occ.any():
+        assert float(np.abs(gv[occ] - rv[occ]).max()) <= TOL
+    assert np.all(gv[~occ] == 0)
+
+
+# ---- descriptors and addressing -----------------------------------------------------------
+@pytest.mark.parametrize("n_cells", [1, 10, 8192, 12345, 1 << 21, 10**7, (1 << 32) - 5])
+@pytest.mark.parametrize("level", [0, 10, 13])
+def test_keys_cells_hash2_bit_exact(P, n_cells, level):
+    rng = np.random.default_rng(level + n_cells % 1000)
+    n = 5000
+    mat = rng.integers(0, 65536, n).astype(np.uint32)
+    node = rng.integers(0, 65536, n).astype(np.uint32)
+    u = rng.uniform(-0.2, 1.2, n).astype(np.float32)
+    v = rng.uniform(-0.2, 1.2, n).astype(np.float32)
+    edge = np.array([0.0, 1.0, 0.5, 511 / 1024, np.nextafter(np.float32(0.5), np.float32(0)), -0.0,
+                     np.nan, 1.0 - 2**-24], dtype=np.float32)
+    u[: len(edge)] = edge
+    v[-len(edge):] = edge
+    t = lambda a: torch.from_numpy(a.view(np.int32) if a.dtype == np.uint32 else a).cuda()
+    key, cell, h2 = P.compute_keys(t(mat), t(node), t(u), t(v), level, n_cells)
+    torch.cuda.synchronize()
+    key = key.cpu().numpy().view(np.uint64)
+    cell = cell.cpu().numpy().view(np.uint64)
+    h2 = h2.cpu().numpy().view(np.uint32)
+    for i in range(n):
+        k = O.key(int(mat[i]), int(node[i]), level, float(u[i]), float(v[i]))
+        assert int(key[i]) == k
+        assert int(cell[i]) == O.hash1(k) % n_cells
+        assert int(h2[i]) == O.hash2(k)
+
+
+# ---- the tiny 8-node material, 4 passes of 4096 ---------------------------------------------
+def test_tiny_config_cache_on(P):
+    mat = W.material_tiny()
+    pts = W.points_uniform(16384, seed=0)
+    gpu = P.Cache([mat], 8192, 8, uv_level=10)
+    ref = O.Cache([mat], 8192, 8, level=10)
+    for p in range(4):
+        _compare_pass(gpu, ref, P, W.slice_points(pts, 4096 * p, 4096 * (p + 1)))
+    _compare_tables(gpu, ref)
+    assert gpu.stats()["hits"] > 0
+
+
+def test_tiny_config_cache_off(P):
+    mat = W.material_tiny()
+    pts = W.points_uniform(4096, seed=0)
+    gpu = P.Cache([mat], 8192, 8, flags=P.PMC_CACHE_OFF)
+    ref = O.Cache([mat], 8192, 8, cache_off=True)
+    for _ in range(2):
+        _compare_pass(gpu, ref, P, pts)
+    assert gpu.stats()["lookups"] == 0
+
+
+# ---- frame-shaped streams: a band of the 1920-wide frame, several table geometries ----------
+@pytest.mark.parametrize("n_cells,n_entries", [(1 << 21, 8), (1 << 10, 8), (10, 5), (1000, 16), (97, 32), (3, 1)])
+def test_frame_band_parity(P, n_cells, n_entries):
+    spec = W.FrameSpec(width=1920, height=1080, n_mats=64, seed=0)
+    frame = W.Frame(spec)
+    mats = W.random_materials(64, 20, 200, 0.2, seed=0)
+    gpu = P.Cache(mats, n_cells, n_entries)
+    ref = O.Cache(mats, n_cells, n_entries)
+    rows = (0, 9) if n_cells >= 1024 else (0, 3)       # 17,280 / 5,760 points: ragged warps
+    for p in range(3):
+        _compare_pass(gpu, ref, P, frame.points(p, rows=rows))
+    _compare_tables(gpu, ref)
+
+
+def test_frame_band_cache_off(P):
+    frame = W.Frame(W.FrameSpec(seed=3))
+    mats = W.random_materials(64, 20, 200, 0.2, seed=3)
+    gpu = P.Cache(mats, 1 << 16, 8, flags=P.PMC_CACHE_OFF)
+    ref = O.Cache(mats, 1 << 16, 8, cache_off=True)
+    _compare_pass(gpu, ref, P, frame.points(0, rows=(500, 506)))
+
+
+@pytest.mark.parametrize("n", [0, 1, 31, 33, 4097])
+def test_ragged_batch_sizes(P, n):
+    mats = W.random_materials(5, 20, 120, 0.2, seed=9)
+    pts = W.points_uniform(max(n, 1), seed=n, n_mats=5)
+    pts = W.slice_points(pts, 0, n)
+    gpu = P.Cache(mats, 256, 8)
+    ref = O.Cache(mats, 256, 8)
+    for _ in range(2):
+        _compare_pass(gpu, ref, P, pts)
+    _compare_tables(gpu, ref)
+
+
+def test_deep_and_wide_networks(P):
+    # 1000-2000 node networks with long UV-only chains (the learned-surrogate workload shape)
+    rng = np.random.default_rng(4)
+    mats = [W.random_material(rng, int(n), 0.05, n_trees=1) for n in (600, 1500, 2000)]
+    mats += [W.random_material(rng, 800, 0.4)]
+    pts = W.points_uniform(3000, seed=5, n_mats=len(mats))
+    gpu = P.Cache(mats, 4096, 8)
+    ref = O.Cache(mats, 4096, 8)
+    for p in range(2):
+        _compare_pass(gpu, ref, P, W.slice_points(pts, 1500 * p, 1500 * (p + 1)))
+    _compare_tables(gpu, ref)
+
+
+def test_hand_built_nested_roots(P):
+    from .test_oracle_analysis import g_nested, g_two_roots
+    mats = [g_nested(), g_two_roots()]
+    pts = W.points_uniform(600, seed=6, n_mats=2)
+    pts["u"] = (np.floor(pts["u"] * 8) / 1024 + 0.3).astype(np.float32)   # few texels: many hits
+    pts["v"] = (np.floor(pts["v"] * 8) / 1024 + 0.6).astype(np.float32)
+    gpu = P.Cache(mats, 64, 4)
+    ref = O.Cache(mats, 64, 4)
+    for p in range(3):
+        _compare_pass(gpu, ref, P, W.slice_points(pts, 200 * p, 200 * (p + 1)))
+    _compare_tables(gpu, ref)
+    assert gpu.stats()["hits"] > 100
+
+
+# ---- errors, determinism, host entry point ----------------------------------------------------
+def test_bad_material_index_reported(P):
+    mat = W.material_tiny()
+    pts = W.points_uniform(100, seed=7)
+    pts["mat"][17] = 3
+    gpu = P.Cache([mat], 64, 8)
+    d = P.points_to_device(pts)
+    rgb = torch.full((3, 100), 5.0, device="cuda")
+    gpu.eval_batch(d, rgb)
+    with pytest.raises(P.PmcError) as ei:
+        gpu.sync()
+    assert ei.value.status == P.PMC_ERR_INVALID_ARG
+    out = rgb.cpu().numpy()
+    assert np.all(out[:, 17] == 0)
+    assert gpu.stats()["bad_points"] == 1
+    ref = O.Cache([mat], 64, 8)
+    r = ref.run_batch(pts)
+    ok = np.arange(100) != 17
+    assert float(np.abs(out[:, ok] - r["rgb"][:, ok]).max()) <= TOL
+
+
+def test_two_runs_identical(P):
+    frame = W.Frame(W.FrameSpec(seed=2))
+    mats = W.random_materials(64, 20, 200, 0.2, seed=2)
+    outs, tables = [], []
+    for _ in range(2):
+        gpu = P.Cache(mats, 1 << 12, 8)
+        rgbs = [_run_gpu(gpu, P, frame.points(p, rows=(40, 60)))[0] for p in range(3)]
+        outs.append(np.stack(rgbs))
+        tables.append(gpu.table())
+        gpu.close()
+    assert np.array_equal(outs[0], outs[1])
+    assert np.array_equal(tables[0][0], tables[1][0]) and np.array_equal(tables[0][1], tables[1][1])
+
+
+def test_host_entry_point_matches_device_entry(P):
+    frame = W.Frame(W.FrameSpec(seed=1))
+    mats = W.random_materials(64, 20, 200, 0.2, seed=1)
+    a = P.Cache(mats, 1 << 14, 8)
+    b = P.Cache(mats, 1 << 14, 8)
+    for p in range(2):
+        part = frame.points(p, rows=(100, 110))
+        n = len(part["u"])
+        g_rgb, g_hits = _run_gpu(a, P, part)
+        h_rgb = np.zeros(3 * n, dtype=np.float32)
+        h_hits = np.zeros(n, dtype=np.uint16)
+        b.eval_batch_host(part, h_rgb, h_hits)
+        assert np.array_equal(h_rgb.reshape(3, n), g_rgb)
+        assert np.array_equal(h_hits, g_hits)
+    assert np.array_equal(a.table()[0], b.table()[0])
+
+
+def test_reset_empties_table(P):
+    mat = W.material_tiny()
+    pts = W.points_uniform(512, seed=8)
+    gpu = P.Cache([mat], 64, 8)
+    _run_gpu(gpu, P, pts)
+    assert gpu.stats()["inserted"] > 0
+    gpu.reset()
+    gpu.sync()
+    assert gpu.stats()["inserted"] == 0 and not gpu.table()[0].any()
+    _, hits = _run_gpu(gpu, P, pts)
+    assert not hits.any()

@@ -1,0 +1,101 @@
+"""CPU-side checks of the C-ABI library: it loads, exports what include/pmc.h declares,
+agrees with the oracle on the IR numbering and on which nodes are cacheable.  No call
+here touches a GPU."""
+import os
+import re
+
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2305_07238_gb300 import build as B
+from paper_2305_07238_gb300 import pmc as P
+from paper_2305_07238_gb300 import workload as W
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    B.build()
+    return P.load()
+
+
+def _declared(header):
+    text = open(os.path.join(ROOT, header)).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(pmc_[a-z_0-9]+)\s*\(", text)))
+
+
+def test_exports_every_declared_symbol(lib):
+    names = _declared("include/pmc.h")
+    assert "pmc_eval_batch" in names and "pmc_create_cache" in names and "pmc_stats" in names
+    for name in names:
+        assert hasattr(lib, name), name
+    assert set(P.EXPORTED) <= set(names)
+
+
+def _enum(path, prefix):
+    text = open(os.path.join(ROOT, path)).read()
+    return {m.group(1): int(m.group(2)) for m in re.finditer(rf"\b{prefix}([A-Z_]+)\s*=\s*(\d+)", text)}
+
+
+def test_ir_numbering_agrees_everywhere():
+    lib_ops = _enum("include/pmc.h", "PMC_OP_")
+    orc_ops = _enum("oracle/pmc_oracle.h", "ORC_")
+    for code, name in W.OP_NAMES.items():
+        assert lib_ops[name] == code, name
+        assert orc_ops[name] == code, name
+    assert _enum("include/pmc.h", "PMC_")["NUM_OPS"] == W.NUM_OPS == orc_ops["NUM_OPS"]
+
+
+def test_cacheable_nodes_match_oracle(lib):
+    mats = W.random_materials(40, 5, 400, 0.25, seed=11) + [W.material_tiny()]
+    for m in mats:
+        for mr in (1, 2, 3):
+            got = P.analyze_material(m, min_root_nodes=mr)
+            _, exp = O.analyze(m, min_root_nodes=mr)
+            assert np.array_equal(got["roots"], exp)
+            assert got["n_slots"] >= 1 and got["n_instr"] >= 1
+
+
+def test_hand_built_networks_roots(lib):
+    from .test_oracle_analysis import g_nested, g_two_roots
+    assert list(P.analyze_material(g_two_roots())["roots"]) == [4, 10]
+    assert list(P.analyze_material(g_nested())["roots"]) == [2, 7]
+    assert list(P.analyze_material(W.material_tiny())["roots"]) == [7]
+
+
+def test_malformed_networks_rejected(lib):
+    good = W.material_tiny()
+    for mutate in (lambda b: b[5]["inp"].__setitem__(0, 6), lambda b: b[1]["ip"].__setitem__(0, 0),
+                   lambda b: b[2]["fp"].__setitem__(1, 0.9), lambda b: b[0].__setitem__("op", 99),
+                   lambda b: b[3]["inp"].__setitem__(0, 0)):
+        bad = good.copy()
+        mutate(bad)
+        with pytest.raises(P.PmcError) as ei:
+            P.analyze_material(bad)
+        assert ei.value.status == P.PMC_ERR_INVALID_ARG
+
+
+def test_constant_folding_keeps_node_ids(lib):
+    # MUL(CONST, CONST) folds; the cacheable node above it keeps its original ID.
+    b = W.Builder()
+    uv = b.add(W.OP_UV)
+    c1 = b.add(W.OP_CONST, fp=[0.5, 0.5, 0.5])
+    c2 = b.add(W.OP_CONST, fp=[0.25, 1.0, 0.0])
+    k = b.add(W.OP_MUL, [c1, c2])
+    n = b.add(W.OP_FBM, [uv], ip=[2, 1], fp=[4.0, 2.0, 0.5])
+    r = b.add(W.OP_MUL, [n, k])
+    nrm = b.add(W.OP_NORMAL)
+    f = b.add(W.OP_FACING, [nrm], fp=[0, 0, 1])
+    b.add(W.OP_MIX, [r, k, f])
+    m = b.build()
+    info = P.analyze_material(m)
+    assert list(info["roots"]) == list(O.analyze(m)[1]) == [5]
+
+
+def test_generated_programs_are_small(lib):
+    mats = W.random_materials(64, 20, 200, 0.2, seed=0)
+    slots = [P.analyze_material(m)["n_slots"] for m in mats]
+    assert max(slots) <= 64
