@@ -239,6 +239,39 @@ pmc_status pmc_set_timing(pmc_cache* cache, int enable);
 pmc_status pmc_read_timing(pmc_cache* cache, double* ms, uint64_t* kernel_launches,
                            uint64_t* batches);
 
+/* ---- pass without device allocation ---------------------------------------------
+ * The paper has no counterpart to this entry point; it serves callers that must not
+ * allocate device memory while they run.  Examples: an application that hands all of
+ * a GPU's memory to its own pool at start-up and forbids driver allocations after
+ * that; code on a latency-critical thread, where cudaMalloc/cudaFree can synchronise
+ * the device and stall it; a plug-in whose host process owns the device memory.
+ *
+ * pmc_eval_batch_noalloc runs the same pass as pmc_eval_batch (same arguments, same
+ * results) but takes its per-batch scratch from one fixed array compiled into the
+ * library's device image (PMC_NOALLOC_SCRATCH_BYTES, about 2.2 MiB), not from
+ * cudaMalloc; it calls no cudaMalloc, cudaFree or other allocating routine.  Every
+ * GPU that loads the library holds that array until the process exits.  The cache
+ * object (table, programs, counters) must already exist (pmc_create_cache).
+ *
+ * Limits: n <= PMC_NOALLOC_MAX_POINTS; n times the largest number of cacheable nodes
+ * of any material <= PMC_NOALLOC_MAX_PROBES; at most PMC_NOALLOC_MAX_MATERIALS
+ * materials.  A larger request returns PMC_ERR_UNSUPPORTED (with a message on stderr)
+ * and enqueues nothing.
+ *
+ * The first call on a device looks up the array's device address (once per device,
+ * with that device current); make that first call before any stream capture begins.
+ * All calls, from every cache object, share the one array, which keeps the last
+ * call's contents; each call clears what must start at zero.  Calls whose work can
+ * overlap on the GPU (unordered streams, concurrent host threads) race on the array
+ * and corrupt each other's results: order them on one stream.  pmc_set_timing does
+ * not time these calls and pmc_last_hit_masks does not describe them. */
+#define PMC_NOALLOC_MAX_POINTS 8192u
+#define PMC_NOALLOC_MAX_PROBES 32768u
+#define PMC_NOALLOC_MAX_MATERIALS 4096u
+#define PMC_NOALLOC_SCRATCH_BYTES 2343168u
+pmc_status pmc_eval_batch_noalloc(pmc_cache* cache, const pmc_points* pts, float* out_rgb,
+                                  uint16_t* out_hits, void* stream);
+
 /* Human-readable name of a status code (static storage). */
 const char* pmc_status_str(pmc_status s);
 

@@ -5,54 +5,10 @@
 #include <vector>
 
 #include "pmc_internal.h"
+#include "cache_impl.h"
 
 using namespace pmc;
 
-struct pmc_cache {
-    pmc_cache_desc desc{};
-    int use_cache = 1;
-    uint32_t n_mats = 0;
-    uint32_t max_roots = 0;
-    uint32_t max_slots = 0;
-    int num_sms = 0;
-    std::vector<MatInfo> mat_info;
-    std::vector<uint32_t> roots;
-    uint32_t prog_len = 0;
-    // device-resident, owned
-    MatInfo* d_mats = nullptr;
-    uint4* d_prog = nullptr;
-    float* d_params = nullptr;
-    uint32_t* d_roots = nullptr;
-    uint4* d_table = nullptr;
-    unsigned long long* d_claims = nullptr;
-    Control* d_ctl = nullptr;
-    unsigned long long* d_stats = nullptr;
-    // per-batch scratch, grown on demand
-    uint64_t cap_points = 0;
-    uint64_t cap_probes = 0;
-    uint32_t* d_seg = nullptr;      // counts | seg_start | probe_base | item_base | cursor
-    float* d_sorted = nullptr;      // 8 planes of cap_points
-    uint32_t* d_sidx = nullptr;
-    float4* d_probes = nullptr;
-    Candidate* d_cands = nullptr;
-    uint32_t* d_lists = nullptr;    // 3 lists of cap_probes
-    // staging for the host-buffer entry point
-    uint64_t cap_host = 0;
-    float* d_hpts = nullptr;        // 8 float planes + 1 uint32 plane
-    float* d_hrgb = nullptr;
-    uint16_t* d_hhits = nullptr;
-    // state
-    cudaStream_t last_stream = nullptr;
-    pmc_status sticky = PMC_OK;
-    uint32_t epoch_host = 0;
-    uint64_t last_n = 0;
-    // timing
-    bool timing = false;
-    std::vector<cudaEvent_t> events;   // (PH_COUNT + 1) per timed batch, in order
-    size_t events_used = 0;
-    uint64_t launches = 0;
-    uint64_t timed_batches = 0;
-};
 
 namespace {
 

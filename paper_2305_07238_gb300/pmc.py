@@ -25,8 +25,9 @@ EXPORTED = (
     "pmc_create_cache", "pmc_eval_batch", "pmc_eval_batch_host", "pmc_sync", "pmc_stats",
     "pmc_table_dump", "pmc_last_hit_masks", "pmc_reset", "pmc_destroy_cache",
     "pmc_material_info", "pmc_analyze_material", "pmc_compute_keys", "pmc_set_timing",
-    "pmc_read_timing", "pmc_status_str",
+    "pmc_read_timing", "pmc_eval_batch_noalloc", "pmc_status_str",
 )
+NOALLOC_MAX_POINTS, NOALLOC_MAX_PROBES, NOALLOC_MAX_MATERIALS = 8192, 32768, 4096
 PHASES = ("sort", "lookup", "eval", "insert", "finish")
 
 
@@ -103,6 +104,8 @@ def load():
     L.pmc_set_timing.restype = st
     L.pmc_read_timing.argtypes = [vp, vp, vp, vp]
     L.pmc_read_timing.restype = st
+    L.pmc_eval_batch_noalloc.argtypes = [vp, vp, vp, vp, vp]
+    L.pmc_eval_batch_noalloc.restype = st
     L.pmc_status_str.argtypes = [st]
     L.pmc_status_str.restype = C.c_char_p
     _lib = L
@@ -186,6 +189,14 @@ class Cache:
         p = _Points(*[_dptr(pts[k]) for k in POINT_FIELDS], n)
         _check(load().pmc_eval_batch(self._h, C.byref(p), _dptr(out_rgb), _dptr(out_hits),
                                      _stream_handle(stream)), "pmc_eval_batch")
+
+    def eval_batch_noalloc(self, pts, out_rgb, out_hits=None, stream=None):
+        """Same pass as eval_batch with the library's fixed scratch array instead of device
+        allocations (for callers that must not allocate; see include/pmc.h for the limits)."""
+        n = int(pts["u"].numel())
+        p = _Points(*[_dptr(pts[k]) for k in POINT_FIELDS], n)
+        _check(load().pmc_eval_batch_noalloc(self._h, C.byref(p), _dptr(out_rgb), _dptr(out_hits),
+                                             _stream_handle(stream)), "pmc_eval_batch_noalloc")
 
     def eval_batch_host(self, pts: dict, out_rgb: np.ndarray, out_hits: np.ndarray | None = None,
                         stream=None):
