@@ -169,7 +169,9 @@ def ours(args, rank, world, local_rank, dist):
     hits = torch.empty(n, dtype=torch.int16, device=dev)
 
     cached = P.Cache(mats, N_CELLS, N_ENTRIES, uv_level=LEVEL, device=local_rank)
-    uncached = P.Cache(mats, N_CELLS, N_ENTRIES, uv_level=LEVEL, flags=P.PMC_CACHE_OFF, device=local_rank)
+    uncached = None
+    if "uncached" in args.legs.split(","):
+        uncached = P.Cache(mats, N_CELLS, N_ENTRIES, uv_level=LEVEL, flags=P.PMC_CACHE_OFF, device=local_rank)
 
     # ---- cached, device-resident inputs ---------------------------------------------
     for _ in range(args.warmup):
@@ -195,18 +197,23 @@ def ours(args, rank, world, local_rank, dist):
     frame_stats = s1
 
     # ---- uncached --------------------------------------------------------------------
-    for _ in range(max(1, args.warmup)):
-        run_frame(uncached, dev_passes, outs, hits, None)
-    uncached.sync()
-    usecs = timed_steps(torch, uncached, dev_passes, outs, hits, args.steps, barrier)
-    if dist is not None:
-        t = torch.tensor([usecs], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        usecs = float(t.item())
-    u_value = pts_total * world / usecs
+    legs = set(args.legs.split(","))
+    usecs, u_value = float("nan"), float("nan")
+    if "uncached" in legs:
+        for _ in range(max(1, args.warmup)):
+            run_frame(uncached, dev_passes, outs, hits, None)
+        uncached.sync()
+        usecs = timed_steps(torch, uncached, dev_passes, outs, hits, args.steps, barrier)
+        if dist is not None:
+            t = torch.tensor([usecs], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            usecs = float(t.item())
+        u_value = pts_total * world / usecs
 
     # ---- end to end through the host-buffer entry point --------------------------------
-    e2e = e2e_run(torch, P, mats, passes_host, args, local_rank, barrier, dist, dev)
+    e2e = None
+    if "e2e" in legs:
+        e2e = e2e_run(torch, P, mats, passes_host, args, local_rank, barrier, dist, dev)
 
     # ---- roofline of the dominant kernel ------------------------------------------------
     hbm_peak, sm_mhz_max, peak_kind = peaks()
@@ -240,7 +247,7 @@ def ours(args, rank, world, local_rank, dist):
         "config": config_dict({"parallelism": f"replicas x{world}" if world > 1 else "single GPU"}),
         "uncached": {"value": round(u_value, 1), "unit": UNIT,
                      "ms_per_step": round(usecs / args.steps * 1e3, 3),
-                     "speedup_cached_over_uncached": round(value / u_value, 3)},
+                     "speedup_cached_over_uncached": round(value / u_value, 3)} if u_value == u_value else None,
         "hit_rate": round(frame_stats["hits"] / max(1, frame_stats["lookups"]), 4),
         "table": {k: frame_stats[k] for k in ("lookups", "hits", "inserted", "dropped_dup", "dropped_full")},
         "phase_ms_per_step": {k: round(v / args.steps, 3) for k, v in ms.items()},
@@ -250,7 +257,7 @@ def ours(args, rank, world, local_rank, dist):
         "gpu_launches": int(timing["launches"]),
         "clocks": clk.summary(),
     }
-    if rank == 0 and not args.no_cpu_baseline:
+    if rank == 0 and not args.no_cpu_baseline and "cpu" in legs:
         line["cpu_baseline"], line["max_abs_err_vs_fp64"] = cpu_baseline(P, torch, mats, frame, dev)
     return line
 
@@ -365,6 +372,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--legs", default="cached,uncached,e2e,cpu",
+                    help="comma list of cached, uncached, e2e, cpu (profiling runs take 'cached')")
     args = ap.parse_args()
 
     world = int(os.environ.get("WORLD_SIZE", "1"))

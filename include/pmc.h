@@ -117,6 +117,12 @@ typedef struct {
 #define PMC_SORT_BY_MATERIAL 0x2u /* accepted; shading points are always grouped
                                      by material inside the library               */
 #define PMC_DEBUG_CHECKS 0x4u     /* extra device-side bounds checks               */
+#define PMC_EVAL_INLINE 0x8u      /* evaluate missed cacheable nodes inside the
+                                     per-point program (lanes that hit wait) instead of
+                                     in batches of 32 misses of the same node          */
+#define PMC_INSERT_ROUNDS 0x10u   /* resolve inserts by rounds of atomicMin on a claim
+                                     word per cell instead of grouping the candidates
+                                     by cell (same table either way)                   */
 
 typedef struct {
     uint64_t n_cells;        /* N_c >= 1, < 2^32                                  */
@@ -248,7 +254,7 @@ pmc_status pmc_read_timing(pmc_cache* cache, double* ms, uint64_t* kernel_launch
  *
  * pmc_eval_batch_noalloc runs the same pass as pmc_eval_batch (same arguments, same
  * results) but takes its per-batch scratch from one fixed array compiled into the
- * library's device image (PMC_NOALLOC_SCRATCH_BYTES, about 2.2 MiB), not from
+ * library's device image (PMC_NOALLOC_SCRATCH_BYTES, about 3.4 MiB), not from
  * cudaMalloc; it calls no cudaMalloc, cudaFree or other allocating routine.  Every
  * GPU that loads the library holds that array until the process exits.  The cache
  * object (table, programs, counters) must already exist (pmc_create_cache).
@@ -268,7 +274,7 @@ pmc_status pmc_read_timing(pmc_cache* cache, double* ms, uint64_t* kernel_launch
 #define PMC_NOALLOC_MAX_POINTS 8192u
 #define PMC_NOALLOC_MAX_PROBES 32768u
 #define PMC_NOALLOC_MAX_MATERIALS 4096u
-#define PMC_NOALLOC_SCRATCH_BYTES 2343168u
+#define PMC_NOALLOC_SCRATCH_BYTES 3522816u
 pmc_status pmc_eval_batch_noalloc(pmc_cache* cache, const pmc_points* pts, float* out_rgb,
                                   uint16_t* out_hits, void* stream);
 

@@ -18,6 +18,9 @@ struct pmc_cache {
     int num_sms = 0;
     std::vector<MatInfo> mat_info;
     std::vector<uint32_t> roots;
+    std::vector<pmc::RootInfo> root_info;
+    uint32_t max_level = 0;
+    int split = 1;
     uint32_t prog_len = 0;
     // device-resident, owned
     MatInfo* d_mats = nullptr;
@@ -28,6 +31,11 @@ struct pmc_cache {
     unsigned long long* d_claims = nullptr;
     Control* d_ctl = nullptr;
     unsigned long long* d_stats = nullptr;
+    pmc::RootInfo* d_rinfo = nullptr;
+    uint32_t* d_miss_cnt = nullptr;       // roots + MAX_LEVELS
+    uint32_t* d_root_items = nullptr;     // roots + 1
+    uint32_t n_bins = 0;                  // cell-grouped insert bins
+    uint32_t* d_bins = nullptr;           // counts (n_bins) | bases (n_bins + 1)
     // per-batch scratch, grown on demand
     uint64_t cap_points = 0;
     uint64_t cap_probes = 0;
@@ -37,6 +45,8 @@ struct pmc_cache {
     float4* d_probes = nullptr;
     Candidate* d_cands = nullptr;
     uint32_t* d_lists = nullptr;    // 3 lists of cap_probes
+    uint32_t* d_misslist = nullptr; // cap_probes
+    pmc::Candidate* d_cands_binned = nullptr;  // cap_probes
     // staging for the host-buffer entry point
     uint64_t cap_host = 0;
     float* d_hpts = nullptr;        // 8 float planes + 1 uint32 plane

@@ -57,6 +57,8 @@ void free_scratch(pmc_cache* c) {
     dfree(&c->d_probes);
     dfree(&c->d_cands);
     dfree(&c->d_lists);
+    dfree(&c->d_misslist);
+    dfree(&c->d_cands_binned);
     c->cap_points = c->cap_probes = 0;
 }
 
@@ -75,6 +77,8 @@ pmc_status ensure_scratch(pmc_cache* c, uint64_t n) {
     if ((s = dalloc(&c->d_probes, (size_t)pcap)) != PMC_OK) return s;
     if ((s = dalloc(&c->d_cands, (size_t)pcap)) != PMC_OK) return s;
     if ((s = dalloc(&c->d_lists, 3 * (size_t)pcap)) != PMC_OK) return s;
+    if ((s = dalloc(&c->d_misslist, (size_t)pcap)) != PMC_OK) return s;
+    if ((s = dalloc(&c->d_cands_binned, (size_t)pcap)) != PMC_OK) return s;
     c->cap_points = cap;
     c->cap_probes = pcap;
     return PMC_OK;
@@ -87,6 +91,10 @@ pmc_status fold_device_errors(pmc_cache* c) {
     if (err) {
         uint32_t zero = 0;
         cudaMemcpy(&c->d_ctl->err, &zero, sizeof(zero), cudaMemcpyHostToDevice);
+    }
+    if (err & ERR_TIMEOUT) {
+        fprintf(stderr, "pmc: a bounded device wait ran out\n");
+        return PMC_ERR_TIMEOUT;
     }
     if (err & (ERR_INSERT | ERR_BOUNDS)) {
         fprintf(stderr, "pmc: internal device check failed (flags %u)\n", err);
@@ -128,6 +136,10 @@ void pmc_destroy_cache(pmc_cache* c) {
         dfree(&c->d_claims);
         dfree(&c->d_ctl);
         dfree(&c->d_stats);
+        dfree(&c->d_rinfo);
+        dfree(&c->d_miss_cnt);
+        dfree(&c->d_root_items);
+        dfree(&c->d_bins);
         dfree(&c->d_hpts);
         dfree(&c->d_hrgb);
         dfree(&c->d_hhits);
@@ -153,6 +165,7 @@ pmc_status pmc_create_cache(const pmc_cache_desc* desc, const pmc_material* mats
     c->desc = *desc;
     c->desc.min_root_nodes = min_root;
     c->use_cache = off ? 0 : 1;
+    c->split = (desc->flags & PMC_EVAL_INLINE) ? 0 : 1;
     c->n_mats = n_mats;
 
     std::vector<uint4> prog;
@@ -178,6 +191,25 @@ pmc_status pmc_create_cache(const pmc_cache_desc* desc, const pmc_material* mats
             if ((ins.x & 0xFFu) != OP_ROOT_BEGIN) ins.w += pbase;
             prog.push_back(ins);
         }
+        for (size_t r = 0; r < cm.roots.size(); ++r) {
+            RootInfo ri{};
+            ri.prog_start = (uint32_t)prog.size();
+            ri.prog_len = (uint32_t)cm.root_progs[r].size();
+            ri.mat = m;
+            ri.ordinal = (uint32_t)r;
+            ri.level = cm.root_level[r];
+            ri.n_slots = cm.root_slots[r];
+            ri.node = cm.roots[r];
+            ri.out_slot = cm.root_out_slot[r];
+            for (uint4 ins : cm.root_progs[r]) {
+                uint32_t op = ins.x & 0xFFu;
+                if (op != OP_ROOT_BEGIN && op != OP_LOAD_ROOT) ins.w += pbase;
+                prog.push_back(ins);
+            }
+            c->root_info.push_back(ri);
+            c->max_level = std::max(c->max_level, ri.level);
+            c->max_slots = std::max(c->max_slots, ri.n_slots);
+        }
         params.insert(params.end(), cm.params.begin(), cm.params.end());
         c->roots.insert(c->roots.end(), cm.roots.begin(), cm.roots.end());
         c->mat_info.push_back(mi);
@@ -185,6 +217,7 @@ pmc_status pmc_create_cache(const pmc_cache_desc* desc, const pmc_material* mats
         c->max_slots = std::max(c->max_slots, mi.n_slots);
     }
     c->prog_len = (uint32_t)prog.size();
+    if (c->max_level >= MAX_LEVELS) c->split = 0;   // deeper nesting: evaluate misses inline
     if (eval_smem_bytes(c->max_slots) > 200u * 1024u) {
         fprintf(stderr, "pmc: a material needs %u live values; this build supports %zu\n",
                 c->max_slots, (size_t)(200u * 1024u) / eval_smem_bytes(1));
@@ -199,6 +232,7 @@ pmc_status pmc_create_cache(const pmc_cache_desc* desc, const pmc_material* mats
     pmc_status s = PMC_OK;
     const uint64_t slots = c->use_cache ? desc->n_cells * desc->n_entries : 0;
     const uint64_t cells = c->use_cache ? desc->n_cells : 0;
+    c->n_bins = c->use_cache ? (uint32_t)((desc->n_cells + INSERT_BIN_CELLS - 1) / INSERT_BIN_CELLS) : 0;
     if ((s = dalloc(&c->d_mats, n_mats)) != PMC_OK ||
         (s = dalloc(&c->d_prog, prog.size())) != PMC_OK ||
         (s = dalloc(&c->d_params, params.size())) != PMC_OK ||
@@ -206,7 +240,11 @@ pmc_status pmc_create_cache(const pmc_cache_desc* desc, const pmc_material* mats
         (s = dalloc(&c->d_table, slots)) != PMC_OK ||
         (s = dalloc(&c->d_claims, cells)) != PMC_OK ||
         (s = dalloc(&c->d_ctl, 1)) != PMC_OK ||
-        (s = dalloc(&c->d_stats, ST_COUNT)) != PMC_OK) {
+        (s = dalloc(&c->d_stats, ST_COUNT)) != PMC_OK ||
+        (s = dalloc(&c->d_rinfo, c->root_info.size())) != PMC_OK ||
+        (s = dalloc(&c->d_miss_cnt, c->root_info.size() + MAX_LEVELS)) != PMC_OK ||
+        (s = dalloc(&c->d_root_items, c->root_info.size() + 1)) != PMC_OK ||
+        (s = dalloc(&c->d_bins, 2 * (size_t)c->n_bins + 1)) != PMC_OK) {
         pmc_destroy_cache(c);
         return s;
     }
@@ -214,8 +252,11 @@ pmc_status pmc_create_cache(const pmc_cache_desc* desc, const pmc_material* mats
     if (e == cudaSuccess) e = cudaMemcpy(c->d_mats, c->mat_info.data(), n_mats * sizeof(MatInfo), cudaMemcpyHostToDevice);
     if (e == cudaSuccess && !prog.empty()) e = cudaMemcpy(c->d_prog, prog.data(), prog.size() * sizeof(uint4), cudaMemcpyHostToDevice);
     if (e == cudaSuccess && !params.empty()) e = cudaMemcpy(c->d_params, params.data(), params.size() * sizeof(float), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && !c->root_info.empty())
+        e = cudaMemcpy(c->d_rinfo, c->root_info.data(), c->root_info.size() * sizeof(RootInfo), cudaMemcpyHostToDevice);
     if (e == cudaSuccess && !c->roots.empty()) e = cudaMemcpy(c->d_roots, c->roots.data(), c->roots.size() * sizeof(uint32_t), cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = launch_reset(c->d_table, slots, c->d_claims, cells, c->d_ctl, c->d_stats, 0);
+    if (e == cudaSuccess) e = launch_reset(c->d_table, slots, c->d_claims, cells, c->d_ctl, c->d_stats, 0,
+                                           (desc->flags & PMC_INSERT_ROUNDS) != 0);
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
     if (e != cudaSuccess) {
         cuda_fail(nullptr, e);
@@ -241,7 +282,7 @@ pmc_status pmc_eval_batch(pmc_cache* c, const pmc_points* pts, float* out_rgb, u
     pmc_status st = ensure_scratch(c, n);
     if (st != PMC_OK) return st;
     const uint32_t ne = c->desc.n_entries;
-    if (c->use_cache && c->epoch_host + 2 * (ne + 1) > EPOCH_MAX) {
+    if (c->use_cache && (c->desc.flags & PMC_INSERT_ROUNDS) && c->epoch_host + 2 * (ne + 1) > EPOCH_MAX) {
         // claim words carry a 20-bit epoch; restart it before it runs out
         cudaError_t e = cudaMemsetAsync(c->d_claims, 0xFF, c->desc.n_cells * sizeof(unsigned long long), s);
         if (e == cudaSuccess) e = cudaMemsetAsync(&c->d_ctl->epoch, 0, sizeof(uint32_t), s);
@@ -274,6 +315,12 @@ pmc_status pmc_eval_batch(pmc_cache* c, const pmc_points* pts, float* out_rgb, u
     a.cands = c->d_cands;
     a.lists[0] = c->d_lists; a.lists[1] = c->d_lists + c->cap_probes; a.lists[2] = c->d_lists + 2 * c->cap_probes;
     a.ctl = c->d_ctl; a.stats = c->d_stats;
+    a.split = c->use_cache && c->split;
+    a.insert_rounds = (c->desc.flags & PMC_INSERT_ROUNDS) ? 1 : 0;
+    a.n_bins = c->n_bins; a.bin_cnt = c->d_bins; a.bin_base = c->d_bins + c->n_bins;
+    a.cands_binned = c->d_cands_binned;
+    a.rinfo = c->d_rinfo; a.n_roots_total = (uint32_t)c->root_info.size(); a.max_level = c->max_level;
+    a.miss_cnt = c->d_miss_cnt; a.root_item_base = c->d_root_items; a.misslist = c->d_misslist;
     cudaEvent_t* ev = nullptr;
     if (c->timing) {
         while (c->events.size() < c->events_used + PH_COUNT + 1) {
@@ -372,14 +419,30 @@ pmc_status pmc_stats(pmc_cache* c, pmc_stats_t* out) {
 
 pmc_status pmc_table_dump(pmc_cache* c, void* host_dst, size_t bytes) {
     if (!c || !host_dst) return PMC_ERR_INVALID_ARG;
-    const size_t need = c->use_cache ? (size_t)c->desc.n_cells * c->desc.n_entries * 16u : 0;
+    const size_t slots = c->use_cache ? (size_t)c->desc.n_cells * c->desc.n_entries : 0;
+    const size_t need = slots * 16u;
     if (bytes < need) return PMC_ERR_INVALID_ARG;
     pmc_status st = pmc_sync(c);
     if (st == PMC_ERR_CUDA) return st;
     DeviceGuard g(c->desc.device);
     if (need) {
-        cudaError_t e = cudaMemcpy(host_dst, c->d_table, need, cudaMemcpyDeviceToHost);
+        // device cells hold N_e hash2 words followed by N_e packed (r, g, b) values;
+        // the dump format is one {hash2, r, g, b} record per slot
+        std::vector<uint32_t> raw(slots * 4u);
+        cudaError_t e = cudaMemcpy(raw.data(), c->d_table, need, cudaMemcpyDeviceToHost);
         if (e != cudaSuccess) return cuda_fail(c, e);
+        const uint32_t ne = c->desc.n_entries;
+        uint32_t* dst = static_cast<uint32_t*>(host_dst);
+        for (size_t cell = 0; cell < c->desc.n_cells; ++cell) {
+            const uint32_t* cw = raw.data() + cell * 4u * ne;
+            for (uint32_t j = 0; j < ne; ++j) {
+                uint32_t* d = dst + (cell * ne + j) * 4u;
+                d[0] = cw[j];
+                d[1] = cw[ne + 3u * j];
+                d[2] = cw[ne + 3u * j + 1];
+                d[3] = cw[ne + 3u * j + 2];
+            }
+        }
     }
     return st;
 }
@@ -429,7 +492,7 @@ pmc_status pmc_reset(pmc_cache* c, void* stream) {
     const uint64_t slots = c->use_cache ? c->desc.n_cells * c->desc.n_entries : 0;
     const uint64_t cells = c->use_cache ? c->desc.n_cells : 0;
     cudaError_t e = launch_reset(c->d_table, slots, c->d_claims, cells, c->d_ctl, c->d_stats,
-                                 (cudaStream_t)stream);
+                                 (cudaStream_t)stream, (c->desc.flags & PMC_INSERT_ROUNDS) != 0);
     if (e != cudaSuccess) return cuda_fail(c, e);
     c->epoch_host = 0;
     c->last_stream = (cudaStream_t)stream;

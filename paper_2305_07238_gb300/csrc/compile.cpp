@@ -151,6 +151,70 @@ void pack_params(const pmc_node& nd, std::vector<float>* pool) {
     }
 }
 
+
+// Emits a linear program for `order` (nodes in topological order; entries flagged as
+// loads take a cacheable node's value from its probe record instead of evaluating it)
+// with linear-scan slot allocation.  `keep` is the node whose value must survive to the
+// end.  Returns the number of slots; *out_slot receives keep's slot.
+uint32_t emit_standalone(const std::vector<pmc_node>& g, const std::vector<std::pair<uint32_t, bool>>& order,
+                         const std::vector<uint32_t>& ordinal, uint32_t keep, bool keep_is_root,
+                         std::vector<uint4>* prog, std::vector<float>* params, uint32_t* out_slot) {
+    const size_t L = order.size();
+    std::vector<int64_t> last_use(g.size(), -1);
+    std::vector<char> in_order(g.size(), 0);
+    for (auto& e : order) in_order[e.first] = 1;
+    for (size_t p = 0; p < L; ++p) {
+        if (order[p].second) continue;  // loads read nothing
+        uint32_t x = order[p].first;
+        for (int k = 0; k < 4; ++k) {
+            int32_t y = g[x].in[k];
+            if (y >= 0) last_use[y] = std::max<int64_t>(last_use[y], (int64_t)p);
+        }
+    }
+    last_use[keep] = (int64_t)L;
+    std::vector<std::vector<uint32_t>> release_at(L + 1);
+    for (uint32_t x = 0; x < g.size(); ++x)
+        if (in_order[x] && last_use[x] >= 0 && last_use[x] < (int64_t)L) release_at[last_use[x]].push_back(x);
+    std::vector<uint32_t> slot(g.size(), 0xFFFFu), free_slots;
+    uint32_t n_slots = 0;
+    auto take = [&]() {
+        if (free_slots.empty()) return n_slots++;
+        auto it = std::min_element(free_slots.begin(), free_slots.end());
+        uint32_t s2 = *it;
+        free_slots.erase(it);
+        return s2;
+    };
+    for (size_t p = 0; p < L; ++p) {
+        uint32_t x = order[p].first;
+        uint4 ins;
+        if (order[p].second) {
+            for (uint32_t y : release_at[p]) free_slots.push_back(slot[y]);
+            slot[x] = take();
+            ins.x = OP_LOAD_ROOT;
+            ins.y = slot[x] | (ordinal[x] << 16);
+            ins.z = x;
+            ins.w = 0;
+            prog->push_back(ins);
+            continue;
+        }
+        uint32_t in_slot[3] = {0xFFFFu, 0xFFFFu, 0xFFFFu};
+        for (int k = 0; k < 3; ++k)
+            if (g[x].in[k] >= 0) in_slot[k] = slot[g[x].in[k]];
+        for (uint32_t y : release_at[p]) free_slots.push_back(slot[y]);
+        slot[x] = take();
+        const uint32_t flags = (x == keep && keep_is_root) ? FLAG_ROOT : 0u;
+        const uint32_t cost = std::min<uint32_t>(node_cost(g[x]), 0xFFFFu);
+        ins.x = g[x].op | (flags << 8) | (cost << 16);
+        ins.y = slot[x] | (in_slot[0] << 16);
+        ins.z = in_slot[1] | (in_slot[2] << 16);
+        ins.w = (uint32_t)params->size();
+        pack_params(g[x], params);
+        prog->push_back(ins);
+    }
+    *out_slot = slot[keep];
+    return n_slots;
+}
+
 }  // namespace
 
 // FP32 operations per node, counted from the device formulas in kernels.cu with a
@@ -409,6 +473,48 @@ bool compile_material(const pmc_node* nodes_in, uint32_t n, uint32_t min_root_no
     out->out_slot = slot[out_node];
     out->n_slots = n_slots;
     out->n_nodes = n;
+
+    // ---- standalone program of each cacheable node ------------------------------------
+    // its sub-graph in post-order, stopping at other cacheable nodes (read as loads)
+    out->root_progs.assign(out->roots.size(), {});
+    out->root_level.assign(out->roots.size(), 0);
+    out->root_slots.assign(out->roots.size(), 0);
+    out->root_out_slot.assign(out->roots.size(), 0);
+    std::vector<uint32_t> level_of(n, 0);
+    for (size_t ri = 0; ri < out->roots.size(); ++ri) {
+        const uint32_t r = out->roots[ri];
+        std::vector<std::pair<uint32_t, bool>> order_r;
+        std::vector<char> vis(n, 0);
+        std::vector<std::pair<uint32_t, int>> st{{r, 0}};
+        vis[r] = 1;
+        uint32_t lvl = 0;
+        while (!st.empty()) {
+            auto& [x, k] = st.back();
+            if (x != r && is_root[x]) {          // another cacheable node: load its value
+                order_r.push_back({x, true});
+                lvl = std::max(lvl, level_of[x] + 1);
+                st.pop_back();
+                continue;
+            }
+            if (k < 4) {
+                int32_t y = g[x].in[k++];
+                if (y >= 0 && !vis[y]) {
+                    vis[y] = 1;
+                    st.push_back({(uint32_t)y, 0});
+                }
+                continue;
+            }
+            order_r.push_back({x, false});
+            st.pop_back();
+        }
+        level_of[r] = lvl;
+        out->root_level[ri] = lvl;
+        uint32_t os = 0;
+        out->root_slots[ri] = emit_standalone(g, order_r, ordinal, r, true, &out->root_progs[ri],
+                                              &out->params, &os);
+        out->root_out_slot[ri] = os;
+        if (out->root_slots[ri] >= NO_SLOT) { *why = "too many live values"; return false; }
+    }
     return true;
 }
 

@@ -3,14 +3,21 @@
 //   k_hist     material histogram of the batch (+ range check of material indices)
 //   k_scan     per-material segment offsets, probe offsets and warp work items
 //   k_scatter  groups the points by material into structure-of-arrays copies
-//   k_lookup   warp-cooperative probes of every (point, cacheable node) against the
-//              table as it was when the pass started (Sec. 3.2, Fig. 3)
-//   k_eval     warp-uniform interpreter of the material programs (Sec. 2); hit blocks
-//              are skipped, missed cacheable nodes become insert candidates (Sec. 3)
-//   k_claim /  rounds of the insert: every live candidate targets the first slot of
-//   k_resolve  its cell holding its hash2 (duplicate) or 0 (free, Alg. 1); the smallest
-//              (point index, node ID) per cell wins by atomicMin and writes its slot
+//   k_lookup   probes of every (point, cacheable node) against the table as it was
+//              when the pass started (Sec. 3.2, Fig. 3); several probes in flight per lane
+//   k_scan_roots / k_eval_roots
+//              the missed cacheable nodes, listed per node by k_lookup, evaluated 32 at a
+//              time with each node's standalone program; values go back into the probe
+//              records and become insert candidates (Sec. 3)
+//   k_eval     warp-uniform interpreter of the material programs (Sec. 2); every cached
+//              or computed block is skipped by the whole warp
+//   k_insert   rounds of the insert in one cooperative launch: every live candidate
+//              targets the first slot of its cell holding its hash2 (duplicate) or 0
+//              (free, Alg. 1); the smallest (point index, node ID) per cell wins by
+//              atomicMin and writes its slot
 //   k_finish   advances the claim epoch and the batch counters
+#include <algorithm>
+#include <cstddef>
 #include <cstdio>
 
 #include "pmc_internal.h"
@@ -80,47 +87,50 @@ __device__ __forceinline__ uint32_t d_lattice(int i, int j, uint32_t seed) {
     return d_fmix32(((uint32_t)i * 73856093u) ^ ((uint32_t)j * 19349663u) ^ (seed * 83492791u));
 }
 
-// Gradient k of the 8 unit vectors at multiples of 45 degrees: x component.
-// |gx| = 1 for k in {0,4}, 0 for {2,6}, sqrt(1/2) for odd k; negative for k in {3,4,5}.
-__device__ __forceinline__ float d_gx(uint32_t k) {
-    float m = (k & 1u) ? 0.70710678118654752f : ((k & 2u) ? 0.0f : 1.0f);
-    return ((k + 1u) & 4u) ? -m : m;
+// The 8 unit gradients at multiples of 45 degrees, indexed by hash & 7; each kernel that
+// evaluates noise keeps a copy in shared memory (one 8-byte load per lattice corner).
+__device__ __forceinline__ void init_gradients(float2* g) {
+    if (threadIdx.x < 8) {
+        const float R = 0.70710678118654752f;
+        const float gx[8] = {1.0f, R, 0.0f, -R, -1.0f, -R, 0.0f, R};
+        const float gy[8] = {0.0f, R, 1.0f, R, 0.0f, -R, -1.0f, -R};
+        g[threadIdx.x] = make_float2(gx[threadIdx.x], gy[threadIdx.x]);
+    }
 }
-// y component: the x component of the gradient 90 degrees earlier.
-__device__ __forceinline__ float d_gy(uint32_t k) { return d_gx((k + 6u) & 7u); }
 
 __device__ __forceinline__ float d_fade(float t) {
     return t * t * t * fmaf(t, fmaf(t, 6.0f, -15.0f), 10.0f);
 }
 
-__device__ __forceinline__ float d_perlin(float x, float y, uint32_t seed) {
+__device__ __forceinline__ float d_perlin(float x, float y, uint32_t seed, const float2* grad) {
     float fx0 = floorf(x), fy0 = floorf(y);
     int ix = (int)fx0, iy = (int)fy0;
     float fx = x - fx0, fy = y - fy0;
     float fx1 = fx - 1.0f, fy1 = fy - 1.0f;
-    uint32_t h00 = d_lattice(ix, iy, seed) & 7u;
-    uint32_t h10 = d_lattice(ix + 1, iy, seed) & 7u;
-    uint32_t h01 = d_lattice(ix, iy + 1, seed) & 7u;
-    uint32_t h11 = d_lattice(ix + 1, iy + 1, seed) & 7u;
-    float d00 = fmaf(d_gx(h00), fx, d_gy(h00) * fy);
-    float d10 = fmaf(d_gx(h10), fx1, d_gy(h10) * fy);
-    float d01 = fmaf(d_gx(h01), fx, d_gy(h01) * fy1);
-    float d11 = fmaf(d_gx(h11), fx1, d_gy(h11) * fy1);
+    const float2 g00 = grad[d_lattice(ix, iy, seed) & 7u];
+    const float2 g10 = grad[d_lattice(ix + 1, iy, seed) & 7u];
+    const float2 g01 = grad[d_lattice(ix, iy + 1, seed) & 7u];
+    const float2 g11 = grad[d_lattice(ix + 1, iy + 1, seed) & 7u];
+    float d00 = fmaf(g00.x, fx, g00.y * fy);
+    float d10 = fmaf(g10.x, fx1, g10.y * fy);
+    float d01 = fmaf(g01.x, fx, g01.y * fy1);
+    float d11 = fmaf(g11.x, fx1, g11.y * fy1);
     float su = d_fade(fx), sv = d_fade(fy);
     float a = fmaf(su, d10 - d00, d00);
     float b = fmaf(su, d11 - d01, d01);
     return fmaf(sv, b - a, a);
 }
 
-__device__ __forceinline__ float d_clamp01(float x) { return fminf(fmaxf(x, 0.0f), 1.0f); }
+// clamp to [0, 1] (NaN to 0) as a saturating modifier of the producing instruction
+__device__ __forceinline__ float d_clamp01(float x) { return __saturatef(x); }
 
-__device__ __forceinline__ float d_fbm(float x, float y, const float* p) {
+__device__ __forceinline__ float d_fbm(float x, float y, const float* p, const float2* grad) {
     float scale = p[0], lac = p[1], gain = p[2], inv_norm = p[3];
     int oct = __float_as_int(p[4]);
     uint32_t seed = (uint32_t)__float_as_int(p[5]);
     float sum = 0.0f, amp = 1.0f, freq = scale;
     for (int k = 0; k < oct; ++k) {
-        sum = fmaf(amp, d_perlin(x * freq, y * freq, seed + (uint32_t)k), sum);
+        sum = fmaf(amp, d_perlin(x * freq, y * freq, seed + (uint32_t)k, grad), sum);
         amp *= gain;
         freq *= lac;
     }
@@ -186,12 +196,28 @@ __device__ __forceinline__ uint32_t find_material(const uint32_t* item_base, uin
 // =======================================================================================
 // Grouping by material
 // =======================================================================================
-__global__ void k_hist(BatchArgs a) {
-    uint32_t stride = gridDim.x * blockDim.x;
-    uint32_t n_round = (a.n + 31u) & ~31u;
+// Materials counted in shared memory per block; beyond this the counters are global.
+constexpr uint32_t GROUP_SMEM_MATS = 4096;
+
+// Points of block b: the contiguous range [b * chunk, min(n, (b + 1) * chunk)).
+__device__ __forceinline__ void block_range(uint32_t n, uint32_t* lo, uint32_t* hi) {
+    const uint32_t chunk = ((n + gridDim.x - 1) / gridDim.x + 31u) & ~31u;
+    *lo = min(n, blockIdx.x * chunk);
+    *hi = min(n, *lo + chunk);
+}
+
+__global__ void __launch_bounds__(256) k_hist(BatchArgs a) {
+    __shared__ uint32_t s_cnt[GROUP_SMEM_MATS];
+    const bool local = a.n_mats <= GROUP_SMEM_MATS;
+    if (local) {
+        for (uint32_t m = threadIdx.x; m < a.n_mats; m += blockDim.x) s_cnt[m] = 0;
+        __syncthreads();
+    }
+    uint32_t lo, hi;
+    block_range(a.n, &lo, &hi);
     unsigned long long bad = 0;
-    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n_round; i += stride) {
-        bool act = i < a.n;
+    for (uint32_t i = lo + threadIdx.x; i < ((hi + 31u) & ~31u) && lo < hi; i += blockDim.x) {
+        bool act = i < hi;
         uint32_t m = act ? a.mat[i] : 0u;
         bool ok = act && m < a.n_mats;
         if (act && !ok) bad++;
@@ -199,8 +225,13 @@ __global__ void k_hist(BatchArgs a) {
         if (ok) {
             unsigned peers = __match_any_sync(vmask, m);
             int leader = __ffs(peers) - 1;
-            if ((int)lane_id() == leader) atomicAdd(&a.counts[m], (uint32_t)__popc(peers));
+            if ((int)lane_id() == leader) atomicAdd(local ? &s_cnt[m] : &a.counts[m], (uint32_t)__popc(peers));
         }
+    }
+    if (local) {
+        __syncthreads();
+        for (uint32_t m = threadIdx.x; m < a.n_mats; m += blockDim.x)
+            if (s_cnt[m]) atomicAdd(&a.counts[m], s_cnt[m]);
     }
     unsigned long long tot = bad;
 #pragma unroll
@@ -258,110 +289,176 @@ __global__ void k_scan(BatchArgs a) {
     }
 }
 
-__global__ void k_scatter(BatchArgs a) {
-    uint32_t stride = gridDim.x * blockDim.x;
-    uint32_t n_round = (a.n + 31u) & ~31u;
-    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n_round; i += stride) {
-        bool act = i < a.n;
-        uint32_t m = act ? a.mat[i] : 0u;
-        bool ok = act && m < a.n_mats;
-        unsigned vmask = __ballot_sync(FULL_MASK, ok);
+__device__ __forceinline__ void scatter_point(const BatchArgs& a, uint32_t i, uint32_t pos) {
+    a.su[pos] = a.u[i];
+    a.sv[pos] = a.v[i];
+    a.spx[pos] = a.px[i];
+    a.spy[pos] = a.py[i];
+    a.spz[pos] = a.pz[i];
+    a.snx[pos] = a.nx[i];
+    a.sny[pos] = a.ny[i];
+    a.snz[pos] = a.nz[i];
+    a.sidx[pos] = i;
+}
+
+__device__ __forceinline__ void zero_output(const BatchArgs& a, uint32_t i) {
+    // out-of-range material: zero output, no probes
+    a.out_rgb[i] = 0.0f;
+    a.out_rgb[(size_t)a.n + i] = 0.0f;
+    a.out_rgb[2 * (size_t)a.n + i] = 0.0f;
+    if (a.out_hits) a.out_hits[i] = 0;
+}
+
+// Groups the block's contiguous range of points by material.  With few materials the
+// block counts its points per material in shared memory, reserves one range per
+// material with a single global atomic, then hands out positions from shared counters.
+__global__ void __launch_bounds__(256) k_scatter(BatchArgs a) {
+    __shared__ uint32_t s_cnt[GROUP_SMEM_MATS];
+    const bool local = a.n_mats <= GROUP_SMEM_MATS;
+    uint32_t lo, hi;
+    block_range(a.n, &lo, &hi);
+    const uint32_t hi32 = (hi + 31u) & ~31u;
+    if (local) {
+        for (uint32_t m = threadIdx.x; m < a.n_mats; m += blockDim.x) s_cnt[m] = 0;
+        __syncthreads();
+        for (uint32_t i = lo + threadIdx.x; i < hi32 && lo < hi; i += blockDim.x) {
+            const bool act = i < hi;
+            const uint32_t m = act ? a.mat[i] : 0u;
+            const bool ok = act && m < a.n_mats;
+            const unsigned vmask = __ballot_sync(FULL_MASK, ok);
+            if (ok) {
+                const unsigned peers = __match_any_sync(vmask, m);
+                if ((int)lane_id() == __ffs(peers) - 1) atomicAdd(&s_cnt[m], (uint32_t)__popc(peers));
+            }
+        }
+        __syncthreads();
+        // the block's first position in each material segment
+        for (uint32_t m = threadIdx.x; m < a.n_mats; m += blockDim.x)
+            if (s_cnt[m]) s_cnt[m] = atomicAdd(&a.cursor[m], s_cnt[m]);
+        __syncthreads();
+    }
+    for (uint32_t i = lo + threadIdx.x; i < hi32 && lo < hi; i += blockDim.x) {
+        const bool act = i < hi;
+        const uint32_t m = act ? a.mat[i] : 0u;
+        const bool ok = act && m < a.n_mats;
+        const unsigned vmask = __ballot_sync(FULL_MASK, ok);
         if (ok) {
-            unsigned peers = __match_any_sync(vmask, m);
-            int leader = __ffs(peers) - 1;
+            const unsigned peers = __match_any_sync(vmask, m);
+            const int leader = __ffs(peers) - 1;
             uint32_t base = 0;
-            if ((int)lane_id() == leader) base = atomicAdd(&a.cursor[m], (uint32_t)__popc(peers));
+            if ((int)lane_id() == leader)
+                base = atomicAdd(local ? &s_cnt[m] : &a.cursor[m], (uint32_t)__popc(peers));
             base = __shfl_sync(peers, base, leader);
-            uint32_t pos = base + __popc(peers & ((1u << lane_id()) - 1u));
-            a.su[pos] = a.u[i];
-            a.sv[pos] = a.v[i];
-            a.spx[pos] = a.px[i];
-            a.spy[pos] = a.py[i];
-            a.spz[pos] = a.pz[i];
-            a.snx[pos] = a.nx[i];
-            a.sny[pos] = a.ny[i];
-            a.snz[pos] = a.nz[i];
-            a.sidx[pos] = i;
+            scatter_point(a, i, base + __popc(peers & ((1u << lane_id()) - 1u)));
         } else if (act) {
-            // out-of-range material: zero output, no probes
-            a.out_rgb[i] = 0.0f;
-            a.out_rgb[(size_t)a.n + i] = 0.0f;
-            a.out_rgb[2 * (size_t)a.n + i] = 0.0f;
-            if (a.out_hits) a.out_hits[i] = 0;
+            zero_output(a, i);
         }
     }
 }
 
 // =======================================================================================
-// Lookup (Sec. 3.2): G lanes read one cell (one 16-byte slot each) per step
+// Lookup (Sec. 3.2).  Table cell c (16 * N_e bytes): N_e hash2 words, then N_e packed
+// (r, g, b) values.  A probe reads the cell's hash2 words (one 32-byte sector for N_e = 8)
+// and, on a hit, the 12 bytes of the matching value in the same line.
 // =======================================================================================
-constexpr uint32_t PROBE_HIT = 1u;
+constexpr uint32_t PROBE_MISS = 0u;   // record {cell, hash2, first empty slot, 0}
+constexpr uint32_t PROBE_HIT = 1u;    // record {r, g, b, 1}
+constexpr uint32_t PROBE_FULL = 2u;   // record {cell, hash2, N_e, 2}: no empty slot
 
-template <int G>
+__device__ __forceinline__ const uint32_t* cell_words(const uint4* table, uint32_t cell, uint32_t ne) {
+    return reinterpret_cast<const uint32_t*>(table) + (size_t)cell * 4u * ne;
+}
+
+// Scans the hash2 words of a cell held in registers: first slot holding h2 (hit) or 0.
+template <int NQ>
+__device__ __forceinline__ int scan_words(const uint4 (&w)[NQ], uint32_t h2, uint32_t ne, bool* hit) {
+    int first = -1;
+    *hit = false;
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) {
+        const uint32_t v[4] = {w[q].x, w[q].y, w[q].z, w[q].w};
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const uint32_t idx = 4u * q + k;
+            if (first < 0 && idx < ne && (v[k] == h2 || v[k] == 0u)) {
+                first = (int)idx;
+                *hit = v[k] == h2;
+            }
+        }
+    }
+    return first;
+}
+
+// NQ = 16-byte words of hash2 per cell (ceil(N_e / 4)); RB probes in flight per lane.
+template <int NQ, int RB>
 __global__ void __launch_bounds__(256) k_lookup(BatchArgs a) {
-    constexpr int P = 32 / G;  // probes per step
-    __shared__ uint32_t s_cell[8][32];
-    __shared__ uint32_t s_h2[8][32];
     const uint32_t warp = threadIdx.x >> 5, lane = lane_id();
     const uint32_t warps_total = gridDim.x * (blockDim.x >> 5);
     const uint32_t n_items = a.ctl->n_items;
     const uint32_t ne = a.n_entries;
     unsigned long long n_look = 0, n_hit = 0, n_slots = 0;
     for (uint32_t item = blockIdx.x * (blockDim.x >> 5) + warp; item < n_items; item += warps_total) {
-        uint32_t m = find_material(a.item_base, a.n_mats, item);
-        uint32_t cnt = __ldg(&a.counts[m]);
-        uint32_t j = (item - __ldg(&a.item_base[m])) * 32u + lane;
-        bool valid = j < cnt;
-        uint32_t s = __ldg(&a.seg_start[m]) + j;
+        const uint32_t m = find_material(a.item_base, a.n_mats, item);
+        const uint32_t cnt = __ldg(&a.counts[m]);
+        const uint32_t j = (item - __ldg(&a.item_base[m])) * 32u + lane;
+        const bool valid = j < cnt;
+        const uint32_t s = __ldg(&a.seg_start[m]) + j;
         uint32_t iu = 0, iv = 0;
         if (valid) {
             iu = d_texel(a.su[s], a.level);
             iv = d_texel(a.sv[s], a.level);
         }
         const MatInfo mi = a.mats[m];
-        const uint32_t pbase = __ldg(&a.probe_base[m]);
-        for (uint32_t r = 0; r < mi.n_roots; ++r) {
-            uint32_t node = __ldg(&a.roots[mi.root_base + r]);
-            uint32_t cell = 0, h2 = 0;
-            if (valid) d_address(d_key(m, node, a.level, iu, iv), a.n_cells, a.cells_pow2_mask, &cell, &h2);
-            s_cell[warp][lane] = cell;
-            s_h2[warp][lane] = valid ? h2 : 0u;
-            __syncwarp();
-            const uint32_t e = lane % G;
-            const uint32_t grp = lane / G;
+        const size_t rec0 = (size_t)__ldg(&a.probe_base[m]) + j;
+        for (uint32_t r0 = 0; r0 < mi.n_roots; r0 += RB) {
+            uint4 w[RB][NQ];
+            uint32_t cell[RB], h2[RB];
 #pragma unroll
-            for (int step = 0; step < G; ++step) {
-                const uint32_t q = step * P + grp;      // probe of this lane in this step
-                const uint32_t qh2 = s_h2[warp][q];     // 0 = invalid probe
-                const uint32_t qcell = s_cell[warp][q];
-                uint4 slot = make_uint4(0xFFFFFFFFu, 0, 0, 0);
-                bool ld = qh2 != 0u && e < ne;
-                if (ld) slot = __ldg(&a.table[(size_t)qcell * ne + e]);
-                bool match = ld && slot.x == qh2;
-                bool stop = ld && (slot.x == qh2 || slot.x == 0u);
-                unsigned sb = __ballot_sync(FULL_MASK, stop);
-                unsigned mb = __ballot_sync(FULL_MASK, match);
-                const unsigned gmask = (G == 32) ? FULL_MASK : (((1u << G) - 1u) << (grp * G));
-                unsigned gs = sb & gmask;
-                int first = gs ? (__ffs(gs) - 1) : -1;   // lane index of the first stop
-                if (qh2 != 0u) {
-                    size_t rec = (size_t)pbase + (size_t)r * cnt + (item - __ldg(&a.item_base[m])) * 32u + q;
-                    bool hit = first >= 0 && ((mb >> first) & 1u);
-                    if (hit && (int)lane == first) {
-                        a.probes[rec] = make_float4(__uint_as_float(slot.y), __uint_as_float(slot.z),
-                                                    __uint_as_float(slot.w), __uint_as_float(PROBE_HIT));
+            for (int b = 0; b < RB; ++b) {
+                const bool act = valid && r0 + b < mi.n_roots;
+                cell[b] = 0;
+                h2[b] = 0;
+                if (act) {
+                    const uint32_t node = __ldg(&a.roots[mi.root_base + r0 + b]);
+                    d_address(d_key(m, node, a.level, iu, iv), a.n_cells, a.cells_pow2_mask, &cell[b], &h2[b]);
+                }
+                const uint4* cw = reinterpret_cast<const uint4*>(cell_words(a.table, cell[b], ne));
+#pragma unroll
+                for (int q = 0; q < NQ; ++q) w[b][q] = act ? __ldg(cw + q) : make_uint4(0, 0, 0, 0);
+            }
+#pragma unroll
+            for (int b = 0; b < RB; ++b) {
+                if (r0 + b >= mi.n_roots) break;                 // uniform in the warp
+                bool hit = false;
+                const size_t rec = rec0 + (size_t)(r0 + b) * cnt;
+                if (valid) {
+                    const int first = scan_words<NQ>(w[b], h2[b], ne, &hit);
+                    n_look++;
+                    n_slots += first >= 0 ? (uint32_t)first + 1u : ne;
+                    if (hit) {
+                        const float* val = reinterpret_cast<const float*>(cell_words(a.table, cell[b], ne) + ne) + 3u * (uint32_t)first;
+                        a.probes[rec] = make_float4(__ldg(val), __ldg(val + 1), __ldg(val + 2), __uint_as_float(PROBE_HIT));
+                        n_hit++;
+                    } else {
+                        a.probes[rec] = make_float4(__uint_as_float(cell[b]), __uint_as_float(h2[b]),
+                                                    __uint_as_float(first >= 0 ? (uint32_t)first : ne),
+                                                    __uint_as_float(first >= 0 ? PROBE_MISS : PROBE_FULL));
                     }
-                    if (e == 0) {
-                        n_look++;
-                        n_slots += first >= 0 ? (uint32_t)(first - (int)(grp * G)) + 1u : ne;
-                        if (hit) n_hit++;
-                        if (!hit)
-                            a.probes[rec] = make_float4(__uint_as_float(qcell), __uint_as_float(qh2), 0.0f,
-                                                        __uint_as_float(0u));
+                }
+                if (a.split) {
+                    // list the misses of this cacheable node for the batched evaluation
+                    const bool miss = valid && !hit;
+                    const unsigned mm = __ballot_sync(FULL_MASK, miss);
+                    if (mm) {
+                        const int leader = __ffs(mm) - 1;
+                        uint32_t base = 0;
+                        if ((int)lane == leader) base = atomicAdd(&a.miss_cnt[mi.root_base + r0 + b], (uint32_t)__popc(mm));
+                        base = __shfl_sync(FULL_MASK, base, leader);
+                        if (miss)
+                            a.misslist[rec0 - j + (size_t)(r0 + b) * cnt + base + __popc(mm & ((1u << lane) - 1u))] = j;
                     }
                 }
             }
-            __syncwarp();
         }
     }
     warp_add_u64(&a.stats[ST_LOOKUPS], n_look);
@@ -371,20 +468,167 @@ __global__ void __launch_bounds__(256) k_lookup(BatchArgs a) {
 }
 
 // =======================================================================================
-// Evaluation (Sec. 2, Sec. 3): one warp runs one material's program for 32 points
+// Evaluation (Sec. 2, Sec. 3)
 // =======================================================================================
+constexpr uint32_t PROBE_COMPUTED = 3u;   // record {r, g, b, 3}: a miss evaluated this pass
 constexpr uint32_t EVAL_WARPS = 4;
 
 size_t eval_smem_bytes(uint32_t max_slots) {
     return (size_t)EVAL_WARPS * max_slots * 3u * 32u * sizeof(float);
 }
 
+struct PointIn {
+    float u, v, px, py, pz, nx, ny, nz;
+};
+
+// One node instruction for one lane.  V points at the lane's slot file, laid out
+// [slot][channel][lane] so that the 32 lanes of a warp touch 32 consecutive words.
+__device__ __forceinline__ void exec_node(uint32_t op, const uint4& ins, float* V, const PointIn& pt,
+                                          const float* __restrict__ params, const float2* grad) {
+    const uint32_t out = ins.y & 0xFFFFu;
+    const uint32_t i0 = ins.y >> 16, i1 = ins.z & 0xFFFFu, i2 = ins.z >> 16;
+    const float* p = params + ins.w;
+    float r0 = 0.f, r1 = 0.f, r2 = 0.f;
+    switch (op) {
+    case PMC_OP_UV: r0 = pt.u; r1 = pt.v; break;
+    case PMC_OP_POSITION: r0 = pt.px; r1 = pt.py; r2 = pt.pz; break;
+    case PMC_OP_NORMAL: r0 = pt.nx; r1 = pt.ny; r2 = pt.nz; break;
+    case PMC_OP_CONST: r0 = __ldg(&p[0]); r1 = __ldg(&p[1]); r2 = __ldg(&p[2]); break;
+    case PMC_OP_UV_AFFINE: {
+        float x = V[(i0 * 3) * 32], y = V[(i0 * 3 + 1) * 32];
+        r0 = fmaf(__ldg(&p[0]), x, fmaf(__ldg(&p[1]), y, __ldg(&p[4])));
+        r1 = fmaf(__ldg(&p[2]), x, fmaf(__ldg(&p[3]), y, __ldg(&p[5])));
+        break;
+    }
+    case PMC_OP_FBM: {
+        float pp[6];
+#pragma unroll
+        for (int k = 0; k < 6; ++k) pp[k] = __ldg(&p[k]);
+        r0 = r1 = r2 = d_fbm(V[(i0 * 3) * 32], V[(i0 * 3 + 1) * 32], pp, grad);
+        break;
+    }
+    case PMC_OP_VORONOI: {
+        float pp[2] = {__ldg(&p[0]), __ldg(&p[1])};
+        r0 = r1 = r2 = d_voronoi(V[(i0 * 3) * 32], V[(i0 * 3 + 1) * 32], pp);
+        break;
+    }
+    case PMC_OP_CHECKER: {
+        float sc = __ldg(&p[0]);
+        long long k = (long long)floorf(V[(i0 * 3) * 32] * sc) + (long long)floorf(V[(i0 * 3 + 1) * 32] * sc);
+        const float* c = (k & 1) ? p + 4 : p + 1;
+        r0 = d_clamp01(__ldg(&c[0])); r1 = d_clamp01(__ldg(&c[1])); r2 = d_clamp01(__ldg(&c[2]));
+        break;
+    }
+    case PMC_OP_RAMP: {
+        int ns = __float_as_int(__ldg(&p[0]));
+        const float* pos = p + 1;
+        const float* col = p + 5;
+        float t = d_clamp01(V[(i0 * 3) * 32]);
+        if (t <= __ldg(&pos[0])) {
+            r0 = __ldg(&col[0]); r1 = __ldg(&col[1]); r2 = __ldg(&col[2]);
+        } else if (t >= __ldg(&pos[ns - 1])) {
+            r0 = __ldg(&col[3 * (ns - 1)]); r1 = __ldg(&col[3 * (ns - 1) + 1]); r2 = __ldg(&col[3 * (ns - 1) + 2]);
+        } else {
+            int k = 0;
+            while (k + 2 < ns && t >= __ldg(&pos[k + 1])) ++k;
+            float p0 = __ldg(&pos[k]), p1 = __ldg(&pos[k + 1]);
+            float w = (t - p0) / (p1 - p0);
+            float a0 = __ldg(&col[3 * k]), a1 = __ldg(&col[3 * k + 1]), a2 = __ldg(&col[3 * k + 2]);
+            r0 = fmaf(w, __ldg(&col[3 * k + 3]) - a0, a0);
+            r1 = fmaf(w, __ldg(&col[3 * k + 4]) - a1, a1);
+            r2 = fmaf(w, __ldg(&col[3 * k + 5]) - a2, a2);
+        }
+        r0 = d_clamp01(r0); r1 = d_clamp01(r1); r2 = d_clamp01(r2);
+        break;
+    }
+    case PMC_OP_MIX: {
+        float f = d_clamp01(i2 != 0xFFFFu ? V[(i2 * 3) * 32] : __ldg(&p[0]));
+        float a0 = V[(i0 * 3) * 32], a1 = V[(i0 * 3 + 1) * 32], a2 = V[(i0 * 3 + 2) * 32];
+        r0 = d_clamp01(fmaf(f, V[(i1 * 3) * 32] - a0, a0));
+        r1 = d_clamp01(fmaf(f, V[(i1 * 3 + 1) * 32] - a1, a1));
+        r2 = d_clamp01(fmaf(f, V[(i1 * 3 + 2) * 32] - a2, a2));
+        break;
+    }
+    case PMC_OP_ADD:
+        r0 = d_clamp01(V[(i0 * 3) * 32] + V[(i1 * 3) * 32]);
+        r1 = d_clamp01(V[(i0 * 3 + 1) * 32] + V[(i1 * 3 + 1) * 32]);
+        r2 = d_clamp01(V[(i0 * 3 + 2) * 32] + V[(i1 * 3 + 2) * 32]);
+        break;
+    case PMC_OP_MUL:
+        r0 = d_clamp01(V[(i0 * 3) * 32] * V[(i1 * 3) * 32]);
+        r1 = d_clamp01(V[(i0 * 3 + 1) * 32] * V[(i1 * 3 + 1) * 32]);
+        r2 = d_clamp01(V[(i0 * 3 + 2) * 32] * V[(i1 * 3 + 2) * 32]);
+        break;
+    case PMC_OP_POW: {
+        float e = __ldg(&p[0]);
+        r0 = d_clamp01(powf(fmaxf(V[(i0 * 3) * 32], 0.0f), e));
+        r1 = d_clamp01(powf(fmaxf(V[(i0 * 3 + 1) * 32], 0.0f), e));
+        r2 = d_clamp01(powf(fmaxf(V[(i0 * 3 + 2) * 32], 0.0f), e));
+        break;
+    }
+    case PMC_OP_FACING: {
+        float d = fmaf(V[(i0 * 3) * 32], __ldg(&p[0]),
+                       fmaf(V[(i0 * 3 + 1) * 32], __ldg(&p[1]), V[(i0 * 3 + 2) * 32] * __ldg(&p[2])));
+        r0 = r1 = r2 = d_clamp01(fabsf(d));
+        break;
+    }
+    default:
+        break;
+    }
+    V[(out * 3) * 32] = r0;
+    V[(out * 3 + 1) * 32] = r1;
+    V[(out * 3 + 2) * 32] = r2;
+}
+
+// Offers the lanes' freshly evaluated cacheable-node values to the table (Sec. 3).
+// A cell that was full at lookup stays full (nothing is evicted), so its value is
+// counted as dropped without becoming a candidate.  Lanes carrying the same
+// (cell, hash2) collapse onto the smallest point index; the others share its fate.
+// Must be called by all 32 lanes.
+__device__ __forceinline__ void offer(const BatchArgs& a, bool act, uint32_t orig, uint32_t node, uint32_t cell,
+                                      uint32_t h2, uint32_t start, bool full, float r, float g, float b,
+                                      unsigned long long* n_cand, unsigned long long* n_full) {
+    *n_cand += act ? 1u : 0u;
+    *n_full += (act && full) ? 1u : 0u;
+    const bool emit = act && !full;
+    bool winner = false;
+    uint32_t shadows = 0;
+    const unsigned em = __ballot_sync(FULL_MASK, emit);
+    if (emit) {
+        const unsigned long long k64 = ((unsigned long long)cell << 32) | h2;
+        const unsigned grp = __match_any_sync(em, k64);
+        const uint32_t mn = __reduce_min_sync(grp, orig);
+        winner = orig == mn;
+        shadows = (uint32_t)__popc(grp) - 1u;
+    }
+    const uint32_t idx = warp_append(&a.ctl->n_cand, winner);
+    if (winner) {
+        Candidate c;
+        c.prio = ((unsigned long long)orig << 16) | node;
+        c.cell = cell;
+        c.h2 = h2;
+        c.r = r;
+        c.g = g;
+        c.b = b;
+        c.target = start | (shadows << 16);
+        if (idx < a.probe_cap) a.cands[idx] = c;
+        else atomicOr(&a.ctl->err, ERR_BOUNDS);
+    }
+}
+
+// Per-point interpreter: one warp runs one material's program for 32 grouped points.
+// split == 1: every cacheable node already has its value in its probe record (a hit,
+// or computed by k_eval_roots), so every block is skipped by the whole warp.
+// split == 0: a lane whose lookup hit skips the block, the others evaluate it inline.
 __global__ void __launch_bounds__(EVAL_WARPS * 32) k_eval(BatchArgs a, uint32_t* item_ctr) {
     extern __shared__ float s_val[];
+    __shared__ float2 s_grad[8];
+    init_gradients(s_grad);
+    __syncthreads();
     const uint32_t warp = threadIdx.x >> 5, lane = lane_id();
-    float* V = s_val + (size_t)warp * a.max_slots * 96u + lane;   // V[(slot*3 + c) * 32]
+    float* V = s_val + (size_t)warp * a.max_slots * 96u + lane;
     const uint32_t n_items = a.ctl->n_items;
-    unsigned long long n_nodes = 0, n_flops = 0;
+    unsigned long long n_nodes = 0, n_flops = 0, n_cand = 0, n_full = 0;
     for (;;) {
         uint32_t item = 0;
         if (lane == 0) item = atomicAdd(item_ctr, 1u);
@@ -395,19 +639,20 @@ __global__ void __launch_bounds__(EVAL_WARPS * 32) k_eval(BatchArgs a, uint32_t*
         const uint32_t j = (item - __ldg(&a.item_base[m])) * 32u + lane;
         const bool valid = j < cnt;
         const uint32_t s = __ldg(&a.seg_start[m]) + (valid ? j : 0u);
-        float u = 0, v = 0, px = 0, py = 0, pz = 0, nx = 0, ny = 0, nz = 0;
+        PointIn pt{0, 0, 0, 0, 0, 0, 0, 0};
         uint32_t orig = 0;
         if (valid) {
-            u = a.su[s]; v = a.sv[s];
-            px = a.spx[s]; py = a.spy[s]; pz = a.spz[s];
-            nx = a.snx[s]; ny = a.sny[s]; nz = a.snz[s];
+            pt.u = a.su[s]; pt.v = a.sv[s];
+            pt.px = a.spx[s]; pt.py = a.spy[s]; pt.pz = a.spz[s];
+            pt.nx = a.snx[s]; pt.ny = a.sny[s]; pt.nz = a.snz[s];
             orig = a.sidx[s];
         }
         const MatInfo mi = a.mats[m];
         const uint4* prog = a.prog + mi.prog_start;
         const uint32_t pbase = __ldg(&a.probe_base[m]);
         int skip_end = -1;          // lane inactive while pc <= skip_end
-        uint32_t hits = 0, cand_cell = 0, cand_h2 = 0, cand_node = 0;
+        uint32_t hits = 0, cand_cell = 0, cand_h2 = 0, cand_node = 0, cand_start = 0;
+        bool cand_full = false;
         for (int pc = 0; pc < (int)mi.prog_len; ++pc) {
             const uint4 ins = __ldg(&prog[pc]);
             const uint32_t op = ins.x & 0xFFu;
@@ -415,16 +660,22 @@ __global__ void __launch_bounds__(EVAL_WARPS * 32) k_eval(BatchArgs a, uint32_t*
                 const uint32_t slot = ins.y & 0xFFFFu, r = ins.y >> 16;
                 bool need = valid;
                 if (a.use_cache && valid) {
-                    float4 rec = a.probes[(size_t)pbase + (size_t)r * cnt + j];
-                    if (__float_as_uint(rec.w) == PROBE_HIT) {
+                    const float4 rec = a.probes[(size_t)pbase + (size_t)r * cnt + j];
+                    const uint32_t state = __float_as_uint(rec.w);
+                    if (state == PROBE_HIT || state == PROBE_COMPUTED) {
                         V[(slot * 3 + 0) * 32] = rec.x;
                         V[(slot * 3 + 1) * 32] = rec.y;
                         V[(slot * 3 + 2) * 32] = rec.z;
-                        hits++;
+                        hits += state == PROBE_HIT ? 1u : 0u;
+                        need = false;
+                    } else if (a.split) {
+                        atomicOr(&a.ctl->err, ERR_BOUNDS);   // the batched evaluation missed it
                         need = false;
                     } else {
                         cand_cell = __float_as_uint(rec.x);
                         cand_h2 = __float_as_uint(rec.y);
+                        cand_start = __float_as_uint(rec.z);
+                        cand_full = state == PROBE_FULL;
                         cand_node = ins.z;
                     }
                 }
@@ -433,119 +684,15 @@ __global__ void __launch_bounds__(EVAL_WARPS * 32) k_eval(BatchArgs a, uint32_t*
                 continue;
             }
             const bool act = valid && pc > skip_end;
-            const uint32_t out = ins.y & 0xFFFFu;
-            const uint32_t i0 = ins.y >> 16, i1 = ins.z & 0xFFFFu, i2 = ins.z >> 16;
-            const float* p = a.params + ins.w;
             if (act) {
-                float r0 = 0.f, r1 = 0.f, r2 = 0.f;
-                switch (op) {
-                case PMC_OP_UV: r0 = u; r1 = v; break;
-                case PMC_OP_POSITION: r0 = px; r1 = py; r2 = pz; break;
-                case PMC_OP_NORMAL: r0 = nx; r1 = ny; r2 = nz; break;
-                case PMC_OP_CONST: r0 = __ldg(&p[0]); r1 = __ldg(&p[1]); r2 = __ldg(&p[2]); break;
-                case PMC_OP_UV_AFFINE: {
-                    float x = V[(i0 * 3) * 32], y = V[(i0 * 3 + 1) * 32];
-                    r0 = fmaf(__ldg(&p[0]), x, fmaf(__ldg(&p[1]), y, __ldg(&p[4])));
-                    r1 = fmaf(__ldg(&p[2]), x, fmaf(__ldg(&p[3]), y, __ldg(&p[5])));
-                    break;
-                }
-                case PMC_OP_FBM: {
-                    float pp[6];
-#pragma unroll
-                    for (int k = 0; k < 6; ++k) pp[k] = __ldg(&p[k]);
-                    r0 = r1 = r2 = d_fbm(V[(i0 * 3) * 32], V[(i0 * 3 + 1) * 32], pp);
-                    break;
-                }
-                case PMC_OP_VORONOI: {
-                    float pp[2] = {__ldg(&p[0]), __ldg(&p[1])};
-                    r0 = r1 = r2 = d_voronoi(V[(i0 * 3) * 32], V[(i0 * 3 + 1) * 32], pp);
-                    break;
-                }
-                case PMC_OP_CHECKER: {
-                    float sc = __ldg(&p[0]);
-                    long long k = (long long)floorf(V[(i0 * 3) * 32] * sc) + (long long)floorf(V[(i0 * 3 + 1) * 32] * sc);
-                    const float* c = (k & 1) ? p + 4 : p + 1;
-                    r0 = d_clamp01(__ldg(&c[0])); r1 = d_clamp01(__ldg(&c[1])); r2 = d_clamp01(__ldg(&c[2]));
-                    break;
-                }
-                case PMC_OP_RAMP: {
-                    int ns = __float_as_int(__ldg(&p[0]));
-                    const float* pos = p + 1;
-                    const float* col = p + 5;
-                    float t = d_clamp01(V[(i0 * 3) * 32]);
-                    if (t <= __ldg(&pos[0])) {
-                        r0 = __ldg(&col[0]); r1 = __ldg(&col[1]); r2 = __ldg(&col[2]);
-                    } else if (t >= __ldg(&pos[ns - 1])) {
-                        r0 = __ldg(&col[3 * (ns - 1)]); r1 = __ldg(&col[3 * (ns - 1) + 1]); r2 = __ldg(&col[3 * (ns - 1) + 2]);
-                    } else {
-                        int k = 0;
-                        while (k + 2 < ns && t >= __ldg(&pos[k + 1])) ++k;
-                        float p0 = __ldg(&pos[k]), p1 = __ldg(&pos[k + 1]);
-                        float w = (t - p0) / (p1 - p0);
-                        float a0 = __ldg(&col[3 * k]), a1 = __ldg(&col[3 * k + 1]), a2 = __ldg(&col[3 * k + 2]);
-                        r0 = fmaf(w, __ldg(&col[3 * k + 3]) - a0, a0);
-                        r1 = fmaf(w, __ldg(&col[3 * k + 4]) - a1, a1);
-                        r2 = fmaf(w, __ldg(&col[3 * k + 5]) - a2, a2);
-                    }
-                    r0 = d_clamp01(r0); r1 = d_clamp01(r1); r2 = d_clamp01(r2);
-                    break;
-                }
-                case PMC_OP_MIX: {
-                    float f = d_clamp01(i2 != 0xFFFFu ? V[(i2 * 3) * 32] : __ldg(&p[0]));
-                    float a0 = V[(i0 * 3) * 32], a1 = V[(i0 * 3 + 1) * 32], a2 = V[(i0 * 3 + 2) * 32];
-                    r0 = d_clamp01(fmaf(f, V[(i1 * 3) * 32] - a0, a0));
-                    r1 = d_clamp01(fmaf(f, V[(i1 * 3 + 1) * 32] - a1, a1));
-                    r2 = d_clamp01(fmaf(f, V[(i1 * 3 + 2) * 32] - a2, a2));
-                    break;
-                }
-                case PMC_OP_ADD:
-                    r0 = d_clamp01(V[(i0 * 3) * 32] + V[(i1 * 3) * 32]);
-                    r1 = d_clamp01(V[(i0 * 3 + 1) * 32] + V[(i1 * 3 + 1) * 32]);
-                    r2 = d_clamp01(V[(i0 * 3 + 2) * 32] + V[(i1 * 3 + 2) * 32]);
-                    break;
-                case PMC_OP_MUL:
-                    r0 = d_clamp01(V[(i0 * 3) * 32] * V[(i1 * 3) * 32]);
-                    r1 = d_clamp01(V[(i0 * 3 + 1) * 32] * V[(i1 * 3 + 1) * 32]);
-                    r2 = d_clamp01(V[(i0 * 3 + 2) * 32] * V[(i1 * 3 + 2) * 32]);
-                    break;
-                case PMC_OP_POW: {
-                    float e = __ldg(&p[0]);
-                    r0 = d_clamp01(powf(fmaxf(V[(i0 * 3) * 32], 0.0f), e));
-                    r1 = d_clamp01(powf(fmaxf(V[(i0 * 3 + 1) * 32], 0.0f), e));
-                    r2 = d_clamp01(powf(fmaxf(V[(i0 * 3 + 2) * 32], 0.0f), e));
-                    break;
-                }
-                case PMC_OP_FACING: {
-                    float d = fmaf(V[(i0 * 3) * 32], __ldg(&p[0]),
-                                   fmaf(V[(i0 * 3 + 1) * 32], __ldg(&p[1]), V[(i0 * 3 + 2) * 32] * __ldg(&p[2])));
-                    r0 = r1 = r2 = d_clamp01(fabsf(d));
-                    break;
-                }
-                default:
-                    break;
-                }
-                V[(out * 3) * 32] = r0;
-                V[(out * 3 + 1) * 32] = r1;
-                V[(out * 3 + 2) * 32] = r2;
+                exec_node(op, ins, V, pt, a.params, s_grad);
                 n_nodes++;
                 n_flops += ins.x >> 16;
             }
             if (a.use_cache && ((ins.x >> 8) & FLAG_ROOT)) {
-                // a missed cacheable node was evaluated: offer it to the table (Sec. 3)
-                const bool emit = act;
-                uint32_t idx = warp_append(&a.ctl->n_cand, emit);
-                if (emit) {
-                    Candidate c;
-                    c.prio = ((unsigned long long)orig << 16) | cand_node;
-                    c.cell = cand_cell;
-                    c.h2 = cand_h2;
-                    c.r = V[(out * 3) * 32];
-                    c.g = V[(out * 3 + 1) * 32];
-                    c.b = V[(out * 3 + 2) * 32];
-                    c.target = 0;
-                    if (idx < a.probe_cap) a.cands[idx] = c;
-                    else atomicOr(&a.ctl->err, ERR_BOUNDS);
-                }
+                const uint32_t out = ins.y & 0xFFFFu;
+                offer(a, act, orig, cand_node, cand_cell, cand_h2, cand_start, cand_full, V[(out * 3) * 32],
+                      V[(out * 3 + 1) * 32], V[(out * 3 + 2) * 32], &n_cand, &n_full);
             }
         }
         if (valid) {
@@ -557,87 +704,488 @@ __global__ void __launch_bounds__(EVAL_WARPS * 32) k_eval(BatchArgs a, uint32_t*
     }
     warp_add_u64(&a.stats[ST_NODES], n_nodes);
     warp_add_u64(&a.stats[ST_FLOPS], n_flops);
+    warp_add_u64(&a.stats[ST_CANDIDATES], n_cand);
+    warp_add_u64(&a.stats[ST_FULL], n_full);
+}
+
+// Work items of the batched evaluation: ceil(misses / 32) per cacheable node.
+__global__ void k_scan_roots(BatchArgs a) {
+    __shared__ uint32_t s_tot[1024];
+    const uint32_t T = blockDim.x, t = threadIdx.x, N = a.n_roots_total;
+    const uint32_t per = (N + T - 1) / T;
+    const uint32_t lo = min(t * per, N), hi = min(lo + per, N);
+    uint32_t c = 0;
+    for (uint32_t g = lo; g < hi; ++g) c += (a.miss_cnt[g] + 31u) >> 5;
+    s_tot[t] = c;
+    __syncthreads();
+    for (uint32_t off = 1; off < T; off <<= 1) {
+        uint32_t v = t >= off ? s_tot[t - off] : 0u;
+        __syncthreads();
+        s_tot[t] += v;
+        __syncthreads();
+    }
+    uint32_t b = t ? s_tot[t - 1] : 0u;
+    for (uint32_t g = lo; g < hi; ++g) {
+        a.root_item_base[g] = b;
+        b += (a.miss_cnt[g] + 31u) >> 5;
+    }
+    if (t == T - 1) {
+        a.root_item_base[N] = s_tot[t];
+        a.ctl->n_root_items = s_tot[t];
+    }
+}
+
+// Batched evaluation of the missed cacheable nodes (the "missed sub-graphs" of Sec. 3):
+// a warp runs one cacheable node's standalone program for 32 of its misses, writes the
+// values into their probe records and offers them to the table.
+__global__ void __launch_bounds__(EVAL_WARPS * 32) k_eval_roots(BatchArgs a, uint32_t level, uint32_t* item_ctr) {
+    extern __shared__ float s_val[];
+    __shared__ float2 s_grad[8];
+    init_gradients(s_grad);
+    __syncthreads();
+    const uint32_t warp = threadIdx.x >> 5, lane = lane_id();
+    float* V = s_val + (size_t)warp * a.max_slots * 96u + lane;
+    const uint32_t n_items = a.ctl->n_root_items;
+    unsigned long long n_nodes = 0, n_flops = 0, n_cand = 0, n_full = 0;
+    for (;;) {
+        uint32_t item = 0;
+        if (lane == 0) item = atomicAdd(item_ctr, 1u);
+        item = __shfl_sync(FULL_MASK, item, 0);
+        if (item >= n_items) break;
+        const uint32_t g = find_material(a.root_item_base, a.n_roots_total, item);
+        const RootInfo ri = a.rinfo[g];
+        if (ri.level != level) continue;
+        const uint32_t m = ri.mat, r = ri.ordinal;
+        const uint32_t cnt = __ldg(&a.counts[m]);
+        const uint32_t idx = (item - a.root_item_base[g]) * 32u + lane;
+        const bool valid = idx < a.miss_cnt[g];
+        const size_t pbase = __ldg(&a.probe_base[m]);
+        const size_t base = pbase + (size_t)r * cnt;
+        const uint32_t j = valid ? a.misslist[base + idx] : 0u;
+        const uint32_t s = __ldg(&a.seg_start[m]) + j;
+        PointIn pt{0, 0, 0, 0, 0, 0, 0, 0};
+        float4 rec = make_float4(0.f, 0.f, 0.f, 0.f);
+        uint32_t orig = 0;
+        if (valid) {
+            pt.u = a.su[s];
+            pt.v = a.sv[s];
+            orig = a.sidx[s];
+            rec = a.probes[base + j];
+        }
+        const uint4* prog = a.prog + ri.prog_start;
+        for (uint32_t pc = 0; pc < ri.prog_len; ++pc) {
+            const uint4 ins = __ldg(&prog[pc]);
+            const uint32_t op = ins.x & 0xFFu;
+            if (!valid) continue;
+            if (op == OP_LOAD_ROOT) {
+                const uint32_t slot = ins.y & 0xFFFFu, rr = ins.y >> 16;
+                const float4 v = a.probes[pbase + (size_t)rr * cnt + j];
+                V[(slot * 3) * 32] = v.x;
+                V[(slot * 3 + 1) * 32] = v.y;
+                V[(slot * 3 + 2) * 32] = v.z;
+                continue;
+            }
+            exec_node(op, ins, V, pt, a.params, s_grad);
+            n_nodes++;
+            n_flops += ins.x >> 16;
+        }
+        const float v0 = V[(ri.out_slot * 3) * 32], v1 = V[(ri.out_slot * 3 + 1) * 32], v2 = V[(ri.out_slot * 3 + 2) * 32];
+        if (valid) a.probes[base + j] = make_float4(v0, v1, v2, __uint_as_float(PROBE_COMPUTED));
+        offer(a, valid, orig, ri.node, __float_as_uint(rec.x), __float_as_uint(rec.y), __float_as_uint(rec.z),
+              __float_as_uint(rec.w) == PROBE_FULL, v0, v1, v2, &n_cand, &n_full);
+    }
+    warp_add_u64(&a.stats[ST_NODES], n_nodes);
+    warp_add_u64(&a.stats[ST_FLOPS], n_flops);
+    warp_add_u64(&a.stats[ST_CANDIDATES], n_cand);
+    warp_add_u64(&a.stats[ST_FULL], n_full);
 }
 
 // =======================================================================================
-// Insert (Alg. 1 semantics, deterministic): rounds of claim / resolve
+// Insert (Alg. 1 semantics, deterministic): rounds of claim / resolve in one
+// cooperative launch, separated by a grid barrier whose waits are bounded
 // =======================================================================================
 __device__ __forceinline__ unsigned long long claim_word(uint32_t epoch, unsigned long long prio) {
     return ((unsigned long long)(EPOCH_MAX - epoch) << 44) | prio;
 }
 
-__global__ void k_claim(BatchArgs a, uint32_t round, int final_round) {
-    const uint32_t n_in = round == 0 ? min(a.ctl->n_cand, a.probe_cap) : a.ctl->out_count[round - 1];
-    const uint32_t* list_in = round == 0 ? nullptr : a.lists[(round - 1) & 1u];
-    const uint32_t epoch = a.ctl->epoch + round;
-    const uint32_t ne = a.n_entries;
-    uint32_t stride = gridDim.x * blockDim.x;
-    uint32_t n_round = (n_in + 31u) & ~31u;
-    unsigned long long n_dup = 0, n_full = 0;
-    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n_round; i += stride) {
-        bool act = i < n_in;
-        bool live = false;
-        uint32_t idx = 0;
-        if (act) {
-            idx = list_in ? list_in[i] : i;
-            Candidate c = a.cands[idx];
-            const uint4* cell = a.table + (size_t)c.cell * ne;
-            int target = -1;
-            bool dup = false;
-            for (uint32_t e = 0; e < ne; ++e) {
-                uint32_t h = cell[e].x;   // plain load: earlier rounds wrote the table
-                if (h == c.h2) { dup = true; break; }
-                if (h == 0u) { target = (int)e; break; }
-            }
-            if (dup) n_dup++;
-            else if (target < 0) n_full++;
-            else if (final_round) atomicOr(&a.ctl->err, ERR_INSERT);
-            else {
-                a.cands[idx].target = (uint32_t)target;
-                atomicMin(&a.claims[c.cell], claim_word(epoch, c.prio));
-                live = true;
+constexpr uint32_t BARRIER_SPIN_LIMIT = 1u << 24;   // x >= 64 ns sleeps: about a second
+
+// Grid-wide barrier for a cooperative launch (all blocks resident).  Returns false, with
+// ERR_TIMEOUT set, if the other blocks did not arrive within the spin limit.
+__device__ bool grid_barrier(Control* ctl) {
+    __shared__ int s_ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        volatile uint32_t* gen = &ctl->bar_gen;
+        const uint32_t g0 = *gen;
+        __threadfence();
+        const uint32_t arrived = atomicAdd(&ctl->bar_count, 1u);
+        int ok = 1;
+        if (arrived == gridDim.x - 1) {
+            ctl->bar_count = 0;
+            __threadfence();
+            atomicAdd(&ctl->bar_gen, 1u);
+        } else {
+            uint32_t spins = 0;
+            while (*gen == g0) {
+                __nanosleep(64);
+                if (++spins > BARRIER_SPIN_LIMIT) {
+                    atomicOr(&ctl->err, ERR_TIMEOUT);
+                    ok = 0;
+                    break;
+                }
             }
         }
-        uint32_t pos = warp_append(&a.ctl->mid_count[round], live);
-        if (live) a.lists[2][pos] = idx;
+        __threadfence();
+        s_ok = ok;
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+
+__global__ void __launch_bounds__(256) k_insert(BatchArgs a) {
+    const uint32_t ne = a.n_entries;
+    const uint32_t stride = gridDim.x * blockDim.x;
+    unsigned long long n_dup = 0, n_full = 0, n_ins = 0;
+    for (uint32_t round = 0; round <= ne; ++round) {
+        const uint32_t n_in = round == 0 ? min(__ldcg(&a.ctl->n_cand), a.probe_cap) : __ldcg(&a.ctl->out_count[round - 1]);
+        if (n_in == 0) break;                         // same value in every block
+        const uint32_t* list_in = round == 0 ? nullptr : a.lists[(round - 1) & 1u];
+        const uint32_t epoch = __ldcg(&a.ctl->epoch) + round;
+        const bool final_round = round == ne;
+        // ---- claim: first slot holding the candidate's hash2 (duplicate) or 0 (free)
+        const uint32_t n_r = (n_in + 31u) & ~31u;
+        for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n_r; i += stride) {
+            const bool act = i < n_in;
+            bool live = false;
+            uint32_t idx = 0;
+            if (act) {
+                idx = list_in ? __ldcg(&list_in[i]) : i;
+                const unsigned long long prio = __ldcg(&a.cands[idx].prio);
+                const uint32_t cell = __ldcg(&a.cands[idx].cell), h2 = __ldcg(&a.cands[idx].h2);
+                const uint32_t tgt = __ldcg(&a.cands[idx].target);
+                const uint32_t* hw = cell_words(a.table, cell, ne);
+                const uint32_t weight = 1u + (tgt >> 16);
+                int target = -1;
+                bool dup = false;
+                // slots before the start held other keys when the pass began
+                for (uint32_t e = tgt & 0xFFFFu; e < ne; ++e) {
+                    const uint32_t h = __ldcg(&hw[e]);
+                    if (h == h2) { dup = true; break; }
+                    if (h == 0u) { target = (int)e; break; }
+                }
+                if (dup) n_dup += weight;
+                else if (target < 0) n_full += weight;
+                else if (final_round) atomicOr(&a.ctl->err, ERR_INSERT);
+                else {
+                    a.cands[idx].target = (uint32_t)target | (tgt & 0xFFFF0000u);
+                    atomicMin(&a.claims[cell], claim_word(epoch, prio));
+                    live = true;
+                }
+            }
+            const uint32_t pos = warp_append(&a.ctl->mid_count[round], live);
+            if (live) a.lists[2][pos] = idx;
+        }
+        if (!grid_barrier(a.ctl)) return;
+        if (final_round) break;
+        // ---- resolve: the smallest (point, node) per cell writes its slot
+        const uint32_t n_mid = __ldcg(&a.ctl->mid_count[round]);
+        uint32_t* list_out = a.lists[round & 1u];
+        const uint32_t n_m = (n_mid + 31u) & ~31u;
+        for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n_m; i += stride) {
+            const bool act = i < n_mid;
+            bool lose = false;
+            uint32_t idx = 0;
+            if (act) {
+                idx = __ldcg(&a.lists[2][i]);
+                const unsigned long long prio = __ldcg(&a.cands[idx].prio);
+                const uint32_t cell = __ldcg(&a.cands[idx].cell);
+                if (__ldcg(&a.claims[cell]) == claim_word(epoch, prio)) {
+                    const uint32_t tgt = __ldcg(&a.cands[idx].target);
+                    const uint32_t e = tgt & 0xFFFFu;
+                    uint32_t* cw = reinterpret_cast<uint32_t*>(a.table) + (size_t)cell * 4u * ne;
+                    cw[e] = __ldcg(&a.cands[idx].h2);
+                    cw[ne + 3u * e] = __float_as_uint(__ldcg(&a.cands[idx].r));
+                    cw[ne + 3u * e + 1] = __float_as_uint(__ldcg(&a.cands[idx].g));
+                    cw[ne + 3u * e + 2] = __float_as_uint(__ldcg(&a.cands[idx].b));
+                    n_ins++;
+                    n_dup += tgt >> 16;   // its shadows find it in the table
+                } else {
+                    lose = true;
+                }
+            }
+            const uint32_t pos = warp_append(&a.ctl->out_count[round], lose);
+            if (lose) list_out[pos] = idx;
+        }
+        if (!grid_barrier(a.ctl)) return;
     }
     warp_add_u64(&a.stats[ST_DUP], n_dup);
     warp_add_u64(&a.stats[ST_FULL], n_full);
+    warp_add_u64(&a.stats[ST_INSERTED], n_ins);
 }
 
-__global__ void k_resolve(BatchArgs a, uint32_t round) {
-    const uint32_t n_mid = a.ctl->mid_count[round];
-    const uint32_t epoch = a.ctl->epoch + round;
-    uint32_t* list_out = a.lists[round & 1u];
-    uint32_t stride = gridDim.x * blockDim.x;
-    uint32_t n_round = (n_mid + 31u) & ~31u;
-    unsigned long long n_ins = 0;
-    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n_round; i += stride) {
-        bool act = i < n_mid;
-        bool lose = false;
-        uint32_t idx = 0;
-        if (act) {
-            idx = a.lists[2][i];
-            const Candidate c = a.cands[idx];
-            if (a.claims[c.cell] == claim_word(epoch, c.prio)) {
-                a.table[(size_t)c.cell * a.n_entries + c.target] =
-                    make_uint4(c.h2, __float_as_uint(c.r), __float_as_uint(c.g), __float_as_uint(c.b));
-                n_ins++;
-            } else {
-                lose = true;
-            }
-        }
-        uint32_t pos = warp_append(&a.ctl->out_count[round], lose);
-        if (lose) list_out[pos] = idx;
+// ---- cell-grouped insert: the same (point, node) order per cell, without rounds.
+// Candidates are partitioned into bins of INS_CELLS consecutive cells (count, scan,
+// scatter: coalesced), then one block per bin groups its candidates by cell in shared
+// memory and one thread per cell inserts that cell's candidates in ascending order.
+constexpr uint32_t INS_CELLS = 2048;      // cells per bin
+constexpr uint32_t INS_SMEM_BINS = 4096;  // bins counted in shared memory by the partition
+constexpr uint32_t INS_CAP = 4096;        // candidates grouped in shared memory at a time
+constexpr int INS_REG = 8;                // a cell's candidates sorted in registers
+
+__device__ __forceinline__ void cas_pair(unsigned long long& pa, uint32_t& ia, unsigned long long& pb, uint32_t& ib) {
+    const bool sw = pa > pb;
+    const unsigned long long tp = sw ? pb : pa;
+    const uint32_t ti = sw ? ib : ia;
+    pb = sw ? pa : pb;
+    ib = sw ? ia : ib;
+    pa = tp;
+    ia = ti;
+}
+
+// Inserts one candidate into a cell owned by the calling thread (Alg. 1 scan).
+__device__ __forceinline__ void insert_one(const BatchArgs& a, const Candidate& c, uint32_t ne,
+                                           unsigned long long* n_ins, unsigned long long* n_dup,
+                                           unsigned long long* n_full) {
+    uint32_t* cw = reinterpret_cast<uint32_t*>(a.table) + (size_t)c.cell * 4u * ne;
+    const uint32_t weight = 1u + (c.target >> 16);
+    int target = -1;
+    bool dup = false;
+    // slots before the start held other keys when the pass began
+    for (uint32_t e = c.target & 0xFFFFu; e < ne; ++e) {
+        const uint32_t h = cw[e];
+        if (h == c.h2) { dup = true; break; }
+        if (h == 0u) { target = (int)e; break; }
     }
+    if (dup) {
+        *n_dup += weight;
+    } else if (target < 0) {
+        *n_full += weight;
+    } else {
+        cw[target] = c.h2;
+        cw[ne + 3u * target] = __float_as_uint(c.r);
+        cw[ne + 3u * target + 1] = __float_as_uint(c.g);
+        cw[ne + 3u * target + 2] = __float_as_uint(c.b);
+        *n_ins += 1;
+        *n_dup += c.target >> 16;   // its shadows find it in the table
+    }
+}
+
+__device__ __forceinline__ uint32_t bin_of(uint32_t cell) { return cell / INS_CELLS; }
+
+// Candidates per bin.
+__global__ void __launch_bounds__(256) k_bin_count(BatchArgs a) {
+    __shared__ uint32_t s_cnt[INS_SMEM_BINS];
+    const uint32_t nb = a.n_bins;
+    const bool local = nb <= INS_SMEM_BINS;
+    if (local) {
+        for (uint32_t b = threadIdx.x; b < nb; b += blockDim.x) s_cnt[b] = 0;
+        __syncthreads();
+    }
+    const uint32_t n_in = min(a.ctl->n_cand, a.probe_cap);
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n_in; i += gridDim.x * blockDim.x)
+        atomicAdd(local ? &s_cnt[bin_of(a.cands[i].cell)] : &a.bin_cnt[bin_of(a.cands[i].cell)], 1u);
+    if (local) {
+        __syncthreads();
+        for (uint32_t b = threadIdx.x; b < nb; b += blockDim.x)
+            if (s_cnt[b]) atomicAdd(&a.bin_cnt[b], s_cnt[b]);
+    }
+}
+
+// Exclusive scan of the bin counts (one block); bin_cnt becomes the fill cursor.
+__global__ void k_bin_scan(BatchArgs a) {
+    __shared__ uint32_t s_tot[1024];
+    const uint32_t T = blockDim.x, t = threadIdx.x, N = a.n_bins;
+    const uint32_t per = (N + T - 1) / T;
+    const uint32_t lo = min(t * per, N), hi = min(lo + per, N);
+    uint32_t c = 0;
+    for (uint32_t b = lo; b < hi; ++b) c += a.bin_cnt[b];
+    s_tot[t] = c;
+    __syncthreads();
+    for (uint32_t off = 1; off < T; off <<= 1) {
+        uint32_t v = t >= off ? s_tot[t - off] : 0u;
+        __syncthreads();
+        s_tot[t] += v;
+        __syncthreads();
+    }
+    uint32_t base = t ? s_tot[t - 1] : 0u;
+    for (uint32_t b = lo; b < hi; ++b) {
+        const uint32_t c2 = a.bin_cnt[b];
+        a.bin_base[b] = base;
+        a.bin_cnt[b] = base;
+        base += c2;
+    }
+    if (t == T - 1) a.bin_base[N] = s_tot[t];
+}
+
+// Copies every candidate into its bin's range.
+__global__ void __launch_bounds__(256) k_bin_scatter(BatchArgs a) {
+    __shared__ uint32_t s_cnt[INS_SMEM_BINS];
+    const uint32_t nb = a.n_bins;
+    const bool local = nb <= INS_SMEM_BINS;
+    const uint32_t n_in = min(a.ctl->n_cand, a.probe_cap);
+    uint32_t lo, hi;
+    block_range(n_in, &lo, &hi);
+    if (local) {
+        for (uint32_t b = threadIdx.x; b < nb; b += blockDim.x) s_cnt[b] = 0;
+        __syncthreads();
+        for (uint32_t i = lo + threadIdx.x; i < hi; i += blockDim.x) atomicAdd(&s_cnt[bin_of(a.cands[i].cell)], 1u);
+        __syncthreads();
+        for (uint32_t b = threadIdx.x; b < nb; b += blockDim.x)
+            if (s_cnt[b]) s_cnt[b] = atomicAdd(&a.bin_cnt[b], s_cnt[b]);
+        __syncthreads();
+    }
+    for (uint32_t i = lo + threadIdx.x; i < hi; i += blockDim.x) {
+        const Candidate c = a.cands[i];
+        const uint32_t b = bin_of(c.cell);
+        const uint32_t pos = atomicAdd(local ? &s_cnt[b] : &a.bin_cnt[b], 1u);
+        a.cands_binned[pos] = c;
+    }
+}
+
+// One block per bin: group by cell in shared memory, then insert per cell in order.
+__global__ void __launch_bounds__(256) k_bin_insert(BatchArgs a) {
+    __shared__ uint32_t s_cnt[INS_CELLS];
+    __shared__ uint32_t s_off[INS_CELLS + 1];
+    __shared__ uint32_t s_cur[INS_CELLS];
+    __shared__ uint32_t s_order[INS_CAP];
+    __shared__ uint32_t s_part[256];
+    __shared__ uint32_t s_range[2];
+    __shared__ unsigned long long s_best[256];
+    __shared__ uint32_t s_bidx[256];
+    const uint32_t ne = a.n_entries;
+    const uint32_t t = threadIdx.x, T = blockDim.x;
+    unsigned long long n_dup = 0, n_full = 0, n_ins = 0;
+    for (uint32_t bin = blockIdx.x; bin < a.n_bins; bin += gridDim.x) {
+        const uint32_t lo = a.bin_base[bin], hi = a.bin_base[bin + 1];
+        if (lo == hi) continue;                                 // uniform in the block
+        const uint32_t c0 = bin * INS_CELLS;
+        const Candidate* cb = a.cands_binned;
+        for (uint32_t k = t; k < INS_CELLS; k += T) s_cnt[k] = 0;
+        __syncthreads();
+        for (uint32_t i = lo + t; i < hi; i += T) atomicAdd(&s_cnt[cb[i].cell - c0], 1u);
+        __syncthreads();
+        // exclusive scan of the per-cell counts (INS_CELLS / T consecutive cells per thread)
+        const uint32_t per = INS_CELLS / T;
+        uint32_t part = 0;
+        for (uint32_t k = 0; k < per; ++k) part += s_cnt[t * per + k];
+        s_part[t] = part;
+        __syncthreads();
+        for (uint32_t off = 1; off < T; off <<= 1) {
+            uint32_t v = t >= off ? s_part[t - off] : 0u;
+            __syncthreads();
+            s_part[t] += v;
+            __syncthreads();
+        }
+        uint32_t run = t ? s_part[t - 1] : 0u;
+        for (uint32_t k = 0; k < per; ++k) {
+            s_off[t * per + k] = run;
+            run += s_cnt[t * per + k];
+        }
+        if (t == T - 1) s_off[INS_CELLS] = run;
+        __syncthreads();
+        // cells [s, e) whose candidates fit in s_order at once
+        uint32_t s = 0;
+        while (s < INS_CELLS) {
+            if (t == 0) {
+                uint32_t e = s + 1;
+                while (e < INS_CELLS && s_off[e + 1] - s_off[s] <= INS_CAP) ++e;
+                s_range[0] = e;
+            }
+            __syncthreads();
+            const uint32_t e = s_range[0];
+            const uint32_t base = s_off[s];
+            const bool giant = s_off[e] - base > INS_CAP;     // a single cell beyond the cap
+            if (!giant) {
+                for (uint32_t k = s + t; k < e; k += T) s_cur[k] = s_off[k] - base;
+                __syncthreads();
+                for (uint32_t i = lo + t; i < hi; i += T) {
+                    const uint32_t k = cb[i].cell - c0;
+                    if (k >= s && k < e) s_order[atomicAdd(&s_cur[k], 1u)] = i;
+                }
+                __syncthreads();
+                for (uint32_t k = s + t; k < e; k += T) {
+                    const uint32_t cnt = s_cnt[k];
+                    if (cnt == 0) continue;
+                    const uint32_t* seg = s_order + (s_off[k] - base);
+                    if (cnt <= (uint32_t)INS_REG) {
+                        unsigned long long pr[INS_REG];
+                        uint32_t id[INS_REG];
+#pragma unroll
+                        for (int q = 0; q < INS_REG; ++q) {
+                            id[q] = (uint32_t)q < cnt ? seg[q] : 0u;
+                            pr[q] = (uint32_t)q < cnt ? cb[id[q]].prio : ~0ull;
+                        }
+                        // odd-even merge sort network of 8 (Batcher)
+                        cas_pair(pr[0], id[0], pr[1], id[1]); cas_pair(pr[2], id[2], pr[3], id[3]);
+                        cas_pair(pr[4], id[4], pr[5], id[5]); cas_pair(pr[6], id[6], pr[7], id[7]);
+                        cas_pair(pr[0], id[0], pr[2], id[2]); cas_pair(pr[1], id[1], pr[3], id[3]);
+                        cas_pair(pr[4], id[4], pr[6], id[6]); cas_pair(pr[5], id[5], pr[7], id[7]);
+                        cas_pair(pr[1], id[1], pr[2], id[2]); cas_pair(pr[5], id[5], pr[6], id[6]);
+                        cas_pair(pr[0], id[0], pr[4], id[4]); cas_pair(pr[1], id[1], pr[5], id[5]);
+                        cas_pair(pr[2], id[2], pr[6], id[6]); cas_pair(pr[3], id[3], pr[7], id[7]);
+                        cas_pair(pr[2], id[2], pr[4], id[4]); cas_pair(pr[3], id[3], pr[5], id[5]);
+                        cas_pair(pr[1], id[1], pr[2], id[2]); cas_pair(pr[3], id[3], pr[4], id[4]);
+                        cas_pair(pr[5], id[5], pr[6], id[6]);
+#pragma unroll
+                        for (int q = 0; q < INS_REG; ++q)
+                            if ((uint32_t)q < cnt) insert_one(a, cb[id[q]], ne, &n_ins, &n_dup, &n_full);
+                    } else {
+                        // insertion sort of the cell's segment (its own part of s_order)
+                        uint32_t* sg = s_order + (s_off[k] - base);
+                        for (uint32_t x = 1; x < cnt; ++x) {
+                            const uint32_t v = sg[x];
+                            const unsigned long long pv = cb[v].prio;
+                            uint32_t y = x;
+                            while (y > 0 && cb[sg[y - 1]].prio > pv) {
+                                sg[y] = sg[y - 1];
+                                --y;
+                            }
+                            sg[y] = v;
+                        }
+                        for (uint32_t x = 0; x < cnt; ++x) insert_one(a, cb[sg[x]], ne, &n_ins, &n_dup, &n_full);
+                    }
+                }
+                __syncthreads();
+            } else {
+                // one cell with more candidates than fit: the block selects them in order
+                const uint32_t cell = c0 + s;
+                const uint32_t cnt = s_cnt[s];
+                unsigned long long last = 0;
+                for (uint32_t step = 0; step < cnt; ++step) {
+                    unsigned long long best = ~0ull;
+                    uint32_t bi = 0;
+                    for (uint32_t i = lo + t; i < hi; i += T) {
+                        if (cb[i].cell != cell) continue;
+                        const unsigned long long p = cb[i].prio;
+                        if ((step == 0 || p > last) && p < best) { best = p; bi = i; }
+                    }
+                    s_best[t] = best;
+                    s_bidx[t] = bi;
+                    __syncthreads();
+                    for (uint32_t off = T / 2; off > 0; off >>= 1) {
+                        if (t < off && s_best[t + off] < s_best[t]) {
+                            s_best[t] = s_best[t + off];
+                            s_bidx[t] = s_bidx[t + off];
+                        }
+                        __syncthreads();
+                    }
+                    if (t == 0 && s_best[0] != ~0ull) insert_one(a, cb[s_bidx[0]], ne, &n_ins, &n_dup, &n_full);
+                    last = s_best[0];
+                    __syncthreads();
+                }
+            }
+            s = e;
+        }
+    }
+    warp_add_u64(&a.stats[ST_DUP], n_dup);
+    warp_add_u64(&a.stats[ST_FULL], n_full);
     warp_add_u64(&a.stats[ST_INSERTED], n_ins);
 }
 
 __global__ void k_finish(BatchArgs a) {
     if (threadIdx.x == 0 && blockIdx.x == 0) {
-        uint32_t nc = min(a.ctl->n_cand, a.probe_cap);
         if (a.use_cache) a.ctl->epoch += a.n_entries + 1u;
-        a.stats[ST_CANDIDATES] += nc;
         a.stats[ST_BATCHES] += 1ull;
     }
 }
@@ -675,12 +1223,25 @@ cudaError_t launch_keys(const uint32_t* mat, const uint32_t* node, const float* 
 }
 
 cudaError_t launch_reset(uint4* table, size_t slots, unsigned long long* claims, size_t cells,
-                         Control* ctl, unsigned long long* stats, cudaStream_t s) {
+                         Control* ctl, unsigned long long* stats, cudaStream_t s, bool claim_words) {
     cudaError_t e;
     if (slots && (e = cudaMemsetAsync(table, 0, slots * sizeof(uint4), s)) != cudaSuccess) return e;
+    // all-ones: the largest claim word of the atomicMin rounds, an empty list per cell
+    // for the grouped insert
+    (void)claim_words;
     if (cells && (e = cudaMemsetAsync(claims, 0xFF, cells * sizeof(unsigned long long), s)) != cudaSuccess) return e;
     if ((e = cudaMemsetAsync(ctl, 0, sizeof(Control), s)) != cudaSuccess) return e;
     return cudaMemsetAsync(stats, 0, ST_COUNT * sizeof(unsigned long long), s);
+}
+
+int insert_grid(int num_sms) {
+    static int per_sm = 0;
+    if (per_sm == 0) {
+        int v = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, k_insert, 256, 0) != cudaSuccess || v <= 0) v = 1;
+        per_sm = v;
+    }
+    return per_sm * num_sms;
 }
 
 cudaError_t launch_batch(const BatchArgs& a, cudaStream_t s, int num_sms, cudaEvent_t* ev,
@@ -689,11 +1250,13 @@ cudaError_t launch_batch(const BatchArgs& a, cudaStream_t s, int num_sms, cudaEv
     uint64_t nl = 0;
     auto mark = [&](int k) { return ev ? cudaEventRecord(ev[k], s) : cudaSuccess; };
     if ((e = mark(0)) != cudaSuccess) return e;
-    // per-batch counters: items, probes, candidates, round counts (epoch and err persist)
-    if ((e = cudaMemsetAsync(a.ctl, 0, 3 * sizeof(uint32_t), s)) != cudaSuccess) return e;
+    // per-batch counters (epoch, errors and the barrier persist)
+    if ((e = cudaMemsetAsync(a.ctl, 0, offsetof(Control, epoch), s)) != cudaSuccess) return e;
     if ((e = cudaMemsetAsync(a.ctl->mid_count, 0, 2 * (MAX_ENTRIES + 2) * sizeof(uint32_t), s)) != cudaSuccess) return e;
+    // counts has n_mats + 1 entries; the last one is the evaluation's work-item counter
     if ((e = cudaMemsetAsync(a.counts, 0, (a.n_mats + 1) * sizeof(uint32_t), s)) != cudaSuccess) return e;
-    // counts has n_mats + 1 entries; the last one is the eval work-item counter
+    if (a.split && (e = cudaMemsetAsync(a.miss_cnt, 0, (a.n_roots_total + MAX_LEVELS) * sizeof(uint32_t), s)) != cudaSuccess)
+        return e;
     uint32_t* item_ctr = a.counts + a.n_mats;
     const int gs_blocks = num_sms * 4;
     if (a.n > 0) {
@@ -710,30 +1273,48 @@ cudaError_t launch_batch(const BatchArgs& a, cudaStream_t s, int num_sms, cudaEv
     if (a.n > 0 && a.use_cache) {
         uint32_t ne = a.n_entries;
         int lb = num_sms * 8;
-        if (ne <= 4) k_lookup<4><<<lb, 256, 0, s>>>(a);
-        else if (ne <= 8) k_lookup<8><<<lb, 256, 0, s>>>(a);
-        else if (ne <= 16) k_lookup<16><<<lb, 256, 0, s>>>(a);
-        else k_lookup<32><<<lb, 256, 0, s>>>(a);
+        if (ne <= 4) k_lookup<1, 4><<<lb, 256, 0, s>>>(a);
+        else if (ne <= 8) k_lookup<2, 4><<<lb, 256, 0, s>>>(a);
+        else if (ne <= 16) k_lookup<4, 2><<<lb, 256, 0, s>>>(a);
+        else k_lookup<8, 1><<<lb, 256, 0, s>>>(a);
         nl++;
     }
     if ((e = mark(2)) != cudaSuccess) return e;
     if (a.n > 0) {
         size_t smem = eval_smem_bytes(a.max_slots);
-        if (smem > 48 * 1024 &&
-            (e = cudaFuncSetAttribute(k_eval, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
-            return e;
+        if (smem > 48 * 1024) {
+            if ((e = cudaFuncSetAttribute(k_eval, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
+                return e;
+            if ((e = cudaFuncSetAttribute(k_eval_roots, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
+                return e;
+        }
+        if (a.use_cache && a.split) {
+            k_scan_roots<<<1, 1024, 0, s>>>(a);
+            nl++;
+            // the level counters live after the per-root miss counters
+            for (uint32_t lv = 0; lv <= a.max_level; ++lv) {
+                k_eval_roots<<<num_sms * 16, EVAL_WARPS * 32, smem, s>>>(a, lv, a.miss_cnt + a.n_roots_total + lv);
+                nl++;
+            }
+        }
         k_eval<<<num_sms * 16, EVAL_WARPS * 32, smem, s>>>(a, item_ctr);
         nl++;
     }
     if ((e = mark(3)) != cudaSuccess) return e;
-    if (a.n > 0 && a.use_cache) {
-        for (uint32_t r = 0; r < a.n_entries; ++r) {
-            k_claim<<<gs_blocks, 256, 0, s>>>(a, r, 0);
-            k_resolve<<<gs_blocks, 256, 0, s>>>(a, r);
-            nl += 2;
-        }
-        k_claim<<<gs_blocks, 256, 0, s>>>(a, a.n_entries, 1);
+    if (a.n > 0 && a.use_cache && a.insert_rounds) {
+        BatchArgs arg = a;
+        void* params[] = {&arg};
+        if ((e = cudaLaunchCooperativeKernel((const void*)k_insert, dim3(insert_grid(num_sms)), dim3(256), params, 0, s)) !=
+            cudaSuccess)
+            return e;
         nl++;
+    } else if (a.n > 0 && a.use_cache) {
+        if ((e = cudaMemsetAsync(a.bin_cnt, 0, (size_t)a.n_bins * sizeof(uint32_t), s)) != cudaSuccess) return e;
+        k_bin_count<<<gs_blocks, 256, 0, s>>>(a);
+        k_bin_scan<<<1, 1024, 0, s>>>(a);
+        k_bin_scatter<<<gs_blocks, 256, 0, s>>>(a);
+        k_bin_insert<<<std::min<uint32_t>(a.n_bins, (uint32_t)num_sms * 8u), 256, 0, s>>>(a);
+        nl += 4;
     }
     if ((e = mark(4)) != cudaSuccess) return e;
     k_finish<<<1, 32, 0, s>>>(a);

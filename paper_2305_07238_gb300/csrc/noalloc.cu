@@ -22,7 +22,9 @@ constexpr size_t OFF_SIDX = OFF_SORTED + align256(8 * NA_POINTS * 4);  // u32 po
 constexpr size_t OFF_PROBES = OFF_SIDX + align256(NA_POINTS * 4);      // 16-B probe records
 constexpr size_t OFF_CANDS = OFF_PROBES + align256(NA_PROBES * 16);    // 32-B candidates
 constexpr size_t OFF_LISTS = OFF_CANDS + align256(NA_PROBES * 32);     // 3 u32 index lists
-constexpr size_t SCRATCH_BYTES = OFF_LISTS + align256(3 * NA_PROBES * 4);
+constexpr size_t OFF_MISS = OFF_LISTS + align256(3 * NA_PROBES * 4);   // u32 miss lists
+constexpr size_t OFF_BINNED = OFF_MISS + align256(NA_PROBES * 4);    // 32-B binned candidates
+constexpr size_t SCRATCH_BYTES = OFF_BINNED + align256(NA_PROBES * 32);
 static_assert(SCRATCH_BYTES == PMC_NOALLOC_SCRATCH_BYTES, "pmc.h states the array size");
 
 }  // namespace
@@ -88,7 +90,7 @@ extern "C" pmc_status pmc_eval_batch_noalloc(pmc_cache* c, const pmc_points* pts
     if (st != PMC_OK) return st;
     cudaStream_t s = (cudaStream_t)stream;
     const uint32_t ne = c->desc.n_entries;
-    if (c->use_cache && c->epoch_host + 2 * (ne + 1) > EPOCH_MAX) {
+    if (c->use_cache && (c->desc.flags & PMC_INSERT_ROUNDS) && c->epoch_host + 2 * (ne + 1) > EPOCH_MAX) {
         cudaError_t e = cudaMemsetAsync(c->d_claims, 0xFF, c->desc.n_cells * sizeof(unsigned long long), s);
         if (e == cudaSuccess) e = cudaMemsetAsync(&c->d_ctl->epoch, 0, sizeof(uint32_t), s);
         if (e != cudaSuccess) {
@@ -128,6 +130,13 @@ extern "C" pmc_status pmc_eval_batch_noalloc(pmc_cache* c, const pmc_points* pts
     uint32_t* lists = reinterpret_cast<uint32_t*>(base + OFF_LISTS);
     a.lists[0] = lists; a.lists[1] = lists + NA_PROBES; a.lists[2] = lists + 2 * NA_PROBES;
     a.ctl = c->d_ctl; a.stats = c->d_stats;
+    a.split = c->use_cache && c->split;
+    a.insert_rounds = (c->desc.flags & PMC_INSERT_ROUNDS) ? 1 : 0;
+    a.n_bins = c->n_bins; a.bin_cnt = c->d_bins; a.bin_base = c->d_bins + c->n_bins;
+    a.cands_binned = reinterpret_cast<Candidate*>(base + OFF_BINNED);
+    a.rinfo = c->d_rinfo; a.n_roots_total = (uint32_t)c->root_info.size(); a.max_level = c->max_level;
+    a.miss_cnt = c->d_miss_cnt; a.root_item_base = c->d_root_items;
+    a.misslist = reinterpret_cast<uint32_t*>(base + OFF_MISS);
     // launch_batch clears the counters and offsets that must start at zero; every other
     // region is written before it is read within the pass.
     cudaError_t e = launch_batch(a, s, c->num_sms, nullptr, &c->launches);

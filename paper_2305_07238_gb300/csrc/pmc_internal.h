@@ -26,7 +26,22 @@ namespace pmc {
 // contiguous block: ROOT_BEGIN(r), the exclusive nodes, then r flagged FLAG_ROOT.  A
 // lane whose lookup hit takes the cached value at ROOT_BEGIN and skips the block.
 constexpr uint32_t OP_ROOT_BEGIN = 32;
+constexpr uint32_t OP_LOAD_ROOT = 33;   // y: out slot | root ordinal; reads that node's probe record
 constexpr uint32_t FLAG_ROOT = 1;
+
+// Each cacheable node also gets a standalone program (its sub-graph, with any cacheable
+// node below it read from its probe record) so that its misses can be evaluated 32 at
+// a time.  Level 0 programs read no other cacheable node; level l reads levels < l.
+struct RootInfo {
+    uint32_t prog_start;  // in the shared program pool
+    uint32_t prog_len;
+    uint32_t mat;
+    uint32_t ordinal;
+    uint32_t level;
+    uint32_t n_slots;
+    uint32_t node;
+    uint32_t out_slot;
+};
 
 struct MatInfo {
     uint32_t prog_start;  // first instruction in the program pool
@@ -43,6 +58,10 @@ struct CompiledMaterial {
     std::vector<uint4> prog;
     std::vector<float> params;     // parameter offsets in prog are relative to this
     std::vector<uint32_t> roots;   // node IDs of cacheable nodes, ascending
+    std::vector<std::vector<uint4>> root_progs;  // standalone program per cacheable node
+    std::vector<uint32_t> root_level;
+    std::vector<uint32_t> root_slots;
+    std::vector<uint32_t> root_out_slot;
     uint32_t out_slot = 0;
     uint32_t n_slots = 0;
     uint32_t n_nodes = 0;
@@ -70,14 +89,22 @@ constexpr uint32_t EPOCH_BITS = 20;
 constexpr uint32_t EPOCH_MAX = (1u << EPOCH_BITS) - 1;
 constexpr uint64_t MAX_POINTS = 1ull << 28;
 
+constexpr uint32_t MAX_LEVELS = 16;     // nesting depth of cacheable nodes handled in batches
+
 // Device-side control block of one cache object.
 struct Control {
+    // cleared at the start of every batch
     uint32_t n_items;           // warp work items of the current batch
     uint32_t total_probes;
     uint32_t n_cand;            // candidates emitted by the evaluation
+    uint32_t n_root_items;      // work items of the batched evaluation of misses
+    uint32_t pad0;
+    uint32_t pad1;
+    // persistent
     uint32_t epoch;             // claim epoch of round 0 of the current batch
     uint32_t err;               // ERR_* bits
-    uint32_t pad[3];
+    uint32_t bar_count;         // grid barrier of the insert kernel
+    uint32_t bar_gen;
     uint32_t mid_count[MAX_ENTRIES + 2];
     uint32_t out_count[MAX_ENTRIES + 2];
 };
@@ -85,6 +112,7 @@ struct Control {
 constexpr uint32_t ERR_BAD_MAT = 1;
 constexpr uint32_t ERR_INSERT = 2;
 constexpr uint32_t ERR_BOUNDS = 4;
+constexpr uint32_t ERR_TIMEOUT = 8;
 
 // Counter indices in the device stats array.
 enum {
@@ -117,7 +145,20 @@ struct BatchArgs {
     float4* probes; uint32_t probe_cap;
     Candidate* cands; uint32_t* lists[3];
     Control* ctl; unsigned long long* stats;
+    // batched evaluation of misses
+    int split;
+    const RootInfo* rinfo; uint32_t n_roots_total; uint32_t max_level;
+    uint32_t* miss_cnt;        // n_roots_total counters, then MAX_LEVELS item counters
+    uint32_t* root_item_base;  // n_roots_total + 1
+    uint32_t* misslist;        // probe_cap
+    int insert_rounds;         // 1: atomicMin rounds (claims hold epoch words); 0: cell-grouped
+    uint32_t n_bins;           // cell-grouped insert: ceil(n_cells / 2048) bins
+    uint32_t* bin_cnt;         // n_bins
+    uint32_t* bin_base;        // n_bins + 1
+    Candidate* cands_binned;   // probe_cap
 };
+
+constexpr uint32_t INSERT_BIN_CELLS = 2048;
 
 // Phases timed by the optional CUDA events of a batch.
 enum { PH_SORT = 0, PH_LOOKUP, PH_EVAL, PH_INSERT, PH_FINISH, PH_COUNT };
@@ -127,7 +168,7 @@ enum { PH_SORT = 0, PH_LOOKUP, PH_EVAL, PH_INSERT, PH_FINISH, PH_COUNT };
 cudaError_t launch_batch(const BatchArgs& a, cudaStream_t s, int num_sms, cudaEvent_t* ev,
                          uint64_t* launches);
 cudaError_t launch_reset(uint4* table, size_t slots, unsigned long long* claims, size_t cells,
-                         Control* ctl, unsigned long long* stats, cudaStream_t s);
+                         Control* ctl, unsigned long long* stats, cudaStream_t s, bool claim_words);
 cudaError_t launch_keys(const uint32_t* mat, const uint32_t* node, const float* u,
                         const float* v, uint64_t n, uint32_t level, uint64_t n_cells,
                         uint64_t* key, uint64_t* cell, uint32_t* h2, cudaStream_t s);

@@ -20,6 +20,8 @@ PMC_OK, PMC_ERR_INVALID_ARG, PMC_ERR_OOM, PMC_ERR_CUDA, PMC_ERR_TIMEOUT, PMC_ERR
 PMC_CACHE_OFF = 0x1
 PMC_SORT_BY_MATERIAL = 0x2
 PMC_DEBUG_CHECKS = 0x4
+PMC_EVAL_INLINE = 0x8
+PMC_INSERT_ROUNDS = 0x10
 
 EXPORTED = (
     "pmc_create_cache", "pmc_eval_batch", "pmc_eval_batch_host", "pmc_sync", "pmc_stats",

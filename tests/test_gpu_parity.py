@@ -126,12 +126,16 @@ def test_tiny_config_cache_off(P):
 
 
 # ---- frame-shaped streams: a band of the 1920-wide frame, several table geometries ----------
+MODES = {"grouped": 0, "inline": 0x8, "rounds": 0x10}   # PMC_EVAL_INLINE, PMC_INSERT_ROUNDS
+
+
+@pytest.mark.parametrize("mode", sorted(MODES))
 @pytest.mark.parametrize("n_cells,n_entries", [(1 << 21, 8), (1 << 10, 8), (10, 5), (1000, 16), (97, 32), (3, 1)])
-def test_frame_band_parity(P, n_cells, n_entries):
+def test_frame_band_parity(P, n_cells, n_entries, mode):
     spec = W.FrameSpec(width=1920, height=1080, n_mats=64, seed=0)
     frame = W.Frame(spec)
     mats = W.random_materials(64, 20, 200, 0.2, seed=0)
-    gpu = P.Cache(mats, n_cells, n_entries)
+    gpu = P.Cache(mats, n_cells, n_entries, flags=MODES[mode])
     ref = O.Cache(mats, n_cells, n_entries)
     rows = (0, 9) if n_cells >= 1024 else (0, 3)       # 17,280 / 5,760 points: ragged warps
     for p in range(3):
@@ -152,7 +156,7 @@ def test_ragged_batch_sizes(P, n):
     mats = W.random_materials(5, 20, 120, 0.2, seed=9)
     pts = W.points_uniform(max(n, 1), seed=n, n_mats=5)
     pts = W.slice_points(pts, 0, n)
-    gpu = P.Cache(mats, 256, 8)
+    gpu = P.Cache(mats, 256, 8, flags=MODES["rounds"] if n % 2 else 0)
     ref = O.Cache(mats, 256, 8)
     for _ in range(2):
         _compare_pass(gpu, ref, P, pts)
@@ -172,13 +176,14 @@ def test_deep_and_wide_networks(P):
     _compare_tables(gpu, ref)
 
 
-def test_hand_built_nested_roots(P):
+@pytest.mark.parametrize("mode", sorted(MODES))
+def test_hand_built_nested_roots(P, mode):
     from .test_oracle_analysis import g_nested, g_two_roots
     mats = [g_nested(), g_two_roots()]
     pts = W.points_uniform(600, seed=6, n_mats=2)
     pts["u"] = (np.floor(pts["u"] * 8) / 1024 + 0.3).astype(np.float32)   # few texels: many hits
     pts["v"] = (np.floor(pts["v"] * 8) / 1024 + 0.6).astype(np.float32)
-    gpu = P.Cache(mats, 64, 4)
+    gpu = P.Cache(mats, 64, 4, flags=MODES[mode])
     ref = O.Cache(mats, 64, 4)
     for p in range(3):
         _compare_pass(gpu, ref, P, W.slice_points(pts, 200 * p, 200 * (p + 1)))
@@ -238,10 +243,11 @@ def test_host_entry_point_matches_device_entry(P):
     assert np.array_equal(a.table()[0], b.table()[0])
 
 
-def test_reset_empties_table(P):
+@pytest.mark.parametrize("mode", sorted(MODES))
+def test_reset_empties_table(P, mode):
     mat = W.material_tiny()
     pts = W.points_uniform(512, seed=8)
-    gpu = P.Cache([mat], 64, 8)
+    gpu = P.Cache([mat], 64, 8, flags=MODES[mode])
     _run_gpu(gpu, P, pts)
     assert gpu.stats()["inserted"] > 0
     gpu.reset()
