@@ -35,6 +35,8 @@ struct pmc_cache {
     uint32_t* d_miss_cnt = nullptr;       // roots + MAX_LEVELS
     uint32_t* d_root_items = nullptr;     // roots + 1
     uint32_t n_bins = 0;                  // cell-grouped insert bins
+    bool table_empty = true;              // nothing inserted since creation or reset
+    bool last_all_miss = false;           // the last batch ran on an empty table
     uint32_t* d_bins = nullptr;           // counts (n_bins) | bases (n_bins + 1)
     // per-batch scratch, grown on demand
     uint64_t cap_points = 0;

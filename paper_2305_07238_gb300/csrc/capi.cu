@@ -237,7 +237,7 @@ pmc_status pmc_create_cache(const pmc_cache_desc* desc, const pmc_material* mats
         (s = dalloc(&c->d_prog, prog.size())) != PMC_OK ||
         (s = dalloc(&c->d_params, params.size())) != PMC_OK ||
         (s = dalloc(&c->d_roots, c->roots.size())) != PMC_OK ||
-        (s = dalloc(&c->d_table, slots)) != PMC_OK ||
+        (s = dalloc(&c->d_table, slots ? slots + 16 : 0)) != PMC_OK ||
         (s = dalloc(&c->d_claims, cells)) != PMC_OK ||
         (s = dalloc(&c->d_ctl, 1)) != PMC_OK ||
         (s = dalloc(&c->d_stats, ST_COUNT)) != PMC_OK ||
@@ -306,6 +306,8 @@ pmc_status pmc_eval_batch(pmc_cache* c, const pmc_points* pts, float* out_rgb, u
     a.spz = c->d_sorted + 4 * P; a.snx = c->d_sorted + 5 * P; a.sny = c->d_sorted + 6 * P;
     a.snz = c->d_sorted + 7 * P; a.sidx = c->d_sidx;
     a.table = c->d_table; a.claims = c->d_claims;
+    a.table_empty = c->table_empty ? 1 : 0;
+    a.keys_inline = (c->use_cache && c->table_empty) ? 1 : 0;
     a.n_cells = c->use_cache ? c->desc.n_cells : 1; a.n_entries = c->use_cache ? ne : 1;
     a.level = c->desc.uv_level;
     const uint64_t nc = a.n_cells;
@@ -336,6 +338,8 @@ pmc_status pmc_eval_batch(pmc_cache* c, const pmc_points* pts, float* out_rgb, u
     cudaError_t e = launch_batch(a, s, c->num_sms, ev, &c->launches);
     if (e != cudaSuccess) return cuda_fail(c, e);
     if (c->use_cache) c->epoch_host += ne + 1;
+    c->last_all_miss = a.keys_inline != 0;
+    if (n > 0) c->table_empty = false;
     c->last_stream = s;
     c->last_n = n;
     return PMC_OK;
@@ -453,7 +457,7 @@ pmc_status pmc_last_hit_masks(pmc_cache* c, uint64_t* host_dst, uint64_t n) {
     pmc_status st = pmc_sync(c);
     if (st == PMC_ERR_CUDA) return st;
     std::memset(host_dst, 0, n * sizeof(uint64_t));
-    if (!c->use_cache || n == 0) return st;
+    if (!c->use_cache || n == 0 || c->last_all_miss) return st;   // an empty table: no hits
     DeviceGuard g(c->desc.device);
     const size_t M1 = (size_t)c->n_mats + 1;
     std::vector<uint32_t> seg(5 * M1);
@@ -495,6 +499,7 @@ pmc_status pmc_reset(pmc_cache* c, void* stream) {
                                  (cudaStream_t)stream, (c->desc.flags & PMC_INSERT_ROUNDS) != 0);
     if (e != cudaSuccess) return cuda_fail(c, e);
     c->epoch_host = 0;
+    c->table_empty = true;
     c->last_stream = (cudaStream_t)stream;
     return PMC_OK;
 }

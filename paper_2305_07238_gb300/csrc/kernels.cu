@@ -361,13 +361,16 @@ __global__ void __launch_bounds__(256) k_scatter(BatchArgs a) {
 // (r, g, b) values.  A probe reads the cell's hash2 words (one 32-byte sector for N_e = 8)
 // and, on a hit, the 12 bytes of the matching value in the same line.
 // =======================================================================================
+__device__ __forceinline__ uint32_t* cell_h2(const BatchArgs& a, uint32_t cell) {
+    return reinterpret_cast<uint32_t*>(a.table) + (size_t)cell * 4u * a.n_entries;
+}
+__device__ __forceinline__ float* cell_val(const BatchArgs& a, uint32_t cell, uint32_t j) {
+    return reinterpret_cast<float*>(a.table) + (size_t)cell * 4u * a.n_entries + a.n_entries + 3u * j;
+}
 constexpr uint32_t PROBE_MISS = 0u;   // record {cell, hash2, first empty slot, 0}
 constexpr uint32_t PROBE_HIT = 1u;    // record {r, g, b, 1}
 constexpr uint32_t PROBE_FULL = 2u;   // record {cell, hash2, N_e, 2}: no empty slot
 
-__device__ __forceinline__ const uint32_t* cell_words(const uint4* table, uint32_t cell, uint32_t ne) {
-    return reinterpret_cast<const uint32_t*>(table) + (size_t)cell * 4u * ne;
-}
 
 // Scans the hash2 words of a cell held in registers: first slot holding h2 (hit) or 0.
 template <int NQ>
@@ -422,9 +425,10 @@ __global__ void __launch_bounds__(256) k_lookup(BatchArgs a) {
                     const uint32_t node = __ldg(&a.roots[mi.root_base + r0 + b]);
                     d_address(d_key(m, node, a.level, iu, iv), a.n_cells, a.cells_pow2_mask, &cell[b], &h2[b]);
                 }
-                const uint4* cw = reinterpret_cast<const uint4*>(cell_words(a.table, cell[b], ne));
+                const uint4* hw = reinterpret_cast<const uint4*>(cell_h2(a, cell[b]));
+                const bool ld = act && !a.table_empty;   // an empty table misses at slot 0
 #pragma unroll
-                for (int q = 0; q < NQ; ++q) w[b][q] = act ? __ldg(cw + q) : make_uint4(0, 0, 0, 0);
+                for (int q = 0; q < NQ; ++q) w[b][q] = ld ? __ldg(hw + q) : make_uint4(0, 0, 0, 0);
             }
 #pragma unroll
             for (int b = 0; b < RB; ++b) {
@@ -436,7 +440,7 @@ __global__ void __launch_bounds__(256) k_lookup(BatchArgs a) {
                     n_look++;
                     n_slots += first >= 0 ? (uint32_t)first + 1u : ne;
                     if (hit) {
-                        const float* val = reinterpret_cast<const float*>(cell_words(a.table, cell[b], ne) + ne) + 3u * (uint32_t)first;
+                        const float* val = cell_val(a, cell[b], (uint32_t)first);
                         a.probes[rec] = make_float4(__ldg(val), __ldg(val + 1), __ldg(val + 2), __uint_as_float(PROBE_HIT));
                         n_hit++;
                     } else {
@@ -628,7 +632,7 @@ __global__ void __launch_bounds__(EVAL_WARPS * 32) k_eval(BatchArgs a, uint32_t*
     const uint32_t warp = threadIdx.x >> 5, lane = lane_id();
     float* V = s_val + (size_t)warp * a.max_slots * 96u + lane;
     const uint32_t n_items = a.ctl->n_items;
-    unsigned long long n_nodes = 0, n_flops = 0, n_cand = 0, n_full = 0;
+    unsigned long long n_nodes = 0, n_flops = 0, n_cand = 0, n_full = 0, n_look = 0;
     for (;;) {
         uint32_t item = 0;
         if (lane == 0) item = atomicAdd(item_ctr, 1u);
@@ -653,13 +657,28 @@ __global__ void __launch_bounds__(EVAL_WARPS * 32) k_eval(BatchArgs a, uint32_t*
         int skip_end = -1;          // lane inactive while pc <= skip_end
         uint32_t hits = 0, cand_cell = 0, cand_h2 = 0, cand_node = 0, cand_start = 0;
         bool cand_full = false;
+        uint32_t iu = 0, iv = 0;
+        if (a.keys_inline && valid) {
+            iu = d_texel(pt.u, a.level);
+            iv = d_texel(pt.v, a.level);
+        }
         for (int pc = 0; pc < (int)mi.prog_len; ++pc) {
             const uint4 ins = __ldg(&prog[pc]);
             const uint32_t op = ins.x & 0xFFu;
             if (op == OP_ROOT_BEGIN) {
                 const uint32_t slot = ins.y & 0xFFFFu, r = ins.y >> 16;
                 bool need = valid;
-                if (a.use_cache && valid) {
+                if (a.keys_inline) {
+                    // empty table: every probe misses at slot 0, so the descriptor is all
+                    // the insert needs (no lookup kernel, no probe record)
+                    if (valid) {
+                        d_address(d_key(m, ins.z, a.level, iu, iv), a.n_cells, a.cells_pow2_mask, &cand_cell, &cand_h2);
+                        cand_start = 0;
+                        cand_full = false;
+                        cand_node = ins.z;
+                        n_look++;
+                    }
+                } else if (a.use_cache && valid) {
                     const float4 rec = a.probes[(size_t)pbase + (size_t)r * cnt + j];
                     const uint32_t state = __float_as_uint(rec.w);
                     if (state == PROBE_HIT || state == PROBE_COMPUTED) {
@@ -706,6 +725,11 @@ __global__ void __launch_bounds__(EVAL_WARPS * 32) k_eval(BatchArgs a, uint32_t*
     warp_add_u64(&a.stats[ST_FLOPS], n_flops);
     warp_add_u64(&a.stats[ST_CANDIDATES], n_cand);
     warp_add_u64(&a.stats[ST_FULL], n_full);
+    if (a.keys_inline) {
+        warp_add_u64(&a.stats[ST_LOOKUPS], n_look);
+        warp_add_u64(&a.stats[ST_MISSES], n_look);
+        warp_add_u64(&a.stats[ST_SLOTS], n_look);   // one (empty) slot examined per probe
+    }
 }
 
 // Work items of the batched evaluation: ceil(misses / 32) per cacheable node.
@@ -864,7 +888,7 @@ __global__ void __launch_bounds__(256) k_insert(BatchArgs a) {
                 const unsigned long long prio = __ldcg(&a.cands[idx].prio);
                 const uint32_t cell = __ldcg(&a.cands[idx].cell), h2 = __ldcg(&a.cands[idx].h2);
                 const uint32_t tgt = __ldcg(&a.cands[idx].target);
-                const uint32_t* hw = cell_words(a.table, cell, ne);
+                const uint32_t* hw = cell_h2(a, cell);
                 const uint32_t weight = 1u + (tgt >> 16);
                 int target = -1;
                 bool dup = false;
@@ -903,11 +927,11 @@ __global__ void __launch_bounds__(256) k_insert(BatchArgs a) {
                 if (__ldcg(&a.claims[cell]) == claim_word(epoch, prio)) {
                     const uint32_t tgt = __ldcg(&a.cands[idx].target);
                     const uint32_t e = tgt & 0xFFFFu;
-                    uint32_t* cw = reinterpret_cast<uint32_t*>(a.table) + (size_t)cell * 4u * ne;
-                    cw[e] = __ldcg(&a.cands[idx].h2);
-                    cw[ne + 3u * e] = __float_as_uint(__ldcg(&a.cands[idx].r));
-                    cw[ne + 3u * e + 1] = __float_as_uint(__ldcg(&a.cands[idx].g));
-                    cw[ne + 3u * e + 2] = __float_as_uint(__ldcg(&a.cands[idx].b));
+                    cell_h2(a, cell)[e] = __ldcg(&a.cands[idx].h2);
+                    float* val = cell_val(a, cell, e);
+                    val[0] = __ldcg(&a.cands[idx].r);
+                    val[1] = __ldcg(&a.cands[idx].g);
+                    val[2] = __ldcg(&a.cands[idx].b);
                     n_ins++;
                     n_dup += tgt >> 16;   // its shadows find it in the table
                 } else {
@@ -928,7 +952,7 @@ __global__ void __launch_bounds__(256) k_insert(BatchArgs a) {
 // Candidates are partitioned into bins of INS_CELLS consecutive cells (count, scan,
 // scatter: coalesced), then one block per bin groups its candidates by cell in shared
 // memory and one thread per cell inserts that cell's candidates in ascending order.
-constexpr uint32_t INS_CELLS = 2048;      // cells per bin
+constexpr uint32_t INS_CELLS = INSERT_BIN_CELLS;   // cells per bin (a multiple of 256)
 constexpr uint32_t INS_SMEM_BINS = 4096;  // bins counted in shared memory by the partition
 constexpr uint32_t INS_CAP = 4096;        // candidates grouped in shared memory at a time
 constexpr int INS_REG = 8;                // a cell's candidates sorted in registers
@@ -947,7 +971,7 @@ __device__ __forceinline__ void cas_pair(unsigned long long& pa, uint32_t& ia, u
 __device__ __forceinline__ void insert_one(const BatchArgs& a, const Candidate& c, uint32_t ne,
                                            unsigned long long* n_ins, unsigned long long* n_dup,
                                            unsigned long long* n_full) {
-    uint32_t* cw = reinterpret_cast<uint32_t*>(a.table) + (size_t)c.cell * 4u * ne;
+    uint32_t* cw = cell_h2(a, c.cell);
     const uint32_t weight = 1u + (c.target >> 16);
     int target = -1;
     bool dup = false;
@@ -963,9 +987,10 @@ __device__ __forceinline__ void insert_one(const BatchArgs& a, const Candidate& 
         *n_full += weight;
     } else {
         cw[target] = c.h2;
-        cw[ne + 3u * target] = __float_as_uint(c.r);
-        cw[ne + 3u * target + 1] = __float_as_uint(c.g);
-        cw[ne + 3u * target + 2] = __float_as_uint(c.b);
+        float* val = cell_val(a, c.cell, (uint32_t)target);
+        val[0] = c.r;
+        val[1] = c.g;
+        val[2] = c.b;
         *n_ins += 1;
         *n_dup += c.target >> 16;   // its shadows find it in the table
     }
@@ -1044,7 +1069,13 @@ __global__ void __launch_bounds__(256) k_bin_scatter(BatchArgs a) {
 }
 
 // One block per bin: group by cell in shared memory, then insert per cell in order.
+constexpr uint32_t INS_SMALL = 1024;      // bins up to this size are sorted by (cell, priority)
+
+static_assert(INS_CELLS % 256 == 0, "k_bin_insert scans INS_CELLS / 256 cells per thread");
+static_assert(INS_SMALL <= INS_CAP, "small bins keep their candidate indices in s_order");
+
 __global__ void __launch_bounds__(256) k_bin_insert(BatchArgs a) {
+    __shared__ unsigned long long s_key[INS_SMALL];       // small bins: (cell, priority) keys
     __shared__ uint32_t s_cnt[INS_CELLS];
     __shared__ uint32_t s_off[INS_CELLS + 1];
     __shared__ uint32_t s_cur[INS_CELLS];
@@ -1061,6 +1092,47 @@ __global__ void __launch_bounds__(256) k_bin_insert(BatchArgs a) {
         if (lo == hi) continue;                                 // uniform in the block
         const uint32_t c0 = bin * INS_CELLS;
         const Candidate* cb = a.cands_binned;
+        if (hi - lo <= INS_SMALL) {
+            // few candidates: bitonic sort of (cell, priority) keys, then the first of each
+            // run of equal cells inserts the run in order
+            unsigned long long* key = s_key;
+            uint32_t* idx = s_order;
+            const uint32_t n = hi - lo;
+            uint32_t N = 1;
+            while (N < n) N <<= 1;
+            for (uint32_t i = t; i < N; i += T) {
+                key[i] = i < n ? ((unsigned long long)(cb[lo + i].cell - c0) << 44) | cb[lo + i].prio : ~0ull;
+                idx[i] = lo + i;
+            }
+            __syncthreads();
+            for (uint32_t k = 2; k <= N; k <<= 1) {
+                for (uint32_t j = k >> 1; j > 0; j >>= 1) {
+                    for (uint32_t i = t; i < N; i += T) {
+                        const uint32_t ixj = i ^ j;
+                        if (ixj > i) {
+                            const bool up = (i & k) == 0;
+                            const unsigned long long ki = key[i], kj = key[ixj];
+                            if ((ki > kj) == up) {
+                                key[i] = kj;
+                                key[ixj] = ki;
+                                const uint32_t tmp = idx[i];
+                                idx[i] = idx[ixj];
+                                idx[ixj] = tmp;
+                            }
+                        }
+                    }
+                    __syncthreads();
+                }
+            }
+            for (uint32_t i = t; i < n; i += T) {
+                const uint32_t cell_i = (uint32_t)(key[i] >> 44);
+                if (i > 0 && (uint32_t)(key[i - 1] >> 44) == cell_i) continue;
+                for (uint32_t x = i; x < n && (uint32_t)(key[x] >> 44) == cell_i; ++x)
+                    insert_one(a, cb[idx[x]], ne, &n_ins, &n_dup, &n_full);
+            }
+            __syncthreads();
+            continue;
+        }
         for (uint32_t k = t; k < INS_CELLS; k += T) s_cnt[k] = 0;
         __syncthreads();
         for (uint32_t i = lo + t; i < hi; i += T) atomicAdd(&s_cnt[cb[i].cell - c0], 1u);
@@ -1225,7 +1297,7 @@ cudaError_t launch_keys(const uint32_t* mat, const uint32_t* node, const float* 
 cudaError_t launch_reset(uint4* table, size_t slots, unsigned long long* claims, size_t cells,
                          Control* ctl, unsigned long long* stats, cudaStream_t s, bool claim_words) {
     cudaError_t e;
-    if (slots && (e = cudaMemsetAsync(table, 0, slots * sizeof(uint4), s)) != cudaSuccess) return e;
+    if (slots && (e = cudaMemsetAsync(table, 0, (slots + 16) * sizeof(uint4), s)) != cudaSuccess) return e;
     // all-ones: the largest claim word of the atomicMin rounds, an empty list per cell
     // for the grouped insert
     (void)claim_words;
@@ -1270,9 +1342,9 @@ cudaError_t launch_batch(const BatchArgs& a, cudaStream_t s, int num_sms, cudaEv
         nl++;
     }
     if ((e = mark(1)) != cudaSuccess) return e;
-    if (a.n > 0 && a.use_cache) {
+    if (a.n > 0 && a.use_cache && !a.keys_inline) {
         uint32_t ne = a.n_entries;
-        int lb = num_sms * 8;
+        const unsigned lb = (unsigned)num_sms * 8u;
         if (ne <= 4) k_lookup<1, 4><<<lb, 256, 0, s>>>(a);
         else if (ne <= 8) k_lookup<2, 4><<<lb, 256, 0, s>>>(a);
         else if (ne <= 16) k_lookup<4, 2><<<lb, 256, 0, s>>>(a);
@@ -1288,7 +1360,7 @@ cudaError_t launch_batch(const BatchArgs& a, cudaStream_t s, int num_sms, cudaEv
             if ((e = cudaFuncSetAttribute(k_eval_roots, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
                 return e;
         }
-        if (a.use_cache && a.split) {
+        if (a.use_cache && a.split && !a.keys_inline) {
             k_scan_roots<<<1, 1024, 0, s>>>(a);
             nl++;
             // the level counters live after the per-root miss counters
@@ -1313,7 +1385,7 @@ cudaError_t launch_batch(const BatchArgs& a, cudaStream_t s, int num_sms, cudaEv
         k_bin_count<<<gs_blocks, 256, 0, s>>>(a);
         k_bin_scan<<<1, 1024, 0, s>>>(a);
         k_bin_scatter<<<gs_blocks, 256, 0, s>>>(a);
-        k_bin_insert<<<std::min<uint32_t>(a.n_bins, (uint32_t)num_sms * 8u), 256, 0, s>>>(a);
+        k_bin_insert<<<std::min<uint32_t>(a.n_bins, (uint32_t)num_sms * 16u), 256, 0, s>>>(a);
         nl += 4;
     }
     if ((e = mark(4)) != cudaSuccess) return e;

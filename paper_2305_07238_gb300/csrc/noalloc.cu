@@ -119,6 +119,8 @@ extern "C" pmc_status pmc_eval_batch_noalloc(pmc_cache* c, const pmc_points* pts
     a.snz = sorted + 7 * NA_POINTS;
     a.sidx = reinterpret_cast<uint32_t*>(base + OFF_SIDX);
     a.table = c->d_table; a.claims = c->d_claims;
+    a.table_empty = c->table_empty ? 1 : 0;
+    a.keys_inline = (c->use_cache && c->table_empty) ? 1 : 0;
     a.n_cells = c->use_cache ? c->desc.n_cells : 1; a.n_entries = c->use_cache ? ne : 1;
     a.level = c->desc.uv_level;
     const uint64_t nc = a.n_cells;
@@ -146,6 +148,7 @@ extern "C" pmc_status pmc_eval_batch_noalloc(pmc_cache* c, const pmc_points* pts
         return PMC_ERR_CUDA;
     }
     if (c->use_cache) c->epoch_host += ne + 1;
+    if (n > 0) c->table_empty = false;
     c->last_stream = s;
     return PMC_OK;
 }

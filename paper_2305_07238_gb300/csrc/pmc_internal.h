@@ -138,8 +138,11 @@ struct BatchArgs {
     uint32_t* cursor;
     float* su; float* sv; float* spx; float* spy; float* spz;
     float* snx; float* sny; float* snz; uint32_t* sidx;
-    // cache
+    // cache: cell c = N_e hash2 words then N_e packed (r, g, b) values (16 * N_e bytes)
     uint4* table; unsigned long long* claims;
+    int table_empty;           // nothing inserted yet: every probe misses at slot 0
+    int keys_inline;           // empty table: the evaluator forms descriptors itself and
+                               // emits every cacheable node (no lookup pass)
     uint64_t n_cells; uint32_t n_entries; uint32_t level; uint32_t cells_pow2_mask;
     int use_cache; int debug;
     float4* probes; uint32_t probe_cap;
@@ -152,13 +155,14 @@ struct BatchArgs {
     uint32_t* root_item_base;  // n_roots_total + 1
     uint32_t* misslist;        // probe_cap
     int insert_rounds;         // 1: atomicMin rounds (claims hold epoch words); 0: cell-grouped
-    uint32_t n_bins;           // cell-grouped insert: ceil(n_cells / 2048) bins
+    uint32_t n_bins;           // cell-grouped insert: ceil(n_cells / 512) bins
     uint32_t* bin_cnt;         // n_bins
     uint32_t* bin_base;        // n_bins + 1
     Candidate* cands_binned;   // probe_cap
 };
 
-constexpr uint32_t INSERT_BIN_CELLS = 2048;
+constexpr uint32_t INSERT_BIN_CELLS = 512;
+
 
 // Phases timed by the optional CUDA events of a batch.
 enum { PH_SORT = 0, PH_LOOKUP, PH_EVAL, PH_INSERT, PH_FINISH, PH_COUNT };
