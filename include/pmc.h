@@ -163,6 +163,7 @@ typedef struct {
     uint64_t slots_probed;    /* table slots examined by lookups                     */
     uint64_t points;
     uint64_t bad_points;      /* points whose material index was out of range        */
+    uint64_t surrogate_evals; /* cacheable-node values produced by learned surrogates    */
 } pmc_stats_t;
 
 /* Compiles the networks (cacheable-node analysis, constant folding, serialisation;
@@ -244,6 +245,74 @@ pmc_status pmc_set_timing(pmc_cache* cache, int enable);
  * launched in that time and the number of batches; clears the accumulators. */
 pmc_status pmc_read_timing(pmc_cache* cache, double* ms, uint64_t* kernel_launches,
                            uint64_t* batches);
+
+/* ---- learned surrogates --------------------------------------------------------------
+ * A cacheable node's UV-only sub-graph (Sec. 3) can be replaced by a small network of
+ * (u, v), trained on values of the exact evaluator:
+ *   features = [sin pi k u, cos pi k u, sin pi k v, cos pi k v], k = 1..16 (64;
+ *              half-range frequencies, so a network need not repeat from u = 0 to 1)
+ *   h1 = relu(f W1 + b1) (64), h2 = relu(h1 W2 + b2) (64), y = h2 W3 + b3 (3),
+ *   value = clamp(y, 0, 1).
+ * Parameters: PMC_MLP_PARAMS floats, W1 [64][64], b1 [64], W2 [64][64], b2 [64],
+ * W3 [64][3], b3 [3].  Products take BF16 operands and accumulate in FP32 on tensor
+ * cores; FP32 master weights take Adam steps.  Per material the candidate node is its
+ * most expensive cacheable node with no cacheable node below it.  A node with an enabled
+ * surrogate is not probed: every pass evaluates the network for it. */
+#define PMC_MLP_PARAMS 8515u
+
+typedef struct {
+    uint32_t n_train;   /* training pairs per material, a power of two >= 128          */
+    uint32_t n_valid;   /* held-out pairs per material for the validation RMSE, >= 1   */
+    uint32_t epochs;    /* passes over the training pairs, >= 1                        */
+    float lr;           /* initial Adam step size (cosine decay to 5 %); 0 = 1e-2        */
+    float rmse_max;     /* enable a network only if its validation RMSE <= this; 0 = 2e-3 */
+    uint64_t seed;      /* training and validation (u, v) come from SplitMix64(seed, ...) */
+    const uint32_t* mats; /* host: materials to train; NULL = every material with a candidate */
+    uint32_t n_mats;
+} pmc_train_desc;
+
+/* Generates pairs with the exact evaluator, trains one network per listed material on
+ * the GPU, measures each one's RMSE on held-out pairs against the exact values and
+ * enables those within rmse_max (others keep exact evaluation).  rmse: host, one per
+ * listed material (NULL allowed; -1 for a material without a candidate node).
+ * Synchronous; allocates its own temporary buffers. */
+pmc_status pmc_train_surrogates(pmc_cache* cache, const pmc_train_desc* desc, float* rmse,
+                                void* stream);
+
+/* Installs (theta != NULL, host, PMC_MLP_PARAMS floats) and enables, or removes
+ * (theta == NULL), the surrogate of a material's candidate node. */
+pmc_status pmc_set_surrogate(pmc_cache* cache, uint32_t mat, const float* theta);
+
+/* Copies a material's surrogate parameters (host, may be NULL), its candidate node ID
+ * (UINT32_MAX if none) and whether it is enabled. */
+pmc_status pmc_get_surrogate(pmc_cache* cache, uint32_t mat, float* theta, uint32_t* node,
+                             int* enabled);
+
+/* Whether later passes use the enabled surrogates (default on). */
+pmc_status pmc_use_surrogates(pmc_cache* cache, int enable);
+
+/* Stand-alone network, DEVICE arrays: values of n points (planar 3 x n), clamped to
+ * [0, 1] if clamp != 0.  Asynchronous on `stream`. */
+pmc_status pmc_mlp_forward(const float* theta, const float* u, const float* v, uint64_t n,
+                           float* out, int clamp, void* stream);
+
+/* Gradient of the mean squared error over n rows (a multiple of 128) of `data` (DEVICE,
+ * n x 5 floats: u, v, r, g, b) with respect to theta (DEVICE): grad (DEVICE,
+ * PMC_MLP_PARAMS) is overwritten, *loss (DEVICE, 1 float) receives the sum of squared
+ * errors over the 3n outputs.  The same kernel as training, without the Adam step.
+ * Asynchronous on `stream`. */
+pmc_status pmc_mlp_gradient(const float* theta, const float* data, uint64_t n, float* grad,
+                            float* loss, void* stream);
+
+/* Stand-alone training of one network on caller data (DEVICE): n rows (a power of two
+ * >= 128) of `data` (u, v, r, g, b); theta (FP32, updated in place), adam_m and adam_v
+ * (PMC_MLP_PARAMS each, zero before the first step) persist between calls; `steps`
+ * minibatches of 128 rows, Adam steps numbered from step0 + 1, learning rate
+ * lr * (0.05 + 0.95 * (1 + cos(pi * step / total_steps)) / 2).  *loss (DEVICE) receives
+ * the sum of squared errors of the minibatches.  Asynchronous on `stream`. */
+pmc_status pmc_mlp_train(float* theta, float* adam_m, float* adam_v, const float* data,
+                         uint64_t n, uint32_t steps, uint32_t step0, uint32_t total_steps,
+                         float lr, float* loss, void* stream);
 
 /* ---- pass without device allocation ---------------------------------------------
  * The paper has no counterpart to this entry point; it serves callers that must not

@@ -82,6 +82,10 @@ def lib():
         L.orc_cache_table.argtypes = [vp, vp, vp]
         L.orc_cache_stats.restype = None
         L.orc_cache_stats.argtypes = [vp, vp]
+        L.orc_mlp_forward.restype = None
+        L.orc_mlp_forward.argtypes = [vp, f64, f64, C.c_int, vp]
+        L.orc_cache_set_surrogate.restype = C.c_int
+        L.orc_cache_set_surrogate.argtypes = [vp, u32, u32, vp, C.c_int]
         _lib = L
     return _lib
 
@@ -149,6 +153,19 @@ def eval_point_nocache(nodes, sp) -> np.ndarray:
     return out
 
 
+def mlp_forward(theta, u, v, bf16=False) -> np.ndarray:
+    """The surrogate network in C (FP64; bf16 rounds where the kernels round): (n, 3)."""
+    th = np.ascontiguousarray(theta, dtype=np.float64)
+    uu = np.asarray(u, dtype=np.float64)
+    vv = np.asarray(v, dtype=np.float64)
+    out = np.zeros((len(uu), 3))
+    y = np.zeros(3)
+    for i in range(len(uu)):
+        lib().orc_mlp_forward(_ptr(th), float(uu[i]), float(vv[i]), int(bf16), _ptr(y))
+        out[i] = y
+    return out
+
+
 class Cache:
     """Sequential emulation of the progressive cache over a set of materials."""
 
@@ -180,6 +197,13 @@ class Cache:
 
     def reset(self):
         lib().orc_cache_reset(self._h)
+
+    def set_surrogate(self, mat, node, theta, bf16=True):
+        th = None if theta is None else np.ascontiguousarray(theta, dtype=np.float64)
+        self._surr = getattr(self, "_surr", {})
+        self._surr[mat] = th
+        if lib().orc_cache_set_surrogate(self._h, mat, node, _ptr(th), int(bf16)) != 0:
+            raise ValueError("bad surrogate")
 
     def n_roots(self, m):
         return lib().orc_cache_n_roots(self._h, m)

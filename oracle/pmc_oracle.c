@@ -406,6 +406,9 @@ typedef struct {
     uint8_t* is_root;
     uint32_t n_roots;
     uint32_t* roots; /* ascending node IDs */
+    double* surr_theta; /* learned surrogate of node surr_node, or NULL */
+    uint32_t surr_node;
+    int surr_bf16;
 } orc_mat;
 
 struct orc_cache {
@@ -439,6 +442,7 @@ orc_cache* orc_cache_new(uint64_t n_cells, uint32_t n_entries, uint32_t level,
 
 static void free_mats(orc_cache* c) {
     for (uint32_t m = 0; m < c->n_mats; ++m) {
+        free(c->mats[m].surr_theta);
         free(c->mats[m].nodes);
         free(c->mats[m].is_root);
         free(c->mats[m].roots);
@@ -504,6 +508,66 @@ void orc_cache_roots(const orc_cache* c, uint32_t mat, uint32_t* out) {
     for (uint32_t r = 0; r < c->mats[mat].n_roots; ++r) out[r] = c->mats[mat].roots[r];
 }
 
+/* bfloat16 nearest (ties to even) of the float32 nearest to x, as a double */
+static double bf16(double x) {
+    float f = (float)x;
+    uint32_t b;
+    memcpy(&b, &f, 4);
+    b = (b + 0x7FFFu + ((b >> 16) & 1u)) & 0xFFFF0000u;
+    memcpy(&f, &b, 4);
+    return (double)f;
+}
+
+void orc_mlp_forward(const double* th, double u, double v, int use_bf16, double y[3]) {
+    double g[64], h1[64], h2[64];
+    for (int k = 0; k < 16; ++k) {
+        const double a = M_PI * (double)(k + 1);
+        g[k] = sin(a * u);
+        g[16 + k] = cos(a * u);
+        g[32 + k] = sin(a * v);
+        g[48 + k] = cos(a * v);
+    }
+    if (use_bf16)
+        for (int k = 0; k < 64; ++k) g[k] = bf16(g[k]);
+    const double* W1 = th;
+    const double* b1 = th + 4096;
+    const double* W2 = th + 4160;
+    const double* b2 = th + 8256;
+    const double* W3 = th + 8320;
+    const double* b3 = th + 8512;
+    for (int o = 0; o < 64; ++o) {
+        double z = b1[o];
+        for (int i = 0; i < 64; ++i) z += g[i] * (use_bf16 ? bf16(W1[i * 64 + o]) : W1[i * 64 + o]);
+        h1[o] = z > 0.0 ? z : 0.0;
+        if (use_bf16) h1[o] = bf16(h1[o]);
+    }
+    for (int o = 0; o < 64; ++o) {
+        double z = b2[o];
+        for (int i = 0; i < 64; ++i) z += h1[i] * (use_bf16 ? bf16(W2[i * 64 + o]) : W2[i * 64 + o]);
+        h2[o] = z > 0.0 ? z : 0.0;
+        if (use_bf16) h2[o] = bf16(h2[o]);
+    }
+    for (int o = 0; o < 3; ++o) {
+        double z = b3[o];
+        for (int i = 0; i < 64; ++i) z += h2[i] * (use_bf16 ? bf16(W3[i * 3 + o]) : W3[i * 3 + o]);
+        y[o] = z;
+    }
+}
+
+int orc_cache_set_surrogate(orc_cache* c, uint32_t mat, uint32_t node, const double* theta, int use_bf16) {
+    if (mat >= c->n_mats) return ORC_ERR_ARG;
+    orc_mat* M = &c->mats[mat];
+    free(M->surr_theta);
+    M->surr_theta = NULL;
+    if (!theta) return ORC_OK;
+    if (node >= M->n || !M->is_root[node]) return ORC_ERR_ARG;
+    M->surr_theta = (double*)malloc(ORC_MLP_PARAMS * sizeof(double));
+    memcpy(M->surr_theta, theta, ORC_MLP_PARAMS * sizeof(double));
+    M->surr_node = node;
+    M->surr_bf16 = use_bf16;
+    return ORC_OK;
+}
+
 static void cell_and_check(const orc_cache* c, uint64_t key, uint64_t* cell, uint32_t* h2) {
     if (c->hook) {
         c->hook(key, c->n_cells, cell, h2);
@@ -566,6 +630,14 @@ int orc_run_batch(orc_cache* c, uint64_t n, const float* u, const float* v,
         memset(hit, 0, M->n);
         for (uint32_t r = 0; r < M->n_roots; ++r) {
             uint32_t node = M->roots[r];
+            /* a node with a learned surrogate takes the network's value, no lookup */
+            const int surr = M->surr_theta && node == M->surr_node;
+            if (surr) {
+                double y[3];
+                orc_mlp_forward(M->surr_theta, u[i], v[i], M->surr_bf16, y);
+                hit[node] = 1;
+                for (int k = 0; k < 3; ++k) hitval[3 * node + k] = clamp01(y[k]);
+            }
             if (c->off) continue;
             uint64_t key = orc_key(mat[i], node, c->level, u[i], v[i]);
             uint64_t cell, slot;
@@ -573,15 +645,18 @@ int orc_run_batch(orc_cache* c, uint64_t n, const float* u, const float* v,
             cell_and_check(c, key, &cell, &h2);
             rcell[node] = cell;
             rh2[node] = h2;
-            int found = scan_cell(c, cell, h2, &slot) == 1;
-            c->stats[0]++;
-            if (found) {
-                hit[node] = 1;
-                for (int k = 0; k < 3; ++k) hitval[3 * node + k] = (double)c->rgb[3 * slot + k];
-                c->stats[1]++;
-                n_hit++;
-            } else {
-                c->stats[2]++;
+            int found = 0;
+            if (!surr) {
+                found = scan_cell(c, cell, h2, &slot) == 1;
+                c->stats[0]++;
+                if (found) {
+                    hit[node] = 1;
+                    for (int k = 0; k < 3; ++k) hitval[3 * node + k] = (double)c->rgb[3 * slot + k];
+                    c->stats[1]++;
+                    n_hit++;
+                } else {
+                    c->stats[2]++;
+                }
             }
             if (probe_key) probe_key[probe] = key;
             if (probe_cell) probe_cell[probe] = cell;

@@ -150,6 +150,17 @@ int orc_run_batch(orc_cache* c, uint64_t n, const float* u, const float* v,
 /* Table contents: h2[N_c*N_e], rgb[3*N_c*N_e] (slot-major r,g,b). */
 void orc_cache_table(const orc_cache* c, uint32_t* h2, float* rgb);
 
+/* ---- learned surrogate of a cacheable node -------------------------------------------
+ * Network of (u, v): features [sin pi k u, cos pi k u, sin pi k v, cos pi k v], k=1..16,
+ * -> relu(64) -> relu(64) -> 3; theta = W1[64][64], b1, W2[64][64], b2, W3[64][3], b3.
+ * bf16 != 0 rounds features, weights and hidden activations to bfloat16 (nearest, ties to
+ * even) where the tensor-core kernels round them; everything else is FP64. */
+#define ORC_MLP_PARAMS 8515
+void orc_mlp_forward(const double* theta, double u, double v, int bf16, double y[3]);
+/* From the next batch on, node `node` of material `mat` takes clamp(network(u, v), 0, 1)
+ * instead of a lookup and its sub-graph; theta == NULL removes it. */
+int orc_cache_set_surrogate(orc_cache* c, uint32_t mat, uint32_t node, const double* theta, int bf16);
+
 /* Counters, in this order:
  * 0 lookups, 1 hits, 2 misses, 3 candidates, 4 inserted, 5 dropped_dup,
  * 6 dropped_full, 7 nodes_evaluated, 8 batches. */

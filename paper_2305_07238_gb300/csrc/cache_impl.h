@@ -37,6 +37,17 @@ struct pmc_cache {
     uint32_t n_bins = 0;                  // cell-grouped insert bins
     bool table_empty = true;              // nothing inserted since creation or reset
     bool last_all_miss = false;           // the last batch ran on an empty table
+    // learned surrogates
+    int use_surrogates = 1;
+    std::vector<int32_t> surr_cand;       // per material: candidate node ordinal, -1 if none
+    std::vector<int32_t> surr_slot;       // per material: parameter slot, -1 if none
+    std::vector<uint8_t> surr_on;         // per material: enabled
+    uint32_t n_surr_slots = 0, cap_surr_slots = 0;
+    float* d_surr_theta = nullptr;        // cap_surr_slots x MLP_PARAMS
+    int32_t* d_surr_slot = nullptr;       // n_mats: slot if enabled, else -1
+    int32_t* d_surr_ord = nullptr;        // n_mats: ordinal if enabled, else -1
+    uint32_t* d_surr_items = nullptr;     // n_mats + 1
+    bool any_surr_on = false;
     uint32_t* d_bins = nullptr;           // counts (n_bins) | bases (n_bins + 1)
     // per-batch scratch, grown on demand
     uint64_t cap_points = 0;

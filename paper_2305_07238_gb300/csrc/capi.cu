@@ -1,4 +1,6 @@
 // capi.cu -- the extern "C" entry points declared in include/pmc.h.
+#include <algorithm>
+#include <cmath>
 #include <cstdio>
 #include <cstring>
 #include <new>
@@ -62,8 +64,10 @@ void free_scratch(pmc_cache* c) {
     c->cap_points = c->cap_probes = 0;
 }
 
+bool surrogates_active(const pmc_cache* c) { return c->use_surrogates && c->any_surr_on; }
+
 pmc_status ensure_scratch(pmc_cache* c, uint64_t n) {
-    uint64_t need_probes = c->use_cache ? n * (uint64_t)c->max_roots : 0;
+    uint64_t need_probes = (c->use_cache || surrogates_active(c)) ? n * (uint64_t)c->max_roots : 0;
     if (c->d_seg && n <= c->cap_points && need_probes <= c->cap_probes) return PMC_OK;
     if (c->last_stream || c->d_seg) cudaDeviceSynchronize();
     free_scratch(c);
@@ -140,6 +144,10 @@ void pmc_destroy_cache(pmc_cache* c) {
         dfree(&c->d_miss_cnt);
         dfree(&c->d_root_items);
         dfree(&c->d_bins);
+        dfree(&c->d_surr_theta);
+        dfree(&c->d_surr_slot);
+        dfree(&c->d_surr_ord);
+        dfree(&c->d_surr_items);
         dfree(&c->d_hpts);
         dfree(&c->d_hrgb);
         dfree(&c->d_hhits);
@@ -191,6 +199,15 @@ pmc_status pmc_create_cache(const pmc_cache_desc* desc, const pmc_material* mats
             if ((ins.x & 0xFFu) != OP_ROOT_BEGIN) ins.w += pbase;
             prog.push_back(ins);
         }
+        int32_t cand = -1;
+        uint64_t best_cost = 0;
+        for (size_t r = 0; r < cm.roots.size(); ++r) {
+            if (cm.root_level[r] != 0) continue;   // a surrogate replaces a whole sub-graph
+            uint64_t cost = 0;
+            for (uint4 ins : cm.root_progs[r]) cost += ins.x >> 16;
+            if (cand < 0 || cost > best_cost) { cand = (int32_t)r; best_cost = cost; }
+        }
+        c->surr_cand.push_back(cand);
         for (size_t r = 0; r < cm.roots.size(); ++r) {
             RootInfo ri{};
             ri.prog_start = (uint32_t)prog.size();
@@ -244,7 +261,10 @@ pmc_status pmc_create_cache(const pmc_cache_desc* desc, const pmc_material* mats
         (s = dalloc(&c->d_rinfo, c->root_info.size())) != PMC_OK ||
         (s = dalloc(&c->d_miss_cnt, c->root_info.size() + MAX_LEVELS)) != PMC_OK ||
         (s = dalloc(&c->d_root_items, c->root_info.size() + 1)) != PMC_OK ||
-        (s = dalloc(&c->d_bins, 2 * (size_t)c->n_bins + 1)) != PMC_OK) {
+        (s = dalloc(&c->d_bins, 2 * (size_t)c->n_bins + 1)) != PMC_OK ||
+        (s = dalloc(&c->d_surr_slot, n_mats)) != PMC_OK ||
+        (s = dalloc(&c->d_surr_ord, n_mats)) != PMC_OK ||
+        (s = dalloc(&c->d_surr_items, (size_t)n_mats + 1)) != PMC_OK) {
         pmc_destroy_cache(c);
         return s;
     }
@@ -255,6 +275,10 @@ pmc_status pmc_create_cache(const pmc_cache_desc* desc, const pmc_material* mats
     if (e == cudaSuccess && !c->root_info.empty())
         e = cudaMemcpy(c->d_rinfo, c->root_info.data(), c->root_info.size() * sizeof(RootInfo), cudaMemcpyHostToDevice);
     if (e == cudaSuccess && !c->roots.empty()) e = cudaMemcpy(c->d_roots, c->roots.data(), c->roots.size() * sizeof(uint32_t), cudaMemcpyHostToDevice);
+    c->surr_slot.assign(n_mats, -1);
+    c->surr_on.assign(n_mats, 0);
+    if (e == cudaSuccess) e = cudaMemset(c->d_surr_slot, 0xFF, n_mats * sizeof(int32_t));
+    if (e == cudaSuccess) e = cudaMemset(c->d_surr_ord, 0xFF, n_mats * sizeof(int32_t));
     if (e == cudaSuccess) e = launch_reset(c->d_table, slots, c->d_claims, cells, c->d_ctl, c->d_stats, 0,
                                            (desc->flags & PMC_INSERT_ROUNDS) != 0);
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
@@ -321,6 +345,10 @@ pmc_status pmc_eval_batch(pmc_cache* c, const pmc_points* pts, float* out_rgb, u
     a.insert_rounds = (c->desc.flags & PMC_INSERT_ROUNDS) ? 1 : 0;
     a.n_bins = c->n_bins; a.bin_cnt = c->d_bins; a.bin_base = c->d_bins + c->n_bins;
     a.cands_binned = c->d_cands_binned;
+    if (surrogates_active(c)) {
+        a.surr_slot = c->d_surr_slot; a.surr_ord = c->d_surr_ord; a.surr_theta = c->d_surr_theta;
+        a.surr_item_base = c->d_surr_items;
+    }
     a.rinfo = c->d_rinfo; a.n_roots_total = (uint32_t)c->root_info.size(); a.max_level = c->max_level;
     a.miss_cnt = c->d_miss_cnt; a.root_item_base = c->d_root_items; a.misslist = c->d_misslist;
     cudaEvent_t* ev = nullptr;
@@ -418,6 +446,7 @@ pmc_status pmc_stats(pmc_cache* c, pmc_stats_t* out) {
     out->slots_probed = v[ST_SLOTS];
     out->points = v[ST_POINTS];
     out->bad_points = v[ST_BAD];
+    out->surrogate_evals = v[ST_SURR];
     return st;
 }
 
@@ -559,6 +588,246 @@ pmc_status pmc_analyze_material(const pmc_material* mat, uint32_t min_root_nodes
     if (n_instr) *n_instr = (uint32_t)cm.prog.size();
     if (n_slots) *n_slots = cm.n_slots;
     return PMC_OK;
+}
+
+// ---- learned surrogates ------------------------------------------------------------
+namespace {
+
+pmc_status grow_surrogate_slots(pmc_cache* c, uint32_t need) {
+    if (need <= c->cap_surr_slots) return PMC_OK;
+    uint32_t cap = std::max<uint32_t>(need, 2 * c->cap_surr_slots);
+    float* nt = nullptr;
+    pmc_status st = dalloc(&nt, (size_t)cap * MLP_PARAMS);
+    if (st != PMC_OK) return st;
+    cudaDeviceSynchronize();
+    if (c->d_surr_theta && c->n_surr_slots)
+        cudaMemcpy(nt, c->d_surr_theta, (size_t)c->n_surr_slots * MLP_PARAMS * sizeof(float), cudaMemcpyDeviceToDevice);
+    dfree(&c->d_surr_theta);
+    c->d_surr_theta = nt;
+    c->cap_surr_slots = cap;
+    return PMC_OK;
+}
+
+cudaError_t upload_surrogate_maps(pmc_cache* c) {
+    std::vector<int32_t> slot(c->n_mats, -1), ord(c->n_mats, -1);
+    c->any_surr_on = false;
+    for (uint32_t m = 0; m < c->n_mats; ++m) {
+        if (c->surr_on[m] && c->surr_slot[m] >= 0 && c->surr_cand[m] >= 0) {
+            slot[m] = c->surr_slot[m];
+            ord[m] = c->surr_cand[m];
+            c->any_surr_on = true;
+        }
+    }
+    cudaError_t e = cudaMemcpy(c->d_surr_slot, slot.data(), c->n_mats * sizeof(int32_t), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(c->d_surr_ord, ord.data(), c->n_mats * sizeof(int32_t), cudaMemcpyHostToDevice);
+    return e;
+}
+
+// He-uniform initial weights from SplitMix64, zero biases.
+void init_theta(uint64_t seed, float* th) {
+    uint64_t st = seed;
+    auto next = [&]() {
+        st += 0x9E3779B97F4A7C15ull;
+        uint64_t z = st;
+        z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+        z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+        z ^= z >> 31;
+        return (double)(z >> 11) * (1.0 / 9007199254740992.0);
+    };
+    const double l1 = std::sqrt(6.0 / 64.0), l3 = std::sqrt(6.0 / 64.0);
+    for (uint32_t i = 0; i < MLP_PARAMS; ++i) th[i] = 0.0f;
+    for (uint32_t i = 0; i < 4096; ++i) th[i] = (float)((2.0 * next() - 1.0) * l1);
+    for (uint32_t i = 0; i < 4096; ++i) th[4160 + i] = (float)((2.0 * next() - 1.0) * l1);
+    for (uint32_t i = 0; i < 192; ++i) th[8320 + i] = (float)((2.0 * next() - 1.0) * l3 * 0.5);
+    for (uint32_t i = 0; i < 3; ++i) th[8512 + i] = 0.5f;
+}
+
+}  // namespace
+
+pmc_status pmc_train_surrogates(pmc_cache* c, const pmc_train_desc* d, float* rmse, void* stream) {
+    if (!c || !d) return PMC_ERR_INVALID_ARG;
+    if (c->sticky != PMC_OK) return c->sticky;
+    if (d->n_train < 128 || (d->n_train & (d->n_train - 1)) || d->n_valid == 0 || d->epochs == 0)
+        return PMC_ERR_INVALID_ARG;
+    std::vector<uint32_t> list;
+    if (d->mats) {
+        for (uint32_t i = 0; i < d->n_mats; ++i) {
+            if (d->mats[i] >= c->n_mats) return PMC_ERR_INVALID_ARG;
+            list.push_back(d->mats[i]);
+        }
+    } else {
+        for (uint32_t m = 0; m < c->n_mats; ++m) list.push_back(m);
+    }
+    std::vector<uint32_t> train;   // materials with a candidate node
+    for (uint32_t m : list)
+        if (c->surr_cand[m] >= 0) train.push_back(m);
+    if (rmse)
+        for (size_t i = 0; i < list.size(); ++i) rmse[i] = -1.0f;
+    if (train.empty()) return PMC_OK;
+    DeviceGuard g(c->desc.device);
+    cudaStream_t s = (cudaStream_t)stream;
+    const uint32_t L = (uint32_t)train.size();
+    const uint32_t s0 = c->n_surr_slots;
+    pmc_status st = grow_surrogate_slots(c, s0 + L);
+    if (st != PMC_OK) return st;
+    // initial parameters
+    std::vector<float> th((size_t)L * MLP_PARAMS);
+    for (uint32_t i = 0; i < L; ++i) init_theta(d->seed * 0x100000001B3ull + train[i] + 1, th.data() + (size_t)i * MLP_PARAMS);
+    float* theta = c->d_surr_theta + (size_t)s0 * MLP_PARAMS;
+    cudaError_t e = cudaMemcpyAsync(theta, th.data(), th.size() * sizeof(float), cudaMemcpyHostToDevice, s);
+    // temporaries: Adam moments, pairs, losses, validation predictions
+    float *m1 = nullptr, *m2 = nullptr, *data = nullptr, *loss = nullptr, *pred = nullptr;
+    uint32_t* groots = nullptr;
+    const uint32_t nv = d->n_valid;
+    if ((st = dalloc(&m1, th.size())) != PMC_OK || (st = dalloc(&m2, th.size())) != PMC_OK ||
+        (st = dalloc(&data, (size_t)L * std::max(d->n_train, nv) * 5)) != PMC_OK || (st = dalloc(&loss, L)) != PMC_OK ||
+        (st = dalloc(&pred, (size_t)3 * nv)) != PMC_OK || (st = dalloc(&groots, L)) != PMC_OK) {
+        dfree(&m1); dfree(&m2); dfree(&data); dfree(&loss); dfree(&pred); dfree(&groots);
+        return st;
+    }
+    std::vector<uint32_t> gr(L);
+    for (uint32_t i = 0; i < L; ++i) gr[i] = c->mat_info[train[i]].root_base + (uint32_t)c->surr_cand[train[i]];
+    if (e == cudaSuccess) e = cudaMemcpyAsync(groots, gr.data(), L * sizeof(uint32_t), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(m1, 0, th.size() * sizeof(float), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(m2, 0, th.size() * sizeof(float), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(loss, 0, L * sizeof(float), s);
+    // training pairs from the exact evaluator
+    if (e == cudaSuccess)
+        e = launch_root_samples(c->d_prog, c->d_params, c->d_rinfo, groots, L, d->n_train, d->seed, data,
+                                c->max_slots ? c->max_slots : 1, c->num_sms, s);
+    const uint32_t steps_per_epoch = d->n_train / 128u;
+    const uint32_t total = steps_per_epoch * d->epochs;
+    const float lr = d->lr > 0.0f ? d->lr : 1e-2f;
+    for (uint32_t done = 0; e == cudaSuccess && done < total;) {
+        const uint32_t chunk = std::min<uint32_t>(total - done, 256u);
+        e = launch_mlp_train(theta, m1, m2, nullptr, data, loss, L, d->n_train, chunk, (uint64_t)done * 128u, done,
+                             total, lr, 2.0f / (3.0f * 128.0f), 0, 1, s);
+        done += chunk;
+    }
+    // validation against held-out exact values
+    std::vector<float> valid((size_t)nv * 5), out((size_t)3 * nv);
+    if (e == cudaSuccess)
+        e = launch_root_samples(c->d_prog, c->d_params, c->d_rinfo, groots, L, nv, d->seed ^ 0x5DEECE66Dull, data,
+                                c->max_slots ? c->max_slots : 1, c->num_sms, s);
+    std::vector<float> host_data((size_t)L * nv * 5);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(host_data.data(), data, host_data.size() * sizeof(float), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    // the validation (u, v) live inside `data`: run the network on copies of them
+    float *du = nullptr, *dv = nullptr;
+    if (e == cudaSuccess && (dalloc(&du, nv) != PMC_OK || dalloc(&dv, nv) != PMC_OK)) e = cudaErrorMemoryAllocation;
+    std::vector<float> uu(nv), vv(nv);
+    for (uint32_t i = 0; e == cudaSuccess && i < L; ++i) {
+        const float* hd = host_data.data() + (size_t)i * nv * 5;
+        for (uint32_t r = 0; r < nv; ++r) {
+            uu[r] = hd[5 * r];
+            vv[r] = hd[5 * r + 1];
+        }
+        e = cudaMemcpy(du, uu.data(), nv * sizeof(float), cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMemcpy(dv, vv.data(), nv * sizeof(float), cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = launch_mlp_forward(theta + (size_t)i * MLP_PARAMS, du, dv, nv, pred, 1, c->num_sms, s);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(out.data(), pred, out.size() * sizeof(float), cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) break;
+        double se = 0.0;
+        for (uint32_t r = 0; r < nv; ++r)
+            for (int k = 0; k < 3; ++k) {
+                const double df = (double)out[(size_t)k * nv + r] - (double)hd[5 * r + 2 + k];
+                se += df * df;
+            }
+        const float err = (float)std::sqrt(se / (3.0 * nv));
+        const uint32_t m = train[i];
+        c->surr_slot[m] = (int32_t)(s0 + i);
+        c->surr_on[m] = err <= (d->rmse_max > 0.0f ? d->rmse_max : 2e-3f);
+        if (rmse)
+            for (size_t k = 0; k < list.size(); ++k)
+                if (list[k] == m) rmse[k] = err;
+    }
+    dfree(&du); dfree(&dv);
+    dfree(&m1); dfree(&m2); dfree(&data); dfree(&loss); dfree(&pred); dfree(&groots);
+    if (e != cudaSuccess) return cuda_fail(c, e);
+    c->n_surr_slots = s0 + L;
+    e = upload_surrogate_maps(c);
+    if (e != cudaSuccess) return cuda_fail(c, e);
+    return PMC_OK;
+}
+
+pmc_status pmc_set_surrogate(pmc_cache* c, uint32_t mat, const float* theta) {
+    if (!c || mat >= c->n_mats) return PMC_ERR_INVALID_ARG;
+    if (c->surr_cand[mat] < 0) return PMC_ERR_UNSUPPORTED;
+    DeviceGuard g(c->desc.device);
+    if (!theta) {
+        c->surr_on[mat] = 0;
+    } else {
+        if (c->surr_slot[mat] < 0) {
+            pmc_status st = grow_surrogate_slots(c, c->n_surr_slots + 1);
+            if (st != PMC_OK) return st;
+            c->surr_slot[mat] = (int32_t)c->n_surr_slots++;
+        }
+        cudaDeviceSynchronize();
+        cudaError_t e = cudaMemcpy(c->d_surr_theta + (size_t)c->surr_slot[mat] * MLP_PARAMS, theta,
+                                   MLP_PARAMS * sizeof(float), cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) return cuda_fail(c, e);
+        c->surr_on[mat] = 1;
+    }
+    cudaDeviceSynchronize();
+    cudaError_t e = upload_surrogate_maps(c);
+    return e == cudaSuccess ? PMC_OK : cuda_fail(c, e);
+}
+
+pmc_status pmc_get_surrogate(pmc_cache* c, uint32_t mat, float* theta, uint32_t* node, int* enabled) {
+    if (!c || mat >= c->n_mats) return PMC_ERR_INVALID_ARG;
+    if (node) *node = c->surr_cand[mat] >= 0 ? c->roots[c->mat_info[mat].root_base + c->surr_cand[mat]] : 0xFFFFFFFFu;
+    if (enabled) *enabled = c->surr_on[mat] && c->surr_slot[mat] >= 0;
+    if (theta) {
+        if (c->surr_slot[mat] < 0) return PMC_ERR_INVALID_ARG;
+        DeviceGuard g(c->desc.device);
+        cudaDeviceSynchronize();
+        cudaError_t e = cudaMemcpy(theta, c->d_surr_theta + (size_t)c->surr_slot[mat] * MLP_PARAMS,
+                                   MLP_PARAMS * sizeof(float), cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) return cuda_fail(c, e);
+    }
+    return PMC_OK;
+}
+
+pmc_status pmc_use_surrogates(pmc_cache* c, int enable) {
+    if (!c) return PMC_ERR_INVALID_ARG;
+    c->use_surrogates = enable != 0;
+    return PMC_OK;
+}
+
+pmc_status pmc_mlp_forward(const float* theta, const float* u, const float* v, uint64_t n, float* out, int clamp,
+                           void* stream) {
+    if (n && (!theta || !u || !v || !out)) return PMC_ERR_INVALID_ARG;
+    if (n >= (1ull << 31)) return PMC_ERR_UNSUPPORTED;
+    int dev = 0, sms = 1;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaError_t e = launch_mlp_forward(theta, u, v, (uint32_t)n, out, clamp, sms, (cudaStream_t)stream);
+    return e == cudaSuccess ? PMC_OK : cuda_fail(nullptr, e);
+}
+
+pmc_status pmc_mlp_gradient(const float* theta, const float* data, uint64_t n, float* grad, float* loss,
+                            void* stream) {
+    if (!theta || !data || !grad || !loss || n == 0 || n % 128 || n >= (1ull << 31)) return PMC_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t e = cudaMemsetAsync(grad, 0, MLP_PARAMS * sizeof(float), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(loss, 0, sizeof(float), s);
+    // gradient mode: one step of 128 rows per block, rows taken in order
+    if (e == cudaSuccess)
+        e = launch_mlp_train(const_cast<float*>(theta), nullptr, nullptr, grad, data, loss, 1, (uint32_t)n, 1, 0, 0, 1,
+                             0.0f, 2.0f / (3.0f * (float)n), 1, (uint32_t)(n / 128), s);
+    return e == cudaSuccess ? PMC_OK : cuda_fail(nullptr, e);
+}
+
+pmc_status pmc_mlp_train(float* theta, float* adam_m, float* adam_v, const float* data, uint64_t n, uint32_t steps,
+                         uint32_t step0, uint32_t total_steps, float lr, float* loss, void* stream) {
+    if (!theta || !adam_m || !adam_v || !data || !loss || n < 128 || (n & (n - 1)) || n >= (1ull << 31))
+        return PMC_ERR_INVALID_ARG;
+    cudaError_t e = launch_mlp_train(theta, adam_m, adam_v, nullptr, data, loss, 1, (uint32_t)n, steps,
+                                     (uint64_t)step0 * 128u, step0, total_steps, lr, 2.0f / (3.0f * 128.0f), 0, 1,
+                                     (cudaStream_t)stream);
+    return e == cudaSuccess ? PMC_OK : cuda_fail(nullptr, e);
 }
 
 pmc_status pmc_compute_keys(const uint32_t* mat, const uint32_t* node, const float* u, const float* v,

@@ -68,7 +68,7 @@ extern "C" pmc_status pmc_eval_batch_noalloc(pmc_cache* c, const pmc_points* pts
     if (n > 0 && (!pts->u || !pts->v || !pts->mat || !pts->px || !pts->py || !pts->pz || !pts->nx ||
                   !pts->ny || !pts->nz || !out_rgb))
         return PMC_ERR_INVALID_ARG;
-    const uint64_t probes = c->use_cache ? n * (uint64_t)c->max_roots : 0;
+    const uint64_t probes = (c->use_cache || (c->use_surrogates && c->any_surr_on)) ? n * (uint64_t)c->max_roots : 0;
     if (n > PMC_NOALLOC_MAX_POINTS || c->n_mats > PMC_NOALLOC_MAX_MATERIALS || probes > PMC_NOALLOC_MAX_PROBES) {
         fprintf(stderr,
                 "pmc_eval_batch_noalloc: %llu points x %u cacheable nodes over %u materials exceeds the fixed "
@@ -136,6 +136,10 @@ extern "C" pmc_status pmc_eval_batch_noalloc(pmc_cache* c, const pmc_points* pts
     a.insert_rounds = (c->desc.flags & PMC_INSERT_ROUNDS) ? 1 : 0;
     a.n_bins = c->n_bins; a.bin_cnt = c->d_bins; a.bin_base = c->d_bins + c->n_bins;
     a.cands_binned = reinterpret_cast<Candidate*>(base + OFF_BINNED);
+    if (c->use_surrogates && c->any_surr_on) {
+        a.surr_slot = c->d_surr_slot; a.surr_ord = c->d_surr_ord; a.surr_theta = c->d_surr_theta;
+        a.surr_item_base = c->d_surr_items;
+    }
     a.rinfo = c->d_rinfo; a.n_roots_total = (uint32_t)c->root_info.size(); a.max_level = c->max_level;
     a.miss_cnt = c->d_miss_cnt; a.root_item_base = c->d_root_items;
     a.misslist = reinterpret_cast<uint32_t*>(base + OFF_MISS);

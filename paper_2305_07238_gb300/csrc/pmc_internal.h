@@ -89,7 +89,8 @@ constexpr uint32_t EPOCH_BITS = 20;
 constexpr uint32_t EPOCH_MAX = (1u << EPOCH_BITS) - 1;
 constexpr uint64_t MAX_POINTS = 1ull << 28;
 
-constexpr uint32_t MAX_LEVELS = 16;     // nesting depth of cacheable nodes handled in batches
+constexpr uint32_t MAX_LEVELS = 16;
+constexpr uint32_t MLP_PARAMS = 8515;  // learned surrogate: 64 -> 64 -> 64 -> 3     // nesting depth of cacheable nodes handled in batches
 
 // Device-side control block of one cache object.
 struct Control {
@@ -98,7 +99,7 @@ struct Control {
     uint32_t total_probes;
     uint32_t n_cand;            // candidates emitted by the evaluation
     uint32_t n_root_items;      // work items of the batched evaluation of misses
-    uint32_t pad0;
+    uint32_t n_surr_items;      // work items of the surrogate inference
     uint32_t pad1;
     // persistent
     uint32_t epoch;             // claim epoch of round 0 of the current batch
@@ -117,7 +118,7 @@ constexpr uint32_t ERR_TIMEOUT = 8;
 // Counter indices in the device stats array.
 enum {
     ST_LOOKUPS = 0, ST_HITS, ST_MISSES, ST_CANDIDATES, ST_INSERTED, ST_DUP, ST_FULL,
-    ST_NODES, ST_BATCHES, ST_FLOPS, ST_SLOTS, ST_POINTS, ST_BAD, ST_COUNT = 16
+    ST_NODES, ST_BATCHES, ST_FLOPS, ST_SLOTS, ST_POINTS, ST_BAD, ST_SURR, ST_COUNT = 16
 };
 
 // Everything a batch's kernels need, by value.
@@ -155,6 +156,10 @@ struct BatchArgs {
     uint32_t* root_item_base;  // n_roots_total + 1
     uint32_t* misslist;        // probe_cap
     int insert_rounds;         // 1: atomicMin rounds (claims hold epoch words); 0: cell-grouped
+    // learned surrogates: per material the surrogate's slot (-1 = none) and cacheable-node
+    // ordinal; FP32 parameters per slot; work items of 128 points per material
+    const int32_t* surr_slot; const int32_t* surr_ord; const float* surr_theta;
+    uint32_t* surr_item_base;  // n_mats + 1 (computed by k_scan)
     uint32_t n_bins;           // cell-grouped insert: ceil(n_cells / 512) bins
     uint32_t* bin_cnt;         // n_bins
     uint32_t* bin_base;        // n_bins + 1
@@ -177,5 +182,19 @@ cudaError_t launch_keys(const uint32_t* mat, const uint32_t* node, const float* 
                         const float* v, uint64_t n, uint32_t level, uint64_t n_cells,
                         uint64_t* key, uint64_t* cell, uint32_t* h2, cudaStream_t s);
 size_t eval_smem_bytes(uint32_t max_slots);
+
+// Learned surrogate kernels (mlp.cu).
+size_t mlp_train_smem();
+size_t mlp_infer_smem();
+cudaError_t launch_mlp_train(float* theta, float* adam_m, float* adam_v, float* grad, const float* data, float* loss,
+                             uint32_t n_mats, uint32_t n_data, uint32_t steps, uint64_t sample0, uint32_t step0,
+                             uint32_t total_steps, float lr, float grad_scale, int mode, uint32_t splits,
+                             cudaStream_t s);
+cudaError_t launch_mlp_forward(const float* theta, const float* u, const float* v, uint32_t n, float* out, int clamp,
+                               int num_sms, cudaStream_t s);
+cudaError_t launch_root_samples(const uint4* prog, const float* params, const RootInfo* rinfo, const uint32_t* groots,
+                                uint32_t n_train_mats, uint32_t n_rows, uint64_t seed, float* data, uint32_t max_slots,
+                                int num_sms, cudaStream_t s);
+cudaError_t launch_surrogate(const BatchArgs& a, int num_sms, cudaStream_t s);
 
 }  // namespace pmc

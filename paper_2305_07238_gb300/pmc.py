@@ -27,7 +27,9 @@ EXPORTED = (
     "pmc_create_cache", "pmc_eval_batch", "pmc_eval_batch_host", "pmc_sync", "pmc_stats",
     "pmc_table_dump", "pmc_last_hit_masks", "pmc_reset", "pmc_destroy_cache",
     "pmc_material_info", "pmc_analyze_material", "pmc_compute_keys", "pmc_set_timing",
-    "pmc_read_timing", "pmc_eval_batch_noalloc", "pmc_status_str",
+    "pmc_read_timing", "pmc_eval_batch_noalloc", "pmc_train_surrogates", "pmc_set_surrogate",
+    "pmc_get_surrogate", "pmc_use_surrogates", "pmc_mlp_forward", "pmc_mlp_gradient", "pmc_mlp_train",
+    "pmc_status_str",
 )
 NOALLOC_MAX_POINTS, NOALLOC_MAX_PROBES, NOALLOC_MAX_MATERIALS = 8192, 32768, 4096
 PHASES = ("sort", "lookup", "eval", "insert", "finish")
@@ -57,7 +59,14 @@ class _Points(C.Structure):
 
 
 STAT_FIELDS = ("lookups", "hits", "misses", "candidates", "inserted", "dropped_dup", "dropped_full",
-               "nodes_evaluated", "batches", "flops", "slots_probed", "points", "bad_points")
+               "nodes_evaluated", "batches", "flops", "slots_probed", "points", "bad_points",
+               "surrogate_evals")
+MLP_PARAMS = 8515
+
+
+class _TrainDesc(C.Structure):
+    _fields_ = [("n_train", C.c_uint32), ("n_valid", C.c_uint32), ("epochs", C.c_uint32), ("lr", C.c_float),
+                ("rmse_max", C.c_float), ("seed", C.c_uint64), ("mats", C.c_void_p), ("n_mats", C.c_uint32)]
 
 
 class _Stats(C.Structure):
@@ -108,6 +117,20 @@ def load():
     L.pmc_read_timing.restype = st
     L.pmc_eval_batch_noalloc.argtypes = [vp, vp, vp, vp, vp]
     L.pmc_eval_batch_noalloc.restype = st
+    L.pmc_train_surrogates.argtypes = [vp, vp, vp, vp]
+    L.pmc_train_surrogates.restype = st
+    L.pmc_set_surrogate.argtypes = [vp, u32, vp]
+    L.pmc_set_surrogate.restype = st
+    L.pmc_get_surrogate.argtypes = [vp, u32, vp, vp, vp]
+    L.pmc_get_surrogate.restype = st
+    L.pmc_use_surrogates.argtypes = [vp, C.c_int]
+    L.pmc_use_surrogates.restype = st
+    L.pmc_mlp_forward.argtypes = [vp, vp, vp, u64, vp, C.c_int, vp]
+    L.pmc_mlp_forward.restype = st
+    L.pmc_mlp_gradient.argtypes = [vp, vp, u64, vp, vp, vp]
+    L.pmc_mlp_gradient.restype = st
+    L.pmc_mlp_train.argtypes = [vp, vp, vp, vp, u64, u32, u32, u32, C.c_float, vp, vp]
+    L.pmc_mlp_train.restype = st
     L.pmc_status_str.argtypes = [st]
     L.pmc_status_str.restype = C.c_char_p
     _lib = L
@@ -247,12 +270,70 @@ class Cache:
         _check(load().pmc_read_timing(self._h, ms.ctypes.data, C.byref(nl), C.byref(nb)), "pmc_read_timing")
         return {"ms": dict(zip(PHASES, ms.tolist())), "launches": nl.value, "batches": nb.value}
 
+    # ---- learned surrogates ------------------------------------------------------------
+    def train_surrogates(self, n_train=1 << 16, n_valid=8192, epochs=4, lr=0.0, rmse_max=0.0, seed=1,
+                         mats=None, stream=None) -> np.ndarray:
+        """Trains and validates surrogates; returns the validation RMSE per listed material."""
+        ml = None if mats is None else np.ascontiguousarray(mats, dtype=np.uint32)
+        n = self.n_mats if ml is None else len(ml)
+        d = _TrainDesc(n_train, n_valid, epochs, lr, rmse_max, seed,
+                       None if ml is None else ml.ctypes.data, 0 if ml is None else len(ml))
+        out = np.zeros(max(n, 1), dtype=np.float32)
+        _check(load().pmc_train_surrogates(self._h, C.byref(d), out.ctypes.data, _stream_handle(stream)),
+               "pmc_train_surrogates")
+        return out[:n]
+
+    def set_surrogate(self, m: int, theta):
+        th = None if theta is None else np.ascontiguousarray(theta, dtype=np.float32)
+        _check(load().pmc_set_surrogate(self._h, m, None if th is None else th.ctypes.data), "pmc_set_surrogate")
+
+    def get_surrogate(self, m: int, with_theta=True) -> dict:
+        node, en = C.c_uint32(), C.c_int()
+        th = np.zeros(MLP_PARAMS, dtype=np.float32) if with_theta else None
+        _check(load().pmc_get_surrogate(self._h, m, None if th is None else th.ctypes.data, C.byref(node),
+                                        C.byref(en)), "pmc_get_surrogate")
+        return {"theta": th, "node": node.value, "enabled": bool(en.value)}
+
+    def use_surrogates(self, on: bool):
+        _check(load().pmc_use_surrogates(self._h, int(bool(on))), "pmc_use_surrogates")
+
     def material_info(self, m: int) -> dict:
         nr, ni, ns = C.c_uint32(), C.c_uint32(), C.c_uint32()
         roots = np.zeros(65536, dtype=np.uint32)
         _check(load().pmc_material_info(self._h, m, C.byref(nr), roots.ctypes.data, 65536,
                                         C.byref(ni), C.byref(ns)), "pmc_material_info")
         return {"roots": roots[: nr.value].copy(), "n_instr": ni.value, "n_slots": ns.value}
+
+
+def mlp_forward(theta, u, v, clamp=True, stream=None):
+    """The surrogate network on device tensors: theta (8515 float32), u, v -> (3, n)."""
+    import torch
+    n = int(u.numel())
+    out = torch.empty((3, n), dtype=torch.float32, device=u.device)
+    _check(load().pmc_mlp_forward(_dptr(theta), _dptr(u), _dptr(v), n, _dptr(out), int(clamp),
+                                  _stream_handle(stream)), "pmc_mlp_forward")
+    return out
+
+
+def mlp_gradient(theta, data, stream=None):
+    """Gradient (8515) and summed squared error of the mean-squared loss over data (n x 5)."""
+    import torch
+    n = int(data.shape[0])
+    grad = torch.empty(MLP_PARAMS, dtype=torch.float32, device=data.device)
+    loss = torch.empty(1, dtype=torch.float32, device=data.device)
+    _check(load().pmc_mlp_gradient(_dptr(theta), _dptr(data), n, _dptr(grad), _dptr(loss),
+                                   _stream_handle(stream)), "pmc_mlp_gradient")
+    return grad, loss
+
+
+def mlp_train(theta, adam_m, adam_v, data, steps, step0, total_steps, lr, stream=None):
+    """Adam steps of the surrogate network on data (n x 5, n a power of two) in place."""
+    import torch
+    loss = torch.zeros(1, dtype=torch.float32, device=data.device)
+    _check(load().pmc_mlp_train(_dptr(theta), _dptr(adam_m), _dptr(adam_v), _dptr(data), int(data.shape[0]),
+                                steps, step0, total_steps, lr, _dptr(loss), _stream_handle(stream)),
+           "pmc_mlp_train")
+    return loss
 
 
 def analyze_material(nodes, min_root_nodes=2) -> dict:

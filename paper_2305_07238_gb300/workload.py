@@ -156,8 +156,9 @@ def _loguniform(rng, lo, hi):
 class _NetGen:
     """Grows one network: UV-only texture trees joined by shading-point dependent nodes."""
 
-    def __init__(self, rng):
+    def __init__(self, rng, smooth=False):
         self.rng = rng
+        self.smooth = smooth   # low-frequency textures only (no checker), for surrogates
         self.b = Builder()
         self.uv = self.b.add(OP_UV)
         self.pos = None
@@ -194,7 +195,7 @@ class _NetGen:
         """A texture coordinate: the UV node itself or an affine map of it."""
         if budget >= 1 and self.rng.random() < 0.5:
             th = float(self.rng.uniform(0.0, 2.0 * math.pi))
-            sc = _loguniform(self.rng, 0.5, 2.0)
+            sc = _loguniform(self.rng, 0.5, 1.5 if self.smooth else 2.0)
             c, s = sc * math.cos(th), sc * math.sin(th)
             off = [float(x) for x in self.rng.uniform(0.0, 4.0, 2)]
             return self.b.add(OP_UV_AFFINE, [self.uv], fp=[c, -s, s, c, off[0], off[1]]), 1
@@ -203,15 +204,15 @@ class _NetGen:
     def _texture(self, budget):
         """A texture leaf using about `budget` nodes (>= 1)."""
         rng = self.rng
-        kind = rng.choice(["fbm", "fbm", "voronoi", "checker"])
+        kind = rng.choice(["fbm", "fbm", "voronoi"] if self.smooth else ["fbm", "fbm", "voronoi", "checker"])
         if kind == "checker":
             s = float(2 ** int(rng.integers(1, 10)))
             return self.b.add(OP_CHECKER, [self.uv], fp=[s] + self._color() + self._color())
         coord, used = self._coord(budget - 1)
         if kind == "fbm":
-            ip, fp = self._fbm_params(2.0, 16.0, 256.0)
+            ip, fp = self._fbm_params(0.5, 2.0, 4.0) if self.smooth else self._fbm_params(2.0, 16.0, 256.0)
             return self.b.add(OP_FBM, [coord], ip=ip, fp=fp)
-        s = _loguniform(rng, 2.0, 32.0)
+        s = _loguniform(rng, 0.5, 2.0) if self.smooth else _loguniform(rng, 2.0, 32.0)
         return self.b.add(OP_VORONOI, [coord], ip=[0, self._seed()], fp=[s])
 
     def _ramp(self, src):
@@ -282,12 +283,12 @@ class _NetGen:
 
 
 def random_material(rng: np.random.Generator, n_nodes: int, sp_frac: float,
-                    n_trees: int | None = None) -> np.ndarray:
+                    n_trees: int | None = None, smooth: bool = False) -> np.ndarray:
     """A network of about n_nodes nodes in which about sp_frac of the nodes depend on
     position or normal.  UV-only texture trees (noise, Worley, checker, ramps, mixes,
     add/multiply, power) are joined by MIX nodes whose factor depends on the shading
     point, so the top node of each tree is a cacheable node."""
-    g = _NetGen(rng)
+    g = _NetGen(rng, smooth=smooth)
     n_sp = max(2, int(round(sp_frac * n_nodes)))
     if n_trees is None:
         n_trees = max(1, n_sp // 2)
@@ -319,6 +320,19 @@ def random_materials(n_mats: int, lo: int, hi: int, sp_frac: float, seed: int = 
     for _ in range(n_mats):
         n = int(round(_loguniform(rng, lo, hi)))
         mats.append(random_material(rng, n, sp_frac))
+    return mats
+
+
+def surrogate_materials(n_mats: int, lo: int = 500, hi: int = 2000, seed: int = 0) -> list:
+    """Networks whose one cacheable node sits on a deep UV-only tree of low-frequency
+    textures (noise of 1-3 octaves at scales 0.5-2, Worley at 0.5-2, ramps, mixes,
+    add/multiply, power), feeding a single shading-point dependent mix: the shape a
+    learned surrogate stands in for.  Node counts log-uniform on [lo, hi]."""
+    rng = np.random.Generator(np.random.PCG64([seed, 4]))
+    mats = []
+    for _ in range(n_mats):
+        n = int(round(_loguniform(rng, lo, hi)))
+        mats.append(random_material(rng, n, 2.0 / n, n_trees=1, smooth=True))
     return mats
 
 
