@@ -222,9 +222,12 @@ def ours(args, rank, world, local_rank, dist):
     fp32_peak = N_SMS * FP32_LANES_PER_SM * 2 * sm_mhz_max * 1e6 / 1e12   # TFLOP/s
     flops_per_frame = frame_stats["flops"]
     eval_tflops = flops_per_frame * args.steps / (ms["eval"] / 1e3) / 1e12 if ms["eval"] else 0.0
-    look_bytes_frame = (8 * n * SPP                               # u, v of every point
-                        + 16 * frame_stats["slots_probed"]        # slots examined
-                        + 16 * frame_stats["lookups"])            # one 16-B record per probe
+    # algorithmic bytes of the lookup: u, v of every grouped point, the hash2 words
+    # examined (4 B each), the 12-B value of every hit and one 16-B record per probe
+    look_bytes_frame = (8 * n * SPP
+                        + 4 * frame_stats["slots_probed"]
+                        + 12 * frame_stats["hits"]
+                        + 16 * frame_stats["lookups"])
     look_gbs = look_bytes_frame * args.steps / (ms["lookup"] / 1e3) / 1e9 if ms["lookup"] else 0.0
     kernels = {
         "eval": {"bound": "alu", "achieved": round(eval_tflops, 3), "peak": round(fp32_peak, 2),
@@ -257,9 +260,59 @@ def ours(args, rank, world, local_rank, dist):
         "gpu_launches": int(timing["launches"]),
         "clocks": clk.summary(),
     }
+    if "surr" in legs:
+        line["surrogate"] = surrogate_leg(torch, P, dev, local_rank, seed=rank)
     if rank == 0 and not args.no_cpu_baseline and "cpu" in legs:
         line["cpu_baseline"], line["max_abs_err_vs_fp64"] = cpu_baseline(P, torch, mats, frame, dev)
     return line
+
+
+SURR_MATS, SURR_LO, SURR_HI, SURR_PASSES = 256, 500, 2000, 8
+
+
+def surrogate_leg(torch, P, dev, local_rank, seed=0):
+    """Deep networks (256 of 500-2000 nodes, one cacheable node on a low-frequency UV tree
+    each) shaded over 1920x1080 passes: exact without cache, exact with the cache, and
+    with trained surrogates (cache on for any other node).  Training time, the fraction
+    of networks within RMSE 2e-3 and the median RMSE are reported."""
+    mats = W.surrogate_materials(SURR_MATS, SURR_LO, SURR_HI, seed=seed)
+    frame = W.Frame(W.FrameSpec(width=WIDTH, height=HEIGHT, n_mats=SURR_MATS, seed=seed + 100))
+    passes = [P.points_to_device(frame.points(p), dev) for p in range(SURR_PASSES)]
+    n = WIDTH * HEIGHT
+    outs = torch.empty((3, n), dtype=torch.float32, device=dev)
+    res = {"config": f"{SURR_MATS} networks of {SURR_LO}-{SURR_HI} nodes, one cacheable node each on a "
+                     f"low-frequency UV tree; {SURR_PASSES} passes of {n} points; table {N_CELLS}x{N_ENTRIES}"}
+
+    def run(cache):
+        cache.reset()
+        for p in range(SURR_PASSES):
+            cache.eval_batch(passes[p], outs)
+        cache.sync()
+        torch.cuda.synchronize()
+        t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        cache.reset()
+        t0.record()
+        for p in range(SURR_PASSES):
+            cache.eval_batch(passes[p], outs)
+        t1.record()
+        torch.cuda.synchronize()
+        return n * SURR_PASSES / (t0.elapsed_time(t1) / 1e3)
+
+    res["uncached"] = round(run(P.Cache(mats, N_CELLS, N_ENTRIES, flags=P.PMC_CACHE_OFF, device=local_rank)), 1)
+    cached = P.Cache(mats, N_CELLS, N_ENTRIES, device=local_rank)
+    res["cached"] = round(run(cached), 1)
+    t = time.perf_counter()
+    rmse = cached.train_surrogates(n_train=1 << 16, n_valid=8192, epochs=32, lr=1e-2, seed=1)
+    torch.cuda.synchronize()
+    res["train_s"] = round(time.perf_counter() - t, 3)
+    res["train_pairs_per_network"] = (1 << 16) * 32
+    res["within_2e-3"] = round(float(np.mean((rmse >= 0) & (rmse <= 2e-3))), 4)
+    res["rmse_median"] = float(np.median(rmse[rmse >= 0])) if np.any(rmse >= 0) else None
+    res["surrogate"] = round(run(cached), 1)
+    res["unit"] = UNIT
+    res["speedup_surrogate_over_uncached"] = round(res["surrogate"] / res["uncached"], 2)
+    res["speedup_cached_over_uncached"] = round(res["cached"] / res["uncached"], 2)
+    return res
 
 
 def e2e_run(torch, P, mats, passes_host, args, local_rank, barrier, dist, dev):
@@ -372,8 +425,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--legs", default="cached,uncached,e2e,cpu",
-                    help="comma list of cached, uncached, e2e, cpu (profiling runs take 'cached')")
+    ap.add_argument("--legs", default="cached,uncached,e2e,surr,cpu",
+                    help="comma list of cached, uncached, e2e, surr, cpu (profiling runs take 'cached')")
     args = ap.parse_args()
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
