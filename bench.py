@@ -151,6 +151,21 @@ def timed_steps(torch, cache, dev_passes, outs, hits, steps, dist_barrier):
     return t0.elapsed_time(t1) / 1000.0
 
 
+def timed_graph(torch, graph, steps, dist_barrier):
+    stream = torch.cuda.current_stream()
+    dist_barrier()
+    torch.cuda.synchronize()
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    for _ in range(steps):
+        graph.launch(stream)
+    t1.record(stream)
+    torch.cuda.synchronize()
+    dist_barrier()
+    return t0.elapsed_time(t1) / 1000.0
+
+
 def ours(args, rank, world, local_rank, dist):
     import torch
     from paper_2305_07238_gb300 import build as B
@@ -176,34 +191,48 @@ def ours(args, rank, world, local_rank, dist):
     # ---- cached, device-resident inputs ---------------------------------------------
     for _ in range(args.warmup):
         run_frame(cached, dev_passes, outs, hits, None)
+    # autotune the schedule on a warm table (two passes in), then start over
+    cached.reset()
+    for p in range(2):
+        cached.eval_batch(dev_passes[p], outs, hits)
+    tune = cached.autotune(dev_passes[2], reps=3)
     cached.sync()
-    s0 = cached.stats()
     cached.read_timing()
     cached.set_timing(True)
-    with ClockSampler(local_rank) as clk:
-        secs = timed_steps(torch, cached, dev_passes, outs, hits, args.steps, barrier)
-    cached.set_timing(False)
-    timing = cached.read_timing()
-    s1 = cached.stats()
-    # the timed steps each start from an empty table, so per-step counters repeat
     pts_total = n * SPP * args.steps
+    with ClockSampler(local_rank) as clk:
+        # eager launches with per-phase events: the per-kernel times of the roofline
+        secs_eager = timed_steps(torch, cached, dev_passes, outs, hits, args.steps, barrier)
+        cached.set_timing(False)
+        timing = cached.read_timing()
+        frame_stats = cached.stats()   # reset() zeroes the counters per frame: one frame's worth
+        # the whole frame (reset + 16 passes) as one CUDA graph: the headline
+        graph = cached.graph(dev_passes, [outs] * SPP, [hits] * SPP, reset=True)
+        for _ in range(max(1, args.warmup)):
+            graph.launch()
+        cached.sync()
+        cached.read_timing()
+        secs = timed_graph(torch, graph, args.steps, barrier)
+        g_launches = cached.read_timing()["launches"]
+    graph.close()
     secs_max = secs
     if dist is not None:
         t = torch.tensor([secs], device=dev)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         secs_max = float(t.item())
     value = pts_total * world / secs_max
-    # counters: read directly after the last timed step (reset() zeroes them per frame)
-    frame_stats = s1
 
     # ---- uncached --------------------------------------------------------------------
     legs = set(args.legs.split(","))
     usecs, u_value = float("nan"), float("nan")
     if "uncached" in legs:
+        uncached.autotune(dev_passes[2], reps=3)
+        ugraph = uncached.graph(dev_passes, [outs] * SPP, [hits] * SPP, reset=True)
         for _ in range(max(1, args.warmup)):
-            run_frame(uncached, dev_passes, outs, hits, None)
+            ugraph.launch()
         uncached.sync()
-        usecs = timed_steps(torch, uncached, dev_passes, outs, hits, args.steps, barrier)
+        usecs = timed_graph(torch, ugraph, args.steps, barrier)
+        ugraph.close()
         if dist is not None:
             t = torch.tensor([usecs], device=dev)
             dist.all_reduce(t, op=dist.ReduceOp.MAX)
@@ -257,14 +286,106 @@ def ours(args, rank, world, local_rank, dist):
         "roofline": roof,
         "kernels": kernels,
         "e2e": e2e,
-        "gpu_launches": int(timing["launches"]),
+        "gpu_launches": int(g_launches),
         "clocks": clk.summary(),
+        "launch": "one CUDA graph per frame (reset + 16 passes); schedule from pmc_autotune",
+        "schedule": tune["schedule"],
+        "autotune_ms": {f"{t['flags']:#x}/rb{t['lookup_rb']}": round(t["ms"], 3) for t in tune["tried"]},
+        "eager": {"value": round(pts_total * world / secs_eager, 1), "unit": UNIT,
+                  "ms_per_step": round(secs_eager / args.steps * 1e3, 3),
+                  "gpu_launches": int(timing["launches"])},
     }
     if "surr" in legs:
         line["surrogate"] = surrogate_leg(torch, P, dev, local_rank, seed=rank)
+    if "f128" in legs:
+        line["frame128"] = frame128_leg(torch, P, dev, local_rank, seed=rank)
     if rank == 0 and not args.no_cpu_baseline and "cpu" in legs:
         line["cpu_baseline"], line["max_abs_err_vs_fp64"] = cpu_baseline(P, torch, mats, frame, dev)
     return line
+
+
+F128_MATS, F128_LO, F128_HI, F128_PASSES, F128_CELLS = 1024, 5, 2000, 128, 1 << 23
+
+
+def frame128_leg(torch, P, dev, local_rank, seed=0):
+    """1024 networks of 5-2000 nodes (20 % SP); one 1920x1080 frame rendered as 128 passes
+    of one sample per pixel against a 1 GB table (2^23 cells x 8).  Frame throughput with
+    stream launches and as one CUDA graph; grouped by material vs unsorted; the autotuned
+    schedule; the uncached frame.  Points come from the torch form of the frame generator
+    (9.6 GB resident)."""
+    from paper_2305_07238_gb300 import pmc as Pm
+    mats = W.random_materials(F128_MATS, F128_LO, F128_HI, SP_FRAC, seed=seed + 300)
+    frame = W.Frame(W.FrameSpec(width=WIDTH, height=HEIGHT, n_mats=F128_MATS, seed=seed + 300))
+    passes = [frame.points_torch(p, dev) for p in range(F128_PASSES)]
+    n = WIDTH * HEIGHT
+    # materials are fixed per tile, so every pass needs the same number of probe records
+    roots = np.array([len(P.analyze_material(m)["roots"]) for m in mats])
+    need = int(roots[frame.tile_mat[frame.pix_tile]].sum())
+    outs = torch.empty((3, n), dtype=torch.float32, device=dev)
+    hits = torch.empty(n, dtype=torch.int16, device=dev)
+    pts_frame = n * F128_PASSES
+    res = {"config": f"frame {WIDTH}x{HEIGHT}, {F128_PASSES} passes of 1 spp ({pts_frame} points), "
+                     f"{F128_MATS} materials {F128_LO}-{F128_HI} nodes ({int(SP_FRAC * 100)}% SP), Zipf 1.1, "
+                     f"table {F128_CELLS}x{N_ENTRIES} slots (1 GB), lambda {LEVEL}",
+           "unit": UNIT, "probes_per_pass": need}
+
+    def make(flags=0):
+        return P.Cache(mats, F128_CELLS, N_ENTRIES, uv_level=LEVEL, flags=flags, device=local_rank,
+                       probe_capacity=need)
+
+    def graph_rate(c, reps=2):
+        g = c.graph(passes, [outs] * F128_PASSES, [hits] * F128_PASSES, reset=True)
+        g.launch()
+        c.sync()
+        torch.cuda.synchronize()
+        t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        t0.record()
+        for _ in range(reps):
+            g.launch()
+        t1.record()
+        torch.cuda.synchronize()
+        c.sync()
+        g.close()
+        return pts_frame * reps / (t0.elapsed_time(t1) / 1e3)
+
+    c = make()
+    # stream launches, one event pair per pass: all passes and warm passes (>= 2)
+    for rep in range(2):
+        c.reset()
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(F128_PASSES + 1)]
+        ev[0].record()
+        for p in range(F128_PASSES):
+            c.eval_batch(passes[p], outs, hits)
+            ev[p + 1].record()
+        torch.cuda.synchronize()
+    per_pass = [ev[p].elapsed_time(ev[p + 1]) for p in range(F128_PASSES)]
+    st = c.stats()
+    res["eager"] = round(pts_frame / (sum(per_pass) / 1e3), 1)
+    res["eager_warm_passes"] = round(n * (F128_PASSES - 2) / (sum(per_pass[2:]) / 1e3), 1)
+    res["hit_rate"] = round(st["hits"] / max(1, st["lookups"]), 4)
+    res["graph_grouped"] = round(graph_rate(c), 1)
+    c.set_schedule(Pm.PMC_UNSORTED | Pm.PMC_EVAL_INLINE, 4)
+    res["graph_unsorted"] = round(graph_rate(c), 1)
+    c.set_schedule(0, 4)
+    c.reset()
+    for p in range(2):
+        c.eval_batch(passes[p], outs, hits)
+    tune = c.autotune(passes[2], reps=2)
+    res["autotuned_schedule"] = tune["schedule"]
+    res["graph_autotuned"] = round(graph_rate(c), 1)
+    c.close()
+    u = make(Pm.PMC_CACHE_OFF)
+    res["uncached_graph_grouped"] = round(graph_rate(u, 1), 1)
+    u.set_schedule(Pm.PMC_UNSORTED | Pm.PMC_EVAL_INLINE, 4)
+    res["uncached_graph_unsorted"] = round(graph_rate(u, 1), 1)
+    u.close()
+    best = max(res["graph_grouped"], res["graph_unsorted"], res["graph_autotuned"])
+    res["speedup_cached_over_uncached"] = round(best / max(res["uncached_graph_grouped"],
+                                                           res["uncached_graph_unsorted"]), 3)
+    res["graph_over_eager"] = round(res["graph_grouped"] / res["eager"], 3)
+    del passes
+    torch.cuda.empty_cache()
+    return res
 
 
 SURR_MATS, SURR_LO, SURR_HI, SURR_PASSES = 256, 500, 2000, 8
@@ -425,8 +546,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--legs", default="cached,uncached,e2e,surr,cpu",
-                    help="comma list of cached, uncached, e2e, surr, cpu (profiling runs take 'cached')")
+    ap.add_argument("--legs", default="cached,uncached,e2e,surr,f128,cpu",
+                    help="comma list of cached, uncached, e2e, surr, f128, cpu (profiling runs take 'cached')")
     args = ap.parse_args()
 
     world = int(os.environ.get("WORLD_SIZE", "1"))

@@ -16,8 +16,9 @@
  *   - Alg. 1: an entry is taken at the first slot whose stored hash is Hash2(desc)
  *     or 0.  This library resolves concurrent inserts deterministically: a batch
  *     looks up against the table as it was when the batch started, then inserts
- *     its misses in ascending (point index, node ID) order, which it realises with
- *     rounds of atomicMin on a per-cell claim word.
+ *     its misses in ascending (point index, node ID) order, which it realises by
+ *     grouping the candidates by cell (default) or with rounds of atomicMin on a
+ *     per-cell claim word (PMC_INSERT_ROUNDS).
  *
  * Conventions for every entry point:
  *   - All pointers to shading points and outputs are DEVICE pointers owned by the
@@ -114,8 +115,8 @@ typedef struct {
 
 /* ---- cache description (Sec. 3.2, Fig. 3, Alg. 1 inputs N_c and N_e) --------- */
 #define PMC_CACHE_OFF 0x1u        /* evaluate every node, no lookups, no inserts   */
-#define PMC_SORT_BY_MATERIAL 0x2u /* accepted; shading points are always grouped
-                                     by material inside the library               */
+#define PMC_SORT_BY_MATERIAL 0x2u /* accepted; grouping shading points by material
+                                     is the default (see PMC_UNSORTED)             */
 #define PMC_DEBUG_CHECKS 0x4u     /* extra device-side bounds checks               */
 #define PMC_EVAL_INLINE 0x8u      /* evaluate missed cacheable nodes inside the
                                      per-point program (lanes that hit wait) instead of
@@ -123,15 +124,24 @@ typedef struct {
 #define PMC_INSERT_ROUNDS 0x10u   /* resolve inserts by rounds of atomicMin on a claim
                                      word per cell instead of grouping the candidates
                                      by cell (same table either way)                   */
+#define PMC_UNSORTED 0x20u        /* no grouping by material: a warp evaluates 32
+                                     consecutive points, one material at a time, and
+                                     probes the table inline (same results; not
+                                     combinable with learned surrogates)               */
 
 typedef struct {
     uint64_t n_cells;        /* N_c >= 1, < 2^32                                  */
     uint32_t n_entries;      /* N_e, 1 .. 32; a slot is 16 bytes {hash2, r, g, b} */
     uint32_t uv_level;       /* lambda of Eq. 1: 2^lambda texels per axis, 0 .. 13 */
-    uint32_t flags;          /* PMC_CACHE_OFF | PMC_DEBUG_CHECKS                   */
+    uint32_t flags;          /* PMC_* flags above                                  */
     uint32_t min_root_nodes; /* a cacheable node's sub-graph must hold at least this
                                 many non-input nodes (0 is read as 2)              */
     int device;              /* CUDA device ordinal                                */
+    uint64_t probe_capacity; /* (point, cacheable node) probes per batch that the
+                                scratch is sized for; 0 = n times the largest number
+                                of cacheable nodes of any material.  A batch that
+                                needs more does no work and the next pmc_sync /
+                                pmc_stats returns PMC_ERR_UNSUPPORTED            */
 } pmc_cache_desc;
 
 /* ---- shading points: structure of arrays, n entries each, DEVICE memory ----- */
@@ -346,6 +356,58 @@ pmc_status pmc_mlp_train(float* theta, float* adam_m, float* adam_v, const float
 #define PMC_NOALLOC_SCRATCH_BYTES 3522816u
 pmc_status pmc_eval_batch_noalloc(pmc_cache* cache, const pmc_points* pts, float* out_rgb,
                                   uint16_t* out_hits, void* stream);
+
+/* ---- schedule, graphs of passes, autotuning -------------------------------------
+ * None of these change results: every schedule produces the same outputs, hit counts,
+ * counters and table, bit for bit. */
+typedef struct {
+    uint32_t flags;     /* subset of PMC_EVAL_INLINE | PMC_INSERT_ROUNDS | PMC_UNSORTED  */
+    uint32_t lookup_rb; /* probes in flight per lane in the lookup kernel: 1, 2 or 4    */
+} pmc_schedule;
+
+/* Reads / replaces the schedule of later passes.  pmc_set_schedule returns
+ * PMC_ERR_UNSUPPORTED for PMC_UNSORTED while learned surrogates are in use and for a
+ * batched evaluation of misses (no PMC_EVAL_INLINE) of networks whose cacheable nodes
+ * nest deeper than this build handles (it then keeps PMC_EVAL_INLINE). */
+pmc_status pmc_get_schedule(const pmc_cache* cache, pmc_schedule* out);
+pmc_status pmc_set_schedule(pmc_cache* cache, const pmc_schedule* sched);
+
+/* A CUDA graph of whole passes: the launches of n_passes consecutive pmc_eval_batch
+ * calls (passes[k] -> out_rgb[k], out_hits[k]; out_hits may be NULL, or any entry of
+ * it), preceded by pmc_reset if flags has PMC_GRAPH_RESET, recorded once by stream
+ * capture and replayed by pmc_graph_launch with one launch call.  Nothing runs at
+ * creation.  The points and outputs are bound by address: a replay reads whatever
+ * the caller's buffers hold then.  A replay is the same work as the calls it
+ * recorded: without PMC_GRAPH_RESET every pass looks up the table as it stands.
+ * A graph holds the cache's scratch addresses: scratch growth (a larger batch), a
+ * schedule change, or a change to learned surrogates makes it stale, and
+ * pmc_graph_launch then returns PMC_ERR_INVALID_ARG without launching.  Graphs must
+ * be destroyed before their cache. */
+typedef struct pmc_graph pmc_graph;
+#define PMC_GRAPH_RESET 0x1u
+pmc_status pmc_graph_create(pmc_cache* cache, const pmc_points* passes, uint32_t n_passes,
+                            float* const* out_rgb, uint16_t* const* out_hits, uint32_t flags,
+                            pmc_graph** out);
+/* Enqueues one replay on `stream` (asynchronous). */
+pmc_status pmc_graph_launch(pmc_graph* graph, void* stream);
+void pmc_graph_destroy(pmc_graph* graph);
+
+/* Times the candidate schedules on one batch (DEVICE points, as pmc_eval_batch) and
+ * keeps the fastest.  Each candidate runs `reps` times (1 .. 16) from the same table
+ * state; the table, counters and hit history are restored afterwards, so the call
+ * leaves the cache as it found it except for the schedule.  Tune on a table that has
+ * seen a few passes: on an empty table every schedule takes the empty-table path.
+ * Synchronous.  Allocates temporary device memory (a copy of the table and outputs).
+ * out (host, may be NULL): per candidate its schedule and best time. */
+#define PMC_TUNE_MAX 16
+typedef struct {
+    uint32_t n_tried;
+    uint32_t best;                        /* index into tried[] of the kept schedule */
+    pmc_schedule tried[PMC_TUNE_MAX];
+    float ms[PMC_TUNE_MAX];
+} pmc_tune_result;
+pmc_status pmc_autotune(pmc_cache* cache, const pmc_points* sample, uint32_t reps,
+                        pmc_tune_result* out);
 
 /* Human-readable name of a status code (static storage). */
 const char* pmc_status_str(pmc_status s);

@@ -21,6 +21,9 @@ struct pmc_cache {
     std::vector<pmc::RootInfo> root_info;
     uint32_t max_level = 0;
     int split = 1;
+    int unsorted = 0;                     // PMC_UNSORTED schedule
+    uint32_t lookup_rb = 4;               // probes in flight per lane in k_lookup
+    uint64_t layout_gen = 1;              // bumped whenever a recorded graph would go stale
     uint32_t prog_len = 0;
     // device-resident, owned
     MatInfo* d_mats = nullptr;
@@ -37,6 +40,7 @@ struct pmc_cache {
     uint32_t n_bins = 0;                  // cell-grouped insert bins
     bool table_empty = true;              // nothing inserted since creation or reset
     bool last_all_miss = false;           // the last batch ran on an empty table
+    bool last_unsorted = false;           // the last batch kept no probe records
     // learned surrogates
     int use_surrogates = 1;
     std::vector<int32_t> surr_cand;       // per material: candidate node ordinal, -1 if none

@@ -68,9 +68,11 @@ bool surrogates_active(const pmc_cache* c) { return c->use_surrogates && c->any_
 
 pmc_status ensure_scratch(pmc_cache* c, uint64_t n) {
     uint64_t need_probes = (c->use_cache || surrogates_active(c)) ? n * (uint64_t)c->max_roots : 0;
+    if (c->desc.probe_capacity) need_probes = std::min<uint64_t>(need_probes, c->desc.probe_capacity);
     if (c->d_seg && n <= c->cap_points && need_probes <= c->cap_probes) return PMC_OK;
     if (c->last_stream || c->d_seg) cudaDeviceSynchronize();
     free_scratch(c);
+    c->layout_gen++;
     uint64_t cap = n > 0 ? n : 1;
     uint64_t pcap = need_probes > 0 ? need_probes : 1;
     if (pcap > 0xFFFFFFFFull) return PMC_ERR_UNSUPPORTED;
@@ -99,6 +101,11 @@ pmc_status fold_device_errors(pmc_cache* c) {
     if (err & ERR_TIMEOUT) {
         fprintf(stderr, "pmc: a bounded device wait ran out\n");
         return PMC_ERR_TIMEOUT;
+    }
+    if (err & ERR_CAPACITY) {
+        fprintf(stderr, "pmc: a batch needed more probe records than pmc_cache_desc.probe_capacity; "
+                        "its outputs are not valid\n");
+        return PMC_ERR_UNSUPPORTED;
     }
     if (err & (ERR_INSERT | ERR_BOUNDS)) {
         fprintf(stderr, "pmc: internal device check failed (flags %u)\n", err);
@@ -174,6 +181,7 @@ pmc_status pmc_create_cache(const pmc_cache_desc* desc, const pmc_material* mats
     c->desc.min_root_nodes = min_root;
     c->use_cache = off ? 0 : 1;
     c->split = (desc->flags & PMC_EVAL_INLINE) ? 0 : 1;
+    c->unsorted = (desc->flags & PMC_UNSORTED) ? 1 : 0;
     c->n_mats = n_mats;
 
     std::vector<uint4> prog;
@@ -291,18 +299,26 @@ pmc_status pmc_create_cache(const pmc_cache_desc* desc, const pmc_material* mats
     return PMC_OK;
 }
 
-pmc_status pmc_eval_batch(pmc_cache* c, const pmc_points* pts, float* out_rgb, uint16_t* out_hits,
-                          void* stream) {
-    if (!c || !pts) return PMC_ERR_INVALID_ARG;
-    if (c->sticky != PMC_OK) return c->sticky;
+namespace {
+
+// Inputs of a pass: n below the limit and, when n > 0, every plane (and the output if
+// `need_out`) present.
+pmc_status check_points(const pmc_points* pts, const float* out_rgb, bool need_out = true) {
+    if (!pts) return PMC_ERR_INVALID_ARG;
     const uint64_t n = pts->n;
     if (n >= MAX_POINTS) return PMC_ERR_UNSUPPORTED;
     if (n > 0 && (!pts->u || !pts->v || !pts->mat || !pts->px || !pts->py || !pts->pz || !pts->nx ||
-                  !pts->ny || !pts->nz || !out_rgb))
+                  !pts->ny || !pts->nz || (need_out && !out_rgb)))
         return PMC_ERR_INVALID_ARG;
-    DeviceGuard g(c->desc.device);
-    if (!g.ok) return PMC_ERR_INVALID_ARG;
-    cudaStream_t s = (cudaStream_t)stream;
+    return PMC_OK;
+}
+
+// Enqueues one pass.  `recording`: inside a stream capture (no timing events, no
+// scratch growth: the caller sized the scratch before the capture began).
+pmc_status enqueue_batch(pmc_cache* c, const pmc_points* pts, float* out_rgb, uint16_t* out_hits,
+                         cudaStream_t s, bool recording) {
+    const uint64_t n = pts->n;
+    if (c->unsorted && surrogates_active(c)) return PMC_ERR_UNSUPPORTED;
     pmc_status st = ensure_scratch(c, n);
     if (st != PMC_OK) return st;
     const uint32_t ne = c->desc.n_entries;
@@ -351,8 +367,10 @@ pmc_status pmc_eval_batch(pmc_cache* c, const pmc_points* pts, float* out_rgb, u
     }
     a.rinfo = c->d_rinfo; a.n_roots_total = (uint32_t)c->root_info.size(); a.max_level = c->max_level;
     a.miss_cnt = c->d_miss_cnt; a.root_item_base = c->d_root_items; a.misslist = c->d_misslist;
+    a.unsorted = c->unsorted;
+    a.lookup_rb = c->lookup_rb;
     cudaEvent_t* ev = nullptr;
-    if (c->timing) {
+    if (c->timing && !recording) {
         while (c->events.size() < c->events_used + PH_COUNT + 1) {
             cudaEvent_t x;
             cudaError_t ce = cudaEventCreate(&x);
@@ -367,10 +385,24 @@ pmc_status pmc_eval_batch(pmc_cache* c, const pmc_points* pts, float* out_rgb, u
     if (e != cudaSuccess) return cuda_fail(c, e);
     if (c->use_cache) c->epoch_host += ne + 1;
     c->last_all_miss = a.keys_inline != 0;
+    c->last_unsorted = a.unsorted != 0;
     if (n > 0) c->table_empty = false;
     c->last_stream = s;
     c->last_n = n;
     return PMC_OK;
+}
+
+}  // namespace
+
+pmc_status pmc_eval_batch(pmc_cache* c, const pmc_points* pts, float* out_rgb, uint16_t* out_hits,
+                          void* stream) {
+    if (!c || !pts) return PMC_ERR_INVALID_ARG;
+    if (c->sticky != PMC_OK) return c->sticky;
+    pmc_status st = check_points(pts, out_rgb);
+    if (st != PMC_OK) return st;
+    DeviceGuard g(c->desc.device);
+    if (!g.ok) return PMC_ERR_INVALID_ARG;
+    return enqueue_batch(c, pts, out_rgb, out_hits, (cudaStream_t)stream, false);
 }
 
 pmc_status pmc_eval_batch_host(pmc_cache* c, const pmc_points* hp, float* host_rgb, uint16_t* host_hits,
@@ -487,6 +519,7 @@ pmc_status pmc_last_hit_masks(pmc_cache* c, uint64_t* host_dst, uint64_t n) {
     if (st == PMC_ERR_CUDA) return st;
     std::memset(host_dst, 0, n * sizeof(uint64_t));
     if (!c->use_cache || n == 0 || c->last_all_miss) return st;   // an empty table: no hits
+    if (c->last_unsorted) return PMC_ERR_UNSUPPORTED;              // no probe records kept
     DeviceGuard g(c->desc.device);
     const size_t M1 = (size_t)c->n_mats + 1;
     std::vector<uint32_t> seg(5 * M1);
@@ -605,12 +638,14 @@ pmc_status grow_surrogate_slots(pmc_cache* c, uint32_t need) {
     dfree(&c->d_surr_theta);
     c->d_surr_theta = nt;
     c->cap_surr_slots = cap;
+    c->layout_gen++;
     return PMC_OK;
 }
 
 cudaError_t upload_surrogate_maps(pmc_cache* c) {
     std::vector<int32_t> slot(c->n_mats, -1), ord(c->n_mats, -1);
     c->any_surr_on = false;
+    c->layout_gen++;
     for (uint32_t m = 0; m < c->n_mats; ++m) {
         if (c->surr_on[m] && c->surr_slot[m] >= 0 && c->surr_cand[m] >= 0) {
             slot[m] = c->surr_slot[m];
@@ -792,6 +827,7 @@ pmc_status pmc_get_surrogate(pmc_cache* c, uint32_t mat, float* theta, uint32_t*
 
 pmc_status pmc_use_surrogates(pmc_cache* c, int enable) {
     if (!c) return PMC_ERR_INVALID_ARG;
+    if ((enable != 0) != (c->use_surrogates != 0)) c->layout_gen++;
     c->use_surrogates = enable != 0;
     return PMC_OK;
 }
@@ -837,6 +873,269 @@ pmc_status pmc_compute_keys(const uint32_t* mat, const uint32_t* node, const flo
     if (n && (!mat || !node || !u || !v || !key || !cell || !h2)) return PMC_ERR_INVALID_ARG;
     cudaError_t e = launch_keys(mat, node, u, v, n, level, n_cells, key, cell, h2, (cudaStream_t)stream);
     if (e != cudaSuccess) return cuda_fail(nullptr, e);
+    return PMC_OK;
+}
+
+// ---- schedule, graphs of passes, autotuning ----------------------------------------
+pmc_status pmc_get_schedule(const pmc_cache* c, pmc_schedule* out) {
+    if (!c || !out) return PMC_ERR_INVALID_ARG;
+    out->flags = (c->split ? 0u : PMC_EVAL_INLINE) | ((c->desc.flags & PMC_INSERT_ROUNDS) ? PMC_INSERT_ROUNDS : 0u) |
+                 (c->unsorted ? PMC_UNSORTED : 0u);
+    out->lookup_rb = c->lookup_rb;
+    return PMC_OK;
+}
+
+pmc_status pmc_set_schedule(pmc_cache* c, const pmc_schedule* sc) {
+    if (!c || !sc) return PMC_ERR_INVALID_ARG;
+    const uint32_t known = PMC_EVAL_INLINE | PMC_INSERT_ROUNDS | PMC_UNSORTED;
+    if (sc->flags & ~known) return PMC_ERR_INVALID_ARG;
+    if (sc->lookup_rb != 1 && sc->lookup_rb != 2 && sc->lookup_rb != 4) return PMC_ERR_INVALID_ARG;
+    if ((sc->flags & PMC_UNSORTED) && surrogates_active(c)) return PMC_ERR_UNSUPPORTED;
+    if (!(sc->flags & PMC_EVAL_INLINE) && c->max_level >= MAX_LEVELS) return PMC_ERR_UNSUPPORTED;
+    c->split = (sc->flags & PMC_EVAL_INLINE) ? 0 : 1;
+    c->unsorted = (sc->flags & PMC_UNSORTED) ? 1 : 0;
+    c->lookup_rb = sc->lookup_rb;
+    c->desc.flags = (c->desc.flags & ~PMC_INSERT_ROUNDS) | (sc->flags & PMC_INSERT_ROUNDS);
+    c->layout_gen++;
+    return PMC_OK;
+}
+
+}  // extern "C"
+
+struct pmc_graph {
+    pmc_cache* c = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    uint64_t gen = 0;
+    int surr = 0;
+    // host-side state of the cache after a replay
+    bool table_empty = false, last_all_miss = false, last_unsorted = false;
+    uint32_t epoch = 0;
+    uint64_t launches = 0, last_n = 0;
+};
+
+extern "C" {
+
+pmc_status pmc_graph_create(pmc_cache* c, const pmc_points* passes, uint32_t n_passes, float* const* out_rgb,
+                            uint16_t* const* out_hits, uint32_t flags, pmc_graph** out) {
+    if (!c || !out || (n_passes && (!passes || !out_rgb)) || (flags & ~PMC_GRAPH_RESET)) return PMC_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (c->sticky != PMC_OK) return c->sticky;
+    uint64_t max_n = 0;
+    for (uint32_t k = 0; k < n_passes; ++k) {
+        pmc_status st = check_points(&passes[k], out_rgb[k]);
+        if (st != PMC_OK) return st;
+        max_n = std::max<uint64_t>(max_n, passes[k].n);
+    }
+    const uint32_t ne = c->desc.n_entries;
+    const bool rounds = c->use_cache && (c->desc.flags & PMC_INSERT_ROUNDS);
+    // a replay restarts the claim epochs, so they only have to last n_passes batches
+    if (rounds && (uint64_t)(n_passes + 2) * (ne + 1) > EPOCH_MAX) return PMC_ERR_UNSUPPORTED;
+    if (c->unsorted && surrogates_active(c)) return PMC_ERR_UNSUPPORTED;
+    DeviceGuard g(c->desc.device);
+    if (!g.ok) return PMC_ERR_INVALID_ARG;
+    pmc_status st = ensure_scratch(c, max_n);   // no allocation inside the capture
+    if (st != PMC_OK) return st;
+    pmc_graph* gr = new (std::nothrow) pmc_graph();
+    if (!gr) return PMC_ERR_OOM;
+    // the capture runs nothing; the cache's host-side state is put back afterwards
+    const bool s_empty = c->table_empty, s_all_miss = c->last_all_miss, s_unsorted = c->last_unsorted;
+    const uint32_t s_epoch = c->epoch_host;
+    const uint64_t s_launches = c->launches, s_last_n = c->last_n;
+    cudaStream_t last = c->last_stream;
+    cudaStream_t s = nullptr;
+    cudaError_t e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+    if (e != cudaSuccess) { delete gr; return cuda_fail(c, e); }
+    e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
+    pmc_status rec = PMC_OK;
+    if (e == cudaSuccess) {
+        const uint64_t slots = c->use_cache ? c->desc.n_cells * ne : 0;
+        const uint64_t cells = c->use_cache ? c->desc.n_cells : 0;
+        if (flags & PMC_GRAPH_RESET) {
+            e = launch_reset(c->d_table, slots, c->d_claims, cells, c->d_ctl, c->d_stats, s, rounds);
+            c->table_empty = true;
+        } else {
+            c->table_empty = false;   // the table's contents at replay time are unknown
+            if (rounds) {
+                e = cudaMemsetAsync(c->d_claims, 0xFF, cells * sizeof(unsigned long long), s);
+                if (e == cudaSuccess) e = cudaMemsetAsync(&c->d_ctl->epoch, 0, sizeof(uint32_t), s);
+            }
+        }
+        c->epoch_host = 0;
+        c->launches = 0;
+        for (uint32_t k = 0; k < n_passes && e == cudaSuccess && rec == PMC_OK; ++k)
+            rec = enqueue_batch(c, &passes[k], out_rgb[k], out_hits ? out_hits[k] : nullptr, s, true);
+        cudaGraph_t graph = nullptr;
+        cudaError_t e2 = cudaStreamEndCapture(s, &graph);
+        if (e == cudaSuccess) e = e2;
+        gr->graph = graph;
+    }
+    gr->table_empty = c->table_empty;
+    gr->last_all_miss = c->last_all_miss;
+    gr->last_unsorted = c->last_unsorted;
+    gr->epoch = c->epoch_host;
+    gr->launches = c->launches;
+    gr->last_n = n_passes ? passes[n_passes - 1].n : c->last_n;
+    c->table_empty = s_empty; c->last_all_miss = s_all_miss; c->last_unsorted = s_unsorted;
+    c->epoch_host = s_epoch; c->launches = s_launches; c->last_n = s_last_n; c->last_stream = last;
+    if (rec == PMC_ERR_CUDA) c->sticky = PMC_OK;   // a failed capture poisons nothing that ran
+    if (e == cudaSuccess && rec == PMC_OK) e = cudaGraphInstantiate(&gr->exec, gr->graph, 0);
+    cudaStreamDestroy(s);
+    if (e != cudaSuccess || rec != PMC_OK) {
+        if (gr->exec) cudaGraphExecDestroy(gr->exec);
+        if (gr->graph) cudaGraphDestroy(gr->graph);
+        delete gr;
+        cudaGetLastError();
+        if (rec != PMC_OK) return rec;
+        fprintf(stderr, "pmc: graph capture failed: %s\n", cudaGetErrorString(e));
+        return PMC_ERR_CUDA;
+    }
+    gr->c = c;
+    gr->gen = c->layout_gen;
+    gr->surr = surrogates_active(c) ? 1 : 0;
+    *out = gr;
+    return PMC_OK;
+}
+
+pmc_status pmc_graph_launch(pmc_graph* gr, void* stream) {
+    if (!gr || !gr->c) return PMC_ERR_INVALID_ARG;
+    pmc_cache* c = gr->c;
+    if (c->sticky != PMC_OK) return c->sticky;
+    if (gr->gen != c->layout_gen || gr->surr != (surrogates_active(c) ? 1 : 0)) {
+        fprintf(stderr, "pmc: graph is stale (scratch, schedule or surrogates changed since it was recorded)\n");
+        return PMC_ERR_INVALID_ARG;
+    }
+    DeviceGuard g(c->desc.device);
+    if (!g.ok) return PMC_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t e = cudaGraphLaunch(gr->exec, s);
+    if (e != cudaSuccess) return cuda_fail(c, e);
+    c->table_empty = gr->table_empty;
+    c->last_all_miss = gr->last_all_miss;
+    c->last_unsorted = gr->last_unsorted;
+    c->epoch_host = gr->epoch;
+    c->launches += gr->launches;
+    c->last_n = gr->last_n;
+    c->last_stream = s;
+    return PMC_OK;
+}
+
+void pmc_graph_destroy(pmc_graph* gr) {
+    if (!gr) return;
+    if (gr->exec) cudaGraphExecDestroy(gr->exec);
+    if (gr->graph) cudaGraphDestroy(gr->graph);
+    delete gr;
+}
+
+pmc_status pmc_autotune(pmc_cache* c, const pmc_points* sample, uint32_t reps, pmc_tune_result* out) {
+    if (!c || !sample || reps == 0 || reps > 16) return PMC_ERR_INVALID_ARG;
+    if (c->sticky != PMC_OK) return c->sticky;
+    pmc_status st = check_points(sample, nullptr, false);
+    if (st != PMC_OK) return st;
+    st = pmc_sync(c);
+    if (st != PMC_OK) return st;
+    DeviceGuard g(c->desc.device);
+    if (!g.ok) return PMC_ERR_INVALID_ARG;
+    const uint64_t n = sample->n;
+    if ((st = ensure_scratch(c, n)) != PMC_OK) return st;
+    // candidates: grouped with batched misses at 4/2/1 probes in flight, grouped with
+    // inline misses, unsorted inline probing, and the claim-round insert
+    pmc_schedule orig;
+    pmc_get_schedule(c, &orig);
+    const uint32_t keep = orig.flags & PMC_INSERT_ROUNDS;
+    std::vector<pmc_schedule> cand;
+    if (c->max_level < MAX_LEVELS) {
+        cand.push_back({keep, 4});
+        if (c->use_cache) {
+            cand.push_back({keep, 2});
+            cand.push_back({keep, 1});
+        }
+    }
+    if (c->use_cache) cand.push_back({keep | PMC_EVAL_INLINE, 4});
+    if (!surrogates_active(c)) cand.push_back({keep | PMC_EVAL_INLINE | PMC_UNSORTED, 4});
+    if (c->use_cache && c->max_level < MAX_LEVELS) cand.push_back({keep ^ PMC_INSERT_ROUNDS, 4});
+    if (cand.empty()) cand.push_back(orig);
+    if (cand.size() > PMC_TUNE_MAX) cand.resize(PMC_TUNE_MAX);
+
+    const uint64_t slots = c->use_cache ? c->desc.n_cells * c->desc.n_entries : 0;
+    const size_t table_bytes = slots ? (size_t)(slots + 16) * sizeof(uint4) : 0;
+    uint4* saved = nullptr;
+    float* rgb = nullptr;
+    uint16_t* hits = nullptr;
+    unsigned long long stats[ST_COUNT];
+    if (table_bytes && (st = dalloc(&saved, slots + 16)) != PMC_OK) return st;
+    if ((st = dalloc(&rgb, 3 * (size_t)std::max<uint64_t>(n, 1))) != PMC_OK) { dfree(&saved); return st; }
+    if ((st = dalloc(&hits, (size_t)std::max<uint64_t>(n, 1))) != PMC_OK) { dfree(&saved); dfree(&rgb); return st; }
+    cudaStream_t s = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaError_t e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    if (e == cudaSuccess && table_bytes) e = cudaMemcpy(saved, c->d_table, table_bytes, cudaMemcpyDeviceToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(stats, c->d_stats, sizeof(stats), cudaMemcpyDeviceToHost);
+    const bool s_empty = c->table_empty, s_all_miss = c->last_all_miss, s_unsorted = c->last_unsorted;
+    const bool s_timing = c->timing;
+    const uint64_t s_last_n = c->last_n, s_launches = c->launches;
+    cudaStream_t s_last = c->last_stream;
+    c->timing = false;
+    const uint64_t cells = c->use_cache ? c->desc.n_cells : 0;
+    auto restore = [&]() -> cudaError_t {
+        cudaError_t r = cudaSuccess;
+        if (table_bytes) r = cudaMemcpyAsync(c->d_table, saved, table_bytes, cudaMemcpyDeviceToDevice, s);
+        if (r == cudaSuccess && cells) r = cudaMemsetAsync(c->d_claims, 0xFF, cells * sizeof(unsigned long long), s);
+        if (r == cudaSuccess) r = cudaMemsetAsync(&c->d_ctl->epoch, 0, sizeof(uint32_t), s);
+        c->epoch_host = 0;
+        c->table_empty = s_empty;
+        return r;
+    };
+    std::vector<float> best_ms(cand.size(), 0.0f);
+    for (size_t k = 0; k < cand.size() && e == cudaSuccess && st == PMC_OK; ++k) {
+        if ((st = pmc_set_schedule(c, &cand[k])) != PMC_OK) break;
+        float bm = 0.0f;
+        for (uint32_t r = 0; r < reps && e == cudaSuccess && st == PMC_OK; ++r) {
+            if ((e = restore()) != cudaSuccess) break;
+            if ((e = cudaEventRecord(e0, s)) != cudaSuccess) break;
+            if ((st = enqueue_batch(c, sample, rgb, hits, s, false)) != PMC_OK) break;
+            if ((e = cudaEventRecord(e1, s)) != cudaSuccess) break;
+            if ((e = cudaEventSynchronize(e1)) != cudaSuccess) break;
+            float ms = 0.0f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (r == 0 || ms < bm) bm = ms;
+        }
+        best_ms[k] = bm;
+    }
+    if (e == cudaSuccess && st == PMC_OK) st = fold_device_errors(c);
+    // put the table, counters and history back, keep the fastest schedule
+    size_t best = 0;
+    for (size_t k = 1; k < cand.size(); ++k)
+        if (best_ms[k] < best_ms[best]) best = k;
+    if (e == cudaSuccess) e = restore();
+    if (e == cudaSuccess) e = cudaMemcpyAsync(c->d_stats, stats, sizeof(stats), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    c->last_all_miss = s_all_miss;
+    c->last_unsorted = s_unsorted;
+    c->last_n = s_last_n;
+    c->launches = s_launches;
+    c->last_stream = s_last;
+    c->timing = s_timing;
+    pmc_set_schedule(c, st == PMC_OK && e == cudaSuccess ? &cand[best] : &orig);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (s) cudaStreamDestroy(s);
+    dfree(&saved);
+    dfree(&rgb);
+    dfree(&hits);
+    if (e != cudaSuccess) return cuda_fail(c, e);
+    if (st != PMC_OK) return st;
+    if (out) {
+        std::memset(out, 0, sizeof(*out));
+        out->n_tried = (uint32_t)cand.size();
+        out->best = (uint32_t)best;
+        for (size_t k = 0; k < cand.size(); ++k) {
+            out->tried[k] = cand[k];
+            out->ms[k] = best_ms[k];
+        }
+    }
     return PMC_OK;
 }
 

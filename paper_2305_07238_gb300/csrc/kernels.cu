@@ -162,7 +162,13 @@ __global__ void k_scan(BatchArgs a) {
         a.ctl->n_surr_items = surr ? s_tot[3][t] : 0u;
         a.ctl->n_items = s_tot[2][t];
         a.ctl->total_probes = s_tot[1][t];
-        if (s_tot[1][t] > a.probe_cap) atomicOr(&a.ctl->err, ERR_BOUNDS);
+        if (s_tot[1][t] > a.probe_cap) {
+            // more probe records than the scratch holds: the batch does no work and the
+            // next synchronising call reports it
+            a.ctl->n_items = 0;
+            a.ctl->n_surr_items = 0;
+            atomicOr(&a.ctl->err, ERR_CAPACITY);
+        }
         atomicAdd(&a.stats[ST_POINTS], (unsigned long long)a.n);
     }
 }
@@ -393,7 +399,7 @@ __device__ __forceinline__ void offer(const BatchArgs& a, bool act, uint32_t ori
         c.b = b;
         c.target = start | (shadows << 16);
         if (idx < a.probe_cap) a.cands[idx] = c;
-        else atomicOr(&a.ctl->err, ERR_BOUNDS);
+        else atomicOr(&a.ctl->err, ERR_CAPACITY);
     }
 }
 
@@ -439,8 +445,12 @@ __global__ void __launch_bounds__(EVAL_WARPS * 32) k_eval(BatchArgs a, uint32_t*
             iu = d_texel(pt.u, a.level);
             iv = d_texel(pt.v, a.level);
         }
-        for (int pc = 0; pc < (int)mi.prog_len; ++pc) {
-            const uint4 ins = __ldg(&prog[pc]);
+        // the next instruction is fetched while the current one executes
+        const int len = (int)mi.prog_len;
+        uint4 nxt = len > 0 ? __ldg(&prog[0]) : make_uint4(0, 0, 0, 0);
+        for (int pc = 0; pc < len; ++pc) {
+            const uint4 ins = nxt;
+            if (pc + 1 < len) nxt = __ldg(&prog[pc + 1]);
             const uint32_t op = ins.x & 0xFFu;
             if (op == OP_ROOT_BEGIN) {
                 const uint32_t slot = ins.y & 0xFFFFu, r = ins.y >> 16;
@@ -485,7 +495,10 @@ __global__ void __launch_bounds__(EVAL_WARPS * 32) k_eval(BatchArgs a, uint32_t*
                     }
                 }
                 if (!need) skip_end = pc + (int)ins.w;
-                if (__all_sync(FULL_MASK, !need)) pc += (int)ins.w;
+                if (__all_sync(FULL_MASK, !need)) {
+                    pc += (int)ins.w;
+                    if (pc + 1 < len) nxt = __ldg(&prog[pc + 1]);
+                }
                 continue;
             }
             const bool act = valid && pc > skip_end;
@@ -516,6 +529,144 @@ __global__ void __launch_bounds__(EVAL_WARPS * 32) k_eval(BatchArgs a, uint32_t*
         warp_add_u64(&a.stats[ST_MISSES], n_look);
         warp_add_u64(&a.stats[ST_SLOTS], n_look);   // one (empty) slot examined per probe
     }
+}
+
+// Scans cell `cell` for h2 (Alg. 1's entry loop read as a lookup): the first slot that
+// holds h2 (hit) or 0 (miss), -1 if every slot holds another hash (full).
+__device__ __forceinline__ int probe_cell(const BatchArgs& a, uint32_t cell, uint32_t h2, bool* hit) {
+    const uint4* hw = reinterpret_cast<const uint4*>(cell_h2(a, cell));
+    const uint32_t ne = a.n_entries;
+    *hit = false;
+    for (uint32_t q = 0; 4u * q < ne; q += 2) {
+        // two 16-byte words per step; words past N_e are never compared
+        const uint4 w0 = __ldg(hw + q);
+        const uint4 w1 = 4u * (q + 1) < ne ? __ldg(hw + q + 1) : make_uint4(0, 0, 0, 0);
+        const uint32_t v[8] = {w0.x, w0.y, w0.z, w0.w, w1.x, w1.y, w1.z, w1.w};
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            const uint32_t idx = 4u * q + k;
+            if (idx < ne && (v[k] == h2 || v[k] == 0u)) {
+                *hit = v[k] == h2;
+                return (int)idx;
+            }
+        }
+    }
+    return -1;
+}
+
+// Unsorted evaluation: the in-shader form of Sec. 3.  A warp takes 32 consecutive
+// shading points in batch order, runs each distinct material among them in turn (the
+// other lanes idle) and probes the table when it reaches a cacheable node: a hit skips
+// the node's block, a miss evaluates it and offers the value.  No grouping pass, no
+// probe records; the table is read-only until the insert phase, so every probe sees the
+// snapshot left by the previous batch, as in the grouped pipeline.
+__global__ void __launch_bounds__(EVAL_WARPS * 32) k_eval_fused(BatchArgs a) {
+    extern __shared__ float s_val[];
+    __shared__ float2 s_grad[8];
+    init_gradients(s_grad);
+    __syncthreads();
+    const uint32_t warp = threadIdx.x >> 5, lane = lane_id();
+    float* V = s_val + (size_t)warp * a.max_slots * 96u + lane;
+    const uint32_t n_chunks = (a.n + 31u) >> 5;
+    const uint32_t ne = a.n_entries;
+    unsigned long long n_nodes = 0, n_flops = 0, n_cand = 0, n_full = 0;
+    unsigned long long n_look = 0, n_hit = 0, n_slots = 0, n_bad = 0;
+    for (uint32_t chunk = blockIdx.x * EVAL_WARPS + warp; chunk < n_chunks; chunk += gridDim.x * EVAL_WARPS) {
+        const uint32_t i = chunk * 32u + lane;
+        const bool in = i < a.n;
+        const uint32_t m = in ? a.mat[i] : 0u;
+        const bool ok = in && m < a.n_mats;
+        if (in && !ok) {
+            zero_output(a, i);
+            n_bad++;
+        }
+        PointIn pt{0, 0, 0, 0, 0, 0, 0, 0};
+        uint32_t iu = 0, iv = 0;
+        if (ok) {
+            pt.u = a.u[i]; pt.v = a.v[i];
+            pt.px = a.px[i]; pt.py = a.py[i]; pt.pz = a.pz[i];
+            pt.nx = a.nx[i]; pt.ny = a.ny[i]; pt.nz = a.nz[i];
+            iu = d_texel(pt.u, a.level);
+            iv = d_texel(pt.v, a.level);
+        }
+        unsigned todo = __ballot_sync(FULL_MASK, ok);
+        while (todo) {
+            const uint32_t mg = __shfl_sync(FULL_MASK, m, __ffs(todo) - 1);
+            const unsigned grp = __ballot_sync(FULL_MASK, ok && m == mg);
+            todo &= ~grp;
+            const bool mine = (grp >> lane) & 1u;
+            const MatInfo mi = a.mats[mg];
+            const uint4* prog = a.prog + mi.prog_start;
+            int skip_end = -1;
+            uint32_t hits = 0, cand_cell = 0, cand_h2 = 0, cand_node = 0, cand_start = 0;
+            bool cand_full = false;
+            const int len = (int)mi.prog_len;
+            uint4 nxt = len > 0 ? __ldg(&prog[0]) : make_uint4(0, 0, 0, 0);
+            for (int pc = 0; pc < len; ++pc) {
+                const uint4 ins = nxt;
+                if (pc + 1 < len) nxt = __ldg(&prog[pc + 1]);
+                const uint32_t op = ins.x & 0xFFu;
+                if (op == OP_ROOT_BEGIN) {
+                    bool need = mine;
+                    if (a.use_cache && mine) {
+                        d_address(d_key(mg, ins.z, a.level, iu, iv), a.n_cells, a.cells_pow2_mask, &cand_cell, &cand_h2);
+                        bool hit = false;
+                        const int first = a.table_empty ? 0 : probe_cell(a, cand_cell, cand_h2, &hit);
+                        n_look++;
+                        n_slots += first >= 0 ? (uint32_t)first + 1u : ne;
+                        if (hit) {
+                            const uint32_t slot = ins.y & 0xFFFFu;
+                            const float* val = cell_val(a, cand_cell, (uint32_t)first);
+                            V[(slot * 3 + 0) * 32] = __ldg(val);
+                            V[(slot * 3 + 1) * 32] = __ldg(val + 1);
+                            V[(slot * 3 + 2) * 32] = __ldg(val + 2);
+                            hits++;
+                            n_hit++;
+                            need = false;
+                        } else {
+                            cand_start = first >= 0 ? (uint32_t)first : ne;
+                            cand_full = first < 0;
+                            cand_node = ins.z;
+                        }
+                    }
+                    if (!need) skip_end = pc + (int)ins.w;
+                    if (__all_sync(FULL_MASK, !need)) {
+                        pc += (int)ins.w;
+                        if (pc + 1 < len) nxt = __ldg(&prog[pc + 1]);
+                    }
+                    continue;
+                }
+                const bool act = mine && pc > skip_end;
+                if (act) {
+                    exec_node(op, ins, V, pt, a.params, s_grad);
+                    n_nodes++;
+                    n_flops += ins.x >> 16;
+                }
+                if (a.use_cache && ((ins.x >> 8) & FLAG_ROOT)) {
+                    const uint32_t out = ins.y & 0xFFFFu;
+                    offer(a, act, i, cand_node, cand_cell, cand_h2, cand_start, cand_full, V[(out * 3) * 32],
+                          V[(out * 3 + 1) * 32], V[(out * 3 + 2) * 32], &n_cand, &n_full);
+                }
+            }
+            if (mine) {
+                a.out_rgb[i] = V[(mi.out_slot * 3) * 32];
+                a.out_rgb[(size_t)a.n + i] = V[(mi.out_slot * 3 + 1) * 32];
+                a.out_rgb[2 * (size_t)a.n + i] = V[(mi.out_slot * 3 + 2) * 32];
+                if (a.out_hits) a.out_hits[i] = (uint16_t)min(hits, 65535u);
+            }
+        }
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(&a.stats[ST_POINTS], (unsigned long long)a.n);
+    warp_add_u64(&a.stats[ST_NODES], n_nodes);
+    warp_add_u64(&a.stats[ST_FLOPS], n_flops);
+    warp_add_u64(&a.stats[ST_CANDIDATES], n_cand);
+    warp_add_u64(&a.stats[ST_FULL], n_full);
+    warp_add_u64(&a.stats[ST_LOOKUPS], n_look);
+    warp_add_u64(&a.stats[ST_HITS], n_hit);
+    warp_add_u64(&a.stats[ST_MISSES], n_look - n_hit);
+    warp_add_u64(&a.stats[ST_SLOTS], n_slots);
+    warp_add_u64(&a.stats[ST_BAD], n_bad);
+    if (__any_sync(FULL_MASK, n_bad != 0) && lane == 0) atomicOr(&a.ctl->err, ERR_BAD_MAT);
 }
 
 // Work items of the batched evaluation: ceil(misses / 32) per cacheable node.
@@ -583,8 +734,10 @@ __global__ void __launch_bounds__(EVAL_WARPS * 32) k_eval_roots(BatchArgs a, uin
             rec = a.probes[base + j];
         }
         const uint4* prog = a.prog + ri.prog_start;
+        uint4 nxt = ri.prog_len > 0 ? __ldg(&prog[0]) : make_uint4(0, 0, 0, 0);
         for (uint32_t pc = 0; pc < ri.prog_len; ++pc) {
-            const uint4 ins = __ldg(&prog[pc]);
+            const uint4 ins = nxt;
+            if (pc + 1 < ri.prog_len) nxt = __ldg(&prog[pc + 1]);
             const uint32_t op = ins.x & 0xFFu;
             if (!valid) continue;
             if (op == OP_LOAD_ROOT) {
@@ -1102,6 +1255,28 @@ int insert_grid(int num_sms) {
     return per_sm * num_sms;
 }
 
+// Insert phase: the candidates of the batch into the table (Alg. 1 semantics).
+static cudaError_t launch_insert(const BatchArgs& a, cudaStream_t s, int num_sms, uint64_t* nl) {
+    cudaError_t e = cudaSuccess;
+    const int gs_blocks = num_sms * 4;
+    if (a.n > 0 && a.use_cache && a.insert_rounds) {
+        BatchArgs arg = a;
+        void* params[] = {&arg};
+        if ((e = cudaLaunchCooperativeKernel((const void*)k_insert, dim3(insert_grid(num_sms)), dim3(256), params, 0, s)) !=
+            cudaSuccess)
+            return e;
+        *nl += 1;
+    } else if (a.n > 0 && a.use_cache) {
+        if ((e = cudaMemsetAsync(a.bin_cnt, 0, (size_t)a.n_bins * sizeof(uint32_t), s)) != cudaSuccess) return e;
+        k_bin_count<<<gs_blocks, 256, 0, s>>>(a);
+        k_bin_scan<<<1, 1024, 0, s>>>(a);
+        k_bin_scatter<<<gs_blocks, 256, 0, s>>>(a);
+        k_bin_insert<<<std::min<uint32_t>(a.n_bins, (uint32_t)num_sms * 16u), 256, 0, s>>>(a);
+        *nl += 4;
+    }
+    return e;
+}
+
 cudaError_t launch_batch(const BatchArgs& a, cudaStream_t s, int num_sms, cudaEvent_t* ev,
                          uint64_t* launches) {
     cudaError_t e;
@@ -1117,6 +1292,27 @@ cudaError_t launch_batch(const BatchArgs& a, cudaStream_t s, int num_sms, cudaEv
         return e;
     uint32_t* item_ctr = a.counts + a.n_mats;
     const int gs_blocks = num_sms * 4;
+    if (a.unsorted) {
+        // one fused launch: probes inline, no grouping and no probe records
+        if ((e = mark(1)) != cudaSuccess) return e;
+        if ((e = mark(2)) != cudaSuccess) return e;
+        if (a.n > 0) {
+            const size_t smem = eval_smem_bytes(a.max_slots);
+            if (smem > 48 * 1024 &&
+                (e = cudaFuncSetAttribute(k_eval_fused, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
+                return e;
+            k_eval_fused<<<num_sms * 16, EVAL_WARPS * 32, smem, s>>>(a);
+            nl++;
+        }
+        if ((e = mark(3)) != cudaSuccess) return e;
+        if ((e = launch_insert(a, s, num_sms, &nl)) != cudaSuccess) return e;
+        if ((e = mark(4)) != cudaSuccess) return e;
+        k_finish<<<1, 32, 0, s>>>(a);
+        nl++;
+        if ((e = mark(5)) != cudaSuccess) return e;
+        if (launches) *launches += nl;
+        return cudaGetLastError();
+    }
     if (a.n > 0) {
         k_hist<<<gs_blocks, 256, 0, s>>>(a);
         nl++;
@@ -1129,12 +1325,22 @@ cudaError_t launch_batch(const BatchArgs& a, cudaStream_t s, int num_sms, cudaEv
     }
     if ((e = mark(1)) != cudaSuccess) return e;
     if (a.n > 0 && a.use_cache && !a.keys_inline) {
-        uint32_t ne = a.n_entries;
+        const uint32_t ne = a.n_entries, rb = a.lookup_rb;
         const unsigned lb = (unsigned)num_sms * 8u;
-        if (ne <= 4) k_lookup<1, 4><<<lb, 256, 0, s>>>(a);
-        else if (ne <= 8) k_lookup<2, 4><<<lb, 256, 0, s>>>(a);
-        else if (ne <= 16) k_lookup<4, 2><<<lb, 256, 0, s>>>(a);
-        else k_lookup<8, 1><<<lb, 256, 0, s>>>(a);
+        if (ne <= 4) {
+            if (rb >= 4) k_lookup<1, 4><<<lb, 256, 0, s>>>(a);
+            else if (rb >= 2) k_lookup<1, 2><<<lb, 256, 0, s>>>(a);
+            else k_lookup<1, 1><<<lb, 256, 0, s>>>(a);
+        } else if (ne <= 8) {
+            if (rb >= 4) k_lookup<2, 4><<<lb, 256, 0, s>>>(a);
+            else if (rb >= 2) k_lookup<2, 2><<<lb, 256, 0, s>>>(a);
+            else k_lookup<2, 1><<<lb, 256, 0, s>>>(a);
+        } else if (ne <= 16) {
+            if (rb >= 2) k_lookup<4, 2><<<lb, 256, 0, s>>>(a);
+            else k_lookup<4, 1><<<lb, 256, 0, s>>>(a);
+        } else {
+            k_lookup<8, 1><<<lb, 256, 0, s>>>(a);
+        }
         nl++;
     }
     if (a.n > 0 && a.surr_slot) {
@@ -1163,21 +1369,7 @@ cudaError_t launch_batch(const BatchArgs& a, cudaStream_t s, int num_sms, cudaEv
         nl++;
     }
     if ((e = mark(3)) != cudaSuccess) return e;
-    if (a.n > 0 && a.use_cache && a.insert_rounds) {
-        BatchArgs arg = a;
-        void* params[] = {&arg};
-        if ((e = cudaLaunchCooperativeKernel((const void*)k_insert, dim3(insert_grid(num_sms)), dim3(256), params, 0, s)) !=
-            cudaSuccess)
-            return e;
-        nl++;
-    } else if (a.n > 0 && a.use_cache) {
-        if ((e = cudaMemsetAsync(a.bin_cnt, 0, (size_t)a.n_bins * sizeof(uint32_t), s)) != cudaSuccess) return e;
-        k_bin_count<<<gs_blocks, 256, 0, s>>>(a);
-        k_bin_scan<<<1, 1024, 0, s>>>(a);
-        k_bin_scatter<<<gs_blocks, 256, 0, s>>>(a);
-        k_bin_insert<<<std::min<uint32_t>(a.n_bins, (uint32_t)num_sms * 16u), 256, 0, s>>>(a);
-        nl += 4;
-    }
+    if ((e = launch_insert(a, s, num_sms, &nl)) != cudaSuccess) return e;
     if ((e = mark(4)) != cudaSuccess) return e;
     k_finish<<<1, 32, 0, s>>>(a);
     nl++;

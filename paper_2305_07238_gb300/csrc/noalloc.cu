@@ -77,6 +77,7 @@ extern "C" pmc_status pmc_eval_batch_noalloc(pmc_cache* c, const pmc_points* pts
                 PMC_NOALLOC_MAX_PROBES, PMC_NOALLOC_MAX_MATERIALS);
         return PMC_ERR_UNSUPPORTED;
     }
+    if (c->unsorted && c->use_surrogates && c->any_surr_on) return PMC_ERR_UNSUPPORTED;
     int prev = -1;
     if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
     if (prev != c->desc.device && cudaSetDevice(c->desc.device) != cudaSuccess) return PMC_ERR_INVALID_ARG;
@@ -143,6 +144,8 @@ extern "C" pmc_status pmc_eval_batch_noalloc(pmc_cache* c, const pmc_points* pts
     a.rinfo = c->d_rinfo; a.n_roots_total = (uint32_t)c->root_info.size(); a.max_level = c->max_level;
     a.miss_cnt = c->d_miss_cnt; a.root_item_base = c->d_root_items;
     a.misslist = reinterpret_cast<uint32_t*>(base + OFF_MISS);
+    a.unsorted = c->unsorted;
+    a.lookup_rb = c->lookup_rb;
     // launch_batch clears the counters and offsets that must start at zero; every other
     // region is written before it is read within the pass.
     cudaError_t e = launch_batch(a, s, c->num_sms, nullptr, &c->launches);

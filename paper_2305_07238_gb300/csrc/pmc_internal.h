@@ -89,8 +89,8 @@ constexpr uint32_t EPOCH_BITS = 20;
 constexpr uint32_t EPOCH_MAX = (1u << EPOCH_BITS) - 1;
 constexpr uint64_t MAX_POINTS = 1ull << 28;
 
-constexpr uint32_t MAX_LEVELS = 16;
-constexpr uint32_t MLP_PARAMS = 8515;  // learned surrogate: 64 -> 64 -> 64 -> 3     // nesting depth of cacheable nodes handled in batches
+constexpr uint32_t MAX_LEVELS = 16;    // nesting depth of cacheable nodes handled in batches
+constexpr uint32_t MLP_PARAMS = 8515;  // learned surrogate: 64 -> 64 -> 64 -> 3
 
 // Device-side control block of one cache object.
 struct Control {
@@ -114,6 +114,7 @@ constexpr uint32_t ERR_BAD_MAT = 1;
 constexpr uint32_t ERR_INSERT = 2;
 constexpr uint32_t ERR_BOUNDS = 4;
 constexpr uint32_t ERR_TIMEOUT = 8;
+constexpr uint32_t ERR_CAPACITY = 16;   // the batch needs more probe records than the scratch holds
 
 // Counter indices in the device stats array.
 enum {
@@ -164,6 +165,9 @@ struct BatchArgs {
     uint32_t* bin_cnt;         // n_bins
     uint32_t* bin_base;        // n_bins + 1
     Candidate* cands_binned;   // probe_cap
+    // schedule (chosen by the caller's flags or by the autotuner)
+    int unsorted;              // 1: no grouping; k_eval_fused probes inline in batch order
+    uint32_t lookup_rb;        // k_lookup: probes in flight per lane (1, 2 or 4)
 };
 
 constexpr uint32_t INSERT_BIN_CELLS = 512;

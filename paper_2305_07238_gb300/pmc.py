@@ -22,6 +22,9 @@ PMC_SORT_BY_MATERIAL = 0x2
 PMC_DEBUG_CHECKS = 0x4
 PMC_EVAL_INLINE = 0x8
 PMC_INSERT_ROUNDS = 0x10
+PMC_UNSORTED = 0x20
+PMC_GRAPH_RESET = 0x1
+TUNE_MAX = 16
 
 EXPORTED = (
     "pmc_create_cache", "pmc_eval_batch", "pmc_eval_batch_host", "pmc_sync", "pmc_stats",
@@ -29,7 +32,8 @@ EXPORTED = (
     "pmc_material_info", "pmc_analyze_material", "pmc_compute_keys", "pmc_set_timing",
     "pmc_read_timing", "pmc_eval_batch_noalloc", "pmc_train_surrogates", "pmc_set_surrogate",
     "pmc_get_surrogate", "pmc_use_surrogates", "pmc_mlp_forward", "pmc_mlp_gradient", "pmc_mlp_train",
-    "pmc_status_str",
+    "pmc_get_schedule", "pmc_set_schedule", "pmc_graph_create", "pmc_graph_launch", "pmc_graph_destroy",
+    "pmc_autotune", "pmc_status_str",
 )
 NOALLOC_MAX_POINTS, NOALLOC_MAX_PROBES, NOALLOC_MAX_MATERIALS = 8192, 32768, 4096
 PHASES = ("sort", "lookup", "eval", "insert", "finish")
@@ -51,7 +55,17 @@ class _Material(C.Structure):
 
 class _Desc(C.Structure):
     _fields_ = [("n_cells", C.c_uint64), ("n_entries", C.c_uint32), ("uv_level", C.c_uint32),
-                ("flags", C.c_uint32), ("min_root_nodes", C.c_uint32), ("device", C.c_int)]
+                ("flags", C.c_uint32), ("min_root_nodes", C.c_uint32), ("device", C.c_int),
+                ("probe_capacity", C.c_uint64)]
+
+
+class _Schedule(C.Structure):
+    _fields_ = [("flags", C.c_uint32), ("lookup_rb", C.c_uint32)]
+
+
+class _TuneResult(C.Structure):
+    _fields_ = [("n_tried", C.c_uint32), ("best", C.c_uint32), ("tried", _Schedule * TUNE_MAX),
+                ("ms", C.c_float * TUNE_MAX)]
 
 
 class _Points(C.Structure):
@@ -131,6 +145,18 @@ def load():
     L.pmc_mlp_gradient.restype = st
     L.pmc_mlp_train.argtypes = [vp, vp, vp, vp, u64, u32, u32, u32, C.c_float, vp, vp]
     L.pmc_mlp_train.restype = st
+    L.pmc_get_schedule.argtypes = [vp, vp]
+    L.pmc_get_schedule.restype = st
+    L.pmc_set_schedule.argtypes = [vp, vp]
+    L.pmc_set_schedule.restype = st
+    L.pmc_graph_create.argtypes = [vp, vp, u32, vp, vp, u32, vp]
+    L.pmc_graph_create.restype = st
+    L.pmc_graph_launch.argtypes = [vp, vp]
+    L.pmc_graph_launch.restype = st
+    L.pmc_graph_destroy.argtypes = [vp]
+    L.pmc_graph_destroy.restype = None
+    L.pmc_autotune.argtypes = [vp, vp, u32, vp]
+    L.pmc_autotune.restype = st
     L.pmc_status_str.argtypes = [st]
     L.pmc_status_str.restype = C.c_char_p
     _lib = L
@@ -176,14 +202,15 @@ def points_to_device(pts: dict, device="cuda"):
 class Cache:
     """A cache object of libpmc: compiled materials + a table of n_cells x n_entries slots."""
 
-    def __init__(self, materials, n_cells, n_entries, uv_level=10, flags=0, min_root_nodes=2, device=0):
+    def __init__(self, materials, n_cells, n_entries, uv_level=10, flags=0, min_root_nodes=2, device=0,
+                 probe_capacity=0):
         L = load()
         self._mats = [np.ascontiguousarray(m, dtype=NODE_DTYPE) for m in materials]
         arr = (_Material * len(self._mats))()
         for i, m in enumerate(self._mats):
             arr[i].n_nodes = len(m)
             arr[i].nodes = m.ctypes.data
-        desc = _Desc(n_cells, n_entries, uv_level, flags, min_root_nodes, device)
+        desc = _Desc(n_cells, n_entries, uv_level, flags, min_root_nodes, device, probe_capacity)
         h = C.c_void_p()
         _check(L.pmc_create_cache(C.byref(desc), arr, len(self._mats), C.byref(h)), "pmc_create_cache")
         self._h = h
@@ -235,6 +262,31 @@ class Cache:
 
     def sync(self):
         _check(load().pmc_sync(self._h), "pmc_sync")
+
+    # ---- schedule, graphs of passes, autotuning ----------------------------------------
+    def schedule(self) -> dict:
+        sc = _Schedule()
+        _check(load().pmc_get_schedule(self._h, C.byref(sc)), "pmc_get_schedule")
+        return {"flags": int(sc.flags), "lookup_rb": int(sc.lookup_rb)}
+
+    def set_schedule(self, flags: int, lookup_rb: int = 4):
+        sc = _Schedule(flags, lookup_rb)
+        _check(load().pmc_set_schedule(self._h, C.byref(sc)), "pmc_set_schedule")
+
+    def graph(self, passes, out_rgb, out_hits=None, reset=False) -> "Graph":
+        """Records len(passes) passes (dicts of device tensors) writing out_rgb[k] (and
+        out_hits[k]) as one CUDA graph; see Graph.launch."""
+        return Graph(self, passes, out_rgb, out_hits, reset)
+
+    def autotune(self, pts, reps=3) -> dict:
+        """Times the candidate schedules on one device batch and keeps the fastest."""
+        n = int(pts["u"].numel())
+        p = _Points(*[_dptr(pts[k]) for k in POINT_FIELDS], n)
+        r = _TuneResult()
+        _check(load().pmc_autotune(self._h, C.byref(p), reps, C.byref(r)), "pmc_autotune")
+        tried = [{"flags": int(r.tried[k].flags), "lookup_rb": int(r.tried[k].lookup_rb), "ms": float(r.ms[k])}
+                 for k in range(r.n_tried)]
+        return {"tried": tried, "best": int(r.best), "schedule": self.schedule()}
 
     def reset(self, stream=None):
         _check(load().pmc_reset(self._h, _stream_handle(stream)), "pmc_reset")
@@ -303,6 +355,41 @@ class Cache:
         _check(load().pmc_material_info(self._h, m, C.byref(nr), roots.ctypes.data, 65536,
                                         C.byref(ni), C.byref(ns)), "pmc_material_info")
         return {"roots": roots[: nr.value].copy(), "n_instr": ni.value, "n_slots": ns.value}
+
+
+class Graph:
+    """A CUDA graph of consecutive passes of one cache (pmc_graph_create).  The tensors
+    are bound by address and kept alive here."""
+
+    def __init__(self, cache: Cache, passes, out_rgb, out_hits=None, reset=False):
+        L = load()
+        k = len(passes)
+        self._keep = (passes, out_rgb, out_hits, cache)
+        pts = (_Points * max(k, 1))()
+        for i, pp in enumerate(passes):
+            pts[i] = _Points(*[_dptr(pp[f]) for f in POINT_FIELDS], int(pp["u"].numel()))
+        rgb = (C.c_void_p * max(k, 1))(*[t.data_ptr() for t in out_rgb])
+        hits = None
+        if out_hits is not None:
+            hits = (C.c_void_p * max(k, 1))(*[None if t is None else t.data_ptr() for t in out_hits])
+        h = C.c_void_p()
+        _check(L.pmc_graph_create(cache._h, pts, k, rgb, hits, PMC_GRAPH_RESET if reset else 0, C.byref(h)),
+               "pmc_graph_create")
+        self._h = h
+
+    def launch(self, stream=None):
+        _check(load().pmc_graph_launch(self._h, _stream_handle(stream)), "pmc_graph_launch")
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().pmc_graph_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def mlp_forward(theta, u, v, clamp=True, stream=None):

@@ -387,6 +387,25 @@ class Frame:
     def n_pixels(self):
         return self.spec.width * self.spec.height
 
+    def _pixel_layout(self):
+        """Per-pixel copies of the per-tile quantities (built once, then reused)."""
+        if getattr(self, "_pix", None) is None:
+            t = self.pix_tile
+            spec = self.spec
+            self._pix = {
+                "bx": (self.px_x % spec.tile).astype(np.float64),
+                "by": (self.px_y % spec.tile).astype(np.float64),
+                "fx": self.px_x.astype(np.float64), "fy": self.px_y.astype(np.float64),
+                "ou": np.ascontiguousarray(self.tile_o[t, 0]), "ov": np.ascontiguousarray(self.tile_o[t, 1]),
+                "d": self.tile_delta[t],
+                "c": [np.ascontiguousarray(self.tile_c[t, k]) for k in range(3)],
+                "e1": [np.ascontiguousarray(self.tile_e1[t, k]) for k in range(3)],
+                "e2": [np.ascontiguousarray(self.tile_e2[t, k]) for k in range(3)],
+                "mat": np.ascontiguousarray(self.tile_mat[t], dtype=np.uint32),
+                "n": [np.ascontiguousarray(self.tile_n[t, k], dtype=np.float32) for k in range(3)],
+            }
+        return self._pix
+
     def points(self, pass_index: int, rows: tuple | None = None) -> dict:
         """One sample per pixel (scanline order) for pass `pass_index`; `rows` = (y0, y1)
         restricts to a band of pixel rows (same draws as the full pass)."""
@@ -396,15 +415,47 @@ class Frame:
         sel = slice(None)
         if rows is not None:
             sel = slice(rows[0] * spec.width, rows[1] * spec.width)
-        t = self.pix_tile[sel]
-        lx = (self.px_x[sel] % spec.tile) + jit[0][sel]
-        ly = (self.px_y[sel] % spec.tile) + jit[1][sel]
-        d = self.tile_delta[t]
-        u = np.mod(self.tile_o[t, 0] + d * lx, 1.0)
-        v = np.mod(self.tile_o[t, 1] + d * ly, 1.0)
-        gx = self.px_x[sel] + jit[0][sel]
-        gy = self.px_y[sel] + jit[1][sel]
+        L = self._pixel_layout()
+        jx, jy = jit[0][sel], jit[1][sel]
+        d = L["d"][sel]
+        u = np.mod(L["ou"][sel] + d * (L["bx"][sel] + jx), 1.0)
+        v = np.mod(L["ov"][sel] + d * (L["by"][sel] + jy), 1.0)
         w = 0.01
-        p = (self.tile_c[t] + (w * gx)[:, None] * self.tile_e1[t]
-             + (w * gy)[:, None] * self.tile_e2[t]) * 0.25
-        return _pack(u, v, self.tile_mat[t], p.T, self.tile_n[t].T)
+        wx = w * (L["fx"][sel] + jx)
+        wy = w * (L["fy"][sel] + jy)
+        p = [(L["c"][k][sel] + wx * L["e1"][k][sel] + wy * L["e2"][k][sel]) * 0.25 for k in range(3)]
+        return _pack(u, v, L["mat"][sel], p, [L["n"][k][sel] for k in range(3)])
+
+    def points_torch(self, pass_index: int, device="cuda", rows: tuple | None = None) -> dict:
+        """The same recipe drawn with torch's generator on `device` (for long sequences of
+        passes whose host generation would dominate); the jitter comes from a different
+        generator, so the values differ from points().  Returns torch tensors (mat as
+        int32), SoA like points()."""
+        import torch
+        spec = self.spec
+        key = ("_tpix", str(device))
+        if getattr(self, "_tpix_key", None) != key:
+            L = self._pixel_layout()
+            T = lambda a: torch.as_tensor(a, device=device)
+            self._tpix = {k: ([T(x) for x in v] if isinstance(v, list) else T(v)) for k, v in L.items()}
+            self._tpix["mat"] = T(L["mat"].view(np.int32))
+            self._tpix_key = key
+        L = self._tpix
+        g = torch.Generator(device=device)
+        g.manual_seed(((spec.seed * 1_000_003) ^ (pass_index * 7919) ^ 0x5EED) & 0x7FFFFFFFFFFFFFFF)
+        jit = torch.rand((2, self.n_pixels), generator=g, device=device, dtype=torch.float64)
+        sel = slice(None)
+        if rows is not None:
+            sel = slice(rows[0] * spec.width, rows[1] * spec.width)
+        jx, jy = jit[0][sel], jit[1][sel]
+        d = L["d"][sel]
+        u = torch.remainder(L["ou"][sel] + d * (L["bx"][sel] + jx), 1.0)
+        v = torch.remainder(L["ov"][sel] + d * (L["by"][sel] + jy), 1.0)
+        wx = 0.01 * (L["fx"][sel] + jx)
+        wy = 0.01 * (L["fy"][sel] + jy)
+        out = {"u": u.float().contiguous(), "v": v.float().contiguous(), "mat": L["mat"][sel].contiguous()}
+        for k, name in enumerate(("px", "py", "pz")):
+            out[name] = ((L["c"][k][sel] + wx * L["e1"][k][sel] + wy * L["e2"][k][sel]) * 0.25).float().contiguous()
+        for k, name in enumerate(("nx", "ny", "nz")):
+            out[name] = L["n"][k][sel].contiguous()
+        return out

@@ -58,7 +58,7 @@ def _compare_pass(gpu, ref, P, part, check_masks=True):
     err = float(np.abs(g_rgb - r["rgb"]).max()) if len(part["u"]) else 0.0
     assert err <= TOL, f"max-abs error {err}"
     assert np.array_equal(g_hits, r["hits"])
-    if check_masks and not ref.off:
+    if check_masks and not ref.off and not gpu.flags & 0x20:   # unsorted passes keep no probe records
         assert np.array_equal(gpu.last_hit_masks(len(part["u"])), _oracle_masks(ref, part, r))
     gs, rs = gpu.stats(), ref.stats()
     for k in EXACT_STATS:
@@ -126,7 +126,8 @@ def test_tiny_config_cache_off(P):
 
 
 # ---- frame-shaped streams: a band of the 1920-wide frame, several table geometries ----------
-MODES = {"grouped": 0, "inline": 0x8, "rounds": 0x10}   # PMC_EVAL_INLINE, PMC_INSERT_ROUNDS
+# PMC_EVAL_INLINE, PMC_INSERT_ROUNDS, PMC_UNSORTED
+MODES = {"grouped": 0, "inline": 0x8, "rounds": 0x10, "unsorted": 0x20, "unsorted_rounds": 0x30}
 
 
 @pytest.mark.parametrize("mode", sorted(MODES))
@@ -156,7 +157,8 @@ def test_ragged_batch_sizes(P, n):
     mats = W.random_materials(5, 20, 120, 0.2, seed=9)
     pts = W.points_uniform(max(n, 1), seed=n, n_mats=5)
     pts = W.slice_points(pts, 0, n)
-    gpu = P.Cache(mats, 256, 8, flags=MODES["rounds"] if n % 2 else 0)
+    flags = (MODES["rounds"] if n % 2 else 0) | (MODES["unsorted"] if n in (1, 33) else 0)
+    gpu = P.Cache(mats, 256, 8, flags=flags)
     ref = O.Cache(mats, 256, 8)
     for _ in range(2):
         _compare_pass(gpu, ref, P, pts)
@@ -192,11 +194,12 @@ def test_hand_built_nested_roots(P, mode):
 
 
 # ---- errors, determinism, host entry point ----------------------------------------------------
-def test_bad_material_index_reported(P):
+@pytest.mark.parametrize("mode", ["grouped", "unsorted"])
+def test_bad_material_index_reported(P, mode):
     mat = W.material_tiny()
     pts = W.points_uniform(100, seed=7)
     pts["mat"][17] = 3
-    gpu = P.Cache([mat], 64, 8)
+    gpu = P.Cache([mat], 64, 8, flags=MODES[mode])
     d = P.points_to_device(pts)
     rgb = torch.full((3, 100), 5.0, device="cuda")
     gpu.eval_batch(d, rgb)
