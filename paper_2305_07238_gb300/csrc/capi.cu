@@ -202,6 +202,7 @@ pmc_status pmc_create_cache(const pmc_cache_desc* desc, const pmc_material* mats
         mi.out_slot = cm.out_slot;
         mi.n_slots = cm.n_slots;
         mi.n_nodes = cm.n_nodes;
+        params.resize((params.size() + 3) & ~size_t(3), 0.0f);   // 16-byte aligned per material
         const uint32_t pbase = (uint32_t)params.size();
         for (uint4 ins : cm.prog) {
             if ((ins.x & 0xFFu) != OP_ROOT_BEGIN) ins.w += pbase;
@@ -242,6 +243,8 @@ pmc_status pmc_create_cache(const pmc_cache_desc* desc, const pmc_material* mats
         c->max_slots = std::max(c->max_slots, mi.n_slots);
     }
     c->prog_len = (uint32_t)prog.size();
+    // the interpreters fetch eight parameters ahead of a node, even one without any
+    params.resize(((params.size() + 3) & ~size_t(3)) + 8, 0.0f);
     if (c->max_level >= MAX_LEVELS) c->split = 0;   // deeper nesting: evaluate misses inline
     if (eval_smem_bytes(c->max_slots) > 200u * 1024u) {
         fprintf(stderr, "pmc: a material needs %u live values; this build supports %zu\n",

@@ -114,6 +114,8 @@ bool fold(const pmc_node& nd, const std::vector<pmc_node>& g, pmc_node* out) {
     return true;
 }
 
+// Appends a node's parameters to the pool.  Every node's parameters start on a 16-byte
+// boundary so that an interpreter can fetch the first eight with two vector loads.
 void pack_params(const pmc_node& nd, std::vector<float>* pool) {
     auto bits = [](int32_t x) { float f; std::memcpy(&f, &x, 4); return f; };
     const float* p = nd.fp;
@@ -207,6 +209,7 @@ uint32_t emit_standalone(const std::vector<pmc_node>& g, const std::vector<std::
         ins.x = g[x].op | (flags << 8) | (cost << 16);
         ins.y = slot[x] | (in_slot[0] << 16);
         ins.z = in_slot[1] | (in_slot[2] << 16);
+        params->resize((params->size() + 3) & ~size_t(3), 0.0f);
         ins.w = (uint32_t)params->size();
         pack_params(g[x], params);
         prog->push_back(ins);
@@ -465,6 +468,7 @@ bool compile_material(const pmc_node* nodes_in, uint32_t n, uint32_t min_root_no
         ins.x = g[x].op | (flags << 8) | (cost << 16);
         ins.y = slot[x] | (in_slot[0] << 16);
         ins.z = in_slot[1] | (in_slot[2] << 16);
+        out->params.resize((out->params.size() + 3) & ~size_t(3), 0.0f);
         ins.w = (uint32_t)out->params.size();
         pack_params(g[x], &out->params);
         out->prog.push_back(ins);

@@ -277,6 +277,9 @@ __device__ __forceinline__ int scan_words(const uint4 (&w)[NQ], uint32_t h2, uin
 }
 
 // NQ = 16-byte words of hash2 per cell (ceil(N_e / 4)); RB probes in flight per lane.
+// Each group of RB probes takes two dependent round trips to memory, both fully
+// overlapped across the group: first every probe's hash2 words, then the values of
+// the hits.  Records and miss lists are written after both.
 template <int NQ, int RB>
 __global__ void __launch_bounds__(256) k_lookup(BatchArgs a) {
     const uint32_t warp = threadIdx.x >> 5, lane = lane_id();
@@ -296,48 +299,60 @@ __global__ void __launch_bounds__(256) k_lookup(BatchArgs a) {
             iv = d_texel(a.sv[s], a.level);
         }
         const MatInfo mi = a.mats[m];
+        const int32_t surr = a.surr_ord ? a.surr_ord[m] : -1;   // a surrogate's node is not probed
         const size_t rec0 = (size_t)__ldg(&a.probe_base[m]) + j;
         for (uint32_t r0 = 0; r0 < mi.n_roots; r0 += RB) {
             uint4 w[RB][NQ];
             uint32_t cell[RB], h2[RB];
+            bool act[RB];
+            // round trip 1: the hash2 words of every probe of the group
 #pragma unroll
             for (int b = 0; b < RB; ++b) {
-                const bool act = valid && r0 + b < mi.n_roots && !(a.surr_ord && a.surr_ord[m] == (int32_t)(r0 + b));
+                act[b] = valid && r0 + b < mi.n_roots && (int32_t)(r0 + b) != surr;
                 cell[b] = 0;
                 h2[b] = 0;
-                if (act) {
+                if (act[b]) {
                     const uint32_t node = __ldg(&a.roots[mi.root_base + r0 + b]);
                     d_address(d_key(m, node, a.level, iu, iv), a.n_cells, a.cells_pow2_mask, &cell[b], &h2[b]);
                 }
                 const uint4* hw = reinterpret_cast<const uint4*>(cell_h2(a, cell[b]));
-                const bool ld = act && !a.table_empty;   // an empty table misses at slot 0
+                const bool ld = act[b] && !a.table_empty;   // an empty table misses at slot 0
 #pragma unroll
                 for (int q = 0; q < NQ; ++q) w[b][q] = ld ? __ldg(hw + q) : make_uint4(0, 0, 0, 0);
+            }
+            // round trip 2: the values of the hits
+            int first[RB];
+            bool hit[RB];
+            float v[RB][3];
+#pragma unroll
+            for (int b = 0; b < RB; ++b) {
+                first[b] = scan_words<NQ>(w[b], h2[b], ne, &hit[b]);
+                hit[b] = hit[b] && act[b];
+                const float* val = cell_val(a, cell[b], hit[b] ? (uint32_t)first[b] : 0u);
+                v[b][0] = hit[b] ? __ldg(val) : 0.0f;
+                v[b][1] = hit[b] ? __ldg(val + 1) : 0.0f;
+                v[b][2] = hit[b] ? __ldg(val + 2) : 0.0f;
             }
 #pragma unroll
             for (int b = 0; b < RB; ++b) {
                 if (r0 + b >= mi.n_roots) break;                 // uniform in the warp
-                // a node replaced by its learned surrogate is not probed (uniform)
-                if (a.surr_ord && a.surr_ord[m] == (int32_t)(r0 + b)) continue;
-                bool hit = false;
+                if ((int32_t)(r0 + b) == surr) continue;          // uniform
                 const size_t rec = rec0 + (size_t)(r0 + b) * cnt;
                 if (valid) {
-                    const int first = scan_words<NQ>(w[b], h2[b], ne, &hit);
                     n_look++;
-                    n_slots += first >= 0 ? (uint32_t)first + 1u : ne;
-                    if (hit) {
-                        const float* val = cell_val(a, cell[b], (uint32_t)first);
-                        a.probes[rec] = make_float4(__ldg(val), __ldg(val + 1), __ldg(val + 2), __uint_as_float(PROBE_HIT));
+                    n_slots += first[b] >= 0 ? (uint32_t)first[b] + 1u : ne;
+                    if (hit[b]) {
+                        a.probes[rec] = make_float4(v[b][0], v[b][1], v[b][2], __uint_as_float(PROBE_HIT));
                         n_hit++;
                     } else {
                         a.probes[rec] = make_float4(__uint_as_float(cell[b]), __uint_as_float(h2[b]),
-                                                    __uint_as_float(first >= 0 ? (uint32_t)first : ne),
-                                                    __uint_as_float(first >= 0 ? PROBE_MISS : PROBE_FULL));
+                                                    __uint_as_float(first[b] >= 0 ? (uint32_t)first[b] : ne),
+                                                    __uint_as_float(first[b] >= 0 ? PROBE_MISS : PROBE_FULL));
                     }
                 }
                 if (a.split) {
                     // list the misses of this cacheable node for the batched evaluation
-                    const bool miss = valid && !hit;
+                    const bool miss = valid && !hit[b];
                     const unsigned mm = __ballot_sync(FULL_MASK, miss);
                     if (mm) {
                         const int leader = __ffs(mm) - 1;
@@ -455,10 +470,13 @@ __global__ void __launch_bounds__(EVAL_WARPS * 32) k_eval(BatchArgs a, uint32_t*
             if (op == OP_ROOT_BEGIN) {
                 const uint32_t slot = ins.y & 0xFFFFu, r = ins.y >> 16;
                 bool need = valid;
+                // the node's probe record: a hit, a miss, or a value computed this pass
+                float4 rec = make_float4(0.f, 0.f, 0.f, 0.f);
+                if (valid && ((a.use_cache && !a.keys_inline) || a.surr_ord))
+                    rec = a.probes[(size_t)pbase + (size_t)r * cnt + j];
                 if (a.surr_ord && a.surr_ord[m] == (int32_t)r) {
                     // the learned surrogate already wrote this node's value
                     if (valid) {
-                        const float4 rec = a.probes[(size_t)pbase + (size_t)r * cnt + j];
                         V[(slot * 3 + 0) * 32] = rec.x;
                         V[(slot * 3 + 1) * 32] = rec.y;
                         V[(slot * 3 + 2) * 32] = rec.z;
@@ -475,7 +493,6 @@ __global__ void __launch_bounds__(EVAL_WARPS * 32) k_eval(BatchArgs a, uint32_t*
                         n_look++;
                     }
                 } else if (a.use_cache && valid) {
-                    const float4 rec = a.probes[(size_t)pbase + (size_t)r * cnt + j];
                     const uint32_t state = __float_as_uint(rec.w);
                     if (state == PROBE_HIT || state == PROBE_COMPUTED) {
                         V[(slot * 3 + 0) * 32] = rec.x;
@@ -1349,7 +1366,7 @@ cudaError_t launch_batch(const BatchArgs& a, cudaStream_t s, int num_sms, cudaEv
     }
     if ((e = mark(2)) != cudaSuccess) return e;
     if (a.n > 0) {
-        size_t smem = eval_smem_bytes(a.max_slots);
+        const size_t smem = eval_smem_bytes(a.max_slots);
         if (smem > 48 * 1024) {
             if ((e = cudaFuncSetAttribute(k_eval, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
                 return e;

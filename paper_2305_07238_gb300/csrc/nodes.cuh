@@ -151,36 +151,47 @@ __device__ __forceinline__ void exec_node(uint32_t op, const uint4& ins, float* 
                                           const float* __restrict__ params, const float2* grad) {
     const uint32_t out = ins.y & 0xFFFFu;
     const uint32_t i0 = ins.y >> 16, i1 = ins.z & 0xFFFFu, i2 = ins.z >> 16;
+    // a node's parameters start on a 16-byte boundary: vector loads fetch them
     const float* p = params + ins.w;
+    const float4* p4 = reinterpret_cast<const float4*>(p);
     float r0 = 0.f, r1 = 0.f, r2 = 0.f;
     switch (op) {
     case PMC_OP_UV: r0 = pt.u; r1 = pt.v; break;
     case PMC_OP_POSITION: r0 = pt.px; r1 = pt.py; r2 = pt.pz; break;
     case PMC_OP_NORMAL: r0 = pt.nx; r1 = pt.ny; r2 = pt.nz; break;
-    case PMC_OP_CONST: r0 = __ldg(&p[0]); r1 = __ldg(&p[1]); r2 = __ldg(&p[2]); break;
+    case PMC_OP_CONST: {
+        const float4 q = __ldg(p4);
+        r0 = q.x; r1 = q.y; r2 = q.z;
+        break;
+    }
     case PMC_OP_UV_AFFINE: {
+        const float4 q = __ldg(p4);
+        const float4 t = __ldg(p4 + 1);
         float x = V[(i0 * 3) * 32], y = V[(i0 * 3 + 1) * 32];
-        r0 = fmaf(__ldg(&p[0]), x, fmaf(__ldg(&p[1]), y, __ldg(&p[4])));
-        r1 = fmaf(__ldg(&p[2]), x, fmaf(__ldg(&p[3]), y, __ldg(&p[5])));
+        r0 = fmaf(q.x, x, fmaf(q.y, y, t.x));
+        r1 = fmaf(q.z, x, fmaf(q.w, y, t.y));
         break;
     }
     case PMC_OP_FBM: {
-        float pp[6];
-#pragma unroll
-        for (int k = 0; k < 6; ++k) pp[k] = __ldg(&p[k]);
+        const float4 q = __ldg(p4);
+        const float4 t = __ldg(p4 + 1);
+        const float pp[6] = {q.x, q.y, q.z, q.w, t.x, t.y};
         r0 = r1 = r2 = d_fbm(V[(i0 * 3) * 32], V[(i0 * 3 + 1) * 32], pp, grad);
         break;
     }
     case PMC_OP_VORONOI: {
-        float pp[2] = {__ldg(&p[0]), __ldg(&p[1])};
+        const float4 q = __ldg(p4);
+        const float pp[2] = {q.x, q.y};
         r0 = r1 = r2 = d_voronoi(V[(i0 * 3) * 32], V[(i0 * 3 + 1) * 32], pp);
         break;
     }
     case PMC_OP_CHECKER: {
-        float sc = __ldg(&p[0]);
+        const float4 q = __ldg(p4);
+        const float4 t = __ldg(p4 + 1);
+        const float sc = q.x;
         long long k = (long long)floorf(V[(i0 * 3) * 32] * sc) + (long long)floorf(V[(i0 * 3 + 1) * 32] * sc);
-        const float* c = (k & 1) ? p + 4 : p + 1;
-        r0 = d_clamp01(__ldg(&c[0])); r1 = d_clamp01(__ldg(&c[1])); r2 = d_clamp01(__ldg(&c[2]));
+        const bool odd = (k & 1) != 0;
+        r0 = d_clamp01(odd ? t.x : q.y); r1 = d_clamp01(odd ? t.y : q.z); r2 = d_clamp01(odd ? t.z : q.w);
         break;
     }
     case PMC_OP_RAMP: {
@@ -231,8 +242,8 @@ __device__ __forceinline__ void exec_node(uint32_t op, const uint4& ins, float* 
         break;
     }
     case PMC_OP_FACING: {
-        float d = fmaf(V[(i0 * 3) * 32], __ldg(&p[0]),
-                       fmaf(V[(i0 * 3 + 1) * 32], __ldg(&p[1]), V[(i0 * 3 + 2) * 32] * __ldg(&p[2])));
+        const float4 q = __ldg(p4);
+        float d = fmaf(V[(i0 * 3) * 32], q.x, fmaf(V[(i0 * 3 + 1) * 32], q.y, V[(i0 * 3 + 2) * 32] * q.z));
         r0 = r1 = r2 = d_clamp01(fabsf(d));
         break;
     }
