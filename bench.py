@@ -41,7 +41,8 @@ N_CELLS, N_ENTRIES, LEVEL = 1 << 21, 8, 10
 SAMPLE_ROWS = (0, 40)            # CPU-oracle sample: 40 full-width rows, all 16 passes
 REF_ROWS = (0, 16)               # reference arm: 16 full-width rows per step, all 16 passes
 # ncu capture of k_eval / k_lookup on the same workload (profiles/): DRAM bytes per launch
-NCU_TRAFFIC = {"eval": None, "lookup": None}
+# (profiles/launches_frame1080p.md: mean over the 16 k_eval and 15 k_lookup launches of one frame)
+NCU_TRAFFIC = {"eval": 309.8e6, "eval_roots": None, "lookup": 1050.0e6}
 
 FP32_LANES_PER_SM = 128          # Blackwell SM: 4 partitions x 32 FP32 lanes
 N_SMS = 152
@@ -248,9 +249,14 @@ def ours(args, rank, world, local_rank, dist):
     hbm_peak, sm_mhz_max, peak_kind = peaks()
     ms = timing["ms"]
     per_launch_ms = {k: v / max(1, timing["batches"]) for k, v in ms.items()}
+    # the first pass of a frame runs on an empty table: no lookup launch
+    per_launch_ms["lookup"] = ms["lookup"] / max(1, timing["batches"] - args.steps)
     fp32_peak = N_SMS * FP32_LANES_PER_SM * 2 * sm_mhz_max * 1e6 / 1e12   # TFLOP/s
-    flops_per_frame = frame_stats["flops"]
-    eval_tflops = flops_per_frame * args.steps / (ms["eval"] / 1e3) / 1e12 if ms["eval"] else 0.0
+    # FP32 work of the per-point programs (k_eval) and of the batched misses (k_eval_roots)
+    flops_missed = frame_stats["flops_missed"]
+    flops_eval = frame_stats["flops"] - flops_missed
+    eval_tflops = flops_eval * args.steps / (ms["eval"] / 1e3) / 1e12 if ms["eval"] else 0.0
+    missed_tflops = flops_missed * args.steps / (ms["missed"] / 1e3) / 1e12 if ms["missed"] else 0.0
     # algorithmic bytes of the lookup: u, v of every grouped point, the hash2 words
     # examined (4 B each), the 12-B value of every hit and one 16-B record per probe
     look_bytes_frame = (8 * n * SPP
@@ -262,14 +268,18 @@ def ours(args, rank, world, local_rank, dist):
         "eval": {"bound": "alu", "achieved": round(eval_tflops, 3), "peak": round(fp32_peak, 2),
                  "unit": "TFLOP/s", "frac": round(eval_tflops / fp32_peak, 4),
                  "ms_per_launch": round(per_launch_ms["eval"], 4), "traffic": NCU_TRAFFIC["eval"]},
+        "eval_roots": {"bound": "alu", "achieved": round(missed_tflops, 3), "peak": round(fp32_peak, 2),
+                       "unit": "TFLOP/s", "frac": round(missed_tflops / fp32_peak, 4),
+                       "ms_per_pass": round(per_launch_ms["missed"], 4), "traffic": NCU_TRAFFIC["eval_roots"]},
         "lookup": {"bound": "hbm", "achieved": round(look_gbs, 1), "peak": hbm_peak, "unit": "GB/s",
                    "frac": round(look_gbs / hbm_peak, 4), "ms_per_launch": round(per_launch_ms["lookup"], 4),
                    "traffic": NCU_TRAFFIC["lookup"]},
     }
-    dominant = max(("eval", "lookup"), key=lambda k: ms[k])
+    phase_of = {"eval": "eval", "eval_roots": "missed", "lookup": "lookup"}
+    dominant = max(phase_of, key=lambda k: ms[phase_of[k]])
     roof = dict(kernels[dominant])
-    roof["kernel"] = "k_eval" if dominant == "eval" else "k_lookup"
-    roof["peak_kind"] = f"{'FP32 lanes x 2 x max SM clock' if dominant == 'eval' else peak_kind + ' HBM copy'}"
+    roof["kernel"] = {"eval": "k_eval", "eval_roots": "k_eval_roots", "lookup": "k_lookup"}[dominant]
+    roof["peak_kind"] = "FP32 lanes x 2 x max SM clock" if dominant != "lookup" else peak_kind + " HBM copy"
 
     line = {
         "metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": world,
@@ -503,6 +513,29 @@ def cpu_baseline(P, torch, mats, frame, dev):
             err)
 
 
+def profile_run(args):
+    """Eager frames only (default schedule, no autotuning, no graph, no other legs), so
+    that an ncu launch list can select whole frames: W warm-up frames, then K frames."""
+    import torch
+    from paper_2305_07238_gb300 import build as B
+    from paper_2305_07238_gb300 import pmc as P
+    B.build()
+    mats, frame = workload(seed=0)
+    dev_passes = [P.points_to_device(frame.points(p)) for p in range(SPP)]
+    n = WIDTH * HEIGHT
+    outs = torch.empty((3, n), dtype=torch.float32, device="cuda")
+    hits = torch.empty(n, dtype=torch.int16, device="cuda")
+    cache = P.Cache(mats, N_CELLS, N_ENTRIES, uv_level=LEVEL)
+    for _ in range(args.warmup):
+        run_frame(cache, dev_passes, outs, hits, None)
+    cache.sync()
+    cache.read_timing()
+    secs = timed_steps(torch, cache, dev_passes, outs, hits, args.steps, lambda: None)
+    launches = cache.read_timing()["launches"]
+    return {"profile": "eager frames", "value": round(n * SPP * args.steps / secs, 1), "unit": UNIT,
+            "steps": args.steps, "warmup": args.warmup, "launches_per_frame": launches // max(1, args.steps)}
+
+
 # --------------------------------------------------------------------------------------
 # reference arm: the CPU oracle as it stands
 # --------------------------------------------------------------------------------------
@@ -548,7 +581,12 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--legs", default="cached,uncached,e2e,surr,f128,cpu",
                     help="comma list of cached, uncached, e2e, surr, f128, cpu (profiling runs take 'cached')")
+    ap.add_argument("--profile", action="store_true",
+                    help="eager frames only, for ncu launch lists (prints launches per frame)")
     args = ap.parse_args()
+    if args.profile:
+        print(json.dumps(profile_run(args)), flush=True)
+        return 0
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

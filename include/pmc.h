@@ -174,6 +174,8 @@ typedef struct {
     uint64_t points;
     uint64_t bad_points;      /* points whose material index was out of range        */
     uint64_t surrogate_evals; /* cacheable-node values produced by learned surrogates    */
+    uint64_t flops_missed;    /* part of flops spent on missed cacheable nodes evaluated
+                                 in batches (the batched-miss kernel)                  */
 } pmc_stats_t;
 
 /* Compiles the networks (cacheable-node analysis, constant folding, serialisation;
@@ -246,12 +248,14 @@ pmc_status pmc_compute_keys(const uint32_t* mat, const uint32_t* node, const flo
 
 /* Per-phase device timing of later batches, measured with CUDA events recorded on
  * each batch's stream: 0 = grouping by material (histogram, scan, scatter),
- * 1 = lookup, 2 = evaluation, 3 = insert rounds, 4 = bookkeeping.  Timing adds two
- * event records per phase and is off by default. */
+ * 1 = lookup (and learned surrogates), 2 = batched evaluation of missed cacheable
+ * nodes, 3 = evaluation of the per-point programs, 4 = insert, 5 = bookkeeping.
+ * Timing adds one event record per phase boundary and is off by default; graph
+ * replays are not timed. */
 pmc_status pmc_set_timing(pmc_cache* cache, int enable);
 
 /* Synchronises, then returns the milliseconds per phase summed over the batches
- * enqueued since the last read (ms[5], host), the number of kernels the library
+ * enqueued since the last read (ms[6], host), the number of kernels the library
  * launched in that time and the number of batches; clears the accumulators. */
 pmc_status pmc_read_timing(pmc_cache* cache, double* ms, uint64_t* kernel_launches,
                            uint64_t* batches);

@@ -482,6 +482,7 @@ pmc_status pmc_stats(pmc_cache* c, pmc_stats_t* out) {
     out->points = v[ST_POINTS];
     out->bad_points = v[ST_BAD];
     out->surrogate_evals = v[ST_SURR];
+    out->flops_missed = v[ST_FLOPS_MISSED];
     return st;
 }
 
@@ -580,7 +581,7 @@ pmc_status pmc_read_timing(pmc_cache* c, double* ms, uint64_t* kernel_launches, 
     pmc_status st = pmc_sync(c);
     if (st == PMC_ERR_CUDA) return st;
     DeviceGuard g(c->desc.device);
-    double acc[PH_COUNT] = {0, 0, 0, 0, 0};
+    double acc[PH_COUNT] = {};
     for (size_t b = 0; b + PH_COUNT + 1 <= c->events_used; b += PH_COUNT + 1) {
         for (int k = 0; k < PH_COUNT; ++k) {
             float t = 0.0f;

@@ -776,6 +776,7 @@ __global__ void __launch_bounds__(EVAL_WARPS * 32) k_eval_roots(BatchArgs a, uin
     }
     warp_add_u64(&a.stats[ST_NODES], n_nodes);
     warp_add_u64(&a.stats[ST_FLOPS], n_flops);
+    warp_add_u64(&a.stats[ST_FLOPS_MISSED], n_flops);
     warp_add_u64(&a.stats[ST_CANDIDATES], n_cand);
     warp_add_u64(&a.stats[ST_FULL], n_full);
 }
@@ -1313,6 +1314,7 @@ cudaError_t launch_batch(const BatchArgs& a, cudaStream_t s, int num_sms, cudaEv
         // one fused launch: probes inline, no grouping and no probe records
         if ((e = mark(1)) != cudaSuccess) return e;
         if ((e = mark(2)) != cudaSuccess) return e;
+        if ((e = mark(3)) != cudaSuccess) return e;
         if (a.n > 0) {
             const size_t smem = eval_smem_bytes(a.max_slots);
             if (smem > 48 * 1024 &&
@@ -1321,12 +1323,12 @@ cudaError_t launch_batch(const BatchArgs& a, cudaStream_t s, int num_sms, cudaEv
             k_eval_fused<<<num_sms * 16, EVAL_WARPS * 32, smem, s>>>(a);
             nl++;
         }
-        if ((e = mark(3)) != cudaSuccess) return e;
-        if ((e = launch_insert(a, s, num_sms, &nl)) != cudaSuccess) return e;
         if ((e = mark(4)) != cudaSuccess) return e;
+        if ((e = launch_insert(a, s, num_sms, &nl)) != cudaSuccess) return e;
+        if ((e = mark(5)) != cudaSuccess) return e;
         k_finish<<<1, 32, 0, s>>>(a);
         nl++;
-        if ((e = mark(5)) != cudaSuccess) return e;
+        if ((e = mark(6)) != cudaSuccess) return e;
         if (launches) *launches += nl;
         return cudaGetLastError();
     }
@@ -1382,15 +1384,18 @@ cudaError_t launch_batch(const BatchArgs& a, cudaStream_t s, int num_sms, cudaEv
                 nl++;
             }
         }
+        if ((e = mark(3)) != cudaSuccess) return e;
         k_eval<<<num_sms * 16, EVAL_WARPS * 32, smem, s>>>(a, item_ctr);
         nl++;
+    } else if ((e = mark(3)) != cudaSuccess) {
+        return e;
     }
-    if ((e = mark(3)) != cudaSuccess) return e;
-    if ((e = launch_insert(a, s, num_sms, &nl)) != cudaSuccess) return e;
     if ((e = mark(4)) != cudaSuccess) return e;
+    if ((e = launch_insert(a, s, num_sms, &nl)) != cudaSuccess) return e;
+    if ((e = mark(5)) != cudaSuccess) return e;
     k_finish<<<1, 32, 0, s>>>(a);
     nl++;
-    if ((e = mark(5)) != cudaSuccess) return e;
+    if ((e = mark(6)) != cudaSuccess) return e;
     if (launches) *launches += nl;
     return cudaGetLastError();
 }

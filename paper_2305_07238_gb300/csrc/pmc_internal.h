@@ -119,7 +119,7 @@ constexpr uint32_t ERR_CAPACITY = 16;   // the batch needs more probe records th
 // Counter indices in the device stats array.
 enum {
     ST_LOOKUPS = 0, ST_HITS, ST_MISSES, ST_CANDIDATES, ST_INSERTED, ST_DUP, ST_FULL,
-    ST_NODES, ST_BATCHES, ST_FLOPS, ST_SLOTS, ST_POINTS, ST_BAD, ST_SURR, ST_COUNT = 16
+    ST_NODES, ST_BATCHES, ST_FLOPS, ST_SLOTS, ST_POINTS, ST_BAD, ST_SURR, ST_FLOPS_MISSED, ST_COUNT = 16
 };
 
 // Everything a batch's kernels need, by value.
@@ -174,7 +174,7 @@ constexpr uint32_t INSERT_BIN_CELLS = 512;
 
 
 // Phases timed by the optional CUDA events of a batch.
-enum { PH_SORT = 0, PH_LOOKUP, PH_EVAL, PH_INSERT, PH_FINISH, PH_COUNT };
+enum { PH_SORT = 0, PH_LOOKUP, PH_MISSED, PH_EVAL, PH_INSERT, PH_FINISH, PH_COUNT };
 
 // Launch sequence of one batch (kernels.cu).  `ev`, if not null, holds PH_COUNT + 1
 // events recorded on `s` at the phase boundaries; `*launches` counts kernel launches.

@@ -36,7 +36,7 @@ EXPORTED = (
     "pmc_autotune", "pmc_status_str",
 )
 NOALLOC_MAX_POINTS, NOALLOC_MAX_PROBES, NOALLOC_MAX_MATERIALS = 8192, 32768, 4096
-PHASES = ("sort", "lookup", "eval", "insert", "finish")
+PHASES = ("sort", "lookup", "missed", "eval", "insert", "finish")
 
 
 class PmcError(RuntimeError):
@@ -74,7 +74,7 @@ class _Points(C.Structure):
 
 STAT_FIELDS = ("lookups", "hits", "misses", "candidates", "inserted", "dropped_dup", "dropped_full",
                "nodes_evaluated", "batches", "flops", "slots_probed", "points", "bad_points",
-               "surrogate_evals")
+               "surrogate_evals", "flops_missed")
 MLP_PARAMS = 8515
 
 
