@@ -269,7 +269,8 @@ pmc_status pmc_read_timing(pmc_cache* cache, double* ms, uint64_t* kernel_launch
  *   value = clamp(y, 0, 1).
  * Parameters: PMC_MLP_PARAMS floats, W1 [64][64], b1 [64], W2 [64][64], b2 [64],
  * W3 [64][3], b3 [3].  Products take BF16 operands and accumulate in FP32 on tensor
- * cores; FP32 master weights take Adam steps.  Per material the candidate node is its
+ * cores (inference: tcgen05.mma with tensor-memory accumulators; training: mma.sync);
+ * FP32 master weights take Adam steps.  Per material the candidate node is its
  * most expensive cacheable node with no cacheable node below it.  A node with an enabled
  * surrogate is not probed: every pass evaluates the network for it. */
 #define PMC_MLP_PARAMS 8515u
@@ -306,7 +307,9 @@ pmc_status pmc_get_surrogate(pmc_cache* cache, uint32_t mat, float* theta, uint3
 pmc_status pmc_use_surrogates(pmc_cache* cache, int enable);
 
 /* Stand-alone network, DEVICE arrays: values of n points (planar 3 x n), clamped to
- * [0, 1] if clamp != 0.  Asynchronous on `stream`. */
+ * [0, 1] if clamp != 0.  Evaluated like the in-pass inference on the tcgen05 tensor
+ * cores (BF16 operands, FP32 accumulators in tensor memory).  Asynchronous on `stream`;
+ * if a bounded wait for the tensor cores runs out, the affected outputs are NaN. */
 pmc_status pmc_mlp_forward(const float* theta, const float* u, const float* v, uint64_t n,
                            float* out, int clamp, void* stream);
 

@@ -14,7 +14,9 @@ struct pmc_cache {
     int use_cache = 1;
     uint32_t n_mats = 0;
     uint32_t max_roots = 0;
-    uint32_t max_slots = 0;
+    uint32_t max_slots = 0;         // per-point programs (k_eval, k_eval_fused)
+    uint32_t max_slots_roots = 0;   // standalone cacheable-node programs (k_eval_roots, sampling)
+    uint32_t max_slots_outer = 0;   // outer programs (k_eval once every block has its value)
     int num_sms = 0;
     std::vector<MatInfo> mat_info;
     std::vector<uint32_t> roots;

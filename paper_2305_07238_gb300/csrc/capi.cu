@@ -217,6 +217,15 @@ pmc_status pmc_create_cache(const pmc_cache_desc* desc, const pmc_material* mats
             if (cand < 0 || cost > best_cost) { cand = (int32_t)r; best_cost = cost; }
         }
         c->surr_cand.push_back(cand);
+        mi.outer_start = (uint32_t)prog.size();
+        mi.outer_len = (uint32_t)cm.outer_prog.size();
+        mi.outer_out_slot = cm.outer_out_slot;
+        mi.outer_slots = cm.outer_slots;
+        for (uint4 ins : cm.outer_prog) {
+            if ((ins.x & 0xFFu) != OP_LOAD_ROOT) ins.w += pbase;
+            prog.push_back(ins);
+        }
+        c->max_slots_outer = std::max(c->max_slots_outer, cm.outer_slots);
         for (size_t r = 0; r < cm.roots.size(); ++r) {
             RootInfo ri{};
             ri.prog_start = (uint32_t)prog.size();
@@ -234,7 +243,7 @@ pmc_status pmc_create_cache(const pmc_cache_desc* desc, const pmc_material* mats
             }
             c->root_info.push_back(ri);
             c->max_level = std::max(c->max_level, ri.level);
-            c->max_slots = std::max(c->max_slots, ri.n_slots);
+            c->max_slots_roots = std::max(c->max_slots_roots, ri.n_slots);
         }
         params.insert(params.end(), cm.params.begin(), cm.params.end());
         c->roots.insert(c->roots.end(), cm.roots.begin(), cm.roots.end());
@@ -246,9 +255,9 @@ pmc_status pmc_create_cache(const pmc_cache_desc* desc, const pmc_material* mats
     // the interpreters fetch eight parameters ahead of a node, even one without any
     params.resize(((params.size() + 3) & ~size_t(3)) + 8, 0.0f);
     if (c->max_level >= MAX_LEVELS) c->split = 0;   // deeper nesting: evaluate misses inline
-    if (eval_smem_bytes(c->max_slots) > 200u * 1024u) {
+    if (eval_smem_bytes(std::max(c->max_slots, c->max_slots_roots)) > 200u * 1024u) {
         fprintf(stderr, "pmc: a material needs %u live values; this build supports %zu\n",
-                c->max_slots, (size_t)(200u * 1024u) / eval_smem_bytes(1));
+                std::max(c->max_slots, c->max_slots_roots), (size_t)(200u * 1024u) / eval_smem_bytes(1));
         delete c;
         return PMC_ERR_UNSUPPORTED;
     }
@@ -341,6 +350,8 @@ pmc_status enqueue_batch(pmc_cache* c, const pmc_points* pts, float* out_rgb, ui
     a.mats = c->d_mats; a.n_mats = c->n_mats;
     a.prog = c->d_prog; a.params = c->d_params; a.roots = c->d_roots;
     a.max_slots = c->max_slots ? c->max_slots : 1;
+    a.max_slots_roots = c->max_slots_roots ? c->max_slots_roots : 1;
+    a.max_slots_outer = c->max_slots_outer ? c->max_slots_outer : 1;
     const size_t M1 = (size_t)c->n_mats + 1;
     a.counts = c->d_seg; a.seg_start = c->d_seg + M1; a.probe_base = c->d_seg + 2 * M1;
     a.item_base = c->d_seg + 3 * M1; a.cursor = c->d_seg + 4 * M1;
@@ -733,7 +744,7 @@ pmc_status pmc_train_surrogates(pmc_cache* c, const pmc_train_desc* d, float* rm
     // training pairs from the exact evaluator
     if (e == cudaSuccess)
         e = launch_root_samples(c->d_prog, c->d_params, c->d_rinfo, groots, L, d->n_train, d->seed, data,
-                                c->max_slots ? c->max_slots : 1, c->num_sms, s);
+                                c->max_slots_roots ? c->max_slots_roots : 1, c->num_sms, s);
     const uint32_t steps_per_epoch = d->n_train / 128u;
     const uint32_t total = steps_per_epoch * d->epochs;
     const float lr = d->lr > 0.0f ? d->lr : 1e-2f;
@@ -747,7 +758,7 @@ pmc_status pmc_train_surrogates(pmc_cache* c, const pmc_train_desc* d, float* rm
     std::vector<float> valid((size_t)nv * 5), out((size_t)3 * nv);
     if (e == cudaSuccess)
         e = launch_root_samples(c->d_prog, c->d_params, c->d_rinfo, groots, L, nv, d->seed ^ 0x5DEECE66Dull, data,
-                                c->max_slots ? c->max_slots : 1, c->num_sms, s);
+                                c->max_slots_roots ? c->max_slots_roots : 1, c->num_sms, s);
     std::vector<float> host_data((size_t)L * nv * 5);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(host_data.data(), data, host_data.size() * sizeof(float), cudaMemcpyDeviceToHost, s);
@@ -764,7 +775,8 @@ pmc_status pmc_train_surrogates(pmc_cache* c, const pmc_train_desc* d, float* rm
         }
         e = cudaMemcpy(du, uu.data(), nv * sizeof(float), cudaMemcpyHostToDevice);
         if (e == cudaSuccess) e = cudaMemcpy(dv, vv.data(), nv * sizeof(float), cudaMemcpyHostToDevice);
-        if (e == cudaSuccess) e = launch_mlp_forward(theta + (size_t)i * MLP_PARAMS, du, dv, nv, pred, 1, c->num_sms, s);
+        if (e == cudaSuccess)
+            e = launch_mlp_forward_tc(theta + (size_t)i * MLP_PARAMS, du, dv, nv, pred, 1, &c->d_ctl->err, c->num_sms, s);
         if (e == cudaSuccess) e = cudaMemcpyAsync(out.data(), pred, out.size() * sizeof(float), cudaMemcpyDeviceToHost, s);
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);
         if (e != cudaSuccess) break;
@@ -843,7 +855,7 @@ pmc_status pmc_mlp_forward(const float* theta, const float* u, const float* v, u
     int dev = 0, sms = 1;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaError_t e = launch_mlp_forward(theta, u, v, (uint32_t)n, out, clamp, sms, (cudaStream_t)stream);
+    cudaError_t e = launch_mlp_forward_tc(theta, u, v, (uint32_t)n, out, clamp, nullptr, sms, (cudaStream_t)stream);
     return e == cudaSuccess ? PMC_OK : cuda_fail(nullptr, e);
 }
 

@@ -519,6 +519,35 @@ bool compile_material(const pmc_node* nodes_in, uint32_t n, uint32_t min_root_no
         out->root_out_slot[ri] = os;
         if (out->root_slots[ri] >= NO_SLOT) { *why = "too many live values"; return false; }
     }
+
+    // ---- outer program: the per-point program with every block replaced by a load of
+    // its cacheable node's value (used when all of them have values before evaluation)
+    {
+        std::vector<std::pair<uint32_t, bool>> order_o;
+        for (size_t p = 0; p < order.size(); ++p) {
+            if (order[p].begin) {
+                order_o.push_back({order[p].node, true});
+                p += members[order[p].node].size();   // the block: exclusive nodes + the node
+                continue;
+            }
+            order_o.push_back({order[p].node, false});
+        }
+        // drop what only blocks consumed (every load stays: it also counts the node's hit)
+        std::vector<char> need(n, 0);
+        need[out_node] = 1;
+        for (size_t p = order_o.size(); p-- > 0;) {
+            if (order_o[p].second || !need[order_o[p].first]) continue;
+            for (int k = 0; k < 4; ++k)
+                if (g[order_o[p].first].in[k] >= 0) need[g[order_o[p].first].in[k]] = 1;
+        }
+        std::vector<std::pair<uint32_t, bool>> kept;
+        for (auto& e : order_o)
+            if (need[e.first] || e.second) kept.push_back(e);
+        uint32_t os = 0;
+        out->outer_slots = emit_standalone(g, kept, ordinal, out_node, false, &out->outer_prog, &out->params, &os);
+        out->outer_out_slot = os;
+        if (out->outer_slots >= NO_SLOT) { *why = "too many live values"; return false; }
+    }
     return true;
 }
 

@@ -428,7 +428,10 @@ __global__ void __launch_bounds__(EVAL_WARPS * 32) k_eval(BatchArgs a, uint32_t*
     init_gradients(s_grad);
     __syncthreads();
     const uint32_t warp = threadIdx.x >> 5, lane = lane_id();
-    float* V = s_val + (size_t)warp * a.max_slots * 96u + lane;
+    // when the batched evaluation has given every cacheable node a value, the outer
+    // program runs: each block replaced by a load of its node's record
+    const bool outer = a.split && !a.keys_inline;
+    float* V = s_val + (size_t)warp * (outer ? a.max_slots_outer : a.max_slots) * 96u + lane;
     const uint32_t n_items = a.ctl->n_items;
     unsigned long long n_nodes = 0, n_flops = 0, n_cand = 0, n_full = 0, n_look = 0;
     for (;;) {
@@ -450,7 +453,8 @@ __global__ void __launch_bounds__(EVAL_WARPS * 32) k_eval(BatchArgs a, uint32_t*
             orig = a.sidx[s];
         }
         const MatInfo mi = a.mats[m];
-        const uint4* prog = a.prog + mi.prog_start;
+        const uint4* prog = a.prog + (outer ? mi.outer_start : mi.prog_start);
+        const uint32_t out_slot = outer ? mi.outer_out_slot : mi.out_slot;
         const uint32_t pbase = __ldg(&a.probe_base[m]);
         int skip_end = -1;          // lane inactive while pc <= skip_end
         uint32_t hits = 0, cand_cell = 0, cand_h2 = 0, cand_node = 0, cand_start = 0;
@@ -461,12 +465,30 @@ __global__ void __launch_bounds__(EVAL_WARPS * 32) k_eval(BatchArgs a, uint32_t*
             iv = d_texel(pt.v, a.level);
         }
         // the next instruction is fetched while the current one executes
-        const int len = (int)mi.prog_len;
+        const int len = (int)(outer ? mi.outer_len : mi.prog_len);
         uint4 nxt = len > 0 ? __ldg(&prog[0]) : make_uint4(0, 0, 0, 0);
         for (int pc = 0; pc < len; ++pc) {
             const uint4 ins = nxt;
             if (pc + 1 < len) nxt = __ldg(&prog[pc + 1]);
             const uint32_t op = ins.x & 0xFFu;
+            if (op == OP_LOAD_ROOT) {
+                // outer program: a hit, or a value computed this pass by the batched
+                // evaluation or a learned surrogate
+                const uint32_t slot = ins.y & 0xFFFFu, r = ins.y >> 16;
+                if (valid) {
+                    const float4 rec = a.probes[(size_t)pbase + (size_t)r * cnt + j];
+                    const uint32_t state = __float_as_uint(rec.w);
+                    if (state == PROBE_HIT || state == PROBE_COMPUTED) {
+                        V[(slot * 3 + 0) * 32] = rec.x;
+                        V[(slot * 3 + 1) * 32] = rec.y;
+                        V[(slot * 3 + 2) * 32] = rec.z;
+                        hits += state == PROBE_HIT ? 1u : 0u;
+                    } else {
+                        atomicOr(&a.ctl->err, ERR_BOUNDS);   // the batched evaluation missed it
+                    }
+                }
+                continue;
+            }
             if (op == OP_ROOT_BEGIN) {
                 const uint32_t slot = ins.y & 0xFFFFu, r = ins.y >> 16;
                 bool need = valid;
@@ -531,9 +553,9 @@ __global__ void __launch_bounds__(EVAL_WARPS * 32) k_eval(BatchArgs a, uint32_t*
             }
         }
         if (valid) {
-            a.out_rgb[orig] = V[(mi.out_slot * 3) * 32];
-            a.out_rgb[(size_t)a.n + orig] = V[(mi.out_slot * 3 + 1) * 32];
-            a.out_rgb[2 * (size_t)a.n + orig] = V[(mi.out_slot * 3 + 2) * 32];
+            a.out_rgb[orig] = V[(out_slot * 3) * 32];
+            a.out_rgb[(size_t)a.n + orig] = V[(out_slot * 3 + 1) * 32];
+            a.out_rgb[2 * (size_t)a.n + orig] = V[(out_slot * 3 + 2) * 32];
             if (a.out_hits) a.out_hits[orig] = (uint16_t)min(hits, 65535u);
         }
     }
@@ -722,7 +744,7 @@ __global__ void __launch_bounds__(EVAL_WARPS * 32) k_eval_roots(BatchArgs a, uin
     init_gradients(s_grad);
     __syncthreads();
     const uint32_t warp = threadIdx.x >> 5, lane = lane_id();
-    float* V = s_val + (size_t)warp * a.max_slots * 96u + lane;
+    float* V = s_val + (size_t)warp * a.max_slots_roots * 96u + lane;
     const uint32_t n_items = a.ctl->n_root_items;
     unsigned long long n_nodes = 0, n_flops = 0, n_cand = 0, n_full = 0;
     for (;;) {
@@ -1368,19 +1390,22 @@ cudaError_t launch_batch(const BatchArgs& a, cudaStream_t s, int num_sms, cudaEv
     }
     if ((e = mark(2)) != cudaSuccess) return e;
     if (a.n > 0) {
-        const size_t smem = eval_smem_bytes(a.max_slots);
-        if (smem > 48 * 1024) {
-            if ((e = cudaFuncSetAttribute(k_eval, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
-                return e;
-            if ((e = cudaFuncSetAttribute(k_eval_roots, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
-                return e;
-        }
+        const bool outer = a.use_cache && a.split && !a.keys_inline;
+        const size_t smem = eval_smem_bytes(outer ? a.max_slots_outer : a.max_slots),
+                     smem_roots = eval_smem_bytes(a.max_slots_roots);
+        if (smem > 48 * 1024 &&
+            (e = cudaFuncSetAttribute(k_eval, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
+            return e;
+        if (smem_roots > 48 * 1024 &&
+            (e = cudaFuncSetAttribute(k_eval_roots, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_roots)) !=
+                cudaSuccess)
+            return e;
         if (a.use_cache && a.split && !a.keys_inline) {
             k_scan_roots<<<1, 1024, 0, s>>>(a);
             nl++;
             // the level counters live after the per-root miss counters
             for (uint32_t lv = 0; lv <= a.max_level; ++lv) {
-                k_eval_roots<<<num_sms * 16, EVAL_WARPS * 32, smem, s>>>(a, lv, a.miss_cnt + a.n_roots_total + lv);
+                k_eval_roots<<<num_sms * 16, EVAL_WARPS * 32, smem_roots, s>>>(a, lv, a.miss_cnt + a.n_roots_total + lv);
                 nl++;
             }
         }

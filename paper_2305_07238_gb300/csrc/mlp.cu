@@ -398,35 +398,6 @@ __global__ void __launch_bounds__(256) k_mlp_train(TrainArgs A) {
     if (lane == 0) atomicAdd(&A.loss[mat], loss);
 }
 
-// Forward of the network for 16-row tiles; rows from (u, v) arrays.  Output: planar
-// (3 x n) values clamped to [0, 1] when `clamp` (the node's range), raw otherwise.
-__global__ void __launch_bounds__(256) k_mlp_forward(const float* __restrict__ theta, const float* __restrict__ u,
-                                                     const float* __restrict__ v, uint32_t n, float* out, int clamp) {
-    extern __shared__ __align__(16) unsigned char sm[];
-    load_weights(sm, theta, false);
-    __syncthreads();
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
-    const float* bias = at<float>(sm, Smem::bias);
-    const uint32_t tiles = (n + 15) / 16;
-    for (uint32_t tile = blockIdx.x * 8 + warp; tile < tiles; tile += gridDim.x * 8) {
-        const uint32_t r0 = tile * 16 + g, r1 = r0 + 8;
-        const float u0 = r0 < n ? u[r0] : 0.0f, v0 = r0 < n ? v[r0] : 0.0f;
-        const float u1 = r1 < n ? u[r1] : 0.0f, v1 = r1 < n ? v[r1] : 0.0f;
-        uint32_t a0[4][4], a1[4][4], a2[4][4];
-        features(u0, v0, u1, v1, a0, nullptr, 0);
-        hidden(a0, at<__nv_bfloat16>(sm, Smem::w1t), bias, a1, nullptr, 0);
-        hidden(a1, at<__nv_bfloat16>(sm, Smem::w2t), bias + 64, a2, nullptr, 0);
-        float y[4];
-        output(a2, at<__nv_bfloat16>(sm, Smem::w3t), bias + 128, y);
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            const int o = 2 * t + (k & 1);
-            const uint32_t r = (k >> 1) ? r1 : r0;
-            if (o < 3 && r < n) out[(size_t)o * n + r] = clamp ? __saturatef(y[k]) : y[k];
-        }
-    }
-}
-
 // Training pairs of the exact evaluator: uniform (u, v) from a counter-based generator
 // (SplitMix64 of seed ^ (material, row)), value = the cacheable node's standalone program.
 __global__ void __launch_bounds__(128) k_root_samples(const uint4* __restrict__ prog, const float* __restrict__ params,
@@ -473,68 +444,7 @@ __global__ void __launch_bounds__(128) k_root_samples(const uint4* __restrict__ 
     }
 }
 
-// In-pass inference: a block takes 128 grouped points of one material whose cacheable
-// node has a learned surrogate, evaluates the network and writes the node's value into
-// the points' probe records.
-__global__ void __launch_bounds__(256) k_surrogate(BatchArgs a) {
-    extern __shared__ __align__(16) unsigned char sm[];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
-    const float* bias = at<float>(sm, Smem::bias);
-    const uint32_t n_items = a.ctl->n_surr_items;
-    uint32_t loaded = 0xFFFFFFFFu;
-    unsigned long long n_eval = 0;
-    for (uint32_t item = blockIdx.x; item < n_items; item += gridDim.x) {
-        uint32_t lo = 0, hi = a.n_mats;   // largest m with surr_item_base[m] <= item
-        while (hi - lo > 1) {
-            const uint32_t mid = (lo + hi) >> 1;
-            if (a.surr_item_base[mid] <= item) lo = mid;
-            else hi = mid;
-        }
-        const uint32_t m = lo;
-        if (m != loaded) {
-            __syncthreads();
-            load_weights(sm, a.surr_theta + (size_t)a.surr_slot[m] * MLP_PARAMS, false);
-            __syncthreads();
-            loaded = m;
-        }
-        const uint32_t cnt = a.counts[m], r = (uint32_t)a.surr_ord[m];
-        const uint32_t jb = (item - a.surr_item_base[m]) * 128u + warp * 16u;
-        const uint32_t j0 = jb + g, j1 = j0 + 8;
-        const uint32_t s0 = a.seg_start[m];
-        const float u0 = j0 < cnt ? a.su[s0 + j0] : 0.0f, v0 = j0 < cnt ? a.sv[s0 + j0] : 0.0f;
-        const float u1 = j1 < cnt ? a.su[s0 + j1] : 0.0f, v1 = j1 < cnt ? a.sv[s0 + j1] : 0.0f;
-        uint32_t a0[4][4], a1[4][4], a2[4][4];
-        features(u0, v0, u1, v1, a0, nullptr, 0);
-        hidden(a0, at<__nv_bfloat16>(sm, Smem::w1t), bias, a1, nullptr, 0);
-        hidden(a1, at<__nv_bfloat16>(sm, Smem::w2t), bias + 64, a2, nullptr, 0);
-        float y[4];
-        output(a2, at<__nv_bfloat16>(sm, Smem::w3t), bias + 128, y);
-        // gather the three outputs of each row to the lane with t == 0 (columns 0..2 live
-        // in lanes t = 0 (0, 1) and t = 1 (2))
-        const float o2r0 = __shfl_down_sync(FULL, y[0], 1), o2r1 = __shfl_down_sync(FULL, y[2], 1);
-        if (t == 0) {
-            const size_t base = (size_t)a.probe_base[m] + (size_t)r * cnt;
-            if (j0 < cnt) {
-                a.probes[base + j0] = make_float4(__saturatef(y[0]), __saturatef(y[1]), __saturatef(o2r0), __uint_as_float(3u));
-                n_eval++;
-            }
-            if (j1 < cnt) {
-                a.probes[base + j1] = make_float4(__saturatef(y[2]), __saturatef(y[3]), __saturatef(o2r1), __uint_as_float(3u));
-                n_eval++;
-            }
-        }
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) n_eval += __shfl_xor_sync(FULL, n_eval, o);
-    if (lane == 0 && n_eval) atomicAdd(&a.stats[ST_SURR], n_eval);
-}
-
 }  // namespace
-
-cudaError_t launch_surrogate(const BatchArgs& a, int num_sms, cudaStream_t s) {
-    k_surrogate<<<num_sms * 4, 256, Smem::infer_end, s>>>(a);
-    return cudaGetLastError();
-}
 
 size_t mlp_train_smem() { return Smem::train_end; }
 size_t mlp_infer_smem() { return Smem::infer_end; }
@@ -547,16 +457,6 @@ cudaError_t launch_mlp_train(float* theta, float* adam_m, float* adam_v, float* 
     cudaError_t e = cudaFuncSetAttribute(k_mlp_train, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Smem::train_end);
     if (e != cudaSuccess) return e;
     k_mlp_train<<<dim3(splits, n_mats), 256, Smem::train_end, s>>>(A);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_mlp_forward(const float* theta, const float* u, const float* v, uint32_t n, float* out, int clamp,
-                               int num_sms, cudaStream_t s) {
-    const uint32_t tiles = (n + 15) / 16;
-    uint32_t blocks = (tiles + 7) / 8;
-    if (blocks > (uint32_t)num_sms * 4u) blocks = (uint32_t)num_sms * 4u;
-    if (blocks == 0) return cudaSuccess;
-    k_mlp_forward<<<blocks, 256, Smem::infer_end, s>>>(theta, u, v, n, out, clamp);
     return cudaGetLastError();
 }
 

@@ -110,6 +110,8 @@ extern "C" pmc_status pmc_eval_batch_noalloc(pmc_cache* c, const pmc_points* pts
     a.mats = c->d_mats; a.n_mats = c->n_mats;
     a.prog = c->d_prog; a.params = c->d_params; a.roots = c->d_roots;
     a.max_slots = c->max_slots ? c->max_slots : 1;
+    a.max_slots_roots = c->max_slots_roots ? c->max_slots_roots : 1;
+    a.max_slots_outer = c->max_slots_outer ? c->max_slots_outer : 1;
     uint32_t* seg = reinterpret_cast<uint32_t*>(base + OFF_SEG);
     const size_t M1 = (size_t)c->n_mats + 1;
     a.counts = seg; a.seg_start = seg + M1; a.probe_base = seg + 2 * M1;

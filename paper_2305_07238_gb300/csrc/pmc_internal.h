@@ -51,6 +51,10 @@ struct MatInfo {
     uint32_t out_slot;    // slot holding the material output after the program
     uint32_t n_slots;
     uint32_t n_nodes;
+    uint32_t outer_start; // outer program: blocks replaced by loads of their node's record
+    uint32_t outer_len;
+    uint32_t outer_out_slot;
+    uint32_t outer_slots;
     uint32_t pad;
 };
 
@@ -62,6 +66,9 @@ struct CompiledMaterial {
     std::vector<uint32_t> root_level;
     std::vector<uint32_t> root_slots;
     std::vector<uint32_t> root_out_slot;
+    std::vector<uint4> outer_prog;    // the program with each block replaced by OP_LOAD_ROOT
+    uint32_t outer_slots = 0;
+    uint32_t outer_out_slot = 0;
     uint32_t out_slot = 0;
     uint32_t n_slots = 0;
     uint32_t n_nodes = 0;
@@ -134,7 +141,9 @@ struct BatchArgs {
     // materials
     const MatInfo* mats; uint32_t n_mats;
     const uint4* prog; const float* params; const uint32_t* roots;
-    uint32_t max_slots;
+    uint32_t max_slots;        // value slots of the largest per-point program
+    uint32_t max_slots_roots;  // value slots of the largest standalone cacheable-node program
+    uint32_t max_slots_outer;  // value slots of the largest outer program
     // sort / segments
     uint32_t* counts; uint32_t* seg_start; uint32_t* probe_base; uint32_t* item_base;
     uint32_t* cursor;
@@ -194,8 +203,9 @@ cudaError_t launch_mlp_train(float* theta, float* adam_m, float* adam_v, float* 
                              uint32_t n_mats, uint32_t n_data, uint32_t steps, uint64_t sample0, uint32_t step0,
                              uint32_t total_steps, float lr, float grad_scale, int mode, uint32_t splits,
                              cudaStream_t s);
-cudaError_t launch_mlp_forward(const float* theta, const float* u, const float* v, uint32_t n, float* out, int clamp,
-                               int num_sms, cudaStream_t s);
+// Tensor-core (tcgen05) inference (mlp_tc.cu); err may be null.
+cudaError_t launch_mlp_forward_tc(const float* theta, const float* u, const float* v, uint32_t n, float* out, int clamp,
+                                  uint32_t* err, int num_sms, cudaStream_t s);
 cudaError_t launch_root_samples(const uint4* prog, const float* params, const RootInfo* rinfo, const uint32_t* groots,
                                 uint32_t n_train_mats, uint32_t n_rows, uint64_t seed, float* data, uint32_t max_slots,
                                 int num_sms, cudaStream_t s);
