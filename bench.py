@@ -309,6 +309,8 @@ def ours(args, rank, world, local_rank, dist):
         line["surrogate"] = surrogate_leg(torch, P, dev, local_rank, seed=rank)
     if "f128" in legs:
         line["frame128"] = frame128_leg(torch, P, dev, local_rank, seed=rank)
+    if "sweep" in legs:
+        line["scale_sweep"] = sweep_leg(torch, P, dev, local_rank, seed=rank)
     if rank == 0 and not args.no_cpu_baseline and "cpu" in legs:
         line["cpu_baseline"], line["max_abs_err_vs_fp64"] = cpu_baseline(P, torch, mats, frame, dev)
     return line
@@ -393,6 +395,76 @@ def frame128_leg(torch, P, dev, local_rank, seed=0):
     res["speedup_cached_over_uncached"] = round(best / max(res["uncached_graph_grouped"],
                                                            res["uncached_graph_unsorted"]), 3)
     res["graph_over_eager"] = round(res["graph_grouped"] / res["eager"], 3)
+    del passes
+    torch.cuda.empty_cache()
+    return res
+
+
+SCALE_MATS, SCALE_LO, SCALE_HI, SCALE_SP, SCALE_ZIPF, SCALE_SIDE, SCALE_BATCHES = 4096, 10, 2000, 0.4, 0.9, 2048, 64
+
+
+def sweep_leg(torch, P, dev, local_rank, seed=0):
+    """The scale configuration: 4096 networks of 10-2000 nodes (40 % SP), materials
+    Zipf(0.9) per 8x8 tile of a 2048x2048 stream, 2^28 points in 64 batches of 2^22; the
+    table swept from 2^20 to 2^29 slots (16 MB - 8 GB).  Per size: points/s of the whole
+    stream replayed as one CUDA graph, hit rate, inserted and dropped counts.  Then the
+    surrogate mix at 2^26 slots: networks trained for every material's candidate node,
+    the ones within RMSE 2e-3 enabled."""
+    from paper_2305_07238_gb300 import pmc as Pm
+    t0 = time.perf_counter()
+    mats = W.random_materials(SCALE_MATS, SCALE_LO, SCALE_HI, SCALE_SP, seed=seed + 500)
+    frame = W.Frame(W.FrameSpec(width=SCALE_SIDE, height=SCALE_SIDE, n_mats=SCALE_MATS, zipf_s=SCALE_ZIPF,
+                                seed=seed + 500))
+    passes = [frame.points_torch(p, dev) for p in range(SCALE_BATCHES)]
+    n = SCALE_SIDE * SCALE_SIDE
+    roots = np.array([len(P.analyze_material(m)["roots"]) for m in mats])
+    need = int(roots[frame.tile_mat[frame.pix_tile]].sum())
+    outs = torch.empty((3, n), dtype=torch.float32, device=dev)
+    hits = torch.empty(n, dtype=torch.int16, device=dev)
+    total = n * SCALE_BATCHES
+    res = {"config": f"{SCALE_MATS} materials {SCALE_LO}-{SCALE_HI} nodes ({int(SCALE_SP * 100)}% SP), "
+                     f"Zipf {SCALE_ZIPF} per 8x8 tile of {SCALE_SIDE}x{SCALE_SIDE}, {SCALE_BATCHES} batches of {n} "
+                     f"points ({total} points)",
+           "unit": UNIT, "probes_per_batch": need, "setup_s": round(time.perf_counter() - t0, 1)}
+
+    def rate(c):
+        g = c.graph(passes, [outs] * SCALE_BATCHES, [hits] * SCALE_BATCHES, reset=True)
+        g.launch()
+        c.sync()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        g.launch()
+        e1.record()
+        torch.cuda.synchronize()
+        g.close()
+        return total / (e0.elapsed_time(e1) / 1e3)
+
+    u = P.Cache(mats, 1 << 17, N_ENTRIES, uv_level=LEVEL, flags=Pm.PMC_CACHE_OFF, device=local_rank)
+    res["uncached"] = round(rate(u), 1)
+    u.close()
+    rows = []
+    for log_slots in range(20, 30):
+        c = P.Cache(mats, 1 << (log_slots - 3), N_ENTRIES, uv_level=LEVEL, device=local_rank, probe_capacity=need)
+        r = rate(c)
+        s = c.stats()
+        rows.append({"slots": 1 << log_slots, "table_mb": (16 << log_slots) >> 20, "value": round(r, 1),
+                     "hit_rate": round(s["hits"] / max(1, s["lookups"]), 4), "inserted": s["inserted"],
+                     "dropped_full": s["dropped_full"], "speedup_over_uncached": round(r / res["uncached"], 3)})
+        c.close()
+    res["sweep"] = rows
+    c = P.Cache(mats, 1 << 23, N_ENTRIES, uv_level=LEVEL, device=local_rank, probe_capacity=need)
+    t = time.perf_counter()
+    rmse = c.train_surrogates(n_train=1 << 16, n_valid=1 << 13, epochs=16, lr=1e-2, seed=2)
+    torch.cuda.synchronize()
+    res["surrogate_mix"] = {"slots": 1 << 26, "train_s": round(time.perf_counter() - t, 2),
+                            "candidates": int(np.sum(rmse >= 0)),
+                            "enabled": int(np.sum((rmse >= 0) & (rmse <= 2e-3))),
+                            "value": round(rate(c), 1)}
+    s = c.stats()
+    res["surrogate_mix"]["hit_rate"] = round(s["hits"] / max(1, s["lookups"]), 4)
+    res["surrogate_mix"]["surrogate_evals"] = s["surrogate_evals"]
+    c.close()
     del passes
     torch.cuda.empty_cache()
     return res
@@ -584,7 +656,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--legs", default="cached,uncached,e2e,surr,f128,cpu",
-                    help="comma list of cached, uncached, e2e, surr, f128, cpu (profiling runs take 'cached')")
+                    help="comma list of cached, uncached, e2e, surr, f128, sweep, cpu (sweep is not in the "
+                         "default: about a minute more; profiling runs take 'cached')")
     ap.add_argument("--profile", action="store_true",
                     help="eager frames only, for ncu launch lists (prints launches per frame)")
     args = ap.parse_args()

@@ -128,6 +128,9 @@ typedef struct {
                                      consecutive points, one material at a time, and
                                      probes the table inline (same results; not
                                      combinable with learned surrogates)               */
+#define PMC_PROBE_INLINE 0x40u    /* grouped by material, the evaluator probes the
+                                     table itself when it reaches a cacheable node: no
+                                     lookup kernel and no probe records (same results) */
 
 typedef struct {
     uint64_t n_cells;        /* N_c >= 1, < 2^32                                  */
@@ -214,7 +217,9 @@ pmc_status pmc_table_dump(pmc_cache* cache, void* host_dst, size_t bytes);
 
 /* Synchronises and copies, for the last batch, one 64-bit mask per point (host
  * memory, n entries, original point order): bit r set when the point's r-th
- * cacheable node (ascending node ID, r < 64) was found in the table. */
+ * cacheable node (ascending node ID, r < 64) was found in the table.  Returns
+ * PMC_ERR_UNSUPPORTED after a batch that kept no probe records (PMC_UNSORTED or
+ * PMC_PROBE_INLINE schedules). */
 pmc_status pmc_last_hit_masks(pmc_cache* cache, uint64_t* host_dst, uint64_t n);
 
 /* Empties the table and clears the counters (enqueued on `stream`). */
@@ -368,7 +373,8 @@ pmc_status pmc_eval_batch_noalloc(pmc_cache* cache, const pmc_points* pts, float
  * None of these change results: every schedule produces the same outputs, hit counts,
  * counters and table, bit for bit. */
 typedef struct {
-    uint32_t flags;     /* subset of PMC_EVAL_INLINE | PMC_INSERT_ROUNDS | PMC_UNSORTED  */
+    uint32_t flags;     /* subset of PMC_EVAL_INLINE | PMC_INSERT_ROUNDS | PMC_UNSORTED |
+                           PMC_PROBE_INLINE                                             */
     uint32_t lookup_rb; /* probes in flight per lane in the lookup kernel: 1, 2 or 4    */
 } pmc_schedule;
 

@@ -24,6 +24,7 @@ struct pmc_cache {
     uint32_t max_level = 0;
     int split = 1;
     int unsorted = 0;                     // PMC_UNSORTED schedule
+    int probe_inline = 0;                 // PMC_PROBE_INLINE schedule
     uint32_t lookup_rb = 4;               // probes in flight per lane in k_lookup
     uint64_t layout_gen = 1;              // bumped whenever a recorded graph would go stale
     uint32_t prog_len = 0;

@@ -182,6 +182,7 @@ pmc_status pmc_create_cache(const pmc_cache_desc* desc, const pmc_material* mats
     c->use_cache = off ? 0 : 1;
     c->split = (desc->flags & PMC_EVAL_INLINE) ? 0 : 1;
     c->unsorted = (desc->flags & PMC_UNSORTED) ? 1 : 0;
+    c->probe_inline = (desc->flags & PMC_PROBE_INLINE) ? 1 : 0;
     c->n_mats = n_mats;
 
     std::vector<uint4> prog;
@@ -382,6 +383,7 @@ pmc_status enqueue_batch(pmc_cache* c, const pmc_points* pts, float* out_rgb, ui
     a.rinfo = c->d_rinfo; a.n_roots_total = (uint32_t)c->root_info.size(); a.max_level = c->max_level;
     a.miss_cnt = c->d_miss_cnt; a.root_item_base = c->d_root_items; a.misslist = c->d_misslist;
     a.unsorted = c->unsorted;
+    a.probe_inline = c->probe_inline;
     a.lookup_rb = c->lookup_rb;
     cudaEvent_t* ev = nullptr;
     if (c->timing && !recording) {
@@ -399,7 +401,7 @@ pmc_status enqueue_batch(pmc_cache* c, const pmc_points* pts, float* out_rgb, ui
     if (e != cudaSuccess) return cuda_fail(c, e);
     if (c->use_cache) c->epoch_host += ne + 1;
     c->last_all_miss = a.keys_inline != 0;
-    c->last_unsorted = a.unsorted != 0;
+    c->last_unsorted = a.unsorted != 0 || (a.probe_inline != 0 && a.use_cache);
     if (n > 0) c->table_empty = false;
     c->last_stream = s;
     c->last_n = n;
@@ -896,20 +898,21 @@ pmc_status pmc_compute_keys(const uint32_t* mat, const uint32_t* node, const flo
 pmc_status pmc_get_schedule(const pmc_cache* c, pmc_schedule* out) {
     if (!c || !out) return PMC_ERR_INVALID_ARG;
     out->flags = (c->split ? 0u : PMC_EVAL_INLINE) | ((c->desc.flags & PMC_INSERT_ROUNDS) ? PMC_INSERT_ROUNDS : 0u) |
-                 (c->unsorted ? PMC_UNSORTED : 0u);
+                 (c->unsorted ? PMC_UNSORTED : 0u) | (c->probe_inline ? PMC_PROBE_INLINE : 0u);
     out->lookup_rb = c->lookup_rb;
     return PMC_OK;
 }
 
 pmc_status pmc_set_schedule(pmc_cache* c, const pmc_schedule* sc) {
     if (!c || !sc) return PMC_ERR_INVALID_ARG;
-    const uint32_t known = PMC_EVAL_INLINE | PMC_INSERT_ROUNDS | PMC_UNSORTED;
+    const uint32_t known = PMC_EVAL_INLINE | PMC_INSERT_ROUNDS | PMC_UNSORTED | PMC_PROBE_INLINE;
     if (sc->flags & ~known) return PMC_ERR_INVALID_ARG;
     if (sc->lookup_rb != 1 && sc->lookup_rb != 2 && sc->lookup_rb != 4) return PMC_ERR_INVALID_ARG;
     if ((sc->flags & PMC_UNSORTED) && surrogates_active(c)) return PMC_ERR_UNSUPPORTED;
     if (!(sc->flags & PMC_EVAL_INLINE) && c->max_level >= MAX_LEVELS) return PMC_ERR_UNSUPPORTED;
     c->split = (sc->flags & PMC_EVAL_INLINE) ? 0 : 1;
     c->unsorted = (sc->flags & PMC_UNSORTED) ? 1 : 0;
+    c->probe_inline = (sc->flags & PMC_PROBE_INLINE) ? 1 : 0;
     c->lookup_rb = sc->lookup_rb;
     c->desc.flags = (c->desc.flags & ~PMC_INSERT_ROUNDS) | (sc->flags & PMC_INSERT_ROUNDS);
     c->layout_gen++;
@@ -1068,6 +1071,7 @@ pmc_status pmc_autotune(pmc_cache* c, const pmc_points* sample, uint32_t reps, p
         }
     }
     if (c->use_cache) cand.push_back({keep | PMC_EVAL_INLINE, 4});
+    if (c->use_cache) cand.push_back({keep | PMC_PROBE_INLINE, 4});
     if (!surrogates_active(c)) cand.push_back({keep | PMC_EVAL_INLINE | PMC_UNSORTED, 4});
     if (c->use_cache && c->max_level < MAX_LEVELS) cand.push_back({keep ^ PMC_INSERT_ROUNDS, 4});
     if (cand.empty()) cand.push_back(orig);

@@ -599,35 +599,65 @@ __device__ __forceinline__ int probe_cell(const BatchArgs& a, uint32_t cell, uin
 // the node's block, a miss evaluates it and offers the value.  No grouping pass, no
 // probe records; the table is read-only until the insert phase, so every probe sees the
 // snapshot left by the previous batch, as in the grouped pipeline.
-__global__ void __launch_bounds__(EVAL_WARPS * 32) k_eval_fused(BatchArgs a) {
+// GROUPED: the same evaluator over the material-grouped points (work items of 32 points
+// of one material from the grouping pass), so a warp runs one program; a cacheable node
+// replaced by a learned surrogate takes its value from the surrogate's record.
+template <bool GROUPED>
+__global__ void __launch_bounds__(EVAL_WARPS * 32) k_eval_fused(BatchArgs a, uint32_t* item_ctr) {
     extern __shared__ float s_val[];
     __shared__ float2 s_grad[8];
     init_gradients(s_grad);
     __syncthreads();
     const uint32_t warp = threadIdx.x >> 5, lane = lane_id();
     float* V = s_val + (size_t)warp * a.max_slots * 96u + lane;
-    const uint32_t n_chunks = (a.n + 31u) >> 5;
+    const uint32_t n_chunks = GROUPED ? a.ctl->n_items : (a.n + 31u) >> 5;
     const uint32_t ne = a.n_entries;
     unsigned long long n_nodes = 0, n_flops = 0, n_cand = 0, n_full = 0;
     unsigned long long n_look = 0, n_hit = 0, n_slots = 0, n_bad = 0;
-    for (uint32_t chunk = blockIdx.x * EVAL_WARPS + warp; chunk < n_chunks; chunk += gridDim.x * EVAL_WARPS) {
-        const uint32_t i = chunk * 32u + lane;
-        const bool in = i < a.n;
-        const uint32_t m = in ? a.mat[i] : 0u;
-        const bool ok = in && m < a.n_mats;
-        if (in && !ok) {
-            zero_output(a, i);
-            n_bad++;
+    uint32_t chunk = blockIdx.x * EVAL_WARPS + warp;
+    for (;;) {
+        if (GROUPED) {
+            uint32_t item = 0;
+            if (lane == 0) item = atomicAdd(item_ctr, 1u);
+            chunk = __shfl_sync(FULL_MASK, item, 0);
         }
+        if (chunk >= n_chunks) break;
+        uint32_t i = 0, m = 0, cnt = 0, jj = 0;   // i: the point's index in the batch
+        bool ok = false;
         PointIn pt{0, 0, 0, 0, 0, 0, 0, 0};
+        if (GROUPED) {
+            m = find_material(a.item_base, a.n_mats, chunk);
+            cnt = __ldg(&a.counts[m]);
+            jj = (chunk - __ldg(&a.item_base[m])) * 32u + lane;
+            ok = jj < cnt;
+            if (ok) {
+                const uint32_t s = __ldg(&a.seg_start[m]) + jj;
+                pt.u = a.su[s]; pt.v = a.sv[s];
+                pt.px = a.spx[s]; pt.py = a.spy[s]; pt.pz = a.spz[s];
+                pt.nx = a.snx[s]; pt.ny = a.sny[s]; pt.nz = a.snz[s];
+                i = a.sidx[s];
+            }
+        } else {
+            i = chunk * 32u + lane;
+            const bool in = i < a.n;
+            m = in ? a.mat[i] : 0u;
+            ok = in && m < a.n_mats;
+            if (in && !ok) {
+                zero_output(a, i);
+                n_bad++;
+            }
+            if (ok) {
+                pt.u = a.u[i]; pt.v = a.v[i];
+                pt.px = a.px[i]; pt.py = a.py[i]; pt.pz = a.pz[i];
+                pt.nx = a.nx[i]; pt.ny = a.ny[i]; pt.nz = a.nz[i];
+            }
+        }
         uint32_t iu = 0, iv = 0;
         if (ok) {
-            pt.u = a.u[i]; pt.v = a.v[i];
-            pt.px = a.px[i]; pt.py = a.py[i]; pt.pz = a.pz[i];
-            pt.nx = a.nx[i]; pt.ny = a.ny[i]; pt.nz = a.nz[i];
             iu = d_texel(pt.u, a.level);
             iv = d_texel(pt.v, a.level);
         }
+        const int32_t surr = (GROUPED && a.surr_ord) ? a.surr_ord[m] : -1;
         unsigned todo = __ballot_sync(FULL_MASK, ok);
         while (todo) {
             const uint32_t mg = __shfl_sync(FULL_MASK, m, __ffs(todo) - 1);
@@ -647,7 +677,17 @@ __global__ void __launch_bounds__(EVAL_WARPS * 32) k_eval_fused(BatchArgs a) {
                 const uint32_t op = ins.x & 0xFFu;
                 if (op == OP_ROOT_BEGIN) {
                     bool need = mine;
-                    if (a.use_cache && mine) {
+                    if (GROUPED && surr == (int32_t)(ins.y >> 16)) {
+                        // the learned surrogate wrote this node's value
+                        if (mine) {
+                            const uint32_t slot = ins.y & 0xFFFFu;
+                            const float4 rec = a.probes[(size_t)__ldg(&a.probe_base[mg]) + (size_t)(ins.y >> 16) * cnt + jj];
+                            V[(slot * 3 + 0) * 32] = rec.x;
+                            V[(slot * 3 + 1) * 32] = rec.y;
+                            V[(slot * 3 + 2) * 32] = rec.z;
+                        }
+                        need = false;
+                    } else if (a.use_cache && mine) {
                         d_address(d_key(mg, ins.z, a.level, iu, iv), a.n_cells, a.cells_pow2_mask, &cand_cell, &cand_h2);
                         bool hit = false;
                         const int first = a.table_empty ? 0 : probe_cell(a, cand_cell, cand_h2, &hit);
@@ -694,8 +734,9 @@ __global__ void __launch_bounds__(EVAL_WARPS * 32) k_eval_fused(BatchArgs a) {
                 if (a.out_hits) a.out_hits[i] = (uint16_t)min(hits, 65535u);
             }
         }
+        if (!GROUPED) chunk += gridDim.x * EVAL_WARPS;
     }
-    if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(&a.stats[ST_POINTS], (unsigned long long)a.n);
+    if (!GROUPED && blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(&a.stats[ST_POINTS], (unsigned long long)a.n);
     warp_add_u64(&a.stats[ST_NODES], n_nodes);
     warp_add_u64(&a.stats[ST_FLOPS], n_flops);
     warp_add_u64(&a.stats[ST_CANDIDATES], n_cand);
@@ -704,8 +745,10 @@ __global__ void __launch_bounds__(EVAL_WARPS * 32) k_eval_fused(BatchArgs a) {
     warp_add_u64(&a.stats[ST_HITS], n_hit);
     warp_add_u64(&a.stats[ST_MISSES], n_look - n_hit);
     warp_add_u64(&a.stats[ST_SLOTS], n_slots);
-    warp_add_u64(&a.stats[ST_BAD], n_bad);
-    if (__any_sync(FULL_MASK, n_bad != 0) && lane == 0) atomicOr(&a.ctl->err, ERR_BAD_MAT);
+    if (!GROUPED) {
+        warp_add_u64(&a.stats[ST_BAD], n_bad);
+        if (__any_sync(FULL_MASK, n_bad != 0) && lane == 0) atomicOr(&a.ctl->err, ERR_BAD_MAT);
+    }
 }
 
 // Work items of the batched evaluation: ceil(misses / 32) per cacheable node.
@@ -975,6 +1018,45 @@ __device__ __forceinline__ void insert_one(const BatchArgs& a, const Candidate& 
     }
 }
 
+// Inserts the candidates of one cell, given in ascending priority (indices into cb), with
+// the cell's hash2 words held by this thread: the one thread that owns the cell in this
+// batch resolves duplicates and a full cell without re-reading the table.  Occupied
+// slots form a prefix, so the cell's first empty slot is its next free one.
+__device__ void insert_cell(const BatchArgs& a, uint32_t cell, const Candidate* cb, const uint32_t* ids, uint32_t cnt,
+                            uint32_t ne, unsigned long long* n_ins, unsigned long long* n_dup,
+                            unsigned long long* n_full) {
+    uint32_t* cw = cell_h2(a, cell);
+    uint32_t h[MAX_ENTRIES];
+    uint32_t used = ne;
+    for (uint32_t e = 0; e < ne; ++e) {
+        h[e] = __ldcg(&cw[e]);
+        if (h[e] == 0u && used == ne) used = e;
+    }
+    for (uint32_t x = 0; x < cnt; ++x) {
+        const Candidate c = cb[ids[x]];
+        const uint32_t shadows = c.target >> 16;
+        bool dup = false;
+        // slots before the candidate's start held other keys when the pass began
+        for (uint32_t e = c.target & 0xFFFFu; e < used; ++e)
+            if (h[e] == c.h2) { dup = true; break; }
+        if (dup) {
+            *n_dup += 1u + shadows;
+        } else if (used >= ne) {
+            *n_full += 1u + shadows;
+        } else {
+            h[used] = c.h2;
+            cw[used] = c.h2;
+            float* val = cell_val(a, cell, used);
+            val[0] = c.r;
+            val[1] = c.g;
+            val[2] = c.b;
+            used++;
+            *n_ins += 1;
+            *n_dup += shadows;   // its shadows find it in the table
+        }
+    }
+}
+
 __device__ __forceinline__ uint32_t bin_of(uint32_t cell) { return cell / INS_CELLS; }
 
 // Candidates per bin.
@@ -1106,8 +1188,9 @@ __global__ void __launch_bounds__(256) k_bin_insert(BatchArgs a) {
             for (uint32_t i = t; i < n; i += T) {
                 const uint32_t cell_i = (uint32_t)(key[i] >> 44);
                 if (i > 0 && (uint32_t)(key[i - 1] >> 44) == cell_i) continue;
-                for (uint32_t x = i; x < n && (uint32_t)(key[x] >> 44) == cell_i; ++x)
-                    insert_one(a, cb[idx[x]], ne, &n_ins, &n_dup, &n_full);
+                uint32_t run = 1;
+                while (i + run < n && (uint32_t)(key[i + run] >> 44) == cell_i) ++run;
+                insert_cell(a, c0 + cell_i, cb, idx + i, run, ne, &n_ins, &n_dup, &n_full);
             }
             __syncthreads();
             continue;
@@ -1140,6 +1223,7 @@ __global__ void __launch_bounds__(256) k_bin_insert(BatchArgs a) {
         while (s < INS_CELLS) {
             if (t == 0) {
                 uint32_t e = s + 1;
+                if (s == 0 && s_off[INS_CELLS] <= INS_CAP) e = INS_CELLS;   // the whole bin fits
                 while (e < INS_CELLS && s_off[e + 1] - s_off[s] <= INS_CAP) ++e;
                 s_range[0] = e;
             }
@@ -1178,9 +1262,12 @@ __global__ void __launch_bounds__(256) k_bin_insert(BatchArgs a) {
                         cas_pair(pr[2], id[2], pr[4], id[4]); cas_pair(pr[3], id[3], pr[5], id[5]);
                         cas_pair(pr[1], id[1], pr[2], id[2]); cas_pair(pr[3], id[3], pr[4], id[4]);
                         cas_pair(pr[5], id[5], pr[6], id[6]);
+                        // the sorted indices go back to the cell's own segment
+                        uint32_t* sg = s_order + (s_off[k] - base);
 #pragma unroll
                         for (int q = 0; q < INS_REG; ++q)
-                            if ((uint32_t)q < cnt) insert_one(a, cb[id[q]], ne, &n_ins, &n_dup, &n_full);
+                            if ((uint32_t)q < cnt) sg[q] = id[q];
+                        insert_cell(a, c0 + k, cb, sg, cnt, ne, &n_ins, &n_dup, &n_full);
                     } else {
                         // insertion sort of the cell's segment (its own part of s_order)
                         uint32_t* sg = s_order + (s_off[k] - base);
@@ -1194,7 +1281,7 @@ __global__ void __launch_bounds__(256) k_bin_insert(BatchArgs a) {
                             }
                             sg[y] = v;
                         }
-                        for (uint32_t x = 0; x < cnt; ++x) insert_one(a, cb[sg[x]], ne, &n_ins, &n_dup, &n_full);
+                        insert_cell(a, c0 + k, cb, sg, cnt, ne, &n_ins, &n_dup, &n_full);
                     }
                 }
                 __syncthreads();
@@ -1340,9 +1427,10 @@ cudaError_t launch_batch(const BatchArgs& a, cudaStream_t s, int num_sms, cudaEv
         if (a.n > 0) {
             const size_t smem = eval_smem_bytes(a.max_slots);
             if (smem > 48 * 1024 &&
-                (e = cudaFuncSetAttribute(k_eval_fused, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
+                (e = cudaFuncSetAttribute(k_eval_fused<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) !=
+                    cudaSuccess)
                 return e;
-            k_eval_fused<<<num_sms * 16, EVAL_WARPS * 32, smem, s>>>(a);
+            k_eval_fused<false><<<num_sms * 16, EVAL_WARPS * 32, smem, s>>>(a, nullptr);
             nl++;
         }
         if ((e = mark(4)) != cudaSuccess) return e;
@@ -1365,7 +1453,9 @@ cudaError_t launch_batch(const BatchArgs& a, cudaStream_t s, int num_sms, cudaEv
         nl++;
     }
     if ((e = mark(1)) != cudaSuccess) return e;
-    if (a.n > 0 && a.use_cache && !a.keys_inline) {
+    // grouped schedule with the probes in the evaluator: no lookup kernel, no records
+    const bool fused = a.probe_inline && a.use_cache;
+    if (a.n > 0 && a.use_cache && !a.keys_inline && !fused) {
         const uint32_t ne = a.n_entries, rb = a.lookup_rb;
         const unsigned lb = (unsigned)num_sms * 8u;
         if (ne <= 4) {
@@ -1389,7 +1479,16 @@ cudaError_t launch_batch(const BatchArgs& a, cudaStream_t s, int num_sms, cudaEv
         nl++;
     }
     if ((e = mark(2)) != cudaSuccess) return e;
-    if (a.n > 0) {
+    if (a.n > 0 && fused) {
+        const size_t smem = eval_smem_bytes(a.max_slots);
+        if (smem > 48 * 1024 &&
+            (e = cudaFuncSetAttribute(k_eval_fused<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) !=
+                cudaSuccess)
+            return e;
+        if ((e = mark(3)) != cudaSuccess) return e;
+        k_eval_fused<true><<<num_sms * 16, EVAL_WARPS * 32, smem, s>>>(a, item_ctr);
+        nl++;
+    } else if (a.n > 0) {
         const bool outer = a.use_cache && a.split && !a.keys_inline;
         const size_t smem = eval_smem_bytes(outer ? a.max_slots_outer : a.max_slots),
                      smem_roots = eval_smem_bytes(a.max_slots_roots);

@@ -147,6 +147,7 @@ extern "C" pmc_status pmc_eval_batch_noalloc(pmc_cache* c, const pmc_points* pts
     a.miss_cnt = c->d_miss_cnt; a.root_item_base = c->d_root_items;
     a.misslist = reinterpret_cast<uint32_t*>(base + OFF_MISS);
     a.unsorted = c->unsorted;
+    a.probe_inline = c->probe_inline;
     a.lookup_rb = c->lookup_rb;
     // launch_batch clears the counters and offsets that must start at zero; every other
     // region is written before it is read within the pass.

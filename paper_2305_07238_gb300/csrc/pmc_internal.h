@@ -176,6 +176,7 @@ struct BatchArgs {
     Candidate* cands_binned;   // probe_cap
     // schedule (chosen by the caller's flags or by the autotuner)
     int unsorted;              // 1: no grouping; k_eval_fused probes inline in batch order
+    int probe_inline;          // 1: grouped; k_eval_fused probes inline (no lookup kernel)
     uint32_t lookup_rb;        // k_lookup: probes in flight per lane (1, 2 or 4)
 };
 

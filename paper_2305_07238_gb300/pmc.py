@@ -23,6 +23,7 @@ PMC_DEBUG_CHECKS = 0x4
 PMC_EVAL_INLINE = 0x8
 PMC_INSERT_ROUNDS = 0x10
 PMC_UNSORTED = 0x20
+PMC_PROBE_INLINE = 0x40
 PMC_GRAPH_RESET = 0x1
 TUNE_MAX = 16
 

@@ -58,7 +58,7 @@ def _compare_pass(gpu, ref, P, part, check_masks=True):
     err = float(np.abs(g_rgb - r["rgb"]).max()) if len(part["u"]) else 0.0
     assert err <= TOL, f"max-abs error {err}"
     assert np.array_equal(g_hits, r["hits"])
-    if check_masks and not ref.off and not gpu.flags & 0x20:   # unsorted passes keep no probe records
+    if check_masks and not ref.off and not gpu.flags & 0x60:   # these schedules keep no probe records
         assert np.array_equal(gpu.last_hit_masks(len(part["u"])), _oracle_masks(ref, part, r))
     gs, rs = gpu.stats(), ref.stats()
     for k in EXACT_STATS:
@@ -126,8 +126,9 @@ def test_tiny_config_cache_off(P):
 
 
 # ---- frame-shaped streams: a band of the 1920-wide frame, several table geometries ----------
-# PMC_EVAL_INLINE, PMC_INSERT_ROUNDS, PMC_UNSORTED
-MODES = {"grouped": 0, "inline": 0x8, "rounds": 0x10, "unsorted": 0x20, "unsorted_rounds": 0x30}
+# PMC_EVAL_INLINE, PMC_INSERT_ROUNDS, PMC_UNSORTED, PMC_PROBE_INLINE
+MODES = {"grouped": 0, "inline": 0x8, "rounds": 0x10, "unsorted": 0x20, "unsorted_rounds": 0x30,
+         "probe_inline": 0x40, "probe_inline_rounds": 0x50}
 
 
 @pytest.mark.parametrize("mode", sorted(MODES))
@@ -141,6 +142,23 @@ def test_frame_band_parity(P, n_cells, n_entries, mode):
     rows = (0, 9) if n_cells >= 1024 else (0, 3)       # 17,280 / 5,760 points: ragged warps
     for p in range(3):
         _compare_pass(gpu, ref, P, frame.points(p, rows=rows))
+    _compare_tables(gpu, ref)
+
+
+@pytest.fixture(scope="module")
+def scale_mats():
+    # the scale configuration: 4096 networks of 10-2000 nodes, 40 % shading-point dependent
+    return W.random_materials(4096, 10, 2000, 0.4, seed=5)
+
+
+@pytest.mark.parametrize("n_cells", [1 << 17, 1 << 12])
+def test_scale_config_band_parity(P, scale_mats, n_cells):
+    # a band of the 2048x2048 stream (2^22 points per batch), materials Zipf(0.9) over 4096
+    frame = W.Frame(W.FrameSpec(width=2048, height=2048, n_mats=4096, zipf_s=0.9, seed=5))
+    gpu = P.Cache(scale_mats, n_cells, 8)
+    ref = O.Cache(scale_mats, n_cells, 8)
+    for p in range(3):
+        _compare_pass(gpu, ref, P, frame.points(p, rows=(1000, 1008)))
     _compare_tables(gpu, ref)
 
 

@@ -55,7 +55,7 @@ def _host(ts):
     return [t.cpu().numpy() for t in ts]
 
 
-SCHEDULES = [(0, 4), (0, 2), (0, 1), (0x8, 4), (0x28, 4), (0x10, 4), (0x30, 2)]
+SCHEDULES = [(0, 4), (0, 2), (0, 1), (0x8, 4), (0x28, 4), (0x10, 4), (0x30, 2), (0x40, 4), (0x50, 4)]
 
 
 def test_every_schedule_same_results(P, band):
@@ -81,7 +81,7 @@ def test_every_schedule_same_results(P, band):
         assert got[3] == base[3], (flags, rb)
 
 
-@pytest.mark.parametrize("flags", [0, 0x20, 0x10])
+@pytest.mark.parametrize("flags", [0, 0x20, 0x10, 0x40])
 def test_graph_with_reset_replays_the_frame(P, band, flags):
     mats, parts = band
     dparts = [P.points_to_device(p) for p in parts]

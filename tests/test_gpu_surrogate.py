@@ -168,6 +168,30 @@ def test_pass_with_surrogates_matches_oracle(P, trained):
     assert np.array_equal(cache.table()[0], ref.table()[0])
 
 
+def test_pass_with_surrogates_probe_inline_schedule(P, trained):
+    """The grouped inline-probing schedule with surrogates equals the default schedule."""
+    mats, cache, _ = trained
+    pts = W.points_uniform(4000, seed=12, n_mats=len(mats))
+    d = P.points_to_device(pts)
+    outs = []
+    for flags in (0, 0x40):
+        cache.reset()
+        cache.set_schedule(flags, 4)
+        got = []
+        for p in range(2):
+            rgb = torch.empty((3, 4000), device="cuda")
+            hits = torch.empty(4000, dtype=torch.int16, device="cuda")
+            cache.eval_batch(d, rgb, hits)
+            cache.sync()
+            got.append((rgb.cpu().numpy(), hits.cpu().numpy()))
+        outs.append((got, cache.table()[0].copy(), cache.stats()["surrogate_evals"]))
+    cache.set_schedule(0, 4)
+    for (ra, ha), (rb, hb) in zip(outs[0][0], outs[1][0]):
+        assert np.array_equal(ra, rb) and np.array_equal(ha, hb)
+    assert np.array_equal(outs[0][1], outs[1][1])
+    assert outs[0][2] == outs[1][2] > 0
+
+
 def test_surrogate_pass_beats_exact_evaluation(P, trained):
     mats, cache, _ = trained
     deep = [m for m in range(6) if cache.get_surrogate(m, with_theta=False)["enabled"]]
