@@ -976,18 +976,6 @@ __global__ void __launch_bounds__(256) k_insert(BatchArgs a) {
 // memory and one thread per cell inserts that cell's candidates in ascending order.
 constexpr uint32_t INS_CELLS = INSERT_BIN_CELLS;   // cells per bin (a multiple of 256)
 constexpr uint32_t INS_SMEM_BINS = 4096;  // bins counted in shared memory by the partition
-constexpr uint32_t INS_CAP = 4096;        // candidates grouped in shared memory at a time
-constexpr int INS_REG = 8;                // a cell's candidates sorted in registers
-
-__device__ __forceinline__ void cas_pair(unsigned long long& pa, uint32_t& ia, unsigned long long& pb, uint32_t& ib) {
-    const bool sw = pa > pb;
-    const unsigned long long tp = sw ? pb : pa;
-    const uint32_t ti = sw ? ib : ia;
-    pb = sw ? pa : pb;
-    ib = sw ? ia : ib;
-    pa = tp;
-    ia = ti;
-}
 
 // Inserts one candidate into a cell owned by the calling thread (Alg. 1 scan).
 __device__ __forceinline__ void insert_one(const BatchArgs& a, const Candidate& c, uint32_t ne,
@@ -1015,45 +1003,6 @@ __device__ __forceinline__ void insert_one(const BatchArgs& a, const Candidate& 
         val[2] = c.b;
         *n_ins += 1;
         *n_dup += c.target >> 16;   // its shadows find it in the table
-    }
-}
-
-// Inserts the candidates of one cell, given in ascending priority (indices into cb), with
-// the cell's hash2 words held by this thread: the one thread that owns the cell in this
-// batch resolves duplicates and a full cell without re-reading the table.  Occupied
-// slots form a prefix, so the cell's first empty slot is its next free one.
-__device__ void insert_cell(const BatchArgs& a, uint32_t cell, const Candidate* cb, const uint32_t* ids, uint32_t cnt,
-                            uint32_t ne, unsigned long long* n_ins, unsigned long long* n_dup,
-                            unsigned long long* n_full) {
-    uint32_t* cw = cell_h2(a, cell);
-    uint32_t h[MAX_ENTRIES];
-    uint32_t used = ne;
-    for (uint32_t e = 0; e < ne; ++e) {
-        h[e] = __ldcg(&cw[e]);
-        if (h[e] == 0u && used == ne) used = e;
-    }
-    for (uint32_t x = 0; x < cnt; ++x) {
-        const Candidate c = cb[ids[x]];
-        const uint32_t shadows = c.target >> 16;
-        bool dup = false;
-        // slots before the candidate's start held other keys when the pass began
-        for (uint32_t e = c.target & 0xFFFFu; e < used; ++e)
-            if (h[e] == c.h2) { dup = true; break; }
-        if (dup) {
-            *n_dup += 1u + shadows;
-        } else if (used >= ne) {
-            *n_full += 1u + shadows;
-        } else {
-            h[used] = c.h2;
-            cw[used] = c.h2;
-            float* val = cell_val(a, cell, used);
-            val[0] = c.r;
-            val[1] = c.g;
-            val[2] = c.b;
-            used++;
-            *n_ins += 1;
-            *n_dup += shadows;   // its shadows find it in the table
-        }
     }
 }
 
@@ -1105,7 +1054,7 @@ __global__ void k_bin_scan(BatchArgs a) {
 }
 
 // Copies every candidate into its bin's range.
-__global__ void __launch_bounds__(256) k_bin_scatter(BatchArgs a) {
+__global__ void __launch_bounds__(512) k_bin_scatter(BatchArgs a) {
     __shared__ uint32_t s_cnt[INS_SMEM_BINS];
     const uint32_t nb = a.n_bins;
     const bool local = nb <= INS_SMEM_BINS;
@@ -1129,164 +1078,201 @@ __global__ void __launch_bounds__(256) k_bin_scatter(BatchArgs a) {
     }
 }
 
-// One block per bin: group by cell in shared memory, then insert per cell in order.
-constexpr uint32_t INS_SMALL = 1024;      // bins up to this size are sorted by (cell, priority)
-
+// One block per bin.  The bin's candidates (or, for a bin beyond INS_STAGE, those of a
+// range of its cells) are staged in shared memory grouped by cell: sort key (cell offset
+// << 44 | priority), hash2, target and source index.  One thread per cell sorts its
+// segment and inserts it with the cell's hash2 words in registers; a range holding a cell
+// with more than INS_CELL_SORT candidates is sorted by the whole block instead.  A single
+// cell with more candidates than INS_STAGE is resolved by a block-wide selection.
+constexpr uint32_t INS_STAGE = 1024;
+constexpr uint32_t INS_CELL_SORT = 64;
 static_assert(INS_CELLS % 256 == 0, "k_bin_insert scans INS_CELLS / 256 cells per thread");
-static_assert(INS_SMALL <= INS_CAP, "small bins keep their candidate indices in s_order");
 
-__global__ void __launch_bounds__(256) k_bin_insert(BatchArgs a) {
-    __shared__ unsigned long long s_key[INS_SMALL];       // small bins: (cell, priority) keys
-    __shared__ uint32_t s_cnt[INS_CELLS];
-    __shared__ uint32_t s_off[INS_CELLS + 1];
-    __shared__ uint32_t s_cur[INS_CELLS];
-    __shared__ uint32_t s_order[INS_CAP];
-    __shared__ uint32_t s_part[256];
-    __shared__ uint32_t s_range[2];
-    __shared__ unsigned long long s_best[256];
-    __shared__ uint32_t s_bidx[256];
+struct InsSmem {   // byte offsets into dynamic shared memory
+    static constexpr uint32_t key = 0;                                   // u64 [INS_STAGE]
+    static constexpr uint32_t idx = key + INS_STAGE * 8;                 // u32 [INS_STAGE]
+    static constexpr uint32_t h2 = idx + INS_STAGE * 4;                  // u32 [INS_STAGE]
+    static constexpr uint32_t tgt = h2 + INS_STAGE * 4;                  // u32 [INS_STAGE]
+    static constexpr uint32_t src = tgt + INS_STAGE * 4;                 // u32 [INS_STAGE]
+    static constexpr uint32_t cnt = src + INS_STAGE * 4;                 // u32 [INS_CELLS]
+    static constexpr uint32_t off = cnt + INS_CELLS * 4;                 // u32 [INS_CELLS + 1]
+    static constexpr uint32_t cur = off + (INS_CELLS + 4) * 4;           // u32 [INS_CELLS]
+    static constexpr uint32_t part = cur + INS_CELLS * 4;                // u32 [256]
+    static constexpr uint32_t best = part + 256 * 4;                     // u64 [256]
+    static constexpr uint32_t bidx = best + 256 * 8;                     // u32 [256]
+    static constexpr uint32_t misc = bidx + 256 * 4;                     // u32 [4]
+    static constexpr uint32_t end = misc + 16;
+};
+
+size_t insert_smem_bytes() { return InsSmem::end; }
+
+// Resolves one cell from its staged, sorted segment [x0, x0 + n) (one thread).
+__device__ __forceinline__ void insert_staged_cell(const BatchArgs& a, const Candidate* cb, uint32_t cell,
+                                                   const uint32_t* idx, const uint32_t* sh2, const uint32_t* stgt,
+                                                   const uint32_t* ssrc, uint32_t x0, uint32_t n, uint32_t ne,
+                                                   unsigned long long* n_ins, unsigned long long* n_dup,
+                                                   unsigned long long* n_full) {
+    uint32_t* cw = cell_h2(a, cell);
+    uint32_t h[MAX_ENTRIES];
+    uint32_t used = ne;
+    for (uint32_t e = 0; e < ne; ++e) {
+        h[e] = __ldcg(&cw[e]);
+        if (h[e] == 0u && used == ne) used = e;
+    }
+    for (uint32_t x = x0; x < x0 + n; ++x) {
+        const uint32_t j = idx[x];
+        const uint32_t hc = sh2[j], tg = stgt[j];
+        const uint32_t shadows = tg >> 16;
+        bool dup = false;
+        // slots before the candidate's start held other keys when the pass began
+        for (uint32_t e = tg & 0xFFFFu; e < used; ++e)
+            if (h[e] == hc) { dup = true; break; }
+        if (dup) {
+            *n_dup += 1u + shadows;
+        } else if (used >= ne) {
+            *n_full += 1u + shadows;
+        } else {
+            const float4 v = __ldcg(reinterpret_cast<const float4*>(&cb[ssrc[j]].r));   // r, g, b, target
+            h[used] = hc;
+            cw[used] = hc;
+            float* val = cell_val(a, cell, used);
+            val[0] = v.x;
+            val[1] = v.y;
+            val[2] = v.z;
+            used++;
+            *n_ins += 1;
+            *n_dup += shadows;   // its shadows find it in the table
+        }
+    }
+}
+
+__global__ void __launch_bounds__(256, 6) k_bin_insert(BatchArgs a) {
+    extern __shared__ __align__(16) unsigned char ism[];
+    unsigned long long* s_key = reinterpret_cast<unsigned long long*>(ism + InsSmem::key);
+    uint32_t* s_idx = reinterpret_cast<uint32_t*>(ism + InsSmem::idx);
+    uint32_t* s_h2 = reinterpret_cast<uint32_t*>(ism + InsSmem::h2);
+    uint32_t* s_tgt = reinterpret_cast<uint32_t*>(ism + InsSmem::tgt);
+    uint32_t* s_src = reinterpret_cast<uint32_t*>(ism + InsSmem::src);
+    uint32_t* s_cnt = reinterpret_cast<uint32_t*>(ism + InsSmem::cnt);
+    uint32_t* s_off = reinterpret_cast<uint32_t*>(ism + InsSmem::off);
+    uint32_t* s_cur = reinterpret_cast<uint32_t*>(ism + InsSmem::cur);
+    uint32_t* s_part = reinterpret_cast<uint32_t*>(ism + InsSmem::part);
+    unsigned long long* s_best = reinterpret_cast<unsigned long long*>(ism + InsSmem::best);
+    uint32_t* s_bidx = reinterpret_cast<uint32_t*>(ism + InsSmem::bidx);
+    uint32_t* s_misc = reinterpret_cast<uint32_t*>(ism + InsSmem::misc);
     const uint32_t ne = a.n_entries;
     const uint32_t t = threadIdx.x, T = blockDim.x;
+    const Candidate* cb = a.cands_binned;
     unsigned long long n_dup = 0, n_full = 0, n_ins = 0;
     for (uint32_t bin = blockIdx.x; bin < a.n_bins; bin += gridDim.x) {
         const uint32_t lo = a.bin_base[bin], hi = a.bin_base[bin + 1];
         if (lo == hi) continue;                                 // uniform in the block
         const uint32_t c0 = bin * INS_CELLS;
-        const Candidate* cb = a.cands_binned;
-        if (hi - lo <= INS_SMALL) {
-            // few candidates: bitonic sort of (cell, priority) keys, then the first of each
-            // run of equal cells inserts the run in order
-            unsigned long long* key = s_key;
-            uint32_t* idx = s_order;
-            const uint32_t n = hi - lo;
-            uint32_t N = 1;
-            while (N < n) N <<= 1;
-            for (uint32_t i = t; i < N; i += T) {
-                key[i] = i < n ? ((unsigned long long)(cb[lo + i].cell - c0) << 44) | cb[lo + i].prio : ~0ull;
-                idx[i] = lo + i;
-            }
-            __syncthreads();
-            for (uint32_t k = 2; k <= N; k <<= 1) {
-                for (uint32_t j = k >> 1; j > 0; j >>= 1) {
-                    for (uint32_t i = t; i < N; i += T) {
-                        const uint32_t ixj = i ^ j;
-                        if (ixj > i) {
-                            const bool up = (i & k) == 0;
-                            const unsigned long long ki = key[i], kj = key[ixj];
-                            if ((ki > kj) == up) {
-                                key[i] = kj;
-                                key[ixj] = ki;
-                                const uint32_t tmp = idx[i];
-                                idx[i] = idx[ixj];
-                                idx[ixj] = tmp;
-                            }
-                        }
-                    }
-                    __syncthreads();
-                }
-            }
-            for (uint32_t i = t; i < n; i += T) {
-                const uint32_t cell_i = (uint32_t)(key[i] >> 44);
-                if (i > 0 && (uint32_t)(key[i - 1] >> 44) == cell_i) continue;
-                uint32_t run = 1;
-                while (i + run < n && (uint32_t)(key[i + run] >> 44) == cell_i) ++run;
-                insert_cell(a, c0 + cell_i, cb, idx + i, run, ne, &n_ins, &n_dup, &n_full);
-            }
-            __syncthreads();
-            continue;
-        }
+        // ---- per-cell counts and their exclusive scan
         for (uint32_t k = t; k < INS_CELLS; k += T) s_cnt[k] = 0;
         __syncthreads();
-        for (uint32_t i = lo + t; i < hi; i += T) atomicAdd(&s_cnt[cb[i].cell - c0], 1u);
+        for (uint32_t i = lo + t; i < hi; i += T) atomicAdd(&s_cnt[__ldcg(&cb[i].cell) - c0], 1u);
         __syncthreads();
-        // exclusive scan of the per-cell counts (INS_CELLS / T consecutive cells per thread)
         const uint32_t per = INS_CELLS / T;
         uint32_t part = 0;
         for (uint32_t k = 0; k < per; ++k) part += s_cnt[t * per + k];
         s_part[t] = part;
         __syncthreads();
-        for (uint32_t off = 1; off < T; off <<= 1) {
-            uint32_t v = t >= off ? s_part[t - off] : 0u;
+        for (uint32_t o = 1; o < T; o <<= 1) {
+            const uint32_t v = t >= o ? s_part[t - o] : 0u;
             __syncthreads();
             s_part[t] += v;
             __syncthreads();
         }
-        uint32_t run = t ? s_part[t - 1] : 0u;
+        uint32_t run = s_part[t] - part;
         for (uint32_t k = 0; k < per; ++k) {
             s_off[t * per + k] = run;
             run += s_cnt[t * per + k];
         }
         if (t == T - 1) s_off[INS_CELLS] = run;
         __syncthreads();
-        // cells [s, e) whose candidates fit in s_order at once
+        // ---- ranges of cells whose candidates fit the stage
         uint32_t s = 0;
         while (s < INS_CELLS) {
             if (t == 0) {
                 uint32_t e = s + 1;
-                if (s == 0 && s_off[INS_CELLS] <= INS_CAP) e = INS_CELLS;   // the whole bin fits
-                while (e < INS_CELLS && s_off[e + 1] - s_off[s] <= INS_CAP) ++e;
-                s_range[0] = e;
+                if (s == 0 && s_off[INS_CELLS] <= INS_STAGE) e = INS_CELLS;   // the whole bin fits
+                while (e < INS_CELLS && s_off[e + 1] - s_off[s] <= INS_STAGE) ++e;
+                s_misc[0] = e;
             }
             __syncthreads();
-            const uint32_t e = s_range[0];
-            const uint32_t base = s_off[s];
-            const bool giant = s_off[e] - base > INS_CAP;     // a single cell beyond the cap
-            if (!giant) {
+            const uint32_t e = s_misc[0];
+            const uint32_t base = s_off[s], R = s_off[e] - base;
+            if (R <= INS_STAGE) {
+                // stage the range grouped by cell
                 for (uint32_t k = s + t; k < e; k += T) s_cur[k] = s_off[k] - base;
                 __syncthreads();
                 for (uint32_t i = lo + t; i < hi; i += T) {
-                    const uint32_t k = cb[i].cell - c0;
-                    if (k >= s && k < e) s_order[atomicAdd(&s_cur[k], 1u)] = i;
+                    const uint32_t k = __ldcg(&cb[i].cell) - c0;
+                    if (k < s || k >= e) continue;
+                    const uint32_t pos = atomicAdd(&s_cur[k], 1u);
+                    s_key[pos] = ((unsigned long long)k << 44) | __ldcg(&cb[i].prio);
+                    s_idx[pos] = pos;
+                    s_h2[pos] = __ldcg(&cb[i].h2);
+                    s_tgt[pos] = __ldcg(&cb[i].target);
+                    s_src[pos] = i;
                 }
-                __syncthreads();
-                for (uint32_t k = s + t; k < e; k += T) {
-                    const uint32_t cnt = s_cnt[k];
-                    if (cnt == 0) continue;
-                    const uint32_t* seg = s_order + (s_off[k] - base);
-                    if (cnt <= (uint32_t)INS_REG) {
-                        unsigned long long pr[INS_REG];
-                        uint32_t id[INS_REG];
-#pragma unroll
-                        for (int q = 0; q < INS_REG; ++q) {
-                            id[q] = (uint32_t)q < cnt ? seg[q] : 0u;
-                            pr[q] = (uint32_t)q < cnt ? cb[id[q]].prio : ~0ull;
+                bool heavy = false;
+                for (uint32_t k = s + t; k < e; k += T) heavy |= s_cnt[k] > INS_CELL_SORT;
+                heavy = __syncthreads_or(heavy) != 0;
+                if (heavy) {
+                    // a crowded cell: sort the whole range by (cell, priority)
+                    uint32_t N = 1;
+                    while (N < R) N <<= 1;
+                    for (uint32_t i = R + t; i < N; i += T) {
+                        s_key[i] = ~0ull;
+                        s_idx[i] = 0;
+                    }
+                    __syncthreads();
+                    for (uint32_t kk = 2; kk <= N; kk <<= 1) {
+                        for (uint32_t j = kk >> 1; j > 0; j >>= 1) {
+                            for (uint32_t i = t; i < N; i += T) {
+                                const uint32_t ixj = i ^ j;
+                                if (ixj > i) {
+                                    const bool up = (i & kk) == 0;
+                                    const unsigned long long ki = s_key[i], kj = s_key[ixj];
+                                    if ((ki > kj) == up) {
+                                        s_key[i] = kj;
+                                        s_key[ixj] = ki;
+                                        const uint32_t tmp = s_idx[i];
+                                        s_idx[i] = s_idx[ixj];
+                                        s_idx[ixj] = tmp;
+                                    }
+                                }
+                            }
+                            __syncthreads();
                         }
-                        // odd-even merge sort network of 8 (Batcher)
-                        cas_pair(pr[0], id[0], pr[1], id[1]); cas_pair(pr[2], id[2], pr[3], id[3]);
-                        cas_pair(pr[4], id[4], pr[5], id[5]); cas_pair(pr[6], id[6], pr[7], id[7]);
-                        cas_pair(pr[0], id[0], pr[2], id[2]); cas_pair(pr[1], id[1], pr[3], id[3]);
-                        cas_pair(pr[4], id[4], pr[6], id[6]); cas_pair(pr[5], id[5], pr[7], id[7]);
-                        cas_pair(pr[1], id[1], pr[2], id[2]); cas_pair(pr[5], id[5], pr[6], id[6]);
-                        cas_pair(pr[0], id[0], pr[4], id[4]); cas_pair(pr[1], id[1], pr[5], id[5]);
-                        cas_pair(pr[2], id[2], pr[6], id[6]); cas_pair(pr[3], id[3], pr[7], id[7]);
-                        cas_pair(pr[2], id[2], pr[4], id[4]); cas_pair(pr[3], id[3], pr[5], id[5]);
-                        cas_pair(pr[1], id[1], pr[2], id[2]); cas_pair(pr[3], id[3], pr[4], id[4]);
-                        cas_pair(pr[5], id[5], pr[6], id[6]);
-                        // the sorted indices go back to the cell's own segment
-                        uint32_t* sg = s_order + (s_off[k] - base);
-#pragma unroll
-                        for (int q = 0; q < INS_REG; ++q)
-                            if ((uint32_t)q < cnt) sg[q] = id[q];
-                        insert_cell(a, c0 + k, cb, sg, cnt, ne, &n_ins, &n_dup, &n_full);
-                    } else {
-                        // insertion sort of the cell's segment (its own part of s_order)
-                        uint32_t* sg = s_order + (s_off[k] - base);
-                        for (uint32_t x = 1; x < cnt; ++x) {
-                            const uint32_t v = sg[x];
-                            const unsigned long long pv = cb[v].prio;
+                    }
+                }
+                for (uint32_t k = s + t; k < e; k += T) {
+                    const uint32_t n = s_cnt[k];
+                    if (n == 0) continue;
+                    const uint32_t x0 = s_off[k] - base;
+                    if (!heavy) {
+                        // insertion sort of the cell's own segment
+                        for (uint32_t x = x0 + 1; x < x0 + n; ++x) {
+                            const unsigned long long kv = s_key[x];
+                            const uint32_t iv = s_idx[x];
                             uint32_t y = x;
-                            while (y > 0 && cb[sg[y - 1]].prio > pv) {
-                                sg[y] = sg[y - 1];
+                            while (y > x0 && s_key[y - 1] > kv) {
+                                s_key[y] = s_key[y - 1];
+                                s_idx[y] = s_idx[y - 1];
                                 --y;
                             }
-                            sg[y] = v;
+                            s_key[y] = kv;
+                            s_idx[y] = iv;
                         }
-                        insert_cell(a, c0 + k, cb, sg, cnt, ne, &n_ins, &n_dup, &n_full);
                     }
+                    insert_staged_cell(a, cb, c0 + k, s_idx, s_h2, s_tgt, s_src, x0, n, ne, &n_ins, &n_dup, &n_full);
                 }
                 __syncthreads();
             } else {
-                // one cell with more candidates than fit: the block selects them in order
+                // one cell with more candidates than the stage: the block selects them in order
                 const uint32_t cell = c0 + s;
                 const uint32_t cnt = s_cnt[s];
                 unsigned long long last = 0;
@@ -1301,10 +1287,10 @@ __global__ void __launch_bounds__(256) k_bin_insert(BatchArgs a) {
                     s_best[t] = best;
                     s_bidx[t] = bi;
                     __syncthreads();
-                    for (uint32_t off = T / 2; off > 0; off >>= 1) {
-                        if (t < off && s_best[t + off] < s_best[t]) {
-                            s_best[t] = s_best[t + off];
-                            s_bidx[t] = s_bidx[t + off];
+                    for (uint32_t o = T / 2; o > 0; o >>= 1) {
+                        if (t < o && s_best[t + o] < s_best[t]) {
+                            s_best[t] = s_best[t + o];
+                            s_bidx[t] = s_bidx[t + o];
                         }
                         __syncthreads();
                     }
@@ -1397,8 +1383,12 @@ static cudaError_t launch_insert(const BatchArgs& a, cudaStream_t s, int num_sms
         if ((e = cudaMemsetAsync(a.bin_cnt, 0, (size_t)a.n_bins * sizeof(uint32_t), s)) != cudaSuccess) return e;
         k_bin_count<<<gs_blocks, 256, 0, s>>>(a);
         k_bin_scan<<<1, 1024, 0, s>>>(a);
-        k_bin_scatter<<<gs_blocks, 256, 0, s>>>(a);
-        k_bin_insert<<<std::min<uint32_t>(a.n_bins, (uint32_t)num_sms * 16u), 256, 0, s>>>(a);
+        // one block per SM: each block reserves its range of every bin with one atomic
+        k_bin_scatter<<<num_sms, 512, 0, s>>>(a);
+        const size_t ism = insert_smem_bytes();
+        if ((e = cudaFuncSetAttribute(k_bin_insert, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ism)) != cudaSuccess)
+            return e;
+        k_bin_insert<<<std::min<uint32_t>(a.n_bins, (uint32_t)num_sms * 12u), 256, ism, s>>>(a);
         *nl += 4;
     }
     return e;
