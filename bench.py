@@ -41,8 +41,8 @@ N_CELLS, N_ENTRIES, LEVEL = 1 << 21, 8, 10
 SAMPLE_ROWS = (0, 40)            # CPU-oracle sample: 40 full-width rows, all 16 passes
 REF_ROWS = (0, 16)               # reference arm: 16 full-width rows per step, all 16 passes
 # ncu capture of k_eval / k_lookup on the same workload (profiles/): DRAM bytes per launch
-# (profiles/launches_frame1080p.md: mean over the 16 k_eval and 15 k_lookup launches of one frame)
-NCU_TRAFFIC = {"eval": 309.8e6, "eval_roots": None, "lookup": 1050.0e6}
+# (profiles/launches_frame1080p.md: mean over the launches of one frame of each kernel)
+NCU_TRAFFIC = {"eval": 309.9e6, "eval_roots": 179.8e6, "lookup": 1046.9e6}
 
 FP32_LANES_PER_SM = 128          # Blackwell SM: 4 partitions x 32 FP32 lanes
 N_SMS = 152
@@ -472,6 +472,16 @@ def sweep_leg(torch, P, dev, local_rank, seed=0):
 
 SURR_MATS, SURR_LO, SURR_HI, SURR_PASSES = 256, 500, 2000, 64
 SURR_TRAIN, SURR_VALID, SURR_EPOCHS = 1 << 20, 1 << 16, 2
+MLP_FLOPS_PER_POINT = 2 * (64 * 64 + 64 * 64 + 64 * 3)   # the network's multiply-adds, FMA = 2
+
+
+def bf16_peak():
+    """Dense BF16 tensor peak: the measured cuBLAS burst figure, else the fallback."""
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            return float(json.load(f)["bf16_tflops"]), "measured cuBLAS BF16 burst"
+    return 1900.0, "fallback"
 
 
 def surrogate_leg(torch, P, dev, local_rank, seed=0):
@@ -516,6 +526,40 @@ def surrogate_leg(torch, P, dev, local_rank, seed=0):
     res["within_2e-3"] = round(float(np.mean((rmse >= 0) & (rmse <= 2e-3))), 4)
     res["rmse_median"] = float(np.median(rmse[rmse >= 0])) if np.any(rmse >= 0) else None
     res["surrogate"] = round(run(cached), 1)
+    # tensor-core roofline of the in-pass inference (k_surrogate_tc): with one cacheable node
+    # per network and every network's surrogate enabled, the lookup phase is that kernel
+    cached.reset()
+    cached.sync()
+    cached.read_timing()
+    cached.set_timing(True)
+    for p in range(SURR_PASSES):
+        cached.eval_batch(passes[p], outs)
+    cached.set_timing(False)
+    tm = cached.read_timing()
+    st = cached.stats()
+    peak = bf16_peak()
+    flops = MLP_FLOPS_PER_POINT * st["surrogate_evals"]
+    ms_inf = tm["ms"]["lookup"]
+    tf = flops / (ms_inf / 1e3) / 1e12 if ms_inf else 0.0
+    res["tensor_roofline"] = {"kernel": "k_surrogate_tc", "bound": "tensor", "achieved": round(tf, 2),
+                              "peak": peak[0], "unit": "TFLOP/s", "frac": round(tf / peak[0], 4),
+                              "peak_kind": peak[1], "ms_per_pass": round(ms_inf / SURR_PASSES, 4),
+                              "flops_per_point": MLP_FLOPS_PER_POINT}
+    th = torch.tensor(cached.get_surrogate(0)["theta"], device=dev)
+    u, v = passes[0]["u"], passes[0]["v"]
+    for _ in range(3):
+        P.mlp_forward(th, u, v)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(10):
+        P.mlp_forward(th, u, v)
+    e1.record()
+    torch.cuda.synchronize()
+    ms_fw = e0.elapsed_time(e1) / 10
+    tf_fw = MLP_FLOPS_PER_POINT * n / (ms_fw / 1e3) / 1e12
+    res["mlp_forward"] = {"points_per_s": round(n / (ms_fw / 1e3), 1), "achieved": round(tf_fw, 2),
+                          "unit": "TFLOP/s", "frac": round(tf_fw / peak[0], 4)}
     res["unit"] = UNIT
     res["speedup_surrogate_over_uncached"] = round(res["surrogate"] / res["uncached"], 2)
     res["speedup_cached_over_uncached"] = round(res["cached"] / res["uncached"], 2)
@@ -591,11 +635,28 @@ def cpu_baseline(P, torch, mats, frame, dev):
 
 def profile_run(args):
     """Eager frames only (default schedule, no autotuning, no graph, no other legs), so
-    that an ncu launch list can select whole frames: W warm-up frames, then K frames."""
+    that an ncu launch list can select whole frames: W warm-up frames, then K frames.
+    With --profile-surrogate: 32 deep networks with trained surrogates, K passes of
+    2,073,600 points (the tensor-core inference kernel on a full pass)."""
     import torch
     from paper_2305_07238_gb300 import build as B
     from paper_2305_07238_gb300 import pmc as P
     B.build()
+    if args.profile_surrogate:
+        mats = W.surrogate_materials(32, SURR_LO, SURR_HI, seed=0)
+        frame = W.Frame(W.FrameSpec(width=WIDTH, height=HEIGHT, n_mats=32, seed=100))
+        n = WIDTH * HEIGHT
+        outs = torch.empty((3, n), dtype=torch.float32, device="cuda")
+        cache = P.Cache(mats, N_CELLS, N_ENTRIES, uv_level=LEVEL)
+        rmse = cache.train_surrogates(n_train=1 << 14, n_valid=1024, epochs=4, lr=1e-2, seed=1)
+        for m in range(len(mats)):   # every network on, whatever its fit, for the kernel's sake
+            cache.set_surrogate(m, cache.get_surrogate(m)["theta"])
+        passes = [frame.points_torch(p, "cuda") for p in range(max(1, args.steps))]
+        for d in passes:
+            cache.eval_batch(d, outs)
+        cache.sync()
+        return {"profile": "surrogate passes", "passes": len(passes), "networks": len(mats),
+                "surrogate_evals": cache.stats()["surrogate_evals"], "rmse_median": float(np.median(rmse))}
     mats, frame = workload(seed=0)
     dev_passes = [P.points_to_device(frame.points(p)) for p in range(SPP)]
     n = WIDTH * HEIGHT
@@ -660,6 +721,8 @@ def main():
                          "default: about a minute more; profiling runs take 'cached')")
     ap.add_argument("--profile", action="store_true",
                     help="eager frames only, for ncu launch lists (prints launches per frame)")
+    ap.add_argument("--profile-surrogate", action="store_true",
+                    help="with --profile: passes of 32 networks with surrogates (tensor-core kernel)")
     args = ap.parse_args()
     if args.profile:
         print(json.dumps(profile_run(args)), flush=True)
