@@ -282,7 +282,7 @@ pmc_status pmc_create_cache(const pmc_cache_desc* desc, const pmc_material* mats
         (s = dalloc(&c->d_rinfo, c->root_info.size())) != PMC_OK ||
         (s = dalloc(&c->d_miss_cnt, c->root_info.size() + MAX_LEVELS)) != PMC_OK ||
         (s = dalloc(&c->d_root_items, c->root_info.size() + 1)) != PMC_OK ||
-        (s = dalloc(&c->d_bins, 2 * (size_t)c->n_bins + 1)) != PMC_OK ||
+        (s = dalloc(&c->d_bins, 3 * (size_t)c->n_bins + 1)) != PMC_OK ||
         (s = dalloc(&c->d_surr_slot, n_mats)) != PMC_OK ||
         (s = dalloc(&c->d_surr_ord, n_mats)) != PMC_OK ||
         (s = dalloc(&c->d_surr_items, (size_t)n_mats + 1)) != PMC_OK) {
@@ -375,6 +375,7 @@ pmc_status enqueue_batch(pmc_cache* c, const pmc_points* pts, float* out_rgb, ui
     a.split = c->use_cache && c->split;
     a.insert_rounds = (c->desc.flags & PMC_INSERT_ROUNDS) ? 1 : 0;
     a.n_bins = c->n_bins; a.bin_cnt = c->d_bins; a.bin_base = c->d_bins + c->n_bins;
+    a.bin_list = c->d_bins + 2 * (size_t)c->n_bins + 1;
     a.cands_binned = c->d_cands_binned;
     if (surrogates_active(c)) {
         a.surr_slot = c->d_surr_slot; a.surr_ord = c->d_surr_ord; a.surr_theta = c->d_surr_theta;

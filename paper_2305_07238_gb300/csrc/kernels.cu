@@ -75,6 +75,38 @@ __device__ __forceinline__ void block_range(uint32_t n, uint32_t* lo, uint32_t* 
     *hi = min(n, *lo + chunk);
 }
 
+// Inclusive scan of one value per thread over the block (blockDim.x a multiple of 32, at
+// most 1024) with warp shuffles and two block barriers; tmp holds 33 values of shared
+// memory, *total receives the block's sum.  Every thread of the block must call it.
+template <typename U>
+__device__ __forceinline__ U block_incl_scan(U v, U* tmp, U* total) {
+    const uint32_t lane = lane_id(), warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    U x = v;
+#pragma unroll
+    for (uint32_t o = 1; o < 32; o <<= 1) {
+        const U y = __shfl_up_sync(FULL_MASK, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) tmp[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+        const U w = lane < nw ? tmp[lane] : U(0);
+        U wi = w;
+#pragma unroll
+        for (uint32_t o = 1; o < 32; o <<= 1) {
+            const U y = __shfl_up_sync(FULL_MASK, wi, o);
+            if (lane >= o) wi += y;
+        }
+        tmp[lane] = wi - w;
+        if (lane == 31) tmp[32] = wi;
+    }
+    __syncthreads();
+    const U r = x + tmp[warp];
+    *total = tmp[32];
+    __syncthreads();   // tmp is free for the next call
+    return r;
+}
+
 __global__ void __launch_bounds__(256) k_hist(BatchArgs a) {
     __shared__ uint32_t s_cnt[GROUP_SMEM_MATS];
     const bool local = a.n_mats <= GROUP_SMEM_MATS;
@@ -113,7 +145,7 @@ __global__ void __launch_bounds__(256) k_hist(BatchArgs a) {
 
 // One block: exclusive scans of counts, counts * roots and ceil(counts / 32).
 __global__ void k_scan(BatchArgs a) {
-    __shared__ uint32_t s_tot[4][1024];
+    __shared__ uint32_t s_tmp[33];
     const uint32_t T = blockDim.x, t = threadIdx.x;
     const uint32_t per = (a.n_mats + T - 1) / T;
     const uint32_t lo = min(t * per, a.n_mats), hi = min(lo + per, a.n_mats);
@@ -129,18 +161,11 @@ __global__ void k_scan(BatchArgs a) {
         c2 += (c + 31u) >> 5;
         c3 += (surr && a.surr_slot[m] >= 0) ? (c + 127u) >> 7 : 0u;
     }
-    s_tot[0][t] = c0; s_tot[1][t] = c1; s_tot[2][t] = c2; s_tot[3][t] = c3;
-    __syncthreads();
-    // Hillis-Steele inclusive scan over the per-thread totals
-    for (uint32_t off = 1; off < T; off <<= 1) {
-        uint32_t v0 = 0, v1 = 0, v2 = 0, v3 = 0;
-        if (t >= off) { v0 = s_tot[0][t - off]; v1 = s_tot[1][t - off]; v2 = s_tot[2][t - off]; v3 = s_tot[3][t - off]; }
-        __syncthreads();
-        s_tot[0][t] += v0; s_tot[1][t] += v1; s_tot[2][t] += v2; s_tot[3][t] += v3;
-        __syncthreads();
-    }
-    uint32_t b0 = t ? s_tot[0][t - 1] : 0, b1 = t ? s_tot[1][t - 1] : 0, b2 = t ? s_tot[2][t - 1] : 0;
-    uint32_t b3 = t ? s_tot[3][t - 1] : 0;
+    uint32_t tot0, tot1, tot2, tot3;
+    uint32_t b0 = block_incl_scan(c0, s_tmp, &tot0) - c0;
+    uint32_t b1 = block_incl_scan(c1, s_tmp, &tot1) - c1;
+    uint32_t b2 = block_incl_scan(c2, s_tmp, &tot2) - c2;
+    uint32_t b3 = block_incl_scan(c3, s_tmp, &tot3) - c3;
     for (uint32_t m = lo; m < hi; ++m) {
         uint32_t c = a.counts[m];
         uint32_t k = (a.use_cache || surr) ? a.mats[m].n_roots : 0u;
@@ -155,14 +180,14 @@ __global__ void k_scan(BatchArgs a) {
         b3 += (surr && a.surr_slot[m] >= 0) ? (c + 127u) >> 7 : 0u;
     }
     if (t == T - 1) {
-        a.seg_start[a.n_mats] = s_tot[0][t];
-        a.probe_base[a.n_mats] = s_tot[1][t];
-        a.item_base[a.n_mats] = s_tot[2][t];
-        if (surr) a.surr_item_base[a.n_mats] = s_tot[3][t];
-        a.ctl->n_surr_items = surr ? s_tot[3][t] : 0u;
-        a.ctl->n_items = s_tot[2][t];
-        a.ctl->total_probes = s_tot[1][t];
-        if (s_tot[1][t] > a.probe_cap) {
+        a.seg_start[a.n_mats] = tot0;
+        a.probe_base[a.n_mats] = tot1;
+        a.item_base[a.n_mats] = tot2;
+        if (surr) a.surr_item_base[a.n_mats] = tot3;
+        a.ctl->n_surr_items = surr ? tot3 : 0u;
+        a.ctl->n_items = tot2;
+        a.ctl->total_probes = tot1;
+        if (tot1 > a.probe_cap) {
             // more probe records than the scratch holds: the batch does no work and the
             // next synchronising call reports it
             a.ctl->n_items = 0;
@@ -413,8 +438,12 @@ __device__ __forceinline__ void offer(const BatchArgs& a, bool act, uint32_t ori
         c.g = g;
         c.b = b;
         c.target = start | (shadows << 16);
-        if (idx < a.probe_cap) a.cands[idx] = c;
-        else atomicOr(&a.ctl->err, ERR_CAPACITY);
+        if (idx < a.probe_cap) {
+            a.cands[idx] = c;
+            if (!a.insert_rounds) a.lists[0][idx] = cell;   // compact cells for the binning
+        } else {
+            atomicOr(&a.ctl->err, ERR_CAPACITY);
+        }
     }
 }
 
@@ -753,28 +782,21 @@ __global__ void __launch_bounds__(EVAL_WARPS * 32) k_eval_fused(BatchArgs a, uin
 
 // Work items of the batched evaluation: ceil(misses / 32) per cacheable node.
 __global__ void k_scan_roots(BatchArgs a) {
-    __shared__ uint32_t s_tot[1024];
+    __shared__ uint32_t s_tmp[33];
     const uint32_t T = blockDim.x, t = threadIdx.x, N = a.n_roots_total;
     const uint32_t per = (N + T - 1) / T;
     const uint32_t lo = min(t * per, N), hi = min(lo + per, N);
     uint32_t c = 0;
     for (uint32_t g = lo; g < hi; ++g) c += (a.miss_cnt[g] + 31u) >> 5;
-    s_tot[t] = c;
-    __syncthreads();
-    for (uint32_t off = 1; off < T; off <<= 1) {
-        uint32_t v = t >= off ? s_tot[t - off] : 0u;
-        __syncthreads();
-        s_tot[t] += v;
-        __syncthreads();
-    }
-    uint32_t b = t ? s_tot[t - 1] : 0u;
+    uint32_t tot;
+    uint32_t b = block_incl_scan(c, s_tmp, &tot) - c;
     for (uint32_t g = lo; g < hi; ++g) {
         a.root_item_base[g] = b;
         b += (a.miss_cnt[g] + 31u) >> 5;
     }
     if (t == T - 1) {
-        a.root_item_base[N] = s_tot[t];
-        a.ctl->n_root_items = s_tot[t];
+        a.root_item_base[N] = tot;
+        a.ctl->n_root_items = tot;
     }
 }
 
@@ -975,7 +997,9 @@ __global__ void __launch_bounds__(256) k_insert(BatchArgs a) {
 // scatter: coalesced), then one block per bin groups its candidates by cell in shared
 // memory and one thread per cell inserts that cell's candidates in ascending order.
 constexpr uint32_t INS_CELLS = INSERT_BIN_CELLS;   // cells per bin (a multiple of 256)
-constexpr uint32_t INS_SMEM_BINS = 4096;  // bins counted in shared memory by the partition
+constexpr uint32_t INS_SMEM_BINS = 8192;  // bins counted in shared memory by the partition
+constexpr uint32_t INS_WARP_MAX = 256;     // a bin with at most this many candidates: one warp
+constexpr uint32_t INS_MID = 2048;         // at most this many: one block, staged in one pass
 
 // Inserts one candidate into a cell owned by the calling thread (Alg. 1 scan).
 __device__ __forceinline__ void insert_one(const BatchArgs& a, const Candidate& c, uint32_t ne,
@@ -1008,18 +1032,30 @@ __device__ __forceinline__ void insert_one(const BatchArgs& a, const Candidate& 
 
 __device__ __forceinline__ uint32_t bin_of(uint32_t cell) { return cell / INS_CELLS; }
 
-// Candidates per bin.
+// Candidates per bin, counted from the compact cell array the evaluation wrote.
 __global__ void __launch_bounds__(256) k_bin_count(BatchArgs a) {
     __shared__ uint32_t s_cnt[INS_SMEM_BINS];
     const uint32_t nb = a.n_bins;
-    const bool local = nb <= INS_SMEM_BINS;
+    const uint32_t n_in = min(a.ctl->n_cand, a.probe_cap);
+    if (blockIdx.x * blockDim.x >= n_in) return;   // uniform: this block has no candidates
+    // few candidates per bin: global atomics are cheaper than clearing and flushing the
+    // shared histogram
+    const bool local = nb <= INS_SMEM_BINS && n_in / gridDim.x >= nb / 4u;
     if (local) {
         for (uint32_t b = threadIdx.x; b < nb; b += blockDim.x) s_cnt[b] = 0;
         __syncthreads();
     }
-    const uint32_t n_in = min(a.ctl->n_cand, a.probe_cap);
-    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n_in; i += gridDim.x * blockDim.x)
-        atomicAdd(local ? &s_cnt[bin_of(a.cands[i].cell)] : &a.bin_cnt[bin_of(a.cands[i].cell)], 1u);
+    const uint32_t* cc = a.lists[0];
+    const uint32_t stride = gridDim.x * blockDim.x;
+    // four independent loads in flight per thread
+    for (uint32_t i0 = blockIdx.x * blockDim.x + threadIdx.x; i0 < n_in; i0 += 4 * stride) {
+        uint32_t c[4];
+#pragma unroll
+        for (uint32_t k = 0; k < 4; ++k) c[k] = i0 + k * stride < n_in ? cc[i0 + k * stride] : 0u;
+#pragma unroll
+        for (uint32_t k = 0; k < 4; ++k)
+            if (i0 + k * stride < n_in) atomicAdd(local ? &s_cnt[bin_of(c[k])] : &a.bin_cnt[bin_of(c[k])], 1u);
+    }
     if (local) {
         __syncthreads();
         for (uint32_t b = threadIdx.x; b < nb; b += blockDim.x)
@@ -1027,63 +1063,524 @@ __global__ void __launch_bounds__(256) k_bin_count(BatchArgs a) {
     }
 }
 
-// Exclusive scan of the bin counts (one block); bin_cnt becomes the fill cursor.
+// Exclusive scan of the bin counts (one block); bin_cnt becomes the fill cursor.  Also lists
+// the non-empty bins by the kernel that resolves them: a warp (at most INS_WARP_MAX
+// candidates), a block (at most INS_MID) or a block in ranges of cells (more).
 __global__ void k_bin_scan(BatchArgs a) {
-    __shared__ uint32_t s_tot[1024];
+    __shared__ uint32_t s_tmp[33];
+    __shared__ unsigned long long s_tmp64[33];
+    constexpr uint32_t PER_MAX = 8;   // bins per thread held in registers
     const uint32_t T = blockDim.x, t = threadIdx.x, N = a.n_bins;
     const uint32_t per = (N + T - 1) / T;
     const uint32_t lo = min(t * per, N), hi = min(lo + per, N);
+    // the class of a bin, as one of three 21-bit fields of a 64-bit counter
+    auto cls = [](uint32_t x) -> unsigned long long {
+        return x == 0 ? 0ull : x <= INS_WARP_MAX ? 1ull : x <= INS_MID ? (1ull << 21) : (1ull << 42);
+    };
+    uint32_t cv[PER_MAX];
     uint32_t c = 0;
-    for (uint32_t b = lo; b < hi; ++b) c += a.bin_cnt[b];
-    s_tot[t] = c;
-    __syncthreads();
-    for (uint32_t off = 1; off < T; off <<= 1) {
-        uint32_t v = t >= off ? s_tot[t - off] : 0u;
-        __syncthreads();
-        s_tot[t] += v;
-        __syncthreads();
+    unsigned long long nc = 0;
+    if (per <= PER_MAX) {
+#pragma unroll
+        for (uint32_t k = 0; k < PER_MAX; ++k) cv[k] = lo + k < hi ? a.bin_cnt[lo + k] : 0u;
+#pragma unroll
+        for (uint32_t k = 0; k < PER_MAX; ++k) {
+            c += cv[k];
+            nc += cls(cv[k]);
+        }
+    } else {
+        for (uint32_t b = lo; b < hi; ++b) {
+            const uint32_t x = a.bin_cnt[b];
+            c += x;
+            nc += cls(x);
+        }
     }
-    uint32_t base = t ? s_tot[t - 1] : 0u;
-    for (uint32_t b = lo; b < hi; ++b) {
-        const uint32_t c2 = a.bin_cnt[b];
+    uint32_t tot;
+    unsigned long long tcls;
+    uint32_t base = block_incl_scan(c, s_tmp, &tot) - c;
+    const unsigned long long pc = block_incl_scan(nc, s_tmp64, &tcls) - nc;
+    const uint32_t M21 = (1u << 21) - 1u;
+    const uint32_t tw = (uint32_t)tcls & M21, tm = (uint32_t)(tcls >> 21) & M21, tb = (uint32_t)(tcls >> 42) & M21;
+    uint32_t pw = (uint32_t)pc & M21, pm = tw + ((uint32_t)(pc >> 21) & M21), pb = tw + tm + ((uint32_t)(pc >> 42) & M21);
+    auto emit = [&](uint32_t b, uint32_t x) {
         a.bin_base[b] = base;
         a.bin_cnt[b] = base;
-        base += c2;
+        base += x;
+        if (x == 0) return;
+        if (x <= INS_WARP_MAX) a.bin_list[pw++] = b;
+        else if (x <= INS_MID) a.bin_list[pm++] = b;
+        else a.bin_list[pb++] = b;
+    };
+    if (per <= PER_MAX) {
+#pragma unroll
+        for (uint32_t k = 0; k < PER_MAX; ++k)
+            if (lo + k < hi) emit(lo + k, cv[k]);
+    } else {
+        for (uint32_t b = lo; b < hi; ++b) emit(b, a.bin_cnt[b]);
     }
-    if (t == T - 1) a.bin_base[N] = s_tot[t];
+    if (t == T - 1) {
+        a.bin_base[N] = tot;
+        a.ctl->bins_warp = tw;
+        a.ctl->bins_mid = tm;
+        a.ctl->bins_big = tb;
+    }
 }
 
-// Copies every candidate into its bin's range.
-__global__ void __launch_bounds__(512) k_bin_scatter(BatchArgs a) {
+// Copies every candidate into its bin's range.  A block takes a contiguous range of
+// candidates: it counts them per bin in shared memory, reserves its part of every bin with
+// one global atomic per bin, then places them.  The writes land at scattered positions;
+// nothing else is written (a scattered 4-byte write costs nearly as much as a 32-byte one).
+__global__ void __launch_bounds__(256) k_bin_scatter(BatchArgs a) {
     __shared__ uint32_t s_cnt[INS_SMEM_BINS];
+    constexpr uint32_t U = 4;   // candidates in flight per thread
     const uint32_t nb = a.n_bins;
-    const bool local = nb <= INS_SMEM_BINS;
     const uint32_t n_in = min(a.ctl->n_cand, a.probe_cap);
+    const uint32_t* cc = a.lists[0];
+    const uint32_t T = blockDim.x;
     uint32_t lo, hi;
     block_range(n_in, &lo, &hi);
+    if (lo >= hi) return;   // uniform: this block has no candidates
+    // few candidates in this block per bin: take positions with global atomics instead of
+    // clearing, filling and flushing the shared histogram
+    const bool local = nb <= INS_SMEM_BINS && hi - lo >= nb / 4u;
     if (local) {
-        for (uint32_t b = threadIdx.x; b < nb; b += blockDim.x) s_cnt[b] = 0;
+        for (uint32_t b = threadIdx.x; b < nb; b += T) s_cnt[b] = 0;
         __syncthreads();
-        for (uint32_t i = lo + threadIdx.x; i < hi; i += blockDim.x) atomicAdd(&s_cnt[bin_of(a.cands[i].cell)], 1u);
+        for (uint32_t i0 = lo + threadIdx.x; i0 < hi; i0 += U * T) {
+            uint32_t c[U];
+#pragma unroll
+            for (uint32_t k = 0; k < U; ++k) c[k] = i0 + k * T < hi ? cc[i0 + k * T] : 0u;
+#pragma unroll
+            for (uint32_t k = 0; k < U; ++k)
+                if (i0 + k * T < hi) atomicAdd(&s_cnt[bin_of(c[k])], 1u);
+        }
         __syncthreads();
-        for (uint32_t b = threadIdx.x; b < nb; b += blockDim.x)
+        for (uint32_t b = threadIdx.x; b < nb; b += T)
             if (s_cnt[b]) s_cnt[b] = atomicAdd(&a.bin_cnt[b], s_cnt[b]);
         __syncthreads();
     }
-    for (uint32_t i = lo + threadIdx.x; i < hi; i += blockDim.x) {
-        const Candidate c = a.cands[i];
-        const uint32_t b = bin_of(c.cell);
-        const uint32_t pos = atomicAdd(local ? &s_cnt[b] : &a.bin_cnt[b], 1u);
-        a.cands_binned[pos] = c;
+    const uint4* src = reinterpret_cast<const uint4*>(a.cands);
+    uint4* dst = reinterpret_cast<uint4*>(a.cands_binned);
+    for (uint32_t i0 = lo + threadIdx.x; i0 < hi; i0 += U * T) {
+        uint32_t c[U];
+        uint4 x[U][2];
+#pragma unroll
+        for (uint32_t k = 0; k < U; ++k) {
+            const uint32_t i = i0 + k * T;
+            if (i < hi) {
+                c[k] = cc[i];
+                x[k][0] = __ldcs(src + 2 * (size_t)i);
+                x[k][1] = __ldcs(src + 2 * (size_t)i + 1);
+            }
+        }
+#pragma unroll
+        for (uint32_t k = 0; k < U; ++k) {
+            const uint32_t i = i0 + k * T;
+            if (i < hi) {
+                const uint32_t b = bin_of(c[k]);
+                const uint32_t pos = atomicAdd(local ? &s_cnt[b] : &a.bin_cnt[b], 1u);
+                dst[2 * (size_t)pos] = x[k][0];
+                dst[2 * (size_t)pos + 1] = x[k][1];
+            }
+        }
     }
 }
 
-// One block per bin.  The bin's candidates (or, for a bin beyond INS_STAGE, those of a
-// range of its cells) are staged in shared memory grouped by cell: sort key (cell offset
-// << 44 | priority), hash2, target and source index.  One thread per cell sorts its
-// segment and inserts it with the cell's hash2 words in registers; a range holding a cell
-// with more than INS_CELL_SORT candidates is sorted by the whole block instead.  A single
-// cell with more candidates than INS_STAGE is resolved by a block-wide selection.
+// ---- resolution of one bin: its candidates are grouped by cell and each cell is resolved
+// in ascending (point, node) order by one thread holding the cell's hash2 words.  Bins are
+// resolved by one of three kernels according to their number of candidates: a warp per bin
+// (at most INS_WARP_MAX), a block per bin staged in one pass (at most INS_MID), or a block
+// per bin staged in ranges of cells (more).
+constexpr uint32_t INS_MID_T = INS_CELLS;               // one thread per cell of the bin
+constexpr uint32_t INS_MID_PER = INS_MID / INS_MID_T;   // candidates per thread
+constexpr uint8_t RES_NONE = 0xFFu;
+
+// Resolves one cell (one thread).  order[x0 .. x0 + n) lists the cell's candidates in
+// ascending priority as indices into the staged hash2 / target arrays; the slot each
+// inserted candidate took is written to res[] (RES_NONE for the others).  Every candidate
+// of a cell saw the same snapshot, so slots before its start held other keys and only the
+// slots filled by this insert can hold its hash2.
+template <typename IDX>
+__device__ __forceinline__ void resolve_cell(const BatchArgs& a, uint32_t cell, const IDX* order, uint32_t x0,
+                                             uint32_t n, const uint32_t* sh2, const uint32_t* stgt, uint8_t* res,
+                                             uint32_t ne, unsigned long long* n_ins, unsigned long long* n_dup,
+                                             unsigned long long* n_full) {
+    uint32_t* cw = cell_h2(a, cell);
+    uint32_t h[MAX_ENTRIES];
+    uint32_t used = ne;
+    for (uint32_t e = 0; e < ne; ++e) {
+        h[e] = __ldcg(&cw[e]);
+        if (h[e] == 0u && used == ne) used = e;
+    }
+    for (uint32_t x = x0; x < x0 + n; ++x) {
+        const uint32_t j = order[x];
+        const uint32_t hc = sh2[j], tg = stgt[j];
+        const uint32_t shadows = tg >> 16;
+        bool dup = false;
+        for (uint32_t e = tg & 0xFFFFu; e < used; ++e)
+            if (h[e] == hc) { dup = true; break; }
+        if (dup) {
+            *n_dup += 1u + shadows;
+        } else if (used >= ne) {
+            *n_full += 1u + shadows;
+        } else {
+            h[used] = hc;
+            cw[used] = hc;
+            res[j] = (uint8_t)used;
+            used++;
+            *n_ins += 1;
+            *n_dup += shadows;   // its shadows find it in the table
+        }
+    }
+}
+
+// The same for N_e <= 8 with the cell's hash2 words held in registers (w0, w1: the cell's
+// first 32 bytes, loaded by the caller).
+template <typename IDX>
+__device__ __forceinline__ void resolve_cell8(const BatchArgs& a, uint32_t cell, uint4 w0, uint4 w1, const IDX* order,
+                                              uint32_t x0, uint32_t n, const uint32_t* sh2, const uint32_t* stgt,
+                                              uint8_t* res, uint32_t ne, unsigned long long* n_ins,
+                                              unsigned long long* n_dup, unsigned long long* n_full) {
+    uint32_t h[8] = {w0.x, w0.y, w0.z, w0.w, w1.x, w1.y, w1.z, w1.w};
+    uint32_t used = ne;
+#pragma unroll
+    for (int e = 7; e >= 0; --e)
+        if ((uint32_t)e < ne && h[e] == 0u) used = (uint32_t)e;   // the first empty slot
+    uint32_t* cw = cell_h2(a, cell);
+    for (uint32_t x = x0; x < x0 + n; ++x) {
+        const uint32_t j = order[x];
+        const uint32_t hc = sh2[j], tg = stgt[j];
+        const uint32_t shadows = tg >> 16, st = tg & 0xFFFFu;
+        bool dup = false;
+#pragma unroll
+        for (uint32_t e = 0; e < 8; ++e) dup |= e >= st && e < used && h[e] == hc;
+        if (dup) {
+            *n_dup += 1u + shadows;
+        } else if (used >= ne) {
+            *n_full += 1u + shadows;
+        } else {
+#pragma unroll
+            for (uint32_t e = 0; e < 8; ++e)
+                if (e == used) h[e] = hc;
+            cw[used] = hc;
+            res[j] = (uint8_t)used;
+            used++;
+            *n_ins += 1;
+            *n_dup += shadows;   // its shadows find it in the table
+        }
+    }
+}
+
+// The first 32 bytes of a cell (its hash2 words for N_e <= 8; a cell is 16 * N_e bytes,
+// so 16 bytes are read for N_e <= 4).
+__device__ __forceinline__ void load_cell_words(const BatchArgs& a, uint32_t cell, uint4* w0, uint4* w1) {
+    const uint4* hw = reinterpret_cast<const uint4*>(cell_h2(a, cell));
+    *w0 = __ldcg(hw);
+    *w1 = a.n_entries > 4 ? __ldcg(hw + 1) : make_uint4(0, 0, 0, 0);
+}
+
+// Writes the value of an inserted candidate (binned index i) into its slot.
+__device__ __forceinline__ void write_value(const BatchArgs& a, uint32_t i, uint32_t cell, uint32_t slot) {
+    const float4 v = __ldcg(reinterpret_cast<const float4*>(&a.cands_binned[i].r));   // r, g, b, target
+    float* val = cell_val(a, cell, slot);
+    val[0] = v.x;
+    val[1] = v.y;
+    val[2] = v.z;
+}
+
+// Bins of 1 .. INS_WARP_MAX candidates: one warp per bin, with its own stage in shared
+// memory and no block barrier, so that many sparse bins are in flight per SM.  Lane l
+// reads candidates l, l + 32, ... once; a count per cell and a warp scan stage the bin
+// grouped by cell; each candidate's rank by priority within its cell orders the cell's segment;
+// lane l resolves cells 8l .. 8l + 7; then the inserted candidates write their values.
+constexpr uint32_t INS_WARP_PER = INS_WARP_MAX / 32;
+constexpr uint32_t INS_WARPS = 4;   // warps (bins in flight) per block
+static_assert(INS_CELLS == 8 * 32, "a lane resolves 8 consecutive cells of a bin");
+
+struct WarpStage {
+    unsigned long long key[INS_WARP_MAX];   // priority
+    uint32_t h2[INS_WARP_MAX];
+    uint32_t tgt[INS_WARP_MAX];
+    uint32_t cnt[INS_CELLS];
+    uint32_t off[INS_CELLS + 1];
+    uint16_t ord[INS_WARP_MAX];
+    uint8_t res[INS_WARP_MAX];
+};
+
+__global__ void __launch_bounds__(INS_WARPS * 32, 6) k_bin_insert_warp(BatchArgs a) {
+    __shared__ WarpStage s_stage[INS_WARPS];
+    const uint32_t w = threadIdx.x >> 5, lane = lane_id();
+    WarpStage& st = s_stage[w];
+    const uint32_t ne = a.n_entries;
+    const Candidate* cb = a.cands_binned;
+    unsigned long long n_dup = 0, n_full = 0, n_ins = 0;
+    const uint32_t n_list = a.ctl->bins_warp;
+    for (uint32_t x = blockIdx.x * INS_WARPS + w; x < n_list; x += gridDim.x * INS_WARPS) {
+        const uint32_t bin = a.bin_list[x];
+        const uint32_t lo = a.bin_base[bin], hi = a.bin_base[bin + 1];
+        const uint32_t c0 = bin * INS_CELLS;
+#pragma unroll
+        for (uint32_t q = 0; q < 8; ++q) st.cnt[8 * lane + q] = 0;
+        __syncwarp();
+        // ---- one read of every candidate; count per cell, rank of arrival in its cell
+        uint32_t cl[INS_WARP_PER], pos[INS_WARP_PER], hh[INS_WARP_PER], tg[INS_WARP_PER];
+        unsigned long long pr[INS_WARP_PER];
+#pragma unroll
+        for (uint32_t k = 0; k < INS_WARP_PER; ++k) {
+            const uint32_t i = lo + lane + 32 * k;
+            cl[k] = 0;
+            if (i < hi) {
+                const uint4 q = __ldcg(reinterpret_cast<const uint4*>(&cb[i]));   // prio, cell, hash2
+                tg[k] = __ldcg(&cb[i].target);
+                pr[k] = ((unsigned long long)q.y << 32) | q.x;
+                cl[k] = q.z - c0;
+                hh[k] = q.w;
+            }
+        }
+#pragma unroll
+        for (uint32_t k = 0; k < INS_WARP_PER; ++k) {
+            const uint32_t i = lo + lane + 32 * k;
+            pos[k] = i < hi ? atomicAdd(&st.cnt[cl[k]], 1u) : 0u;
+        }
+        __syncwarp();
+        // ---- exclusive scan of the counts: lane l holds cells 8l .. 8l + 7
+        uint32_t v[8], sum = 0;
+#pragma unroll
+        for (uint32_t q = 0; q < 8; ++q) {
+            v[q] = st.cnt[8 * lane + q];
+            sum += v[q];
+        }
+        uint32_t incl = sum;
+#pragma unroll
+        for (uint32_t o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(FULL_MASK, incl, o);
+            if (lane >= o) incl += y;
+        }
+        uint32_t run = incl - sum;
+#pragma unroll
+        for (uint32_t q = 0; q < 8; ++q) {
+            st.off[8 * lane + q] = run;
+            run += v[q];
+        }
+        if (lane == 31) st.off[INS_CELLS] = incl;
+        __syncwarp();
+        // ---- place: priority, hash2 and target, grouped by cell
+#pragma unroll
+        for (uint32_t k = 0; k < INS_WARP_PER; ++k) {
+            const uint32_t i = lo + lane + 32 * k;
+            pos[k] += st.off[cl[k]];
+            if (i < hi) {
+                st.key[pos[k]] = pr[k];
+                st.h2[pos[k]] = hh[k];
+                st.tgt[pos[k]] = tg[k];
+                st.res[pos[k]] = RES_NONE;
+            }
+        }
+        __syncwarp();
+        // ---- order each cell's segment by priority
+#pragma unroll
+        for (uint32_t k = 0; k < INS_WARP_PER; ++k) {
+            const uint32_t i = lo + lane + 32 * k;
+            if (i < hi) {
+                const uint32_t x0 = st.off[cl[k]], x1 = st.off[cl[k] + 1];
+                const unsigned long long kv = st.key[pos[k]];
+                uint32_t rank = 0;
+                for (uint32_t y = x0; y < x1; ++y) rank += st.key[y] < kv ? 1u : 0u;
+                st.ord[x0 + rank] = (uint16_t)pos[k];
+            }
+        }
+        __syncwarp();
+        // ---- resolve this lane's cells, two at a time so that their loads overlap
+#pragma unroll
+        for (uint32_t q = 0; q < 8; q += 2) {
+            const uint32_t ca = 8 * lane + q, cbb = ca + 1;
+            const uint32_t xa = st.off[ca], xb = st.off[cbb], xe = st.off[cbb + 1];
+            if (ne <= 8) {
+                uint4 a0 = make_uint4(0, 0, 0, 0), a1 = a0, b0 = a0, b1 = a0;
+                if (xb > xa) load_cell_words(a, c0 + ca, &a0, &a1);
+                if (xe > xb) load_cell_words(a, c0 + cbb, &b0, &b1);
+                if (xb > xa)
+                    resolve_cell8(a, c0 + ca, a0, a1, st.ord, xa, xb - xa, st.h2, st.tgt, st.res, ne, &n_ins, &n_dup,
+                                  &n_full);
+                if (xe > xb)
+                    resolve_cell8(a, c0 + cbb, b0, b1, st.ord, xb, xe - xb, st.h2, st.tgt, st.res, ne, &n_ins, &n_dup,
+                                  &n_full);
+            } else {
+                if (xb > xa) resolve_cell(a, c0 + ca, st.ord, xa, xb - xa, st.h2, st.tgt, st.res, ne, &n_ins, &n_dup, &n_full);
+                if (xe > xb) resolve_cell(a, c0 + cbb, st.ord, xb, xe - xb, st.h2, st.tgt, st.res, ne, &n_ins, &n_dup, &n_full);
+            }
+        }
+        __syncwarp();
+        // ---- values of the inserted candidates
+#pragma unroll
+        for (uint32_t k = 0; k < INS_WARP_PER; ++k) {
+            const uint32_t i = lo + lane + 32 * k;
+            if (i < hi) {
+                const uint8_t r = st.res[pos[k]];
+                if (r != RES_NONE) write_value(a, i, c0 + cl[k], r);
+            }
+        }
+        __syncwarp();
+    }
+    warp_add_u64(&a.stats[ST_DUP], n_dup);
+    warp_add_u64(&a.stats[ST_FULL], n_full);
+    warp_add_u64(&a.stats[ST_INSERTED], n_ins);
+}
+
+struct MidSmem {   // byte offsets into dynamic shared memory
+    static constexpr uint32_t key = 0;                                // u64 [INS_MID] priority
+    static constexpr uint32_t h2 = key + INS_MID * 8;                 // u32 [INS_MID]
+    static constexpr uint32_t tgt = h2 + INS_MID * 4;                 // u32 [INS_MID]
+    static constexpr uint32_t ord = tgt + INS_MID * 4;                // u16 [INS_MID]
+    static constexpr uint32_t res = ord + INS_MID * 2;                // u8  [INS_MID]
+    static constexpr uint32_t cnt = res + INS_MID;                    // u32 [INS_CELLS]
+    static constexpr uint32_t off = cnt + INS_CELLS * 4;              // u32 [INS_CELLS + 4]
+    static constexpr uint32_t wsum = off + (INS_CELLS + 4) * 4;       // u32 [32]
+    static constexpr uint32_t end = wsum + 32 * 4;
+};
+static_assert(INS_MID <= 65536, "staged indices are 16-bit");
+static_assert(INS_MID_T % 32 == 0 && INS_MID_T <= 1024, "one thread per cell of a bin");
+
+size_t insert_mid_smem_bytes() { return MidSmem::end; }
+
+// Bins of INS_WARP_MAX + 1 .. INS_MID candidates: a block per bin, one thread per cell.  Each
+// thread takes up to INS_MID_PER candidates; a count per cell, a block scan and one
+// placement stage the bin grouped by cell in a single read.  Each candidate's rank by
+// priority within its cell orders the cell's segment (all candidates in parallel); one
+// thread per cell resolves it with the cell's hash2 words, loaded while the bin is
+// staged; then the inserted candidates write their values, all in parallel.
+__global__ void __launch_bounds__(INS_MID_T, 4) k_bin_insert_mid(BatchArgs a) {
+    extern __shared__ __align__(16) unsigned char msm[];
+    unsigned long long* s_key = reinterpret_cast<unsigned long long*>(msm + MidSmem::key);
+    uint32_t* s_h2 = reinterpret_cast<uint32_t*>(msm + MidSmem::h2);
+    uint32_t* s_tgt = reinterpret_cast<uint32_t*>(msm + MidSmem::tgt);
+    uint16_t* s_ord = reinterpret_cast<uint16_t*>(msm + MidSmem::ord);
+    uint8_t* s_res = reinterpret_cast<uint8_t*>(msm + MidSmem::res);
+    uint32_t* s_cnt = reinterpret_cast<uint32_t*>(msm + MidSmem::cnt);
+    uint32_t* s_off = reinterpret_cast<uint32_t*>(msm + MidSmem::off);
+    uint32_t* s_wsum = reinterpret_cast<uint32_t*>(msm + MidSmem::wsum);
+    const uint32_t t = threadIdx.x, lane = lane_id(), warp = t >> 5;
+    const uint32_t ne = a.n_entries;
+    const Candidate* cb = a.cands_binned;
+    unsigned long long n_dup = 0, n_full = 0, n_ins = 0;
+    const uint32_t n_list = a.ctl->bins_mid, first = a.ctl->bins_warp;
+    for (uint32_t x = blockIdx.x; x < n_list; x += gridDim.x) {
+        const uint32_t bin = a.bin_list[first + x];
+        const uint32_t lo = a.bin_base[bin], hi = a.bin_base[bin + 1];
+        const uint32_t c0 = bin * INS_CELLS;
+        s_cnt[t] = 0;
+        __syncthreads();
+        // ---- count per cell; each candidate's rank of arrival among its cell's
+        uint32_t cl[INS_MID_PER], pos[INS_MID_PER];
+#pragma unroll
+        for (uint32_t k = 0; k < INS_MID_PER; ++k) {
+            const uint32_t i = lo + t + k * INS_MID_T;
+            cl[k] = i < hi ? __ldcg(&cb[i].cell) - c0 : 0u;
+        }
+#pragma unroll
+        for (uint32_t k = 0; k < INS_MID_PER; ++k) {
+            const uint32_t i = lo + t + k * INS_MID_T;
+            pos[k] = i < hi ? atomicAdd(&s_cnt[cl[k]], 1u) : 0u;
+        }
+        __syncthreads();
+        // ---- this thread's cell: start loading its hash2 words
+        const uint32_t v = s_cnt[t];
+        uint4 w0 = make_uint4(0, 0, 0, 0), w1 = w0;
+        if (v && ne <= 8) load_cell_words(a, c0 + t, &w0, &w1);
+        // ---- exclusive scan of the per-cell counts (thread t holds cell t)
+        uint32_t incl = v;
+#pragma unroll
+        for (uint32_t o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(FULL_MASK, incl, o);
+            if (lane >= o) incl += y;
+        }
+        if (lane == 31) s_wsum[warp] = incl;
+        __syncthreads();
+        if (warp == 0) {
+            const uint32_t wv = lane < INS_MID_T / 32 ? s_wsum[lane] : 0u;
+            uint32_t wi = wv;
+#pragma unroll
+            for (uint32_t o = 1; o < 32; o <<= 1) {
+                const uint32_t y = __shfl_up_sync(FULL_MASK, wi, o);
+                if (lane >= o) wi += y;
+            }
+            s_wsum[lane] = wi - wv;
+        }
+        __syncthreads();
+        const uint32_t excl = incl - v + s_wsum[warp];
+        s_off[t] = excl;
+        __syncthreads();
+        // ---- place: priority, hash2 and target, grouped by cell
+#pragma unroll
+        for (uint32_t k = 0; k < INS_MID_PER; ++k) pos[k] += s_off[cl[k]];
+#pragma unroll
+        for (uint32_t h = 0; h < INS_MID_PER; h += 4) {
+            uint4 q[4];
+            uint32_t tg[4];
+#pragma unroll
+            for (uint32_t k = 0; k < 4; ++k) {
+                const uint32_t i = lo + t + (h + k) * INS_MID_T;
+                if (i < hi) {
+                    q[k] = __ldcg(reinterpret_cast<const uint4*>(&cb[i]));   // prio, cell, hash2
+                    tg[k] = __ldcg(&cb[i].target);
+                }
+            }
+#pragma unroll
+            for (uint32_t k = 0; k < 4; ++k) {
+                const uint32_t i = lo + t + (h + k) * INS_MID_T;
+                if (i < hi) {
+                    const uint32_t p = pos[h + k];
+                    s_key[p] = ((unsigned long long)q[k].y << 32) | q[k].x;
+                    s_h2[p] = q[k].w;
+                    s_tgt[p] = tg[k];
+                    s_res[p] = RES_NONE;
+                }
+            }
+        }
+        __syncthreads();
+        // ---- order each cell's segment by priority: every candidate finds its rank
+#pragma unroll
+        for (uint32_t k = 0; k < INS_MID_PER; ++k) {
+            const uint32_t i = lo + t + k * INS_MID_T;
+            if (i < hi) {
+                const uint32_t x0 = s_off[cl[k]], n = s_cnt[cl[k]];
+                const unsigned long long kv = s_key[pos[k]];
+                uint32_t rank = 0;
+                for (uint32_t y = x0; y < x0 + n; ++y) rank += s_key[y] < kv ? 1u : 0u;
+                s_ord[x0 + rank] = (uint16_t)pos[k];
+            }
+        }
+        __syncthreads();
+        // ---- resolve: one thread per cell
+        if (v) {
+            if (ne <= 8)
+                resolve_cell8(a, c0 + t, w0, w1, s_ord, excl, v, s_h2, s_tgt, s_res, ne, &n_ins, &n_dup, &n_full);
+            else
+                resolve_cell(a, c0 + t, s_ord, excl, v, s_h2, s_tgt, s_res, ne, &n_ins, &n_dup, &n_full);
+        }
+        __syncthreads();
+        // ---- values of the inserted candidates
+#pragma unroll
+        for (uint32_t k = 0; k < INS_MID_PER; ++k) {
+            const uint32_t i = lo + t + k * INS_MID_T;
+            if (i < hi) {
+                const uint8_t r = s_res[pos[k]];
+                if (r != RES_NONE) write_value(a, i, c0 + cl[k], r);
+            }
+        }
+        __syncthreads();
+    }
+    warp_add_u64(&a.stats[ST_DUP], n_dup);
+    warp_add_u64(&a.stats[ST_FULL], n_full);
+    warp_add_u64(&a.stats[ST_INSERTED], n_ins);
+}
+
+// Bins of more than INS_MID candidates: one block per bin stages the candidates of a range
+// of cells at a time in shared memory, grouped by cell: sort key (cell offset << 44 |
+// priority), hash2, target and source index.  One thread per cell sorts its segment and inserts it with the cell's hash2
+// words in registers; a range holding a cell with more than INS_CELL_SORT candidates is
+// sorted by the whole block instead.  A single cell with more candidates than INS_STAGE is
+// resolved by a block-wide selection.
 constexpr uint32_t INS_STAGE = 1024;
 constexpr uint32_t INS_CELL_SORT = 64;
 static_assert(INS_CELLS % 256 == 0, "k_bin_insert scans INS_CELLS / 256 cells per thread");
@@ -1164,9 +1661,10 @@ __global__ void __launch_bounds__(256, 6) k_bin_insert(BatchArgs a) {
     const uint32_t t = threadIdx.x, T = blockDim.x;
     const Candidate* cb = a.cands_binned;
     unsigned long long n_dup = 0, n_full = 0, n_ins = 0;
-    for (uint32_t bin = blockIdx.x; bin < a.n_bins; bin += gridDim.x) {
+    const uint32_t n_list = a.ctl->bins_big, first = a.ctl->bins_warp + a.ctl->bins_mid;
+    for (uint32_t x = blockIdx.x; x < n_list; x += gridDim.x) {
+        const uint32_t bin = a.bin_list[first + x];
         const uint32_t lo = a.bin_base[bin], hi = a.bin_base[bin + 1];
-        if (lo == hi) continue;                                 // uniform in the block
         const uint32_t c0 = bin * INS_CELLS;
         // ---- per-cell counts and their exclusive scan
         for (uint32_t k = t; k < INS_CELLS; k += T) s_cnt[k] = 0;
@@ -1280,7 +1778,7 @@ __global__ void __launch_bounds__(256, 6) k_bin_insert(BatchArgs a) {
                     unsigned long long best = ~0ull;
                     uint32_t bi = 0;
                     for (uint32_t i = lo + t; i < hi; i += T) {
-                        if (cb[i].cell != cell) continue;
+                        if (__ldcg(&cb[i].cell) != cell) continue;
                         const unsigned long long p = cb[i].prio;
                         if ((step == 0 || p > last) && p < best) { best = p; bi = i; }
                     }
@@ -1383,13 +1881,20 @@ static cudaError_t launch_insert(const BatchArgs& a, cudaStream_t s, int num_sms
         if ((e = cudaMemsetAsync(a.bin_cnt, 0, (size_t)a.n_bins * sizeof(uint32_t), s)) != cudaSuccess) return e;
         k_bin_count<<<gs_blocks, 256, 0, s>>>(a);
         k_bin_scan<<<1, 1024, 0, s>>>(a);
-        // one block per SM: each block reserves its range of every bin with one atomic
-        k_bin_scatter<<<num_sms, 512, 0, s>>>(a);
+        k_bin_scatter<<<num_sms * 8, 256, 0, s>>>(a);
+        // each bin is resolved by exactly one of the three kernels, chosen by its size
+        k_bin_insert_warp<<<std::min<uint32_t>((a.n_bins + INS_WARPS - 1) / INS_WARPS, (uint32_t)num_sms * 8u),
+                            INS_WARPS * 32, 0, s>>>(a);
+        const size_t msm = insert_mid_smem_bytes();
+        if ((e = cudaFuncSetAttribute(k_bin_insert_mid, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)msm)) !=
+            cudaSuccess)
+            return e;
+        k_bin_insert_mid<<<std::min<uint32_t>(a.n_bins, (uint32_t)num_sms * 4u), INS_MID_T, msm, s>>>(a);
         const size_t ism = insert_smem_bytes();
         if ((e = cudaFuncSetAttribute(k_bin_insert, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ism)) != cudaSuccess)
             return e;
-        k_bin_insert<<<std::min<uint32_t>(a.n_bins, (uint32_t)num_sms * 12u), 256, ism, s>>>(a);
-        *nl += 4;
+        k_bin_insert<<<std::min<uint32_t>(a.n_bins, (uint32_t)num_sms * 6u), 256, ism, s>>>(a);
+        *nl += 6;
     }
     return e;
 }

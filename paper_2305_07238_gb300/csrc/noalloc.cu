@@ -138,6 +138,7 @@ extern "C" pmc_status pmc_eval_batch_noalloc(pmc_cache* c, const pmc_points* pts
     a.split = c->use_cache && c->split;
     a.insert_rounds = (c->desc.flags & PMC_INSERT_ROUNDS) ? 1 : 0;
     a.n_bins = c->n_bins; a.bin_cnt = c->d_bins; a.bin_base = c->d_bins + c->n_bins;
+    a.bin_list = c->d_bins + 2 * (size_t)c->n_bins + 1;
     a.cands_binned = reinterpret_cast<Candidate*>(base + OFF_BINNED);
     if (c->use_surrogates && c->any_surr_on) {
         a.surr_slot = c->d_surr_slot; a.surr_ord = c->d_surr_ord; a.surr_theta = c->d_surr_theta;

@@ -107,6 +107,9 @@ struct Control {
     uint32_t n_cand;            // candidates emitted by the evaluation
     uint32_t n_root_items;      // work items of the batched evaluation of misses
     uint32_t n_surr_items;      // work items of the surrogate inference
+    uint32_t bins_warp;         // insert bins resolved by a warp, by a block, by ranges
+    uint32_t bins_mid;
+    uint32_t bins_big;
     uint32_t pad1;
     // persistent
     uint32_t epoch;             // claim epoch of round 0 of the current batch
@@ -157,7 +160,10 @@ struct BatchArgs {
     uint64_t n_cells; uint32_t n_entries; uint32_t level; uint32_t cells_pow2_mask;
     int use_cache; int debug;
     float4* probes; uint32_t probe_cap;
-    Candidate* cands; uint32_t* lists[3];
+    Candidate* cands;
+    // index lists of the claim-round insert; the cell-grouped insert uses lists[0] for
+    // the cells of the candidates in emission order
+    uint32_t* lists[3];
     Control* ctl; unsigned long long* stats;
     // batched evaluation of misses
     int split;
@@ -170,9 +176,11 @@ struct BatchArgs {
     // ordinal; FP32 parameters per slot; work items of 128 points per material
     const int32_t* surr_slot; const int32_t* surr_ord; const float* surr_theta;
     uint32_t* surr_item_base;  // n_mats + 1 (computed by k_scan)
-    uint32_t n_bins;           // cell-grouped insert: ceil(n_cells / 512) bins
+    uint32_t n_bins;           // cell-grouped insert: ceil(n_cells / INSERT_BIN_CELLS) bins
     uint32_t* bin_cnt;         // n_bins
     uint32_t* bin_base;        // n_bins + 1
+    uint32_t* bin_list;        // n_bins: the non-empty bins by resolving kernel (warp, block,
+                               // ranges), each class in ascending bin order
     Candidate* cands_binned;   // probe_cap
     // schedule (chosen by the caller's flags or by the autotuner)
     int unsorted;              // 1: no grouping; k_eval_fused probes inline in batch order
@@ -180,7 +188,7 @@ struct BatchArgs {
     uint32_t lookup_rb;        // k_lookup: probes in flight per lane (1, 2 or 4)
 };
 
-constexpr uint32_t INSERT_BIN_CELLS = 512;
+constexpr uint32_t INSERT_BIN_CELLS = 256;
 
 
 // Phases timed by the optional CUDA events of a batch.
