@@ -10,7 +10,7 @@ import ctypes as C
 
 import numpy as np
 
-from paper_2305_07238_gb300.workload import NODE_DTYPE, POINT_FIELDS
+from paper_2305_07238_gb300.workload import CONE_FIELDS, NODE_DTYPE, POINT_FIELDS
 
 from .build import build_oracle
 
@@ -77,7 +77,11 @@ def lib():
         L.orc_cache_roots.restype = None
         L.orc_cache_roots.argtypes = [vp, u32, vp]
         L.orc_run_batch.restype = C.c_int
-        L.orc_run_batch.argtypes = [vp, u64] + [vp] * 9 + [vp] * 7
+        L.orc_run_batch.argtypes = [vp, u64] + [vp] * 9 + [vp] * 7 + [vp] * 4
+        L.orc_level.restype = C.c_int32
+        L.orc_level.argtypes = [C.c_float] * 4 + [C.c_int32]
+        L.orc_cache_set_level_offset.restype = None
+        L.orc_cache_set_level_offset.argtypes = [vp, C.c_int32]
         L.orc_cache_table.restype = None
         L.orc_cache_table.argtypes = [vp, vp, vp]
         L.orc_cache_stats.restype = None
@@ -110,6 +114,7 @@ def fbm(x, y, scale, octaves, lac, gain, seed): return lib().orc_fbm(x, y, scale
 def voronoi_f1(x, y, seed): return lib().orc_voronoi_f1(x, y, seed)
 def texel(u, level): return lib().orc_texel(u, level)
 def key(mat, node, level, u, v): return lib().orc_key(mat, node, level, u, v)
+def level(g1u, g1v, g2u, g2v, offset=0): return lib().orc_level(g1u, g1v, g2u, g2v, offset)
 def hash1(k): return lib().orc_hash1(k)
 def hash2(k): return lib().orc_hash2(k)
 
@@ -170,7 +175,7 @@ class Cache:
     """Sequential emulation of the progressive cache over a set of materials."""
 
     def __init__(self, materials, n_cells, n_entries, level=10, min_root_nodes=2,
-                 cache_off=False, hash_hook=None):
+                 cache_off=False, hash_hook=None, level_offset=0):
         self._mats = [_nodes(m) for m in materials]
         self.n_cells, self.n_entries, self.level = n_cells, n_entries, level
         self.off = bool(cache_off) or n_cells == 0 or n_entries == 0
@@ -181,6 +186,7 @@ class Cache:
         counts = np.array([len(m) for m in self._mats], dtype=np.uint32)
         if lib().orc_cache_set_materials(self._h, len(self._mats), ptrs, _ptr(counts)) != 0:
             raise ValueError("malformed network")
+        lib().orc_cache_set_level_offset(self._h, int(level_offset))
         self._hook = None
         if hash_hook is not None:
             def _cb(k, nc, cell, h2):
@@ -215,9 +221,12 @@ class Cache:
 
     def run_batch(self, pts: dict, probes: bool = False):
         """One progressive pass.  Returns a dict with rgb (3, n) float64, hits,
-        evaluated, status and (if probes) key/cell/h2/hit per (point, root)."""
+        evaluated, status and (if probes) key/cell/h2/hit per (point, root).  If pts holds
+        the ray-cone gradients (CONE_FIELDS), each point takes its own mip level."""
         arrs = [np.ascontiguousarray(pts[k], dtype=np.uint32 if k == "mat" else np.float32)
                 for k in POINT_FIELDS]
+        cones = [np.ascontiguousarray(pts[k], dtype=np.float32) for k in CONE_FIELDS] \
+            if all(k in pts for k in CONE_FIELDS) else [None] * 4
         n = len(arrs[0])
         rgb = np.zeros(3 * n, dtype=np.float64)
         hits = np.zeros(n, dtype=np.uint16)
@@ -233,7 +242,8 @@ class Cache:
             ph = np.zeros(max(total, 1), dtype=np.uint32)
             phit = np.zeros(max(total, 1), dtype=np.uint8)
         st = lib().orc_run_batch(self._h, n, *[_ptr(a) for a in arrs], _ptr(rgb), _ptr(hits),
-                                 _ptr(ev), _ptr(pk), _ptr(pc), _ptr(ph), _ptr(phit))
+                                 _ptr(ev), _ptr(pk), _ptr(pc), _ptr(ph), _ptr(phit),
+                                 *[_ptr(g) for g in cones])
         out = {"rgb": rgb.reshape(3, n), "hits": hits, "evaluated": ev, "status": st}
         if probes:
             out.update(key=pk[:total], cell=pc[:total], h2=ph[:total], hit=phit[:total])

@@ -236,6 +236,30 @@ uint32_t orc_texel(float u, uint32_t level) {
     return (uint32_t)t;
 }
 
+/* Mip level of the virtual texture from the ray-cone footprint (Sec. 3.1, Eq. 1):
+ * lambda = -log2(min(|g1|, |g2|)), g1 and g2 the texture-coordinate gradients along the
+ * axes of the footprint ellipse.  Readings: each squared norm is formed in FP32 with
+ * every product and the sum rounded to nearest (the decision is taken in the precision
+ * the inputs have); the level is the floor of Eq. 1, so that a texel is at least as wide
+ * as the footprint; the offset of the discussion (Sec. 4) is added; the result is
+ * clamped to [0, 13].  A zero footprint gives the finest level, an infinite or NaN one
+ * the coarsest. */
+int32_t orc_level(float g1u, float g1v, float g2u, float g2v, int32_t offset) {
+    const float a = g1u * g1u, b = g1v * g1v, c = g2u * g2u, d = g2v * g2v;   /* no contraction */
+    const float s1 = a + b, s2 = c + d;
+    double lam;
+    if (isnan(s1) || isnan(s2)) {
+        lam = -INFINITY;
+    } else {
+        const double m = sqrt((double)(s1 < s2 ? s1 : s2));   /* min(|g1|, |g2|) */
+        lam = m == 0.0 ? INFINITY : floor(-log2(m));
+    }
+    lam += (double)offset;
+    if (!(lam > 0.0)) return 0;
+    if (lam > 13.0) return 13;
+    return (int32_t)lam;
+}
+
 /* Descriptor (Sec. 3.1): material ID, node ID (index in the network as given),
  * mip level lambda, texel indices, packed as
  * mat<<48 | node<<32 | level<<26 | iu<<13 | iv. */
@@ -414,7 +438,8 @@ typedef struct {
 struct orc_cache {
     uint64_t n_cells;
     uint32_t n_entries;
-    uint32_t level;
+    uint32_t level;        /* every point's level when no gradients are given */
+    int32_t level_offset;  /* added to the ray-cone level (Sec. 4) */
     uint32_t min_root_nodes;
     int off;
     uint32_t* h2;  /* n_cells * n_entries, 0 = empty */
@@ -489,6 +514,8 @@ int orc_cache_set_materials(orc_cache* c, uint32_t n_mats, const orc_node* const
 }
 
 void orc_cache_set_hash_override(orc_cache* c, orc_hash_override_fn fn) { c->hook = fn; }
+
+void orc_cache_set_level_offset(orc_cache* c, int32_t offset) { c->level_offset = offset; }
 
 void orc_cache_reset(orc_cache* c) {
     size_t slots = c->off ? 0 : (size_t)c->n_cells * c->n_entries;
@@ -599,7 +626,8 @@ int orc_run_batch(orc_cache* c, uint64_t n, const float* u, const float* v,
                   const uint32_t* mat, const float* px, const float* py, const float* pz,
                   const float* nx, const float* ny, const float* nz, double* rgb,
                   uint16_t* hits, uint32_t* evaluated, uint64_t* probe_key,
-                  uint64_t* probe_cell, uint32_t* probe_h2, uint8_t* probe_hit) {
+                  uint64_t* probe_cell, uint32_t* probe_h2, uint8_t* probe_hit,
+                  const float* g1u, const float* g1v, const float* g2u, const float* g2v) {
     int status = ORC_OK;
     uint32_t max_n = 1;
     for (uint32_t m = 0; m < c->n_mats; ++m)
@@ -626,6 +654,9 @@ int orc_run_batch(orc_cache* c, uint64_t n, const float* u, const float* v,
         }
         const orc_mat* M = &c->mats[mat[i]];
         const double sp[8] = {u[i], v[i], px[i], py[i], pz[i], nx[i], ny[i], nz[i]};
+        /* the point's mip level: from its ray-cone gradients (Eq. 1) if given */
+        const uint32_t level =
+            g1u ? (uint32_t)orc_level(g1u[i], g1v[i], g2u[i], g2v[i], c->level_offset) : c->level;
         uint32_t n_hit = 0;
         memset(hit, 0, M->n);
         for (uint32_t r = 0; r < M->n_roots; ++r) {
@@ -639,7 +670,7 @@ int orc_run_batch(orc_cache* c, uint64_t n, const float* u, const float* v,
                 for (int k = 0; k < 3; ++k) hitval[3 * node + k] = clamp01(y[k]);
             }
             if (c->off) continue;
-            uint64_t key = orc_key(mat[i], node, c->level, u[i], v[i]);
+            uint64_t key = orc_key(mat[i], node, level, u[i], v[i]);
             uint64_t cell, slot;
             uint32_t h2;
             cell_and_check(c, key, &cell, &h2);

@@ -98,6 +98,9 @@ void orc_eval_node(const orc_node* nd, const double* a, const double* b, const d
 
 /* ---- descriptor and hashes (Sec. 3.1, Eq. 1, Sec. 3.2) -------------------- */
 uint32_t orc_texel(float u, uint32_t level);
+/* Eq. 1: floor(-log2(min(|g1|, |g2|))) + offset, clamped to [0, 13] (squared norms in
+ * FP32; a zero footprint gives 13, an infinite or NaN one 0). */
+int32_t orc_level(float g1u, float g1v, float g2u, float g2v, int32_t offset);
 uint64_t orc_key(uint32_t mat, uint32_t node, uint32_t level, float u, float v);
 uint64_t orc_hash1(uint64_t key);
 uint32_t orc_hash2(uint64_t key);
@@ -129,6 +132,8 @@ void orc_cache_free(orc_cache* c);
 int orc_cache_set_materials(orc_cache* c, uint32_t n_mats, const orc_node* const* mat_nodes,
                             const uint32_t* n_nodes);
 void orc_cache_set_hash_override(orc_cache* c, orc_hash_override_fn fn);
+/* Offset added to the ray-cone level of every point (default 0). */
+void orc_cache_set_level_offset(orc_cache* c, int32_t offset);
 void orc_cache_reset(orc_cache* c);
 uint32_t orc_cache_n_roots(const orc_cache* c, uint32_t mat);
 /* Root node IDs of a material in ascending order (n_roots entries). */
@@ -139,13 +144,16 @@ void orc_cache_roots(const orc_cache* c, uint32_t mat, uint32_t* out);
  * evaluated (n; nodes evaluated per point), may be NULL;
  * probe_* arrays (sum over points of the point's root count, point-major,
  * roots in ascending node ID), each may be NULL.
+ * g1u, g1v, g2u, g2v: per-point ray-cone texture-coordinate gradients (n each) that
+ * give each point its own mip level (orc_level), or all NULL for the cache's level.
  * Returns ORC_OK, or ORC_ERR_BADMAT if some mat[i] >= n_mats (those points
  * get rgb 0, hits 0 and no probes). */
 int orc_run_batch(orc_cache* c, uint64_t n, const float* u, const float* v,
                   const uint32_t* mat, const float* px, const float* py, const float* pz,
                   const float* nx, const float* ny, const float* nz, double* rgb,
                   uint16_t* hits, uint32_t* evaluated, uint64_t* probe_key,
-                  uint64_t* probe_cell, uint32_t* probe_h2, uint8_t* probe_hit);
+                  uint64_t* probe_cell, uint32_t* probe_h2, uint8_t* probe_hit,
+                  const float* g1u, const float* g1v, const float* g2u, const float* g2v);
 
 /* Table contents: h2[N_c*N_e], rgb[3*N_c*N_e] (slot-major r,g,b). */
 void orc_cache_table(const orc_cache* c, uint32_t* h2, float* rgb);

@@ -56,6 +56,8 @@ NODE_DTYPE = np.dtype(
 assert NODE_DTYPE.itemsize == 100
 
 POINT_FIELDS = ("u", "v", "mat", "px", "py", "pz", "nx", "ny", "nz")
+# optional per-point ray-cone texture-coordinate gradients (the two axes of the footprint)
+CONE_FIELDS = ("g1u", "g1v", "g2u", "g2v")
 
 
 class Builder:
@@ -138,12 +140,16 @@ def _pack(u, v, mat, p, nrm) -> dict:
     }
 
 
+def _fields(pts: dict):
+    return POINT_FIELDS + (CONE_FIELDS if all(k in pts for k in CONE_FIELDS) else ())
+
+
 def slice_points(pts: dict, lo: int, hi: int) -> dict:
-    return {k: np.ascontiguousarray(pts[k][lo:hi]) for k in POINT_FIELDS}
+    return {k: np.ascontiguousarray(pts[k][lo:hi]) for k in _fields(pts)}
 
 
 def concat_points(parts) -> dict:
-    return {k: np.concatenate([p[k] for p in parts]) for k in POINT_FIELDS}
+    return {k: np.concatenate([p[k] for p in parts]) for k in _fields(parts[0])}
 
 
 # --------------------------------------------------------------------------------------
@@ -349,6 +355,8 @@ class FrameSpec:
     delta_lo: float = 2.0 ** -12
     delta_hi: float = 2.0 ** -8
     seed: int = 0
+    aniso_hi: float = 4.0       # ray-cone footprints: axis ratio log-uniform on [1, aniso_hi]
+    spread: float = 0.5         # footprint width = delta * 2^U(-spread, spread) per sample
 
 
 class Frame:
@@ -377,6 +385,10 @@ class Frame:
         self.tile_e1 = e1
         self.tile_e2 = np.cross(nrm, e1)
         self.tile_c = rng.uniform(-8.0, 8.0, (nt, 3))
+        # ray-cone footprint of a tile: orientation and axis ratio of the ellipse in UV
+        crng = np.random.Generator(np.random.PCG64([spec.seed, 5]))
+        self.tile_theta = crng.uniform(0.0, 2.0 * math.pi, nt)
+        self.tile_aniso = np.exp(crng.uniform(0.0, math.log(spec.aniso_hi), nt))
         self.tiles_x = tx
         ys, xs = np.mgrid[0:spec.height, 0:spec.width]
         self.px_x = xs.ravel()
@@ -403,12 +415,16 @@ class Frame:
                 "e2": [np.ascontiguousarray(self.tile_e2[t, k]) for k in range(3)],
                 "mat": np.ascontiguousarray(self.tile_mat[t], dtype=np.uint32),
                 "n": [np.ascontiguousarray(self.tile_n[t, k], dtype=np.float32) for k in range(3)],
+                "cos": np.cos(self.tile_theta[t]), "sin": np.sin(self.tile_theta[t]),
+                "aniso": self.tile_aniso[t],
             }
         return self._pix
 
-    def points(self, pass_index: int, rows: tuple | None = None) -> dict:
+    def points(self, pass_index: int, rows: tuple | None = None, cones: bool = False) -> dict:
         """One sample per pixel (scanline order) for pass `pass_index`; `rows` = (y0, y1)
-        restricts to a band of pixel rows (same draws as the full pass)."""
+        restricts to a band of pixel rows (same draws as the full pass).  cones: add the
+        ray-cone gradients of every sample (CONE_FIELDS): an ellipse of the tile's
+        orientation and axis ratio whose minor axis is delta * 2^U(-spread, spread)."""
         spec = self.spec
         rng = np.random.Generator(np.random.PCG64([spec.seed, 2, pass_index]))
         jit = rng.random((2, self.n_pixels))
@@ -424,7 +440,14 @@ class Frame:
         wx = w * (L["fx"][sel] + jx)
         wy = w * (L["fy"][sel] + jy)
         p = [(L["c"][k][sel] + wx * L["e1"][k][sel] + wy * L["e2"][k][sel]) * 0.25 for k in range(3)]
-        return _pack(u, v, L["mat"][sel], p, [L["n"][k][sel] for k in range(3)])
+        out = _pack(u, v, L["mat"][sel], p, [L["n"][k][sel] for k in range(3)])
+        if cones:
+            crng = np.random.Generator(np.random.PCG64([spec.seed, 6, pass_index]))
+            f = d * np.exp2(crng.uniform(-spec.spread, spec.spread, self.n_pixels)[sel])
+            c, s_, b = L["cos"][sel], L["sin"][sel], L["aniso"][sel]
+            out.update(g1u=(f * c).astype(np.float32), g1v=(f * s_).astype(np.float32),
+                       g2u=(-f * b * s_).astype(np.float32), g2v=(f * b * c).astype(np.float32))
+        return out
 
     def points_torch(self, pass_index: int, device="cuda", rows: tuple | None = None) -> dict:
         """The same recipe drawn with torch's generator on `device` (for long sequences of
