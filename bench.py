@@ -309,6 +309,12 @@ def ours(args, rank, world, local_rank, dist):
         line["surrogate"] = surrogate_leg(torch, P, dev, local_rank, seed=rank)
     if "f128" in legs:
         line["frame128"] = frame128_leg(torch, P, dev, local_rank, seed=rank)
+    if "cones" in legs:
+        line["ray_cones"] = cones_leg(torch, P, dev, local_rank, seed=rank)
+        if line["ray_cones"] and u_value == u_value:
+            for off in (0, -1):
+                r = line["ray_cones"][f"offset{off}"]
+                r["speedup_cached_over_uncached"] = round(r["cached"] / u_value, 3)
     if "sweep" in legs:
         line["scale_sweep"] = sweep_leg(torch, P, dev, local_rank, seed=rank)
     if rank == 0 and not args.no_cpu_baseline and "cpu" in legs:
@@ -395,6 +401,50 @@ def frame128_leg(torch, P, dev, local_rank, seed=0):
     res["speedup_cached_over_uncached"] = round(best / max(res["uncached_graph_grouped"],
                                                            res["uncached_graph_unsorted"]), 3)
     res["graph_over_eager"] = round(res["graph_grouped"] / res["eager"], 3)
+    del passes
+    torch.cuda.empty_cache()
+    return res
+
+
+def cones_leg(torch, P, dev, local_rank, seed=0):
+    """The benchmark frame with every shading point at its own mip level, from the
+    texture-coordinate gradients of its ray-cone footprint (Eq. 1; footprint minor axis
+    delta * 2^U(-1/2, 1/2), axis ratio log-uniform on [1, 4]), for level offsets 0 and -1:
+    cached points/s (whole frame as one CUDA graph, autotuned schedule), hit rate and the
+    levels the first pass uses.  Uncached evaluation does not depend on the level."""
+    mats, frame = workload(seed)
+    n = WIDTH * HEIGHT
+    passes = [P.points_to_device(frame.points(p, cones=True), dev) for p in range(SPP)]
+    outs = torch.empty((3, n), dtype=torch.float32, device=dev)
+    hits = torch.empty(n, dtype=torch.int16, device=dev)
+    lv = P.compute_levels(passes[0]["g1u"], passes[0]["g1v"], passes[0]["g2u"], passes[0]["g2v"])
+    hist = torch.bincount(lv.long(), minlength=14).cpu().numpy()
+    res = {"config": "frame 1920x1080x16spp, per-point mip level from ray-cone gradients, "
+                     f"table {N_CELLS}x{N_ENTRIES} slots", "unit": UNIT,
+           "levels_pass0": {int(k): int(v) for k, v in enumerate(hist) if v}}
+    for off in (0, -1):
+        c = P.Cache(mats, N_CELLS, N_ENTRIES, uv_level=LEVEL, level_offset=off, device=local_rank)
+        for p in range(2):
+            c.eval_batch(passes[p], outs, hits)
+        c.autotune(passes[2], reps=2)
+        c.reset()
+        for p in range(SPP):
+            c.eval_batch(passes[p], outs, hits)
+        st = c.stats()
+        g = c.graph(passes, [outs] * SPP, [hits] * SPP, reset=True)
+        g.launch()
+        torch.cuda.synchronize()
+        t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        t0.record()
+        for _ in range(3):
+            g.launch()
+        t1.record()
+        torch.cuda.synchronize()
+        g.close()
+        c.close()
+        res[f"offset{off}"] = {"cached": round(3 * n * SPP / (t0.elapsed_time(t1) / 1e3), 1),
+                               "hit_rate": round(st["hits"] / max(1, st["lookups"]), 4),
+                               "inserted": st["inserted"], "dropped_full": st["dropped_full"]}
     del passes
     torch.cuda.empty_cache()
     return res
@@ -716,8 +766,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--legs", default="cached,uncached,e2e,surr,f128,cpu",
-                    help="comma list of cached, uncached, e2e, surr, f128, sweep, cpu (sweep is not in the "
+    ap.add_argument("--legs", default="cached,uncached,e2e,surr,f128,cones,cpu",
+                    help="comma list of cached, uncached, e2e, surr, f128, cones, sweep, cpu (sweep is not in the "
                          "default: about a minute more; profiling runs take 'cached')")
     ap.add_argument("--profile", action="store_true",
                     help="eager frames only, for ncu launch lists (prints launches per frame)")

@@ -145,9 +145,19 @@ typedef struct {
                                 of cacheable nodes of any material.  A batch that
                                 needs more does no work and the next pmc_sync /
                                 pmc_stats returns PMC_ERR_UNSUPPORTED            */
+    int32_t level_offset;    /* -13 .. 13, added to the level of every point that
+                                carries ray-cone gradients (pmc_points g1u ..);
+                                positive values give finer texels (Sec. 4)      */
 } pmc_cache_desc;
 
-/* ---- shading points: structure of arrays, n entries each, DEVICE memory ----- */
+/* ---- shading points: structure of arrays, n entries each, DEVICE memory ----- *
+ * g1u, g1v, g2u, g2v (optional): the texture-coordinate gradients along the two axes of
+ * the point's ray-cone footprint (Sec. 3.1).  With them every point takes its own mip
+ * level of the virtual texture (Eq. 1):
+ *   level = clamp(floor(-log2(min(|g1|, |g2|))) + level_offset, 0, 13),
+ * the squared norms formed in FP32 (each product and the sum rounded to nearest); a
+ * zero footprint gives 13, an infinite or NaN one 0.  All four NULL: every point uses
+ * the cache's uv_level.  Either all four or none must be given. */
 typedef struct {
     const float* u;
     const float* v;
@@ -159,6 +169,10 @@ typedef struct {
     const float* ny;
     const float* nz;
     uint64_t n; /* 0 .. 2^28 */
+    const float* g1u;
+    const float* g1v;
+    const float* g2u;
+    const float* g2v;
 } pmc_points;
 
 /* Cumulative counters since creation or pmc_reset. */
@@ -197,9 +211,9 @@ pmc_status pmc_create_cache(const pmc_cache_desc* desc, const pmc_material* mats
 pmc_status pmc_eval_batch(pmc_cache* cache, const pmc_points* pts, float* out_rgb,
                           uint16_t* out_hits, void* stream);
 
-/* Same pass with HOST buffers: copies the points in, runs pmc_eval_batch, copies
- * rgb (and hits if non-NULL) out and waits for `stream`.  Pinned host memory gives
- * the fastest copies; pageable memory works. */
+/* Same pass with HOST buffers (the gradients too, if given): copies the points in, runs
+ * pmc_eval_batch, copies rgb (and hits if non-NULL) out and waits for `stream`.  Pinned
+ * host memory gives the fastest copies; pageable memory works. */
 pmc_status pmc_eval_batch_host(pmc_cache* cache, const pmc_points* host_pts,
                                float* host_rgb, uint16_t* host_hits, void* stream);
 
@@ -250,6 +264,12 @@ pmc_status pmc_analyze_material(const pmc_material* mat, uint32_t min_root_nodes
 pmc_status pmc_compute_keys(const uint32_t* mat, const uint32_t* node, const float* u,
                             const float* v, uint64_t n, uint32_t level, uint64_t n_cells,
                             uint64_t* key, uint64_t* cell, uint32_t* h2, void* stream);
+
+/* The per-point mip level of Eq. 1 (Sec. 3.1) for n gradient pairs, DEVICE arrays:
+ * level[i] = clamp(floor(-log2(min(|g1_i|, |g2_i|))) + offset, 0, 13) as a pass computes
+ * it (see pmc_points).  offset: -13 .. 13.  Asynchronous on `stream`. */
+pmc_status pmc_compute_levels(const float* g1u, const float* g1v, const float* g2u, const float* g2v,
+                              uint64_t n, int32_t offset, uint32_t* level, void* stream);
 
 /* Per-phase device timing of later batches, measured with CUDA events recorded on
  * each batch's stream: 0 = grouping by material (histogram, scan, scatter),
@@ -365,7 +385,7 @@ pmc_status pmc_mlp_train(float* theta, float* adam_m, float* adam_v, const float
 #define PMC_NOALLOC_MAX_POINTS 8192u
 #define PMC_NOALLOC_MAX_PROBES 32768u
 #define PMC_NOALLOC_MAX_MATERIALS 4096u
-#define PMC_NOALLOC_SCRATCH_BYTES 3522816u
+#define PMC_NOALLOC_SCRATCH_BYTES 3555584u
 pmc_status pmc_eval_batch_noalloc(pmc_cache* cache, const pmc_points* pts, float* out_rgb,
                                   uint16_t* out_hits, void* stream);
 

@@ -78,7 +78,7 @@ pmc_status ensure_scratch(pmc_cache* c, uint64_t n) {
     if (pcap > 0xFFFFFFFFull) return PMC_ERR_UNSUPPORTED;
     pmc_status s;
     if ((s = dalloc(&c->d_seg, 5 * ((size_t)c->n_mats + 1))) != PMC_OK) return s;
-    if ((s = dalloc(&c->d_sorted, 8 * (size_t)cap)) != PMC_OK) return s;
+    if ((s = dalloc(&c->d_sorted, 9 * (size_t)cap)) != PMC_OK) return s;   // 8 planes + levels
     if ((s = dalloc(&c->d_sidx, (size_t)cap)) != PMC_OK) return s;
     if ((s = dalloc(&c->d_probes, (size_t)pcap)) != PMC_OK) return s;
     if ((s = dalloc(&c->d_cands, (size_t)pcap)) != PMC_OK) return s;
@@ -168,6 +168,7 @@ pmc_status pmc_create_cache(const pmc_cache_desc* desc, const pmc_material* mats
     *out = nullptr;
     if (n_mats == 0 || n_mats > 65536u) return PMC_ERR_INVALID_ARG;
     if (desc->uv_level > 13) return PMC_ERR_INVALID_ARG;
+    if (desc->level_offset < -13 || desc->level_offset > 13) return PMC_ERR_INVALID_ARG;
     const bool off = (desc->flags & PMC_CACHE_OFF) != 0;
     if (!off) {
         if (desc->n_cells == 0 || desc->n_cells > 0xFFFFFFFFull) return PMC_ERR_INVALID_ARG;
@@ -323,6 +324,9 @@ pmc_status check_points(const pmc_points* pts, const float* out_rgb, bool need_o
     if (n > 0 && (!pts->u || !pts->v || !pts->mat || !pts->px || !pts->py || !pts->pz || !pts->nx ||
                   !pts->ny || !pts->nz || (need_out && !out_rgb)))
         return PMC_ERR_INVALID_ARG;
+    // the ray-cone gradients come as all four arrays or none
+    const int ng = (pts->g1u != nullptr) + (pts->g1v != nullptr) + (pts->g2u != nullptr) + (pts->g2v != nullptr);
+    if (ng != 0 && ng != 4) return PMC_ERR_INVALID_ARG;
     return PMC_OK;
 }
 
@@ -347,6 +351,8 @@ pmc_status enqueue_batch(pmc_cache* c, const pmc_points* pts, float* out_rgb, ui
     a.px = pts->px; a.py = pts->py; a.pz = pts->pz;
     a.nx = pts->nx; a.ny = pts->ny; a.nz = pts->nz;
     a.n = (uint32_t)n;
+    a.g1u = pts->g1u; a.g1v = pts->g1v; a.g2u = pts->g2u; a.g2v = pts->g2v;
+    a.level_offset = c->desc.level_offset;
     a.out_rgb = out_rgb; a.out_hits = out_hits;
     a.mats = c->d_mats; a.n_mats = c->n_mats;
     a.prog = c->d_prog; a.params = c->d_params; a.roots = c->d_roots;
@@ -360,6 +366,7 @@ pmc_status enqueue_batch(pmc_cache* c, const pmc_points* pts, float* out_rgb, ui
     a.su = c->d_sorted; a.sv = c->d_sorted + P; a.spx = c->d_sorted + 2 * P; a.spy = c->d_sorted + 3 * P;
     a.spz = c->d_sorted + 4 * P; a.snx = c->d_sorted + 5 * P; a.sny = c->d_sorted + 6 * P;
     a.snz = c->d_sorted + 7 * P; a.sidx = c->d_sidx;
+    a.slev = reinterpret_cast<uint32_t*>(c->d_sorted + 8 * P);
     a.table = c->d_table; a.claims = c->d_claims;
     a.table_empty = c->table_empty ? 1 : 0;
     a.keys_inline = (c->use_cache && c->table_empty) ? 1 : 0;
@@ -431,6 +438,9 @@ pmc_status pmc_eval_batch_host(pmc_cache* c, const pmc_points* hp, float* host_r
     if (n > 0 && (!hp->u || !hp->v || !hp->mat || !hp->px || !hp->py || !hp->pz || !hp->nx || !hp->ny ||
                   !hp->nz || !host_rgb))
         return PMC_ERR_INVALID_ARG;
+    pmc_status cs = check_points(hp, host_rgb);
+    if (cs != PMC_OK) return cs;
+    const bool cones = hp->g1u != nullptr;
     DeviceGuard g(c->desc.device);
     if (!g.ok) return PMC_ERR_INVALID_ARG;
     cudaStream_t s = (cudaStream_t)stream;
@@ -441,20 +451,24 @@ pmc_status pmc_eval_batch_host(pmc_cache* c, const pmc_points* hp, float* host_r
         dfree(&c->d_hhits);
         c->cap_host = 0;
         pmc_status st;
-        if ((st = dalloc(&c->d_hpts, 9 * (size_t)n)) != PMC_OK) return st;
+        if ((st = dalloc(&c->d_hpts, 13 * (size_t)n)) != PMC_OK) return st;   // 9 planes + gradients
         if ((st = dalloc(&c->d_hrgb, 3 * (size_t)n)) != PMC_OK) return st;
         if ((st = dalloc(&c->d_hhits, (size_t)n)) != PMC_OK) return st;
         c->cap_host = n;
     }
     const size_t C = c->cap_host;
     float* d = c->d_hpts;
-    const void* src[9] = {hp->u, hp->v, hp->mat, hp->px, hp->py, hp->pz, hp->nx, hp->ny, hp->nz};
+    const void* src[13] = {hp->u, hp->v, hp->mat, hp->px, hp->py, hp->pz, hp->nx, hp->ny, hp->nz,
+                           hp->g1u, hp->g1v, hp->g2u, hp->g2v};
     cudaError_t e = cudaSuccess;
-    for (int k = 0; k < 9 && e == cudaSuccess && n; ++k)
+    const int planes = cones ? 13 : 9;
+    for (int k = 0; k < planes && e == cudaSuccess && n; ++k)
         e = cudaMemcpyAsync(d + k * C, src[k], n * 4, cudaMemcpyHostToDevice, s);
     if (e != cudaSuccess) return cuda_fail(c, e);
     pmc_points dp{d, d + C, (const uint32_t*)(d + 2 * C), d + 3 * C, d + 4 * C, d + 5 * C,
-                  d + 6 * C, d + 7 * C, d + 8 * C, n};
+                  d + 6 * C, d + 7 * C, d + 8 * C, n,
+                  cones ? d + 9 * C : nullptr, cones ? d + 10 * C : nullptr,
+                  cones ? d + 11 * C : nullptr, cones ? d + 12 * C : nullptr};
     pmc_status st = pmc_eval_batch(c, &dp, c->d_hrgb, host_hits ? c->d_hhits : nullptr, stream);
     if (st != PMC_OK) return st;
     for (int k = 0; k < 3 && e == cudaSuccess && n; ++k)
@@ -883,6 +897,15 @@ pmc_status pmc_mlp_train(float* theta, float* adam_m, float* adam_v, const float
                                      (uint64_t)step0 * 128u, step0, total_steps, lr, 2.0f / (3.0f * 128.0f), 0, 1,
                                      (cudaStream_t)stream);
     return e == cudaSuccess ? PMC_OK : cuda_fail(nullptr, e);
+}
+
+pmc_status pmc_compute_levels(const float* g1u, const float* g1v, const float* g2u, const float* g2v,
+                              uint64_t n, int32_t offset, uint32_t* level, void* stream) {
+    if (offset < -13 || offset > 13) return PMC_ERR_INVALID_ARG;
+    if (n && (!g1u || !g1v || !g2u || !g2v || !level)) return PMC_ERR_INVALID_ARG;
+    cudaError_t e = launch_levels(g1u, g1v, g2u, g2v, n, offset, level, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(nullptr, e);
+    return PMC_OK;
 }
 
 pmc_status pmc_compute_keys(const uint32_t* mat, const uint32_t* node, const float* u, const float* v,

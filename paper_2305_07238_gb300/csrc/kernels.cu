@@ -208,6 +208,7 @@ __device__ __forceinline__ void scatter_point(const BatchArgs& a, uint32_t i, ui
     a.sny[pos] = a.ny[i];
     a.snz[pos] = a.nz[i];
     a.sidx[pos] = i;
+    if (a.g1u) a.slev[pos] = d_level(a.g1u[i], a.g1v[i], a.g2u[i], a.g2v[i], a.level_offset);
 }
 
 __device__ __forceinline__ void zero_output(const BatchArgs& a, uint32_t i) {
@@ -318,10 +319,11 @@ __global__ void __launch_bounds__(256) k_lookup(BatchArgs a) {
         const uint32_t j = (item - __ldg(&a.item_base[m])) * 32u + lane;
         const bool valid = j < cnt;
         const uint32_t s = __ldg(&a.seg_start[m]) + j;
-        uint32_t iu = 0, iv = 0;
+        uint32_t iu = 0, iv = 0, lev = a.level;
         if (valid) {
-            iu = d_texel(a.su[s], a.level);
-            iv = d_texel(a.sv[s], a.level);
+            if (a.g1u) lev = a.slev[s];
+            iu = d_texel(a.su[s], lev);
+            iv = d_texel(a.sv[s], lev);
         }
         const MatInfo mi = a.mats[m];
         const int32_t surr = a.surr_ord ? a.surr_ord[m] : -1;   // a surrogate's node is not probed
@@ -338,7 +340,7 @@ __global__ void __launch_bounds__(256) k_lookup(BatchArgs a) {
                 h2[b] = 0;
                 if (act[b]) {
                     const uint32_t node = __ldg(&a.roots[mi.root_base + r0 + b]);
-                    d_address(d_key(m, node, a.level, iu, iv), a.n_cells, a.cells_pow2_mask, &cell[b], &h2[b]);
+                    d_address(d_key(m, node, lev, iu, iv), a.n_cells, a.cells_pow2_mask, &cell[b], &h2[b]);
                 }
                 const uint4* hw = reinterpret_cast<const uint4*>(cell_h2(a, cell[b]));
                 const bool ld = act[b] && !a.table_empty;   // an empty table misses at slot 0
@@ -488,10 +490,11 @@ __global__ void __launch_bounds__(EVAL_WARPS * 32) k_eval(BatchArgs a, uint32_t*
         int skip_end = -1;          // lane inactive while pc <= skip_end
         uint32_t hits = 0, cand_cell = 0, cand_h2 = 0, cand_node = 0, cand_start = 0;
         bool cand_full = false;
-        uint32_t iu = 0, iv = 0;
+        uint32_t iu = 0, iv = 0, lev = a.level;
         if (a.keys_inline && valid) {
-            iu = d_texel(pt.u, a.level);
-            iv = d_texel(pt.v, a.level);
+            if (a.g1u) lev = a.slev[s];
+            iu = d_texel(pt.u, lev);
+            iv = d_texel(pt.v, lev);
         }
         // the next instruction is fetched while the current one executes
         const int len = (int)(outer ? mi.outer_len : mi.prog_len);
@@ -537,7 +540,7 @@ __global__ void __launch_bounds__(EVAL_WARPS * 32) k_eval(BatchArgs a, uint32_t*
                     // empty table: every probe misses at slot 0, so the descriptor is all
                     // the insert needs (no lookup kernel, no probe record)
                     if (valid) {
-                        d_address(d_key(m, ins.z, a.level, iu, iv), a.n_cells, a.cells_pow2_mask, &cand_cell, &cand_h2);
+                        d_address(d_key(m, ins.z, lev, iu, iv), a.n_cells, a.cells_pow2_mask, &cand_cell, &cand_h2);
                         cand_start = 0;
                         cand_full = false;
                         cand_node = ins.z;
@@ -652,6 +655,7 @@ __global__ void __launch_bounds__(EVAL_WARPS * 32) k_eval_fused(BatchArgs a, uin
         }
         if (chunk >= n_chunks) break;
         uint32_t i = 0, m = 0, cnt = 0, jj = 0;   // i: the point's index in the batch
+        uint32_t lev = a.level;
         bool ok = false;
         PointIn pt{0, 0, 0, 0, 0, 0, 0, 0};
         if (GROUPED) {
@@ -665,6 +669,7 @@ __global__ void __launch_bounds__(EVAL_WARPS * 32) k_eval_fused(BatchArgs a, uin
                 pt.px = a.spx[s]; pt.py = a.spy[s]; pt.pz = a.spz[s];
                 pt.nx = a.snx[s]; pt.ny = a.sny[s]; pt.nz = a.snz[s];
                 i = a.sidx[s];
+                if (a.g1u) lev = a.slev[s];
             }
         } else {
             i = chunk * 32u + lane;
@@ -679,12 +684,13 @@ __global__ void __launch_bounds__(EVAL_WARPS * 32) k_eval_fused(BatchArgs a, uin
                 pt.u = a.u[i]; pt.v = a.v[i];
                 pt.px = a.px[i]; pt.py = a.py[i]; pt.pz = a.pz[i];
                 pt.nx = a.nx[i]; pt.ny = a.ny[i]; pt.nz = a.nz[i];
+                if (a.g1u) lev = d_level(a.g1u[i], a.g1v[i], a.g2u[i], a.g2v[i], a.level_offset);
             }
         }
         uint32_t iu = 0, iv = 0;
         if (ok) {
-            iu = d_texel(pt.u, a.level);
-            iv = d_texel(pt.v, a.level);
+            iu = d_texel(pt.u, lev);
+            iv = d_texel(pt.v, lev);
         }
         const int32_t surr = (GROUPED && a.surr_ord) ? a.surr_ord[m] : -1;
         unsigned todo = __ballot_sync(FULL_MASK, ok);
@@ -717,7 +723,7 @@ __global__ void __launch_bounds__(EVAL_WARPS * 32) k_eval_fused(BatchArgs a, uin
                         }
                         need = false;
                     } else if (a.use_cache && mine) {
-                        d_address(d_key(mg, ins.z, a.level, iu, iv), a.n_cells, a.cells_pow2_mask, &cand_cell, &cand_h2);
+                        d_address(d_key(mg, ins.z, lev, iu, iv), a.n_cells, a.cells_pow2_mask, &cand_cell, &cand_h2);
                         bool hit = false;
                         const int first = a.table_empty ? 0 : probe_cell(a, cand_cell, cand_h2, &hit);
                         n_look++;
@@ -1810,6 +1816,24 @@ __global__ void k_finish(BatchArgs a) {
         if (a.use_cache) a.ctl->epoch += a.n_entries + 1u;
         a.stats[ST_BATCHES] += 1ull;
     }
+}
+
+// =======================================================================================
+// Stand-alone mip levels (parity checks of Eq. 1)
+// =======================================================================================
+__global__ void k_levels(const float* g1u, const float* g1v, const float* g2u, const float* g2v, uint64_t n,
+                         int32_t offset, uint32_t* level) {
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x)
+        level[i] = d_level(g1u[i], g1v[i], g2u[i], g2v[i], offset);
+}
+
+cudaError_t launch_levels(const float* g1u, const float* g1v, const float* g2u, const float* g2v, uint64_t n,
+                          int32_t offset, uint32_t* level, cudaStream_t s) {
+    if (n == 0) return cudaSuccess;
+    uint64_t blocks = (n + 255) / 256;
+    if (blocks > 65535) blocks = 65535;
+    k_levels<<<(unsigned)blocks, 256, 0, s>>>(g1u, g1v, g2u, g2v, n, offset, level);
+    return cudaGetLastError();
 }
 
 // =======================================================================================

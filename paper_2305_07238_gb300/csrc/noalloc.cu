@@ -17,8 +17,8 @@ constexpr size_t NA_MATS1 = (size_t)PMC_NOALLOC_MAX_MATERIALS + 1;
 constexpr size_t NA_POINTS = PMC_NOALLOC_MAX_POINTS;
 constexpr size_t NA_PROBES = PMC_NOALLOC_MAX_PROBES;
 constexpr size_t OFF_SEG = 0;                                          // 5 x (mats + 1) u32
-constexpr size_t OFF_SORTED = OFF_SEG + align256(5 * NA_MATS1 * 4);     // 8 float planes
-constexpr size_t OFF_SIDX = OFF_SORTED + align256(8 * NA_POINTS * 4);  // u32 point indices
+constexpr size_t OFF_SORTED = OFF_SEG + align256(5 * NA_MATS1 * 4);     // 8 float planes, u32 levels
+constexpr size_t OFF_SIDX = OFF_SORTED + align256(9 * NA_POINTS * 4);  // u32 point indices
 constexpr size_t OFF_PROBES = OFF_SIDX + align256(NA_POINTS * 4);      // 16-B probe records
 constexpr size_t OFF_CANDS = OFF_PROBES + align256(NA_PROBES * 16);    // 32-B candidates
 constexpr size_t OFF_LISTS = OFF_CANDS + align256(NA_PROBES * 32);     // 3 u32 index lists
@@ -68,6 +68,8 @@ extern "C" pmc_status pmc_eval_batch_noalloc(pmc_cache* c, const pmc_points* pts
     if (n > 0 && (!pts->u || !pts->v || !pts->mat || !pts->px || !pts->py || !pts->pz || !pts->nx ||
                   !pts->ny || !pts->nz || !out_rgb))
         return PMC_ERR_INVALID_ARG;
+    const int ng = (pts->g1u != nullptr) + (pts->g1v != nullptr) + (pts->g2u != nullptr) + (pts->g2v != nullptr);
+    if (ng != 0 && ng != 4) return PMC_ERR_INVALID_ARG;   // all four gradients or none
     const uint64_t probes = (c->use_cache || (c->use_surrogates && c->any_surr_on)) ? n * (uint64_t)c->max_roots : 0;
     if (n > PMC_NOALLOC_MAX_POINTS || c->n_mats > PMC_NOALLOC_MAX_MATERIALS || probes > PMC_NOALLOC_MAX_PROBES) {
         fprintf(stderr,
@@ -106,6 +108,8 @@ extern "C" pmc_status pmc_eval_batch_noalloc(pmc_cache* c, const pmc_points* pts
     a.px = pts->px; a.py = pts->py; a.pz = pts->pz;
     a.nx = pts->nx; a.ny = pts->ny; a.nz = pts->nz;
     a.n = (uint32_t)n;
+    a.g1u = pts->g1u; a.g1v = pts->g1v; a.g2u = pts->g2u; a.g2v = pts->g2v;
+    a.level_offset = c->desc.level_offset;
     a.out_rgb = out_rgb; a.out_hits = out_hits;
     a.mats = c->d_mats; a.n_mats = c->n_mats;
     a.prog = c->d_prog; a.params = c->d_params; a.roots = c->d_roots;
@@ -120,6 +124,7 @@ extern "C" pmc_status pmc_eval_batch_noalloc(pmc_cache* c, const pmc_points* pts
     a.su = sorted; a.sv = sorted + NA_POINTS; a.spx = sorted + 2 * NA_POINTS; a.spy = sorted + 3 * NA_POINTS;
     a.spz = sorted + 4 * NA_POINTS; a.snx = sorted + 5 * NA_POINTS; a.sny = sorted + 6 * NA_POINTS;
     a.snz = sorted + 7 * NA_POINTS;
+    a.slev = reinterpret_cast<uint32_t*>(sorted + 8 * NA_POINTS);
     a.sidx = reinterpret_cast<uint32_t*>(base + OFF_SIDX);
     a.table = c->d_table; a.claims = c->d_claims;
     a.table_empty = c->table_empty ? 1 : 0;

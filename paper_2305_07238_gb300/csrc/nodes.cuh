@@ -48,6 +48,26 @@ __device__ __forceinline__ uint32_t d_texel(float u, uint32_t level) {
     return min(t, res - 1u);
 }
 
+// Mip level of the virtual texture from the ray-cone footprint (Sec. 3.1, Eq. 1):
+// floor(-log2(min(|g1|, |g2|))) + offset, clamped to [0, 13].  The squared norms are formed
+// in FP32 with every product and the sum rounded to nearest (no fused multiply-add), and
+// the floor is read off the exponent E and fraction f of the smaller one, s = (1 + f) 2^E:
+// -log2(sqrt(s)) = -(E + log2(1 + f)) / 2, whose floor is -ceil(E / 2) when f = 0 and
+// -floor(E / 2) - 1 otherwise.  A zero or subnormal s (level 63 or more) gives 13 for any
+// offset of at least -13; an infinite or NaN one gives 0.
+__device__ __forceinline__ uint32_t d_level(float g1u, float g1v, float g2u, float g2v, int32_t offset) {
+    const float s1 = __fadd_rn(__fmul_rn(g1u, g1u), __fmul_rn(g1v, g1v));
+    const float s2 = __fadd_rn(__fmul_rn(g2u, g2u), __fmul_rn(g2v, g2v));
+    if (s1 != s1 || s2 != s2) return 0u;
+    const uint32_t b = __float_as_uint(fminf(s1, s2));
+    const int be = (int)(b >> 23);   // s >= 0: the sign bit is clear
+    if (be == 0) return 13u;
+    if (be == 255) return 0u;
+    const int E = be - 127;
+    const int L = (b & 0x7FFFFFu) ? -((E + 2) >> 1) : -((E + 1) >> 1);
+    return (uint32_t)min(13, max(0, L + offset));
+}
+
 __device__ __forceinline__ uint64_t d_key(uint32_t mat, uint32_t node, uint32_t level,
                                           uint32_t iu, uint32_t iv) {
     return ((uint64_t)mat << 48) | ((uint64_t)node << 32) | ((uint64_t)level << 26) |

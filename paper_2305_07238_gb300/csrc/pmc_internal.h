@@ -139,6 +139,9 @@ struct BatchArgs {
     const float* px; const float* py; const float* pz;
     const float* nx; const float* ny; const float* nz;
     uint32_t n;
+    // ray-cone gradients (caller-owned, optional): each point's own mip level (Eq. 1)
+    const float* g1u; const float* g1v; const float* g2u; const float* g2v;
+    int32_t level_offset;
     // outputs
     float* out_rgb; uint16_t* out_hits;
     // materials
@@ -152,6 +155,7 @@ struct BatchArgs {
     uint32_t* cursor;
     float* su; float* sv; float* spx; float* spy; float* spz;
     float* snx; float* sny; float* snz; uint32_t* sidx;
+    uint32_t* slev;            // grouped per-point mip levels (with ray-cone gradients)
     // cache: cell c = N_e hash2 words then N_e packed (r, g, b) values (16 * N_e bytes)
     uint4* table; unsigned long long* claims;
     int table_empty;           // nothing inserted yet: every probe misses at slot 0
@@ -200,6 +204,8 @@ cudaError_t launch_batch(const BatchArgs& a, cudaStream_t s, int num_sms, cudaEv
                          uint64_t* launches);
 cudaError_t launch_reset(uint4* table, size_t slots, unsigned long long* claims, size_t cells,
                          Control* ctl, unsigned long long* stats, cudaStream_t s, bool claim_words);
+cudaError_t launch_levels(const float* g1u, const float* g1v, const float* g2u, const float* g2v, uint64_t n,
+                          int32_t offset, uint32_t* level, cudaStream_t s);
 cudaError_t launch_keys(const uint32_t* mat, const uint32_t* node, const float* u,
                         const float* v, uint64_t n, uint32_t level, uint64_t n_cells,
                         uint64_t* key, uint64_t* cell, uint32_t* h2, cudaStream_t s);

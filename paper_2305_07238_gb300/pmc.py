@@ -11,7 +11,7 @@ import os
 
 import numpy as np
 
-from .workload import NODE_DTYPE, POINT_FIELDS
+from .workload import CONE_FIELDS, NODE_DTYPE, POINT_FIELDS
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "_build", "libpmc.so")
@@ -30,7 +30,7 @@ TUNE_MAX = 16
 EXPORTED = (
     "pmc_create_cache", "pmc_eval_batch", "pmc_eval_batch_host", "pmc_sync", "pmc_stats",
     "pmc_table_dump", "pmc_last_hit_masks", "pmc_reset", "pmc_destroy_cache",
-    "pmc_material_info", "pmc_analyze_material", "pmc_compute_keys", "pmc_set_timing",
+    "pmc_material_info", "pmc_analyze_material", "pmc_compute_keys", "pmc_compute_levels", "pmc_set_timing",
     "pmc_read_timing", "pmc_eval_batch_noalloc", "pmc_train_surrogates", "pmc_set_surrogate",
     "pmc_get_surrogate", "pmc_use_surrogates", "pmc_mlp_forward", "pmc_mlp_gradient", "pmc_mlp_train",
     "pmc_get_schedule", "pmc_set_schedule", "pmc_graph_create", "pmc_graph_launch", "pmc_graph_destroy",
@@ -57,7 +57,7 @@ class _Material(C.Structure):
 class _Desc(C.Structure):
     _fields_ = [("n_cells", C.c_uint64), ("n_entries", C.c_uint32), ("uv_level", C.c_uint32),
                 ("flags", C.c_uint32), ("min_root_nodes", C.c_uint32), ("device", C.c_int),
-                ("probe_capacity", C.c_uint64)]
+                ("probe_capacity", C.c_uint64), ("level_offset", C.c_int32)]
 
 
 class _Schedule(C.Structure):
@@ -70,7 +70,8 @@ class _TuneResult(C.Structure):
 
 
 class _Points(C.Structure):
-    _fields_ = [(k, C.c_void_p) for k in POINT_FIELDS] + [("n", C.c_uint64)]
+    _fields_ = [(k, C.c_void_p) for k in POINT_FIELDS] + [("n", C.c_uint64)] + \
+        [(k, C.c_void_p) for k in CONE_FIELDS]
 
 
 STAT_FIELDS = ("lookups", "hits", "misses", "candidates", "inserted", "dropped_dup", "dropped_full",
@@ -126,6 +127,8 @@ def load():
     L.pmc_analyze_material.restype = st
     L.pmc_compute_keys.argtypes = [vp, vp, vp, vp, u64, u32, u64, vp, vp, vp, vp]
     L.pmc_compute_keys.restype = st
+    L.pmc_compute_levels.argtypes = [vp, vp, vp, vp, u64, C.c_int32, vp, vp]
+    L.pmc_compute_levels.restype = st
     L.pmc_set_timing.argtypes = [vp, C.c_int]
     L.pmc_set_timing.restype = st
     L.pmc_read_timing.argtypes = [vp, vp, vp, vp]
@@ -189,11 +192,23 @@ def _dptr(t):
     return None if t is None else C.c_void_p(t.data_ptr())
 
 
+def _has_cones(pts) -> bool:
+    return all(pts.get(k) is not None for k in CONE_FIELDS)
+
+
+def _points(pts, n, ptr):
+    """The pmc_points struct of a point dict; ptr maps an array to its address.  The
+    gradients present are passed as they are (the library rejects a partial set)."""
+    cones = [ptr(pts[k]) if pts.get(k) is not None else None for k in CONE_FIELDS]
+    return _Points(*[ptr(pts[k]) for k in POINT_FIELDS], n, *cones)
+
+
 def points_to_device(pts: dict, device="cuda"):
-    """Copies a host point batch (numpy SoA) into torch device tensors."""
+    """Copies a host point batch (numpy SoA, with or without the ray-cone gradients)
+    into torch device tensors."""
     import torch
     out = {}
-    for k in POINT_FIELDS:
+    for k in POINT_FIELDS + (CONE_FIELDS if _has_cones(pts) else ()):
         a = np.ascontiguousarray(pts[k])
         t = torch.from_numpy(a.view(np.int32) if k == "mat" else a)
         out[k] = t.to(device)
@@ -204,14 +219,14 @@ class Cache:
     """A cache object of libpmc: compiled materials + a table of n_cells x n_entries slots."""
 
     def __init__(self, materials, n_cells, n_entries, uv_level=10, flags=0, min_root_nodes=2, device=0,
-                 probe_capacity=0):
+                 probe_capacity=0, level_offset=0):
         L = load()
         self._mats = [np.ascontiguousarray(m, dtype=NODE_DTYPE) for m in materials]
         arr = (_Material * len(self._mats))()
         for i, m in enumerate(self._mats):
             arr[i].n_nodes = len(m)
             arr[i].nodes = m.ctypes.data
-        desc = _Desc(n_cells, n_entries, uv_level, flags, min_root_nodes, device, probe_capacity)
+        desc = _Desc(n_cells, n_entries, uv_level, flags, min_root_nodes, device, probe_capacity, level_offset)
         h = C.c_void_p()
         _check(L.pmc_create_cache(C.byref(desc), arr, len(self._mats), C.byref(h)), "pmc_create_cache")
         self._h = h
@@ -236,10 +251,11 @@ class Cache:
 
     # ---- the pass --------------------------------------------------------------------
     def eval_batch(self, pts, out_rgb, out_hits=None, stream=None):
-        """pts: dict of device tensors (float32; mat int32/uint32); out_rgb: float32 (3, n)
-        device tensor; out_hits: int16/uint16 (n,) device tensor or None."""
+        """pts: dict of device tensors (float32; mat int32/uint32; optionally the ray-cone
+        gradients g1u, g1v, g2u, g2v); out_rgb: float32 (3, n) device tensor; out_hits:
+        int16/uint16 (n,) device tensor or None."""
         n = int(pts["u"].numel())
-        p = _Points(*[_dptr(pts[k]) for k in POINT_FIELDS], n)
+        p = _points(pts, n, _dptr)
         _check(load().pmc_eval_batch(self._h, C.byref(p), _dptr(out_rgb), _dptr(out_hits),
                                      _stream_handle(stream)), "pmc_eval_batch")
 
@@ -247,16 +263,16 @@ class Cache:
         """Same pass as eval_batch with the library's fixed scratch array instead of device
         allocations (for callers that must not allocate; see include/pmc.h for the limits)."""
         n = int(pts["u"].numel())
-        p = _Points(*[_dptr(pts[k]) for k in POINT_FIELDS], n)
+        p = _points(pts, n, _dptr)
         _check(load().pmc_eval_batch_noalloc(self._h, C.byref(p), _dptr(out_rgb), _dptr(out_hits),
                                              _stream_handle(stream)), "pmc_eval_batch_noalloc")
 
     def eval_batch_host(self, pts: dict, out_rgb: np.ndarray, out_hits: np.ndarray | None = None,
                         stream=None):
         """Host buffers in and out; returns once the results are in out_rgb/out_hits."""
-        arrs = [np.ascontiguousarray(pts[k]) for k in POINT_FIELDS]
-        n = len(arrs[0])
-        p = _Points(*[a.ctypes.data for a in arrs], n)
+        keep = {k: np.ascontiguousarray(pts[k]) for k in POINT_FIELDS + (CONE_FIELDS if _has_cones(pts) else ())}
+        n = len(keep["u"])
+        p = _points(keep, n, lambda a: a.ctypes.data)
         _check(load().pmc_eval_batch_host(self._h, C.byref(p), out_rgb.ctypes.data,
                                           None if out_hits is None else out_hits.ctypes.data,
                                           _stream_handle(stream)), "pmc_eval_batch_host")
@@ -282,7 +298,7 @@ class Cache:
     def autotune(self, pts, reps=3) -> dict:
         """Times the candidate schedules on one device batch and keeps the fastest."""
         n = int(pts["u"].numel())
-        p = _Points(*[_dptr(pts[k]) for k in POINT_FIELDS], n)
+        p = _points(pts, n, _dptr)
         r = _TuneResult()
         _check(load().pmc_autotune(self._h, C.byref(p), reps, C.byref(r)), "pmc_autotune")
         tried = [{"flags": int(r.tried[k].flags), "lookup_rb": int(r.tried[k].lookup_rb), "ms": float(r.ms[k])}
@@ -358,6 +374,17 @@ class Cache:
         return {"roots": roots[: nr.value].copy(), "n_instr": ni.value, "n_slots": ns.value}
 
 
+def compute_levels(g1u, g1v, g2u, g2v, offset=0, stream=None):
+    """Mip level of Eq. 1 for device tensors of ray-cone gradients (float32): uint32 levels
+    as int32 tensor."""
+    import torch
+    n = int(g1u.numel())
+    level = torch.empty(n, dtype=torch.int32, device=g1u.device)
+    _check(load().pmc_compute_levels(_dptr(g1u), _dptr(g1v), _dptr(g2u), _dptr(g2v), n, offset, _dptr(level),
+                                     _stream_handle(stream)), "pmc_compute_levels")
+    return level
+
+
 class Graph:
     """A CUDA graph of consecutive passes of one cache (pmc_graph_create).  The tensors
     are bound by address and kept alive here."""
@@ -368,7 +395,7 @@ class Graph:
         self._keep = (passes, out_rgb, out_hits, cache)
         pts = (_Points * max(k, 1))()
         for i, pp in enumerate(passes):
-            pts[i] = _Points(*[_dptr(pp[f]) for f in POINT_FIELDS], int(pp["u"].numel()))
+            pts[i] = _points(pp, int(pp["u"].numel()), _dptr)
         rgb = (C.c_void_p * max(k, 1))(*[t.data_ptr() for t in out_rgb])
         hits = None
         if out_hits is not None:
