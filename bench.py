@@ -309,6 +309,10 @@ def ours(args, rank, world, local_rank, dist):
         line["surrogate"] = surrogate_leg(torch, P, dev, local_rank, seed=rank)
     if "f128" in legs:
         line["frame128"] = frame128_leg(torch, P, dev, local_rank, seed=rank)
+    if "alg1" in legs:
+        line["alg1"] = alg1_leg(torch, P, mats, dev_passes, outs, hits, local_rank)
+        if u_value == u_value:
+            line["alg1"]["speedup_cached_over_uncached"] = round(line["alg1"]["cached"] / u_value, 3)
     if "cones" in legs:
         line["ray_cones"] = cones_leg(torch, P, dev, local_rank, seed=rank)
         if line["ray_cones"] and u_value == u_value:
@@ -404,6 +408,39 @@ def frame128_leg(torch, P, dev, local_rank, seed=0):
     del passes
     torch.cuda.empty_cache()
     return res
+
+
+def alg1_leg(torch, P, mats, dev_passes, outs, hits, local_rank):
+    """The paper's concurrent update (Sec. 3.3, Alg. 1; PMC_ALG1) on the benchmark frame:
+    8-byte slots {hash2, RGB9E5 value}, lookups and one-CAS inserts inside the evaluator,
+    entries visible within the pass.  Cached points/s (whole frame as one CUDA graph, the
+    schedule autotuned between grouped and unsorted), hit rate and counters of a frame."""
+    n = WIDTH * HEIGHT
+    c = P.Cache(mats, N_CELLS, N_ENTRIES, uv_level=LEVEL, flags=P.PMC_ALG1, device=local_rank)
+    for p in range(2):
+        c.eval_batch(dev_passes[p], outs, hits)
+    tune = c.autotune(dev_passes[2], reps=2)
+    c.reset()
+    for p in range(SPP):
+        c.eval_batch(dev_passes[p], outs, hits)
+    st = c.stats()
+    g = c.graph(dev_passes, [outs] * SPP, [hits] * SPP, reset=True)
+    g.launch()
+    torch.cuda.synchronize()
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t0.record()
+    for _ in range(3):
+        g.launch()
+    t1.record()
+    torch.cuda.synchronize()
+    g.close()
+    c.close()
+    return {"config": f"frame 1920x1080x16spp, table {N_CELLS}x{N_ENTRIES} slots of 8 B (128 MB), "
+                      "RGB9E5 values, one 64-bit CAS per insert", "unit": UNIT,
+            "cached": round(3 * n * SPP / (t0.elapsed_time(t1) / 1e3), 1),
+            "schedule": tune["schedule"],
+            "hit_rate": round(st["hits"] / max(1, st["lookups"]), 4),
+            "table": {k: st[k] for k in ("inserted", "dropped_dup", "dropped_full", "dropped_race")}}
 
 
 def cones_leg(torch, P, dev, local_rank, seed=0):
@@ -766,8 +803,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--legs", default="cached,uncached,e2e,surr,f128,cones,cpu",
-                    help="comma list of cached, uncached, e2e, surr, f128, cones, sweep, cpu (sweep is not in the "
+    ap.add_argument("--legs", default="cached,uncached,e2e,surr,f128,alg1,cones,cpu",
+                    help="comma list of cached, uncached, e2e, surr, f128, alg1, cones, sweep, cpu (sweep is not in the "
                          "default: about a minute more; profiling runs take 'cached')")
     ap.add_argument("--profile", action="store_true",
                     help="eager frames only, for ncu launch lists (prints launches per frame)")

@@ -131,6 +131,19 @@ typedef struct {
 #define PMC_PROBE_INLINE 0x40u    /* grouped by material, the evaluator probes the
                                      table itself when it reaches a cacheable node: no
                                      lookup kernel and no probe records (same results) */
+#define PMC_ALG1 0x80u            /* the paper's concurrent update (Sec. 3.3, Alg. 1)
+                                     instead of the deterministic two-phase one: 8-byte
+                                     slots {hash2, value encoded in 32 bits (shared-
+                                     exponent RGB9E5)}; the evaluator looks a cacheable
+                                     node up when it reaches it and, on a miss, inserts
+                                     the value it evaluated at once with one 64-bit
+                                     compare-and-swap into the first slot holding its
+                                     hash2 or 0 (a lost race drops the value).  Entries
+                                     inserted earlier in the same pass are visible, so
+                                     hits, outputs and the table depend on thread timing;
+                                     a hit returns the decoded value.  Only the grouped and
+                                     unsorted schedules apply; pmc_last_hit_masks is not
+                                     available */
 
 typedef struct {
     uint64_t n_cells;        /* N_c >= 1, < 2^32                                  */
@@ -193,11 +206,13 @@ typedef struct {
     uint64_t surrogate_evals; /* cacheable-node values produced by learned surrogates    */
     uint64_t flops_missed;    /* part of flops spent on missed cacheable nodes evaluated
                                  in batches (the batched-miss kernel)                  */
+    uint64_t dropped_race;    /* PMC_ALG1: the compare-and-swap found its slot taken by
+                                 another key (always 0 otherwise)                      */
 } pmc_stats_t;
 
 /* Compiles the networks (cacheable-node analysis, constant folding, serialisation;
  * Sec. 2 and 3), uploads them to `desc->device` and allocates a zeroed table of
- * n_cells * n_entries 16-byte slots.  Returns PMC_ERR_INVALID_ARG for a malformed
+ * n_cells * n_entries 16-byte slots (8-byte slots with PMC_ALG1).  Returns PMC_ERR_INVALID_ARG for a malformed
  * network or description, PMC_ERR_OOM if the table does not fit. */
 pmc_status pmc_create_cache(const pmc_cache_desc* desc, const pmc_material* mats,
                             uint32_t n_mats, pmc_cache** out);
@@ -225,8 +240,8 @@ pmc_status pmc_sync(pmc_cache* cache);
 pmc_status pmc_stats(pmc_cache* cache, pmc_stats_t* out);
 
 /* Synchronises and copies the table to `host_dst`: n_cells * n_entries slots of
- * 16 bytes {uint32 hash2 (0 = empty); float r, g, b}.  `bytes` must be at least
- * that size. */
+ * 16 bytes {uint32 hash2 (0 = empty); float r, g, b} (with PMC_ALG1 the values are the
+ * decoded RGB9E5 codes).  `bytes` must be at least that size. */
 pmc_status pmc_table_dump(pmc_cache* cache, void* host_dst, size_t bytes);
 
 /* Synchronises and copies, for the last batch, one 64-bit mask per point (host

@@ -82,6 +82,12 @@ def lib():
         L.orc_level.argtypes = [C.c_float] * 4 + [C.c_int32]
         L.orc_cache_set_level_offset.restype = None
         L.orc_cache_set_level_offset.argtypes = [vp, C.c_int32]
+        L.orc_cache_set_alg1.restype = None
+        L.orc_cache_set_alg1.argtypes = [vp, C.c_int]
+        L.orc_rgb9e5_encode.restype = u32
+        L.orc_rgb9e5_encode.argtypes = [C.c_float] * 3
+        L.orc_rgb9e5_decode.restype = None
+        L.orc_rgb9e5_decode.argtypes = [u32, vp]
         L.orc_cache_table.restype = None
         L.orc_cache_table.argtypes = [vp, vp, vp]
         L.orc_cache_stats.restype = None
@@ -115,6 +121,13 @@ def voronoi_f1(x, y, seed): return lib().orc_voronoi_f1(x, y, seed)
 def texel(u, level): return lib().orc_texel(u, level)
 def key(mat, node, level, u, v): return lib().orc_key(mat, node, level, u, v)
 def level(g1u, g1v, g2u, g2v, offset=0): return lib().orc_level(g1u, g1v, g2u, g2v, offset)
+def rgb9e5_encode(r, g, b): return lib().orc_rgb9e5_encode(r, g, b)
+
+
+def rgb9e5_decode(code):
+    out = np.zeros(3, dtype=np.float32)
+    lib().orc_rgb9e5_decode(code, _ptr(out))
+    return out
 def hash1(k): return lib().orc_hash1(k)
 def hash2(k): return lib().orc_hash2(k)
 
@@ -175,7 +188,7 @@ class Cache:
     """Sequential emulation of the progressive cache over a set of materials."""
 
     def __init__(self, materials, n_cells, n_entries, level=10, min_root_nodes=2,
-                 cache_off=False, hash_hook=None, level_offset=0):
+                 cache_off=False, hash_hook=None, level_offset=0, alg1=False):
         self._mats = [_nodes(m) for m in materials]
         self.n_cells, self.n_entries, self.level = n_cells, n_entries, level
         self.off = bool(cache_off) or n_cells == 0 or n_entries == 0
@@ -187,6 +200,7 @@ class Cache:
         if lib().orc_cache_set_materials(self._h, len(self._mats), ptrs, _ptr(counts)) != 0:
             raise ValueError("malformed network")
         lib().orc_cache_set_level_offset(self._h, int(level_offset))
+        lib().orc_cache_set_alg1(self._h, int(alg1))
         self._hook = None
         if hash_hook is not None:
             def _cb(k, nc, cell, h2):

@@ -260,6 +260,40 @@ int32_t orc_level(float g1u, float g1v, float g2u, float g2v, int32_t offset) {
     return (int32_t)lam;
 }
 
+/* The 32-bit encoding of a cached value (Sec. 3.3, Alg. 1 "Encode"): the paper packs the
+ * second hash and the encoded value into one 64-bit word for a single compare-and-swap
+ * but does not name the format.  Reading: the shared-exponent format of OpenGL's
+ * EXT_texture_shared_exponent (RGB9E5): three 9-bit mantissas and one 5-bit exponent
+ * with bias 15, bits r 0-8, g 9-17, b 18-26, exponent 27-31; components clamped to
+ * [0, 511/512 * 2^16] (NaN to 0), each rounded to nearest with ties up at the exponent of
+ * the largest.  Written from the format's definition, in FP64 on the FP32 value. */
+uint32_t orc_rgb9e5_encode(float r, float g, float b) {
+    const double maxv = 511.0 / 512.0 * 65536.0;
+    double c[3] = {r, g, b};
+    double mx = 0.0;
+    for (int k = 0; k < 3; ++k) {
+        if (!(c[k] > 0.0)) c[k] = 0.0;   /* negative and NaN */
+        if (c[k] > maxv) c[k] = maxv;
+        if (c[k] > mx) mx = c[k];
+    }
+    int fl = -16;                       /* max(-B - 1, floor(log2(max))) */
+    if (mx > 0.0) {
+        int e;
+        frexp(mx, &e);                  /* mx = m 2^e, m in [0.5, 1): floor(log2 mx) = e - 1 */
+        if (e - 1 > fl) fl = e - 1;
+    }
+    int ex = fl + 16;                   /* + 1 + B */
+    if (floor(ldexp(mx, 24 - ex) + 0.5) == 512.0) ex += 1;
+    uint32_t code = (uint32_t)ex << 27;
+    for (int k = 0; k < 3; ++k) code |= (uint32_t)floor(ldexp(c[k], 24 - ex) + 0.5) << (9 * k);
+    return code;
+}
+
+void orc_rgb9e5_decode(uint32_t code, float out[3]) {
+    const int ex = (int)(code >> 27);
+    for (int k = 0; k < 3; ++k) out[k] = (float)ldexp((double)((code >> (9 * k)) & 511u), ex - 24);
+}
+
 /* Descriptor (Sec. 3.1): material ID, node ID (index in the network as given),
  * mip level lambda, texel indices, packed as
  * mat<<48 | node<<32 | level<<26 | iu<<13 | iv. */
@@ -440,6 +474,7 @@ struct orc_cache {
     uint32_t n_entries;
     uint32_t level;        /* every point's level when no gradients are given */
     int32_t level_offset;  /* added to the ray-cone level (Sec. 4) */
+    int alg1;              /* the paper's concurrent update, serialised point by point */
     uint32_t min_root_nodes;
     int off;
     uint32_t* h2;  /* n_cells * n_entries, 0 = empty */
@@ -516,6 +551,8 @@ int orc_cache_set_materials(orc_cache* c, uint32_t n_mats, const orc_node* const
 void orc_cache_set_hash_override(orc_cache* c, orc_hash_override_fn fn) { c->hook = fn; }
 
 void orc_cache_set_level_offset(orc_cache* c, int32_t offset) { c->level_offset = offset; }
+
+void orc_cache_set_alg1(orc_cache* c, int on) { c->alg1 = on != 0; }
 
 void orc_cache_reset(orc_cache* c) {
     size_t slots = c->off ? 0 : (size_t)c->n_cells * c->n_entries;
@@ -622,6 +659,30 @@ typedef struct {
     float rgb[3];
 } orc_candidate;
 
+/* Inserts candidates one at a time in the given order (Alg. 1 serialised: the
+ * compare-and-swap on an empty entry always succeeds; the first value is kept).  With the
+ * paper's concurrent update the stored value is the 32-bit encoding of the value, and a
+ * hit returns its decoding. */
+static void insert_candidates(orc_cache* c, const orc_candidate* cand, size_t n_cand) {
+    for (size_t q = 0; q < n_cand; ++q) {
+        uint64_t slot;
+        int r = scan_cell(c, cand[q].cell, cand[q].h2, &slot);
+        if (r == 1) {
+            c->stats[5]++;
+        } else if (r == 0) {
+            c->h2[slot] = cand[q].h2;
+            if (c->alg1)
+                orc_rgb9e5_decode(orc_rgb9e5_encode(cand[q].rgb[0], cand[q].rgb[1], cand[q].rgb[2]),
+                                  &c->rgb[3 * slot]);
+            else
+                for (int k = 0; k < 3; ++k) c->rgb[3 * slot + k] = cand[q].rgb[k];
+            c->stats[4]++;
+        } else {
+            c->stats[6]++;
+        }
+    }
+}
+
 int orc_run_batch(orc_cache* c, uint64_t n, const float* u, const float* v,
                   const uint32_t* mat, const float* px, const float* py, const float* pz,
                   const float* nx, const float* ny, const float* nz, double* rgb,
@@ -643,7 +704,8 @@ int orc_run_batch(orc_cache* c, uint64_t n, const float* u, const float* v,
     uint64_t probe = 0;
 
     /* Phase L and evaluation: every point sees the table as it was when the
-     * batch started. */
+     * batch started (with the paper's concurrent update, as the earlier points of the
+     * batch left it). */
     for (uint64_t i = 0; i < n; ++i) {
         if (mat[i] >= c->n_mats) {
             status = ORC_ERR_BADMAT;
@@ -733,25 +795,20 @@ int orc_run_batch(orc_cache* c, uint64_t n, const float* u, const float* v,
         for (int k = 0; k < 3; ++k) rgb[(size_t)k * n + i] = val[3 * (M->n - 1) + k];
         if (hits) hits[i] = (uint16_t)n_hit;
         if (evaluated) evaluated[i] = n_eval;
+        if (c->alg1) {
+            /* the paper's concurrent update, serialised one shading point at a time:
+             * the point's values are in the table before the next point looks up */
+            c->stats[3] += n_cand;
+            insert_candidates(c, cand, n_cand);
+            n_cand = 0;
+        }
     }
 
     /* Phase I: candidates were produced in ascending (point index, node ID)
      * order; insert them one at a time in that order (Alg. 1 serialised: the
      * CAS on an empty entry always succeeds; the first value is kept). */
     c->stats[3] += n_cand;
-    for (size_t q = 0; q < n_cand; ++q) {
-        uint64_t slot;
-        int r = scan_cell(c, cand[q].cell, cand[q].h2, &slot);
-        if (r == 1) {
-            c->stats[5]++;
-        } else if (r == 0) {
-            c->h2[slot] = cand[q].h2;
-            for (int k = 0; k < 3; ++k) c->rgb[3 * slot + k] = cand[q].rgb[k];
-            c->stats[4]++;
-        } else {
-            c->stats[6]++;
-        }
-    }
+    insert_candidates(c, cand, n_cand);
     c->stats[8]++;
     free(val);
     free(hit);

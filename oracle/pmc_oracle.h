@@ -101,6 +101,9 @@ uint32_t orc_texel(float u, uint32_t level);
 /* Eq. 1: floor(-log2(min(|g1|, |g2|))) + offset, clamped to [0, 13] (squared norms in
  * FP32; a zero footprint gives 13, an infinite or NaN one 0). */
 int32_t orc_level(float g1u, float g1v, float g2u, float g2v, int32_t offset);
+/* The 32-bit encoding of a cached value (Alg. 1 "Encode"): shared-exponent RGB9E5. */
+uint32_t orc_rgb9e5_encode(float r, float g, float b);
+void orc_rgb9e5_decode(uint32_t code, float out[3]);
 uint64_t orc_key(uint32_t mat, uint32_t node, uint32_t level, float u, float v);
 uint64_t orc_hash1(uint64_t key);
 uint32_t orc_hash2(uint64_t key);
@@ -134,6 +137,10 @@ int orc_cache_set_materials(orc_cache* c, uint32_t n_mats, const orc_node* const
 void orc_cache_set_hash_override(orc_cache* c, orc_hash_override_fn fn);
 /* Offset added to the ray-cone level of every point (default 0). */
 void orc_cache_set_level_offset(orc_cache* c, int32_t offset);
+/* on != 0: the paper's concurrent update (Alg. 1) serialised point by point: each point
+ * looks up the table as the earlier points of its batch left it and inserts its evaluated
+ * cacheable nodes at once, with values stored as their 32-bit encoding (RGB9E5). */
+void orc_cache_set_alg1(orc_cache* c, int on);
 void orc_cache_reset(orc_cache* c);
 uint32_t orc_cache_n_roots(const orc_cache* c, uint32_t mat);
 /* Root node IDs of a material in ascending order (n_roots entries). */

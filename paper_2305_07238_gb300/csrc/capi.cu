@@ -66,6 +66,16 @@ void free_scratch(pmc_cache* c) {
 
 bool surrogates_active(const pmc_cache* c) { return c->use_surrogates && c->any_surr_on; }
 
+bool alg1_table(const pmc_cache* c) { return c->use_cache && (c->desc.flags & PMC_ALG1) != 0; }
+
+// The table in 16-byte units: 16-byte slots, or 8-byte slots with the paper's concurrent
+// update.
+uint64_t table_units(const pmc_cache* c) {
+    if (!c->use_cache) return 0;
+    const uint64_t slots = c->desc.n_cells * c->desc.n_entries;
+    return alg1_table(c) ? (slots + 1) / 2 : slots;
+}
+
 pmc_status ensure_scratch(pmc_cache* c, uint64_t n) {
     uint64_t need_probes = (c->use_cache || surrogates_active(c)) ? n * (uint64_t)c->max_roots : 0;
     if (c->desc.probe_capacity) need_probes = std::min<uint64_t>(need_probes, c->desc.probe_capacity);
@@ -276,7 +286,7 @@ pmc_status pmc_create_cache(const pmc_cache_desc* desc, const pmc_material* mats
         (s = dalloc(&c->d_prog, prog.size())) != PMC_OK ||
         (s = dalloc(&c->d_params, params.size())) != PMC_OK ||
         (s = dalloc(&c->d_roots, c->roots.size())) != PMC_OK ||
-        (s = dalloc(&c->d_table, slots ? slots + 16 : 0)) != PMC_OK ||
+        (s = dalloc(&c->d_table, slots ? table_units(c) + 16 : 0)) != PMC_OK ||
         (s = dalloc(&c->d_claims, cells)) != PMC_OK ||
         (s = dalloc(&c->d_ctl, 1)) != PMC_OK ||
         (s = dalloc(&c->d_stats, ST_COUNT)) != PMC_OK ||
@@ -301,7 +311,7 @@ pmc_status pmc_create_cache(const pmc_cache_desc* desc, const pmc_material* mats
     c->surr_on.assign(n_mats, 0);
     if (e == cudaSuccess) e = cudaMemset(c->d_surr_slot, 0xFF, n_mats * sizeof(int32_t));
     if (e == cudaSuccess) e = cudaMemset(c->d_surr_ord, 0xFF, n_mats * sizeof(int32_t));
-    if (e == cudaSuccess) e = launch_reset(c->d_table, slots, c->d_claims, cells, c->d_ctl, c->d_stats, 0,
+    if (e == cudaSuccess) e = launch_reset(c->d_table, table_units(c), c->d_claims, cells, c->d_ctl, c->d_stats, 0,
                                            (desc->flags & PMC_INSERT_ROUNDS) != 0);
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
     if (e != cudaSuccess) {
@@ -368,8 +378,9 @@ pmc_status enqueue_batch(pmc_cache* c, const pmc_points* pts, float* out_rgb, ui
     a.snz = c->d_sorted + 7 * P; a.sidx = c->d_sidx;
     a.slev = reinterpret_cast<uint32_t*>(c->d_sorted + 8 * P);
     a.table = c->d_table; a.claims = c->d_claims;
-    a.table_empty = c->table_empty ? 1 : 0;
-    a.keys_inline = (c->use_cache && c->table_empty) ? 1 : 0;
+    a.alg1 = alg1_table(c) ? 1 : 0;
+    a.table_empty = (c->table_empty && !a.alg1) ? 1 : 0;   // alg1 fills the table during the pass
+    a.keys_inline = (c->use_cache && c->table_empty && !a.alg1) ? 1 : 0;
     a.n_cells = c->use_cache ? c->desc.n_cells : 1; a.n_entries = c->use_cache ? ne : 1;
     a.level = c->desc.uv_level;
     const uint64_t nc = a.n_cells;
@@ -409,7 +420,7 @@ pmc_status enqueue_batch(pmc_cache* c, const pmc_points* pts, float* out_rgb, ui
     if (e != cudaSuccess) return cuda_fail(c, e);
     if (c->use_cache) c->epoch_host += ne + 1;
     c->last_all_miss = a.keys_inline != 0;
-    c->last_unsorted = a.unsorted != 0 || (a.probe_inline != 0 && a.use_cache);
+    c->last_unsorted = a.unsorted != 0 || (a.probe_inline != 0 && a.use_cache) || a.alg1 != 0;
     if (n > 0) c->table_empty = false;
     c->last_stream = s;
     c->last_n = n;
@@ -503,6 +514,7 @@ pmc_status pmc_stats(pmc_cache* c, pmc_stats_t* out) {
     out->inserted = v[ST_INSERTED];
     out->dropped_dup = v[ST_DUP];
     out->dropped_full = v[ST_FULL];
+    out->dropped_race = v[ST_RACE];
     out->nodes_evaluated = v[ST_NODES];
     out->batches = v[ST_BATCHES];
     out->flops = v[ST_FLOPS];
@@ -522,7 +534,22 @@ pmc_status pmc_table_dump(pmc_cache* c, void* host_dst, size_t bytes) {
     pmc_status st = pmc_sync(c);
     if (st == PMC_ERR_CUDA) return st;
     DeviceGuard g(c->desc.device);
-    if (need) {
+    if (need && alg1_table(c)) {
+        // 8-byte slots {hash2, RGB9E5 code}: the dump decodes the code (value = mantissa *
+        // 2^(exponent - 24), exactly as the kernels decode it)
+        std::vector<uint32_t> raw(slots * 2u);
+        cudaError_t e = cudaMemcpy(raw.data(), c->d_table, slots * 8u, cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) return cuda_fail(c, e);
+        uint32_t* dst = static_cast<uint32_t*>(host_dst);
+        for (size_t k = 0; k < slots; ++k) {
+            const uint32_t h = raw[2 * k], code = raw[2 * k + 1];
+            dst[4 * k] = h;
+            for (int q = 0; q < 3; ++q) {
+                const float v = std::ldexp((float)((code >> (9 * q)) & 511u), (int)(code >> 27) - 24);
+                std::memcpy(&dst[4 * k + 1 + q], &v, 4);
+            }
+        }
+    } else if (need) {
         // device cells hold N_e hash2 words followed by N_e packed (r, g, b) values;
         // the dump format is one {hash2, r, g, b} record per slot
         std::vector<uint32_t> raw(slots * 4u);
@@ -587,9 +614,8 @@ pmc_status pmc_reset(pmc_cache* c, void* stream) {
     if (!c) return PMC_ERR_INVALID_ARG;
     if (c->sticky != PMC_OK) return c->sticky;
     DeviceGuard g(c->desc.device);
-    const uint64_t slots = c->use_cache ? c->desc.n_cells * c->desc.n_entries : 0;
     const uint64_t cells = c->use_cache ? c->desc.n_cells : 0;
-    cudaError_t e = launch_reset(c->d_table, slots, c->d_claims, cells, c->d_ctl, c->d_stats,
+    cudaError_t e = launch_reset(c->d_table, table_units(c), c->d_claims, cells, c->d_ctl, c->d_stats,
                                  (cudaStream_t)stream, (c->desc.flags & PMC_INSERT_ROUNDS) != 0);
     if (e != cudaSuccess) return cuda_fail(c, e);
     c->epoch_host = 0;
@@ -995,7 +1021,7 @@ pmc_status pmc_graph_create(pmc_cache* c, const pmc_points* passes, uint32_t n_p
         const uint64_t slots = c->use_cache ? c->desc.n_cells * ne : 0;
         const uint64_t cells = c->use_cache ? c->desc.n_cells : 0;
         if (flags & PMC_GRAPH_RESET) {
-            e = launch_reset(c->d_table, slots, c->d_claims, cells, c->d_ctl, c->d_stats, s, rounds);
+            e = launch_reset(c->d_table, table_units(c), c->d_claims, cells, c->d_ctl, c->d_stats, s, rounds);
             c->table_empty = true;
         } else {
             c->table_empty = false;   // the table's contents at replay time are unknown
@@ -1087,27 +1113,33 @@ pmc_status pmc_autotune(pmc_cache* c, const pmc_points* sample, uint32_t reps, p
     pmc_get_schedule(c, &orig);
     const uint32_t keep = orig.flags & PMC_INSERT_ROUNDS;
     std::vector<pmc_schedule> cand;
-    if (c->max_level < MAX_LEVELS) {
+    if (alg1_table(c)) {
+        // the paper's concurrent update runs inside the evaluator: grouped or unsorted
+        cand.push_back({keep, 4});
+        if (!surrogates_active(c)) cand.push_back({keep | PMC_UNSORTED, 4});
+    } else if (c->max_level < MAX_LEVELS) {
         cand.push_back({keep, 4});
         if (c->use_cache) {
             cand.push_back({keep, 2});
             cand.push_back({keep, 1});
         }
     }
-    if (c->use_cache) cand.push_back({keep | PMC_EVAL_INLINE, 4});
-    if (c->use_cache) cand.push_back({keep | PMC_PROBE_INLINE, 4});
-    if (!surrogates_active(c)) cand.push_back({keep | PMC_EVAL_INLINE | PMC_UNSORTED, 4});
-    if (c->use_cache && c->max_level < MAX_LEVELS) cand.push_back({keep ^ PMC_INSERT_ROUNDS, 4});
+    if (!alg1_table(c)) {
+        if (c->use_cache) cand.push_back({keep | PMC_EVAL_INLINE, 4});
+        if (c->use_cache) cand.push_back({keep | PMC_PROBE_INLINE, 4});
+        if (!surrogates_active(c)) cand.push_back({keep | PMC_EVAL_INLINE | PMC_UNSORTED, 4});
+        if (c->use_cache && c->max_level < MAX_LEVELS) cand.push_back({keep ^ PMC_INSERT_ROUNDS, 4});
+    }
     if (cand.empty()) cand.push_back(orig);
     if (cand.size() > PMC_TUNE_MAX) cand.resize(PMC_TUNE_MAX);
 
-    const uint64_t slots = c->use_cache ? c->desc.n_cells * c->desc.n_entries : 0;
-    const size_t table_bytes = slots ? (size_t)(slots + 16) * sizeof(uint4) : 0;
+    const uint64_t units = table_units(c);
+    const size_t table_bytes = units ? (size_t)(units + 16) * sizeof(uint4) : 0;
     uint4* saved = nullptr;
     float* rgb = nullptr;
     uint16_t* hits = nullptr;
     unsigned long long stats[ST_COUNT];
-    if (table_bytes && (st = dalloc(&saved, slots + 16)) != PMC_OK) return st;
+    if (table_bytes && (st = dalloc(&saved, units + 16)) != PMC_OK) return st;
     if ((st = dalloc(&rgb, 3 * (size_t)std::max<uint64_t>(n, 1))) != PMC_OK) { dfree(&saved); return st; }
     if ((st = dalloc(&hits, (size_t)std::max<uint64_t>(n, 1))) != PMC_OK) { dfree(&saved); dfree(&rgb); return st; }
     cudaStream_t s = nullptr;

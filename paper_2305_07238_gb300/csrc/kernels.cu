@@ -625,6 +625,107 @@ __device__ __forceinline__ int probe_cell(const BatchArgs& a, uint32_t cell, uin
     return -1;
 }
 
+// ---- the paper's concurrent update (Alg. 1, Sec. 3.3): 8-byte slots {hash2 in the low word,
+// the 32-bit encoded value in the high word}; a slot is empty iff it is 0 (hash2 is never 0).
+__device__ __forceinline__ unsigned long long* alg1_cell(const BatchArgs& a, uint32_t cell) {
+    return reinterpret_cast<unsigned long long*>(a.table) + (size_t)cell * a.n_entries;
+}
+
+// Alg. 1's entry loop over a cell: the first slot whose hash is h2 or that is empty, or -1
+// (full); *word receives that slot.  The slots are read from L2 (other warps insert into
+// them during the pass), all loads of a group of 8 in flight together.
+__device__ __forceinline__ int alg1_scan(const BatchArgs& a, uint32_t cell, uint32_t h2, unsigned long long* word) {
+    const unsigned long long* cw = alg1_cell(a, cell);
+    const uint32_t ne = a.n_entries;
+    for (uint32_t q = 0; q < ne; q += 8) {
+        unsigned long long w[8];
+        if ((ne & 1u) == 0 && q + 8 <= ne) {
+            // 16-byte aligned pairs of slots, read as two 64-bit elements: each slot is read
+            // in one access, so a slot being filled by a compare-and-swap is never seen torn
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const ulonglong2 x = __ldcg(reinterpret_cast<const ulonglong2*>(cw + q) + k);
+                w[2 * k] = x.x;
+                w[2 * k + 1] = x.y;
+            }
+        } else {
+#pragma unroll
+            for (int k = 0; k < 8; ++k) w[k] = q + k < ne ? __ldcg(cw + q + k) : 0ull;
+        }
+#pragma unroll
+        for (int k = 0; k < 8; ++k)
+            if (q + k < ne && ((uint32_t)w[k] == h2 || w[k] == 0ull)) {
+                *word = w[k];
+                return (int)(q + k);
+            }
+    }
+    return -1;
+}
+
+// round(c 2^k), ties up, exactly, for an FP32 c >= 0 whose scaled value is at most 512:
+// c = M 2^E with a 24-bit integer M, so the rounding is an integer shift.
+__device__ __forceinline__ uint32_t scaled_round(float c, int k) {
+    const uint32_t b = __float_as_uint(c);
+    const uint32_t be = b >> 23;
+    uint32_t M = b & 0x7FFFFFu;
+    int E = -149;
+    if (be != 0) {
+        M |= 0x800000u;
+        E = (int)be - 150;
+    }
+    const int sh = E + k;
+    if (sh >= 0) return M << sh;   // only c = 0 gets here within the format's range
+    const int r = -sh;
+    if (r > 25) return 0u;         // M < 2^24 <= 2^(r - 1): rounds to 0
+    return (uint32_t)(((unsigned long long)M + (1ull << (r - 1))) >> r);
+}
+
+// The 32-bit encoding of a value (Alg. 1 "Encode"): shared-exponent RGB9E5 (the format of
+// OpenGL's EXT_texture_shared_exponent): components clamped to [0, 511/512 * 2^16] (NaN to
+// 0), exponent max(-16, floor(log2 max)) + 16, raised by one when the largest mantissa
+// rounds to 512; mantissas rounded to nearest, ties up.  Bits: r 0-8, g 9-17, b 18-26,
+// exponent 27-31.
+__device__ __forceinline__ uint32_t rgb9e5_encode(float r, float g, float b) {
+    float c[3] = {r, g, b};
+    float mx = 0.0f;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        c[k] = c[k] > 0.0f ? fminf(c[k], 65408.0f) : 0.0f;
+        mx = fmaxf(mx, c[k]);
+    }
+    const uint32_t be = __float_as_uint(mx) >> 23;
+    const int fl = be != 0 ? max(-16, (int)be - 127) : -16;   // floor(log2 mx), at least -16
+    int ex = fl + 16;
+    if (scaled_round(mx, 24 - ex) == 512u) ex += 1;
+    uint32_t code = (uint32_t)ex << 27;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) code |= scaled_round(c[k], 24 - ex) << (9 * k);
+    return code;
+}
+
+__device__ __forceinline__ void rgb9e5_decode(uint32_t code, float* r, float* g, float* b) {
+    const float sc = __uint_as_float((uint32_t)((int)(code >> 27) - 24 + 127) << 23);   // 2^(e - 24)
+    *r = (float)(code & 511u) * sc;
+    *g = (float)((code >> 9) & 511u) * sc;
+    *b = (float)((code >> 18) & 511u) * sc;
+}
+
+// Alg. 1 for one evaluated cacheable node: find the slot again, then one compare-and-swap
+// of {hash2, encoded value} into it if it was empty; a lost race drops the value.
+__device__ __forceinline__ void alg1_insert(const BatchArgs& a, uint32_t cell, uint32_t h2, float r, float g, float b,
+                                            unsigned long long* n_ins, unsigned long long* n_dup,
+                                            unsigned long long* n_full, unsigned long long* n_race) {
+    unsigned long long cur = 0;
+    const int j = alg1_scan(a, cell, h2, &cur);
+    if (j < 0) { *n_full += 1; return; }
+    if (cur != 0ull) { *n_dup += 1; return; }   // the key is present
+    const unsigned long long word = ((unsigned long long)rgb9e5_encode(r, g, b) << 32) | h2;
+    const unsigned long long old = atomicCAS(alg1_cell(a, cell) + j, 0ull, word);
+    if (old == 0ull) *n_ins += 1;
+    else if ((uint32_t)old == h2) *n_dup += 1;   // the same key, inserted meanwhile
+    else *n_race += 1;                            // another key took the slot
+}
+
 // Unsorted evaluation: the in-shader form of Sec. 3.  A warp takes 32 consecutive
 // shading points in batch order, runs each distinct material among them in turn (the
 // other lanes idle) and probes the table when it reaches a cacheable node: a hit skips
@@ -646,6 +747,7 @@ __global__ void __launch_bounds__(EVAL_WARPS * 32) k_eval_fused(BatchArgs a, uin
     const uint32_t ne = a.n_entries;
     unsigned long long n_nodes = 0, n_flops = 0, n_cand = 0, n_full = 0;
     unsigned long long n_look = 0, n_hit = 0, n_slots = 0, n_bad = 0;
+    unsigned long long n_ins = 0, n_dup = 0, n_race = 0;   // the paper's concurrent update
     uint32_t chunk = blockIdx.x * EVAL_WARPS + warp;
     for (;;) {
         if (GROUPED) {
@@ -722,6 +824,27 @@ __global__ void __launch_bounds__(EVAL_WARPS * 32) k_eval_fused(BatchArgs a, uin
                             V[(slot * 3 + 2) * 32] = rec.z;
                         }
                         need = false;
+                    } else if (a.use_cache && mine && a.alg1) {
+                        // the paper's scheme: the table as other warps are filling it
+                        d_address(d_key(mg, ins.z, lev, iu, iv), a.n_cells, a.cells_pow2_mask, &cand_cell, &cand_h2);
+                        unsigned long long w = 0;
+                        const int first = alg1_scan(a, cand_cell, cand_h2, &w);
+                        n_look++;
+                        n_slots += first >= 0 ? (uint32_t)first + 1u : ne;
+                        if (first >= 0 && w != 0ull) {
+                            const uint32_t slot = ins.y & 0xFFFFu;
+                            float r, g, b;
+                            rgb9e5_decode((uint32_t)(w >> 32), &r, &g, &b);
+                            V[(slot * 3 + 0) * 32] = r;
+                            V[(slot * 3 + 1) * 32] = g;
+                            V[(slot * 3 + 2) * 32] = b;
+                            hits++;
+                            n_hit++;
+                            need = false;
+                        } else {
+                            cand_full = first < 0;
+                            cand_node = ins.z;
+                        }
                     } else if (a.use_cache && mine) {
                         d_address(d_key(mg, ins.z, lev, iu, iv), a.n_cells, a.cells_pow2_mask, &cand_cell, &cand_h2);
                         bool hit = false;
@@ -758,8 +881,16 @@ __global__ void __launch_bounds__(EVAL_WARPS * 32) k_eval_fused(BatchArgs a, uin
                 }
                 if (a.use_cache && ((ins.x >> 8) & FLAG_ROOT)) {
                     const uint32_t out = ins.y & 0xFFFFu;
-                    offer(a, act, i, cand_node, cand_cell, cand_h2, cand_start, cand_full, V[(out * 3) * 32],
-                          V[(out * 3 + 1) * 32], V[(out * 3 + 2) * 32], &n_cand, &n_full);
+                    if (a.alg1) {
+                        n_cand += act ? 1u : 0u;
+                        n_full += (act && cand_full) ? 1u : 0u;   // a full cell stays full
+                        if (act && !cand_full)
+                            alg1_insert(a, cand_cell, cand_h2, V[(out * 3) * 32], V[(out * 3 + 1) * 32],
+                                        V[(out * 3 + 2) * 32], &n_ins, &n_dup, &n_full, &n_race);
+                    } else {
+                        offer(a, act, i, cand_node, cand_cell, cand_h2, cand_start, cand_full, V[(out * 3) * 32],
+                              V[(out * 3 + 1) * 32], V[(out * 3 + 2) * 32], &n_cand, &n_full);
+                    }
                 }
             }
             if (mine) {
@@ -780,6 +911,11 @@ __global__ void __launch_bounds__(EVAL_WARPS * 32) k_eval_fused(BatchArgs a, uin
     warp_add_u64(&a.stats[ST_HITS], n_hit);
     warp_add_u64(&a.stats[ST_MISSES], n_look - n_hit);
     warp_add_u64(&a.stats[ST_SLOTS], n_slots);
+    if (a.alg1) {
+        warp_add_u64(&a.stats[ST_INSERTED], n_ins);
+        warp_add_u64(&a.stats[ST_DUP], n_dup);
+        warp_add_u64(&a.stats[ST_RACE], n_race);
+    }
     if (!GROUPED) {
         warp_add_u64(&a.stats[ST_BAD], n_bad);
         if (__any_sync(FULL_MASK, n_bad != 0) && lane == 0) atomicOr(&a.ctl->err, ERR_BAD_MAT);
@@ -1868,10 +2004,10 @@ cudaError_t launch_keys(const uint32_t* mat, const uint32_t* node, const float* 
     return cudaGetLastError();
 }
 
-cudaError_t launch_reset(uint4* table, size_t slots, unsigned long long* claims, size_t cells,
+cudaError_t launch_reset(uint4* table, size_t units, unsigned long long* claims, size_t cells,
                          Control* ctl, unsigned long long* stats, cudaStream_t s, bool claim_words) {
     cudaError_t e;
-    if (slots && (e = cudaMemsetAsync(table, 0, (slots + 16) * sizeof(uint4), s)) != cudaSuccess) return e;
+    if (units && (e = cudaMemsetAsync(table, 0, (units + 16) * sizeof(uint4), s)) != cudaSuccess) return e;
     // all-ones: the largest claim word of the atomicMin rounds, an empty list per cell
     // for the grouped insert
     (void)claim_words;
@@ -1938,6 +2074,53 @@ cudaError_t launch_batch(const BatchArgs& a, cudaStream_t s, int num_sms, cudaEv
         return e;
     uint32_t* item_ctr = a.counts + a.n_mats;
     const int gs_blocks = num_sms * 4;
+    if (a.alg1 && a.use_cache) {
+        // the paper's concurrent update: lookups and inserts inside the evaluator, no
+        // lookup kernel, no insert phase; grouped by material unless unsorted
+        if (!a.unsorted && a.n > 0) {
+            k_hist<<<gs_blocks, 256, 0, s>>>(a);
+            nl++;
+        }
+        if (!a.unsorted) {
+            k_scan<<<1, 1024, 0, s>>>(a);
+            nl++;
+        }
+        if (!a.unsorted && a.n > 0) {
+            k_scatter<<<gs_blocks, 256, 0, s>>>(a);
+            nl++;
+        }
+        if ((e = mark(1)) != cudaSuccess) return e;
+        if (!a.unsorted && a.n > 0 && a.surr_slot) {
+            if ((e = launch_surrogate(a, num_sms, s)) != cudaSuccess) return e;
+            nl++;
+        }
+        if ((e = mark(2)) != cudaSuccess) return e;
+        if ((e = mark(3)) != cudaSuccess) return e;
+        if (a.n > 0) {
+            const size_t smem = eval_smem_bytes(a.max_slots);
+            if (a.unsorted) {
+                if (smem > 48 * 1024 &&
+                    (e = cudaFuncSetAttribute(k_eval_fused<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                              (int)smem)) != cudaSuccess)
+                    return e;
+                k_eval_fused<false><<<num_sms * 16, EVAL_WARPS * 32, smem, s>>>(a, nullptr);
+            } else {
+                if (smem > 48 * 1024 &&
+                    (e = cudaFuncSetAttribute(k_eval_fused<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                              (int)smem)) != cudaSuccess)
+                    return e;
+                k_eval_fused<true><<<num_sms * 16, EVAL_WARPS * 32, smem, s>>>(a, item_ctr);
+            }
+            nl++;
+        }
+        if ((e = mark(4)) != cudaSuccess) return e;
+        if ((e = mark(5)) != cudaSuccess) return e;
+        k_finish<<<1, 32, 0, s>>>(a);
+        nl++;
+        if ((e = mark(6)) != cudaSuccess) return e;
+        if (launches) *launches += nl;
+        return cudaGetLastError();
+    }
     if (a.unsorted) {
         // one fused launch: probes inline, no grouping and no probe records
         if ((e = mark(1)) != cudaSuccess) return e;

@@ -127,8 +127,9 @@ extern "C" pmc_status pmc_eval_batch_noalloc(pmc_cache* c, const pmc_points* pts
     a.slev = reinterpret_cast<uint32_t*>(sorted + 8 * NA_POINTS);
     a.sidx = reinterpret_cast<uint32_t*>(base + OFF_SIDX);
     a.table = c->d_table; a.claims = c->d_claims;
-    a.table_empty = c->table_empty ? 1 : 0;
-    a.keys_inline = (c->use_cache && c->table_empty) ? 1 : 0;
+    a.alg1 = (c->use_cache && (c->desc.flags & PMC_ALG1)) ? 1 : 0;
+    a.table_empty = (c->table_empty && !a.alg1) ? 1 : 0;
+    a.keys_inline = (c->use_cache && c->table_empty && !a.alg1) ? 1 : 0;
     a.n_cells = c->use_cache ? c->desc.n_cells : 1; a.n_entries = c->use_cache ? ne : 1;
     a.level = c->desc.uv_level;
     const uint64_t nc = a.n_cells;

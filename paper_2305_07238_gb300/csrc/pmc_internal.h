@@ -129,7 +129,7 @@ constexpr uint32_t ERR_CAPACITY = 16;   // the batch needs more probe records th
 // Counter indices in the device stats array.
 enum {
     ST_LOOKUPS = 0, ST_HITS, ST_MISSES, ST_CANDIDATES, ST_INSERTED, ST_DUP, ST_FULL,
-    ST_NODES, ST_BATCHES, ST_FLOPS, ST_SLOTS, ST_POINTS, ST_BAD, ST_SURR, ST_FLOPS_MISSED, ST_COUNT = 16
+    ST_NODES, ST_BATCHES, ST_FLOPS, ST_SLOTS, ST_POINTS, ST_BAD, ST_SURR, ST_FLOPS_MISSED, ST_RACE, ST_COUNT = 16
 };
 
 // Everything a batch's kernels need, by value.
@@ -156,7 +156,8 @@ struct BatchArgs {
     float* su; float* sv; float* spx; float* spy; float* spz;
     float* snx; float* sny; float* snz; uint32_t* sidx;
     uint32_t* slev;            // grouped per-point mip levels (with ray-cone gradients)
-    // cache: cell c = N_e hash2 words then N_e packed (r, g, b) values (16 * N_e bytes)
+    // cache: cell c = N_e hash2 words then N_e packed (r, g, b) values (16 * N_e bytes), or
+    // with alg1 N_e 8-byte slots
     uint4* table; unsigned long long* claims;
     int table_empty;           // nothing inserted yet: every probe misses at slot 0
     int keys_inline;           // empty table: the evaluator forms descriptors itself and
@@ -190,6 +191,8 @@ struct BatchArgs {
     int unsorted;              // 1: no grouping; k_eval_fused probes inline in batch order
     int probe_inline;          // 1: grouped; k_eval_fused probes inline (no lookup kernel)
     uint32_t lookup_rb;        // k_lookup: probes in flight per lane (1, 2 or 4)
+    int alg1;                  // the paper's concurrent update: 8-byte slots {hash2, RGB9E5},
+                               // looked up and inserted inside the evaluator (one 64-bit CAS)
 };
 
 constexpr uint32_t INSERT_BIN_CELLS = 256;
@@ -202,7 +205,7 @@ enum { PH_SORT = 0, PH_LOOKUP, PH_MISSED, PH_EVAL, PH_INSERT, PH_FINISH, PH_COUN
 // events recorded on `s` at the phase boundaries; `*launches` counts kernel launches.
 cudaError_t launch_batch(const BatchArgs& a, cudaStream_t s, int num_sms, cudaEvent_t* ev,
                          uint64_t* launches);
-cudaError_t launch_reset(uint4* table, size_t slots, unsigned long long* claims, size_t cells,
+cudaError_t launch_reset(uint4* table, size_t units, unsigned long long* claims, size_t cells,
                          Control* ctl, unsigned long long* stats, cudaStream_t s, bool claim_words);
 cudaError_t launch_levels(const float* g1u, const float* g1v, const float* g2u, const float* g2v, uint64_t n,
                           int32_t offset, uint32_t* level, cudaStream_t s);

@@ -24,6 +24,7 @@ PMC_EVAL_INLINE = 0x8
 PMC_INSERT_ROUNDS = 0x10
 PMC_UNSORTED = 0x20
 PMC_PROBE_INLINE = 0x40
+PMC_ALG1 = 0x80
 PMC_GRAPH_RESET = 0x1
 TUNE_MAX = 16
 
@@ -76,7 +77,7 @@ class _Points(C.Structure):
 
 STAT_FIELDS = ("lookups", "hits", "misses", "candidates", "inserted", "dropped_dup", "dropped_full",
                "nodes_evaluated", "batches", "flops", "slots_probed", "points", "bad_points",
-               "surrogate_evals", "flops_missed")
+               "surrogate_evals", "flops_missed", "dropped_race")
 MLP_PARAMS = 8515
 
 
