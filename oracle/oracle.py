@@ -16,9 +16,9 @@ from .build import build_oracle
 
 _lib = None
 
-NSTATS = 9
+NSTATS = 10
 STAT_NAMES = ("lookups", "hits", "misses", "candidates", "inserted", "dropped_dup",
-              "dropped_full", "nodes_evaluated", "batches")
+              "dropped_full", "nodes_evaluated", "batches", "replaced")
 
 HASH_HOOK = C.CFUNCTYPE(None, C.c_uint64, C.c_uint64, C.POINTER(C.c_uint64),
                         C.POINTER(C.c_uint32))
@@ -77,13 +77,17 @@ def lib():
         L.orc_cache_roots.restype = None
         L.orc_cache_roots.argtypes = [vp, u32, vp]
         L.orc_run_batch.restype = C.c_int
-        L.orc_run_batch.argtypes = [vp, u64] + [vp] * 9 + [vp] * 7 + [vp] * 4
+        L.orc_run_batch.argtypes = [vp, u64] + [vp] * 9 + [vp] * 7 + [vp] * 4 + [vp]
         L.orc_level.restype = C.c_int32
         L.orc_level.argtypes = [C.c_float] * 4 + [C.c_int32]
         L.orc_cache_set_level_offset.restype = None
         L.orc_cache_set_level_offset.argtypes = [vp, C.c_int32]
         L.orc_cache_set_alg1.restype = None
         L.orc_cache_set_alg1.argtypes = [vp, C.c_int]
+        L.orc_cache_set_replacement.restype = None
+        L.orc_cache_set_replacement.argtypes = [vp, C.c_int]
+        L.orc_cache_classes.restype = None
+        L.orc_cache_classes.argtypes = [vp, vp]
         L.orc_rgb9e5_encode.restype = u32
         L.orc_rgb9e5_encode.argtypes = [C.c_float] * 3
         L.orc_rgb9e5_decode.restype = None
@@ -188,7 +192,7 @@ class Cache:
     """Sequential emulation of the progressive cache over a set of materials."""
 
     def __init__(self, materials, n_cells, n_entries, level=10, min_root_nodes=2,
-                 cache_off=False, hash_hook=None, level_offset=0, alg1=False):
+                 cache_off=False, hash_hook=None, level_offset=0, alg1=False, replacement=False):
         self._mats = [_nodes(m) for m in materials]
         self.n_cells, self.n_entries, self.level = n_cells, n_entries, level
         self.off = bool(cache_off) or n_cells == 0 or n_entries == 0
@@ -201,6 +205,7 @@ class Cache:
             raise ValueError("malformed network")
         lib().orc_cache_set_level_offset(self._h, int(level_offset))
         lib().orc_cache_set_alg1(self._h, int(alg1))
+        lib().orc_cache_set_replacement(self._h, int(replacement))
         self._hook = None
         if hash_hook is not None:
             def _cb(k, nc, cell, h2):
@@ -236,11 +241,13 @@ class Cache:
     def run_batch(self, pts: dict, probes: bool = False):
         """One progressive pass.  Returns a dict with rgb (3, n) float64, hits,
         evaluated, status and (if probes) key/cell/h2/hit per (point, root).  If pts holds
-        the ray-cone gradients (CONE_FIELDS), each point takes its own mip level."""
+        the ray-cone gradients (CONE_FIELDS), each point takes its own mip level; if it holds
+        "vis", that is each point's visibility class for the replacement policy."""
         arrs = [np.ascontiguousarray(pts[k], dtype=np.uint32 if k == "mat" else np.float32)
                 for k in POINT_FIELDS]
         cones = [np.ascontiguousarray(pts[k], dtype=np.float32) for k in CONE_FIELDS] \
             if all(k in pts for k in CONE_FIELDS) else [None] * 4
+        vis = np.ascontiguousarray(pts["vis"], dtype=np.uint8) if "vis" in pts else None
         n = len(arrs[0])
         rgb = np.zeros(3 * n, dtype=np.float64)
         hits = np.zeros(n, dtype=np.uint16)
@@ -257,7 +264,7 @@ class Cache:
             phit = np.zeros(max(total, 1), dtype=np.uint8)
         st = lib().orc_run_batch(self._h, n, *[_ptr(a) for a in arrs], _ptr(rgb), _ptr(hits),
                                  _ptr(ev), _ptr(pk), _ptr(pc), _ptr(ph), _ptr(phit),
-                                 *[_ptr(g) for g in cones])
+                                 *[_ptr(g) for g in cones], _ptr(vis))
         out = {"rgb": rgb.reshape(3, n), "hits": hits, "evaluated": ev, "status": st}
         if probes:
             out.update(key=pk[:total], cell=pc[:total], h2=ph[:total], hit=phit[:total])
@@ -269,6 +276,13 @@ class Cache:
         rgb = np.zeros(max(3 * slots, 1), dtype=np.float32)
         lib().orc_cache_table(self._h, _ptr(h2), _ptr(rgb))
         return h2[:slots], rgb[: 3 * slots].reshape(slots, 3)
+
+    def classes(self):
+        """Visibility class of every slot's entry (meaningful where the slot's h2 != 0)."""
+        slots = 0 if self.off else self.n_cells * self.n_entries
+        cls = np.zeros(max(slots, 1), dtype=np.uint8)
+        lib().orc_cache_classes(self._h, _ptr(cls))
+        return cls[:slots]
 
     def stats(self) -> dict:
         out = np.zeros(NSTATS, dtype=np.uint64)

@@ -475,10 +475,12 @@ struct orc_cache {
     uint32_t level;        /* every point's level when no gradients are given */
     int32_t level_offset;  /* added to the ray-cone level (Sec. 4) */
     int alg1;              /* the paper's concurrent update, serialised point by point */
+    int replace;           /* replacement by visibility class (Sec. 5), else keep-first */
     uint32_t min_root_nodes;
     int off;
     uint32_t* h2;  /* n_cells * n_entries, 0 = empty */
     float* rgb;    /* 3 per slot */
+    uint8_t* cls;  /* visibility class of each slot's entry (replacement policy only) */
     orc_mat* mats;
     uint32_t n_mats;
     orc_hash_override_fn hook;
@@ -497,6 +499,7 @@ orc_cache* orc_cache_new(uint64_t n_cells, uint32_t n_entries, uint32_t level,
     size_t slots = c->off ? 0 : (size_t)n_cells * n_entries;
     c->h2 = (uint32_t*)calloc(slots ? slots : 1, sizeof(uint32_t));
     c->rgb = (float*)calloc(slots ? 3 * slots : 1, sizeof(float));
+    c->cls = (uint8_t*)calloc(slots ? slots : 1, 1);
     return c;
 }
 
@@ -517,6 +520,7 @@ void orc_cache_free(orc_cache* c) {
     free_mats(c);
     free(c->h2);
     free(c->rgb);
+    free(c->cls);
     free(c);
 }
 
@@ -554,11 +558,14 @@ void orc_cache_set_level_offset(orc_cache* c, int32_t offset) { c->level_offset 
 
 void orc_cache_set_alg1(orc_cache* c, int on) { c->alg1 = on != 0; }
 
+void orc_cache_set_replacement(orc_cache* c, int on) { c->replace = on != 0; }
+
 void orc_cache_reset(orc_cache* c) {
     size_t slots = c->off ? 0 : (size_t)c->n_cells * c->n_entries;
     if (slots) {
         memset(c->h2, 0, slots * sizeof(uint32_t));
         memset(c->rgb, 0, 3 * slots * sizeof(float));
+        memset(c->cls, 0, slots);
     }
     memset(c->stats, 0, sizeof(c->stats));
 }
@@ -657,7 +664,26 @@ typedef struct {
     uint64_t cell;
     uint32_t h2;
     float rgb[3];
+    uint8_t vis;   /* visibility class of the inserting point */
 } orc_candidate;
+
+/* Replacement policy (the prioritisation that Sec. 5 proposes as future work): a full
+ * cell gives up the entry of the least important class, provided that class is less
+ * important than the newcomer's (a larger class number = more bounces away from the
+ * camera).  Returns the slot to overwrite, or -1 when every entry is at least as
+ * important as the newcomer.  Among entries of the same class the first one goes. */
+static int64_t replacement_victim(const orc_cache* c, uint64_t cell, uint8_t vis) {
+    int64_t victim = -1;
+    uint8_t worst = vis;
+    for (uint32_t i = 0; i < c->n_entries; ++i) {
+        uint64_t s = cell * c->n_entries + i;
+        if (c->cls[s] > worst) {
+            worst = c->cls[s];
+            victim = (int64_t)s;
+        }
+    }
+    return victim;
+}
 
 /* Inserts candidates one at a time in the given order (Alg. 1 serialised: the
  * compare-and-swap on an empty entry always succeeds; the first value is kept).  With the
@@ -671,6 +697,7 @@ static void insert_candidates(orc_cache* c, const orc_candidate* cand, size_t n_
             c->stats[5]++;
         } else if (r == 0) {
             c->h2[slot] = cand[q].h2;
+            c->cls[slot] = cand[q].vis;
             if (c->alg1)
                 orc_rgb9e5_decode(orc_rgb9e5_encode(cand[q].rgb[0], cand[q].rgb[1], cand[q].rgb[2]),
                                   &c->rgb[3 * slot]);
@@ -678,7 +705,17 @@ static void insert_candidates(orc_cache* c, const orc_candidate* cand, size_t n_
                 for (int k = 0; k < 3; ++k) c->rgb[3 * slot + k] = cand[q].rgb[k];
             c->stats[4]++;
         } else {
-            c->stats[6]++;
+            int64_t v = c->replace ? replacement_victim(c, cand[q].cell, cand[q].vis) : -1;
+            if (v >= 0) {
+                /* the evicted entry's descriptor misses from now on; the cell stays
+                 * full, so occupied slots still form a prefix */
+                c->h2[v] = cand[q].h2;
+                c->cls[v] = cand[q].vis;
+                for (int k = 0; k < 3; ++k) c->rgb[3 * (uint64_t)v + k] = cand[q].rgb[k];
+                c->stats[9]++;
+            } else {
+                c->stats[6]++;
+            }
         }
     }
 }
@@ -688,7 +725,8 @@ int orc_run_batch(orc_cache* c, uint64_t n, const float* u, const float* v,
                   const float* nx, const float* ny, const float* nz, double* rgb,
                   uint16_t* hits, uint32_t* evaluated, uint64_t* probe_key,
                   uint64_t* probe_cell, uint32_t* probe_h2, uint8_t* probe_hit,
-                  const float* g1u, const float* g1v, const float* g2u, const float* g2v) {
+                  const float* g1u, const float* g1v, const float* g2u, const float* g2v,
+                  const uint8_t* vis) {
     int status = ORC_OK;
     uint32_t max_n = 1;
     for (uint32_t m = 0; m < c->n_mats; ++m)
@@ -787,6 +825,7 @@ int orc_run_batch(orc_cache* c, uint64_t n, const float* u, const float* v,
                 }
                 cand[n_cand].cell = rcell[j];
                 cand[n_cand].h2 = rh2[j];
+                cand[n_cand].vis = vis ? vis[i] : 0;
                 for (int k = 0; k < 3; ++k) cand[n_cand].rgb[k] = (float)val[3 * j + k];
                 n_cand++;
             }
@@ -826,6 +865,11 @@ void orc_cache_table(const orc_cache* c, uint32_t* h2, float* rgb) {
         memcpy(h2, c->h2, slots * sizeof(uint32_t));
         memcpy(rgb, c->rgb, 3 * slots * sizeof(float));
     }
+}
+
+void orc_cache_classes(const orc_cache* c, uint8_t* cls) {
+    size_t slots = c->off ? 0 : (size_t)c->n_cells * c->n_entries;
+    if (slots) memcpy(cls, c->cls, slots);
 }
 
 void orc_cache_stats(const orc_cache* c, uint64_t out[ORC_NSTATS]) {

@@ -141,6 +141,15 @@ void orc_cache_set_level_offset(orc_cache* c, int32_t offset);
  * looks up the table as the earlier points of its batch left it and inserts its evaluated
  * cacheable nodes at once, with values stored as their 32-bit encoding (RGB9E5). */
 void orc_cache_set_alg1(orc_cache* c, int on);
+/* on != 0: replacement by visibility class, the prioritisation of directly visible
+ * shading points that Sec. 5 proposes.  Every point carries a class (0 = seen directly
+ * from the camera, k = reached after k bounces; orc_run_batch's vis) and every entry
+ * the class of the point that inserted it.  An insert into a full cell that holds no
+ * entry of its descriptor overwrites the entry of the largest class, if that class is
+ * larger than the newcomer's (the first such entry on ties), and counts it as replaced;
+ * otherwise the value is dropped as with keep-first.  Lookups do not change classes.
+ * With every class 0 the table evolves exactly as with keep-first. */
+void orc_cache_set_replacement(orc_cache* c, int on);
 void orc_cache_reset(orc_cache* c);
 uint32_t orc_cache_n_roots(const orc_cache* c, uint32_t mat);
 /* Root node IDs of a material in ascending order (n_roots entries). */
@@ -153,6 +162,8 @@ void orc_cache_roots(const orc_cache* c, uint32_t mat, uint32_t* out);
  * roots in ascending node ID), each may be NULL.
  * g1u, g1v, g2u, g2v: per-point ray-cone texture-coordinate gradients (n each) that
  * give each point its own mip level (orc_level), or all NULL for the cache's level.
+ * vis: per-point visibility class (n entries) for the replacement policy, or NULL for
+ * class 0 everywhere.
  * Returns ORC_OK, or ORC_ERR_BADMAT if some mat[i] >= n_mats (those points
  * get rgb 0, hits 0 and no probes). */
 int orc_run_batch(orc_cache* c, uint64_t n, const float* u, const float* v,
@@ -160,10 +171,13 @@ int orc_run_batch(orc_cache* c, uint64_t n, const float* u, const float* v,
                   const float* nx, const float* ny, const float* nz, double* rgb,
                   uint16_t* hits, uint32_t* evaluated, uint64_t* probe_key,
                   uint64_t* probe_cell, uint32_t* probe_h2, uint8_t* probe_hit,
-                  const float* g1u, const float* g1v, const float* g2u, const float* g2v);
+                  const float* g1u, const float* g1v, const float* g2u, const float* g2v,
+                  const uint8_t* vis);
 
 /* Table contents: h2[N_c*N_e], rgb[3*N_c*N_e] (slot-major r,g,b). */
 void orc_cache_table(const orc_cache* c, uint32_t* h2, float* rgb);
+/* Visibility class of every slot's entry (N_c*N_e bytes; meaningful where h2 != 0). */
+void orc_cache_classes(const orc_cache* c, uint8_t* cls);
 
 /* ---- learned surrogate of a cacheable node -------------------------------------------
  * Network of (u, v): features [sin pi k u, cos pi k u, sin pi k v, cos pi k v], k=1..16,
@@ -178,8 +192,9 @@ int orc_cache_set_surrogate(orc_cache* c, uint32_t mat, uint32_t node, const dou
 
 /* Counters, in this order:
  * 0 lookups, 1 hits, 2 misses, 3 candidates, 4 inserted, 5 dropped_dup,
- * 6 dropped_full, 7 nodes_evaluated, 8 batches. */
-#define ORC_NSTATS 9
+ * 6 dropped_full, 7 nodes_evaluated, 8 batches, 9 replaced (entries overwritten by the
+ * replacement policy; inserted counts only empty slots taken). */
+#define ORC_NSTATS 10
 void orc_cache_stats(const orc_cache* c, uint64_t out[ORC_NSTATS]);
 
 #ifdef __cplusplus
