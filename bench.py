@@ -207,6 +207,9 @@ def ours(args, rank, world, local_rank, dist):
         cached.set_timing(False)
         timing = cached.read_timing()
         frame_stats = cached.stats()   # reset() zeroes the counters per frame: one frame's worth
+        cached.reset()
+        cached.eval_batch(dev_passes[0], outs, hits)
+        pass0_stats = cached.stats()   # the empty-table pass: no lookup launch
         # the whole frame (reset + 16 passes) as one CUDA graph: the headline
         graph = cached.graph(dev_passes, [outs] * SPP, [hits] * SPP, reset=True)
         for _ in range(max(1, args.warmup)):
@@ -257,13 +260,20 @@ def ours(args, rank, world, local_rank, dist):
     flops_eval = frame_stats["flops"] - flops_missed
     eval_tflops = flops_eval * args.steps / (ms["eval"] / 1e3) / 1e12 if ms["eval"] else 0.0
     missed_tflops = flops_missed * args.steps / (ms["missed"] / 1e3) / 1e12 if ms["missed"] else 0.0
-    # algorithmic bytes of the lookup: u, v of every grouped point, the hash2 words
-    # examined (4 B each), the 12-B value of every hit and one 16-B record per probe
-    look_bytes_frame = (8 * n * SPP
-                        + 4 * frame_stats["slots_probed"]
-                        + 12 * frame_stats["hits"]
-                        + 16 * frame_stats["lookups"])
+    # algorithmic bytes of the lookup kernel, which runs on passes 1..15 (the empty-table
+    # first pass forms its descriptors in the evaluator): per point 12 B (u, v, material),
+    # per probe 16 B for every slot examined up to the hit or the first empty slot (all N_e
+    # of a full cell) plus a 16-B hit/value write -- the method's per-unit figure, for
+    # 16-byte slots {hash2, r, g, b}.  This layout moves less per probe: 4 B per hash2 word
+    # examined and 12 B per hit value (the "layout" figure below).
+    pts_looked = n * (SPP - 1)
+    look_probes = frame_stats["lookups"] - pass0_stats["lookups"]
+    look_slots = frame_stats["slots_probed"] - pass0_stats["slots_probed"]
+    look_hits = frame_stats["hits"] - pass0_stats["hits"]
+    look_bytes_frame = 12 * pts_looked + 16 * look_slots + 16 * look_probes
+    layout_bytes_frame = 8 * pts_looked + 4 * look_slots + 12 * look_hits + 16 * look_probes
     look_gbs = look_bytes_frame * args.steps / (ms["lookup"] / 1e3) / 1e9 if ms["lookup"] else 0.0
+    layout_gbs = layout_bytes_frame * args.steps / (ms["lookup"] / 1e3) / 1e9 if ms["lookup"] else 0.0
     kernels = {
         "eval": {"bound": "alu", "achieved": round(eval_tflops, 3), "peak": round(fp32_peak, 2),
                  "unit": "TFLOP/s", "frac": round(eval_tflops / fp32_peak, 4),
@@ -273,7 +283,11 @@ def ours(args, rank, world, local_rank, dist):
                        "ms_per_pass": round(per_launch_ms["missed"], 4), "traffic": NCU_TRAFFIC["eval_roots"]},
         "lookup": {"bound": "hbm", "achieved": round(look_gbs, 1), "peak": hbm_peak, "unit": "GB/s",
                    "frac": round(look_gbs / hbm_peak, 4), "ms_per_launch": round(per_launch_ms["lookup"], 4),
-                   "traffic": NCU_TRAFFIC["lookup"]},
+                   "traffic": NCU_TRAFFIC["lookup"],
+                   "bytes_per_launch": round(look_bytes_frame / (SPP - 1)),
+                   "slots_examined_per_probe": round(look_slots / max(1, look_probes), 3),
+                   "achieved_layout_bytes": round(layout_gbs, 1),
+                   "frac_layout_bytes": round(layout_gbs / hbm_peak, 4)},
     }
     phase_of = {"eval": "eval", "eval_roots": "missed", "lookup": "lookup"}
     dominant = max(phase_of, key=lambda k: ms[phase_of[k]])
@@ -319,6 +333,8 @@ def ours(args, rank, world, local_rank, dist):
             for off in (0, -1):
                 r = line["ray_cones"][f"offset{off}"]
                 r["speedup_cached_over_uncached"] = round(r["cached"] / u_value, 3)
+    if "replace" in legs:
+        line["replacement"] = replace_leg(torch, P, dev, local_rank, seed=rank)
     if "sweep" in legs:
         line["scale_sweep"] = sweep_leg(torch, P, dev, local_rank, seed=rank)
     if rank == 0 and not args.no_cpu_baseline and "cpu" in legs:
@@ -441,6 +457,66 @@ def alg1_leg(torch, P, mats, dev_passes, outs, hits, local_rank):
             "schedule": tune["schedule"],
             "hit_rate": round(st["hits"] / max(1, st["lookups"]), 4),
             "table": {k: st[k] for k in ("inserted", "dropped_dup", "dropped_full", "dropped_race")}}
+
+
+REPL_PASSES, REPL_BOUNCES = 8, (0.5, 0.25)
+
+
+def replace_leg(torch, P, dev, local_rank, seed=0):
+    """Path-traced passes of the benchmark frame (Sec. 5's case for prioritising directly
+    visible shading points): each pass is one batch of the 2,073,600 directly visible
+    samples (class 0) followed by the indirect shading points of two bounces (half and a
+    quarter as many, each on the surface seen by a random pixel: classes 1 and 2); 8 passes,
+    table 2^21 x 8.  Keep-first against replacement by visibility class: points/s of the
+    whole sequence (reset + 8 passes) replayed as one CUDA graph, hit rate of all lookups
+    and of the directly visible points' lookups over passes 1..7, entries replaced; and the
+    same passes uncached."""
+    mats, frame = workload(seed)
+    host = [frame.points_paths(p, REPL_BOUNCES) for p in range(REPL_PASSES)]
+    n = len(host[0]["u"])
+    passes = [P.points_to_device(h, dev) for h in host]
+    del host
+    nroots = torch.tensor([len(P.analyze_material(m)["roots"]) for m in mats], dtype=torch.int64, device=dev)
+    outs = torch.empty((3, n), dtype=torch.float32, device=dev)
+    hits = [torch.empty(n, dtype=torch.int16, device=dev) for _ in passes]
+    res = {"config": f"frame 1920x1080, {REPL_PASSES} path-traced passes of {n} points (2073600 direct + "
+                     f"{n - WIDTH * HEIGHT} indirect of 2 bounces), {N_MATS} materials, "
+                     f"table {N_CELLS}x{N_ENTRIES} slots", "unit": UNIT, "points_per_pass": n}
+    for name, flags in (("keep_first", 0), ("replacement", P.PMC_REPLACE_VISIBILITY), ("uncached", P.PMC_CACHE_OFF)):
+        c = P.Cache(mats, N_CELLS, N_ENTRIES, uv_level=LEVEL, flags=flags, device=local_rank)
+        for p in range(2):
+            c.eval_batch(passes[p], outs, hits[p])
+        c.autotune(passes[2], reps=2)
+        g = c.graph(passes, [outs] * REPL_PASSES, hits, reset=True)
+        g.launch()
+        torch.cuda.synchronize()
+        t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        t0.record()
+        for _ in range(3):
+            g.launch()
+        t1.record()
+        torch.cuda.synchronize()
+        g.close()
+        r = {"points_per_s": round(3 * n * REPL_PASSES / (t0.elapsed_time(t1) / 1e3), 1)}
+        if name != "uncached":
+            c.reset()
+            for p in range(REPL_PASSES):
+                c.eval_batch(passes[p], outs, hits[p])
+            st = c.stats()
+            dh = dl = 0
+            for p in range(1, REPL_PASSES):
+                d = passes[p]["vis"] == 0
+                dh += int(hits[p][d].long().sum())
+                dl += int(nroots[passes[p]["mat"][d].long()].sum())
+            r.update(hit_rate=round(st["hits"] / max(1, st["lookups"]), 4), direct_hit_rate=round(dh / max(1, dl), 4),
+                     inserted=st["inserted"], replaced=st["replaced"], dropped_full=st["dropped_full"])
+        c.close()
+        res[name] = r
+    res["speedup_replacement_over_keep_first"] = round(res["replacement"]["points_per_s"] /
+                                                       res["keep_first"]["points_per_s"], 3)
+    del passes
+    torch.cuda.empty_cache()
+    return res
 
 
 def cones_leg(torch, P, dev, local_rank, seed=0):
@@ -803,8 +879,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--legs", default="cached,uncached,e2e,surr,f128,alg1,cones,cpu",
-                    help="comma list of cached, uncached, e2e, surr, f128, alg1, cones, sweep, cpu (sweep is not in the "
+    ap.add_argument("--legs", default="cached,uncached,e2e,surr,f128,alg1,cones,replace,cpu",
+                    help="comma list of cached, uncached, e2e, surr, f128, alg1, cones, replace, sweep, cpu (sweep is not in the "
                          "default: about a minute more; profiling runs take 'cached')")
     ap.add_argument("--profile", action="store_true",
                     help="eager frames only, for ncu launch lists (prints launches per frame)")

@@ -144,6 +144,23 @@ typedef struct {
                                      a hit returns the decoded value.  Only the grouped and
                                      unsorted schedules apply; pmc_last_hit_masks is not
                                      available */
+#define PMC_REPLACE_VISIBILITY 0x100u /* replacement by visibility class instead of
+                                     keep-first, the prioritisation of directly visible
+                                     shading points that Sec. 5 proposes.  Each point may
+                                     carry a class (pmc_points.vis: 0 = seen directly from
+                                     the camera, k = reached after k bounces; NULL = all
+                                     0) and each entry keeps its inserter's class.  Inserts
+                                     are still resolved per cell in ascending (point
+                                     index, node ID) order: a key already in the cell is
+                                     a duplicate; else the first empty slot takes it;
+                                     else the entry of the largest class is overwritten
+                                     if that class is larger than the newcomer's (the
+                                     first such entry on ties; counted in `replaced`);
+                                     else the value is dropped.  Lookups do not change
+                                     classes.  With every class 0 the table evolves as
+                                     with keep-first.  The table is still deterministic.
+                                     Not combinable with PMC_ALG1 or PMC_INSERT_ROUNDS
+                                     (PMC_ERR_INVALID_ARG); one byte per slot more */
 
 typedef struct {
     uint64_t n_cells;        /* N_c >= 1, < 2^32                                  */
@@ -170,7 +187,10 @@ typedef struct {
  *   level = clamp(floor(-log2(min(|g1|, |g2|))) + level_offset, 0, 13),
  * the squared norms formed in FP32 (each product and the sum rounded to nearest); a
  * zero footprint gives 13, an infinite or NaN one 0.  All four NULL: every point uses
- * the cache's uv_level.  Either all four or none must be given. */
+ * the cache's uv_level.  Either all four or none must be given.
+ * vis (optional): one byte per point, its visibility class for PMC_REPLACE_VISIBILITY
+ * (0 = directly visible, k = after k bounces); NULL = class 0 for every point.  Read only
+ * by caches created with that flag. */
 typedef struct {
     const float* u;
     const float* v;
@@ -186,6 +206,7 @@ typedef struct {
     const float* g1v;
     const float* g2u;
     const float* g2v;
+    const uint8_t* vis;
 } pmc_points;
 
 /* Cumulative counters since creation or pmc_reset. */
@@ -194,7 +215,8 @@ typedef struct {
     uint64_t hits;
     uint64_t misses;
     uint64_t candidates;      /* evaluated cacheable nodes offered for insertion     */
-    uint64_t inserted;        /* = occupied slots (nothing is ever evicted)          */
+    uint64_t inserted;        /* = occupied slots (an entry is never removed; only
+                                 PMC_REPLACE_VISIBILITY overwrites one)                */
     uint64_t dropped_dup;     /* an entry with the same (cell, hash2) was present    */
     uint64_t dropped_full;    /* the cell had no empty entry                         */
     uint64_t nodes_evaluated; /* node instructions executed, summed over points      */
@@ -208,6 +230,9 @@ typedef struct {
                                  in batches (the batched-miss kernel)                  */
     uint64_t dropped_race;    /* PMC_ALG1: the compare-and-swap found its slot taken by
                                  another key (always 0 otherwise)                      */
+    uint64_t replaced;        /* PMC_REPLACE_VISIBILITY: entries overwritten by a value of
+                                 a smaller class (inserted counts only empty slots taken,
+                                 so it still equals the occupied slots)                */
 } pmc_stats_t;
 
 /* Compiles the networks (cacheable-node analysis, constant folding, serialisation;
@@ -243,6 +268,11 @@ pmc_status pmc_stats(pmc_cache* cache, pmc_stats_t* out);
  * 16 bytes {uint32 hash2 (0 = empty); float r, g, b} (with PMC_ALG1 the values are the
  * decoded RGB9E5 codes).  `bytes` must be at least that size. */
 pmc_status pmc_table_dump(pmc_cache* cache, void* host_dst, size_t bytes);
+
+/* PMC_REPLACE_VISIBILITY only (else PMC_ERR_UNSUPPORTED): synchronises and copies the
+ * visibility class of every slot's entry to `host_dst` (n_cells * n_entries bytes, slot
+ * order as pmc_table_dump; 0 for an empty slot).  `bytes` must be at least that size. */
+pmc_status pmc_slot_classes(pmc_cache* cache, uint8_t* host_dst, size_t bytes);
 
 /* Synchronises and copies, for the last batch, one 64-bit mask per point (host
  * memory, n entries, original point order): bit r set when the point's r-th

@@ -34,6 +34,7 @@ struct pmc_cache {
     float* d_params = nullptr;
     uint32_t* d_roots = nullptr;
     uint4* d_table = nullptr;
+    uint8_t* d_cls = nullptr;             // PMC_REPLACE_VISIBILITY: class of every slot's entry
     unsigned long long* d_claims = nullptr;
     Control* d_ctl = nullptr;
     unsigned long long* d_stats = nullptr;

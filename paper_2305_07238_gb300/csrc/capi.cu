@@ -68,6 +68,8 @@ bool surrogates_active(const pmc_cache* c) { return c->use_surrogates && c->any_
 
 bool alg1_table(const pmc_cache* c) { return c->use_cache && (c->desc.flags & PMC_ALG1) != 0; }
 
+bool replacing(const pmc_cache* c) { return c->use_cache && (c->desc.flags & PMC_REPLACE_VISIBILITY) != 0; }
+
 // The table in 16-byte units: 16-byte slots, or 8-byte slots with the paper's concurrent
 // update.
 uint64_t table_units(const pmc_cache* c) {
@@ -154,6 +156,7 @@ void pmc_destroy_cache(pmc_cache* c) {
         dfree(&c->d_params);
         dfree(&c->d_roots);
         dfree(&c->d_table);
+        dfree(&c->d_cls);
         dfree(&c->d_claims);
         dfree(&c->d_ctl);
         dfree(&c->d_stats);
@@ -180,6 +183,10 @@ pmc_status pmc_create_cache(const pmc_cache_desc* desc, const pmc_material* mats
     if (desc->uv_level > 13) return PMC_ERR_INVALID_ARG;
     if (desc->level_offset < -13 || desc->level_offset > 13) return PMC_ERR_INVALID_ARG;
     const bool off = (desc->flags & PMC_CACHE_OFF) != 0;
+    // the replacement policy needs the deterministic per-cell insert: not the paper's
+    // concurrent update, not the claim rounds
+    if ((desc->flags & PMC_REPLACE_VISIBILITY) && (desc->flags & (PMC_ALG1 | PMC_INSERT_ROUNDS)))
+        return PMC_ERR_INVALID_ARG;
     if (!off) {
         if (desc->n_cells == 0 || desc->n_cells > 0xFFFFFFFFull) return PMC_ERR_INVALID_ARG;
         if (desc->n_entries == 0 || desc->n_entries > MAX_ENTRIES) return PMC_ERR_INVALID_ARG;
@@ -287,6 +294,7 @@ pmc_status pmc_create_cache(const pmc_cache_desc* desc, const pmc_material* mats
         (s = dalloc(&c->d_params, params.size())) != PMC_OK ||
         (s = dalloc(&c->d_roots, c->roots.size())) != PMC_OK ||
         (s = dalloc(&c->d_table, slots ? table_units(c) + 16 : 0)) != PMC_OK ||
+        (s = dalloc(&c->d_cls, replacing(c) ? slots : 0)) != PMC_OK ||
         (s = dalloc(&c->d_claims, cells)) != PMC_OK ||
         (s = dalloc(&c->d_ctl, 1)) != PMC_OK ||
         (s = dalloc(&c->d_stats, ST_COUNT)) != PMC_OK ||
@@ -404,6 +412,10 @@ pmc_status enqueue_batch(pmc_cache* c, const pmc_points* pts, float* out_rgb, ui
     a.unsorted = c->unsorted;
     a.probe_inline = c->probe_inline;
     a.lookup_rb = c->lookup_rb;
+    if (replacing(c)) {
+        a.slot_cls = c->d_cls;
+        a.vis = pts->vis;
+    }
     cudaEvent_t* ev = nullptr;
     if (c->timing && !recording) {
         while (c->events.size() < c->events_used + PH_COUNT + 1) {
@@ -462,7 +474,8 @@ pmc_status pmc_eval_batch_host(pmc_cache* c, const pmc_points* hp, float* host_r
         dfree(&c->d_hhits);
         c->cap_host = 0;
         pmc_status st;
-        if ((st = dalloc(&c->d_hpts, 13 * (size_t)n)) != PMC_OK) return st;   // 9 planes + gradients
+        // 9 planes + gradients + one plane of which the visibility classes take a quarter
+        if ((st = dalloc(&c->d_hpts, 14 * (size_t)n)) != PMC_OK) return st;
         if ((st = dalloc(&c->d_hrgb, 3 * (size_t)n)) != PMC_OK) return st;
         if ((st = dalloc(&c->d_hhits, (size_t)n)) != PMC_OK) return st;
         c->cap_host = n;
@@ -475,11 +488,14 @@ pmc_status pmc_eval_batch_host(pmc_cache* c, const pmc_points* hp, float* host_r
     const int planes = cones ? 13 : 9;
     for (int k = 0; k < planes && e == cudaSuccess && n; ++k)
         e = cudaMemcpyAsync(d + k * C, src[k], n * 4, cudaMemcpyHostToDevice, s);
+    const uint8_t* dvis = hp->vis ? reinterpret_cast<const uint8_t*>(d + 13 * C) : nullptr;
+    if (e == cudaSuccess && hp->vis && n)
+        e = cudaMemcpyAsync((void*)dvis, hp->vis, n, cudaMemcpyHostToDevice, s);
     if (e != cudaSuccess) return cuda_fail(c, e);
     pmc_points dp{d, d + C, (const uint32_t*)(d + 2 * C), d + 3 * C, d + 4 * C, d + 5 * C,
                   d + 6 * C, d + 7 * C, d + 8 * C, n,
                   cones ? d + 9 * C : nullptr, cones ? d + 10 * C : nullptr,
-                  cones ? d + 11 * C : nullptr, cones ? d + 12 * C : nullptr};
+                  cones ? d + 11 * C : nullptr, cones ? d + 12 * C : nullptr, dvis};
     pmc_status st = pmc_eval_batch(c, &dp, c->d_hrgb, host_hits ? c->d_hhits : nullptr, stream);
     if (st != PMC_OK) return st;
     for (int k = 0; k < 3 && e == cudaSuccess && n; ++k)
@@ -515,6 +531,7 @@ pmc_status pmc_stats(pmc_cache* c, pmc_stats_t* out) {
     out->dropped_dup = v[ST_DUP];
     out->dropped_full = v[ST_FULL];
     out->dropped_race = v[ST_RACE];
+    out->replaced = v[ST_REPLACED];
     out->nodes_evaluated = v[ST_NODES];
     out->batches = v[ST_BATCHES];
     out->flops = v[ST_FLOPS];
@@ -568,6 +585,24 @@ pmc_status pmc_table_dump(pmc_cache* c, void* host_dst, size_t bytes) {
             }
         }
     }
+    return st;
+}
+
+pmc_status pmc_slot_classes(pmc_cache* c, uint8_t* host_dst, size_t bytes) {
+    if (!c || !host_dst) return PMC_ERR_INVALID_ARG;
+    if (!replacing(c)) return PMC_ERR_UNSUPPORTED;
+    const size_t slots = (size_t)c->desc.n_cells * c->desc.n_entries;
+    if (bytes < slots) return PMC_ERR_INVALID_ARG;
+    pmc_status st = pmc_sync(c);
+    if (st == PMC_ERR_CUDA) return st;
+    DeviceGuard g(c->desc.device);
+    cudaError_t e = cudaMemcpy(host_dst, c->d_cls, slots, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(c, e);
+    // an empty slot's class byte is stale: report 0 there
+    std::vector<uint32_t> raw(slots * 4u);
+    if ((st = pmc_table_dump(c, raw.data(), slots * 16u)) == PMC_ERR_CUDA) return st;
+    for (size_t k = 0; k < slots; ++k)
+        if (raw[4 * k] == 0u) host_dst[k] = 0;
     return st;
 }
 
@@ -960,6 +995,7 @@ pmc_status pmc_set_schedule(pmc_cache* c, const pmc_schedule* sc) {
     if (sc->lookup_rb != 1 && sc->lookup_rb != 2 && sc->lookup_rb != 4) return PMC_ERR_INVALID_ARG;
     if ((sc->flags & PMC_UNSORTED) && surrogates_active(c)) return PMC_ERR_UNSUPPORTED;
     if (!(sc->flags & PMC_EVAL_INLINE) && c->max_level >= MAX_LEVELS) return PMC_ERR_UNSUPPORTED;
+    if ((sc->flags & PMC_INSERT_ROUNDS) && (c->desc.flags & PMC_REPLACE_VISIBILITY)) return PMC_ERR_UNSUPPORTED;
     c->split = (sc->flags & PMC_EVAL_INLINE) ? 0 : 1;
     c->unsorted = (sc->flags & PMC_UNSORTED) ? 1 : 0;
     c->probe_inline = (sc->flags & PMC_PROBE_INLINE) ? 1 : 0;
@@ -1128,7 +1164,7 @@ pmc_status pmc_autotune(pmc_cache* c, const pmc_points* sample, uint32_t reps, p
         if (c->use_cache) cand.push_back({keep | PMC_EVAL_INLINE, 4});
         if (c->use_cache) cand.push_back({keep | PMC_PROBE_INLINE, 4});
         if (!surrogates_active(c)) cand.push_back({keep | PMC_EVAL_INLINE | PMC_UNSORTED, 4});
-        if (c->use_cache && c->max_level < MAX_LEVELS) cand.push_back({keep ^ PMC_INSERT_ROUNDS, 4});
+        if (c->use_cache && c->max_level < MAX_LEVELS && !replacing(c)) cand.push_back({keep ^ PMC_INSERT_ROUNDS, 4});
     }
     if (cand.empty()) cand.push_back(orig);
     if (cand.size() > PMC_TUNE_MAX) cand.resize(PMC_TUNE_MAX);
@@ -1136,10 +1172,13 @@ pmc_status pmc_autotune(pmc_cache* c, const pmc_points* sample, uint32_t reps, p
     const uint64_t units = table_units(c);
     const size_t table_bytes = units ? (size_t)(units + 16) * sizeof(uint4) : 0;
     uint4* saved = nullptr;
+    uint8_t* saved_cls = nullptr;
+    const size_t cls_bytes = replacing(c) ? (size_t)c->desc.n_cells * c->desc.n_entries : 0;
     float* rgb = nullptr;
     uint16_t* hits = nullptr;
     unsigned long long stats[ST_COUNT];
     if (table_bytes && (st = dalloc(&saved, units + 16)) != PMC_OK) return st;
+    if (cls_bytes && (st = dalloc(&saved_cls, cls_bytes)) != PMC_OK) { dfree(&saved); return st; }
     if ((st = dalloc(&rgb, 3 * (size_t)std::max<uint64_t>(n, 1))) != PMC_OK) { dfree(&saved); return st; }
     if ((st = dalloc(&hits, (size_t)std::max<uint64_t>(n, 1))) != PMC_OK) { dfree(&saved); dfree(&rgb); return st; }
     cudaStream_t s = nullptr;
@@ -1148,6 +1187,7 @@ pmc_status pmc_autotune(pmc_cache* c, const pmc_points* sample, uint32_t reps, p
     if (e == cudaSuccess) e = cudaEventCreate(&e0);
     if (e == cudaSuccess) e = cudaEventCreate(&e1);
     if (e == cudaSuccess && table_bytes) e = cudaMemcpy(saved, c->d_table, table_bytes, cudaMemcpyDeviceToDevice);
+    if (e == cudaSuccess && cls_bytes) e = cudaMemcpy(saved_cls, c->d_cls, cls_bytes, cudaMemcpyDeviceToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(stats, c->d_stats, sizeof(stats), cudaMemcpyDeviceToHost);
     const bool s_empty = c->table_empty, s_all_miss = c->last_all_miss, s_unsorted = c->last_unsorted;
     const bool s_timing = c->timing;
@@ -1158,6 +1198,7 @@ pmc_status pmc_autotune(pmc_cache* c, const pmc_points* sample, uint32_t reps, p
     auto restore = [&]() -> cudaError_t {
         cudaError_t r = cudaSuccess;
         if (table_bytes) r = cudaMemcpyAsync(c->d_table, saved, table_bytes, cudaMemcpyDeviceToDevice, s);
+        if (r == cudaSuccess && cls_bytes) r = cudaMemcpyAsync(c->d_cls, saved_cls, cls_bytes, cudaMemcpyDeviceToDevice, s);
         if (r == cudaSuccess && cells) r = cudaMemsetAsync(c->d_claims, 0xFF, cells * sizeof(unsigned long long), s);
         if (r == cudaSuccess) r = cudaMemsetAsync(&c->d_ctl->epoch, 0, sizeof(uint32_t), s);
         c->epoch_host = 0;
@@ -1199,6 +1240,7 @@ pmc_status pmc_autotune(pmc_cache* c, const pmc_points* sample, uint32_t reps, p
     if (e1) cudaEventDestroy(e1);
     if (s) cudaStreamDestroy(s);
     dfree(&saved);
+    dfree(&saved_cls);
     dfree(&rgb);
     dfree(&hits);
     if (e != cudaSuccess) return cuda_fail(c, e);

@@ -410,20 +410,27 @@ size_t eval_smem_bytes(uint32_t max_slots) {
 }
 
 // Offers the lanes' freshly evaluated cacheable-node values to the table (Sec. 3).
-// A cell that was full at lookup stays full (nothing is evicted), so its value is
-// counted as dropped without becoming a candidate.  Lanes carrying the same
+// Keep-first: a cell that was full at lookup stays full (nothing is evicted), so its
+// value is counted as dropped without becoming a candidate, and lanes carrying the same
 // (cell, hash2) collapse onto the smallest point index; the others share its fate.
-// Must be called by all 32 lanes.
+// Replacement by visibility class: every value becomes a candidate of its own, since a
+// full cell may still take it and copies of one key with different classes can meet
+// different fates; its dup scan starts at slot 0, since an eviction can put the key
+// anywhere in the cell.  Must be called by all 32 lanes.
 __device__ __forceinline__ void offer(const BatchArgs& a, bool act, uint32_t orig, uint32_t node, uint32_t cell,
                                       uint32_t h2, uint32_t start, bool full, float r, float g, float b,
                                       unsigned long long* n_cand, unsigned long long* n_full) {
+    const bool replace = a.slot_cls != nullptr;   // uniform
     *n_cand += act ? 1u : 0u;
-    *n_full += (act && full) ? 1u : 0u;
-    const bool emit = act && !full;
+    *n_full += (act && full && !replace) ? 1u : 0u;
+    const bool emit = act && (!full || replace);
     bool winner = false;
     uint32_t shadows = 0;
     const unsigned em = __ballot_sync(FULL_MASK, emit);
-    if (emit) {
+    if (emit && replace) {
+        winner = true;
+        start = 0;
+    } else if (emit) {
         const unsigned long long k64 = ((unsigned long long)cell << 32) | h2;
         const unsigned grp = __match_any_sync(em, k64);
         const uint32_t mn = __reduce_min_sync(grp, orig);
@@ -432,6 +439,7 @@ __device__ __forceinline__ void offer(const BatchArgs& a, bool act, uint32_t ori
     }
     const uint32_t idx = warp_append(&a.ctl->n_cand, winner);
     if (winner) {
+        const uint32_t q = (replace && a.vis) ? (uint32_t)__ldg(&a.vis[orig]) : 0u;
         Candidate c;
         c.prio = ((unsigned long long)orig << 16) | node;
         c.cell = cell;
@@ -439,7 +447,7 @@ __device__ __forceinline__ void offer(const BatchArgs& a, bool act, uint32_t ori
         c.r = r;
         c.g = g;
         c.b = b;
-        c.target = start | (shadows << 16);
+        c.target = start | (q << 8) | (shadows << 16);
         if (idx < a.probe_cap) {
             a.cands[idx] = c;
             if (!a.insert_rounds) a.lists[0][idx] = cell;   // compact cells for the binning
@@ -1079,7 +1087,7 @@ __global__ void __launch_bounds__(256) k_insert(BatchArgs a) {
                 int target = -1;
                 bool dup = false;
                 // slots before the start held other keys when the pass began
-                for (uint32_t e = tgt & 0xFFFFu; e < ne; ++e) {
+                for (uint32_t e = tgt & 0xFFu; e < ne; ++e) {
                     const uint32_t h = __ldcg(&hw[e]);
                     if (h == h2) { dup = true; break; }
                     if (h == 0u) { target = (int)e; break; }
@@ -1088,7 +1096,7 @@ __global__ void __launch_bounds__(256) k_insert(BatchArgs a) {
                 else if (target < 0) n_full += weight;
                 else if (final_round) atomicOr(&a.ctl->err, ERR_INSERT);
                 else {
-                    a.cands[idx].target = (uint32_t)target | (tgt & 0xFFFF0000u);
+                    a.cands[idx].target = (uint32_t)target | (tgt & 0xFFFFFF00u);
                     atomicMin(&a.claims[cell], claim_word(epoch, prio));
                     live = true;
                 }
@@ -1112,7 +1120,7 @@ __global__ void __launch_bounds__(256) k_insert(BatchArgs a) {
                 const uint32_t cell = __ldcg(&a.cands[idx].cell);
                 if (__ldcg(&a.claims[cell]) == claim_word(epoch, prio)) {
                     const uint32_t tgt = __ldcg(&a.cands[idx].target);
-                    const uint32_t e = tgt & 0xFFFFu;
+                    const uint32_t e = tgt & 0xFFu;
                     cell_h2(a, cell)[e] = __ldcg(&a.cands[idx].h2);
                     float* val = cell_val(a, cell, e);
                     val[0] = __ldcg(&a.cands[idx].r);
@@ -1146,16 +1154,38 @@ constexpr uint32_t INS_MID = 2048;         // at most this many: one block, stag
 // Inserts one candidate into a cell owned by the calling thread (Alg. 1 scan).
 __device__ __forceinline__ void insert_one(const BatchArgs& a, const Candidate& c, uint32_t ne,
                                            unsigned long long* n_ins, unsigned long long* n_dup,
-                                           unsigned long long* n_full) {
+                                           unsigned long long* n_full, unsigned long long* n_rep) {
     uint32_t* cw = cell_h2(a, c.cell);
     const uint32_t weight = 1u + (c.target >> 16);
     int target = -1;
     bool dup = false;
     // slots before the start held other keys when the pass began
-    for (uint32_t e = c.target & 0xFFFFu; e < ne; ++e) {
+    for (uint32_t e = c.target & 0xFFu; e < ne; ++e) {
         const uint32_t h = cw[e];
         if (h == c.h2) { dup = true; break; }
         if (h == 0u) { target = (int)e; break; }
+    }
+    if (!dup && target < 0 && a.slot_cls) {
+        // replacement by visibility class: the first entry of the largest class, if larger
+        // than the newcomer's
+        const uint8_t* cc = a.slot_cls + (size_t)c.cell * ne;
+        uint32_t worst = (c.target >> 8) & 0xFFu;
+        int victim = -1;
+        for (uint32_t e = 0; e < ne; ++e)
+            if (cc[e] > worst) {
+                worst = cc[e];
+                victim = (int)e;
+            }
+        if (victim >= 0) {
+            cw[victim] = c.h2;
+            a.slot_cls[(size_t)c.cell * ne + victim] = (uint8_t)((c.target >> 8) & 0xFFu);
+            float* val = cell_val(a, c.cell, (uint32_t)victim);
+            val[0] = c.r;
+            val[1] = c.g;
+            val[2] = c.b;
+            *n_rep += 1;
+            return;
+        }
     }
     if (dup) {
         *n_dup += weight;
@@ -1163,6 +1193,7 @@ __device__ __forceinline__ void insert_one(const BatchArgs& a, const Candidate& 
         *n_full += weight;
     } else {
         cw[target] = c.h2;
+        if (a.slot_cls) a.slot_cls[(size_t)c.cell * ne + target] = (uint8_t)((c.target >> 8) & 0xFFu);
         float* val = cell_val(a, c.cell, (uint32_t)target);
         val[0] = c.r;
         val[1] = c.g;
@@ -1359,7 +1390,7 @@ __device__ __forceinline__ void resolve_cell(const BatchArgs& a, uint32_t cell, 
         const uint32_t hc = sh2[j], tg = stgt[j];
         const uint32_t shadows = tg >> 16;
         bool dup = false;
-        for (uint32_t e = tg & 0xFFFFu; e < used; ++e)
+        for (uint32_t e = tg & 0xFFu; e < used; ++e)
             if (h[e] == hc) { dup = true; break; }
         if (dup) {
             *n_dup += 1u + shadows;
@@ -1373,6 +1404,68 @@ __device__ __forceinline__ void resolve_cell(const BatchArgs& a, uint32_t cell, 
             *n_ins += 1;
             *n_dup += shadows;   // its shadows find it in the table
         }
+    }
+}
+
+// The same with replacement by visibility class (the prioritisation Sec. 5 proposes): a
+// candidate whose hash2 is in the cell is a duplicate; otherwise it takes the first empty
+// slot, or else overwrites the entry of the largest class if that class is larger than its
+// own (the first such entry on ties), or is dropped.  An eviction can put a key anywhere,
+// so every occupied slot is compared.  The slot file (hash2 words and classes) is written
+// at once; a slot's value is written afterwards by the candidate left owning it, so a
+// candidate that took a slot and was evicted within this resolution gives up its res[].
+template <typename IDX>
+__device__ __forceinline__ void resolve_cell_replace(const BatchArgs& a, uint32_t cell, const IDX* order, uint32_t x0,
+                                                     uint32_t n, const uint32_t* sh2, const uint32_t* stgt,
+                                                     uint8_t* res, uint32_t ne, unsigned long long* n_ins,
+                                                     unsigned long long* n_dup, unsigned long long* n_full,
+                                                     unsigned long long* n_rep) {
+    uint32_t* cw = cell_h2(a, cell);
+    uint8_t* cc = a.slot_cls + (size_t)cell * ne;
+    uint32_t h[MAX_ENTRIES];
+    uint32_t k[MAX_ENTRIES];
+    uint32_t owner[MAX_ENTRIES];   // staged index of the candidate that took the slot here
+    uint32_t used = ne;
+    for (uint32_t e = 0; e < ne; ++e) {
+        h[e] = __ldcg(&cw[e]);
+        k[e] = h[e] ? (uint32_t)cc[e] : 0u;
+        owner[e] = 0xFFFFFFFFu;
+        if (h[e] == 0u && used == ne) used = e;
+    }
+    for (uint32_t x = x0; x < x0 + n; ++x) {
+        const uint32_t j = order[x];
+        const uint32_t hc = sh2[j], q = (stgt[j] >> 8) & 0xFFu;
+        bool dup = false;
+        for (uint32_t e = 0; e < used; ++e) dup |= h[e] == hc;
+        if (dup) {
+            *n_dup += 1;
+            continue;
+        }
+        uint32_t slot = used;
+        if (used < ne) {
+            used++;
+            *n_ins += 1;
+        } else {
+            uint32_t worst = q;
+            slot = ne;
+            for (uint32_t e = 0; e < ne; ++e)
+                if (k[e] > worst) {
+                    worst = k[e];
+                    slot = e;
+                }
+            if (slot == ne) {
+                *n_full += 1;
+                continue;
+            }
+            if (owner[slot] != 0xFFFFFFFFu) res[owner[slot]] = RES_NONE;
+            *n_rep += 1;
+        }
+        h[slot] = hc;
+        k[slot] = q;
+        owner[slot] = j;
+        cw[slot] = hc;
+        cc[slot] = (uint8_t)q;
+        res[j] = (uint8_t)slot;
     }
 }
 
@@ -1392,7 +1485,7 @@ __device__ __forceinline__ void resolve_cell8(const BatchArgs& a, uint32_t cell,
     for (uint32_t x = x0; x < x0 + n; ++x) {
         const uint32_t j = order[x];
         const uint32_t hc = sh2[j], tg = stgt[j];
-        const uint32_t shadows = tg >> 16, st = tg & 0xFFFFu;
+        const uint32_t shadows = tg >> 16, st = tg & 0xFFu;
         bool dup = false;
 #pragma unroll
         for (uint32_t e = 0; e < 8; ++e) dup |= e >= st && e < used && h[e] == hc;
@@ -1455,7 +1548,7 @@ __global__ void __launch_bounds__(INS_WARPS * 32, 6) k_bin_insert_warp(BatchArgs
     WarpStage& st = s_stage[w];
     const uint32_t ne = a.n_entries;
     const Candidate* cb = a.cands_binned;
-    unsigned long long n_dup = 0, n_full = 0, n_ins = 0;
+    unsigned long long n_dup = 0, n_full = 0, n_ins = 0, n_rep = 0;
     const uint32_t n_list = a.ctl->bins_warp;
     for (uint32_t x = blockIdx.x * INS_WARPS + w; x < n_list; x += gridDim.x * INS_WARPS) {
         const uint32_t bin = a.bin_list[x];
@@ -1537,7 +1630,14 @@ __global__ void __launch_bounds__(INS_WARPS * 32, 6) k_bin_insert_warp(BatchArgs
         for (uint32_t q = 0; q < 8; q += 2) {
             const uint32_t ca = 8 * lane + q, cbb = ca + 1;
             const uint32_t xa = st.off[ca], xb = st.off[cbb], xe = st.off[cbb + 1];
-            if (ne <= 8) {
+            if (a.slot_cls) {
+                if (xb > xa)
+                    resolve_cell_replace(a, c0 + ca, st.ord, xa, xb - xa, st.h2, st.tgt, st.res, ne, &n_ins, &n_dup,
+                                         &n_full, &n_rep);
+                if (xe > xb)
+                    resolve_cell_replace(a, c0 + cbb, st.ord, xb, xe - xb, st.h2, st.tgt, st.res, ne, &n_ins, &n_dup,
+                                         &n_full, &n_rep);
+            } else if (ne <= 8) {
                 uint4 a0 = make_uint4(0, 0, 0, 0), a1 = a0, b0 = a0, b1 = a0;
                 if (xb > xa) load_cell_words(a, c0 + ca, &a0, &a1);
                 if (xe > xb) load_cell_words(a, c0 + cbb, &b0, &b1);
@@ -1567,6 +1667,7 @@ __global__ void __launch_bounds__(INS_WARPS * 32, 6) k_bin_insert_warp(BatchArgs
     warp_add_u64(&a.stats[ST_DUP], n_dup);
     warp_add_u64(&a.stats[ST_FULL], n_full);
     warp_add_u64(&a.stats[ST_INSERTED], n_ins);
+    warp_add_u64(&a.stats[ST_REPLACED], n_rep);
 }
 
 struct MidSmem {   // byte offsets into dynamic shared memory
@@ -1604,7 +1705,7 @@ __global__ void __launch_bounds__(INS_MID_T, 4) k_bin_insert_mid(BatchArgs a) {
     const uint32_t t = threadIdx.x, lane = lane_id(), warp = t >> 5;
     const uint32_t ne = a.n_entries;
     const Candidate* cb = a.cands_binned;
-    unsigned long long n_dup = 0, n_full = 0, n_ins = 0;
+    unsigned long long n_dup = 0, n_full = 0, n_ins = 0, n_rep = 0;
     const uint32_t n_list = a.ctl->bins_mid, first = a.ctl->bins_warp;
     for (uint32_t x = blockIdx.x; x < n_list; x += gridDim.x) {
         const uint32_t bin = a.bin_list[first + x];
@@ -1695,7 +1796,10 @@ __global__ void __launch_bounds__(INS_MID_T, 4) k_bin_insert_mid(BatchArgs a) {
         __syncthreads();
         // ---- resolve: one thread per cell
         if (v) {
-            if (ne <= 8)
+            if (a.slot_cls)
+                resolve_cell_replace(a, c0 + t, s_ord, excl, v, s_h2, s_tgt, s_res, ne, &n_ins, &n_dup, &n_full,
+                                     &n_rep);
+            else if (ne <= 8)
                 resolve_cell8(a, c0 + t, w0, w1, s_ord, excl, v, s_h2, s_tgt, s_res, ne, &n_ins, &n_dup, &n_full);
             else
                 resolve_cell(a, c0 + t, s_ord, excl, v, s_h2, s_tgt, s_res, ne, &n_ins, &n_dup, &n_full);
@@ -1715,6 +1819,7 @@ __global__ void __launch_bounds__(INS_MID_T, 4) k_bin_insert_mid(BatchArgs a) {
     warp_add_u64(&a.stats[ST_DUP], n_dup);
     warp_add_u64(&a.stats[ST_FULL], n_full);
     warp_add_u64(&a.stats[ST_INSERTED], n_ins);
+    warp_add_u64(&a.stats[ST_REPLACED], n_rep);
 }
 
 // Bins of more than INS_MID candidates: one block per bin stages the candidates of a range
@@ -1750,7 +1855,7 @@ __device__ __forceinline__ void insert_staged_cell(const BatchArgs& a, const Can
                                                    const uint32_t* idx, const uint32_t* sh2, const uint32_t* stgt,
                                                    const uint32_t* ssrc, uint32_t x0, uint32_t n, uint32_t ne,
                                                    unsigned long long* n_ins, unsigned long long* n_dup,
-                                                   unsigned long long* n_full) {
+                                                   unsigned long long* n_full, unsigned long long* n_rep) {
     uint32_t* cw = cell_h2(a, cell);
     uint32_t h[MAX_ENTRIES];
     uint32_t used = ne;
@@ -1758,13 +1863,56 @@ __device__ __forceinline__ void insert_staged_cell(const BatchArgs& a, const Can
         h[e] = __ldcg(&cw[e]);
         if (h[e] == 0u && used == ne) used = e;
     }
+    if (a.slot_cls) {
+        // replacement by visibility class, as in resolve_cell_replace; one thread handles
+        // the cell's candidates in order and writes each value at once, so an entry
+        // replaced later in the same resolution is simply overwritten
+        uint8_t* cc = a.slot_cls + (size_t)cell * ne;
+        for (uint32_t x = x0; x < x0 + n; ++x) {
+            const uint32_t j = idx[x];
+            const uint32_t hc = sh2[j], q = (stgt[j] >> 8) & 0xFFu;
+            bool dup = false;
+            for (uint32_t e = 0; e < used; ++e) dup |= h[e] == hc;
+            if (dup) {
+                *n_dup += 1;
+                continue;
+            }
+            uint32_t slot = used;
+            if (used < ne) {
+                used++;
+                *n_ins += 1;
+            } else {
+                uint32_t worst = q;
+                slot = ne;
+                for (uint32_t e = 0; e < ne; ++e)
+                    if ((uint32_t)cc[e] > worst) {
+                        worst = cc[e];
+                        slot = e;
+                    }
+                if (slot == ne) {
+                    *n_full += 1;
+                    continue;
+                }
+                *n_rep += 1;
+            }
+            const float4 v = __ldcg(reinterpret_cast<const float4*>(&cb[ssrc[j]].r));   // r, g, b, target
+            h[slot] = hc;
+            cw[slot] = hc;
+            cc[slot] = (uint8_t)q;
+            float* val = cell_val(a, cell, slot);
+            val[0] = v.x;
+            val[1] = v.y;
+            val[2] = v.z;
+        }
+        return;
+    }
     for (uint32_t x = x0; x < x0 + n; ++x) {
         const uint32_t j = idx[x];
         const uint32_t hc = sh2[j], tg = stgt[j];
         const uint32_t shadows = tg >> 16;
         bool dup = false;
         // slots before the candidate's start held other keys when the pass began
-        for (uint32_t e = tg & 0xFFFFu; e < used; ++e)
+        for (uint32_t e = tg & 0xFFu; e < used; ++e)
             if (h[e] == hc) { dup = true; break; }
         if (dup) {
             *n_dup += 1u + shadows;
@@ -1802,7 +1950,7 @@ __global__ void __launch_bounds__(256, 6) k_bin_insert(BatchArgs a) {
     const uint32_t ne = a.n_entries;
     const uint32_t t = threadIdx.x, T = blockDim.x;
     const Candidate* cb = a.cands_binned;
-    unsigned long long n_dup = 0, n_full = 0, n_ins = 0;
+    unsigned long long n_dup = 0, n_full = 0, n_ins = 0, n_rep = 0;
     const uint32_t n_list = a.ctl->bins_big, first = a.ctl->bins_warp + a.ctl->bins_mid;
     for (uint32_t x = blockIdx.x; x < n_list; x += gridDim.x) {
         const uint32_t bin = a.bin_list[first + x];
@@ -1908,7 +2056,8 @@ __global__ void __launch_bounds__(256, 6) k_bin_insert(BatchArgs a) {
                             s_idx[y] = iv;
                         }
                     }
-                    insert_staged_cell(a, cb, c0 + k, s_idx, s_h2, s_tgt, s_src, x0, n, ne, &n_ins, &n_dup, &n_full);
+                    insert_staged_cell(a, cb, c0 + k, s_idx, s_h2, s_tgt, s_src, x0, n, ne, &n_ins, &n_dup, &n_full,
+                                       &n_rep);
                 }
                 __syncthreads();
             } else {
@@ -1934,7 +2083,7 @@ __global__ void __launch_bounds__(256, 6) k_bin_insert(BatchArgs a) {
                         }
                         __syncthreads();
                     }
-                    if (t == 0 && s_best[0] != ~0ull) insert_one(a, cb[s_bidx[0]], ne, &n_ins, &n_dup, &n_full);
+                    if (t == 0 && s_best[0] != ~0ull) insert_one(a, cb[s_bidx[0]], ne, &n_ins, &n_dup, &n_full, &n_rep);
                     last = s_best[0];
                     __syncthreads();
                 }
@@ -1945,6 +2094,7 @@ __global__ void __launch_bounds__(256, 6) k_bin_insert(BatchArgs a) {
     warp_add_u64(&a.stats[ST_DUP], n_dup);
     warp_add_u64(&a.stats[ST_FULL], n_full);
     warp_add_u64(&a.stats[ST_INSERTED], n_ins);
+    warp_add_u64(&a.stats[ST_REPLACED], n_rep);
 }
 
 __global__ void k_finish(BatchArgs a) {

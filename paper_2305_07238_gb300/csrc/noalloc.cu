@@ -156,6 +156,10 @@ extern "C" pmc_status pmc_eval_batch_noalloc(pmc_cache* c, const pmc_points* pts
     a.unsorted = c->unsorted;
     a.probe_inline = c->probe_inline;
     a.lookup_rb = c->lookup_rb;
+    if (c->use_cache && (c->desc.flags & PMC_REPLACE_VISIBILITY)) {
+        a.slot_cls = c->d_cls;
+        a.vis = pts->vis;
+    }
     // launch_batch clears the counters and offsets that must start at zero; every other
     // region is written before it is read within the pass.
     cudaError_t e = launch_batch(a, s, c->num_sms, nullptr, &c->launches);

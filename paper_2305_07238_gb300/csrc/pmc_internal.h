@@ -87,7 +87,10 @@ struct __align__(16) Candidate {
     uint32_t cell;
     uint32_t h2;
     float r, g, b;
-    uint32_t target;          // slot index chosen in the current round
+    uint32_t target;          // bits 0-7: first slot that can hold the key (the first empty
+                              // slot at lookup; a round's choice in the claim-round insert);
+                              // 8-15: the point's visibility class (replacement policy);
+                              // 16-31: copies of the key merged into this candidate
 };
 static_assert(sizeof(Candidate) == 32, "candidate is one 32-byte sector");
 
@@ -129,7 +132,8 @@ constexpr uint32_t ERR_CAPACITY = 16;   // the batch needs more probe records th
 // Counter indices in the device stats array.
 enum {
     ST_LOOKUPS = 0, ST_HITS, ST_MISSES, ST_CANDIDATES, ST_INSERTED, ST_DUP, ST_FULL,
-    ST_NODES, ST_BATCHES, ST_FLOPS, ST_SLOTS, ST_POINTS, ST_BAD, ST_SURR, ST_FLOPS_MISSED, ST_RACE, ST_COUNT = 16
+    ST_NODES, ST_BATCHES, ST_FLOPS, ST_SLOTS, ST_POINTS, ST_BAD, ST_SURR, ST_FLOPS_MISSED, ST_RACE, ST_REPLACED,
+    ST_COUNT = 17
 };
 
 // Everything a batch's kernels need, by value.
@@ -193,6 +197,10 @@ struct BatchArgs {
     uint32_t lookup_rb;        // k_lookup: probes in flight per lane (1, 2 or 4)
     int alg1;                  // the paper's concurrent update: 8-byte slots {hash2, RGB9E5},
                                // looked up and inserted inside the evaluator (one 64-bit CAS)
+    // replacement by visibility class (Sec. 5): per point its class (caller-owned, optional,
+    // original order), per slot the class of its entry; slot_cls == nullptr = keep-first
+    const uint8_t* vis;
+    uint8_t* slot_cls;
 };
 
 constexpr uint32_t INSERT_BIN_CELLS = 256;

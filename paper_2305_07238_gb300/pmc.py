@@ -25,6 +25,7 @@ PMC_INSERT_ROUNDS = 0x10
 PMC_UNSORTED = 0x20
 PMC_PROBE_INLINE = 0x40
 PMC_ALG1 = 0x80
+PMC_REPLACE_VISIBILITY = 0x100
 PMC_GRAPH_RESET = 0x1
 TUNE_MAX = 16
 
@@ -35,7 +36,7 @@ EXPORTED = (
     "pmc_read_timing", "pmc_eval_batch_noalloc", "pmc_train_surrogates", "pmc_set_surrogate",
     "pmc_get_surrogate", "pmc_use_surrogates", "pmc_mlp_forward", "pmc_mlp_gradient", "pmc_mlp_train",
     "pmc_get_schedule", "pmc_set_schedule", "pmc_graph_create", "pmc_graph_launch", "pmc_graph_destroy",
-    "pmc_autotune", "pmc_status_str",
+    "pmc_autotune", "pmc_status_str", "pmc_slot_classes",
 )
 NOALLOC_MAX_POINTS, NOALLOC_MAX_PROBES, NOALLOC_MAX_MATERIALS = 8192, 32768, 4096
 PHASES = ("sort", "lookup", "missed", "eval", "insert", "finish")
@@ -72,12 +73,12 @@ class _TuneResult(C.Structure):
 
 class _Points(C.Structure):
     _fields_ = [(k, C.c_void_p) for k in POINT_FIELDS] + [("n", C.c_uint64)] + \
-        [(k, C.c_void_p) for k in CONE_FIELDS]
+        [(k, C.c_void_p) for k in CONE_FIELDS] + [("vis", C.c_void_p)]
 
 
 STAT_FIELDS = ("lookups", "hits", "misses", "candidates", "inserted", "dropped_dup", "dropped_full",
                "nodes_evaluated", "batches", "flops", "slots_probed", "points", "bad_points",
-               "surrogate_evals", "flops_missed", "dropped_race")
+               "surrogate_evals", "flops_missed", "dropped_race", "replaced")
 MLP_PARAMS = 8515
 
 
@@ -116,6 +117,8 @@ def load():
     L.pmc_stats.restype = st
     L.pmc_table_dump.argtypes = [vp, vp, C.c_size_t]
     L.pmc_table_dump.restype = st
+    L.pmc_slot_classes.argtypes = [vp, vp, C.c_size_t]
+    L.pmc_slot_classes.restype = st
     L.pmc_last_hit_masks.argtypes = [vp, vp, u64]
     L.pmc_last_hit_masks.restype = st
     L.pmc_reset.argtypes = [vp, vp]
@@ -201,18 +204,21 @@ def _points(pts, n, ptr):
     """The pmc_points struct of a point dict; ptr maps an array to its address.  The
     gradients present are passed as they are (the library rejects a partial set)."""
     cones = [ptr(pts[k]) if pts.get(k) is not None else None for k in CONE_FIELDS]
-    return _Points(*[ptr(pts[k]) for k in POINT_FIELDS], n, *cones)
+    vis = ptr(pts["vis"]) if pts.get("vis") is not None else None
+    return _Points(*[ptr(pts[k]) for k in POINT_FIELDS], n, *cones, vis)
 
 
 def points_to_device(pts: dict, device="cuda"):
-    """Copies a host point batch (numpy SoA, with or without the ray-cone gradients)
-    into torch device tensors."""
+    """Copies a host point batch (numpy SoA, with or without the ray-cone gradients and
+    the visibility classes "vis") into torch device tensors."""
     import torch
     out = {}
     for k in POINT_FIELDS + (CONE_FIELDS if _has_cones(pts) else ()):
         a = np.ascontiguousarray(pts[k])
         t = torch.from_numpy(a.view(np.int32) if k == "mat" else a)
         out[k] = t.to(device)
+    if pts.get("vis") is not None:
+        out["vis"] = torch.from_numpy(np.ascontiguousarray(pts["vis"], dtype=np.uint8)).to(device)
     return out
 
 
@@ -272,6 +278,8 @@ class Cache:
                         stream=None):
         """Host buffers in and out; returns once the results are in out_rgb/out_hits."""
         keep = {k: np.ascontiguousarray(pts[k]) for k in POINT_FIELDS + (CONE_FIELDS if _has_cones(pts) else ())}
+        if pts.get("vis") is not None:
+            keep["vis"] = np.ascontiguousarray(pts["vis"], dtype=np.uint8)
         n = len(keep["u"])
         p = _points(keep, n, lambda a: a.ctypes.data)
         _check(load().pmc_eval_batch_host(self._h, C.byref(p), out_rgb.ctypes.data,
@@ -324,6 +332,14 @@ class Cache:
         _check(load().pmc_table_dump(self._h, buf.ctypes.data, buf.nbytes), "pmc_table_dump")
         buf = buf[:slots]
         return buf[:, 0].copy(), buf[:, 1:].view(np.float32).copy()
+
+    def classes(self) -> np.ndarray:
+        """Visibility class of every slot's entry (uint8[slots]; 0 for an empty slot), for a
+        cache created with PMC_REPLACE_VISIBILITY."""
+        slots = self.n_cells * self.n_entries
+        buf = np.zeros(max(slots, 1), dtype=np.uint8)
+        _check(load().pmc_slot_classes(self._h, buf.ctypes.data, buf.nbytes), "pmc_slot_classes")
+        return buf[:slots].copy()
 
     def last_hit_masks(self, n: int) -> np.ndarray:
         out = np.zeros(max(n, 1), dtype=np.uint64)

@@ -141,7 +141,8 @@ def _pack(u, v, mat, p, nrm) -> dict:
 
 
 def _fields(pts: dict):
-    return POINT_FIELDS + (CONE_FIELDS if all(k in pts for k in CONE_FIELDS) else ())
+    return POINT_FIELDS + (CONE_FIELDS if all(k in pts for k in CONE_FIELDS) else ()) + \
+        (("vis",) if "vis" in pts else ())
 
 
 def slice_points(pts: dict, lo: int, hi: int) -> dict:
@@ -447,6 +448,36 @@ class Frame:
             c, s_, b = L["cos"][sel], L["sin"][sel], L["aniso"][sel]
             out.update(g1u=(f * c).astype(np.float32), g1v=(f * s_).astype(np.float32),
                        g2u=(-f * b * s_).astype(np.float32), g2v=(f * b * c).astype(np.float32))
+        return out
+
+    def points_paths(self, pass_index: int, bounce_frac=(0.5, 0.25), rows: tuple | None = None) -> dict:
+        """One pass of a path tracer as one batch: the directly visible sample of every
+        pixel (points() of the pass, visibility class 0), then for bounce k = 1, 2, ... the
+        shading points of the paths still alive, a fraction bounce_frac[k-1] of the pixels.
+        An indirect ray lands anywhere: each such point lies on the surface seen by a
+        pixel drawn uniformly from the frame (or from the band `rows`), with fresh jitter,
+        and carries class k in "vis"."""
+        spec = self.spec
+        direct = self.points(pass_index, rows=rows)
+        n0 = len(direct["u"])
+        lo = rows[0] * spec.width if rows is not None else 0
+        parts, vis = [direct], [np.zeros(n0, dtype=np.uint8)]
+        L = self._pixel_layout()
+        rng = np.random.Generator(np.random.PCG64([spec.seed, 7, pass_index]))
+        for k, frac in enumerate(bounce_frac, start=1):
+            m = int(round(frac * n0))
+            pix = lo + rng.integers(0, n0, m)
+            jx, jy = rng.random(m), rng.random(m)
+            d = L["d"][pix]
+            u = np.mod(L["ou"][pix] + d * (L["bx"][pix] + jx), 1.0)
+            v = np.mod(L["ov"][pix] + d * (L["by"][pix] + jy), 1.0)
+            wx = 0.01 * (L["fx"][pix] + jx)
+            wy = 0.01 * (L["fy"][pix] + jy)
+            pos = [(L["c"][q][pix] + wx * L["e1"][q][pix] + wy * L["e2"][q][pix]) * 0.25 for q in range(3)]
+            parts.append(_pack(u, v, L["mat"][pix], pos, [L["n"][q][pix] for q in range(3)]))
+            vis.append(np.full(m, k, dtype=np.uint8))
+        out = {f: np.concatenate([p[f] for p in parts]) for f in POINT_FIELDS}
+        out["vis"] = np.concatenate(vis)
         return out
 
     def points_torch(self, pass_index: int, device="cuda", rows: tuple | None = None) -> dict:

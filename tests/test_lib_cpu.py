@@ -99,3 +99,11 @@ def test_generated_programs_are_small(lib):
     mats = W.random_materials(64, 20, 200, 0.2, seed=0)
     slots = [P.analyze_material(m)["n_slots"] for m in mats]
     assert max(slots) <= 64
+
+
+def test_replacement_rejects_concurrent_and_round_inserts(lib):
+    # checked before any device work: the replacement policy needs the per-cell insert
+    for extra in (P.PMC_ALG1, P.PMC_INSERT_ROUNDS):
+        with pytest.raises(P.PmcError) as ei:
+            P.Cache([W.material_tiny()], 64, 4, flags=P.PMC_REPLACE_VISIBILITY | extra)
+        assert ei.value.status == P.PMC_ERR_INVALID_ARG
