@@ -60,6 +60,14 @@ def lib():
         L.orc_validate.argtypes = [vp, u32]
         L.orc_analyze.restype = C.c_int
         L.orc_analyze.argtypes = [vp, u32, u32, vp, vp, vp]
+        L.orc_analyze_desc.restype = C.c_int
+        L.orc_analyze_desc.argtypes = [vp, u32, u32, C.c_int, vp, vp, vp]
+        L.orc_voxel.restype = u32
+        L.orc_voxel.argtypes = [C.c_float, u32]
+        L.orc_key_pos.restype = u64
+        L.orc_key_pos.argtypes = [u32, u32, u32, C.c_float, C.c_float, C.c_float]
+        L.orc_cache_set_position_level.restype = None
+        L.orc_cache_set_position_level.argtypes = [vp, C.c_int32]
         L.orc_eval_point_nocache.restype = C.c_int
         L.orc_eval_point_nocache.argtypes = [vp, u32, vp, vp]
         L.orc_cache_new.restype = vp
@@ -124,6 +132,8 @@ def fbm(x, y, scale, octaves, lac, gain, seed): return lib().orc_fbm(x, y, scale
 def voronoi_f1(x, y, seed): return lib().orc_voronoi_f1(x, y, seed)
 def texel(u, level): return lib().orc_texel(u, level)
 def key(mat, node, level, u, v): return lib().orc_key(mat, node, level, u, v)
+def voxel(p, level): return lib().orc_voxel(p, level)
+def key_pos(mat, node, level, px, py, pz): return lib().orc_key_pos(mat, node, level, px, py, pz)
 def level(g1u, g1v, g2u, g2v, offset=0): return lib().orc_level(g1u, g1v, g2u, g2v, offset)
 def rgb9e5_encode(r, g, b): return lib().orc_rgb9e5_encode(r, g, b)
 
@@ -153,17 +163,19 @@ def validate(nodes) -> bool:
     return lib().orc_validate(_ptr(arr), len(arr)) == 0
 
 
-def analyze(nodes, min_root_nodes=2):
-    """Returns (classes int32[n], root node IDs)."""
+def analyze(nodes, min_root_nodes=2, pos_desc=False, kinds=False):
+    """Returns (classes int32[n], root node IDs) and, if kinds, the descriptor kind of each
+    root (1 = UV, 2 = world position)."""
     arr = _nodes(nodes)
     n = len(arr)
     cls = np.zeros(n, dtype=np.int32)
     is_root = np.zeros(n, dtype=np.uint8)
     nr = np.zeros(1, dtype=np.uint32)
-    rc = lib().orc_analyze(_ptr(arr), n, min_root_nodes, _ptr(cls), _ptr(is_root), _ptr(nr))
+    rc = lib().orc_analyze_desc(_ptr(arr), n, min_root_nodes, int(pos_desc), _ptr(cls), _ptr(is_root), _ptr(nr))
     if rc != 0:
         raise ValueError("malformed network")
-    return cls, np.nonzero(is_root)[0].astype(np.uint32)
+    roots = np.nonzero(is_root)[0].astype(np.uint32)
+    return (cls, roots, is_root[roots]) if kinds else (cls, roots)
 
 
 def eval_point_nocache(nodes, sp) -> np.ndarray:
@@ -192,13 +204,15 @@ class Cache:
     """Sequential emulation of the progressive cache over a set of materials."""
 
     def __init__(self, materials, n_cells, n_entries, level=10, min_root_nodes=2,
-                 cache_off=False, hash_hook=None, level_offset=0, alg1=False, replacement=False):
+                 cache_off=False, hash_hook=None, level_offset=0, alg1=False, replacement=False,
+                 pos_level=-1):
         self._mats = [_nodes(m) for m in materials]
         self.n_cells, self.n_entries, self.level = n_cells, n_entries, level
         self.off = bool(cache_off) or n_cells == 0 or n_entries == 0
         self._h = lib().orc_cache_new(n_cells, n_entries, level, min_root_nodes, int(cache_off))
         if not self._h:
             raise ValueError("bad cache description")
+        lib().orc_cache_set_position_level(self._h, int(pos_level))
         ptrs = (C.c_void_p * len(self._mats))(*[m.ctypes.data for m in self._mats])
         counts = np.array([len(m) for m in self._mats], dtype=np.uint32)
         if lib().orc_cache_set_materials(self._h, len(self._mats), ptrs, _ptr(counts)) != 0:

@@ -303,6 +303,25 @@ uint64_t orc_key(uint32_t mat, uint32_t node, uint32_t level, float u, float v) 
            (iu << 13) | iv;
 }
 
+/* Voxel index of one coordinate on a grid of 2^-level world units: floor(p 2^level)
+ * clamped to [-512, 511], offset to [0, 1023].  p 2^level is exact in FP32 (a power of two
+ * scale); NaN takes the lowest voxel. */
+uint32_t orc_voxel(float p, uint32_t level) {
+    float x = p * ldexpf(1.0f, (int)level);
+    if (!(x >= -512.0f)) x = -512.0f;
+    if (x > 511.0f) x = 511.0f;
+    return (uint32_t)((int32_t)floorf(x) + 512);
+}
+
+/* World-position descriptor (the extension Sec. 3.1 and Sec. 5 suggest): material ID,
+ * node ID and the voxel of the shading point's position, packed as
+ * mat<<48 | node<<32 | 1<<31 | ix<<20 | iy<<10 | iz (bit 31 tells it from a UV key). */
+uint64_t orc_key_pos(uint32_t mat, uint32_t node, uint32_t level, float px, float py, float pz) {
+    return ((uint64_t)mat << 48) | ((uint64_t)node << 32) | (1ull << 31) |
+           ((uint64_t)orc_voxel(px, level) << 20) | ((uint64_t)orc_voxel(py, level) << 10) |
+           (uint64_t)orc_voxel(pz, level);
+}
+
 /* Hash of Alg. 1 (cell selection): SplitMix64 output function of the key. */
 uint64_t orc_hash1(uint64_t key) { return orc_splitmix64_mix(key); }
 
@@ -380,26 +399,38 @@ static void mark_subgraph(const orc_node* nodes, uint32_t r, uint8_t* mark) {
     }
 }
 
+/* Class of a node whose inputs have classes a and b: constants change nothing, two
+ * different shading-point dependences (UV with position, or anything with SP) make it
+ * SP (no descriptor of one kind identifies it). */
+static int join_class(int a, int b) {
+    if (a == b || b == ORC_CLS_CONST) return a;
+    if (a == ORC_CLS_CONST) return b;
+    return ORC_CLS_SP;
+}
+
 /* Dependence classes and cacheable roots.
- *   class(UV input) = UV; class(position, normal) = SP; class(const) = CONST;
- *   any other node takes the highest class of its inputs (CONST < UV < SP).
+ *   class(UV input) = UV; class(normal) = SP; class(const) = CONST;
+ *   class(position) = POS with the world-position descriptor, else SP;
+ *   any other node joins the classes of its inputs (join_class).
  * A node is a cacheable root when it is reachable from the output, has class
- * UV, is not the bare UV input, is the output or feeds some SP-class node
+ * UV (or POS), is not a bare input, is the output or feeds some SP-class node
  * ("the highest possible level", Sec. 3), and its sub-graph holds at least
- * min_root_nodes nodes that are not inputs or constants. */
-int orc_analyze(const orc_node* nodes, uint32_t n, uint32_t min_root_nodes,
-                int32_t* cls, uint8_t* is_root, uint32_t* n_roots) {
+ * min_root_nodes nodes that are not inputs or constants.  is_root[i] = 1 for a
+ * root with a UV descriptor, 2 for one with a world-position descriptor. */
+int orc_analyze_desc(const orc_node* nodes, uint32_t n, uint32_t min_root_nodes, int pos_desc,
+                     int32_t* cls, uint8_t* is_root, uint32_t* n_roots) {
     if (orc_validate(nodes, n) != ORC_OK) return ORC_ERR_ARG;
     for (uint32_t i = 0; i < n; ++i) {
         const orc_node* nd = &nodes[i];
         int c;
         if (nd->op == ORC_UV) c = ORC_CLS_UV;
-        else if (nd->op == ORC_POSITION || nd->op == ORC_NORMAL) c = ORC_CLS_SP;
+        else if (nd->op == ORC_POSITION) c = pos_desc ? ORC_CLS_POS : ORC_CLS_SP;
+        else if (nd->op == ORC_NORMAL) c = ORC_CLS_SP;
         else if (nd->op == ORC_CONST) c = ORC_CLS_CONST;
         else {
             c = ORC_CLS_CONST;
             for (int k = 0; k < 4; ++k)
-                if (nd->in[k] >= 0 && cls[nd->in[k]] > c) c = cls[nd->in[k]];
+                if (nd->in[k] >= 0) c = join_class(c, cls[nd->in[k]]);
         }
         cls[i] = c;
     }
@@ -415,7 +446,8 @@ int orc_analyze(const orc_node* nodes, uint32_t n, uint32_t min_root_nodes,
     uint32_t nr = 0;
     for (uint32_t i = 0; i < n; ++i) {
         is_root[i] = 0;
-        if (!reach[i] || cls[i] != ORC_CLS_UV || nodes[i].op == ORC_UV) continue;
+        if (!reach[i] || (cls[i] != ORC_CLS_UV && cls[i] != ORC_CLS_POS)) continue;
+        if (nodes[i].op == ORC_UV || nodes[i].op == ORC_POSITION) continue;
         if (!(i == n - 1 || feeds_sp[i])) continue;
         memset(mark, 0, n);
         mark_subgraph(nodes, i, mark);
@@ -423,7 +455,7 @@ int orc_analyze(const orc_node* nodes, uint32_t n, uint32_t min_root_nodes,
         for (uint32_t j = 0; j <= i; ++j)
             if (mark[j] && !is_input_op(nodes[j].op)) ++work;
         if (work < min_root_nodes) continue;
-        is_root[i] = 1;
+        is_root[i] = cls[i] == ORC_CLS_POS ? 2 : 1;
         ++nr;
     }
     *n_roots = nr;
@@ -431,6 +463,11 @@ int orc_analyze(const orc_node* nodes, uint32_t n, uint32_t min_root_nodes,
     free(feeds_sp);
     free(mark);
     return ORC_OK;
+}
+
+int orc_analyze(const orc_node* nodes, uint32_t n, uint32_t min_root_nodes,
+                int32_t* cls, uint8_t* is_root, uint32_t* n_roots) {
+    return orc_analyze_desc(nodes, n, min_root_nodes, 0, cls, is_root, n_roots);
 }
 
 static const double* input_value(const orc_node* nd, int k, const double* val) {
@@ -476,6 +513,7 @@ struct orc_cache {
     int32_t level_offset;  /* added to the ray-cone level (Sec. 4) */
     int alg1;              /* the paper's concurrent update, serialised point by point */
     int replace;           /* replacement by visibility class (Sec. 5), else keep-first */
+    int32_t pos_level;     /* world-position descriptor: voxels of 2^-pos_level; -1 = off */
     uint32_t min_root_nodes;
     int off;
     uint32_t* h2;  /* n_cells * n_entries, 0 = empty */
@@ -500,6 +538,7 @@ orc_cache* orc_cache_new(uint64_t n_cells, uint32_t n_entries, uint32_t level,
     c->h2 = (uint32_t*)calloc(slots ? slots : 1, sizeof(uint32_t));
     c->rgb = (float*)calloc(slots ? 3 * slots : 1, sizeof(float));
     c->cls = (uint8_t*)calloc(slots ? slots : 1, 1);
+    c->pos_level = -1;
     return c;
 }
 
@@ -542,7 +581,7 @@ int orc_cache_set_materials(orc_cache* c, uint32_t n_mats, const orc_node* const
         memcpy(M->nodes, mat_nodes[m], n * sizeof(orc_node));
         M->is_root = (uint8_t*)calloc(n, 1);
         int32_t* cls = (int32_t*)malloc(n * sizeof(int32_t));
-        orc_analyze(M->nodes, n, c->min_root_nodes, cls, M->is_root, &M->n_roots);
+        orc_analyze_desc(M->nodes, n, c->min_root_nodes, c->pos_level >= 0, cls, M->is_root, &M->n_roots);
         free(cls);
         M->roots = (uint32_t*)malloc((M->n_roots ? M->n_roots : 1) * sizeof(uint32_t));
         uint32_t r = 0;
@@ -559,6 +598,8 @@ void orc_cache_set_level_offset(orc_cache* c, int32_t offset) { c->level_offset 
 void orc_cache_set_alg1(orc_cache* c, int on) { c->alg1 = on != 0; }
 
 void orc_cache_set_replacement(orc_cache* c, int on) { c->replace = on != 0; }
+
+void orc_cache_set_position_level(orc_cache* c, int32_t level) { c->pos_level = level; }
 
 void orc_cache_reset(orc_cache* c) {
     size_t slots = c->off ? 0 : (size_t)c->n_cells * c->n_entries;
@@ -770,7 +811,9 @@ int orc_run_batch(orc_cache* c, uint64_t n, const float* u, const float* v,
                 for (int k = 0; k < 3; ++k) hitval[3 * node + k] = clamp01(y[k]);
             }
             if (c->off) continue;
-            uint64_t key = orc_key(mat[i], node, level, u[i], v[i]);
+            uint64_t key = M->is_root[node] == 2
+                               ? orc_key_pos(mat[i], node, (uint32_t)c->pos_level, px[i], py[i], pz[i])
+                               : orc_key(mat[i], node, level, u[i], v[i]);
             uint64_t cell, slot;
             uint32_t h2;
             cell_and_check(c, key, &cell, &h2);

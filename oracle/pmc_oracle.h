@@ -69,8 +69,9 @@ enum {
     ORC_NUM_OPS = 14
 };
 
-/* Dependence classes (Sec. 3): CONST < UV < SP. */
-enum { ORC_CLS_CONST = 0, ORC_CLS_UV = 1, ORC_CLS_SP = 2 };
+/* Dependence classes (Sec. 3): CONST < UV < SP; POS (position only) exists only with the
+ * world-position descriptor. */
+enum { ORC_CLS_CONST = 0, ORC_CLS_UV = 1, ORC_CLS_SP = 2, ORC_CLS_POS = 3 };
 
 /* Status codes. */
 enum {
@@ -105,6 +106,10 @@ int32_t orc_level(float g1u, float g1v, float g2u, float g2v, int32_t offset);
 uint32_t orc_rgb9e5_encode(float r, float g, float b);
 void orc_rgb9e5_decode(uint32_t code, float out[3]);
 uint64_t orc_key(uint32_t mat, uint32_t node, uint32_t level, float u, float v);
+/* World-position descriptor: voxel index floor(p 2^level) clamped to [-512, 511] + 512
+ * per axis (NaN -> 0), key = mat<<48 | node<<32 | 1<<31 | ix<<20 | iy<<10 | iz. */
+uint32_t orc_voxel(float p, uint32_t level);
+uint64_t orc_key_pos(uint32_t mat, uint32_t node, uint32_t level, float px, float py, float pz);
 uint64_t orc_hash1(uint64_t key);
 uint32_t orc_hash2(uint64_t key);
 
@@ -114,6 +119,10 @@ uint32_t orc_hash2(uint64_t key);
 int orc_validate(const orc_node* nodes, uint32_t n);
 int orc_analyze(const orc_node* nodes, uint32_t n, uint32_t min_root_nodes,
                 int32_t* cls, uint8_t* is_root, uint32_t* n_roots);
+/* The same with the world-position descriptor if pos_desc != 0: nodes that depend on the
+ * position and on nothing else of the shading point are cacheable too (is_root 2). */
+int orc_analyze_desc(const orc_node* nodes, uint32_t n, uint32_t min_root_nodes, int pos_desc,
+                     int32_t* cls, uint8_t* is_root, uint32_t* n_roots);
 
 /* ---- single shading point, no cache -------------------------------------- */
 /* Plain evaluation of every node reachable from the output. */
@@ -150,6 +159,12 @@ void orc_cache_set_alg1(orc_cache* c, int on);
  * otherwise the value is dropped as with keep-first.  Lookups do not change classes.
  * With every class 0 the table evolves exactly as with keep-first. */
 void orc_cache_set_replacement(orc_cache* c, int on);
+/* level >= 0: the world-position descriptor (Sec. 3.1 names world-space position as a
+ * further descriptor, Sec. 5 lists it as future work).  A node whose sub-graph depends on
+ * the shading point's position and on nothing else of it is cacheable too; its key is
+ * orc_key_pos at this level (voxels of 2^-level world units).  Must be called before
+ * orc_cache_set_materials.  Default -1 (off). */
+void orc_cache_set_position_level(orc_cache* c, int32_t level);
 void orc_cache_reset(orc_cache* c);
 uint32_t orc_cache_n_roots(const orc_cache* c, uint32_t mat);
 /* Root node IDs of a material in ascending order (n_roots entries). */
