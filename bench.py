@@ -42,7 +42,7 @@ SAMPLE_ROWS = (0, 40)            # CPU-oracle sample: 40 full-width rows, all 16
 REF_ROWS = (0, 16)               # reference arm: 16 full-width rows per step, all 16 passes
 # ncu capture of k_eval / k_lookup on the same workload (profiles/): DRAM bytes per launch
 # (profiles/launches_frame1080p.md: mean over the launches of one frame of each kernel)
-NCU_TRAFFIC = {"eval": 309.9e6, "eval_roots": 179.8e6, "lookup": 1046.9e6}
+NCU_TRAFFIC = {"eval": 313.0e6, "eval_roots": 182.1e6, "lookup": 1047.7e6}
 
 FP32_LANES_PER_SM = 128          # Blackwell SM: 4 partitions x 32 FP32 lanes
 N_SMS = 152
@@ -333,6 +333,8 @@ def ours(args, rank, world, local_rank, dist):
             for off in (0, -1):
                 r = line["ray_cones"][f"offset{off}"]
                 r["speedup_cached_over_uncached"] = round(r["cached"] / u_value, 3)
+    if "position" in legs:
+        line["position_descriptor"] = position_leg(torch, P, mats, dev_passes, outs, hits, local_rank)
     if "replace" in legs:
         line["replacement"] = replace_leg(torch, P, dev, local_rank, seed=rank)
     if "sweep" in legs:
@@ -457,6 +459,52 @@ def alg1_leg(torch, P, mats, dev_passes, outs, hits, local_rank):
             "schedule": tune["schedule"],
             "hit_rate": round(st["hits"] / max(1, st["lookups"]), 4),
             "table": {k: st[k] for k in ("inserted", "dropped_dup", "dropped_full", "dropped_race")}}
+
+
+POS_LEVEL = 6   # world-position voxels of 1/64 unit: about 6 pixels of the frame per voxel edge
+
+
+def position_leg(torch, P, mats, dev_passes, outs, hits, local_rank):
+    """The benchmark frame with the world-position descriptor (Sec. 3.1 and Sec. 5): the
+    networks' position noise (single FBM, Worley or checker nodes of the position) becomes
+    cacheable under voxels of 2^-6 units.  Those are single nodes, so both cached runs take
+    min_root_nodes = 1: UV descriptors only, UV and position descriptors, and uncached;
+    the whole frame as one CUDA graph with the autotuned schedule."""
+    n = WIDTH * HEIGHT
+    res = {"config": f"frame 1920x1080x16spp, {N_MATS} materials, table {N_CELLS}x{N_ENTRIES} slots, "
+                     f"min_root_nodes 1, position voxels of 2^-{POS_LEVEL}", "unit": UNIT}
+    runs = (("uv_only", 0), ("uv_and_position", P.PMC_POSITION_DESCRIPTOR), ("uncached", P.PMC_CACHE_OFF))
+    for name, flags in runs:
+        c = P.Cache(mats, N_CELLS, N_ENTRIES, uv_level=LEVEL, flags=flags, min_root_nodes=1, pos_level=POS_LEVEL,
+                    device=local_rank)
+        for p in range(2):
+            c.eval_batch(dev_passes[p], outs, hits)
+        c.autotune(dev_passes[2], reps=2)
+        c.reset()
+        for p in range(SPP):
+            c.eval_batch(dev_passes[p], outs, hits)
+        st = c.stats()
+        g = c.graph(dev_passes, [outs] * SPP, [hits] * SPP, reset=True)
+        g.launch()
+        torch.cuda.synchronize()
+        t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        t0.record()
+        for _ in range(3):
+            g.launch()
+        t1.record()
+        torch.cuda.synchronize()
+        g.close()
+        c.close()
+        r = {"points_per_s": round(3 * n * SPP / (t0.elapsed_time(t1) / 1e3), 1)}
+        if name != "uncached":
+            r.update(hit_rate=round(st["hits"] / max(1, st["lookups"]), 4),
+                     lookups_per_point=round(st["lookups"] / (n * SPP), 3), inserted=st["inserted"],
+                     dropped_full=st["dropped_full"])
+        res[name] = r
+    u = res["uncached"]["points_per_s"]
+    res["speedup_uv_only_over_uncached"] = round(res["uv_only"]["points_per_s"] / u, 3)
+    res["speedup_uv_and_position_over_uncached"] = round(res["uv_and_position"]["points_per_s"] / u, 3)
+    return res
 
 
 REPL_PASSES, REPL_BOUNCES = 8, (0.5, 0.25)
@@ -879,8 +927,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--legs", default="cached,uncached,e2e,surr,f128,alg1,cones,replace,cpu",
-                    help="comma list of cached, uncached, e2e, surr, f128, alg1, cones, replace, sweep, cpu (sweep is not in the "
+    ap.add_argument("--legs", default="cached,uncached,e2e,surr,f128,alg1,cones,position,replace,cpu",
+                    help="comma list of cached, uncached, e2e, surr, f128, alg1, cones, position, replace, sweep, cpu "
+                         "(sweep is not in the "
                          "default: about a minute more; profiling runs take 'cached')")
     ap.add_argument("--profile", action="store_true",
                     help="eager frames only, for ncu launch lists (prints launches per frame)")

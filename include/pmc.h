@@ -161,6 +161,21 @@ typedef struct {
                                      with keep-first.  The table is still deterministic.
                                      Not combinable with PMC_ALG1 or PMC_INSERT_ROUNDS
                                      (PMC_ERR_INVALID_ARG); one byte per slot more */
+#define PMC_POSITION_DESCRIPTOR 0x200u /* world-position descriptor (Sec. 3.1 names a
+                                     world-space position as a further descriptor; Sec. 5
+                                     lists other shading-point information than UV as
+                                     future work).  The position becomes a dependence
+                                     class of its own: a node whose sub-graph depends on
+                                     the position and on nothing else of the shading point
+                                     (no UV, no normal) is cacheable by the same rule as a
+                                     UV-only node, and is looked up under the descriptor
+                                     (material, node, voxel of the position at pos_level):
+                                     per axis floor(p 2^pos_level) clamped to [-512, 511]
+                                     and offset by 512 (NaN -> 0), key = mat<<48 |
+                                     node<<32 | 1<<31 | ix<<20 | iy<<10 | iz.  A node that
+                                     joins UV and position is not cacheable.  Learned
+                                     surrogates stay on UV-only nodes */
+#define PMC_MAX_POS_LEVEL 20u
 
 typedef struct {
     uint64_t n_cells;        /* N_c >= 1, < 2^32                                  */
@@ -178,6 +193,8 @@ typedef struct {
     int32_t level_offset;    /* -13 .. 13, added to the level of every point that
                                 carries ray-cone gradients (pmc_points g1u ..);
                                 positive values give finer texels (Sec. 4)      */
+    uint32_t pos_level;      /* PMC_POSITION_DESCRIPTOR: voxels of 2^-pos_level world
+                                units, 0 .. PMC_MAX_POS_LEVEL (else ignored)       */
 } pmc_cache_desc;
 
 /* ---- shading points: structure of arrays, n entries each, DEVICE memory ----- *
@@ -299,6 +316,13 @@ pmc_status pmc_material_info(const pmc_cache* cache, uint32_t mat, uint32_t* n_r
 pmc_status pmc_analyze_material(const pmc_material* mat, uint32_t min_root_nodes,
                                 uint32_t* n_roots, uint32_t* roots, uint32_t cap,
                                 uint32_t* n_instr, uint32_t* n_slots);
+
+/* The same with creation flags: PMC_POSITION_DESCRIPTOR adds the cacheable nodes of
+ * position class.  kinds (may be NULL): per cacheable node 1 = UV descriptor, 2 = world-
+ * position descriptor.  Needs no GPU. */
+pmc_status pmc_analyze_material_ext(const pmc_material* mat, uint32_t min_root_nodes, uint32_t flags,
+                                    uint32_t* n_roots, uint32_t* roots, uint8_t* kinds, uint32_t cap,
+                                    uint32_t* n_instr, uint32_t* n_slots);
 
 /* Descriptor and table addressing for n (material, node, u, v) tuples, all DEVICE
  * arrays: key = mat<<48 | node<<32 | level<<26 | iu<<13 | iv with

@@ -20,6 +20,7 @@ struct pmc_cache {
     int num_sms = 0;
     std::vector<MatInfo> mat_info;
     std::vector<uint32_t> roots;
+    std::vector<uint32_t> roots_dev;      // the device root table: node ID | ROOT_POS_BIT
     std::vector<pmc::RootInfo> root_info;
     uint32_t max_level = 0;
     int split = 1;

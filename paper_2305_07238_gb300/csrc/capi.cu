@@ -187,6 +187,8 @@ pmc_status pmc_create_cache(const pmc_cache_desc* desc, const pmc_material* mats
     // concurrent update, not the claim rounds
     if ((desc->flags & PMC_REPLACE_VISIBILITY) && (desc->flags & (PMC_ALG1 | PMC_INSERT_ROUNDS)))
         return PMC_ERR_INVALID_ARG;
+    if ((desc->flags & PMC_POSITION_DESCRIPTOR) && desc->pos_level > PMC_MAX_POS_LEVEL) return PMC_ERR_INVALID_ARG;
+    const bool pos_desc = (desc->flags & PMC_POSITION_DESCRIPTOR) != 0;
     if (!off) {
         if (desc->n_cells == 0 || desc->n_cells > 0xFFFFFFFFull) return PMC_ERR_INVALID_ARG;
         if (desc->n_entries == 0 || desc->n_entries > MAX_ENTRIES) return PMC_ERR_INVALID_ARG;
@@ -208,7 +210,7 @@ pmc_status pmc_create_cache(const pmc_cache_desc* desc, const pmc_material* mats
     for (uint32_t m = 0; m < n_mats; ++m) {
         CompiledMaterial cm;
         const char* why = "";
-        if (!mats[m].nodes || !compile_material(mats[m].nodes, mats[m].n_nodes, min_root, &cm, &why)) {
+        if (!mats[m].nodes || !compile_material(mats[m].nodes, mats[m].n_nodes, min_root, pos_desc, &cm, &why)) {
             fprintf(stderr, "pmc: material %u rejected: %s\n", m, why);
             delete c;
             return PMC_ERR_INVALID_ARG;
@@ -231,6 +233,7 @@ pmc_status pmc_create_cache(const pmc_cache_desc* desc, const pmc_material* mats
         uint64_t best_cost = 0;
         for (size_t r = 0; r < cm.roots.size(); ++r) {
             if (cm.root_level[r] != 0) continue;   // a surrogate replaces a whole sub-graph
+            if (cm.root_pos[r]) continue;           // ... of UV alone
             uint64_t cost = 0;
             for (uint4 ins : cm.root_progs[r]) cost += ins.x >> 16;
             if (cand < 0 || cost > best_cost) { cand = (int32_t)r; best_cost = cost; }
@@ -266,6 +269,8 @@ pmc_status pmc_create_cache(const pmc_cache_desc* desc, const pmc_material* mats
         }
         params.insert(params.end(), cm.params.begin(), cm.params.end());
         c->roots.insert(c->roots.end(), cm.roots.begin(), cm.roots.end());
+        for (size_t r = 0; r < cm.roots.size(); ++r)
+            c->roots_dev.push_back(cm.roots[r] | (cm.root_pos[r] ? ROOT_POS_BIT : 0u));
         c->mat_info.push_back(mi);
         c->max_roots = std::max(c->max_roots, mi.n_roots);
         c->max_slots = std::max(c->max_slots, mi.n_slots);
@@ -314,7 +319,8 @@ pmc_status pmc_create_cache(const pmc_cache_desc* desc, const pmc_material* mats
     if (e == cudaSuccess && !params.empty()) e = cudaMemcpy(c->d_params, params.data(), params.size() * sizeof(float), cudaMemcpyHostToDevice);
     if (e == cudaSuccess && !c->root_info.empty())
         e = cudaMemcpy(c->d_rinfo, c->root_info.data(), c->root_info.size() * sizeof(RootInfo), cudaMemcpyHostToDevice);
-    if (e == cudaSuccess && !c->roots.empty()) e = cudaMemcpy(c->d_roots, c->roots.data(), c->roots.size() * sizeof(uint32_t), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && !c->roots.empty())
+        e = cudaMemcpy(c->d_roots, c->roots_dev.data(), c->roots_dev.size() * sizeof(uint32_t), cudaMemcpyHostToDevice);
     c->surr_slot.assign(n_mats, -1);
     c->surr_on.assign(n_mats, 0);
     if (e == cudaSuccess) e = cudaMemset(c->d_surr_slot, 0xFF, n_mats * sizeof(int32_t));
@@ -371,6 +377,7 @@ pmc_status enqueue_batch(pmc_cache* c, const pmc_points* pts, float* out_rgb, ui
     a.n = (uint32_t)n;
     a.g1u = pts->g1u; a.g1v = pts->g1v; a.g2u = pts->g2u; a.g2v = pts->g2v;
     a.level_offset = c->desc.level_offset;
+    a.pos_level = (c->use_cache && (c->desc.flags & PMC_POSITION_DESCRIPTOR)) ? (int32_t)c->desc.pos_level : -1;
     a.out_rgb = out_rgb; a.out_hits = out_hits;
     a.mats = c->d_mats; a.n_mats = c->n_mats;
     a.prog = c->d_prog; a.params = c->d_params; a.roots = c->d_roots;
@@ -701,19 +708,28 @@ pmc_status pmc_material_info(const pmc_cache* c, uint32_t mat, uint32_t* n_roots
     return PMC_OK;
 }
 
-pmc_status pmc_analyze_material(const pmc_material* mat, uint32_t min_root_nodes, uint32_t* n_roots,
-                                uint32_t* roots, uint32_t cap, uint32_t* n_instr, uint32_t* n_slots) {
+pmc_status pmc_analyze_material_ext(const pmc_material* mat, uint32_t min_root_nodes, uint32_t flags,
+                                    uint32_t* n_roots, uint32_t* roots, uint8_t* kinds, uint32_t cap,
+                                    uint32_t* n_instr, uint32_t* n_slots) {
     if (!mat || !mat->nodes) return PMC_ERR_INVALID_ARG;
     CompiledMaterial cm;
     const char* why = "";
-    if (!compile_material(mat->nodes, mat->n_nodes, min_root_nodes ? min_root_nodes : 2u, &cm, &why))
+    if (!compile_material(mat->nodes, mat->n_nodes, min_root_nodes ? min_root_nodes : 2u,
+                          (flags & PMC_POSITION_DESCRIPTOR) != 0, &cm, &why))
         return PMC_ERR_INVALID_ARG;
     if (n_roots) *n_roots = (uint32_t)cm.roots.size();
-    if (roots)
-        for (size_t r = 0; r < cm.roots.size() && r < cap; ++r) roots[r] = cm.roots[r];
+    for (size_t r = 0; r < cm.roots.size() && r < cap; ++r) {
+        if (roots) roots[r] = cm.roots[r];
+        if (kinds) kinds[r] = cm.root_pos[r] ? 2 : 1;
+    }
     if (n_instr) *n_instr = (uint32_t)cm.prog.size();
     if (n_slots) *n_slots = cm.n_slots;
     return PMC_OK;
+}
+
+pmc_status pmc_analyze_material(const pmc_material* mat, uint32_t min_root_nodes, uint32_t* n_roots,
+                                uint32_t* roots, uint32_t cap, uint32_t* n_instr, uint32_t* n_slots) {
+    return pmc_analyze_material_ext(mat, min_root_nodes, 0u, n_roots, roots, nullptr, cap, n_instr, n_slots);
 }
 
 // ---- learned surrogates ------------------------------------------------------------

@@ -4,7 +4,10 @@
 //  2. dependence classes CONST < UV < SP and the cacheable nodes ("roots"): reachable
 //     UV-class nodes, other than the bare UV input, that are the output or feed an
 //     SP-class node, with at least min_root_nodes non-input nodes below them -- the
-//     highest level at which the sub-graph depends on nothing but UV (Sec. 3);
+//     highest level at which the sub-graph depends on nothing but UV (Sec. 3).  With the
+//     world-position descriptor the position is a class of its own (POS): a node joining
+//     UV and POS inputs is SP, and POS-class nodes become roots by the same rule, looked
+//     up under a voxel of the position instead of a texel;
 //  3. constant folding of simple arithmetic on constants (Sec. 2);
 //  4. for every other node, the set of roots through which all its uses pass: a node
 //     used only under root r is skipped whenever r hits; such nodes and r form r's block;
@@ -21,7 +24,15 @@
 namespace pmc {
 namespace {
 
-enum { CLS_CONST = 0, CLS_UV = 1, CLS_SP = 2 };
+enum { CLS_CONST = 0, CLS_UV = 1, CLS_SP = 2, CLS_POS = 3 };
+
+// Class of a node with inputs of classes a and b: constants change nothing; two different
+// shading-point dependences make it SP.
+int join_class(int a, int b) {
+    if (a == b || b == CLS_CONST) return a;
+    if (a == CLS_CONST) return b;
+    return CLS_SP;
+}
 constexpr uint32_t NO_SLOT = 0xFFFFu;
 
 int required_inputs(uint32_t op, int* optional) {
@@ -241,7 +252,7 @@ uint32_t node_cost(const pmc_node& nd) {
     }
 }
 
-bool compile_material(const pmc_node* nodes_in, uint32_t n, uint32_t min_root_nodes,
+bool compile_material(const pmc_node* nodes_in, uint32_t n, uint32_t min_root_nodes, bool pos_desc,
                       CompiledMaterial* out, const char** why) {
     if (!validate(nodes_in, n, why)) return false;
     std::vector<pmc_node> g(nodes_in, nodes_in + n);
@@ -258,12 +269,13 @@ bool compile_material(const pmc_node* nodes_in, uint32_t n, uint32_t min_root_no
     for (uint32_t i = 0; i < n; ++i) {
         uint32_t op = g[i].op;
         if (op == PMC_OP_UV) cls[i] = CLS_UV;
-        else if (op == PMC_OP_POSITION || op == PMC_OP_NORMAL) cls[i] = CLS_SP;
+        else if (op == PMC_OP_POSITION) cls[i] = pos_desc ? CLS_POS : CLS_SP;
+        else if (op == PMC_OP_NORMAL) cls[i] = CLS_SP;
         else if (op == PMC_OP_CONST) cls[i] = CLS_CONST;
         else {
             int c = CLS_CONST;
             for (int k = 0; k < 4; ++k)
-                if (g[i].in[k] >= 0) c = std::max(c, cls[g[i].in[k]]);
+                if (g[i].in[k] >= 0) c = join_class(c, cls[g[i].in[k]]);
             cls[i] = c;
         }
     }
@@ -277,7 +289,8 @@ bool compile_material(const pmc_node* nodes_in, uint32_t n, uint32_t min_root_no
     std::vector<char> is_root(n, 0);
     std::vector<char> mark(n);
     for (uint32_t i = 0; i < n; ++i) {
-        if (!reach[i] || cls[i] != CLS_UV || g[i].op == PMC_OP_UV) continue;
+        if (!reach[i] || (cls[i] != CLS_UV && cls[i] != CLS_POS)) continue;
+        if (g[i].op == PMC_OP_UV || g[i].op == PMC_OP_POSITION) continue;
         if (!(i == out_node || feeds_sp[i])) continue;
         std::fill(mark.begin(), mark.end(), 0);
         mark[i] = 1;
@@ -291,8 +304,12 @@ bool compile_material(const pmc_node* nodes_in, uint32_t n, uint32_t min_root_no
         if (work >= min_root_nodes) is_root[i] = 1;
     }
     out->roots.clear();
+    out->root_pos.clear();
     for (uint32_t i = 0; i < n; ++i)
-        if (is_root[i]) out->roots.push_back(i);
+        if (is_root[i]) {
+            out->roots.push_back(i);
+            out->root_pos.push_back(cls[i] == CLS_POS ? 1 : 0);
+        }
     std::vector<uint32_t> ordinal(n, 0);
     for (uint32_t r = 0; r < out->roots.size(); ++r) ordinal[out->roots[r]] = r;
 
@@ -449,7 +466,7 @@ bool compile_material(const pmc_node* nodes_in, uint32_t n, uint32_t min_root_no
             slot[x] = take();
             uint4 ins;
             uint32_t skip = (uint32_t)members[x].size();  // exclusive nodes + the root itself
-            ins.x = OP_ROOT_BEGIN;
+            ins.x = OP_ROOT_BEGIN | ((cls[x] == CLS_POS ? FLAG_POSROOT : 0u) << 8);
             ins.y = slot[x] | (ordinal[x] << 16);
             ins.z = x;
             ins.w = skip;

@@ -320,10 +320,16 @@ __global__ void __launch_bounds__(256) k_lookup(BatchArgs a) {
         const bool valid = j < cnt;
         const uint32_t s = __ldg(&a.seg_start[m]) + j;
         uint32_t iu = 0, iv = 0, lev = a.level;
+        float px = 0.f, py = 0.f, pz = 0.f;
         if (valid) {
             if (a.g1u) lev = a.slev[s];
             iu = d_texel(a.su[s], lev);
             iv = d_texel(a.sv[s], lev);
+            if (a.pos_level >= 0) {
+                px = a.spx[s];
+                py = a.spy[s];
+                pz = a.spz[s];
+            }
         }
         const MatInfo mi = a.mats[m];
         const int32_t surr = a.surr_ord ? a.surr_ord[m] : -1;   // a surrogate's node is not probed
@@ -340,7 +346,10 @@ __global__ void __launch_bounds__(256) k_lookup(BatchArgs a) {
                 h2[b] = 0;
                 if (act[b]) {
                     const uint32_t node = __ldg(&a.roots[mi.root_base + r0 + b]);
-                    d_address(d_key(m, node, lev, iu, iv), a.n_cells, a.cells_pow2_mask, &cell[b], &h2[b]);
+                    const uint64_t key = (node & ROOT_POS_BIT)
+                                             ? d_key_pos(m, node & 0xFFFFu, (uint32_t)a.pos_level, px, py, pz)
+                                             : d_key(m, node, lev, iu, iv);
+                    d_address(key, a.n_cells, a.cells_pow2_mask, &cell[b], &h2[b]);
                 }
                 const uint4* hw = reinterpret_cast<const uint4*>(cell_h2(a, cell[b]));
                 const bool ld = act[b] && !a.table_empty;   // an empty table misses at slot 0
@@ -548,7 +557,10 @@ __global__ void __launch_bounds__(EVAL_WARPS * 32) k_eval(BatchArgs a, uint32_t*
                     // empty table: every probe misses at slot 0, so the descriptor is all
                     // the insert needs (no lookup kernel, no probe record)
                     if (valid) {
-                        d_address(d_key(m, ins.z, lev, iu, iv), a.n_cells, a.cells_pow2_mask, &cand_cell, &cand_h2);
+                        const uint64_t key = ((ins.x >> 8) & FLAG_POSROOT)
+                                                 ? d_key_pos(m, ins.z, (uint32_t)a.pos_level, pt.px, pt.py, pt.pz)
+                                                 : d_key(m, ins.z, lev, iu, iv);
+                        d_address(key, a.n_cells, a.cells_pow2_mask, &cand_cell, &cand_h2);
                         cand_start = 0;
                         cand_full = false;
                         cand_node = ins.z;
@@ -834,7 +846,9 @@ __global__ void __launch_bounds__(EVAL_WARPS * 32) k_eval_fused(BatchArgs a, uin
                         need = false;
                     } else if (a.use_cache && mine && a.alg1) {
                         // the paper's scheme: the table as other warps are filling it
-                        d_address(d_key(mg, ins.z, lev, iu, iv), a.n_cells, a.cells_pow2_mask, &cand_cell, &cand_h2);
+                        d_address(((ins.x >> 8) & FLAG_POSROOT) ? d_key_pos(mg, ins.z, (uint32_t)a.pos_level, pt.px, pt.py, pt.pz)
+                                                                  : d_key(mg, ins.z, lev, iu, iv),
+                                  a.n_cells, a.cells_pow2_mask, &cand_cell, &cand_h2);
                         unsigned long long w = 0;
                         const int first = alg1_scan(a, cand_cell, cand_h2, &w);
                         n_look++;
@@ -854,7 +868,9 @@ __global__ void __launch_bounds__(EVAL_WARPS * 32) k_eval_fused(BatchArgs a, uin
                             cand_node = ins.z;
                         }
                     } else if (a.use_cache && mine) {
-                        d_address(d_key(mg, ins.z, lev, iu, iv), a.n_cells, a.cells_pow2_mask, &cand_cell, &cand_h2);
+                        d_address(((ins.x >> 8) & FLAG_POSROOT) ? d_key_pos(mg, ins.z, (uint32_t)a.pos_level, pt.px, pt.py, pt.pz)
+                                                                  : d_key(mg, ins.z, lev, iu, iv),
+                                  a.n_cells, a.cells_pow2_mask, &cand_cell, &cand_h2);
                         bool hit = false;
                         const int first = a.table_empty ? 0 : probe_cell(a, cand_cell, cand_h2, &hit);
                         n_look++;
@@ -984,6 +1000,11 @@ __global__ void __launch_bounds__(EVAL_WARPS * 32) k_eval_roots(BatchArgs a, uin
         if (valid) {
             pt.u = a.su[s];
             pt.v = a.sv[s];
+            if (a.pos_level >= 0) {   // a position-class node reads the position
+                pt.px = a.spx[s];
+                pt.py = a.spy[s];
+                pt.pz = a.spz[s];
+            }
             orig = a.sidx[s];
             rec = a.probes[base + j];
         }

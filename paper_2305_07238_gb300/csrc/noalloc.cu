@@ -110,6 +110,7 @@ extern "C" pmc_status pmc_eval_batch_noalloc(pmc_cache* c, const pmc_points* pts
     a.n = (uint32_t)n;
     a.g1u = pts->g1u; a.g1v = pts->g1v; a.g2u = pts->g2u; a.g2v = pts->g2v;
     a.level_offset = c->desc.level_offset;
+    a.pos_level = (c->use_cache && (c->desc.flags & PMC_POSITION_DESCRIPTOR)) ? (int32_t)c->desc.pos_level : -1;
     a.out_rgb = out_rgb; a.out_hits = out_hits;
     a.mats = c->d_mats; a.n_mats = c->n_mats;
     a.prog = c->d_prog; a.params = c->d_params; a.roots = c->d_roots;

@@ -74,6 +74,23 @@ __device__ __forceinline__ uint64_t d_key(uint32_t mat, uint32_t node, uint32_t 
            ((uint64_t)iu << 13) | (uint64_t)iv;
 }
 
+// Voxel of one position coordinate on a grid of 2^-level world units: floor(p 2^level)
+// clamped to [-512, 511] and offset to [0, 1023]; p 2^level is exact in FP32 (a power-of-two
+// scale), so the index is the same in any wider precision; NaN takes the lowest voxel.
+__device__ __forceinline__ uint32_t d_voxel(float p, uint32_t level) {
+    float x = p * __int_as_float((int)(127u + level) << 23);
+    if (!(x >= -512.0f)) x = -512.0f;
+    if (x > 511.0f) x = 511.0f;
+    return (uint32_t)((int)floorf(x) + 512);
+}
+
+// World-position descriptor: (material, node, voxel of the position); bit 31 set.
+__device__ __forceinline__ uint64_t d_key_pos(uint32_t mat, uint32_t node, uint32_t level, float px, float py,
+                                              float pz) {
+    return ((uint64_t)mat << 48) | ((uint64_t)node << 32) | (1ull << 31) | ((uint64_t)d_voxel(px, level) << 20) |
+           ((uint64_t)d_voxel(py, level) << 10) | (uint64_t)d_voxel(pz, level);
+}
+
 __device__ __forceinline__ void d_address(uint64_t key, uint64_t n_cells, uint32_t pow2_mask,
                                           uint32_t* cell, uint32_t* h2) {
     uint64_t h1 = d_splitmix(key);

@@ -28,6 +28,8 @@ namespace pmc {
 constexpr uint32_t OP_ROOT_BEGIN = 32;
 constexpr uint32_t OP_LOAD_ROOT = 33;   // y: out slot | root ordinal; reads that node's probe record
 constexpr uint32_t FLAG_ROOT = 1;
+constexpr uint32_t FLAG_POSROOT = 2;    // ROOT_BEGIN of a node looked up under a position voxel
+constexpr uint32_t ROOT_POS_BIT = 1u << 31;   // device root table: node ID | this bit for such nodes
 
 // Each cacheable node also gets a standalone program (its sub-graph, with any cacheable
 // node below it read from its probe record) so that its misses can be evaluated 32 at
@@ -62,6 +64,7 @@ struct CompiledMaterial {
     std::vector<uint4> prog;
     std::vector<float> params;     // parameter offsets in prog are relative to this
     std::vector<uint32_t> roots;   // node IDs of cacheable nodes, ascending
+    std::vector<uint8_t> root_pos; // per cacheable node: 1 = world-position descriptor
     std::vector<std::vector<uint4>> root_progs;  // standalone program per cacheable node
     std::vector<uint32_t> root_level;
     std::vector<uint32_t> root_slots;
@@ -75,7 +78,7 @@ struct CompiledMaterial {
 };
 
 // Compiles one network.  Returns false (with a reason) for a malformed network.
-bool compile_material(const pmc_node* nodes, uint32_t n, uint32_t min_root_nodes,
+bool compile_material(const pmc_node* nodes, uint32_t n, uint32_t min_root_nodes, bool pos_desc,
                       CompiledMaterial* out, const char** why);
 
 // FP32 flops of one executed node (FMA counted as 2), from the device formulas.
@@ -146,6 +149,7 @@ struct BatchArgs {
     // ray-cone gradients (caller-owned, optional): each point's own mip level (Eq. 1)
     const float* g1u; const float* g1v; const float* g2u; const float* g2v;
     int32_t level_offset;
+    int32_t pos_level;         // world-position descriptor: voxels of 2^-pos_level; -1 = off
     // outputs
     float* out_rgb; uint16_t* out_hits;
     // materials

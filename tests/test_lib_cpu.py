@@ -107,3 +107,15 @@ def test_replacement_rejects_concurrent_and_round_inserts(lib):
         with pytest.raises(P.PmcError) as ei:
             P.Cache([W.material_tiny()], 64, 4, flags=P.PMC_REPLACE_VISIBILITY | extra)
         assert ei.value.status == P.PMC_ERR_INVALID_ARG
+
+
+def test_position_descriptor_roots_match_oracle(lib):
+    from .test_oracle_position import g_position
+    mats = W.random_materials(30, 5, 400, 0.3, seed=12) + [g_position()]
+    for m in mats:
+        for mr in (1, 2):
+            got = P.analyze_material(m, min_root_nodes=mr, flags=P.PMC_POSITION_DESCRIPTOR)
+            _, roots, kinds = O.analyze(m, min_root_nodes=mr, pos_desc=True, kinds=True)
+            assert np.array_equal(got["roots"], roots)
+            assert np.array_equal(got["kinds"], kinds)
+    assert list(P.analyze_material(g_position(), flags=P.PMC_POSITION_DESCRIPTOR)["kinds"]) == [2, 1, 2]
