@@ -453,10 +453,11 @@ class Frame:
     def points_paths(self, pass_index: int, bounce_frac=(0.5, 0.25), rows: tuple | None = None) -> dict:
         """One pass of a path tracer as one batch: the directly visible sample of every
         pixel (points() of the pass, visibility class 0), then for bounce k = 1, 2, ... the
-        shading points of the paths still alive, a fraction bounce_frac[k-1] of the pixels.
-        An indirect ray lands anywhere: each such point lies on the surface seen by a
-        pixel drawn uniformly from the frame (or from the band `rows`), with fresh jitter,
-        and carries class k in "vis"."""
+        shading points of the paths still alive, a fraction bounce_frac[k-1] of the pixels,
+        carrying class k in "vis".  An indirect ray lands anywhere in the scene, mostly off
+        the parts the camera sees: each such point takes the material of a tile drawn
+        uniformly from the frame (or from the band `rows`), a UV uniform on [0,1)^2 of that
+        material and a position uniform in the scene's box, with that tile's normal."""
         spec = self.spec
         direct = self.points(pass_index, rows=rows)
         n0 = len(direct["u"])
@@ -467,14 +468,9 @@ class Frame:
         for k, frac in enumerate(bounce_frac, start=1):
             m = int(round(frac * n0))
             pix = lo + rng.integers(0, n0, m)
-            jx, jy = rng.random(m), rng.random(m)
-            d = L["d"][pix]
-            u = np.mod(L["ou"][pix] + d * (L["bx"][pix] + jx), 1.0)
-            v = np.mod(L["ov"][pix] + d * (L["by"][pix] + jy), 1.0)
-            wx = 0.01 * (L["fx"][pix] + jx)
-            wy = 0.01 * (L["fy"][pix] + jy)
-            pos = [(L["c"][q][pix] + wx * L["e1"][q][pix] + wy * L["e2"][q][pix]) * 0.25 for q in range(3)]
-            parts.append(_pack(u, v, L["mat"][pix], pos, [L["n"][q][pix] for q in range(3)]))
+            uv = rng.random((2, m))
+            pos = rng.uniform(-4.0, 4.0, (3, m))
+            parts.append(_pack(uv[0], uv[1], L["mat"][pix], pos, [L["n"][q][pix] for q in range(3)]))
             vis.append(np.full(m, k, dtype=np.uint8))
         out = {f: np.concatenate([p[f] for p in parts]) for f in POINT_FIELDS}
         out["vis"] = np.concatenate(vis)
