@@ -302,11 +302,13 @@ __device__ __forceinline__ int scan_words(const uint4 (&w)[NQ], uint32_t h2, uin
     return first;
 }
 
-// NQ = 16-byte words of hash2 per cell (ceil(N_e / 4)); RB probes in flight per lane.
+// NQ = 16-byte words of hash2 per cell (ceil(N_e / 4)); RB probes in flight per lane; POS:
+// the cache has the world-position descriptor (a separate instantiation, so that caches
+// without it keep the registers the position keys would take).
 // Each group of RB probes takes two dependent round trips to memory, both fully
 // overlapped across the group: first every probe's hash2 words, then the values of
 // the hits.  Records and miss lists are written after both.
-template <int NQ, int RB>
+template <int NQ, int RB, bool POS>
 __global__ void __launch_bounds__(256) k_lookup(BatchArgs a) {
     const uint32_t warp = threadIdx.x >> 5, lane = lane_id();
     const uint32_t warps_total = gridDim.x * (blockDim.x >> 5);
@@ -325,7 +327,7 @@ __global__ void __launch_bounds__(256) k_lookup(BatchArgs a) {
             if (a.g1u) lev = a.slev[s];
             iu = d_texel(a.su[s], lev);
             iv = d_texel(a.sv[s], lev);
-            if (a.pos_level >= 0) {
+            if (POS) {
                 px = a.spx[s];
                 py = a.spy[s];
                 pz = a.spz[s];
@@ -346,7 +348,7 @@ __global__ void __launch_bounds__(256) k_lookup(BatchArgs a) {
                 h2[b] = 0;
                 if (act[b]) {
                     const uint32_t node = __ldg(&a.roots[mi.root_base + r0 + b]);
-                    const uint64_t key = (node & ROOT_POS_BIT)
+                    const uint64_t key = (POS && (node & ROOT_POS_BIT))
                                              ? d_key_pos(m, node & 0xFFFFu, (uint32_t)a.pos_level, px, py, pz)
                                              : d_key(m, node, lev, iu, iv);
                     d_address(key, a.n_cells, a.cells_pow2_mask, &cell[b], &h2[b]);
@@ -969,6 +971,7 @@ __global__ void k_scan_roots(BatchArgs a) {
 // Batched evaluation of the missed cacheable nodes (the "missed sub-graphs" of Sec. 3):
 // a warp runs one cacheable node's standalone program for 32 of its misses, writes the
 // values into their probe records and offers them to the table.
+template <bool POS>
 __global__ void __launch_bounds__(EVAL_WARPS * 32) k_eval_roots(BatchArgs a, uint32_t level, uint32_t* item_ctr) {
     extern __shared__ float s_val[];
     __shared__ float2 s_grad[8];
@@ -1000,7 +1003,7 @@ __global__ void __launch_bounds__(EVAL_WARPS * 32) k_eval_roots(BatchArgs a, uin
         if (valid) {
             pt.u = a.su[s];
             pt.v = a.sv[s];
-            if (a.pos_level >= 0) {   // a position-class node reads the position
+            if (POS) {   // a position-class node reads the position
                 pt.px = a.spx[s];
                 pt.py = a.spy[s];
                 pt.pz = a.spz[s];
@@ -2230,6 +2233,25 @@ static cudaError_t launch_insert(const BatchArgs& a, cudaStream_t s, int num_sms
     return e;
 }
 
+// The lookup instantiation for N_e (hash2 words per cell) and the probes in flight.
+template <bool POS>
+void launch_lookup(const BatchArgs& a, uint32_t ne, uint32_t rb, unsigned lb, cudaStream_t s) {
+    if (ne <= 4) {
+        if (rb >= 4) k_lookup<1, 4, POS><<<lb, 256, 0, s>>>(a);
+        else if (rb >= 2) k_lookup<1, 2, POS><<<lb, 256, 0, s>>>(a);
+        else k_lookup<1, 1, POS><<<lb, 256, 0, s>>>(a);
+    } else if (ne <= 8) {
+        if (rb >= 4) k_lookup<2, 4, POS><<<lb, 256, 0, s>>>(a);
+        else if (rb >= 2) k_lookup<2, 2, POS><<<lb, 256, 0, s>>>(a);
+        else k_lookup<2, 1, POS><<<lb, 256, 0, s>>>(a);
+    } else if (ne <= 16) {
+        if (rb >= 2) k_lookup<4, 2, POS><<<lb, 256, 0, s>>>(a);
+        else k_lookup<4, 1, POS><<<lb, 256, 0, s>>>(a);
+    } else {
+        k_lookup<8, 1, POS><<<lb, 256, 0, s>>>(a);
+    }
+}
+
 cudaError_t launch_batch(const BatchArgs& a, cudaStream_t s, int num_sms, cudaEvent_t* ev,
                          uint64_t* launches) {
     cudaError_t e;
@@ -2331,20 +2353,10 @@ cudaError_t launch_batch(const BatchArgs& a, cudaStream_t s, int num_sms, cudaEv
     if (a.n > 0 && a.use_cache && !a.keys_inline && !fused) {
         const uint32_t ne = a.n_entries, rb = a.lookup_rb;
         const unsigned lb = (unsigned)num_sms * 8u;
-        if (ne <= 4) {
-            if (rb >= 4) k_lookup<1, 4><<<lb, 256, 0, s>>>(a);
-            else if (rb >= 2) k_lookup<1, 2><<<lb, 256, 0, s>>>(a);
-            else k_lookup<1, 1><<<lb, 256, 0, s>>>(a);
-        } else if (ne <= 8) {
-            if (rb >= 4) k_lookup<2, 4><<<lb, 256, 0, s>>>(a);
-            else if (rb >= 2) k_lookup<2, 2><<<lb, 256, 0, s>>>(a);
-            else k_lookup<2, 1><<<lb, 256, 0, s>>>(a);
-        } else if (ne <= 16) {
-            if (rb >= 2) k_lookup<4, 2><<<lb, 256, 0, s>>>(a);
-            else k_lookup<4, 1><<<lb, 256, 0, s>>>(a);
-        } else {
-            k_lookup<8, 1><<<lb, 256, 0, s>>>(a);
-        }
+        if (a.pos_level >= 0)
+            launch_lookup<true>(a, ne, rb, lb, s);
+        else
+            launch_lookup<false>(a, ne, rb, lb, s);
         nl++;
     }
     if (a.n > 0 && a.surr_slot) {
@@ -2369,15 +2381,22 @@ cudaError_t launch_batch(const BatchArgs& a, cudaStream_t s, int num_sms, cudaEv
             (e = cudaFuncSetAttribute(k_eval, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
             return e;
         if (smem_roots > 48 * 1024 &&
-            (e = cudaFuncSetAttribute(k_eval_roots, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_roots)) !=
-                cudaSuccess)
+            ((e = cudaFuncSetAttribute(k_eval_roots<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem_roots)) != cudaSuccess ||
+             (e = cudaFuncSetAttribute(k_eval_roots<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem_roots)) != cudaSuccess))
             return e;
         if (a.use_cache && a.split && !a.keys_inline) {
             k_scan_roots<<<1, 1024, 0, s>>>(a);
             nl++;
             // the level counters live after the per-root miss counters
             for (uint32_t lv = 0; lv <= a.max_level; ++lv) {
-                k_eval_roots<<<num_sms * 16, EVAL_WARPS * 32, smem_roots, s>>>(a, lv, a.miss_cnt + a.n_roots_total + lv);
+                if (a.pos_level >= 0)
+                    k_eval_roots<true><<<num_sms * 16, EVAL_WARPS * 32, smem_roots, s>>>(a, lv,
+                                                                                      a.miss_cnt + a.n_roots_total + lv);
+                else
+                    k_eval_roots<false><<<num_sms * 16, EVAL_WARPS * 32, smem_roots, s>>>(a, lv,
+                                                                                       a.miss_cnt + a.n_roots_total + lv);
                 nl++;
             }
         }
