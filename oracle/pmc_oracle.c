@@ -778,6 +778,7 @@ int orc_run_batch(orc_cache* c, uint64_t n, const float* u, const float* v,
     uint8_t* needed = (uint8_t*)malloc(max_n);
     uint64_t* rcell = (uint64_t*)malloc((size_t)max_n * sizeof(uint64_t));
     uint32_t* rh2 = (uint32_t*)malloc((size_t)max_n * sizeof(uint32_t));
+    uint8_t* rclosed = (uint8_t*)malloc(max_n);   /* replacement: the cell cannot take it */
     size_t cand_cap = 1024, n_cand = 0;
     orc_candidate* cand = (orc_candidate*)malloc(cand_cap * sizeof(orc_candidate));
     uint64_t probe = 0;
@@ -820,8 +821,20 @@ int orc_run_batch(orc_cache* c, uint64_t n, const float* u, const float* v,
             rcell[node] = cell;
             rh2[node] = h2;
             int found = 0;
+            rclosed[node] = 0;
             if (!surr) {
-                found = scan_cell(c, cell, h2, &slot) == 1;
+                const int sc = scan_cell(c, cell, h2, &slot);
+                found = sc == 1;
+                /* Replacement: a cell that is full of entries whose classes are all at most
+                 * the point's own can never take its value in this batch (classes in a
+                 * full cell only decrease), so the value is dropped as full at lookup. */
+                if (sc < 0 && c->replace) {
+                    const uint8_t q = vis ? vis[i] : 0;
+                    uint8_t mx = 0;
+                    for (uint32_t e = 0; e < c->n_entries; ++e)
+                        if (c->cls[cell * c->n_entries + e] > mx) mx = c->cls[cell * c->n_entries + e];
+                    rclosed[node] = mx <= q;
+                }
                 c->stats[0]++;
                 if (found) {
                     hit[node] = 1;
@@ -859,7 +872,10 @@ int orc_run_batch(orc_cache* c, uint64_t n, const float* u, const float* v,
             orc_eval_node(nd, input_value(nd, 0, val), input_value(nd, 1, val),
                           input_value(nd, 2, val), sp, &val[3 * j]);
             n_eval++;
-            if (!c->off && M->is_root[j]) {
+            if (!c->off && M->is_root[j] && rclosed[j]) {
+                c->stats[3]++;
+                c->stats[6]++;
+            } else if (!c->off && M->is_root[j]) {
                 /* A missed root that was evaluated becomes an insert candidate
                  * carrying its own value rounded to FP32 (Sec. 3). */
                 if (n_cand == cand_cap) {
@@ -898,6 +914,7 @@ int orc_run_batch(orc_cache* c, uint64_t n, const float* u, const float* v,
     free(needed);
     free(rcell);
     free(rh2);
+    free(rclosed);
     free(cand);
     return status;
 }

@@ -157,7 +157,10 @@ void orc_cache_set_alg1(orc_cache* c, int on);
  * entry of its descriptor overwrites the entry of the largest class, if that class is
  * larger than the newcomer's (the first such entry on ties), and counts it as replaced;
  * otherwise the value is dropped as with keep-first.  Lookups do not change classes.
- * With every class 0 the table evolves exactly as with keep-first. */
+ * A value whose cell, at lookup, is full of entries of classes at most its own can never
+ * enter the cell in that batch (a full cell's classes only decrease), so it is dropped as
+ * full there and then, even if a copy of its key with a smaller class enters the cell
+ * earlier in the batch.  With every class 0 the table evolves exactly as with keep-first. */
 void orc_cache_set_replacement(orc_cache* c, int on);
 /* level >= 0: the world-position descriptor (Sec. 3.1 names world-space position as a
  * further descriptor, Sec. 5 lists it as future work).  A node whose sub-graph depends on

@@ -279,7 +279,16 @@ __device__ __forceinline__ float* cell_val(const BatchArgs& a, uint32_t cell, ui
 }
 constexpr uint32_t PROBE_MISS = 0u;   // record {cell, hash2, first empty slot, 0}
 constexpr uint32_t PROBE_HIT = 1u;    // record {r, g, b, 1}
-constexpr uint32_t PROBE_FULL = 2u;   // record {cell, hash2, N_e, 2}: no empty slot
+constexpr uint32_t PROBE_FULL = 2u;   // record {cell, hash2, N_e, 2}: the cell cannot take the value
+
+// Replacement by visibility class: a full cell whose entries all have classes at most q can
+// never take a value of class q in this batch (a full cell's classes only decrease).
+__device__ __forceinline__ bool cell_closed(const BatchArgs& a, uint32_t cell, uint32_t q) {
+    const uint8_t* cc = a.slot_cls + (size_t)cell * a.n_entries;
+    uint32_t mx = 0;
+    for (uint32_t e = 0; e < a.n_entries; ++e) mx = max(mx, (uint32_t)__ldg(&cc[e]));
+    return mx <= q;
+}
 
 
 // Scans the hash2 words of a cell held in registers: first slot holding h2 (hit) or 0.
@@ -336,6 +345,8 @@ __global__ void __launch_bounds__(256) k_lookup(BatchArgs a) {
         const MatInfo mi = a.mats[m];
         const int32_t surr = a.surr_ord ? a.surr_ord[m] : -1;   // a surrogate's node is not probed
         const size_t rec0 = (size_t)__ldg(&a.probe_base[m]) + j;
+        // replacement: the point's visibility class decides whether a full cell is closed
+        const uint32_t q = (a.slot_cls && a.vis && valid) ? (uint32_t)__ldg(&a.vis[a.sidx[s]]) : 0u;
         for (uint32_t r0 = 0; r0 < mi.n_roots; r0 += RB) {
             uint4 w[RB][NQ];
             uint32_t cell[RB], h2[RB];
@@ -383,9 +394,11 @@ __global__ void __launch_bounds__(256) k_lookup(BatchArgs a) {
                         a.probes[rec] = make_float4(v[b][0], v[b][1], v[b][2], __uint_as_float(PROBE_HIT));
                         n_hit++;
                     } else {
+                        bool full = first[b] < 0;
+                        if (full && a.slot_cls) full = cell_closed(a, cell[b], q);
                         a.probes[rec] = make_float4(__uint_as_float(cell[b]), __uint_as_float(h2[b]),
                                                     __uint_as_float(first[b] >= 0 ? (uint32_t)first[b] : ne),
-                                                    __uint_as_float(first[b] >= 0 ? PROBE_MISS : PROBE_FULL));
+                                                    __uint_as_float(full ? PROBE_FULL : PROBE_MISS));
                     }
                 }
                 if (a.split) {
@@ -421,20 +434,21 @@ size_t eval_smem_bytes(uint32_t max_slots) {
 }
 
 // Offers the lanes' freshly evaluated cacheable-node values to the table (Sec. 3).
-// Keep-first: a cell that was full at lookup stays full (nothing is evicted), so its
-// value is counted as dropped without becoming a candidate, and lanes carrying the same
-// (cell, hash2) collapse onto the smallest point index; the others share its fate.
-// Replacement by visibility class: every value becomes a candidate of its own, since a
-// full cell may still take it and copies of one key with different classes can meet
-// different fates; its dup scan starts at slot 0, since an eviction can put the key
-// anywhere in the cell.  Must be called by all 32 lanes.
+// `full`: the cell cannot take the value in this batch, so it is counted as dropped
+// without becoming a candidate.  Keep-first: the cell was full at lookup (nothing is
+// evicted), and lanes carrying the same (cell, hash2) collapse onto the smallest point
+// index; the others share its fate.  Replacement by visibility class: the cell was full
+// at lookup of entries of classes at most the point's own; every other value becomes a
+// candidate of its own, since copies of one key with different classes can meet different
+// fates, and its dup scan starts at slot 0, since an eviction can put the key anywhere in
+// the cell.  Must be called by all 32 lanes.
 __device__ __forceinline__ void offer(const BatchArgs& a, bool act, uint32_t orig, uint32_t node, uint32_t cell,
                                       uint32_t h2, uint32_t start, bool full, float r, float g, float b,
                                       unsigned long long* n_cand, unsigned long long* n_full) {
     const bool replace = a.slot_cls != nullptr;   // uniform
     *n_cand += act ? 1u : 0u;
-    *n_full += (act && full && !replace) ? 1u : 0u;
-    const bool emit = act && (!full || replace);
+    *n_full += (act && full) ? 1u : 0u;
+    const bool emit = act && !full;
     bool winner = false;
     uint32_t shadows = 0;
     const unsigned em = __ballot_sync(FULL_MASK, emit);
@@ -889,6 +903,8 @@ __global__ void __launch_bounds__(EVAL_WARPS * 32) k_eval_fused(BatchArgs a, uin
                         } else {
                             cand_start = first >= 0 ? (uint32_t)first : ne;
                             cand_full = first < 0;
+                            if (cand_full && a.slot_cls)
+                                cand_full = cell_closed(a, cand_cell, a.vis ? (uint32_t)__ldg(&a.vis[i]) : 0u);
                             cand_node = ins.z;
                         }
                     }

@@ -83,13 +83,22 @@ def test_same_descriptor_two_classes_in_one_batch():
     assert _cell(c) == ([_h2(5)], [0])
     st = c.stats()
     assert (st["replaced"], st["dropped_full"], st["dropped_dup"]) == (1, 1, 0)
-    # and a copy after an eviction in the same batch is a duplicate
+    # a copy after an eviction in the same batch is a duplicate if its cell, at lookup, held
+    # an entry it could have evicted (class 3 > 2) ...
     c2 = _one_cell(1)
-    c2.run_batch(_texel_points([0], [1]))
+    c2.run_batch(_texel_points([0], [3]))
     c2.run_batch(_texel_points([6, 6], [0, 2]))
     assert _cell(c2) == ([_h2(6)], [0])
     st = c2.stats()
     assert (st["replaced"], st["dropped_dup"], st["dropped_full"]) == (1, 1, 0)
+    # ... and is dropped as full at lookup if every entry there was of its class or smaller
+    # (class 1 <= 2): it could never have entered the cell in this batch
+    c3 = _one_cell(1)
+    c3.run_batch(_texel_points([0], [1]))
+    c3.run_batch(_texel_points([6, 6], [0, 2]))
+    assert _cell(c3) == ([_h2(6)], [0])
+    st = c3.stats()
+    assert (st["replaced"], st["dropped_dup"], st["dropped_full"]) == (1, 0, 1)
 
 
 def test_ties_evict_the_first_entry_of_the_largest_class():
