@@ -42,7 +42,7 @@ SAMPLE_ROWS = (0, 40)            # CPU-oracle sample: 40 full-width rows, all 16
 REF_ROWS = (0, 16)               # reference arm: 16 full-width rows per step, all 16 passes
 # ncu capture of k_eval / k_lookup on the same workload (profiles/): DRAM bytes per launch
 # (profiles/launches_frame1080p.md: mean over the launches of one frame of each kernel)
-NCU_TRAFFIC = {"eval": 313.0e6, "eval_roots": 182.2e6, "lookup": 1049.2e6}
+NCU_TRAFFIC = {"eval": 313.0e6, "eval_roots": 182.1e6, "lookup": 1050.1e6}
 
 FP32_LANES_PER_SM = 128          # Blackwell SM: 4 partitions x 32 FP32 lanes
 N_SMS = 152
