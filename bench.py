@@ -319,26 +319,35 @@ def ours(args, rank, world, local_rank, dist):
                   "ms_per_step": round(secs_eager / args.steps * 1e3, 3),
                   "gpu_launches": int(timing["launches"])},
     }
+    def guarded(name, fn):
+        # an optional leg that raises reports its error instead of losing the whole line
+        try:
+            line[name] = fn()
+        except Exception as exc:   # noqa: BLE001
+            line[name] = {"error": f"{type(exc).__name__}: {exc}"}
+
     if "surr" in legs:
-        line["surrogate"] = surrogate_leg(torch, P, dev, local_rank, seed=rank)
+        guarded("surrogate", lambda: surrogate_leg(torch, P, dev, local_rank, seed=rank))
     if "f128" in legs:
-        line["frame128"] = frame128_leg(torch, P, dev, local_rank, seed=rank)
+        guarded("frame128", lambda: frame128_leg(torch, P, dev, local_rank, seed=rank))
     if "alg1" in legs:
-        line["alg1"] = alg1_leg(torch, P, mats, dev_passes, outs, hits, local_rank)
-        if u_value == u_value:
+        guarded("alg1", lambda: alg1_leg(torch, P, mats, dev_passes, outs, hits, local_rank))
+        if u_value == u_value and "cached" in line["alg1"]:
             line["alg1"]["speedup_cached_over_uncached"] = round(line["alg1"]["cached"] / u_value, 3)
     if "cones" in legs:
-        line["ray_cones"] = cones_leg(torch, P, dev, local_rank, seed=rank)
-        if line["ray_cones"] and u_value == u_value:
+        guarded("ray_cones", lambda: cones_leg(torch, P, dev, local_rank, seed=rank))
+        if u_value == u_value and "offset0" in line["ray_cones"]:
             for off in (0, -1):
                 r = line["ray_cones"][f"offset{off}"]
                 r["speedup_cached_over_uncached"] = round(r["cached"] / u_value, 3)
+    if "raycast" in legs:
+        guarded("ray_caster", lambda: raycast_leg(torch, P, mats, dev, local_rank, seed=rank))
     if "position" in legs:
-        line["position_descriptor"] = position_leg(torch, P, mats, dev_passes, outs, hits, local_rank)
+        guarded("position_descriptor", lambda: position_leg(torch, P, mats, dev_passes, outs, hits, local_rank))
     if "replace" in legs:
-        line["replacement"] = replace_leg(torch, P, dev, local_rank, seed=rank)
+        guarded("replacement", lambda: replace_leg(torch, P, dev, local_rank, seed=rank))
     if "sweep" in legs:
-        line["scale_sweep"] = sweep_leg(torch, P, dev, local_rank, seed=rank)
+        guarded("scale_sweep", lambda: sweep_leg(torch, P, dev, local_rank, seed=rank))
     if rank == 0 and not args.no_cpu_baseline and "cpu" in legs:
         line["cpu_baseline"], line["max_abs_err_vs_fp64"] = cpu_baseline(P, torch, mats, frame, dev)
     return line
@@ -459,6 +468,68 @@ def alg1_leg(torch, P, mats, dev_passes, outs, hits, local_rank):
             "schedule": tune["schedule"],
             "hit_rate": round(st["hits"] / max(1, st["lookups"]), 4),
             "table": {k: st[k] for k in ("inserted", "dropped_dup", "dropped_full", "dropped_race")}}
+
+
+def raycast_leg(torch, P, mats, dev, local_rank, seed=0):
+    """Shading points from the library's ray caster instead of the synthetic stream: a
+    closed room with 24 spheres, 64 materials (Zipf 1.1 over the objects), a 1920x1080
+    pinhole camera, one primary ray per pixel per pass, 16 passes.  The caster alone
+    (points/s and the HBM roofline of its 56 B of output per point), then cast + pass with
+    per-point levels from the ray cones (Eq. 1), cached and uncached, eager launches."""
+    sc = W.Scene(W.SceneSpec(seed=seed))
+    n = WIDTH * HEIGHT
+    bufs = P.cast_rays(sc.objects, sc.camera, seed=seed + 1, pass_index=0)
+    for p in range(3):
+        P.cast_rays(sc.objects, sc.camera, seed=seed + 1, pass_index=p, out=bufs)
+    torch.cuda.synchronize()
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t0.record()
+    for p in range(SPP):
+        P.cast_rays(sc.objects, sc.camera, seed=seed + 1, pass_index=p, out=bufs)
+    t1.record()
+    torch.cuda.synchronize()
+    cast_s = t0.elapsed_time(t1) / 1e3
+    hbm_peak, sm_mhz_max, peak_kind = peaks()
+    gbs = 56.0 * n * SPP / cast_s / 1e9
+    # FP32 operations per ray, counted from the caster's formulas (a multiply-add as 2):
+    # 12 per plane, 24 per sphere, about 105 for the ray, the shading point and the cone
+    n_planes = int((sc.objects["kind"] == W.KIND_PLANE).sum())
+    flops_ray = 12 * n_planes + 24 * (len(sc.objects) - n_planes) + 105
+    fp32_peak = N_SMS * FP32_LANES_PER_SM * 2 * sm_mhz_max * 1e6 / 1e12
+    tflops = flops_ray * n * SPP / cast_s / 1e12
+    res = {"config": f"room of 6 planes + 24 spheres, 64 materials, {WIDTH}x{HEIGHT} pinhole, {SPP} passes, "
+                     f"table {N_CELLS}x{N_ENTRIES} slots, per-point levels from the ray cones", "unit": UNIT,
+           "cast_points_per_s": round(n * SPP / cast_s, 1),
+           "cast_roofline": {"kernel": "k_cast", "bound": "alu", "achieved": round(tflops, 2),
+                             "peak": round(fp32_peak, 2), "unit": "TFLOP/s", "frac": round(tflops / fp32_peak, 4),
+                             "flops_per_ray": flops_ray, "peak_kind": "FP32 lanes x 2 x max SM clock",
+                             "output_gbs": round(gbs, 1), "output_frac_of_hbm": round(gbs / hbm_peak, 4),
+                             "bytes_per_point": 56}}
+    outs = torch.empty((3, n), dtype=torch.float32, device=dev)
+    hits = torch.empty(n, dtype=torch.int16, device=dev)
+    for name, flags in (("cached", 0), ("uncached", P.PMC_CACHE_OFF)):
+        c = P.Cache(mats, N_CELLS, N_ENTRIES, uv_level=LEVEL, flags=flags, device=local_rank)
+        for p in range(2):
+            P.cast_rays(sc.objects, sc.camera, seed=seed + 1, pass_index=p, out=bufs)
+            c.eval_batch(bufs, outs, hits)
+        c.autotune(bufs, reps=2)
+        c.reset()
+        torch.cuda.synchronize()
+        t0.record()
+        for p in range(SPP):
+            P.cast_rays(sc.objects, sc.camera, seed=seed + 1, pass_index=p, out=bufs)
+            c.eval_batch(bufs, outs, hits)
+        t1.record()
+        torch.cuda.synchronize()
+        st = c.stats()
+        r = {"points_per_s": round(n * SPP / (t0.elapsed_time(t1) / 1e3), 1)}
+        if name == "cached":
+            r.update(hit_rate=round(st["hits"] / max(1, st["lookups"]), 4), inserted=st["inserted"],
+                     dropped_full=st["dropped_full"])
+        c.close()
+        res[name] = r
+    res["speedup_cached_over_uncached"] = round(res["cached"]["points_per_s"] / res["uncached"]["points_per_s"], 3)
+    return res
 
 
 POS_LEVEL = 6   # world-position voxels of 1/64 unit: about 6 pixels of the frame per voxel edge
@@ -927,8 +998,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--legs", default="cached,uncached,e2e,surr,f128,alg1,cones,position,replace,cpu",
-                    help="comma list of cached, uncached, e2e, surr, f128, alg1, cones, position, replace, sweep, cpu "
+    ap.add_argument("--legs", default="cached,uncached,e2e,surr,f128,alg1,cones,raycast,position,replace,cpu",
+                    help="comma list of cached, uncached, e2e, surr, f128, alg1, cones, raycast, position, replace, "
+                         "sweep, cpu "
                          "(sweep is not in the "
                          "default: about a minute more; profiling runs take 'cached')")
     ap.add_argument("--profile", action="store_true",

@@ -511,6 +511,71 @@ typedef struct {
 pmc_status pmc_autotune(pmc_cache* cache, const pmc_points* sample, uint32_t reps,
                         pmc_tune_result* out);
 
+/* ---- shading points from a ray caster ----------------------------------------------
+ * The stage that feeds the material system in the paper's renderer: Sec. 3.1 takes each
+ * shading point's UV, material and ray-cone texture-coordinate gradients from it.  A small
+ * analytic scene (planes and spheres) and a pinhole camera; one primary ray per pixel per
+ * pass, written as the planes of a pass's shading points (pmc_points with the gradients).
+ *
+ * Object (host memory, copied at each call): kind PMC_OBJ_PLANE: p = {n (unit), d}, the
+ * points x with n.x = d, the scene on the side n.x >= d; kind PMC_OBJ_SPHERE: p = {centre,
+ * radius > 0}.  mat: the material index written for its hits.  Texture coordinates are a
+ * planar projection: u = frac(uv_scale x[a0]), v = frac(uv_scale x[a1]) with a0 = axes &
+ * 0xFF, a1 = axes >> 8 (0 = x, 1 = y, 2 = z).
+ * Camera: the ray of pixel (x, y) with sample offsets (jx, jy) in [0, 1) leaves eye along
+ * normalize(fwd + sx right + sy up), sx = (2 (x + jx) / width - 1) tan_half_y width / height,
+ * sy = (1 - 2 (y + jy) / height) tan_half_y.  The offsets come from the k-th output of
+ * SplitMix64 seeded with `seed`, k = pass * 2^32 + y * width + x + 1 (the output function of
+ * seed + k * 0x9E3779B97F4A7C15): jx = (r >> 40) 2^-24, jy = ((r >> 16) & 0xFFFFFF) 2^-24.
+ * Hit: the closest object with distance t > 1e-4 (the first one on ties); a sphere's
+ * discriminant is formed as r^2 - |oc - (d.oc) d|^2, oc = eye - centre.  Shading point:
+ * P = eye + t d; N = n (plane) or (P - centre) / radius; the material and (u, v) above; the
+ * ray cone of spread angle 2 tan_half_y / height has width w = t 2 tan_half_y / height at
+ * the hit; the footprint's axes are A1 = w m1 with m1 = unit(N x d) (head-on, |N x d| <
+ * 1e-6: unit(N x h), h = x axis if |N.x| < 0.9 else y axis) and A2 = w / max(|N.d|, 1e-3)
+ * m2 with m2 = unit(d - (N.d) N) (head-on: unit(N x m1)); the gradients are
+ * g1 = uv_scale (A1[a0], A1[a1]), g2 = uv_scale (A2[a0], A2[a1]).  A ray that hits nothing
+ * writes material UINT32_MAX, which a pass reports as out of range: give a closed scene. */
+#define PMC_MAX_SCENE_OBJECTS 64u
+#define PMC_OBJ_PLANE 0u
+#define PMC_OBJ_SPHERE 1u
+typedef struct {
+    uint32_t kind;
+    uint32_t mat;
+    uint32_t axes;
+    float uv_scale;
+    float p[4];
+} pmc_scene_object; /* 32 bytes */
+
+typedef struct {
+    float eye[3];
+    float fwd[3];
+    float right[3];
+    float up[3];
+    float tan_half_y;
+    uint32_t width;
+    uint32_t height;
+} pmc_camera;
+
+/* Output planes, DEVICE memory owned by the caller, (row1 - row0) * width entries each,
+ * scanline order from row row0. */
+typedef struct {
+    float* u;
+    float* v;
+    uint32_t* mat;
+    float *px, *py, *pz;
+    float *nx, *ny, *nz;
+    float *g1u, *g1v, *g2u, *g2v;
+} pmc_ray_hits;
+
+/* Casts the primary rays of rows row0 .. row1 - 1 for pass `pass` (asynchronous on
+ * `stream`).  PMC_ERR_INVALID_ARG for a malformed object or camera, more than
+ * PMC_MAX_SCENE_OBJECTS objects, rows outside the image or a missing output plane;
+ * PMC_ERR_UNSUPPORTED beyond 2^28 points. */
+pmc_status pmc_cast_rays(const pmc_scene_object* objects, uint32_t n_objects, const pmc_camera* cam,
+                         uint32_t row0, uint32_t row1, uint64_t seed, uint32_t pass,
+                         const pmc_ray_hits* out, void* stream);
+
 /* Human-readable name of a status code (static storage). */
 const char* pmc_status_str(pmc_status s);
 

@@ -17,7 +17,7 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD_DIR = os.path.join(HERE, "_build")
 LIB_PATH = os.path.join(BUILD_DIR, "libpmc.so")
 
-SOURCES = ["kernels.cu", "mlp.cu", "mlp_tc.cu", "capi.cu", "noalloc.cu", "compile.cpp"]
+SOURCES = ["kernels.cu", "mlp.cu", "mlp_tc.cu", "capi.cu", "noalloc.cu", "raycast.cu", "compile.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

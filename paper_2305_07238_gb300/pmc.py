@@ -37,7 +37,7 @@ EXPORTED = (
     "pmc_read_timing", "pmc_eval_batch_noalloc", "pmc_train_surrogates", "pmc_set_surrogate",
     "pmc_get_surrogate", "pmc_use_surrogates", "pmc_mlp_forward", "pmc_mlp_gradient", "pmc_mlp_train",
     "pmc_get_schedule", "pmc_set_schedule", "pmc_graph_create", "pmc_graph_launch", "pmc_graph_destroy",
-    "pmc_autotune", "pmc_status_str", "pmc_slot_classes", "pmc_analyze_material_ext",
+    "pmc_autotune", "pmc_status_str", "pmc_slot_classes", "pmc_analyze_material_ext", "pmc_cast_rays",
 )
 NOALLOC_MAX_POINTS, NOALLOC_MAX_PROBES, NOALLOC_MAX_MATERIALS = 8192, 32768, 4096
 PHASES = ("sort", "lookup", "missed", "eval", "insert", "finish")
@@ -136,6 +136,8 @@ def load():
     L.pmc_compute_keys.restype = st
     L.pmc_compute_levels.argtypes = [vp, vp, vp, vp, u64, C.c_int32, vp, vp]
     L.pmc_compute_levels.restype = st
+    L.pmc_cast_rays.argtypes = [vp, u32, vp, u32, u32, u64, u32, vp, vp]
+    L.pmc_cast_rays.restype = st
     L.pmc_set_timing.argtypes = [vp, C.c_int]
     L.pmc_set_timing.restype = st
     L.pmc_read_timing.argtypes = [vp, vp, vp, vp]
@@ -404,6 +406,44 @@ def compute_levels(g1u, g1v, g2u, g2v, offset=0, stream=None):
     _check(load().pmc_compute_levels(_dptr(g1u), _dptr(g1v), _dptr(g2u), _dptr(g2v), n, offset, _dptr(level),
                                      _stream_handle(stream)), "pmc_compute_levels")
     return level
+
+
+class _Camera(C.Structure):
+    _fields_ = [("eye", C.c_float * 3), ("fwd", C.c_float * 3), ("right", C.c_float * 3), ("up", C.c_float * 3),
+                ("tan_half_y", C.c_float), ("width", C.c_uint32), ("height", C.c_uint32)]
+
+
+RAY_HIT_FIELDS = ("u", "v", "mat", "px", "py", "pz", "nx", "ny", "nz", "g1u", "g1v", "g2u", "g2v")
+
+
+class _RayHits(C.Structure):
+    _fields_ = [(k, C.c_void_p) for k in RAY_HIT_FIELDS]
+
+
+def cast_rays(objects, camera: dict, seed: int, pass_index: int, rows=None, device="cuda", stream=None,
+              out=None) -> dict:
+    """Shading points of one pass from the library's ray caster: objects is a
+    workload.OBJECT_DTYPE array (host), camera a dict with eye, fwd, right, up (3 floats),
+    tan_half_y, width, height.  Returns device tensors u, v, mat (int32), px .. nz and the
+    ray-cone gradients g1u .. g2v, one entry per pixel of rows (y0, y1) (all rows if None),
+    ready for Cache.eval_batch.  `out`: the dict of a previous call of the same size, to
+    write into instead of allocating."""
+    import torch
+    from .workload import OBJECT_DTYPE
+    objs = np.ascontiguousarray(objects, dtype=OBJECT_DTYPE)
+    W, H = int(camera["width"]), int(camera["height"])
+    y0, y1 = rows if rows is not None else (0, H)
+    n = max(0, (y1 - y0) * W)
+    cam = _Camera((C.c_float * 3)(*camera["eye"]), (C.c_float * 3)(*camera["fwd"]),
+                  (C.c_float * 3)(*camera["right"]), (C.c_float * 3)(*camera["up"]),
+                  float(camera["tan_half_y"]), W, H)
+    if out is None or any(int(out[k].numel()) != n for k in RAY_HIT_FIELDS):
+        out = {k: torch.empty(n, dtype=torch.int32 if k == "mat" else torch.float32, device=device)
+               for k in RAY_HIT_FIELDS}
+    hits = _RayHits(*[_dptr(out[k]) for k in RAY_HIT_FIELDS])
+    _check(load().pmc_cast_rays(objs.ctypes.data, len(objs), C.byref(cam), y0, y1, seed & ((1 << 64) - 1),
+                                pass_index, C.byref(hits), _stream_handle(stream)), "pmc_cast_rays")
+    return out
 
 
 class Graph:

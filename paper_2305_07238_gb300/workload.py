@@ -509,3 +509,71 @@ class Frame:
         for k, name in enumerate(("nx", "ny", "nz")):
             out[name] = L["n"][k][sel].contiguous()
         return out
+
+
+# --------------------------------------------------------------------------------------
+# Procedural scene for the ray caster: a closed room and spheres resting on its floor
+# --------------------------------------------------------------------------------------
+# One record per object.  kind 0 = plane {n (unit), d}: the points x with n.x = d, the room
+# on the side n.x >= d; kind 1 = sphere {centre, radius}.  Texture coordinates are a planar
+# projection: (u, v) = fractional parts of uv_scale * (x[a0], x[a1]), a0 = axes & 0xFF,
+# a1 = axes >> 8.  The layout is the library's input format; its C header states it again.
+OBJECT_DTYPE = np.dtype([("kind", "<u4"), ("mat", "<u4"), ("axes", "<u4"), ("uv_scale", "<f4"),
+                         ("p", "<f4", (4,))])
+KIND_PLANE, KIND_SPHERE = 0, 1
+CAMERA_FIELDS = ("eye", "fwd", "right", "up")
+
+
+@dataclass
+class SceneSpec:
+    n_mats: int = 64
+    n_spheres: int = 24
+    room: tuple = (8.0, 6.0, 8.0)      # half width, height, half depth
+    zipf_s: float = 1.1
+    width: int = 1920
+    height: int = 1080
+    fov_y_deg: float = 60.0
+    eye: tuple = (0.0, 3.0, 7.5)
+    target: tuple = (0.0, 1.0, 0.0)
+    seed: int = 0
+
+
+class Scene:
+    """Objects (OBJECT_DTYPE records) and a pinhole camera whose basis is given as FP32
+    vectors: rays leave `eye` along fwd + sx right + sy up, with sx, sy the pixel's
+    position on the image plane scaled by tan_half_y (and the aspect ratio for sx)."""
+
+    def __init__(self, spec: SceneSpec):
+        self.spec = spec
+        rng = np.random.Generator(np.random.PCG64([spec.seed, 11]))
+        bx, by, bz = spec.room
+        planes = [((0, 1, 0), 0.0, (0, 2)), ((0, -1, 0), -by, (0, 2)),
+                  ((1, 0, 0), -bx, (2, 1)), ((-1, 0, 0), -bx, (2, 1)),
+                  ((0, 0, 1), -bz, (0, 1)), ((0, 0, -1), -bz, (0, 1))]
+        n_obj = len(planes) + spec.n_spheres
+        ranks = np.arange(1, spec.n_mats + 1, dtype=np.float64)
+        pz = ranks ** (-spec.zipf_s)
+        pz /= pz.sum()
+        rank_to_mat = rng.permutation(spec.n_mats)
+        mats = rank_to_mat[rng.choice(spec.n_mats, size=n_obj, p=pz)]
+        scales = np.exp(rng.uniform(math.log(0.05), math.log(0.5), n_obj))
+        objs = np.zeros(n_obj, dtype=OBJECT_DTYPE)
+        for k, (nrm, d, axes) in enumerate(planes):
+            objs[k] = (KIND_PLANE, mats[k], axes[0] | (axes[1] << 8), scales[k], (*nrm, d))
+        for k in range(spec.n_spheres):
+            r = float(np.exp(rng.uniform(math.log(0.3), math.log(1.5))))
+            cx = float(rng.uniform(-bx + r, bx - r))
+            cz = float(rng.uniform(-bz + r, bz - 2.0 - r))
+            objs[len(planes) + k] = (KIND_SPHERE, mats[len(planes) + k], 0 | (2 << 8), scales[len(planes) + k],
+                                     (cx, r, cz, r))
+        self.objects = objs
+        eye = np.array(spec.eye, dtype=np.float64)
+        fwd = np.array(spec.target, dtype=np.float64) - eye
+        fwd /= np.linalg.norm(fwd)
+        right = np.cross(fwd, np.array([0.0, 1.0, 0.0]))
+        right /= np.linalg.norm(right)
+        up = np.cross(right, fwd)
+        self.camera = {"eye": eye.astype(np.float32), "fwd": fwd.astype(np.float32),
+                       "right": right.astype(np.float32), "up": up.astype(np.float32),
+                       "tan_half_y": np.float32(math.tan(math.radians(spec.fov_y_deg) / 2.0)),
+                       "width": spec.width, "height": spec.height}

@@ -119,3 +119,25 @@ def test_position_descriptor_roots_match_oracle(lib):
             assert np.array_equal(got["roots"], roots)
             assert np.array_equal(got["kinds"], kinds)
     assert list(P.analyze_material(g_position(), flags=P.PMC_POSITION_DESCRIPTOR)["kinds"]) == [2, 1, 2]
+
+
+def test_cast_rays_rejects_bad_arguments(lib):
+    # checked before any device work
+    import ctypes as C
+    sc = W.Scene(W.SceneSpec(width=16, height=8))
+    cam = sc.camera
+    mk = lambda w, h: P._Camera((C.c_float * 3)(*cam["eye"]), (C.c_float * 3)(*cam["fwd"]),
+                                (C.c_float * 3)(*cam["right"]), (C.c_float * 3)(*cam["up"]),
+                                float(cam["tan_half_y"]), w, h)
+    hits = P._RayHits()   # no output planes
+    objs = np.ascontiguousarray(sc.objects)
+    call = lambda o, n, c, r0, r1: lib.pmc_cast_rays(o.ctypes.data, n, C.byref(c), r0, r1, 0, 0, C.byref(hits), None)
+    assert call(objs, 0, mk(16, 8), 0, 8) == P.PMC_ERR_INVALID_ARG                 # no objects
+    assert call(objs, 65, mk(16, 8), 0, 8) == P.PMC_ERR_INVALID_ARG                # too many
+    assert call(objs, len(objs), mk(0, 8), 0, 0) == P.PMC_ERR_INVALID_ARG          # empty image
+    assert call(objs, len(objs), mk(16, 8), 4, 9) == P.PMC_ERR_INVALID_ARG         # rows outside
+    assert call(objs, len(objs), mk(16, 8), 0, 8) == P.PMC_ERR_INVALID_ARG         # no outputs
+    bad = objs.copy()
+    bad[7]["p"][3] = 0.0                                                            # zero radius
+    assert call(bad, len(bad), mk(16, 8), 0, 0) == P.PMC_ERR_INVALID_ARG
+    assert call(objs, len(objs), mk(16, 8), 3, 3) == 0                              # nothing to do
