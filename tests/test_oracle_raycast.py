@@ -137,3 +137,20 @@ def test_room_scene_invariants():
         else:
             assert np.allclose(np.linalg.norm(P[sel] - p[:3], axis=1), p[3], atol=1e-9)
     assert r["robust"].mean() > 0.99
+
+
+def test_floor_levels_follow_eq1():
+    # on the floor the smaller gradient is the minor axis, of length s w, so Eq. 1 gives
+    # floor(-log2(s w)) there; the oracle's level function must agree on the FP32 values
+    from oracle import oracle as O
+    s, h, W_, H_, th = 0.25, 2.0, 6, 4, np.float32(0.02)
+    objs, cam = _floor_scene(s, h, W_, H_, th)
+    r = R.cast(objs, cam, seed=9, pass_index=1)
+    w = r["t"] * 2 * float(th) / H_
+    expect = np.clip(np.floor(-np.log2(s * w)), 0, 13).astype(int)
+    got = [O.level(np.float32(a), np.float32(b), np.float32(c), np.float32(d))
+           for a, b, c, d in zip(r["g1u"], r["g1v"], r["g2u"], r["g2v"])]
+    # away from a power of two (where FP32 rounding may tip the floor) they agree exactly
+    frac = -np.log2(s * w) - np.floor(-np.log2(s * w))
+    ok = (frac > 1e-4) & (frac < 1 - 1e-4)
+    assert ok.sum() > 0 and np.array_equal(np.asarray(got)[ok], expect[ok])
