@@ -13,7 +13,12 @@ streams below stand in for them:
 * ``frame``    -- randomly generated networks (node counts log-uniform), materials
   drawn per 8x8 pixel tile from a Zipf law, UV an affine function of the pixel
   position inside the tile plus per-sample jitter, position on a per-tile plane,
-  one normal per tile, one sample per pixel per pass.
+  one normal per tile, one sample per pixel per pass; optionally ray-cone gradients
+  per sample, or whole path-traced passes (direct samples, then indirect points of
+  later bounces that land anywhere in the scene, each with its visibility class).
+* ``scene``    -- a closed room of planes with spheres on its floor, a material per
+  object (Zipf) and a pinhole camera: the input of the ray caster that generates
+  shading points.
 """
 from __future__ import annotations
 
