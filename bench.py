@@ -131,6 +131,21 @@ def peaks():
     return 6800.0, 2070.0, "fallback"
 
 
+def max_over_ranks(torch, dist, secs, device):
+    """The slowest rank's time (every rank gets it); `secs` itself on one process."""
+    if dist is None:
+        return secs
+    t = torch.tensor([secs], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank, world, secs_max):
+    """Units of all replicas per second: every rank processes units_per_rank in the time
+    of the slowest one."""
+    return units_per_rank * world / secs_max
+
+
 def run_frame(cache, dev_passes, outs, hits, stream):
     cache.reset(stream)
     for p in range(SPP):
@@ -219,12 +234,8 @@ def ours(args, rank, world, local_rank, dist):
         secs = timed_graph(torch, graph, args.steps, barrier)
         g_launches = cached.read_timing()["launches"]
     graph.close()
-    secs_max = secs
-    if dist is not None:
-        t = torch.tensor([secs], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        secs_max = float(t.item())
-    value = pts_total * world / secs_max
+    secs_max = max_over_ranks(torch, dist, secs, dev)
+    value = whole_job_rate(pts_total, world, secs_max)
 
     # ---- uncached --------------------------------------------------------------------
     legs = set(args.legs.split(","))
@@ -237,11 +248,8 @@ def ours(args, rank, world, local_rank, dist):
         uncached.sync()
         usecs = timed_graph(torch, ugraph, args.steps, barrier)
         ugraph.close()
-        if dist is not None:
-            t = torch.tensor([usecs], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            usecs = float(t.item())
-        u_value = pts_total * world / usecs
+        usecs = max_over_ranks(torch, dist, usecs, dev)
+        u_value = whole_job_rate(pts_total, world, usecs)
 
     # ---- end to end through the host-buffer entry point --------------------------------
     e2e = None
@@ -879,13 +887,10 @@ def e2e_run(torch, P, mats, passes_host, args, local_rank, barrier, dist, dev):
     torch.cuda.synchronize()
     secs = time.perf_counter() - t
     barrier()
-    if dist is not None:
-        tt = torch.tensor([secs], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        secs = float(tt.item())
+    secs = max_over_ranks(torch, dist, secs, dev)
     world = dist.get_world_size() if dist is not None else 1
     cache.close()
-    return {"value": round(n * SPP * args.steps * world / secs, 1), "unit": UNIT,
+    return {"value": round(whole_job_rate(n * SPP * args.steps, world, secs), 1), "unit": UNIT,
             "h2d_bytes_per_step": int(SPP * n * 36), "d2h_bytes_per_step": int(SPP * n * (12 + 2))}
 
 
