@@ -45,7 +45,11 @@ REF_ROWS = (0, 16)               # reference arm: 16 full-width rows per step, a
 NCU_TRAFFIC = {"eval": 313.0e6, "eval_roots": 182.1e6, "lookup": 1050.1e6}
 
 FP32_LANES_PER_SM = 128          # Blackwell SM: 4 partitions x 32 FP32 lanes
-N_SMS = 152
+
+
+def n_sms(torch, dev):
+    """Streaming multiprocessors of the device, as the driver reports them."""
+    return int(torch.cuda.get_device_properties(torch.device(dev)).multi_processor_count)
 
 
 def workload(seed=0):
@@ -262,7 +266,7 @@ def ours(args, rank, world, local_rank, dist):
     per_launch_ms = {k: v / max(1, timing["batches"]) for k, v in ms.items()}
     # the first pass of a frame runs on an empty table: no lookup launch
     per_launch_ms["lookup"] = ms["lookup"] / max(1, timing["batches"] - args.steps)
-    fp32_peak = N_SMS * FP32_LANES_PER_SM * 2 * sm_mhz_max * 1e6 / 1e12   # TFLOP/s
+    fp32_peak = n_sms(torch, dev) * FP32_LANES_PER_SM * 2 * sm_mhz_max * 1e6 / 1e12   # TFLOP/s
     # FP32 work of the per-point programs (k_eval) and of the batched misses (k_eval_roots)
     flops_missed = frame_stats["flops_missed"]
     flops_eval = frame_stats["flops"] - flops_missed
@@ -503,7 +507,7 @@ def raycast_leg(torch, P, mats, dev, local_rank, seed=0):
     # 12 per plane, 24 per sphere, about 105 for the ray, the shading point and the cone
     n_planes = int((sc.objects["kind"] == W.KIND_PLANE).sum())
     flops_ray = 12 * n_planes + 24 * (len(sc.objects) - n_planes) + 105
-    fp32_peak = N_SMS * FP32_LANES_PER_SM * 2 * sm_mhz_max * 1e6 / 1e12
+    fp32_peak = n_sms(torch, dev) * FP32_LANES_PER_SM * 2 * sm_mhz_max * 1e6 / 1e12
     tflops = flops_ray * n * SPP / cast_s / 1e12
     res = {"config": f"room of 6 planes + 24 spheres, 64 materials, {WIDTH}x{HEIGHT} pinhole, {SPP} passes, "
                      f"table {N_CELLS}x{N_ENTRIES} slots, per-point levels from the ray cones", "unit": UNIT,
@@ -749,7 +753,7 @@ def sweep_leg(torch, P, dev, local_rank, seed=0):
     torch.cuda.synchronize()
     res["surrogate_mix"] = {"slots": 1 << 26, "train_s": round(time.perf_counter() - t, 2),
                             "candidates": int(np.sum(rmse >= 0)),
-                            "enabled": int(np.sum((rmse >= 0) & (rmse <= 2e-3))),
+                            "enabled": int(np.sum((rmse >= 0) & (rmse <= 1.6e-3))),
                             "value": round(rate(c), 1)}
     s = c.stats()
     res["surrogate_mix"]["hit_rate"] = round(s["hits"] / max(1, s["lookups"]), 4)
@@ -778,8 +782,9 @@ def surrogate_leg(torch, P, dev, local_rank, seed=0):
     """Deep networks (256 of 500-2000 nodes, one cacheable node on a low-frequency UV tree
     each) shaded over 64 passes of 1920x1080 points: exact without cache, exact with the
     cache, and with surrogates trained on 2^20 pairs per network and validated on 2^16
-    (cache on for any other node).  Training time, the fraction of networks within RMSE
-    2e-3 and the median RMSE are reported."""
+    (cache on for any other node).  Training time, the fraction of networks enabled (a
+    validation RMSE of at most 1.6e-3, a margin under the 2e-3 bar) and the median RMSE
+    are reported."""
     mats = W.surrogate_materials(SURR_MATS, SURR_LO, SURR_HI, seed=seed)
     frame = W.Frame(W.FrameSpec(width=WIDTH, height=HEIGHT, n_mats=SURR_MATS, seed=seed + 100))
     passes = [frame.points_torch(p, dev) for p in range(SURR_PASSES)]
@@ -813,7 +818,7 @@ def surrogate_leg(torch, P, dev, local_rank, seed=0):
     res["train_pairs_per_network"] = SURR_TRAIN
     res["epochs"] = SURR_EPOCHS
     res["valid_pairs_per_network"] = SURR_VALID
-    res["within_2e-3"] = round(float(np.mean((rmse >= 0) & (rmse <= 2e-3))), 4)
+    res["enabled_fraction"] = round(float(np.mean((rmse >= 0) & (rmse <= 1.6e-3))), 4)
     res["rmse_median"] = float(np.median(rmse[rmse >= 0])) if np.any(rmse >= 0) else None
     res["surrogate"] = round(run(cached), 1)
     # tensor-core roofline of the in-pass inference (k_surrogate_tc): with one cacheable node
@@ -853,6 +858,7 @@ def surrogate_leg(torch, P, dev, local_rank, seed=0):
     res["unit"] = UNIT
     res["speedup_surrogate_over_uncached"] = round(res["surrogate"] / res["uncached"], 2)
     res["speedup_cached_over_uncached"] = round(res["cached"] / res["uncached"], 2)
+    res["speedup_surrogate_over_cached"] = round(res["surrogate"] / res["cached"], 2)
     return res
 
 

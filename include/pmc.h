@@ -74,7 +74,14 @@ typedef struct pmc_cache pmc_cache;
  *                                  0.5 + sum_k gain^k noise(scale lac^k (x,y); seed+k) / sum_k gain^k
  *  PMC_OP_VORONOI   in0 (x, y)     fp0 scale, ip1 seed   Worley F1 at scale (x, y)
  *  PMC_OP_CHECKER   in0 (x, y)     fp0 scale, fp1..3 colour A, fp4..6 colour B
- *                                  A if floor(x s) + floor(y s) is even, else B
+ *                                  A if floor(x s) + floor(y s) is even, else B.
+ *                                  The only discontinuous primitive; so that FP32 and
+ *                                  wider arithmetic agree on the side of every cell edge,
+ *                                  x s must be exact in FP32: in0 is the UV or POSITION
+ *                                  node, or a UV_AFFINE of one of them with fp1 = fp2 =
+ *                                  fp4 = fp5 = 0 and fp0, fp3 powers of two, and s is a
+ *                                  power of two, every power in [2^-20, 2^20].  A network
+ *                                  breaking this is rejected (PMC_ERR_INVALID_ARG)
  *  PMC_OP_RAMP      in0 (x)        ip0 stops (2..4), fp0..3 positions (ascending, in [0,1]),
  *                                  fp4.. colours (3 per stop); piecewise linear, constant outside
  *  PMC_OP_MIX       in0 a, in1 b, in2 f (optional; fp0 if -1)   a + (b - a) clamp(f.x, 0, 1)
@@ -295,7 +302,7 @@ pmc_status pmc_slot_classes(pmc_cache* cache, uint8_t* host_dst, size_t bytes);
  * memory, n entries, original point order): bit r set when the point's r-th
  * cacheable node (ascending node ID, r < 64) was found in the table.  Returns
  * PMC_ERR_UNSUPPORTED after a batch that kept no probe records (PMC_UNSORTED or
- * PMC_PROBE_INLINE schedules). */
+ * PMC_PROBE_INLINE schedules) or a pmc_eval_batch_noalloc pass. */
 pmc_status pmc_last_hit_masks(pmc_cache* cache, uint64_t* host_dst, uint64_t n);
 
 /* Empties the table and clears the counters (enqueued on `stream`). */
@@ -374,7 +381,9 @@ typedef struct {
     uint32_t n_valid;   /* held-out pairs per material for the validation RMSE, >= 1   */
     uint32_t epochs;    /* passes over the training pairs, >= 1                        */
     float lr;           /* initial Adam step size (cosine decay to 5 %); 0 = 1e-2        */
-    float rmse_max;     /* enable a network only if its validation RMSE <= this; 0 = 2e-3 */
+    float rmse_max;     /* enable a network only if its validation RMSE <= this; 0 = 1.6e-3,
+                           a margin under the accuracy bar of 2e-3 (RMSE against exact
+                           values) so that points the validation did not see stay within it */
     uint64_t seed;      /* training and validation (u, v) come from SplitMix64(seed, ...) */
     const uint32_t* mats; /* host: materials to train; NULL = every material with a candidate */
     uint32_t n_mats;
@@ -450,7 +459,9 @@ pmc_status pmc_mlp_train(float* theta, float* adam_m, float* adam_v, const float
  * call's contents; each call clears what must start at zero.  Calls whose work can
  * overlap on the GPU (unordered streams, concurrent host threads) race on the array
  * and corrupt each other's results: order them on one stream.  pmc_set_timing does
- * not time these calls and pmc_last_hit_masks does not describe them. */
+ * not time these calls; pmc_last_hit_masks after one returns PMC_ERR_UNSUPPORTED.
+ * pmc_cache_desc.probe_capacity binds as in pmc_eval_batch (a batch needing more probe
+ * records than it does no work; the next pmc_sync reports PMC_ERR_UNSUPPORTED). */
 #define PMC_NOALLOC_MAX_POINTS 8192u
 #define PMC_NOALLOC_MAX_PROBES 32768u
 #define PMC_NOALLOC_MAX_MATERIALS 4096u

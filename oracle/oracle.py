@@ -56,6 +56,10 @@ def lib():
         L.orc_hash1.argtypes = [u64]
         L.orc_hash2.restype = u32
         L.orc_hash2.argtypes = [u64]
+        L.orc_address_batch.restype = None
+        L.orc_address_batch.argtypes = [vp, vp, vp, vp, u64, u32, u64, vp, vp, vp]
+        L.orc_mix_batch.restype = None
+        L.orc_mix_batch.argtypes = [vp, u64, vp, vp]
         L.orc_validate.restype = C.c_int
         L.orc_validate.argtypes = [vp, u32]
         L.orc_analyze.restype = C.c_int
@@ -94,6 +98,8 @@ def lib():
         L.orc_cache_set_alg1.argtypes = [vp, C.c_int]
         L.orc_cache_set_replacement.restype = None
         L.orc_cache_set_replacement.argtypes = [vp, C.c_int]
+        L.orc_cache_set_close_at_lookup.restype = None
+        L.orc_cache_set_close_at_lookup.argtypes = [vp, C.c_int]
         L.orc_cache_classes.restype = None
         L.orc_cache_classes.argtypes = [vp, vp]
         L.orc_rgb9e5_encode.restype = u32
@@ -144,6 +150,30 @@ def rgb9e5_decode(code):
     return out
 def hash1(k): return lib().orc_hash1(k)
 def hash2(k): return lib().orc_hash2(k)
+
+
+def address_batch(mat, node, u, v, level, n_cells):
+    """(key uint64[n], cell uint64[n], h2 uint32[n]) of n (material, node, u, v) tuples."""
+    mat = np.ascontiguousarray(mat, dtype=np.uint32)
+    node = np.ascontiguousarray(node, dtype=np.uint32)
+    u = np.ascontiguousarray(u, dtype=np.float32)
+    v = np.ascontiguousarray(v, dtype=np.float32)
+    n = len(mat)
+    key = np.zeros(max(n, 1), dtype=np.uint64)
+    cell = np.zeros(max(n, 1), dtype=np.uint64)
+    h2 = np.zeros(max(n, 1), dtype=np.uint32)
+    lib().orc_address_batch(_ptr(mat), _ptr(node), _ptr(u), _ptr(v), n, level, n_cells,
+                            _ptr(key), _ptr(cell), _ptr(h2))
+    return key[:n], cell[:n], h2[:n]
+
+
+def mix_batch(keys):
+    """(SplitMix64 output function, fmix64 of key xor 0x9E3779B97F4A7C15) of n keys."""
+    k = np.ascontiguousarray(keys, dtype=np.uint64)
+    h1 = np.zeros(max(len(k), 1), dtype=np.uint64)
+    m2 = np.zeros(max(len(k), 1), dtype=np.uint64)
+    lib().orc_mix_batch(_ptr(k), len(k), _ptr(h1), _ptr(m2))
+    return h1[: len(k)], m2[: len(k)]
 
 
 def eval_node(node_row, a=None, b=None, c=None, sp=(0.0,) * 8):
@@ -205,7 +235,7 @@ class Cache:
 
     def __init__(self, materials, n_cells, n_entries, level=10, min_root_nodes=2,
                  cache_off=False, hash_hook=None, level_offset=0, alg1=False, replacement=False,
-                 pos_level=-1):
+                 pos_level=-1, close_at_lookup=True):
         self._mats = [_nodes(m) for m in materials]
         self.n_cells, self.n_entries, self.level = n_cells, n_entries, level
         self.off = bool(cache_off) or n_cells == 0 or n_entries == 0
@@ -220,6 +250,7 @@ class Cache:
         lib().orc_cache_set_level_offset(self._h, int(level_offset))
         lib().orc_cache_set_alg1(self._h, int(alg1))
         lib().orc_cache_set_replacement(self._h, int(replacement))
+        lib().orc_cache_set_close_at_lookup(self._h, int(close_at_lookup))
         self._hook = None
         if hash_hook is not None:
             def _cb(k, nc, cell, h2):

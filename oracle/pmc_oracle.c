@@ -332,6 +332,28 @@ uint32_t orc_hash2(uint64_t key) {
     return h == 0 ? 1u : h;
 }
 
+/* Descriptor, cell and check value (Sec. 3.1; Alg. 1) of n (material, node, u, v) tuples
+ * at one level: a loop over orc_key, orc_hash1 mod n_cells and orc_hash2, for comparisons
+ * over many tuples. */
+void orc_address_batch(const uint32_t* mat, const uint32_t* node, const float* u, const float* v,
+                       uint64_t n, uint32_t level, uint64_t n_cells, uint64_t* key, uint64_t* cell,
+                       uint32_t* h2) {
+    for (uint64_t i = 0; i < n; ++i) {
+        key[i] = orc_key(mat[i], node[i], level, u[i], v[i]);
+        cell[i] = orc_hash1(key[i]) % n_cells;
+        h2[i] = orc_hash2(key[i]);
+    }
+}
+
+/* The two 64-bit mixers behind Hash and Hash2 over n keys: h1 = SplitMix64's output
+ * function of the key, m2 = fmix64(key xor golden gamma), whose upper half is Hash2. */
+void orc_mix_batch(const uint64_t* key, uint64_t n, uint64_t* h1, uint64_t* m2) {
+    for (uint64_t i = 0; i < n; ++i) {
+        h1[i] = orc_splitmix64_mix(key[i]);
+        m2[i] = orc_fmix64(key[i] ^ 0x9E3779B97F4A7C15ull);
+    }
+}
+
 /* ========================================================================== */
 /* Network analysis (Sec. 3)                                                  */
 /* ========================================================================== */
@@ -352,6 +374,30 @@ static int n_required_inputs(uint32_t op, int* optional) {
     default:
         return -1;
     }
+}
+
+/* x is 2^e with -20 <= e <= 20. */
+static int power_of_two_scale(float x) {
+    int e;
+    const double m = frexp((double)x, &e);
+    return m == 0.5 && e - 1 >= -20 && e - 1 <= 20;
+}
+
+/* The checker is the one discontinuous primitive: its colour flips where x s or y s
+ * crosses an integer, so FP32 and FP64 may disagree by a whole colour next to an edge
+ * unless the argument is exact in FP32.  It is when x and y come from the UV or the
+ * position input, either directly or through an affine map that only scales each axis by
+ * a power of two (no rotation, no offset), and s is a power of two: every product is then
+ * a power-of-two scaling, exact for any input of magnitude 0 or at least 2^-100. */
+static int exact_checker(const orc_node* nodes, const orc_node* nd) {
+    if (!power_of_two_scale(nd->fp[0])) return 0;
+    const orc_node* src = &nodes[nd->in[0]];
+    if (src->op == ORC_UV || src->op == ORC_POSITION) return 1;
+    if (src->op != ORC_UV_AFFINE) return 0;
+    const uint32_t in = nodes[src->in[0]].op;
+    const float* a = src->fp;
+    return (in == ORC_UV || in == ORC_POSITION) && power_of_two_scale(a[0]) && power_of_two_scale(a[3]) &&
+           a[1] == 0.0f && a[2] == 0.0f && a[4] == 0.0f && a[5] == 0.0f;
 }
 
 int orc_validate(const orc_node* nodes, uint32_t n) {
@@ -381,6 +427,7 @@ int orc_validate(const orc_node* nodes, uint32_t n) {
             }
         }
         if (nd->op == ORC_POW && !(nd->fp[0] > 0.0f)) return ORC_ERR_ARG;
+        if (nd->op == ORC_CHECKER && !exact_checker(nodes, nd)) return ORC_ERR_ARG;
     }
     return ORC_OK;
 }
@@ -513,6 +560,9 @@ struct orc_cache {
     int32_t level_offset;  /* added to the ray-cone level (Sec. 4) */
     int alg1;              /* the paper's concurrent update, serialised point by point */
     int replace;           /* replacement by visibility class (Sec. 5), else keep-first */
+    int close_at_lookup;   /* replacement: drop a value as full at lookup when its full cell
+                              holds no class larger than its own (1, the default); 0 = let
+                              every such value reach the sequential insert */
     int32_t pos_level;     /* world-position descriptor: voxels of 2^-pos_level; -1 = off */
     uint32_t min_root_nodes;
     int off;
@@ -539,6 +589,7 @@ orc_cache* orc_cache_new(uint64_t n_cells, uint32_t n_entries, uint32_t level,
     c->rgb = (float*)calloc(slots ? 3 * slots : 1, sizeof(float));
     c->cls = (uint8_t*)calloc(slots ? slots : 1, 1);
     c->pos_level = -1;
+    c->close_at_lookup = 1;
     return c;
 }
 
@@ -598,6 +649,8 @@ void orc_cache_set_level_offset(orc_cache* c, int32_t offset) { c->level_offset 
 void orc_cache_set_alg1(orc_cache* c, int on) { c->alg1 = on != 0; }
 
 void orc_cache_set_replacement(orc_cache* c, int on) { c->replace = on != 0; }
+
+void orc_cache_set_close_at_lookup(orc_cache* c, int on) { c->close_at_lookup = on != 0; }
 
 void orc_cache_set_position_level(orc_cache* c, int32_t level) { c->pos_level = level; }
 
@@ -828,7 +881,7 @@ int orc_run_batch(orc_cache* c, uint64_t n, const float* u, const float* v,
                 /* Replacement: a cell that is full of entries whose classes are all at most
                  * the point's own can never take its value in this batch (classes in a
                  * full cell only decrease), so the value is dropped as full at lookup. */
-                if (sc < 0 && c->replace) {
+                if (sc < 0 && c->replace && c->close_at_lookup) {
                     const uint8_t q = vis ? vis[i] : 0;
                     uint8_t mx = 0;
                     for (uint32_t e = 0; e < c->n_entries; ++e)

@@ -112,6 +112,13 @@ uint32_t orc_voxel(float p, uint32_t level);
 uint64_t orc_key_pos(uint32_t mat, uint32_t node, uint32_t level, float px, float py, float pz);
 uint64_t orc_hash1(uint64_t key);
 uint32_t orc_hash2(uint64_t key);
+/* Loops over the functions above: descriptor, cell (Hash mod n_cells) and check value of n
+ * (material, node, u, v) tuples at one level; and the two 64-bit mixers (SplitMix64's
+ * output function, fmix64 of key xor 0x9E3779B97F4A7C15) of n keys. */
+void orc_address_batch(const uint32_t* mat, const uint32_t* node, const float* u, const float* v,
+                       uint64_t n, uint32_t level, uint64_t n_cells, uint64_t* key, uint64_t* cell,
+                       uint32_t* h2);
+void orc_mix_batch(const uint64_t* key, uint64_t n, uint64_t* h1, uint64_t* m2);
 
 /* ---- network analysis (Sec. 3) ------------------------------------------- */
 /* Validates the network and fills cls[n] (ORC_CLS_*), is_root[n] (0/1).
@@ -162,6 +169,12 @@ void orc_cache_set_alg1(orc_cache* c, int on);
  * full there and then, even if a copy of its key with a smaller class enters the cell
  * earlier in the batch.  With every class 0 the table evolves exactly as with keep-first. */
 void orc_cache_set_replacement(orc_cache* c, int on);
+/* Replacement only: on (the default) = the rule above, a value whose full cell holds no
+ * class larger than its own is dropped as full at lookup; off = every evaluated miss goes
+ * to the sequential insert, where such a value is dropped as full or, if a copy of its key
+ * with a smaller class entered the cell earlier in the batch, as a duplicate.  The two
+ * rules leave the same table and classes; only that full/duplicate split differs. */
+void orc_cache_set_close_at_lookup(orc_cache* c, int on);
 /* level >= 0: the world-position descriptor (Sec. 3.1 names world-space position as a
  * further descriptor, Sec. 5 lists it as future work).  A node whose sub-graph depends on
  * the shading point's position and on nothing else of it is cacheable too; its key is

@@ -46,6 +46,7 @@ struct pmc_cache {
     bool table_empty = true;              // nothing inserted since creation or reset
     bool last_all_miss = false;           // the last batch ran on an empty table
     bool last_unsorted = false;           // the last batch kept no probe records
+    bool last_noalloc = false;            // the last batch ran in the fixed no-alloc scratch
     // learned surrogates
     int use_surrogates = 1;
     std::vector<int32_t> surr_cand;       // per material: candidate node ordinal, -1 if none

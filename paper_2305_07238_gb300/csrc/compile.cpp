@@ -47,6 +47,34 @@ int required_inputs(uint32_t op, int* optional) {
     }
 }
 
+uint32_t float_bits(float x) {
+    uint32_t b;
+    std::memcpy(&b, &x, sizeof(b));
+    return b;
+}
+
+// A positive power of two 2^e, -20 <= e <= 20, read off the FP32 bits (no fraction).
+bool pow2_scale(float x) {
+    const uint32_t b = float_bits(x);
+    const uint32_t ex = b >> 23;   // includes the sign bit: a negative x never matches
+    return (b & 0x7FFFFFu) == 0 && ex >= 127 - 20 && ex <= 127 + 20;
+}
+
+// The checker flips colour where x s or y s crosses an integer (the only discontinuous
+// primitive).  FP32 and wider arithmetic take the same side of every edge when the
+// argument is exact in FP32: x and y from the UV or position input, directly or through
+// an affine map that scales each axis by a power of two (no rotation or offset), and s a
+// power of two.
+bool exact_checker(const pmc_node* nodes, const pmc_node& nd) {
+    if (!pow2_scale(nd.fp[0])) return false;
+    const pmc_node& src = nodes[nd.in[0]];
+    if (src.op == PMC_OP_UV || src.op == PMC_OP_POSITION) return true;
+    if (src.op != PMC_OP_UV_AFFINE) return false;
+    const uint32_t in = nodes[src.in[0]].op;
+    return (in == PMC_OP_UV || in == PMC_OP_POSITION) && pow2_scale(src.fp[0]) && pow2_scale(src.fp[3]) &&
+           src.fp[1] == 0.0f && src.fp[2] == 0.0f && src.fp[4] == 0.0f && src.fp[5] == 0.0f;
+}
+
 bool is_input_op(uint32_t op) {
     return op == PMC_OP_UV || op == PMC_OP_POSITION || op == PMC_OP_NORMAL || op == PMC_OP_CONST;
 }
@@ -79,6 +107,11 @@ bool validate(const pmc_node* nodes, uint32_t n, const char** why) {
             }
         }
         if (nd.op == PMC_OP_POW && !(nd.fp[0] > 0.0f)) { *why = "exponent must be > 0"; return false; }
+        if (nd.op == PMC_OP_CHECKER && !exact_checker(nodes, nd)) {
+            *why = "a checker's argument must be exact in FP32: UV or position, directly or scaled per "
+                   "axis by powers of two, times a power-of-two scale in [2^-20, 2^20]";
+            return false;
+        }
     }
     return true;
 }

@@ -1,5 +1,6 @@
 // noalloc.cu -- pmc_eval_batch_noalloc: the per-pass pipeline of pmc_eval_batch with its
 // per-batch scratch in one fixed file-scope device array, so the call allocates nothing.
+#include <algorithm>
 #include <cstdio>
 #include <mutex>
 
@@ -137,7 +138,10 @@ extern "C" pmc_status pmc_eval_batch_noalloc(pmc_cache* c, const pmc_points* pts
     a.cells_pow2_mask = (nc > 1 && (nc & (nc - 1)) == 0) ? (uint32_t)(nc - 1) : 0u;
     a.use_cache = c->use_cache; a.debug = (c->desc.flags & PMC_DEBUG_CHECKS) != 0;
     a.probes = reinterpret_cast<float4*>(base + OFF_PROBES);
-    a.probe_cap = (uint32_t)NA_PROBES;
+    // a stated probe capacity binds here as in pmc_eval_batch: a batch needing more
+    // records does no work and the next synchronising call reports it
+    a.probe_cap = (uint32_t)(c->desc.probe_capacity ? std::min<uint64_t>(c->desc.probe_capacity, NA_PROBES)
+                                                    : NA_PROBES);
     a.cands = reinterpret_cast<Candidate*>(base + OFF_CANDS);
     uint32_t* lists = reinterpret_cast<uint32_t*>(base + OFF_LISTS);
     a.lists[0] = lists; a.lists[1] = lists + NA_PROBES; a.lists[2] = lists + 2 * NA_PROBES;
@@ -172,5 +176,7 @@ extern "C" pmc_status pmc_eval_batch_noalloc(pmc_cache* c, const pmc_points* pts
     if (c->use_cache) c->epoch_host += ne + 1;
     if (n > 0) c->table_empty = false;
     c->last_stream = s;
+    c->last_n = n;
+    c->last_noalloc = true;   // pmc_last_hit_masks refuses this pass (PMC_ERR_UNSUPPORTED)
     return PMC_OK;
 }

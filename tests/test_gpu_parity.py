@@ -103,6 +103,25 @@ def test_keys_cells_hash2_bit_exact(P, n_cells, level):
         assert int(h2[i]) == O.hash2(k)
 
 
+@pytest.mark.parametrize("n_cells", [1 << 21, 10**7])
+def test_keys_cells_hash2_bit_exact_on_2_24_tuples(P, n_cells):
+    """CPU == GPU on 2^24 (material, node, u, v) tuples: descriptor, cell and check value
+    bit for bit (the oracle's loop over its scalar definition against pmc_compute_keys)."""
+    rng = np.random.default_rng(29)
+    n = 1 << 24
+    mat = rng.integers(0, 65536, n, dtype=np.uint32)
+    node = rng.integers(0, 65536, n, dtype=np.uint32)
+    u = rng.uniform(-0.05, 1.05, n).astype(np.float32)
+    v = rng.uniform(-0.05, 1.05, n).astype(np.float32)
+    t = lambda a: torch.from_numpy(a.view(np.int32) if a.dtype == np.uint32 else a).cuda()
+    key, cell, h2 = P.compute_keys(t(mat), t(node), t(u), t(v), 10, n_cells)
+    torch.cuda.synchronize()
+    rk, rc, rh = O.address_batch(mat, node, u, v, 10, n_cells)
+    assert np.array_equal(key.cpu().numpy().view(np.uint64), rk)
+    assert np.array_equal(cell.cpu().numpy().view(np.uint64), rc)
+    assert np.array_equal(h2.cpu().numpy().view(np.uint32), rh)
+
+
 # ---- the tiny 8-node material, 4 passes of 4096 ---------------------------------------------
 def test_tiny_config_cache_on(P):
     mat = W.material_tiny()

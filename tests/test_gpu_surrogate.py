@@ -7,8 +7,14 @@
   BF16-rounded weights and features, relative L2 error <= 2e-2 per parameter group;
 * fit: Adam on a closed-form target reaches RMSE <= 2e-3;
 * pass: trained surrogates inside pmc_eval_batch against the oracle given the same
-  weights; every enabled surrogate within RMSE 2e-3 of the FP64 exact node values;
-  the surrogate pass is faster than exact evaluation of the same deep networks.
+  weights; every enabled surrogate within RMSE 2e-3 of the FP64 exact node values on
+  points its validation did not see (networks are enabled at a validation RMSE of at
+  most 1.6e-3); the surrogate pass is faster than exact evaluation of the same deep
+  networks, with the cache as well as without it.
+
+The judge of a surrogate's accuracy is that RMSE against the FP64 exact values.  The
+forward comparison with the oracle's network is a structural check only: the oracle's
+BF16 mode rounds at the points where the kernels round, so it mirrors their structure.
 """
 import numpy as np
 import pytest
@@ -120,7 +126,8 @@ def test_trained_surrogates_accuracy_vs_fp64(P, trained):
     mats, cache, rmse = trained
     assert np.all(rmse >= 0) and np.all(rmse < 0.05)
     enabled = [m for m in range(len(mats)) if cache.get_surrogate(m, with_theta=False)["enabled"]]
-    assert enabled == [m for m in range(len(mats)) if rmse[m] <= 2e-3]   # the rest fall back
+    # enabled at validation RMSE <= 1.6e-3, a margin under the bar; the rest fall back
+    assert enabled == [m for m in range(len(mats)) if rmse[m] <= 1.6e-3]
     assert len(enabled) >= 5, rmse                  # the deep low-frequency networks fit
     rng = np.random.default_rng(9)
     u, v = rng.random(2000).astype(np.float32), rng.random(2000).astype(np.float32)
@@ -131,7 +138,7 @@ def test_trained_surrogates_accuracy_vs_fp64(P, trained):
                           for uu, vv in zip(u, v)]).T
         pred = P.mlp_forward(_dev(info["theta"]), _dev(u), _dev(v), clamp=True).cpu().numpy()
         err = float(np.sqrt(np.mean((pred - exact) ** 2)))
-        assert err <= 2e-3 * 1.25, (m, err)          # validated within 2e-3 on other points
+        assert err <= 2e-3, (m, err)                 # the bar, against FP64, on unseen points
 
 
 def test_pass_with_surrogates_matches_oracle(P, trained):
@@ -214,3 +221,38 @@ def test_surrogate_pass_beats_exact_evaluation(P, trained):
         torch.cuda.synchronize()
         times[name] = t0.elapsed_time(t1) / 3
     assert times["surrogate"] * 3 <= times["exact"], times
+
+
+def test_surrogate_pass_beats_exact_evaluation_with_the_cache(P, trained):
+    """What the trained networks gain over the method without them: the same deep networks
+    with exact evaluation and the progressive cache, on a warm table, against the pass with
+    the surrogates (frame-coherent 1080p passes; timed passes the warm-up did not see)."""
+    mats, cache, _ = trained
+    deep = [m for m in range(6) if cache.get_surrogate(m, with_theta=False)["enabled"]]
+    sub = [mats[m] for m in deep]
+    frame = W.Frame(W.FrameSpec(width=1920, height=1080, n_mats=len(sub), seed=13))
+    passes = [frame.points_torch(p, "cuda") for p in range(8)]
+    n = 1920 * 1080
+    rgb = torch.empty((3, n), device="cuda")
+    exact = P.Cache(sub, 1 << 19, 8)
+    fast = P.Cache(sub, 1 << 19, 8)
+    for i, m in enumerate(deep):
+        fast.set_surrogate(i, cache.get_surrogate(m)["theta"])
+    times, hit_rate = {}, 0.0
+    for name, c in (("cached", exact), ("surrogate", fast)):
+        for p in range(4):                         # warm the table
+            c.eval_batch(passes[p], rgb)
+        c.sync()
+        before = c.stats()
+        t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        t0.record()
+        for p in range(4, 8):
+            c.eval_batch(passes[p], rgb)
+        t1.record()
+        torch.cuda.synchronize()
+        times[name] = t0.elapsed_time(t1)
+        st = c.stats()
+        if name == "cached":
+            hit_rate = (st["hits"] - before["hits"]) / max(1, st["lookups"] - before["lookups"])
+    assert hit_rate > 0.5, hit_rate                # the cache is doing its job ...
+    assert times["surrogate"] * 1.3 <= times["cached"], (times, hit_rate)   # ... and loses

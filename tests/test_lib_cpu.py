@@ -141,3 +141,17 @@ def test_cast_rays_rejects_bad_arguments(lib):
     bad[7]["p"][3] = 0.0                                                            # zero radius
     assert call(bad, len(bad), mk(16, 8), 0, 0) == P.PMC_ERR_INVALID_ARG
     assert call(objs, len(objs), mk(16, 8), 3, 3) == 0                              # nothing to do
+
+
+def test_checker_exactness_rule_matches_oracle(lib):
+    from .test_oracle_analysis import _checker_net
+    for src, scale in (("uv", 8.0), ("pos", 0.5), ("uv", 3.0), ("uv", 2.0 ** 21), ("affine", 8.0),
+                       ("noise", 8.0), ("uv", 2.0 ** -20), ("scale2", 8.0), ("posid", 4.0), ("offset", 8.0),
+                       ("scale3", 8.0)):
+        net = _checker_net(src, scale)
+        if O.validate(net):
+            P.analyze_material(net)
+        else:
+            with pytest.raises(P.PmcError) as ei:
+                P.analyze_material(net)
+            assert ei.value.status == P.PMC_ERR_INVALID_ARG

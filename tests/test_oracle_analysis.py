@@ -117,3 +117,37 @@ def test_generated_networks_have_roots_and_sp_share():
         assert cls[-1] == SP
         sp_share = np.mean(cls == SP)
         assert 0.05 < sp_share < 0.5
+
+
+def _checker_net(src_op, scale):
+    b = W.Builder()
+    uv = b.add(W.OP_UV)
+    pos = b.add(W.OP_POSITION)
+    src = {"uv": uv, "pos": pos,
+           "affine": b.add(W.OP_UV_AFFINE, [uv], fp=[1.0, 0.1, -0.1, 1.0, 0.3, 0.7]),
+           "offset": b.add(W.OP_UV_AFFINE, [uv], fp=[2.0, 0.0, 0.0, 2.0, 0.5, 0.0]),
+           "scale2": b.add(W.OP_UV_AFFINE, [uv], fp=[4.0, 0.0, 0.0, 0.25, 0.0, 0.0]),
+           "scale3": b.add(W.OP_UV_AFFINE, [uv], fp=[3.0, 0.0, 0.0, 1.0, 0.0, 0.0]),
+           "posid": b.add(W.OP_UV_AFFINE, [pos], fp=[1.0, 0.0, 0.0, 1.0, 0.0, 0.0]),
+           "noise": b.add(W.OP_FBM, [uv], ip=[2, 3], fp=[4.0, 2.0, 0.5])}[src_op]
+    b.add(W.OP_CHECKER, [src], fp=[scale, 1, 0, 0, 0, 1, 0])
+    return b.build()
+
+
+@pytest.mark.parametrize("src,scale,ok", [
+    ("uv", 8.0, True), ("uv", 1.0, True), ("pos", 0.5, True), ("uv", 2.0 ** 20, True),
+    ("uv", 2.0 ** -20, True),
+    ("uv", 3.0, False),            # x s rounds in FP32: a point near an edge may flip
+    ("uv", 2.0 ** 21, False), ("uv", 2.0 ** -21, False), ("uv", -8.0, False), ("uv", 0.0, False),
+    ("scale2", 8.0, True), ("posid", 4.0, True),   # per-axis power-of-two scalings are exact
+    ("affine", 8.0, False),        # a rotated, offset image of UV is rounded in FP32
+    ("offset", 8.0, False),        # so is an offset one
+    ("scale3", 8.0, False),        # and one scaled by 3
+    ("noise", 8.0, False),         # and a noise value
+])
+def test_checker_argument_must_be_exact(src, scale, ok):
+    """The checker flips colour where x s or y s crosses an integer, so FP32 and FP64 can
+    disagree by a whole colour near an edge unless x s is exact in both: x from the UV or
+    position input itself and s a power of two (within a range where x s cannot leave
+    FP32's exponent range for a UV or a position)."""
+    assert O.validate(_checker_net(src, scale)) == ok

@@ -60,3 +60,66 @@ def test_cell_is_hash1_mod_cells():
         for nc in (10, 8192, 10**7):
             assert O.hash1(k) % nc < nc
     assert O.hash2(0x0000_0007_2800_0000) != 0
+
+
+def _inverse_xorshift(y, s):
+    # x ^ (x >> s) inverted by repeated substitution (s >= 1, 64-bit words)
+    x = y.copy()
+    for _ in range(64 // s + 1):
+        x = y ^ (x >> np.uint64(s))
+    return x
+
+
+def test_mixers_are_bijections_on_random_keys():
+    """Hash and the mixer behind Hash2 are bijections of 64-bit words: no two of 2^20
+    random keys collide, and the published steps undone one by one (xor-shifts and odd
+    multipliers are invertible mod 2^64) give every key back."""
+    rng = np.random.default_rng(17)
+    keys = np.unique(rng.integers(0, 2**63, size=1 << 20, dtype=np.uint64) * np.uint64(2)
+                     + rng.integers(0, 2, size=1 << 20, dtype=np.uint64))
+    h1, m2 = O.mix_batch(keys)
+    assert len(np.unique(h1)) == len(keys)
+    assert len(np.unique(m2)) == len(keys)
+    M = 1 << 64
+    with np.errstate(over="ignore"):
+        # SplitMix64 output function: z ^= z >> 30; z *= c1; z ^= z >> 27; z *= c2; z ^= z >> 31
+        inv = lambda c: np.uint64(pow(c, -1, M))
+        x = _inverse_xorshift(h1, 31) * inv(0x94D049BB133111EB)
+        x = _inverse_xorshift(x, 27) * inv(0xBF58476D1CE4E5B9)
+        x = _inverse_xorshift(x, 30)
+        assert np.array_equal(x, keys)
+        # fmix64: k ^= k >> 33; k *= c1; k ^= k >> 33; k *= c2; k ^= k >> 33
+        y = _inverse_xorshift(m2, 33) * inv(0xC4CEB9FE1A85EC53)
+        y = _inverse_xorshift(y, 33) * inv(0xFF51AFD7ED558CCD)
+        y = _inverse_xorshift(y, 33) ^ np.uint64(0x9E3779B97F4A7C15)
+        assert np.array_equal(y, keys)
+
+
+def test_mixers_avalanche():
+    """Flipping one key bit flips about half of the output bits, for every input bit and
+    every output bit (strict avalanche, within sampling error over 4096 keys)."""
+    rng = np.random.default_rng(19)
+    keys = rng.integers(0, 2**63, size=4096, dtype=np.uint64)
+    h1, m2 = O.mix_batch(keys)
+    for base in (h1, m2):
+        frac = np.zeros((64, 64))
+        for b in range(64):
+            f1, f2 = O.mix_batch(keys ^ np.uint64(1 << b))
+            diff = base ^ (f1 if base is h1 else f2)
+            bits = (diff[:, None] >> np.arange(64, dtype=np.uint64)) & np.uint64(1)
+            frac[b] = bits.mean(axis=0)
+        assert abs(frac.mean() - 0.5) < 0.005
+        assert frac.min() > 0.42 and frac.max() < 0.58
+
+
+def test_address_batch_is_the_scalar_definition():
+    rng = np.random.default_rng(23)
+    n = 2000
+    mat = rng.integers(0, 1 << 16, n, dtype=np.uint32)
+    node = rng.integers(0, 1 << 16, n, dtype=np.uint32)
+    u = rng.random(n).astype(np.float32)
+    v = rng.random(n).astype(np.float32)
+    key, cell, h2 = O.address_batch(mat, node, u, v, 10, 10**7)
+    for i in range(0, n, 97):
+        k = O.key(int(mat[i]), int(node[i]), 10, float(u[i]), float(v[i]))
+        assert key[i] == k and cell[i] == O.hash1(k) % 10**7 and h2[i] == O.hash2(k)

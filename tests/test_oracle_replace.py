@@ -32,10 +32,11 @@ def _h2(t):
     return (t << 13) + 1
 
 
-def _one_cell(n_entries, replacement=True):
+def _one_cell(n_entries, replacement=True, close_at_lookup=True):
     mat = W.material_tiny()
     hook = lambda k, nc: (0, (k & 0xFFFFFF) + 1)
-    return O.Cache([mat], 1, n_entries, hash_hook=hook, replacement=replacement)
+    return O.Cache([mat], 1, n_entries, hash_hook=hook, replacement=replacement,
+                   close_at_lookup=close_at_lookup)
 
 
 def _cell(c):
@@ -218,3 +219,48 @@ def test_cache_off_and_first_pass_outputs_unchanged(n_entries):
     a = O.Cache(mats, 8, n_entries, replacement=True).run_batch(pts)
     b = O.Cache(mats, 8, n_entries).run_batch(pts)
     assert np.array_equal(a["rgb"], b["rgb"])
+
+
+def test_closing_a_full_cell_at_lookup_changes_only_the_full_duplicate_split():
+    """Dropping a value as full at lookup when its full cell holds no class larger than its
+    own (the rule the CUDA path uses) against sending every evaluated miss to the sequential
+    insert: the same cells, values and classes after every pass, hand cases where the
+    accounting differs, and random passes where nothing but that split may differ."""
+    # hand case: the cell holds class 1; the first copy (class 0) of texel 6 evicts it, the
+    # second copy (class 1, later point) finds its key there.  Closed at lookup it is a full
+    # drop (class 1 <= 1 at lookup); sent to the insert it is a duplicate.
+    split = {}
+    for close in (True, False):
+        c = _one_cell(1, close_at_lookup=close)
+        c.run_batch(_texel_points([0], [1]))
+        c.run_batch(_texel_points([6, 6], [0, 1]))
+        assert _cell(c) == ([_h2(6)], [0])
+        st = c.stats()
+        split[close] = (st["replaced"], st["dropped_dup"], st["dropped_full"])
+    assert split[True] == (1, 0, 1) and split[False] == (1, 1, 0)
+    # a value closed at lookup whose key never enters the cell: a full drop either way
+    for close in (True, False):
+        c = _one_cell(2, close_at_lookup=close)
+        c.run_batch(_texel_points([0, 1], [0, 1]))
+        c.run_batch(_texel_points([2], [1]))
+        assert _cell(c) == ([_h2(0), _h2(1)], [0, 1])
+        assert c.stats()["dropped_full"] == 1 and c.stats()["dropped_dup"] == 0
+    # random passes: identical tables, classes, outputs and hits after every pass; the
+    # counters agree except for the split between duplicates and full drops
+    mats = W.random_materials(4, 8, 30, 0.2, seed=3)
+    a = O.Cache(mats, 16, 4, replacement=True, close_at_lookup=True)
+    b = O.Cache(mats, 16, 4, replacement=True, close_at_lookup=False)
+    moved = 0
+    for pts in _frame_passes(6, 800, 51):
+        ra, rb = a.run_batch(pts), b.run_batch(pts)
+        assert np.array_equal(ra["rgb"], rb["rgb"]) and np.array_equal(ra["hits"], rb["hits"])
+        assert np.array_equal(a.table()[0], b.table()[0])
+        assert np.array_equal(a.table()[1], b.table()[1])
+        assert np.array_equal(a.classes(), b.classes())
+        sa, sb = a.stats(), b.stats()
+        for k in ("lookups", "hits", "misses", "candidates", "inserted", "replaced"):
+            assert sa[k] == sb[k], k
+        assert sa["dropped_dup"] + sa["dropped_full"] == sb["dropped_dup"] + sb["dropped_full"]
+        moved = sb["dropped_dup"] - sa["dropped_dup"]
+        assert moved >= 0
+    assert a.stats()["replaced"] > 0

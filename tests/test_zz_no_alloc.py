@@ -67,3 +67,39 @@ def test_noalloc_rejects_batches_beyond_the_fixed_scratch(P):
         cache.eval_batch_noalloc(d, rgb)
     assert ei.value.status == P.PMC_ERR_UNSUPPORTED
     assert cache.stats()["batches"] == 0
+
+
+def test_hit_masks_are_refused_after_a_noalloc_pass(P):
+    """The probe records of a no-alloc pass live in the shared fixed array, so the masks
+    of that pass cannot be read back from the cache; the call says so instead of reading
+    the records of an older pass."""
+    mats = W.random_materials(4, 20, 60, 0.2, seed=5)
+    cache = P.Cache(mats, 1 << 10, 8)
+    n = 2048
+    d = P.points_to_device(W.points_uniform(n, seed=5, n_mats=4))
+    rgb = torch.empty((3, n), dtype=torch.float32, device="cuda")
+    cache.eval_batch(d, rgb)
+    cache.eval_batch(d, rgb)
+    assert cache.last_hit_masks(n).any()
+    cache.eval_batch_noalloc(d, rgb)
+    with pytest.raises(P.PmcError) as ei:
+        cache.last_hit_masks(n)
+    assert ei.value.status == P.PMC_ERR_UNSUPPORTED
+    cache.eval_batch(d, rgb)                # an allocating pass makes them available again
+    assert cache.last_hit_masks(n).any()
+
+
+def test_noalloc_honours_the_probe_capacity(P):
+    """A cache created with a probe capacity below a batch's needs refuses that batch in
+    both entry points alike: no work, PMC_ERR_UNSUPPORTED at the next synchronising call."""
+    mats = W.random_materials(4, 20, 60, 0.2, seed=6)
+    n = 2048
+    d = P.points_to_device(W.points_uniform(n, seed=6, n_mats=4))
+    rgb = torch.empty((3, n), dtype=torch.float32, device="cuda")
+    for fn in ("eval_batch", "eval_batch_noalloc"):
+        cache = P.Cache(mats, 1 << 10, 8, probe_capacity=64)
+        getattr(cache, fn)(d, rgb)
+        with pytest.raises(P.PmcError) as ei:
+            cache.sync()
+        assert ei.value.status == P.PMC_ERR_UNSUPPORTED, fn
+        assert cache.stats(check=False)["lookups"] == 0, fn
