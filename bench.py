@@ -926,6 +926,70 @@ def cpu_baseline(P, torch, mats, frame, dev):
             err)
 
 
+PRIM_POINTS = 1 << 20
+
+
+def primitive_materials():
+    """Single-primitive networks for counting what each node costs on the device: for every
+    primitive a chain of L copies (L = 1 and 9) fed by UV, each copy reading the previous one
+    (two-input primitives read UV as their second input).  A checker must read UV itself,
+    so its copies are joined by MIX nodes (the MIX chain is measured on its own).  With the
+    cache off every node of a chain is evaluated for every point."""
+    B = W.Builder
+    specs = {
+        "FBM1": (W.OP_FBM, dict(ip=[1, 5], fp=[4.0, 2.0, 0.5])),
+        "FBM4": (W.OP_FBM, dict(ip=[4, 5], fp=[4.0, 2.0, 0.5])),
+        "VORONOI": (W.OP_VORONOI, dict(ip=[0, 5], fp=[8.0])),
+        "RAMP4": (W.OP_RAMP, dict(ip=[4], fp=[0.0, 0.3, 0.6, 1.0, 0.1, 0.2, 0.3, 0.4, 0.5, 0.6,
+                                                0.7, 0.8, 0.9, 0.2, 0.4, 0.6])),
+        "MIX": (W.OP_MIX, dict(fp=[0.3])),
+        "ADD": (W.OP_ADD, {}),
+        "MUL": (W.OP_MUL, {}),
+        "POW": (W.OP_POW, dict(fp=[1.5])),
+        "FACING": (W.OP_FACING, dict(fp=[0.6, 0.8, 0.0])),
+        "UV_AFFINE": (W.OP_UV_AFFINE, dict(fp=[0.8, -0.6, 0.6, 0.8, 0.25, 0.5])),
+        "CHECKER": (W.OP_CHECKER, dict(fp=[8.0, 0.1, 0.2, 0.3, 0.9, 0.8, 0.7])),
+    }
+    out = []
+    for name, (op, kw) in specs.items():
+        for L in (1, 9):
+            b = B()
+            uv = b.add(W.OP_UV)
+            prev = uv
+            for _ in range(L):
+                if op == W.OP_CHECKER:
+                    ck = b.add(op, [uv], **kw)
+                    prev = b.add(W.OP_MIX, [prev, ck], fp=[0.3])
+                elif op in (W.OP_ADD, W.OP_MUL, W.OP_MIX):
+                    prev = b.add(op, [prev, uv], **kw)
+                else:
+                    prev = b.add(op, [prev], **kw)
+            out.append((name, L, b.build()))
+    return out
+
+
+def profile_primitives():
+    """One cache-off pass of PRIM_POINTS uniform points per single-primitive network, in the
+    order printed, so that an ncu capture of k_eval gets one launch per (primitive, chain
+    length): the per-node instruction and FP32 operation counts follow from the difference
+    between the 9-copy and 1-copy chains."""
+    import torch
+    from paper_2305_07238_gb300 import build as B
+    from paper_2305_07238_gb300 import pmc as P
+    B.build()
+    pts = P.points_to_device(W.points_uniform(PRIM_POINTS, seed=0))
+    rgb = torch.empty((3, PRIM_POINTS), dtype=torch.float32, device="cuda")
+    rows = []
+    for name, L, mat in primitive_materials():
+        c = P.Cache([mat], 1, 1, flags=P.PMC_CACHE_OFF)
+        c.eval_batch(pts, rgb)
+        st = c.stats()
+        rows.append({"primitive": name, "chain": L, "nodes_per_point": st["nodes_evaluated"] / PRIM_POINTS,
+                     "flops_per_point": st["flops"] / PRIM_POINTS})
+        c.close()
+    return {"profile": "primitives", "points": PRIM_POINTS, "launch_order": rows}
+
+
 def profile_run(args):
     """Eager frames only (default schedule, no autotuning, no graph, no other legs), so
     that an ncu launch list can select whole frames: W warm-up frames, then K frames.
@@ -951,18 +1015,34 @@ def profile_run(args):
         return {"profile": "surrogate passes", "passes": len(passes), "networks": len(mats),
                 "surrogate_evals": cache.stats()["surrogate_evals"], "rmse_median": float(np.median(rmse))}
     mats, frame = workload(seed=0)
-    dev_passes = [P.points_to_device(frame.points(p)) for p in range(SPP)]
+    n_pass = args.profile_passes or SPP
+    dev_passes = [P.points_to_device(frame.points(p)) for p in range(n_pass)]
     n = WIDTH * HEIGHT
     outs = torch.empty((3, n), dtype=torch.float32, device="cuda")
     hits = torch.empty(n, dtype=torch.int16, device="cuda")
-    cache = P.Cache(mats, N_CELLS, N_ENTRIES, uv_level=LEVEL)
+    flags = P.PMC_CACHE_OFF if args.profile_uncached else 0
+    cache = P.Cache(mats, N_CELLS, N_ENTRIES, uv_level=LEVEL, flags=flags)
+
+    def frame_():
+        cache.reset()
+        for p in range(n_pass):
+            cache.eval_batch(dev_passes[p], outs, hits)
+
     for _ in range(args.warmup):
-        run_frame(cache, dev_passes, outs, hits, None)
+        frame_()
     cache.sync()
     cache.read_timing()
-    secs = timed_steps(torch, cache, dev_passes, outs, hits, args.steps, lambda: None)
+    torch.cuda.synchronize()
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t0.record()
+    for _ in range(args.steps):
+        frame_()
+    t1.record()
+    torch.cuda.synchronize()
+    secs = t0.elapsed_time(t1) / 1e3
     launches = cache.read_timing()["launches"]
-    return {"profile": "eager frames", "value": round(n * SPP * args.steps / secs, 1), "unit": UNIT,
+    return {"profile": "eager frames" + (" (cache off)" if args.profile_uncached else ""),
+            "passes_per_frame": n_pass, "value": round(n * n_pass * args.steps / secs, 1), "unit": UNIT,
             "steps": args.steps, "warmup": args.warmup, "launches_per_frame": launches // max(1, args.steps)}
 
 
@@ -1018,7 +1098,16 @@ def main():
                     help="eager frames only, for ncu launch lists (prints launches per frame)")
     ap.add_argument("--profile-surrogate", action="store_true",
                     help="with --profile: passes of 32 networks with surrogates (tensor-core kernel)")
+    ap.add_argument("--profile-passes", type=int, default=0,
+                    help="with --profile: passes per frame (default 16; fewer for small ncu captures)")
+    ap.add_argument("--profile-uncached", action="store_true",
+                    help="with --profile: the same frames with the cache off")
+    ap.add_argument("--profile-primitives", action="store_true",
+                    help="one cache-off pass per single-primitive network (per-node device costs)")
     args = ap.parse_args()
+    if args.profile_primitives:
+        print(json.dumps(profile_primitives()), flush=True)
+        return 0
     if args.profile:
         print(json.dumps(profile_run(args)), flush=True)
         return 0

@@ -202,6 +202,14 @@ typedef struct {
                                 positive values give finer texels (Sec. 4)      */
     uint32_t pos_level;      /* PMC_POSITION_DESCRIPTOR: voxels of 2^-pos_level world
                                 units, 0 .. PMC_MAX_POS_LEVEL (else ignored)       */
+    uint32_t min_root_cost;  /* a cacheable node's sub-graph (the node and every node it
+                                reads, each once, in the network as given) must cost at
+                                least this many FP32 operations of the node cost model
+                                (pmc_node_cost); 0 = no threshold.  A lookup and an insert
+                                cost the same whatever the sub-graph, so caching a cheap
+                                one can cost more than evaluating it (Sec. 3 caches to save
+                                evaluation).  Nodes below the threshold are evaluated
+                                like any other node and never looked up            */
 } pmc_cache_desc;
 
 /* ---- shading points: structure of arrays, n entries each, DEVICE memory ----- *
@@ -324,12 +332,20 @@ pmc_status pmc_analyze_material(const pmc_material* mat, uint32_t min_root_nodes
                                 uint32_t* n_roots, uint32_t* roots, uint32_t cap,
                                 uint32_t* n_instr, uint32_t* n_slots);
 
-/* The same with creation flags: PMC_POSITION_DESCRIPTOR adds the cacheable nodes of
- * position class.  kinds (may be NULL): per cacheable node 1 = UV descriptor, 2 = world-
- * position descriptor.  Needs no GPU. */
-pmc_status pmc_analyze_material_ext(const pmc_material* mat, uint32_t min_root_nodes, uint32_t flags,
-                                    uint32_t* n_roots, uint32_t* roots, uint8_t* kinds, uint32_t cap,
-                                    uint32_t* n_instr, uint32_t* n_slots);
+/* The same with the cost threshold and creation flags of pmc_cache_desc: min_root_cost as
+ * pmc_cache_desc.min_root_cost; PMC_POSITION_DESCRIPTOR adds the cacheable nodes of position
+ * class.  kinds (may be NULL): per cacheable node 1 = UV descriptor, 2 = world-position
+ * descriptor.  Needs no GPU. */
+pmc_status pmc_analyze_material_ext(const pmc_material* mat, uint32_t min_root_nodes, uint32_t min_root_cost,
+                                    uint32_t flags, uint32_t* n_roots, uint32_t* roots, uint8_t* kinds,
+                                    uint32_t cap, uint32_t* n_instr, uint32_t* n_slots);
+
+/* Node cost model: the FP32 operations of one evaluation of `node` (a fused multiply-add
+ * counts 2), counted from the library's formulas: UV, POSITION, NORMAL, CONST 0; UV_AFFINE
+ * 8; FBM 4 + 47 x octaves; VORONOI 99; CHECKER 4; RAMP 23; MIX 17; ADD, MUL 9; POW 18;
+ * FACING 8.  It sets the cost threshold of pmc_cache_desc.min_root_cost and the FP32 work
+ * counted in pmc_stats_t.flops.  Needs no GPU. */
+uint32_t pmc_node_cost(const pmc_node* node);
 
 /* Descriptor and table addressing for n (material, node, u, v) tuples, all DEVICE
  * arrays: key = mat<<48 | node<<32 | level<<26 | iu<<13 | iv with

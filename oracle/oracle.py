@@ -66,6 +66,12 @@ def lib():
         L.orc_analyze.argtypes = [vp, u32, u32, vp, vp, vp]
         L.orc_analyze_desc.restype = C.c_int
         L.orc_analyze_desc.argtypes = [vp, u32, u32, C.c_int, vp, vp, vp]
+        L.orc_analyze_cost.restype = C.c_int
+        L.orc_analyze_cost.argtypes = [vp, u32, u32, u32, C.c_int, vp, vp, vp]
+        L.orc_node_cost.restype = u32
+        L.orc_node_cost.argtypes = [vp]
+        L.orc_cache_set_min_root_cost.restype = None
+        L.orc_cache_set_min_root_cost.argtypes = [vp, u32]
         L.orc_voxel.restype = u32
         L.orc_voxel.argtypes = [C.c_float, u32]
         L.orc_key_pos.restype = u64
@@ -193,7 +199,13 @@ def validate(nodes) -> bool:
     return lib().orc_validate(_ptr(arr), len(arr)) == 0
 
 
-def analyze(nodes, min_root_nodes=2, pos_desc=False, kinds=False):
+def node_cost(node_row) -> int:
+    """The node cost model: FP32 operations of one evaluation of the node."""
+    nd = np.ascontiguousarray(np.atleast_1d(node_row), dtype=NODE_DTYPE)
+    return int(lib().orc_node_cost(_ptr(nd)))
+
+
+def analyze(nodes, min_root_nodes=2, pos_desc=False, kinds=False, min_root_cost=0):
     """Returns (classes int32[n], root node IDs) and, if kinds, the descriptor kind of each
     root (1 = UV, 2 = world position)."""
     arr = _nodes(nodes)
@@ -201,7 +213,8 @@ def analyze(nodes, min_root_nodes=2, pos_desc=False, kinds=False):
     cls = np.zeros(n, dtype=np.int32)
     is_root = np.zeros(n, dtype=np.uint8)
     nr = np.zeros(1, dtype=np.uint32)
-    rc = lib().orc_analyze_desc(_ptr(arr), n, min_root_nodes, int(pos_desc), _ptr(cls), _ptr(is_root), _ptr(nr))
+    rc = lib().orc_analyze_cost(_ptr(arr), n, min_root_nodes, min_root_cost, int(pos_desc), _ptr(cls),
+                                _ptr(is_root), _ptr(nr))
     if rc != 0:
         raise ValueError("malformed network")
     roots = np.nonzero(is_root)[0].astype(np.uint32)
@@ -235,7 +248,7 @@ class Cache:
 
     def __init__(self, materials, n_cells, n_entries, level=10, min_root_nodes=2,
                  cache_off=False, hash_hook=None, level_offset=0, alg1=False, replacement=False,
-                 pos_level=-1, close_at_lookup=True):
+                 pos_level=-1, close_at_lookup=True, min_root_cost=0):
         self._mats = [_nodes(m) for m in materials]
         self.n_cells, self.n_entries, self.level = n_cells, n_entries, level
         self.off = bool(cache_off) or n_cells == 0 or n_entries == 0
@@ -243,6 +256,7 @@ class Cache:
         if not self._h:
             raise ValueError("bad cache description")
         lib().orc_cache_set_position_level(self._h, int(pos_level))
+        lib().orc_cache_set_min_root_cost(self._h, int(min_root_cost))
         ptrs = (C.c_void_p * len(self._mats))(*[m.ctypes.data for m in self._mats])
         counts = np.array([len(m) for m in self._mats], dtype=np.uint32)
         if lib().orc_cache_set_materials(self._h, len(self._mats), ptrs, _ptr(counts)) != 0:

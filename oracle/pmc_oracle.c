@@ -455,17 +455,36 @@ static int join_class(int a, int b) {
     return ORC_CLS_SP;
 }
 
+/* The node cost model of the library's interface: FP32 operations of one evaluation of a
+ * node, a fused multiply-add counted as 2 (UV, POSITION, NORMAL, CONST 0; UV_AFFINE 8; FBM
+ * 4 + 47 per octave; VORONOI 99; CHECKER 4; RAMP 23; MIX 17; ADD and MUL 9; POW 18; FACING 8). */
+uint32_t orc_node_cost(const orc_node* nd) {
+    switch (nd->op) {
+    case ORC_UV_AFFINE: return 8;
+    case ORC_FBM: return 4 + 47 * (uint32_t)nd->ip[0];
+    case ORC_VORONOI: return 99;
+    case ORC_CHECKER: return 4;
+    case ORC_RAMP: return 23;
+    case ORC_MIX: return 17;
+    case ORC_ADD: case ORC_MUL: return 9;
+    case ORC_POW: return 18;
+    case ORC_FACING: return 8;
+    default: return 0;
+    }
+}
+
 /* Dependence classes and cacheable roots.
  *   class(UV input) = UV; class(normal) = SP; class(const) = CONST;
  *   class(position) = POS with the world-position descriptor, else SP;
  *   any other node joins the classes of its inputs (join_class).
  * A node is a cacheable root when it is reachable from the output, has class
  * UV (or POS), is not a bare input, is the output or feeds some SP-class node
- * ("the highest possible level", Sec. 3), and its sub-graph holds at least
- * min_root_nodes nodes that are not inputs or constants.  is_root[i] = 1 for a
+ * ("the highest possible level", Sec. 3), its sub-graph holds at least
+ * min_root_nodes nodes that are not inputs or constants, and the sub-graph's nodes
+ * (each once) cost at least min_root_cost by orc_node_cost.  is_root[i] = 1 for a
  * root with a UV descriptor, 2 for one with a world-position descriptor. */
-int orc_analyze_desc(const orc_node* nodes, uint32_t n, uint32_t min_root_nodes, int pos_desc,
-                     int32_t* cls, uint8_t* is_root, uint32_t* n_roots) {
+int orc_analyze_cost(const orc_node* nodes, uint32_t n, uint32_t min_root_nodes, uint32_t min_root_cost,
+                     int pos_desc, int32_t* cls, uint8_t* is_root, uint32_t* n_roots) {
     if (orc_validate(nodes, n) != ORC_OK) return ORC_ERR_ARG;
     for (uint32_t i = 0; i < n; ++i) {
         const orc_node* nd = &nodes[i];
@@ -499,9 +518,13 @@ int orc_analyze_desc(const orc_node* nodes, uint32_t n, uint32_t min_root_nodes,
         memset(mark, 0, n);
         mark_subgraph(nodes, i, mark);
         uint32_t work = 0;
-        for (uint32_t j = 0; j <= i; ++j)
-            if (mark[j] && !is_input_op(nodes[j].op)) ++work;
-        if (work < min_root_nodes) continue;
+        uint64_t cost = 0;
+        for (uint32_t j = 0; j <= i; ++j) {
+            if (!mark[j]) continue;
+            if (!is_input_op(nodes[j].op)) ++work;
+            cost += orc_node_cost(&nodes[j]);
+        }
+        if (work < min_root_nodes || cost < min_root_cost) continue;
         is_root[i] = cls[i] == ORC_CLS_POS ? 2 : 1;
         ++nr;
     }
@@ -510,6 +533,11 @@ int orc_analyze_desc(const orc_node* nodes, uint32_t n, uint32_t min_root_nodes,
     free(feeds_sp);
     free(mark);
     return ORC_OK;
+}
+
+int orc_analyze_desc(const orc_node* nodes, uint32_t n, uint32_t min_root_nodes, int pos_desc,
+                     int32_t* cls, uint8_t* is_root, uint32_t* n_roots) {
+    return orc_analyze_cost(nodes, n, min_root_nodes, 0, pos_desc, cls, is_root, n_roots);
 }
 
 int orc_analyze(const orc_node* nodes, uint32_t n, uint32_t min_root_nodes,
@@ -565,6 +593,7 @@ struct orc_cache {
                               every such value reach the sequential insert */
     int32_t pos_level;     /* world-position descriptor: voxels of 2^-pos_level; -1 = off */
     uint32_t min_root_nodes;
+    uint32_t min_root_cost;  /* cost threshold of a cacheable node's sub-graph (0 = none) */
     int off;
     uint32_t* h2;  /* n_cells * n_entries, 0 = empty */
     float* rgb;    /* 3 per slot */
@@ -632,7 +661,8 @@ int orc_cache_set_materials(orc_cache* c, uint32_t n_mats, const orc_node* const
         memcpy(M->nodes, mat_nodes[m], n * sizeof(orc_node));
         M->is_root = (uint8_t*)calloc(n, 1);
         int32_t* cls = (int32_t*)malloc(n * sizeof(int32_t));
-        orc_analyze_desc(M->nodes, n, c->min_root_nodes, c->pos_level >= 0, cls, M->is_root, &M->n_roots);
+        orc_analyze_cost(M->nodes, n, c->min_root_nodes, c->min_root_cost, c->pos_level >= 0, cls, M->is_root,
+                         &M->n_roots);
         free(cls);
         M->roots = (uint32_t*)malloc((M->n_roots ? M->n_roots : 1) * sizeof(uint32_t));
         uint32_t r = 0;
@@ -651,6 +681,8 @@ void orc_cache_set_alg1(orc_cache* c, int on) { c->alg1 = on != 0; }
 void orc_cache_set_replacement(orc_cache* c, int on) { c->replace = on != 0; }
 
 void orc_cache_set_close_at_lookup(orc_cache* c, int on) { c->close_at_lookup = on != 0; }
+
+void orc_cache_set_min_root_cost(orc_cache* c, uint32_t cost) { c->min_root_cost = cost; }
 
 void orc_cache_set_position_level(orc_cache* c, int32_t level) { c->pos_level = level; }
 

@@ -130,6 +130,12 @@ int orc_analyze(const orc_node* nodes, uint32_t n, uint32_t min_root_nodes,
  * position and on nothing else of the shading point are cacheable too (is_root 2). */
 int orc_analyze_desc(const orc_node* nodes, uint32_t n, uint32_t min_root_nodes, int pos_desc,
                      int32_t* cls, uint8_t* is_root, uint32_t* n_roots);
+/* The same with a cost threshold: a root's sub-graph (the node and every node it reads,
+ * each once) must cost at least min_root_cost FP32 operations by orc_node_cost. */
+int orc_analyze_cost(const orc_node* nodes, uint32_t n, uint32_t min_root_nodes, uint32_t min_root_cost,
+                     int pos_desc, int32_t* cls, uint8_t* is_root, uint32_t* n_roots);
+/* The node cost model of the library's interface (FP32 operations, a multiply-add as 2). */
+uint32_t orc_node_cost(const orc_node* nd);
 
 /* ---- single shading point, no cache -------------------------------------- */
 /* Plain evaluation of every node reachable from the output. */
@@ -175,6 +181,8 @@ void orc_cache_set_replacement(orc_cache* c, int on);
  * with a smaller class entered the cell earlier in the batch, as a duplicate.  The two
  * rules leave the same table and classes; only that full/duplicate split differs. */
 void orc_cache_set_close_at_lookup(orc_cache* c, int on);
+/* The cost threshold of cacheable nodes (orc_analyze_cost); set it before the materials. */
+void orc_cache_set_min_root_cost(orc_cache* c, uint32_t cost);
 /* level >= 0: the world-position descriptor (Sec. 3.1 names world-space position as a
  * further descriptor, Sec. 5 lists it as future work).  A node whose sub-graph depends on
  * the shading point's position and on nothing else of it is cacheable too; its key is

@@ -210,7 +210,8 @@ pmc_status pmc_create_cache(const pmc_cache_desc* desc, const pmc_material* mats
     for (uint32_t m = 0; m < n_mats; ++m) {
         CompiledMaterial cm;
         const char* why = "";
-        if (!mats[m].nodes || !compile_material(mats[m].nodes, mats[m].n_nodes, min_root, pos_desc, &cm, &why)) {
+        if (!mats[m].nodes ||
+            !compile_material(mats[m].nodes, mats[m].n_nodes, min_root, desc->min_root_cost, pos_desc, &cm, &why)) {
             fprintf(stderr, "pmc: material %u rejected: %s\n", m, why);
             delete c;
             return PMC_ERR_INVALID_ARG;
@@ -712,13 +713,13 @@ pmc_status pmc_material_info(const pmc_cache* c, uint32_t mat, uint32_t* n_roots
     return PMC_OK;
 }
 
-pmc_status pmc_analyze_material_ext(const pmc_material* mat, uint32_t min_root_nodes, uint32_t flags,
-                                    uint32_t* n_roots, uint32_t* roots, uint8_t* kinds, uint32_t cap,
-                                    uint32_t* n_instr, uint32_t* n_slots) {
+pmc_status pmc_analyze_material_ext(const pmc_material* mat, uint32_t min_root_nodes, uint32_t min_root_cost,
+                                    uint32_t flags, uint32_t* n_roots, uint32_t* roots, uint8_t* kinds,
+                                    uint32_t cap, uint32_t* n_instr, uint32_t* n_slots) {
     if (!mat || !mat->nodes) return PMC_ERR_INVALID_ARG;
     CompiledMaterial cm;
     const char* why = "";
-    if (!compile_material(mat->nodes, mat->n_nodes, min_root_nodes ? min_root_nodes : 2u,
+    if (!compile_material(mat->nodes, mat->n_nodes, min_root_nodes ? min_root_nodes : 2u, min_root_cost,
                           (flags & PMC_POSITION_DESCRIPTOR) != 0, &cm, &why))
         return PMC_ERR_INVALID_ARG;
     if (n_roots) *n_roots = (uint32_t)cm.roots.size();
@@ -733,8 +734,10 @@ pmc_status pmc_analyze_material_ext(const pmc_material* mat, uint32_t min_root_n
 
 pmc_status pmc_analyze_material(const pmc_material* mat, uint32_t min_root_nodes, uint32_t* n_roots,
                                 uint32_t* roots, uint32_t cap, uint32_t* n_instr, uint32_t* n_slots) {
-    return pmc_analyze_material_ext(mat, min_root_nodes, 0u, n_roots, roots, nullptr, cap, n_instr, n_slots);
+    return pmc_analyze_material_ext(mat, min_root_nodes, 0u, 0u, n_roots, roots, nullptr, cap, n_instr, n_slots);
 }
+
+uint32_t pmc_node_cost(const pmc_node* node) { return node ? node_cost(*node) : 0u; }
 
 // ---- learned surrogates ------------------------------------------------------------
 namespace {

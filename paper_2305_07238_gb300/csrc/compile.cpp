@@ -285,8 +285,8 @@ uint32_t node_cost(const pmc_node& nd) {
     }
 }
 
-bool compile_material(const pmc_node* nodes_in, uint32_t n, uint32_t min_root_nodes, bool pos_desc,
-                      CompiledMaterial* out, const char** why) {
+bool compile_material(const pmc_node* nodes_in, uint32_t n, uint32_t min_root_nodes, uint32_t min_root_cost,
+                      bool pos_desc, CompiledMaterial* out, const char** why) {
     if (!validate(nodes_in, n, why)) return false;
     std::vector<pmc_node> g(nodes_in, nodes_in + n);
     const uint32_t out_node = n - 1;
@@ -328,13 +328,15 @@ bool compile_material(const pmc_node* nodes_in, uint32_t n, uint32_t min_root_no
         std::fill(mark.begin(), mark.end(), 0);
         mark[i] = 1;
         uint32_t work = 0;
+        uint64_t cost = 0;   // what a hit saves at most: the FP32 operations of the sub-graph
         for (int32_t j = (int32_t)i; j >= 0; --j) {
             if (!mark[j]) continue;
             if (!is_input_op(g[j].op)) ++work;
+            cost += node_cost(g[j]);
             for (int k = 0; k < 4; ++k)
                 if (g[j].in[k] >= 0) mark[g[j].in[k]] = 1;
         }
-        if (work >= min_root_nodes) is_root[i] = 1;
+        if (work >= min_root_nodes && cost >= min_root_cost) is_root[i] = 1;
     }
     out->roots.clear();
     out->root_pos.clear();

@@ -78,10 +78,13 @@ struct CompiledMaterial {
 };
 
 // Compiles one network.  Returns false (with a reason) for a malformed network.
-bool compile_material(const pmc_node* nodes, uint32_t n, uint32_t min_root_nodes, bool pos_desc,
-                      CompiledMaterial* out, const char** why);
+// min_root_cost: a cacheable node's sub-graph must cost at least this many FP32 operations
+// of the node cost model (node_cost), summed over the network as given; 0 = no threshold.
+bool compile_material(const pmc_node* nodes, uint32_t n, uint32_t min_root_nodes, uint32_t min_root_cost,
+                      bool pos_desc, CompiledMaterial* out, const char** why);
 
-// FP32 flops of one executed node (FMA counted as 2), from the device formulas.
+// FP32 flops of one executed node (FMA counted as 2), from the device formulas: the node
+// cost model of include/pmc.h (pmc_node_cost).
 uint32_t node_cost(const pmc_node& nd);
 
 // ---- insert candidates -----------------------------------------------------------------

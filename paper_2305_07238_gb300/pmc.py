@@ -38,6 +38,7 @@ EXPORTED = (
     "pmc_get_surrogate", "pmc_use_surrogates", "pmc_mlp_forward", "pmc_mlp_gradient", "pmc_mlp_train",
     "pmc_get_schedule", "pmc_set_schedule", "pmc_graph_create", "pmc_graph_launch", "pmc_graph_destroy",
     "pmc_autotune", "pmc_status_str", "pmc_slot_classes", "pmc_analyze_material_ext", "pmc_cast_rays",
+    "pmc_node_cost",
 )
 NOALLOC_MAX_POINTS, NOALLOC_MAX_PROBES, NOALLOC_MAX_MATERIALS = 8192, 32768, 4096
 PHASES = ("sort", "lookup", "missed", "eval", "insert", "finish")
@@ -60,7 +61,8 @@ class _Material(C.Structure):
 class _Desc(C.Structure):
     _fields_ = [("n_cells", C.c_uint64), ("n_entries", C.c_uint32), ("uv_level", C.c_uint32),
                 ("flags", C.c_uint32), ("min_root_nodes", C.c_uint32), ("device", C.c_int),
-                ("probe_capacity", C.c_uint64), ("level_offset", C.c_int32), ("pos_level", C.c_uint32)]
+                ("probe_capacity", C.c_uint64), ("level_offset", C.c_int32), ("pos_level", C.c_uint32),
+                ("min_root_cost", C.c_uint32)]
 
 
 class _Schedule(C.Structure):
@@ -130,7 +132,9 @@ def load():
     L.pmc_material_info.restype = st
     L.pmc_analyze_material.argtypes = [vp, u32, vp, vp, u32, vp, vp]
     L.pmc_analyze_material.restype = st
-    L.pmc_analyze_material_ext.argtypes = [vp, u32, u32, vp, vp, vp, u32, vp, vp]
+    L.pmc_analyze_material_ext.argtypes = [vp, u32, u32, u32, vp, vp, vp, u32, vp, vp]
+    L.pmc_node_cost.argtypes = [vp]
+    L.pmc_node_cost.restype = u32
     L.pmc_analyze_material_ext.restype = st
     L.pmc_compute_keys.argtypes = [vp, vp, vp, vp, u64, u32, u64, vp, vp, vp, vp]
     L.pmc_compute_keys.restype = st
@@ -231,7 +235,7 @@ class Cache:
     """A cache object of libpmc: compiled materials + a table of n_cells x n_entries slots."""
 
     def __init__(self, materials, n_cells, n_entries, uv_level=10, flags=0, min_root_nodes=2, device=0,
-                 probe_capacity=0, level_offset=0, pos_level=0):
+                 probe_capacity=0, level_offset=0, pos_level=0, min_root_cost=0):
         L = load()
         self._mats = [np.ascontiguousarray(m, dtype=NODE_DTYPE) for m in materials]
         arr = (_Material * len(self._mats))()
@@ -239,7 +243,7 @@ class Cache:
             arr[i].n_nodes = len(m)
             arr[i].nodes = m.ctypes.data
         desc = _Desc(n_cells, n_entries, uv_level, flags, min_root_nodes, device, probe_capacity, level_offset,
-                     pos_level)
+                     pos_level, min_root_cost)
         h = C.c_void_p()
         _check(L.pmc_create_cache(C.byref(desc), arr, len(self._mats), C.byref(h)), "pmc_create_cache")
         self._h = h
@@ -512,7 +516,13 @@ def mlp_train(theta, adam_m, adam_v, data, steps, step0, total_steps, lr, stream
     return loss
 
 
-def analyze_material(nodes, min_root_nodes=2, flags=0) -> dict:
+def node_cost(node_row) -> int:
+    """The library's node cost model: FP32 operations of one evaluation of the node."""
+    m = np.ascontiguousarray(np.atleast_1d(node_row), dtype=NODE_DTYPE)
+    return int(load().pmc_node_cost(m.ctypes.data))
+
+
+def analyze_material(nodes, min_root_nodes=2, flags=0, min_root_cost=0) -> dict:
     """Host-only compile of one network: cacheable nodes (and their descriptor kinds, 1 = UV,
     2 = world position), program length, slots."""
     m = np.ascontiguousarray(nodes, dtype=NODE_DTYPE)
@@ -520,7 +530,8 @@ def analyze_material(nodes, min_root_nodes=2, flags=0) -> dict:
     nr, ni, ns = C.c_uint32(), C.c_uint32(), C.c_uint32()
     roots = np.zeros(65536, dtype=np.uint32)
     kinds = np.zeros(65536, dtype=np.uint8)
-    _check(load().pmc_analyze_material_ext(C.byref(mat), min_root_nodes, flags, C.byref(nr), roots.ctypes.data,
+    _check(load().pmc_analyze_material_ext(C.byref(mat), min_root_nodes, min_root_cost, flags, C.byref(nr),
+                                           roots.ctypes.data,
                                            kinds.ctypes.data, 65536, C.byref(ni), C.byref(ns)),
            "pmc_analyze_material_ext")
     return {"roots": roots[: nr.value].copy(), "kinds": kinds[: nr.value].copy(), "n_instr": ni.value,

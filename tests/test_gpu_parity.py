@@ -164,6 +164,26 @@ def test_frame_band_parity(P, n_cells, n_entries, mode):
     _compare_tables(gpu, ref)
 
 
+@pytest.mark.parametrize("mode", ["grouped", "unsorted", "probe_inline", "inline"])
+@pytest.mark.parametrize("min_root_cost", [300, 600])
+def test_frame_band_parity_with_cost_threshold(P, min_root_cost, mode):
+    """Only cacheable nodes whose sub-graph costs at least min_root_cost FP32 operations
+    are looked up and inserted; the rest are evaluated every time.  Same bar as without it."""
+    frame = W.Frame(W.FrameSpec(width=1920, height=1080, n_mats=64, seed=0))
+    mats = W.random_materials(64, 20, 200, 0.2, seed=0)
+    gpu = P.Cache(mats, 1 << 12, 8, flags=MODES[mode], min_root_cost=min_root_cost)
+    ref = O.Cache(mats, 1 << 12, 8, min_root_cost=min_root_cost)
+    for m in range(0, 64, 7):
+        assert list(gpu.material_info(m)["roots"]) == list(ref.roots(m))
+    for p in range(3):
+        _compare_pass(gpu, ref, P, frame.points(p, rows=(0, 9)))
+    _compare_tables(gpu, ref)
+    full = P.Cache(mats, 1 << 12, 8)
+    full.eval_batch(P.points_to_device(frame.points(0, rows=(0, 9))),
+                    torch.empty((3, 9 * 1920), device="cuda"))
+    assert gpu.stats()["lookups"] < 3 * full.stats()["lookups"]
+
+
 @pytest.fixture(scope="module")
 def scale_mats():
     # the scale configuration: 4096 networks of 10-2000 nodes, 40 % shading-point dependent

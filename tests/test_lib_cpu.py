@@ -155,3 +155,18 @@ def test_checker_exactness_rule_matches_oracle(lib):
             with pytest.raises(P.PmcError) as ei:
                 P.analyze_material(net)
             assert ei.value.status == P.PMC_ERR_INVALID_ARG
+
+
+def test_node_cost_model_matches_oracle(lib):
+    for m in W.random_materials(8, 20, 200, 0.2, seed=5) + [W.material_tiny()]:
+        for row in m:
+            assert P.node_cost(row) == O.node_cost(row)
+
+
+def test_cost_threshold_roots_match_oracle(lib):
+    mats = W.random_materials(16, 20, 200, 0.2, seed=9)
+    for m in mats:
+        for thr in (0, 100, 300, 600):
+            got = P.analyze_material(m, min_root_cost=thr)["roots"]
+            want = O.analyze(m, min_root_cost=thr)[1]
+            assert list(got) == list(want), thr

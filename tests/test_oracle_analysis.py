@@ -151,3 +151,87 @@ def test_checker_argument_must_be_exact(src, scale, ok):
     position input itself and s a power of two (within a range where x s cannot leave
     FP32's exponent range for a UV or a position)."""
     assert O.validate(_checker_net(src, scale)) == ok
+
+
+# ---- cost threshold of cacheable nodes --------------------------------------------------
+def test_node_cost_model_hand_values():
+    """The cost model of the interface: FP32 operations per evaluation, FMA = 2."""
+    b = W.Builder()
+    uv = b.add(W.OP_UV)
+    rows = {
+        "uv": (uv, 0), "const": (b.add(W.OP_CONST, fp=[1, 2, 3]), 0),
+        "affine": (b.add(W.OP_UV_AFFINE, [uv], fp=[1, 0, 0, 1, 0, 0]), 8),
+        "fbm1": (b.add(W.OP_FBM, [uv], ip=[1, 1], fp=[4.0, 2.0, 0.5]), 51),
+        "fbm3": (b.add(W.OP_FBM, [uv], ip=[3, 1], fp=[4.0, 2.0, 0.5]), 145),
+        "fbm16": (b.add(W.OP_FBM, [uv], ip=[16, 1], fp=[4.0, 2.0, 0.5]), 756),
+        "voronoi": (b.add(W.OP_VORONOI, [uv], ip=[0, 1], fp=[4.0]), 99),
+        "checker": (b.add(W.OP_CHECKER, [uv], fp=[4.0, 0, 0, 0, 1, 1, 1]), 4),
+        "ramp": (b.add(W.OP_RAMP, [uv], ip=[2], fp=[0, 1, 0, 0, 0, 0, 0, 1, 1, 1]), 23),
+        "mix": (b.add(W.OP_MIX, [uv, uv], fp=[0.5]), 17),
+        "add": (b.add(W.OP_ADD, [uv, uv]), 9), "mul": (b.add(W.OP_MUL, [uv, uv]), 9),
+        "pow": (b.add(W.OP_POW, [uv], fp=[2.0]), 18),
+        "facing": (b.add(W.OP_FACING, [uv], fp=[0, 0, 1]), 8),
+    }
+    net = b.build()
+    for name, (i, cost) in rows.items():
+        assert O.node_cost(net[i]) == cost, name
+
+
+def test_cost_threshold_two_roots():
+    # root 4 = MUL(RAMP(FBM2(uv)), VORONOI(uv)): 98 + 23 + 99 + 9 = 229
+    # root 10 = POW(FBM1(uv)): 51 + 18 = 69
+    g = g_two_roots()
+    for thr, want in ((0, [4, 10]), (69, [4, 10]), (70, [4]), (229, [4]), (230, [])):
+        assert list(O.analyze(g, min_root_cost=thr)[1]) == want, thr
+
+
+def test_cost_threshold_nested_roots():
+    # root 2 = RAMP(FBM2(uv)): 98 + 23 = 121; root 7 = ADD(POW(node 2), uv): 121 + 18 + 9 = 148
+    g = g_nested()
+    for thr, want in ((121, [2, 7]), (122, [7]), (148, [7]), (149, [])):
+        assert list(O.analyze(g, min_root_cost=thr)[1]) == want, thr
+
+
+def test_cost_threshold_counts_a_shared_node_once():
+    # 0 UV; 1 FBM1(0); 2 POW(1); 3 RAMP(1); 4 MUL(2, 3) = output: 51 + 18 + 23 + 9 = 101, the
+    # noise counted once although both branches read it
+    b = W.Builder()
+    uv = b.add(W.OP_UV)
+    n1 = b.add(W.OP_FBM, [uv], ip=[1, 2], fp=[4.0, 2.0, 0.5])
+    p2 = b.add(W.OP_POW, [n1], fp=[2.0])
+    r3 = b.add(W.OP_RAMP, [n1], ip=[2], fp=[0, 1, 0, 0, 0, 0, 0, 1, 1, 1])
+    b.add(W.OP_MUL, [p2, r3])
+    g = b.build()
+    assert list(O.analyze(g, min_root_cost=101)[1]) == [4]
+    assert list(O.analyze(g, min_root_cost=102)[1]) == []
+
+
+def test_cost_threshold_zero_is_the_plain_rule_and_thresholds_only_remove_roots():
+    mats = W.random_materials(24, 20, 200, 0.2, seed=13)
+    for m in mats:
+        base = set(O.analyze(m)[1].tolist())
+        assert set(O.analyze(m, min_root_cost=0)[1].tolist()) == base
+        prev = base
+        for thr in (100, 300, 600, 1000):
+            cur = set(O.analyze(m, min_root_cost=thr)[1].tolist())
+            assert cur <= prev
+            prev = cur
+
+
+def test_cost_threshold_in_the_cache_emulation():
+    """Nodes below the threshold are evaluated like any other node and never looked up:
+    lookups = points x kept cacheable nodes; the first pass equals plain evaluation; a
+    threshold above every node leaves a cache that never looks anything up."""
+    g = g_two_roots()
+    pts = W.points_uniform(300, seed=4)
+    plain = np.array([O.eval_point_nocache(g, [pts[k][i] for k in ("u", "v", "px", "py", "pz", "nx", "ny", "nz")])
+                      for i in range(300)]).T
+    for thr, kept in ((0, 2), (70, 1), (230, 0)):
+        c = O.Cache([g], 1 << 12, 4, min_root_cost=thr)
+        assert list(c.roots(0)) == list(O.analyze(g, min_root_cost=thr)[1])
+        r = c.run_batch(pts)
+        assert np.abs(r["rgb"] - plain).max() <= 1e-12
+        assert c.stats()["lookups"] == 300 * kept
+        r2 = c.run_batch(pts)                        # same points: every kept node hits
+        assert c.stats()["hits"] == 300 * kept
+        assert np.abs(r2["rgb"] - plain).max() <= 1e-6
