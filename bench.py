@@ -203,42 +203,69 @@ def ours(args, rank, world, local_rank, dist):
     outs = torch.empty((3, n), dtype=torch.float32, device=dev)
     hits = torch.empty(n, dtype=torch.int16, device=dev)
 
-    cached = P.Cache(mats, N_CELLS, N_ENTRIES, uv_level=LEVEL, device=local_rank)
     uncached = None
     if "uncached" in args.legs.split(","):
         uncached = P.Cache(mats, N_CELLS, N_ENTRIES, uv_level=LEVEL, flags=P.PMC_CACHE_OFF, device=local_rank)
-
-    # ---- cached, device-resident inputs ---------------------------------------------
-    for _ in range(args.warmup):
-        run_frame(cached, dev_passes, outs, hits, None)
-    # autotune the schedule on a warm table (two passes in), then start over
-    cached.reset()
-    for p in range(2):
-        cached.eval_batch(dev_passes[p], outs, hits)
-    tune = cached.autotune(dev_passes[2], reps=3)
-    cached.sync()
-    cached.read_timing()
-    cached.set_timing(True)
     pts_total = n * SPP * args.steps
-    with ClockSampler(local_rank) as clk:
-        # eager launches with per-phase events: the per-kernel times of the roofline
-        secs_eager = timed_steps(torch, cached, dev_passes, outs, hits, args.steps, barrier)
-        cached.set_timing(False)
-        timing = cached.read_timing()
-        frame_stats = cached.stats()   # reset() zeroes the counters per frame: one frame's worth
-        cached.reset()
-        cached.eval_batch(dev_passes[0], outs, hits)
-        pass0_stats = cached.stats()   # the empty-table pass: no lookup launch
-        # the whole frame (reset + 16 passes) as one CUDA graph: the headline
-        graph = cached.graph(dev_passes, [outs] * SPP, [hits] * SPP, reset=True)
+
+    def measure(cache):
+        """Warm-up frames, the schedule autotuned on a warm table, timed eager frames with
+        per-phase events (the per-kernel times of the roofline), then the whole frame (reset +
+        16 passes) as one CUDA graph."""
+        for _ in range(args.warmup):
+            run_frame(cache, dev_passes, outs, hits, None)
+        cache.reset()
+        for p in range(2):
+            cache.eval_batch(dev_passes[p], outs, hits)
+        tune = cache.autotune(dev_passes[2], reps=3)
+        cache.sync()
+        cache.read_timing()
+        cache.set_timing(True)
+        secs_eager = timed_steps(torch, cache, dev_passes, outs, hits, args.steps, barrier)
+        cache.set_timing(False)
+        timing = cache.read_timing()
+        frame_stats = cache.stats()   # reset() zeroes the counters per frame: one frame's worth
+        cache.reset()
+        cache.eval_batch(dev_passes[0], outs, hits)
+        pass0_stats = cache.stats()   # the empty-table pass: no lookup launch
+        graph = cache.graph(dev_passes, [outs] * SPP, [hits] * SPP, reset=True)
         for _ in range(max(1, args.warmup)):
             graph.launch()
-        cached.sync()
-        cached.read_timing()
+        cache.sync()
+        cache.read_timing()
         secs = timed_graph(torch, graph, args.steps, barrier)
-        g_launches = cached.read_timing()["launches"]
-    graph.close()
-    secs_max = max_over_ranks(torch, dist, secs, dev)
+        g_launches = cache.read_timing()["launches"]
+        graph.close()
+        return dict(tune=tune, secs_eager=secs_eager, timing=timing, frame_stats=frame_stats,
+                    pass0_stats=pass0_stats, secs=max_over_ranks(torch, dist, secs, dev), g_launches=g_launches)
+
+    with ClockSampler(local_rank) as clk:
+        # the evaluation's cost per FP32 operation with the cache off (every node evaluated,
+        # one eager frame with per-phase events)
+        plain = P.Cache(mats, N_CELLS, N_ENTRIES, uv_level=LEVEL, flags=P.PMC_CACHE_OFF, device=local_rank)
+        run_frame(plain, dev_passes, outs, hits, None)
+        plain.sync()
+        plain.read_timing()
+        plain.set_timing(True)
+        plain.reset()
+        run_frame(plain, dev_passes, outs, hits, None)
+        plain_ms = plain.read_timing()["ms"]
+        t_flop = plain_ms["eval"] / max(1, plain.stats()["flops"])
+        plain.close()
+        # the rule of Sec. 3: every maximal UV-only node is cached
+        m_all = measure(P.Cache(mats, N_CELLS, N_ENTRIES, uv_level=LEVEL, device=local_rank))
+        # break-even cost of a cacheable node: a probe (its lookup and insert, from the
+        # all-roots run's phase times) against the evaluation a hit saves at the measured hit
+        # rate
+        ms, st = m_all["timing"]["ms"], m_all["frame_stats"]
+        t_probe = (ms["lookup"] + ms["insert"]) / args.steps / max(1, st["lookups"])
+        hit = st["hits"] / max(1, st["lookups"])
+        min_root_cost = int(round(t_probe / max(1e-30, hit * t_flop) / 50.0) * 50)
+        cached = P.Cache(mats, N_CELLS, N_ENTRIES, uv_level=LEVEL, min_root_cost=min_root_cost, device=local_rank)
+        m = measure(cached)
+    tune, secs_eager, timing = m["tune"], m["secs_eager"], m["timing"]
+    frame_stats, pass0_stats, g_launches = m["frame_stats"], m["pass0_stats"], m["g_launches"]
+    secs_max = m["secs"]
     value = whole_job_rate(pts_total, world, secs_max)
 
     # ---- uncached --------------------------------------------------------------------
@@ -312,10 +339,22 @@ def ours(args, rank, world, local_rank, dist):
         "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": round(secs_max / args.steps * 1e3, 3), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": config_dict({"parallelism": f"replicas x{world}" if world > 1 else "single GPU"}),
+        "config": config_dict({"parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+                               "min_root_cost": min_root_cost}),
+        "min_root_cost": {"value": min_root_cost, "rule": "break-even: (lookup + insert ms per probe, all-roots run) / "
+                                                          "(hit rate x evaluation ms per FP32 op, cache off)",
+                          "probe_ns": round(t_probe * 1e6, 4), "flop_ns": round(t_flop * 1e6, 7),
+                          "hit_rate": round(hit, 4)},
+        "cached_all_roots": {"value": round(whole_job_rate(pts_total, world, m_all["secs"]), 1), "unit": UNIT,
+                             "ms_per_step": round(m_all["secs"] / args.steps * 1e3, 3),
+                             "hit_rate": round(hit, 4),
+                             "lookups_per_point": round(st["lookups"] / (n * SPP), 3),
+                             "phase_ms_per_step": {k: round(v / args.steps, 3) for k, v in ms.items()}},
         "uncached": {"value": round(u_value, 1), "unit": UNIT,
                      "ms_per_step": round(usecs / args.steps * 1e3, 3),
-                     "speedup_cached_over_uncached": round(value / u_value, 3)} if u_value == u_value else None,
+                     "speedup_cached_over_uncached": round(value / u_value, 3),
+                     "speedup_all_roots_over_uncached": round(whole_job_rate(pts_total, world, m_all["secs"]) / u_value, 3)}
+        if u_value == u_value else None,
         "hit_rate": round(frame_stats["hits"] / max(1, frame_stats["lookups"]), 4),
         "table": {k: frame_stats[k] for k in ("lookups", "hits", "inserted", "dropped_dup", "dropped_full")},
         "phase_ms_per_step": {k: round(v / args.steps, 3) for k, v in ms.items()},
@@ -360,6 +399,11 @@ def ours(args, rank, world, local_rank, dist):
         guarded("replacement", lambda: replace_leg(torch, P, dev, local_rank, seed=rank))
     if "sweep" in legs:
         guarded("scale_sweep", lambda: sweep_leg(torch, P, dev, local_rank, seed=rank))
+    if "threshold" in legs:
+        guarded("cost_threshold", lambda: threshold_leg(torch, P, mats, dev_passes, outs, hits, local_rank))
+        if u_value == u_value and "runs" in line["cost_threshold"]:
+            for r in line["cost_threshold"]["runs"]:
+                r["speedup_over_uncached"] = round(r["points_per_s"] / u_value, 3)
     if rank == 0 and not args.no_cpu_baseline and "cpu" in legs:
         line["cpu_baseline"], line["max_abs_err_vs_fp64"] = cpu_baseline(P, torch, mats, frame, dev)
     return line
@@ -425,6 +469,12 @@ def frame128_leg(torch, P, dev, local_rank, seed=0):
     res["eager_warm_passes"] = round(n * (F128_PASSES - 2) / (sum(per_pass[2:]) / 1e3), 1)
     res["hit_rate"] = round(st["hits"] / max(1, st["lookups"]), 4)
     res["graph_grouped"] = round(graph_rate(c), 1)
+    # the per-point evaluator's work distribution: warp pairs of items (above), block-wide
+    # tiles of one material, one point per lane
+    c.set_schedule(Pm.PMC_BLOCK_ITEMS, 4)
+    res["graph_block_per_material"] = round(graph_rate(c), 1)
+    c.set_schedule(Pm.PMC_ONE_POINT, 4)
+    res["graph_one_point_per_lane"] = round(graph_rate(c), 1)
     c.set_schedule(Pm.PMC_UNSORTED | Pm.PMC_EVAL_INLINE, 4)
     res["graph_unsorted"] = round(graph_rate(c), 1)
     c.set_schedule(0, 4)
@@ -437,12 +487,15 @@ def frame128_leg(torch, P, dev, local_rank, seed=0):
     c.close()
     u = make(Pm.PMC_CACHE_OFF)
     res["uncached_graph_grouped"] = round(graph_rate(u, 1), 1)
+    u.set_schedule(Pm.PMC_BLOCK_ITEMS, 4)
+    res["uncached_graph_block_per_material"] = round(graph_rate(u, 1), 1)
     u.set_schedule(Pm.PMC_UNSORTED | Pm.PMC_EVAL_INLINE, 4)
     res["uncached_graph_unsorted"] = round(graph_rate(u, 1), 1)
     u.close()
-    best = max(res["graph_grouped"], res["graph_unsorted"], res["graph_autotuned"])
-    res["speedup_cached_over_uncached"] = round(best / max(res["uncached_graph_grouped"],
-                                                           res["uncached_graph_unsorted"]), 3)
+    best = max(res["graph_grouped"], res["graph_unsorted"], res["graph_autotuned"], res["graph_block_per_material"],
+               res["graph_one_point_per_lane"])
+    res["speedup_cached_over_uncached"] = round(best / max(res["uncached_graph_grouped"], res["uncached_graph_unsorted"],
+                                                           res["uncached_graph_block_per_material"]), 3)
     res["graph_over_eager"] = round(res["graph_grouped"] / res["eager"], 3)
     del passes
     torch.cuda.empty_cache()
@@ -587,6 +640,44 @@ def position_leg(torch, P, mats, dev_passes, outs, hits, local_rank):
     u = res["uncached"]["points_per_s"]
     res["speedup_uv_only_over_uncached"] = round(res["uv_only"]["points_per_s"] / u, 3)
     res["speedup_uv_and_position_over_uncached"] = round(res["uv_and_position"]["points_per_s"] / u, 3)
+    return res
+
+
+THRESHOLDS = (0, 150, 300, 450, 600, 900)
+
+
+def threshold_leg(torch, P, mats, dev_passes, outs, hits, local_rank):
+    """The benchmark frame with cacheable nodes restricted to sub-graphs of at least
+    min_root_cost FP32 operations of the node cost model (0 = every node the rule of Sec. 3
+    picks): probes per point, hit rate and frame throughput (one CUDA graph per frame,
+    autotuned schedule) for each threshold."""
+    n = WIDTH * HEIGHT
+    res = {"config": f"frame 1920x1080x16spp, {N_MATS} materials, table {N_CELLS}x{N_ENTRIES} slots",
+           "unit": UNIT, "runs": []}
+    for thr in THRESHOLDS:
+        c = P.Cache(mats, N_CELLS, N_ENTRIES, uv_level=LEVEL, min_root_cost=thr, device=local_rank)
+        for p in range(2):
+            c.eval_batch(dev_passes[p], outs, hits)
+        c.autotune(dev_passes[2], reps=2)
+        c.reset()
+        for p in range(SPP):
+            c.eval_batch(dev_passes[p], outs, hits)
+        st = c.stats()
+        g = c.graph(dev_passes, [outs] * SPP, [hits] * SPP, reset=True)
+        g.launch()
+        torch.cuda.synchronize()
+        t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        t0.record()
+        for _ in range(3):
+            g.launch()
+        t1.record()
+        torch.cuda.synchronize()
+        g.close()
+        c.close()
+        res["runs"].append({"min_root_cost": thr, "points_per_s": round(3 * n * SPP / (t0.elapsed_time(t1) / 1e3), 1),
+                            "lookups_per_point": round(st["lookups"] / (n * SPP), 3),
+                            "hit_rate": round(st["hits"] / max(1, st["lookups"]), 4),
+                            "flops_per_point": round(st["flops"] / (n * SPP), 1)})
     return res
 
 
@@ -863,8 +954,9 @@ def surrogate_leg(torch, P, dev, local_rank, seed=0):
 
 
 def e2e_run(torch, P, mats, passes_host, args, local_rank, barrier, dist, dev):
-    """Same frame through pmc_eval_batch_host from pinned host buffers: the H2D copy of
-    each pass's points and the D2H copy of its colours and hit counts are timed."""
+    """Same frame through pmc_eval_passes_host from pinned host buffers: every pass's points
+    go in and its colours and hit counts come out inside the timed region, the copies of a
+    pass overlapping the evaluation of its neighbours."""
     n = WIDTH * HEIGHT
     pinned = []
     for h in passes_host:
@@ -873,15 +965,13 @@ def e2e_run(torch, P, mats, passes_host, args, local_rank, barrier, dist, dev):
             t = torch.from_numpy(h[k].view(np.int32) if k == "mat" else h[k]).pin_memory()
             d[k] = t.numpy().view(np.uint32) if k == "mat" else t.numpy()
         pinned.append(d)
-    rgb_t = torch.empty(3 * n, dtype=torch.float32).pin_memory()
-    hits_t = torch.empty(n, dtype=torch.int16).pin_memory()
-    rgb, hits = rgb_t.numpy(), hits_t.numpy().view(np.uint16)
+    rgb = [torch.empty(3 * n, dtype=torch.float32).pin_memory().numpy() for _ in range(SPP)]
+    hits = [torch.empty(n, dtype=torch.int16).pin_memory().numpy().view(np.uint16) for _ in range(SPP)]
     cache = P.Cache(mats, N_CELLS, N_ENTRIES, uv_level=LEVEL, device=local_rank)
 
     def frame_host():
         cache.reset()
-        for p in range(SPP):
-            cache.eval_batch_host(pinned[p], rgb, hits)
+        cache.eval_passes_host(pinned, rgb, hits)
 
     for _ in range(max(1, args.warmup)):
         frame_host()
@@ -900,29 +990,55 @@ def e2e_run(torch, P, mats, passes_host, args, local_rank, barrier, dist, dev):
             "h2d_bytes_per_step": int(SPP * n * 36), "d2h_bytes_per_step": int(SPP * n * (12 + 2))}
 
 
-def cpu_baseline(P, torch, mats, frame, dev):
-    """The FP64 oracle, single-threaded, on the first SAMPLE_ROWS rows of all 16 passes
-    (same table geometry); the CUDA path runs the same sample for the error figure."""
-    from oracle import oracle as O
-    ref = O.Cache(mats, N_CELLS, N_ENTRIES, level=LEVEL)
-    gpu = P.Cache(mats, N_CELLS, N_ENTRIES, uv_level=LEVEL)
-    npts, secs, err = 0, 0.0, 0.0
-    for p in range(SPP):
-        part = frame.points(p, rows=SAMPLE_ROWS)
+def cpu_model():
+    """The host CPU's model name, as the kernel reports it."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.strip().startswith("Model name"):
+                return ln.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    return "unknown"
+
+
+def oracle_rate(O, mats, passes, threads):
+    """Points/s of the FP64 oracle over a sequence of passes from an empty table."""
+    ref = O.Cache(mats, N_CELLS, N_ENTRIES, level=LEVEL, threads=threads)
+    npts, secs, outs = 0, 0.0, []
+    for part in passes:
         t = time.perf_counter()
-        r = ref.run_batch(part)
+        outs.append(ref.run_batch(part)["rgb"])
         secs += time.perf_counter() - t
         npts += len(part["u"])
+    return npts / secs, secs, npts, outs
+
+
+def cpu_baseline(P, torch, mats, frame, dev):
+    """The FP64 oracle on the first SAMPLE_ROWS rows of all 16 passes (same table geometry),
+    over all host cores (its points spread over OpenMP threads, the insert sequential) and
+    on one core; the CUDA path runs the same sample for the error figure."""
+    from oracle import oracle as O
+    passes = [frame.points(p, rows=SAMPLE_ROWS) for p in range(SPP)]
+    cores = os.cpu_count() or 1
+    rate_all, secs_all, npts, outs = oracle_rate(O, mats, passes, cores)
+    rate_one, secs_one, _, _ = oracle_rate(O, mats, passes, 1)
+    gpu = P.Cache(mats, N_CELLS, N_ENTRIES, uv_level=LEVEL)
+    err = 0.0
+    for part, r in zip(passes, outs):
         d = P.points_to_device(part, dev)
         rgb = torch.empty((3, len(part["u"])), dtype=torch.float32, device=dev)
         gpu.eval_batch(d, rgb)
         gpu.sync()
-        err = max(err, float(np.abs(rgb.cpu().numpy() - r["rgb"]).max()))
+        err = max(err, float(np.abs(rgb.cpu().numpy() - r).max()))
     gpu.close()
     rows = SAMPLE_ROWS[1] - SAMPLE_ROWS[0]
-    return ({"value": round(npts / secs, 1), "unit": UNIT, "cores": 1, "kind": "oracle",
-             "sample": f"rows {SAMPLE_ROWS[0]}-{SAMPLE_ROWS[1]} of all {SPP} passes "
-                       f"({rows * WIDTH} points/pass, {npts} points, {secs:.1f} s), same table size"},
+    sample = (f"rows {SAMPLE_ROWS[0]}-{SAMPLE_ROWS[1]} of all {SPP} passes ({rows * WIDTH} points/pass, "
+              f"{npts} points), same table size")
+    return ({"value": round(rate_all, 1), "unit": UNIT, "cores": cores, "kind": "oracle",
+             "cpu": cpu_model(), "sample": f"{sample}; {secs_all:.1f} s on {cores} threads",
+             "single_core": {"value": round(rate_one, 1), "unit": UNIT, "cores": 1,
+                             "sample": f"{sample}; {secs_one:.1f} s"}},
             err)
 
 
@@ -1053,7 +1169,8 @@ def reference(args):
     from oracle import oracle as O
     mats, frame = workload(seed=0)
     passes = [frame.points(p, rows=REF_ROWS) for p in range(SPP)]
-    ref = O.Cache(mats, N_CELLS, N_ENTRIES, level=LEVEL)
+    cores = os.cpu_count() or 1
+    ref = O.Cache(mats, N_CELLS, N_ENTRIES, level=LEVEL, threads=cores)
 
     def step():
         ref.reset()
@@ -1075,9 +1192,9 @@ def reference(args):
             "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": round(secs / args.steps * 1e3, 3), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": config_dict({"parallelism": "single CPU thread"}),
-            "cpu_baseline": {"value": round(value, 1), "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": sample},
+            "config": config_dict({"parallelism": f"{cores} CPU threads (OpenMP), sequential insert"}),
+            "cpu_baseline": {"value": round(value, 1), "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "cpu": cpu_model(), "sample": sample},
             "e2e": {"value": round(value, 1), "unit": UNIT, "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
 

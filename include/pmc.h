@@ -182,6 +182,13 @@ typedef struct {
                                      node<<32 | 1<<31 | ix<<20 | iy<<10 | iz.  A node that
                                      joins UV and position is not cacheable.  Learned
                                      surrogates stay on UV-only nodes */
+#define PMC_BLOCK_ITEMS 0x400u  /* schedule only (pmc_set_schedule): the per-point evaluator
+                                     takes block-wide tiles of one material (the four warps of a
+                                     block, 256 grouped points) per claim instead of one warp's
+                                     64 points, so the warps of a block share the material's
+                                     instruction and parameter lines (same results)          */
+#define PMC_ONE_POINT 0x800u    /* schedule only: one point per lane in the per-point evaluator
+                                     instead of two (same results)                           */
 #define PMC_MAX_POS_LEVEL 20u
 
 typedef struct {
@@ -289,6 +296,17 @@ pmc_status pmc_eval_batch(pmc_cache* cache, const pmc_points* pts, float* out_rg
 pmc_status pmc_eval_batch_host(pmc_cache* cache, const pmc_points* host_pts,
                                float* host_rgb, uint16_t* host_hits, void* stream);
 
+/* n_passes consecutive passes from HOST buffers (host_passes[k] -> host_rgb[k], 3 * n
+ * floats planar, and host_hits[k], n uint16, if host_hits and that entry are non-NULL), each
+ * the same pass as pmc_eval_batch on `stream`.  The copies of a pass overlap the evaluation
+ * of its neighbours: inputs go in on one library-owned stream and outputs come out on
+ * another, through two device staging sets that the cache owns (grown, with a device
+ * synchronisation, when a larger pass comes).  Returns when every output is in host memory.
+ * Page-locked host buffers let the copies overlap; pageable ones work but copy
+ * synchronously. */
+pmc_status pmc_eval_passes_host(pmc_cache* cache, const pmc_points* host_passes, uint32_t n_passes,
+                                float* const* host_rgb, uint16_t* const* host_hits, void* stream);
+
 /* Waits for the last stream used with this cache and reports device-side errors
  * (PMC_ERR_INVALID_ARG for out-of-range material indices). */
 pmc_status pmc_sync(pmc_cache* cache);
@@ -385,9 +403,9 @@ pmc_status pmc_read_timing(pmc_cache* cache, double* ms, uint64_t* kernel_launch
  *   h1 = relu(f W1 + b1) (64), h2 = relu(h1 W2 + b2) (64), y = h2 W3 + b3 (3),
  *   value = clamp(y, 0, 1).
  * Parameters: PMC_MLP_PARAMS floats, W1 [64][64], b1 [64], W2 [64][64], b2 [64],
- * W3 [64][3], b3 [3].  Products take BF16 operands and accumulate in FP32 on tensor
- * cores (inference: tcgen05.mma with tensor-memory accumulators; training: mma.sync);
- * FP32 master weights take Adam steps.  Per material the candidate node is its
+ * W3 [64][3], b3 [3].  Products take BF16 operands and accumulate in FP32 on the
+ * tcgen05 tensor cores (tensor-memory accumulators), in inference and in training (forward,
+ * backward and the weight gradients); FP32 master weights take Adam steps.  Per material the candidate node is its
  * most expensive cacheable node with no cacheable node below it.  A node with an enabled
  * surrogate is not probed: every pass evaluates the network for it. */
 #define PMC_MLP_PARAMS 8515u
@@ -490,7 +508,7 @@ pmc_status pmc_eval_batch_noalloc(pmc_cache* cache, const pmc_points* pts, float
  * counters and table, bit for bit. */
 typedef struct {
     uint32_t flags;     /* subset of PMC_EVAL_INLINE | PMC_INSERT_ROUNDS | PMC_UNSORTED |
-                           PMC_PROBE_INLINE                                             */
+                           PMC_PROBE_INLINE | PMC_BLOCK_ITEMS | PMC_ONE_POINT           */
     uint32_t lookup_rb; /* probes in flight per lane in the lookup kernel: 1, 2 or 4    */
 } pmc_schedule;
 

@@ -72,6 +72,8 @@ def lib():
         L.orc_node_cost.argtypes = [vp]
         L.orc_cache_set_min_root_cost.restype = None
         L.orc_cache_set_min_root_cost.argtypes = [vp, u32]
+        L.orc_cache_set_threads.restype = None
+        L.orc_cache_set_threads.argtypes = [vp, C.c_int]
         L.orc_voxel.restype = u32
         L.orc_voxel.argtypes = [C.c_float, u32]
         L.orc_key_pos.restype = u64
@@ -248,7 +250,7 @@ class Cache:
 
     def __init__(self, materials, n_cells, n_entries, level=10, min_root_nodes=2,
                  cache_off=False, hash_hook=None, level_offset=0, alg1=False, replacement=False,
-                 pos_level=-1, close_at_lookup=True, min_root_cost=0):
+                 pos_level=-1, close_at_lookup=True, min_root_cost=0, threads=1):
         self._mats = [_nodes(m) for m in materials]
         self.n_cells, self.n_entries, self.level = n_cells, n_entries, level
         self.off = bool(cache_off) or n_cells == 0 or n_entries == 0
@@ -265,6 +267,7 @@ class Cache:
         lib().orc_cache_set_alg1(self._h, int(alg1))
         lib().orc_cache_set_replacement(self._h, int(replacement))
         lib().orc_cache_set_close_at_lookup(self._h, int(close_at_lookup))
+        lib().orc_cache_set_threads(self._h, int(threads))
         self._hook = None
         if hash_hook is not None:
             def _cb(k, nc, cell, h2):

@@ -588,6 +588,7 @@ struct orc_cache {
     int32_t level_offset;  /* added to the ray-cone level (Sec. 4) */
     int alg1;              /* the paper's concurrent update, serialised point by point */
     int replace;           /* replacement by visibility class (Sec. 5), else keep-first */
+    int threads;           /* host threads of orc_run_batch (1 = one point after another) */
     int close_at_lookup;   /* replacement: drop a value as full at lookup when its full cell
                               holds no class larger than its own (1, the default); 0 = let
                               every such value reach the sequential insert */
@@ -619,6 +620,7 @@ orc_cache* orc_cache_new(uint64_t n_cells, uint32_t n_entries, uint32_t level,
     c->cls = (uint8_t*)calloc(slots ? slots : 1, 1);
     c->pos_level = -1;
     c->close_at_lookup = 1;
+    c->threads = 1;
     return c;
 }
 
@@ -683,6 +685,8 @@ void orc_cache_set_replacement(orc_cache* c, int on) { c->replace = on != 0; }
 void orc_cache_set_close_at_lookup(orc_cache* c, int on) { c->close_at_lookup = on != 0; }
 
 void orc_cache_set_min_root_cost(orc_cache* c, uint32_t cost) { c->min_root_cost = cost; }
+
+void orc_cache_set_threads(orc_cache* c, int threads) { c->threads = threads > 1 ? threads : 1; }
 
 void orc_cache_set_position_level(orc_cache* c, int32_t level) { c->pos_level = level; }
 
@@ -846,6 +850,183 @@ static void insert_candidates(orc_cache* c, const orc_candidate* cand, size_t n_
     }
 }
 
+/* The inputs and outputs of one batch, as orc_run_batch receives them. */
+typedef struct {
+    uint64_t n;
+    const float *u, *v;
+    const uint32_t* mat;
+    const float *px, *py, *pz, *nx, *ny, *nz;
+    double* rgb;
+    uint16_t* hits;
+    uint32_t* evaluated;
+    uint64_t* probe_key;
+    uint64_t* probe_cell;
+    uint32_t* probe_h2;
+    uint8_t* probe_hit;
+    const float *g1u, *g1v, *g2u, *g2v;
+    const uint8_t* vis;
+} orc_batch;
+
+/* Scratch of one range of points: per-node values and flags, the candidates the range
+ * produced (in point order) and its counters. */
+typedef struct {
+    double* val;
+    uint8_t* hit;
+    double* hitval;
+    uint8_t* needed;
+    uint64_t* rcell;
+    uint32_t* rh2;
+    uint8_t* rclosed;   /* replacement: the cell cannot take the value */
+    orc_candidate* cand;
+    size_t n_cand, cand_cap;
+    uint64_t stats[ORC_NSTATS];
+    int status;
+} orc_work;
+
+static void work_init(orc_work* w, uint32_t max_n) {
+    memset(w, 0, sizeof(*w));
+    w->val = (double*)malloc(3 * (size_t)max_n * sizeof(double));
+    w->hit = (uint8_t*)malloc(max_n);
+    w->hitval = (double*)malloc(3 * (size_t)max_n * sizeof(double));
+    w->needed = (uint8_t*)malloc(max_n);
+    w->rcell = (uint64_t*)malloc((size_t)max_n * sizeof(uint64_t));
+    w->rh2 = (uint32_t*)malloc((size_t)max_n * sizeof(uint32_t));
+    w->rclosed = (uint8_t*)malloc(max_n);
+    w->cand_cap = 1024;
+    w->cand = (orc_candidate*)malloc(w->cand_cap * sizeof(orc_candidate));
+    w->status = ORC_OK;
+}
+
+static void work_free(orc_work* w) {
+    free(w->val);
+    free(w->hit);
+    free(w->hitval);
+    free(w->needed);
+    free(w->rcell);
+    free(w->rh2);
+    free(w->rclosed);
+    free(w->cand);
+}
+
+/* Phase L and evaluation of point i: every point sees the table as it was when the batch
+ * started (with the paper's concurrent update, as the earlier points of the batch left
+ * it).  probe0: the point's first entry in the probe_* arrays. */
+static void process_point(orc_cache* c, const orc_batch* B, uint64_t i, uint64_t probe0, orc_work* w) {
+    const uint64_t n = B->n;
+    if (B->mat[i] >= c->n_mats) {
+        w->status = ORC_ERR_BADMAT;
+        B->rgb[i] = B->rgb[n + i] = B->rgb[2 * n + i] = 0.0;
+        if (B->hits) B->hits[i] = 0;
+        if (B->evaluated) B->evaluated[i] = 0;
+        return;
+    }
+    const uint32_t mi = B->mat[i];
+    const orc_mat* M = &c->mats[mi];
+    const double sp[8] = {B->u[i], B->v[i], B->px[i], B->py[i], B->pz[i], B->nx[i], B->ny[i], B->nz[i]};
+    /* the point's mip level: from its ray-cone gradients (Eq. 1) if given */
+    const uint32_t level =
+        B->g1u ? (uint32_t)orc_level(B->g1u[i], B->g1v[i], B->g2u[i], B->g2v[i], c->level_offset) : c->level;
+    uint32_t n_hit = 0;
+    uint64_t probe = probe0;
+    memset(w->hit, 0, M->n);
+    for (uint32_t r = 0; r < M->n_roots; ++r) {
+        uint32_t node = M->roots[r];
+        /* a node with a learned surrogate takes the network's value, no lookup */
+        const int surr = M->surr_theta && node == M->surr_node;
+        if (surr) {
+            double y[3];
+            orc_mlp_forward(M->surr_theta, B->u[i], B->v[i], M->surr_bf16, y);
+            w->hit[node] = 1;
+            for (int k = 0; k < 3; ++k) w->hitval[3 * node + k] = clamp01(y[k]);
+        }
+        if (c->off) continue;
+        uint64_t key = M->is_root[node] == 2
+                           ? orc_key_pos(mi, node, (uint32_t)c->pos_level, B->px[i], B->py[i], B->pz[i])
+                           : orc_key(mi, node, level, B->u[i], B->v[i]);
+        uint64_t cell, slot;
+        uint32_t h2;
+        cell_and_check(c, key, &cell, &h2);
+        w->rcell[node] = cell;
+        w->rh2[node] = h2;
+        int found = 0;
+        w->rclosed[node] = 0;
+        if (!surr) {
+            const int sc = scan_cell(c, cell, h2, &slot);
+            found = sc == 1;
+            /* Replacement: a cell that is full of entries whose classes are all at most
+             * the point's own can never take its value in this batch (classes in a
+             * full cell only decrease), so the value is dropped as full at lookup. */
+            if (sc < 0 && c->replace && c->close_at_lookup) {
+                const uint8_t q = B->vis ? B->vis[i] : 0;
+                uint8_t mx = 0;
+                for (uint32_t e = 0; e < c->n_entries; ++e)
+                    if (c->cls[cell * c->n_entries + e] > mx) mx = c->cls[cell * c->n_entries + e];
+                w->rclosed[node] = mx <= q;
+            }
+            w->stats[0]++;
+            if (found) {
+                w->hit[node] = 1;
+                for (int k = 0; k < 3; ++k) w->hitval[3 * node + k] = (double)c->rgb[3 * slot + k];
+                w->stats[1]++;
+                n_hit++;
+            } else {
+                w->stats[2]++;
+            }
+        }
+        if (B->probe_key) B->probe_key[probe] = key;
+        if (B->probe_cell) B->probe_cell[probe] = cell;
+        if (B->probe_h2) B->probe_h2[probe] = h2;
+        if (B->probe_hit) B->probe_hit[probe] = (uint8_t)found;
+        probe++;
+    }
+    /* Needed set: the output is needed; a needed node that is not a hit root needs its
+     * inputs (reverse storage order = reverse topological). */
+    memset(w->needed, 0, M->n);
+    w->needed[M->n - 1] = 1;
+    for (int32_t j = (int32_t)M->n - 1; j >= 0; --j) {
+        if (!w->needed[j] || w->hit[j]) continue;
+        for (int k = 0; k < 4; ++k)
+            if (M->nodes[j].in[k] >= 0) w->needed[M->nodes[j].in[k]] = 1;
+    }
+    /* Evaluation in storage order: hit roots take their cached value. */
+    uint32_t n_eval = 0;
+    double* val = w->val;
+    for (uint32_t j = 0; j < M->n; ++j) {
+        if (!w->needed[j]) continue;
+        if (w->hit[j]) {
+            for (int k = 0; k < 3; ++k) val[3 * j + k] = w->hitval[3 * j + k];
+            continue;
+        }
+        const orc_node* nd = &M->nodes[j];
+        orc_eval_node(nd, input_value(nd, 0, val), input_value(nd, 1, val), input_value(nd, 2, val), sp,
+                      &val[3 * j]);
+        n_eval++;
+        if (!c->off && M->is_root[j] && w->rclosed[j]) {
+            w->stats[3]++;
+            w->stats[6]++;
+        } else if (!c->off && M->is_root[j]) {
+            /* A missed root that was evaluated becomes an insert candidate carrying its
+             * own value rounded to FP32 (Sec. 3). */
+            if (w->n_cand == w->cand_cap) {
+                w->cand_cap *= 2;
+                w->cand = (orc_candidate*)realloc(w->cand, w->cand_cap * sizeof(orc_candidate));
+            }
+            orc_candidate* cd = &w->cand[w->n_cand++];
+            cd->cell = w->rcell[j];
+            cd->h2 = w->rh2[j];
+            cd->vis = B->vis ? B->vis[i] : 0;
+            for (int k = 0; k < 3; ++k) cd->rgb[k] = (float)val[3 * j + k];
+        }
+    }
+    w->stats[7] += n_eval;
+    for (int k = 0; k < 3; ++k) B->rgb[(size_t)k * n + i] = val[3 * (M->n - 1) + k];
+    if (B->hits) B->hits[i] = (uint16_t)n_hit;
+    if (B->evaluated) B->evaluated[i] = n_eval;
+}
+
+/* Points per range of the all-core form. */
+#define ORC_CHUNK 2048u
+
 int orc_run_batch(orc_cache* c, uint64_t n, const float* u, const float* v,
                   const uint32_t* mat, const float* px, const float* py, const float* pz,
                   const float* nx, const float* ny, const float* nz, double* rgb,
@@ -853,154 +1034,75 @@ int orc_run_batch(orc_cache* c, uint64_t n, const float* u, const float* v,
                   uint64_t* probe_cell, uint32_t* probe_h2, uint8_t* probe_hit,
                   const float* g1u, const float* g1v, const float* g2u, const float* g2v,
                   const uint8_t* vis) {
-    int status = ORC_OK;
+    const orc_batch B = {n, u, v, mat, px, py, pz, nx, ny, nz, rgb, hits, evaluated, probe_key, probe_cell,
+                         probe_h2, probe_hit, g1u, g1v, g2u, g2v, vis};
     uint32_t max_n = 1;
     for (uint32_t m = 0; m < c->n_mats; ++m)
         if (c->mats[m].n > max_n) max_n = c->mats[m].n;
-    double* val = (double*)malloc(3 * (size_t)max_n * sizeof(double));
-    uint8_t* hit = (uint8_t*)malloc(max_n);
-    double* hitval = (double*)malloc(3 * (size_t)max_n * sizeof(double));
-    uint8_t* needed = (uint8_t*)malloc(max_n);
-    uint64_t* rcell = (uint64_t*)malloc((size_t)max_n * sizeof(uint64_t));
-    uint32_t* rh2 = (uint32_t*)malloc((size_t)max_n * sizeof(uint32_t));
-    uint8_t* rclosed = (uint8_t*)malloc(max_n);   /* replacement: the cell cannot take it */
-    size_t cand_cap = 1024, n_cand = 0;
-    orc_candidate* cand = (orc_candidate*)malloc(cand_cap * sizeof(orc_candidate));
-    uint64_t probe = 0;
-
-    /* Phase L and evaluation: every point sees the table as it was when the
-     * batch started (with the paper's concurrent update, as the earlier points of the
-     * batch left it). */
-    for (uint64_t i = 0; i < n; ++i) {
-        if (mat[i] >= c->n_mats) {
-            status = ORC_ERR_BADMAT;
-            rgb[i] = rgb[n + i] = rgb[2 * n + i] = 0.0;
-            if (hits) hits[i] = 0;
-            if (evaluated) evaluated[i] = 0;
-            continue;
-        }
-        const orc_mat* M = &c->mats[mat[i]];
-        const double sp[8] = {u[i], v[i], px[i], py[i], pz[i], nx[i], ny[i], nz[i]};
-        /* the point's mip level: from its ray-cone gradients (Eq. 1) if given */
-        const uint32_t level =
-            g1u ? (uint32_t)orc_level(g1u[i], g1v[i], g2u[i], g2v[i], c->level_offset) : c->level;
-        uint32_t n_hit = 0;
-        memset(hit, 0, M->n);
-        for (uint32_t r = 0; r < M->n_roots; ++r) {
-            uint32_t node = M->roots[r];
-            /* a node with a learned surrogate takes the network's value, no lookup */
-            const int surr = M->surr_theta && node == M->surr_node;
-            if (surr) {
-                double y[3];
-                orc_mlp_forward(M->surr_theta, u[i], v[i], M->surr_bf16, y);
-                hit[node] = 1;
-                for (int k = 0; k < 3; ++k) hitval[3 * node + k] = clamp01(y[k]);
-            }
-            if (c->off) continue;
-            uint64_t key = M->is_root[node] == 2
-                               ? orc_key_pos(mat[i], node, (uint32_t)c->pos_level, px[i], py[i], pz[i])
-                               : orc_key(mat[i], node, level, u[i], v[i]);
-            uint64_t cell, slot;
-            uint32_t h2;
-            cell_and_check(c, key, &cell, &h2);
-            rcell[node] = cell;
-            rh2[node] = h2;
-            int found = 0;
-            rclosed[node] = 0;
-            if (!surr) {
-                const int sc = scan_cell(c, cell, h2, &slot);
-                found = sc == 1;
-                /* Replacement: a cell that is full of entries whose classes are all at most
-                 * the point's own can never take its value in this batch (classes in a
-                 * full cell only decrease), so the value is dropped as full at lookup. */
-                if (sc < 0 && c->replace && c->close_at_lookup) {
-                    const uint8_t q = vis ? vis[i] : 0;
-                    uint8_t mx = 0;
-                    for (uint32_t e = 0; e < c->n_entries; ++e)
-                        if (c->cls[cell * c->n_entries + e] > mx) mx = c->cls[cell * c->n_entries + e];
-                    rclosed[node] = mx <= q;
-                }
-                c->stats[0]++;
-                if (found) {
-                    hit[node] = 1;
-                    for (int k = 0; k < 3; ++k) hitval[3 * node + k] = (double)c->rgb[3 * slot + k];
-                    c->stats[1]++;
-                    n_hit++;
-                } else {
-                    c->stats[2]++;
-                }
-            }
-            if (probe_key) probe_key[probe] = key;
-            if (probe_cell) probe_cell[probe] = cell;
-            if (probe_h2) probe_h2[probe] = h2;
-            if (probe_hit) probe_hit[probe] = (uint8_t)found;
-            probe++;
-        }
-        /* Needed set: the output is needed; a needed node that is not a hit
-         * root needs its inputs (reverse storage order = reverse topological). */
-        memset(needed, 0, M->n);
-        needed[M->n - 1] = 1;
-        for (int32_t j = (int32_t)M->n - 1; j >= 0; --j) {
-            if (!needed[j] || hit[j]) continue;
-            for (int k = 0; k < 4; ++k)
-                if (M->nodes[j].in[k] >= 0) needed[M->nodes[j].in[k]] = 1;
-        }
-        /* Evaluation in storage order: hit roots take their cached value. */
-        uint32_t n_eval = 0;
-        for (uint32_t j = 0; j < M->n; ++j) {
-            if (!needed[j]) continue;
-            if (hit[j]) {
-                for (int k = 0; k < 3; ++k) val[3 * j + k] = hitval[3 * j + k];
-                continue;
-            }
-            const orc_node* nd = &M->nodes[j];
-            orc_eval_node(nd, input_value(nd, 0, val), input_value(nd, 1, val),
-                          input_value(nd, 2, val), sp, &val[3 * j]);
-            n_eval++;
-            if (!c->off && M->is_root[j] && rclosed[j]) {
-                c->stats[3]++;
-                c->stats[6]++;
-            } else if (!c->off && M->is_root[j]) {
-                /* A missed root that was evaluated becomes an insert candidate
-                 * carrying its own value rounded to FP32 (Sec. 3). */
-                if (n_cand == cand_cap) {
-                    cand_cap *= 2;
-                    cand = (orc_candidate*)realloc(cand, cand_cap * sizeof(orc_candidate));
-                }
-                cand[n_cand].cell = rcell[j];
-                cand[n_cand].h2 = rh2[j];
-                cand[n_cand].vis = vis ? vis[i] : 0;
-                for (int k = 0; k < 3; ++k) cand[n_cand].rgb[k] = (float)val[3 * j + k];
-                n_cand++;
+    int status = ORC_OK;
+    if (c->threads <= 1 || c->alg1) {
+        /* one point after another */
+        orc_work w;
+        work_init(&w, max_n);
+        uint64_t probe = 0;
+        for (uint64_t i = 0; i < n; ++i) {
+            process_point(c, &B, i, probe, &w);
+            if (mat[i] < c->n_mats && !c->off) probe += c->mats[mat[i]].n_roots;
+            if (c->alg1) {
+                /* the paper's concurrent update, serialised one shading point at a time:
+                 * the point's values are in the table before the next point looks up */
+                for (int k = 0; k < ORC_NSTATS; ++k) c->stats[k] += w.stats[k];
+                memset(w.stats, 0, sizeof(w.stats));
+                c->stats[3] += w.n_cand;
+                insert_candidates(c, w.cand, w.n_cand);
+                w.n_cand = 0;
             }
         }
-        c->stats[7] += n_eval;
-        for (int k = 0; k < 3; ++k) rgb[(size_t)k * n + i] = val[3 * (M->n - 1) + k];
-        if (hits) hits[i] = (uint16_t)n_hit;
-        if (evaluated) evaluated[i] = n_eval;
-        if (c->alg1) {
-            /* the paper's concurrent update, serialised one shading point at a time:
-             * the point's values are in the table before the next point looks up */
-            c->stats[3] += n_cand;
-            insert_candidates(c, cand, n_cand);
-            n_cand = 0;
+        for (int k = 0; k < ORC_NSTATS; ++k) c->stats[k] += w.stats[k];
+        status = w.status;
+        /* Phase I: candidates were produced in ascending (point index, node ID) order;
+         * insert them one at a time in that order (Alg. 1 serialised: the CAS on an
+         * empty entry always succeeds; the first value is kept). */
+        c->stats[3] += w.n_cand;
+        insert_candidates(c, w.cand, w.n_cand);
+        work_free(&w);
+    } else {
+        /* All cores: ranges of points evaluated in parallel against the same snapshot of
+         * the table (no point of phase L writes it), then every range's candidates in
+         * range order, i.e. ascending (point index, node ID), inserted one at a time. */
+        const uint64_t n_chunks = (n + ORC_CHUNK - 1) / ORC_CHUNK;
+        uint64_t* probe0 = (uint64_t*)malloc((n_chunks + 1) * sizeof(uint64_t));
+        probe0[0] = 0;
+        for (uint64_t ch = 0; ch < n_chunks; ++ch) {
+            uint64_t p = probe0[ch];
+            for (uint64_t i = ch * ORC_CHUNK; i < n && i < (ch + 1) * ORC_CHUNK; ++i)
+                if (mat[i] < c->n_mats && !c->off) p += c->mats[mat[i]].n_roots;
+            probe0[ch + 1] = p;
         }
+        orc_work* works = (orc_work*)malloc((n_chunks ? n_chunks : 1) * sizeof(orc_work));
+#pragma omp parallel for schedule(dynamic, 1) num_threads(c->threads)
+        for (int64_t ch = 0; ch < (int64_t)n_chunks; ++ch) {
+            orc_work* w = &works[ch];
+            work_init(w, max_n);
+            uint64_t probe = probe0[ch];
+            for (uint64_t i = (uint64_t)ch * ORC_CHUNK; i < n && i < ((uint64_t)ch + 1) * ORC_CHUNK; ++i) {
+                process_point(c, &B, i, probe, w);
+                if (mat[i] < c->n_mats && !c->off) probe += c->mats[mat[i]].n_roots;
+            }
+        }
+        for (uint64_t ch = 0; ch < n_chunks; ++ch) {
+            for (int k = 0; k < ORC_NSTATS; ++k) c->stats[k] += works[ch].stats[k];
+            if (works[ch].status != ORC_OK) status = works[ch].status;
+        }
+        for (uint64_t ch = 0; ch < n_chunks; ++ch) {
+            c->stats[3] += works[ch].n_cand;
+            insert_candidates(c, works[ch].cand, works[ch].n_cand);
+            work_free(&works[ch]);
+        }
+        free(works);
+        free(probe0);
     }
-
-    /* Phase I: candidates were produced in ascending (point index, node ID)
-     * order; insert them one at a time in that order (Alg. 1 serialised: the
-     * CAS on an empty entry always succeeds; the first value is kept). */
-    c->stats[3] += n_cand;
-    insert_candidates(c, cand, n_cand);
     c->stats[8]++;
-    free(val);
-    free(hit);
-    free(hitval);
-    free(needed);
-    free(rcell);
-    free(rh2);
-    free(rclosed);
-    free(cand);
     return status;
 }
 

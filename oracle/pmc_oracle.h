@@ -183,6 +183,11 @@ void orc_cache_set_replacement(orc_cache* c, int on);
 void orc_cache_set_close_at_lookup(orc_cache* c, int on);
 /* The cost threshold of cacheable nodes (orc_analyze_cost); set it before the materials. */
 void orc_cache_set_min_root_cost(orc_cache* c, uint32_t cost);
+/* Host threads that orc_run_batch spreads the lookup and evaluation phase over (ranges of
+ * points against the same snapshot of the table; the insert stays one candidate at a time
+ * in ascending (point index, node ID) order, so the results are those of one thread).  The
+ * paper's concurrent update (orc_cache_set_alg1) always runs on one thread. */
+void orc_cache_set_threads(orc_cache* c, int threads);
 /* level >= 0: the world-position descriptor (Sec. 3.1 names world-space position as a
  * further descriptor, Sec. 5 lists it as future work).  A node whose sub-graph depends on
  * the shading point's position and on nothing else of it is cacheable too; its key is

@@ -27,6 +27,8 @@ struct pmc_cache {
     int unsorted = 0;                     // PMC_UNSORTED schedule
     int probe_inline = 0;                 // PMC_PROBE_INLINE schedule
     uint32_t lookup_rb = 4;               // probes in flight per lane in k_lookup
+    int block_items = 0;                  // PMC_BLOCK_ITEMS schedule
+    int one_point = 0;                    // PMC_ONE_POINT schedule
     uint64_t layout_gen = 1;              // bumped whenever a recorded graph would go stale
     uint32_t prog_len = 0;
     // device-resident, owned
@@ -41,7 +43,8 @@ struct pmc_cache {
     unsigned long long* d_stats = nullptr;
     pmc::RootInfo* d_rinfo = nullptr;
     uint32_t* d_miss_cnt = nullptr;       // roots + MAX_LEVELS
-    uint32_t* d_root_items = nullptr;     // roots + 1
+    uint32_t* d_root_items = nullptr;     // roots + 1, then MAX_LEVELS + 1 level item starts
+    uint32_t* d_root_order = nullptr;     // roots by ascending level, then MAX_LEVELS + 1 starts
     uint32_t n_bins = 0;                  // cell-grouped insert bins
     bool table_empty = true;              // nothing inserted since creation or reset
     bool last_all_miss = false;           // the last batch ran on an empty table
@@ -75,6 +78,14 @@ struct pmc_cache {
     float* d_hpts = nullptr;        // 8 float planes + 1 uint32 plane
     float* d_hrgb = nullptr;
     uint16_t* d_hhits = nullptr;
+    // double-buffered staging of pmc_eval_passes_host: copies of one pass overlap the
+    // evaluation of its neighbours, on two library-owned copy streams
+    uint64_t cap_pipe = 0;
+    float* d_pin[2] = {nullptr, nullptr};     // 13 float planes + one for the classes
+    float* d_prgb[2] = {nullptr, nullptr};
+    uint16_t* d_phits[2] = {nullptr, nullptr};
+    cudaStream_t s_h2d = nullptr, s_d2h = nullptr;
+    cudaEvent_t ev_in[2] = {nullptr, nullptr}, ev_done[2] = {nullptr, nullptr}, ev_out[2] = {nullptr, nullptr};
     // state
     cudaStream_t last_stream = nullptr;
     pmc_status sticky = PMC_OK;

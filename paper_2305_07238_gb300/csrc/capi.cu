@@ -14,6 +14,42 @@ using namespace pmc;
 
 namespace {
 
+// The device form of a compiled instruction: slots become byte offsets into the slot file,
+// a MIX reading its factor from a node gets FLAG_IN2, parameter offsets move by the
+// material's base in the pool.  *ok is cleared if a slot is beyond the 16-bit offsets.
+uint4 device_ins(uint4 ins, uint32_t pbase, bool* ok) {
+    const uint32_t op = ins.x & 0xFFu;
+    auto off = [&](uint32_t slot) -> uint32_t {
+        if (slot == 0xFFFFu) return 0u;   // no such input
+        if (slot > MAX_DEVICE_SLOTS) *ok = false;
+        return slot * SLOT_BYTES;
+    };
+    if (op == OP_ROOT_BEGIN || op == OP_LOAD_ROOT) {
+        ins.y = off(ins.y & 0xFFFFu) | (ins.y & 0xFFFF0000u);   // out | ordinal
+        return ins;
+    }
+    uint32_t flags = (ins.x >> 8) & 0xFFu;
+    if (op == PMC_OP_MIX && (ins.z >> 16) != 0xFFFFu) flags |= FLAG_IN2;
+    ins.x = (ins.x & ~0xFF00u) | (flags << 8);
+    ins.y = off(ins.y & 0xFFFFu) | (off(ins.y >> 16) << 16);
+    ins.z = off(ins.z & 0xFFFFu) | (off(ins.z >> 16) << 16);
+    ins.w += pbase;
+    return ins;
+}
+
+// Nodes and FP32 operations of one run of a program in which every node instruction runs.
+void program_totals(const std::vector<uint4>& prog, uint32_t* nodes, uint32_t* flops) {
+    uint64_t n = 0, f = 0;
+    for (const uint4& ins : prog) {
+        const uint32_t op = ins.x & 0xFFu;
+        if (op == OP_ROOT_BEGIN || op == OP_LOAD_ROOT) continue;
+        n++;
+        f += ins.x >> 16;
+    }
+    *nodes = (uint32_t)std::min<uint64_t>(n, 0xFFFFFFFFull);
+    *flops = (uint32_t)std::min<uint64_t>(f, 0xFFFFFFFFull);
+}
+
 struct DeviceGuard {
     int prev = -1;
     bool ok = true;
@@ -163,6 +199,7 @@ void pmc_destroy_cache(pmc_cache* c) {
         dfree(&c->d_rinfo);
         dfree(&c->d_miss_cnt);
         dfree(&c->d_root_items);
+        dfree(&c->d_root_order);
         dfree(&c->d_bins);
         dfree(&c->d_surr_theta);
         dfree(&c->d_surr_slot);
@@ -171,6 +208,16 @@ void pmc_destroy_cache(pmc_cache* c) {
         dfree(&c->d_hpts);
         dfree(&c->d_hrgb);
         dfree(&c->d_hhits);
+        for (int b = 0; b < 2; ++b) {
+            dfree(&c->d_pin[b]);
+            dfree(&c->d_prgb[b]);
+            dfree(&c->d_phits[b]);
+            if (c->ev_in[b]) cudaEventDestroy(c->ev_in[b]);
+            if (c->ev_done[b]) cudaEventDestroy(c->ev_done[b]);
+            if (c->ev_out[b]) cudaEventDestroy(c->ev_out[b]);
+        }
+        if (c->s_h2d) cudaStreamDestroy(c->s_h2d);
+        if (c->s_d2h) cudaStreamDestroy(c->s_d2h);
     }
     delete c;
 }
@@ -203,6 +250,8 @@ pmc_status pmc_create_cache(const pmc_cache_desc* desc, const pmc_material* mats
     c->split = (desc->flags & PMC_EVAL_INLINE) ? 0 : 1;
     c->unsorted = (desc->flags & PMC_UNSORTED) ? 1 : 0;
     c->probe_inline = (desc->flags & PMC_PROBE_INLINE) ? 1 : 0;
+    c->block_items = (desc->flags & PMC_BLOCK_ITEMS) ? 1 : 0;
+    c->one_point = (desc->flags & PMC_ONE_POINT) ? 1 : 0;
     c->n_mats = n_mats;
 
     std::vector<uint4> prog;
@@ -226,10 +275,10 @@ pmc_status pmc_create_cache(const pmc_cache_desc* desc, const pmc_material* mats
         mi.n_nodes = cm.n_nodes;
         params.resize((params.size() + 3) & ~size_t(3), 0.0f);   // 16-byte aligned per material
         const uint32_t pbase = (uint32_t)params.size();
-        for (uint4 ins : cm.prog) {
-            if ((ins.x & 0xFFu) != OP_ROOT_BEGIN) ins.w += pbase;
-            prog.push_back(ins);
-        }
+        bool slots_ok = true;
+        for (uint4 ins : cm.prog) prog.push_back(device_ins(ins, pbase, &slots_ok));
+        program_totals(cm.prog, &mi.full_nodes, &mi.full_flops);
+        program_totals(cm.outer_prog, &mi.outer_nodes, &mi.outer_flops);
         int32_t cand = -1;
         uint64_t best_cost = 0;
         for (size_t r = 0; r < cm.roots.size(); ++r) {
@@ -244,10 +293,7 @@ pmc_status pmc_create_cache(const pmc_cache_desc* desc, const pmc_material* mats
         mi.outer_len = (uint32_t)cm.outer_prog.size();
         mi.outer_out_slot = cm.outer_out_slot;
         mi.outer_slots = cm.outer_slots;
-        for (uint4 ins : cm.outer_prog) {
-            if ((ins.x & 0xFFu) != OP_LOAD_ROOT) ins.w += pbase;
-            prog.push_back(ins);
-        }
+        for (uint4 ins : cm.outer_prog) prog.push_back(device_ins(ins, pbase, &slots_ok));
         c->max_slots_outer = std::max(c->max_slots_outer, cm.outer_slots);
         for (size_t r = 0; r < cm.roots.size(); ++r) {
             RootInfo ri{};
@@ -259,14 +305,16 @@ pmc_status pmc_create_cache(const pmc_cache_desc* desc, const pmc_material* mats
             ri.n_slots = cm.root_slots[r];
             ri.node = cm.roots[r];
             ri.out_slot = cm.root_out_slot[r];
-            for (uint4 ins : cm.root_progs[r]) {
-                uint32_t op = ins.x & 0xFFu;
-                if (op != OP_ROOT_BEGIN && op != OP_LOAD_ROOT) ins.w += pbase;
-                prog.push_back(ins);
-            }
+            program_totals(cm.root_progs[r], &ri.nodes, &ri.flops);
+            for (uint4 ins : cm.root_progs[r]) prog.push_back(device_ins(ins, pbase, &slots_ok));
             c->root_info.push_back(ri);
             c->max_level = std::max(c->max_level, ri.level);
             c->max_slots_roots = std::max(c->max_slots_roots, ri.n_slots);
+        }
+        if (!slots_ok) {
+            fprintf(stderr, "pmc: material %u needs more than %u live values\n", m, MAX_DEVICE_SLOTS);
+            delete c;
+            return PMC_ERR_UNSUPPORTED;
         }
         params.insert(params.end(), cm.params.begin(), cm.params.end());
         c->roots.insert(c->roots.end(), cm.roots.begin(), cm.roots.end());
@@ -276,6 +324,9 @@ pmc_status pmc_create_cache(const pmc_cache_desc* desc, const pmc_material* mats
         c->max_roots = std::max(c->max_roots, mi.n_roots);
         c->max_slots = std::max(c->max_slots, mi.n_slots);
     }
+    // the interpreters fetch one instruction ahead of the one they run: a zero instruction
+    // past the last program keeps that read inside the pool
+    prog.push_back(make_uint4(0, 0, 0, 0));
     c->prog_len = (uint32_t)prog.size();
     // the interpreters fetch eight parameters ahead of a node, even one without any
     params.resize(((params.size() + 3) & ~size_t(3)) + 8, 0.0f);
@@ -306,7 +357,8 @@ pmc_status pmc_create_cache(const pmc_cache_desc* desc, const pmc_material* mats
         (s = dalloc(&c->d_stats, ST_COUNT)) != PMC_OK ||
         (s = dalloc(&c->d_rinfo, c->root_info.size())) != PMC_OK ||
         (s = dalloc(&c->d_miss_cnt, c->root_info.size() + MAX_LEVELS)) != PMC_OK ||
-        (s = dalloc(&c->d_root_items, c->root_info.size() + 1)) != PMC_OK ||
+        (s = dalloc(&c->d_root_items, c->root_info.size() + 1 + MAX_LEVELS + 1)) != PMC_OK ||
+        (s = dalloc(&c->d_root_order, c->root_info.size() + MAX_LEVELS + 1)) != PMC_OK ||
         (s = dalloc(&c->d_bins, 3 * (size_t)c->n_bins + 1)) != PMC_OK ||
         (s = dalloc(&c->d_surr_slot, n_mats)) != PMC_OK ||
         (s = dalloc(&c->d_surr_ord, n_mats)) != PMC_OK ||
@@ -322,6 +374,24 @@ pmc_status pmc_create_cache(const pmc_cache_desc* desc, const pmc_material* mats
         e = cudaMemcpy(c->d_rinfo, c->root_info.data(), c->root_info.size() * sizeof(RootInfo), cudaMemcpyHostToDevice);
     if (e == cudaSuccess && !c->roots.empty())
         e = cudaMemcpy(c->d_roots, c->roots_dev.data(), c->roots_dev.size() * sizeof(uint32_t), cudaMemcpyHostToDevice);
+    {
+        // cacheable nodes by ascending nesting level (stable), then where each level starts
+        std::vector<uint32_t> order(c->root_info.size());
+        for (uint32_t g = 0; g < order.size(); ++g) order[g] = g;
+        std::stable_sort(order.begin(), order.end(), [&](uint32_t x, uint32_t y) {
+            return c->root_info[x].level < c->root_info[y].level;
+        });
+        const size_t n_roots = order.size();
+        std::vector<uint32_t> starts(MAX_LEVELS + 1);
+        for (uint32_t l = 0; l <= MAX_LEVELS; ++l) {
+            uint32_t start = 0;
+            while (start < n_roots && c->root_info[order[start]].level < l) ++start;
+            starts[l] = start;
+        }
+        order.insert(order.end(), starts.begin(), starts.end());
+        if (e == cudaSuccess)
+            e = cudaMemcpy(c->d_root_order, order.data(), order.size() * sizeof(uint32_t), cudaMemcpyHostToDevice);
+    }
     c->surr_slot.assign(n_mats, -1);
     c->surr_on.assign(n_mats, 0);
     if (e == cudaSuccess) e = cudaMemset(c->d_surr_slot, 0xFF, n_mats * sizeof(int32_t));
@@ -417,9 +487,12 @@ pmc_status enqueue_batch(pmc_cache* c, const pmc_points* pts, float* out_rgb, ui
     }
     a.rinfo = c->d_rinfo; a.n_roots_total = (uint32_t)c->root_info.size(); a.max_level = c->max_level;
     a.miss_cnt = c->d_miss_cnt; a.root_item_base = c->d_root_items; a.misslist = c->d_misslist;
+    a.root_order = c->d_root_order; a.level_start = c->d_root_order + c->root_info.size();
     a.unsorted = c->unsorted;
     a.probe_inline = c->probe_inline;
     a.lookup_rb = c->lookup_rb;
+    a.block_items = c->block_items;
+    a.one_point = c->one_point;
     if (replacing(c)) {
         a.slot_cls = c->d_cls;
         a.vis = pts->vis;
@@ -511,6 +584,92 @@ pmc_status pmc_eval_batch_host(pmc_cache* c, const pmc_points* hp, float* host_r
         e = cudaMemcpyAsync(host_rgb + k * n, c->d_hrgb + k * n, n * 4, cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess && host_hits && n)
         e = cudaMemcpyAsync(host_hits, c->d_hhits, n * 2, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(c, e);
+    return fold_device_errors(c);
+}
+
+pmc_status pmc_eval_passes_host(pmc_cache* c, const pmc_points* hp, uint32_t n_passes, float* const* host_rgb,
+                                 uint16_t* const* host_hits, void* stream) {
+    if (!c || (n_passes && (!hp || !host_rgb))) return PMC_ERR_INVALID_ARG;
+    if (c->sticky != PMC_OK) return c->sticky;
+    uint64_t nmax = 0;
+    for (uint32_t p = 0; p < n_passes; ++p) {
+        pmc_status cs = check_points(&hp[p], host_rgb[p]);
+        if (cs != PMC_OK) return cs;
+        nmax = std::max<uint64_t>(nmax, hp[p].n);
+    }
+    DeviceGuard g(c->desc.device);
+    if (!g.ok) return PMC_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t e = cudaSuccess;
+    if (!c->s_h2d) {
+        if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->s_h2d, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->s_d2h, cudaStreamNonBlocking);
+        for (int b = 0; b < 2 && e == cudaSuccess; ++b) {
+            e = cudaEventCreateWithFlags(&c->ev_in[b], cudaEventDisableTiming);
+            if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_done[b], cudaEventDisableTiming);
+            if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_out[b], cudaEventDisableTiming);
+        }
+        if (e != cudaSuccess) return cuda_fail(c, e);
+    }
+    if (nmax > c->cap_pipe) {
+        cudaDeviceSynchronize();
+        for (int b = 0; b < 2; ++b) {
+            dfree(&c->d_pin[b]);
+            dfree(&c->d_prgb[b]);
+            dfree(&c->d_phits[b]);
+        }
+        c->cap_pipe = 0;
+        pmc_status st;
+        for (int b = 0; b < 2; ++b)
+            if ((st = dalloc(&c->d_pin[b], 14 * (size_t)nmax)) != PMC_OK || (st = dalloc(&c->d_prgb[b], 3 * (size_t)nmax)) != PMC_OK ||
+                (st = dalloc(&c->d_phits[b], (size_t)nmax)) != PMC_OK)
+                return st;
+        c->cap_pipe = nmax;
+    }
+    // both staging sets start free once whatever the caller's stream has enqueued so far
+    // has run (an earlier call's last passes may still be reading them)
+    e = cudaEventRecord(c->ev_done[0], s);
+    if (e == cudaSuccess) e = cudaEventRecord(c->ev_done[1], s);
+    if (e == cudaSuccess) e = cudaEventRecord(c->ev_out[0], s);
+    if (e == cudaSuccess) e = cudaEventRecord(c->ev_out[1], s);
+    const size_t C = c->cap_pipe;
+    for (uint32_t p = 0; p < n_passes && e == cudaSuccess; ++p) {
+        const int b = p & 1;
+        const pmc_points& h = hp[p];
+        const uint64_t n = h.n;
+        const bool cones = h.g1u != nullptr;
+        float* d = c->d_pin[b];
+        // inputs of pass p into set b once the pass that used it last has run
+        e = cudaStreamWaitEvent(c->s_h2d, c->ev_done[b], 0);
+        const void* src[13] = {h.u, h.v, h.mat, h.px, h.py, h.pz, h.nx, h.ny, h.nz, h.g1u, h.g1v, h.g2u, h.g2v};
+        const int planes = cones ? 13 : 9;
+        for (int k = 0; k < planes && e == cudaSuccess && n; ++k)
+            e = cudaMemcpyAsync(d + k * C, src[k], n * 4, cudaMemcpyHostToDevice, c->s_h2d);
+        const uint8_t* dvis = h.vis ? reinterpret_cast<const uint8_t*>(d + 13 * C) : nullptr;
+        if (e == cudaSuccess && h.vis && n) e = cudaMemcpyAsync((void*)dvis, h.vis, n, cudaMemcpyHostToDevice, c->s_h2d);
+        if (e == cudaSuccess) e = cudaEventRecord(c->ev_in[b], c->s_h2d);
+        // the pass, once its inputs are in and the outputs of set b have been copied out
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(s, c->ev_in[b], 0);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(s, c->ev_out[b], 0);
+        if (e != cudaSuccess) break;
+        pmc_points dp{d, d + C, (const uint32_t*)(d + 2 * C), d + 3 * C, d + 4 * C, d + 5 * C, d + 6 * C, d + 7 * C,
+                      d + 8 * C, n, cones ? d + 9 * C : nullptr, cones ? d + 10 * C : nullptr,
+                      cones ? d + 11 * C : nullptr, cones ? d + 12 * C : nullptr, dvis};
+        uint16_t* hh = (host_hits && host_hits[p]) ? c->d_phits[b] : nullptr;
+        pmc_status st = enqueue_batch(c, &dp, c->d_prgb[b], hh, s, false);
+        if (st != PMC_OK) return st;
+        e = cudaEventRecord(c->ev_done[b], s);
+        // outputs of pass p out of set b
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(c->s_d2h, c->ev_done[b], 0);
+        for (int k = 0; k < 3 && e == cudaSuccess && n; ++k)
+            e = cudaMemcpyAsync(host_rgb[p] + k * n, c->d_prgb[b] + k * n, n * 4, cudaMemcpyDeviceToHost, c->s_d2h);
+        if (e == cudaSuccess && hh && n)
+            e = cudaMemcpyAsync(host_hits[p], hh, n * 2, cudaMemcpyDeviceToHost, c->s_d2h);
+        if (e == cudaSuccess) e = cudaEventRecord(c->ev_out[b], c->s_d2h);
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->s_d2h);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return cuda_fail(c, e);
     return fold_device_errors(c);
@@ -851,7 +1010,8 @@ pmc_status pmc_train_surrogates(pmc_cache* c, const pmc_train_desc* d, float* rm
     const float lr = d->lr > 0.0f ? d->lr : 1e-2f;
     for (uint32_t done = 0; e == cudaSuccess && done < total;) {
         const uint32_t chunk = std::min<uint32_t>(total - done, 256u);
-        e = launch_mlp_train(theta, m1, m2, nullptr, data, loss, L, d->n_train, chunk, (uint64_t)done * 128u, done,
+        e = launch_mlp_train(theta, m1, m2, nullptr, data, loss, &c->d_ctl->err, L, d->n_train, chunk,
+                             (uint64_t)done * 128u, done,
                              total, lr, 2.0f / (3.0f * 128.0f), 0, 1, s);
         done += chunk;
     }
@@ -970,7 +1130,8 @@ pmc_status pmc_mlp_gradient(const float* theta, const float* data, uint64_t n, f
     if (e == cudaSuccess) e = cudaMemsetAsync(loss, 0, sizeof(float), s);
     // gradient mode: one step of 128 rows per block, rows taken in order
     if (e == cudaSuccess)
-        e = launch_mlp_train(const_cast<float*>(theta), nullptr, nullptr, grad, data, loss, 1, (uint32_t)n, 1, 0, 0, 1,
+        e = launch_mlp_train(const_cast<float*>(theta), nullptr, nullptr, grad, data, loss, nullptr, 1, (uint32_t)n, 1,
+                             0, 0, 1,
                              0.0f, 2.0f / (3.0f * (float)n), 1, (uint32_t)(n / 128), s);
     return e == cudaSuccess ? PMC_OK : cuda_fail(nullptr, e);
 }
@@ -979,7 +1140,7 @@ pmc_status pmc_mlp_train(float* theta, float* adam_m, float* adam_v, const float
                          uint32_t step0, uint32_t total_steps, float lr, float* loss, void* stream) {
     if (!theta || !adam_m || !adam_v || !data || !loss || n < 128 || (n & (n - 1)) || n >= (1ull << 31))
         return PMC_ERR_INVALID_ARG;
-    cudaError_t e = launch_mlp_train(theta, adam_m, adam_v, nullptr, data, loss, 1, (uint32_t)n, steps,
+    cudaError_t e = launch_mlp_train(theta, adam_m, adam_v, nullptr, data, loss, nullptr, 1, (uint32_t)n, steps,
                                      (uint64_t)step0 * 128u, step0, total_steps, lr, 2.0f / (3.0f * 128.0f), 0, 1,
                                      (cudaStream_t)stream);
     return e == cudaSuccess ? PMC_OK : cuda_fail(nullptr, e);
@@ -1008,14 +1169,16 @@ pmc_status pmc_compute_keys(const uint32_t* mat, const uint32_t* node, const flo
 pmc_status pmc_get_schedule(const pmc_cache* c, pmc_schedule* out) {
     if (!c || !out) return PMC_ERR_INVALID_ARG;
     out->flags = (c->split ? 0u : PMC_EVAL_INLINE) | ((c->desc.flags & PMC_INSERT_ROUNDS) ? PMC_INSERT_ROUNDS : 0u) |
-                 (c->unsorted ? PMC_UNSORTED : 0u) | (c->probe_inline ? PMC_PROBE_INLINE : 0u);
+                 (c->unsorted ? PMC_UNSORTED : 0u) | (c->probe_inline ? PMC_PROBE_INLINE : 0u) |
+                 (c->block_items ? PMC_BLOCK_ITEMS : 0u) | (c->one_point ? PMC_ONE_POINT : 0u);
     out->lookup_rb = c->lookup_rb;
     return PMC_OK;
 }
 
 pmc_status pmc_set_schedule(pmc_cache* c, const pmc_schedule* sc) {
     if (!c || !sc) return PMC_ERR_INVALID_ARG;
-    const uint32_t known = PMC_EVAL_INLINE | PMC_INSERT_ROUNDS | PMC_UNSORTED | PMC_PROBE_INLINE;
+    const uint32_t known =
+        PMC_EVAL_INLINE | PMC_INSERT_ROUNDS | PMC_UNSORTED | PMC_PROBE_INLINE | PMC_BLOCK_ITEMS | PMC_ONE_POINT;
     if (sc->flags & ~known) return PMC_ERR_INVALID_ARG;
     if (sc->lookup_rb != 1 && sc->lookup_rb != 2 && sc->lookup_rb != 4) return PMC_ERR_INVALID_ARG;
     if ((sc->flags & PMC_UNSORTED) && surrogates_active(c)) return PMC_ERR_UNSUPPORTED;
@@ -1024,6 +1187,8 @@ pmc_status pmc_set_schedule(pmc_cache* c, const pmc_schedule* sc) {
     c->split = (sc->flags & PMC_EVAL_INLINE) ? 0 : 1;
     c->unsorted = (sc->flags & PMC_UNSORTED) ? 1 : 0;
     c->probe_inline = (sc->flags & PMC_PROBE_INLINE) ? 1 : 0;
+    c->block_items = (sc->flags & PMC_BLOCK_ITEMS) ? 1 : 0;
+    c->one_point = (sc->flags & PMC_ONE_POINT) ? 1 : 0;
     c->lookup_rb = sc->lookup_rb;
     c->desc.flags = (c->desc.flags & ~PMC_INSERT_ROUNDS) | (sc->flags & PMC_INSERT_ROUNDS);
     c->layout_gen++;
@@ -1184,6 +1349,10 @@ pmc_status pmc_autotune(pmc_cache* c, const pmc_points* sample, uint32_t reps, p
             cand.push_back({keep, 2});
             cand.push_back({keep, 1});
         }
+        // the per-point evaluator's work distribution: warp pairs of items (above), block-wide
+        // tiles of one material, one point per lane
+        cand.push_back({keep | PMC_BLOCK_ITEMS, c->use_cache ? 2u : 4u});
+        cand.push_back({keep | PMC_ONE_POINT, c->use_cache ? 2u : 4u});
     }
     if (!alg1_table(c)) {
         if (c->use_cache) cand.push_back({keep | PMC_EVAL_INLINE, 4});

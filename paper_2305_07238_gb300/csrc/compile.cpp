@@ -183,10 +183,26 @@ void pack_params(const pmc_node& nd, std::vector<float>* pool) {
         pool->insert(pool->end(), {p[0], p[1], p[2], p[3], p[4], p[5], p[6]});
         break;
     case PMC_OP_RAMP: {
-        int ns = nd.ip[0];
-        pool->push_back(bits(ns));
-        for (int k = 0; k < 4; ++k) pool->push_back(p[k]);
-        for (int k = 0; k < 12; ++k) pool->push_back(p[4 + k]);
+        // {first stop, last stop, second stop, third stop} (an absent interior stop reads 2,
+        // above every clamped input), then (stop k, 1 / (stop k+1 - stop k)) of segments 0..2,
+        // two floats of padding, the colours of stops 0..3 and of the last stop, each padded
+        // to four floats; 32 floats, so every group is one aligned vector load
+        const int ns = nd.ip[0];
+        float q[32] = {};
+        q[0] = p[0];
+        q[1] = p[ns - 1];
+        q[2] = ns > 2 ? p[1] : 2.0f;
+        q[3] = ns > 3 ? p[2] : 2.0f;
+        for (int k = 0; k + 1 < ns; ++k) {
+            const double len = (double)p[k + 1] - (double)p[k];
+            q[4 + 2 * k] = p[k];
+            // an empty segment is never selected (no t lies in it); a tiny one saturates
+            q[5 + 2 * k] = len > 0.0 ? (float)std::min(1.0 / len, 3.0e38) : 0.0f;
+        }
+        for (int k = 0; k < ns; ++k)
+            for (int c = 0; c < 3; ++c) q[12 + 4 * k + c] = p[4 + 3 * k + c];
+        for (int c = 0; c < 3; ++c) q[28 + c] = p[4 + 3 * (ns - 1) + c];
+        pool->insert(pool->end(), q, q + 32);
         break;
     }
     case PMC_OP_MIX: case PMC_OP_POW:

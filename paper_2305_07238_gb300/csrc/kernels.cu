@@ -318,7 +318,7 @@ __device__ __forceinline__ int scan_words(const uint4 (&w)[NQ], uint32_t h2, uin
 // overlapped across the group: first every probe's hash2 words, then the values of
 // the hits.  Records and miss lists are written after both.
 template <int NQ, int RB, bool POS>
-__global__ void __launch_bounds__(256) k_lookup(BatchArgs a) {
+__global__ void __launch_bounds__(256, 4) k_lookup(BatchArgs a) {
     const uint32_t warp = threadIdx.x >> 5, lane = lane_id();
     const uint32_t warps_total = gridDim.x * (blockDim.x >> 5);
     const uint32_t n_items = a.ctl->n_items;
@@ -433,6 +433,10 @@ size_t eval_smem_bytes(uint32_t max_slots) {
     return (size_t)EVAL_WARPS * max_slots * 3u * 32u * sizeof(float);
 }
 
+// Largest slot file (bytes per block) with which the two-points-per-lane evaluator runs:
+// six blocks of its size fit an SM's shared memory.
+constexpr size_t EVAL2_MAX_SMEM = 36 * 1024;
+
 // Offers the lanes' freshly evaluated cacheable-node values to the table (Sec. 3).
 // `full`: the cell cannot take the value in this batch, so it is counted as dropped
 // without becoming a candidate.  Keep-first: the cell was full at lookup (nothing is
@@ -483,19 +487,27 @@ __device__ __forceinline__ void offer(const BatchArgs& a, bool act, uint32_t ori
 }
 
 // Per-point interpreter: one warp runs one material's program for 32 grouped points.
-// split == 1: every cacheable node already has its value in its probe record (a hit,
-// or computed by k_eval_roots), so every block is skipped by the whole warp.
-// split == 0: a lane whose lookup hit skips the block, the others evaluate it inline.
+// EVAL_OUTER: every cacheable node already has its value in its probe record (a hit, a
+//   value computed by k_eval_roots or a learned surrogate), so the outer program runs:
+//   each block replaced by a load of its node's record.
+// EVAL_PLAIN: the cache is off; the whole program runs for every point.
+// EVAL_GENERIC: the whole program with per-lane skipping: the first pass on an empty table
+//   (descriptors formed here, every cacheable node offered), the inline evaluation of
+//   misses (a lane whose lookup hit skips the block), learned surrogates on that pass.
+// In the first two modes every lane runs every instruction: a lane past the end of its
+// material's points shadows the segment's last point and stores nothing, and the node and
+// operation counts come from the program's totals.
+enum { EVAL_OUTER = 0, EVAL_PLAIN = 1, EVAL_GENERIC = 2 };
+
+template <int MODE>
 __global__ void __launch_bounds__(EVAL_WARPS * 32) k_eval(BatchArgs a, uint32_t* item_ctr) {
     extern __shared__ float s_val[];
     __shared__ float2 s_grad[8];
     init_gradients(s_grad);
     __syncthreads();
     const uint32_t warp = threadIdx.x >> 5, lane = lane_id();
-    // when the batched evaluation has given every cacheable node a value, the outer
-    // program runs: each block replaced by a load of its node's record
-    const bool outer = a.split && !a.keys_inline;
-    float* V = s_val + (size_t)warp * (outer ? a.max_slots_outer : a.max_slots) * 96u + lane;
+    constexpr bool outer = MODE == EVAL_OUTER;
+    char* Vb = reinterpret_cast<char*>(s_val + (size_t)warp * (outer ? a.max_slots_outer : a.max_slots) * 96u + lane);
     const uint32_t n_items = a.ctl->n_items;
     unsigned long long n_nodes = 0, n_flops = 0, n_cand = 0, n_full = 0, n_look = 0;
     for (;;) {
@@ -507,135 +519,321 @@ __global__ void __launch_bounds__(EVAL_WARPS * 32) k_eval(BatchArgs a, uint32_t*
         const uint32_t cnt = __ldg(&a.counts[m]);
         const uint32_t j = (item - __ldg(&a.item_base[m])) * 32u + lane;
         const bool valid = j < cnt;
-        const uint32_t s = __ldg(&a.seg_start[m]) + (valid ? j : 0u);
-        PointIn pt{0, 0, 0, 0, 0, 0, 0, 0};
-        uint32_t orig = 0;
-        if (valid) {
-            pt.u = a.su[s]; pt.v = a.sv[s];
-            pt.px = a.spx[s]; pt.py = a.spy[s]; pt.pz = a.spz[s];
-            pt.nx = a.snx[s]; pt.ny = a.sny[s]; pt.nz = a.snz[s];
-            orig = a.sidx[s];
-        }
+        const uint32_t jj = valid ? j : cnt - 1u;   // an item holds at least one point
+        const uint32_t s = __ldg(&a.seg_start[m]) + jj;
+        PointIn pt;
+        pt.u = a.su[s]; pt.v = a.sv[s];
+        pt.px = a.spx[s]; pt.py = a.spy[s]; pt.pz = a.spz[s];
+        pt.nx = a.snx[s]; pt.ny = a.sny[s]; pt.nz = a.snz[s];
+        const uint32_t orig = a.sidx[s];
         const MatInfo mi = a.mats[m];
         const uint4* prog = a.prog + (outer ? mi.outer_start : mi.prog_start);
-        const uint32_t out_slot = outer ? mi.outer_out_slot : mi.out_slot;
+        const uint32_t out_off = (outer ? mi.outer_out_slot : mi.out_slot) * SLOT_BYTES;
         const uint32_t pbase = __ldg(&a.probe_base[m]);
-        int skip_end = -1;          // lane inactive while pc <= skip_end
-        uint32_t hits = 0, cand_cell = 0, cand_h2 = 0, cand_node = 0, cand_start = 0;
-        bool cand_full = false;
-        uint32_t iu = 0, iv = 0, lev = a.level;
-        if (a.keys_inline && valid) {
-            if (a.g1u) lev = a.slev[s];
-            iu = d_texel(pt.u, lev);
-            iv = d_texel(pt.v, lev);
-        }
-        // the next instruction is fetched while the current one executes
         const int len = (int)(outer ? mi.outer_len : mi.prog_len);
-        uint4 nxt = len > 0 ? __ldg(&prog[0]) : make_uint4(0, 0, 0, 0);
-        for (int pc = 0; pc < len; ++pc) {
-            const uint4 ins = nxt;
-            if (pc + 1 < len) nxt = __ldg(&prog[pc + 1]);
-            const uint32_t op = ins.x & 0xFFu;
-            if (op == OP_LOAD_ROOT) {
-                // outer program: a hit, or a value computed this pass by the batched
-                // evaluation or a learned surrogate
-                const uint32_t slot = ins.y & 0xFFFFu, r = ins.y >> 16;
-                if (valid) {
-                    const float4 rec = a.probes[(size_t)pbase + (size_t)r * cnt + j];
+        uint32_t hits = 0;
+        if (outer) {
+            // the point's cacheable-node records, read by the program's loads: fetched into
+            // L1 now, so that the loads find them there instead of waiting on memory
+            const float4* rec0 = a.probes + (size_t)pbase + jj;
+            const uint32_t nr = min(mi.n_roots, 16u);
+            for (uint32_t r = 0; r < nr; ++r)
+                asm volatile("prefetch.global.L1 [%0];" ::"l"(rec0 + (size_t)r * cnt));
+        }
+        // the next instruction is fetched while the current one executes (the pool ends
+        // with a padding instruction)
+        uint4 nxt = __ldg(&prog[0]);
+        if (MODE != EVAL_GENERIC) {
+            for (int pc = 0; pc < len; ++pc) {
+                const uint4 ins = nxt;
+                nxt = __ldg(&prog[pc + 1]);
+                const uint32_t op = ins.x & 0xFFu;
+                if (outer && op == OP_LOAD_ROOT) {
+                    const float4 rec = a.probes[(size_t)pbase + (size_t)(ins.y >> 16) * cnt + jj];
                     const uint32_t state = __float_as_uint(rec.w);
-                    if (state == PROBE_HIT || state == PROBE_COMPUTED) {
-                        V[(slot * 3 + 0) * 32] = rec.x;
-                        V[(slot * 3 + 1) * 32] = rec.y;
-                        V[(slot * 3 + 2) * 32] = rec.z;
-                        hits += state == PROBE_HIT ? 1u : 0u;
-                    } else {
-                        atomicOr(&a.ctl->err, ERR_BOUNDS);   // the batched evaluation missed it
-                    }
+                    slot_store(Vb, ins.y & 0xFFFFu, rec.x, rec.y, rec.z);
+                    hits += state == PROBE_HIT ? 1u : 0u;
+                    // the batched evaluation or the surrogate must have given it a value
+                    if (valid && state != PROBE_HIT && state != PROBE_COMPUTED) atomicOr(&a.ctl->err, ERR_BOUNDS);
+                    continue;
                 }
-                continue;
+                if (!outer && op == OP_ROOT_BEGIN) continue;   // a block marker: nothing to skip
+                exec_node(op, ins, Vb, pt, a.params, s_grad);
             }
-            if (op == OP_ROOT_BEGIN) {
-                const uint32_t slot = ins.y & 0xFFFFu, r = ins.y >> 16;
-                bool need = valid;
-                // the node's probe record: a hit, a miss, or a value computed this pass
-                float4 rec = make_float4(0.f, 0.f, 0.f, 0.f);
-                if (valid && ((a.use_cache && !a.keys_inline) || a.surr_ord))
-                    rec = a.probes[(size_t)pbase + (size_t)r * cnt + j];
-                if (a.surr_ord && a.surr_ord[m] == (int32_t)r) {
-                    // the learned surrogate already wrote this node's value
-                    if (valid) {
-                        V[(slot * 3 + 0) * 32] = rec.x;
-                        V[(slot * 3 + 1) * 32] = rec.y;
-                        V[(slot * 3 + 2) * 32] = rec.z;
-                    }
-                    need = false;
-                } else if (a.keys_inline) {
-                    // empty table: every probe misses at slot 0, so the descriptor is all
-                    // the insert needs (no lookup kernel, no probe record)
-                    if (valid) {
-                        const uint64_t key = ((ins.x >> 8) & FLAG_POSROOT)
-                                                 ? d_key_pos(m, ins.z, (uint32_t)a.pos_level, pt.px, pt.py, pt.pz)
-                                                 : d_key(m, ins.z, lev, iu, iv);
-                        d_address(key, a.n_cells, a.cells_pow2_mask, &cand_cell, &cand_h2);
-                        cand_start = 0;
-                        cand_full = false;
-                        cand_node = ins.z;
-                        n_look++;
-                    }
-                } else if (a.use_cache && valid) {
-                    const uint32_t state = __float_as_uint(rec.w);
-                    if (state == PROBE_HIT || state == PROBE_COMPUTED) {
-                        V[(slot * 3 + 0) * 32] = rec.x;
-                        V[(slot * 3 + 1) * 32] = rec.y;
-                        V[(slot * 3 + 2) * 32] = rec.z;
-                        hits += state == PROBE_HIT ? 1u : 0u;
+            if (valid) {
+                n_nodes += outer ? mi.outer_nodes : mi.full_nodes;
+                n_flops += outer ? mi.outer_flops : mi.full_flops;
+            }
+        } else {
+            int skip_end = -1;          // lane inactive while pc <= skip_end
+            uint32_t cand_cell = 0, cand_h2 = 0, cand_node = 0, cand_start = 0;
+            bool cand_full = false;
+            uint32_t iu = 0, iv = 0, lev = a.level;
+            if (a.keys_inline && valid) {
+                if (a.g1u) lev = a.slev[s];
+                iu = d_texel(pt.u, lev);
+                iv = d_texel(pt.v, lev);
+            }
+            for (int pc = 0; pc < len; ++pc) {
+                const uint4 ins = nxt;
+                nxt = __ldg(&prog[pc + 1]);
+                const uint32_t op = ins.x & 0xFFu;
+                if (op == OP_ROOT_BEGIN) {
+                    const uint32_t off = ins.y & 0xFFFFu, r = ins.y >> 16;
+                    bool need = valid;
+                    // the node's probe record: a hit, a miss, or a value computed this pass
+                    float4 rec = make_float4(0.f, 0.f, 0.f, 0.f);
+                    if (valid && ((a.use_cache && !a.keys_inline) || a.surr_ord))
+                        rec = a.probes[(size_t)pbase + (size_t)r * cnt + j];
+                    if (a.surr_ord && a.surr_ord[m] == (int32_t)r) {
+                        // the learned surrogate already wrote this node's value
+                        if (valid) slot_store(Vb, off, rec.x, rec.y, rec.z);
                         need = false;
-                    } else if (a.split) {
-                        atomicOr(&a.ctl->err, ERR_BOUNDS);   // the batched evaluation missed it
-                        need = false;
-                    } else {
-                        cand_cell = __float_as_uint(rec.x);
-                        cand_h2 = __float_as_uint(rec.y);
-                        cand_start = __float_as_uint(rec.z);
-                        cand_full = state == PROBE_FULL;
-                        cand_node = ins.z;
+                    } else if (a.keys_inline) {
+                        // empty table: every probe misses at slot 0, so the descriptor is all
+                        // the insert needs (no lookup kernel, no probe record)
+                        if (valid) {
+                            const uint64_t key = ((ins.x >> 8) & FLAG_POSROOT)
+                                                     ? d_key_pos(m, ins.z, (uint32_t)a.pos_level, pt.px, pt.py, pt.pz)
+                                                     : d_key(m, ins.z, lev, iu, iv);
+                            d_address(key, a.n_cells, a.cells_pow2_mask, &cand_cell, &cand_h2);
+                            cand_start = 0;
+                            cand_full = false;
+                            cand_node = ins.z;
+                            n_look++;
+                        }
+                    } else if (a.use_cache && valid) {
+                        const uint32_t state = __float_as_uint(rec.w);
+                        if (state == PROBE_HIT || state == PROBE_COMPUTED) {
+                            slot_store(Vb, off, rec.x, rec.y, rec.z);
+                            hits += state == PROBE_HIT ? 1u : 0u;
+                            need = false;
+                        } else if (a.split) {
+                            atomicOr(&a.ctl->err, ERR_BOUNDS);   // the batched evaluation missed it
+                            need = false;
+                        } else {
+                            cand_cell = __float_as_uint(rec.x);
+                            cand_h2 = __float_as_uint(rec.y);
+                            cand_start = __float_as_uint(rec.z);
+                            cand_full = state == PROBE_FULL;
+                            cand_node = ins.z;
+                        }
                     }
+                    if (!need) skip_end = pc + (int)ins.w;
+                    if (__all_sync(FULL_MASK, !need)) {
+                        pc += (int)ins.w;
+                        nxt = __ldg(&prog[pc + 1]);
+                    }
+                    continue;
                 }
-                if (!need) skip_end = pc + (int)ins.w;
-                if (__all_sync(FULL_MASK, !need)) {
-                    pc += (int)ins.w;
-                    if (pc + 1 < len) nxt = __ldg(&prog[pc + 1]);
+                const bool act = valid && pc > skip_end;
+                if (act) {
+                    exec_node(op, ins, Vb, pt, a.params, s_grad);
+                    n_nodes++;
+                    n_flops += ins.x >> 16;
                 }
-                continue;
-            }
-            const bool act = valid && pc > skip_end;
-            if (act) {
-                exec_node(op, ins, V, pt, a.params, s_grad);
-                n_nodes++;
-                n_flops += ins.x >> 16;
-            }
-            if (a.use_cache && ((ins.x >> 8) & FLAG_ROOT)) {
-                const uint32_t out = ins.y & 0xFFFFu;
-                offer(a, act, orig, cand_node, cand_cell, cand_h2, cand_start, cand_full, V[(out * 3) * 32],
-                      V[(out * 3 + 1) * 32], V[(out * 3 + 2) * 32], &n_cand, &n_full);
+                if (a.use_cache && ((ins.x >> 8) & FLAG_ROOT)) {
+                    const uint32_t out = ins.y & 0xFFFFu;
+                    offer(a, act, orig, cand_node, cand_cell, cand_h2, cand_start, cand_full, slot_ch(Vb, out, 0),
+                          slot_ch(Vb, out, 1), slot_ch(Vb, out, 2), &n_cand, &n_full);
+                }
             }
         }
         if (valid) {
-            a.out_rgb[orig] = V[(out_slot * 3) * 32];
-            a.out_rgb[(size_t)a.n + orig] = V[(out_slot * 3 + 1) * 32];
-            a.out_rgb[2 * (size_t)a.n + orig] = V[(out_slot * 3 + 2) * 32];
+            a.out_rgb[orig] = slot_ch(Vb, out_off, 0);
+            a.out_rgb[(size_t)a.n + orig] = slot_ch(Vb, out_off, 1);
+            a.out_rgb[2 * (size_t)a.n + orig] = slot_ch(Vb, out_off, 2);
             if (a.out_hits) a.out_hits[orig] = (uint16_t)min(hits, 65535u);
         }
     }
     warp_add_u64(&a.stats[ST_NODES], n_nodes);
     warp_add_u64(&a.stats[ST_FLOPS], n_flops);
-    warp_add_u64(&a.stats[ST_CANDIDATES], n_cand);
-    warp_add_u64(&a.stats[ST_FULL], n_full);
-    if (a.keys_inline) {
-        warp_add_u64(&a.stats[ST_LOOKUPS], n_look);
-        warp_add_u64(&a.stats[ST_MISSES], n_look);
-        warp_add_u64(&a.stats[ST_SLOTS], n_look);   // one (empty) slot examined per probe
+    if (MODE == EVAL_GENERIC) {
+        warp_add_u64(&a.stats[ST_CANDIDATES], n_cand);
+        warp_add_u64(&a.stats[ST_FULL], n_full);
+        if (a.keys_inline) {
+            warp_add_u64(&a.stats[ST_LOOKUPS], n_look);
+            warp_add_u64(&a.stats[ST_MISSES], n_look);
+            warp_add_u64(&a.stats[ST_SLOTS], n_look);   // one (empty) slot examined per probe
+        }
     }
+}
+
+// One 32-point item of the modes in which every lane runs every instruction (EVAL_OUTER,
+// EVAL_PLAIN), one point per lane (Vb: the lane's base in a [slot][channel][lane] file).
+template <int MODE>
+__device__ __forceinline__ void eval_item1(const BatchArgs& a, uint32_t item, uint32_t m, char* Vb, const float2* grad,
+                                           unsigned long long* n_nodes, unsigned long long* n_flops) {
+    constexpr bool outer = MODE == EVAL_OUTER;
+    const uint32_t lane = lane_id();
+    const uint32_t cnt = __ldg(&a.counts[m]);
+    const uint32_t j = (item - __ldg(&a.item_base[m])) * 32u + lane;
+    const bool valid = j < cnt;
+    const uint32_t jj = valid ? j : cnt - 1u;   // an idle lane shadows the segment's last point
+    const uint32_t s = __ldg(&a.seg_start[m]) + jj;
+    PointIn pt;
+    pt.u = a.su[s]; pt.v = a.sv[s];
+    pt.px = a.spx[s]; pt.py = a.spy[s]; pt.pz = a.spz[s];
+    pt.nx = a.snx[s]; pt.ny = a.sny[s]; pt.nz = a.snz[s];
+    const uint32_t orig = a.sidx[s];
+    const MatInfo mi = a.mats[m];
+    const uint4* prog = a.prog + (outer ? mi.outer_start : mi.prog_start);
+    const uint32_t out_off = (outer ? mi.outer_out_slot : mi.out_slot) * SLOT_BYTES;
+    const uint32_t pbase = __ldg(&a.probe_base[m]);
+    const int len = (int)(outer ? mi.outer_len : mi.prog_len);
+    uint32_t hits = 0;
+    if (outer) {
+        const float4* rec0 = a.probes + (size_t)pbase + jj;
+        const uint32_t nr = min(mi.n_roots, 16u);
+        for (uint32_t r = 0; r < nr; ++r) asm volatile("prefetch.global.L1 [%0];" ::"l"(rec0 + (size_t)r * cnt));
+    }
+    uint4 nxt = __ldg(&prog[0]);   // the pool ends with a padding instruction
+    for (int pc = 0; pc < len; ++pc) {
+        const uint4 ins = nxt;
+        nxt = __ldg(&prog[pc + 1]);
+        const uint32_t op = ins.x & 0xFFu;
+        if (outer && op == OP_LOAD_ROOT) {
+            const float4 rec = a.probes[(size_t)pbase + (size_t)(ins.y >> 16) * cnt + jj];
+            const uint32_t state = __float_as_uint(rec.w);
+            slot_store(Vb, ins.y & 0xFFFFu, rec.x, rec.y, rec.z);
+            hits += state == PROBE_HIT ? 1u : 0u;
+            if (valid && state != PROBE_HIT && state != PROBE_COMPUTED) atomicOr(&a.ctl->err, ERR_BOUNDS);
+            continue;
+        }
+        if (!outer && op == OP_ROOT_BEGIN) continue;
+        exec_node(op, ins, Vb, pt, a.params, grad);
+    }
+    if (valid) {
+        a.out_rgb[orig] = slot_ch(Vb, out_off, 0);
+        a.out_rgb[(size_t)a.n + orig] = slot_ch(Vb, out_off, 1);
+        a.out_rgb[2 * (size_t)a.n + orig] = slot_ch(Vb, out_off, 2);
+        if (a.out_hits) a.out_hits[orig] = (uint16_t)min(hits, 65535u);
+        *n_nodes += outer ? mi.outer_nodes : mi.full_nodes;
+        *n_flops += outer ? mi.outer_flops : mi.full_flops;
+    }
+}
+
+// Two consecutive 32-point items of one material, two points per lane (A from the first
+// item, B from the second; Vb: the lane's base in a [slot][channel][lane][2] file).
+template <int MODE>
+__device__ __forceinline__ void eval_item2(const BatchArgs& a, uint32_t item, uint32_t m, char* Vb, const float2* grad,
+                                           unsigned long long* n_nodes, unsigned long long* n_flops) {
+    constexpr bool outer = MODE == EVAL_OUTER;
+    const uint32_t lane = lane_id();
+    const uint32_t cnt = __ldg(&a.counts[m]);
+    const uint32_t j = (item - __ldg(&a.item_base[m])) * 32u + lane;
+    const bool vA = j < cnt, vB = j + 32u < cnt;
+    const uint32_t jA = vA ? j : cnt - 1u, jB = vB ? j + 32u : cnt - 1u;
+    const uint32_t s0 = __ldg(&a.seg_start[m]);
+    const uint32_t sA = s0 + jA, sB = s0 + jB;
+    PointIn A, B;
+    A.u = a.su[sA]; A.v = a.sv[sA]; A.px = a.spx[sA]; A.py = a.spy[sA]; A.pz = a.spz[sA];
+    A.nx = a.snx[sA]; A.ny = a.sny[sA]; A.nz = a.snz[sA];
+    B.u = a.su[sB]; B.v = a.sv[sB]; B.px = a.spx[sB]; B.py = a.spy[sB]; B.pz = a.spz[sB];
+    B.nx = a.snx[sB]; B.ny = a.sny[sB]; B.nz = a.snz[sB];
+    const MatInfo mi = a.mats[m];
+    const uint4* prog = a.prog + (outer ? mi.outer_start : mi.prog_start);
+    const uint32_t out_off = (outer ? mi.outer_out_slot : mi.out_slot) * SLOT_BYTES;
+    const uint32_t pbase = __ldg(&a.probe_base[m]);
+    const int len = (int)(outer ? mi.outer_len : mi.prog_len);
+    uint32_t hA = 0, hB = 0;
+    if (outer) {
+        const float4* ra = a.probes + (size_t)pbase + jA;
+        const float4* rb = a.probes + (size_t)pbase + jB;
+        const uint32_t nr = min(mi.n_roots, 16u);
+        for (uint32_t r = 0; r < nr; ++r) {
+            asm volatile("prefetch.global.L1 [%0];" ::"l"(ra + (size_t)r * cnt));
+            asm volatile("prefetch.global.L1 [%0];" ::"l"(rb + (size_t)r * cnt));
+        }
+    }
+    uint4 nxt = __ldg(&prog[0]);
+    for (int pc = 0; pc < len; ++pc) {
+        const uint4 ins = nxt;
+        nxt = __ldg(&prog[pc + 1]);
+        const uint32_t op = ins.x & 0xFFu;
+        if (outer && op == OP_LOAD_ROOT) {
+            const size_t rb = (size_t)pbase + (size_t)(ins.y >> 16) * cnt;
+            const float4 ra = a.probes[rb + jA], rc = a.probes[rb + jB];
+            const uint32_t sa = __float_as_uint(ra.w), sc = __float_as_uint(rc.w);
+            slot2_store(Vb, ins.y & 0xFFFFu, f2(ra.x, rc.x), f2(ra.y, rc.y), f2(ra.z, rc.z));
+            hA += sa == PROBE_HIT ? 1u : 0u;
+            hB += sc == PROBE_HIT ? 1u : 0u;
+            if ((vA && sa != PROBE_HIT && sa != PROBE_COMPUTED) || (vB && sc != PROBE_HIT && sc != PROBE_COMPUTED))
+                atomicOr(&a.ctl->err, ERR_BOUNDS);
+            continue;
+        }
+        if (!outer && op == OP_ROOT_BEGIN) continue;
+        exec_node2(op, ins, Vb, A, B, a.params, grad);
+    }
+    const float2 o0 = slot2(Vb, out_off, 0), o1 = slot2(Vb, out_off, 1), o2 = slot2(Vb, out_off, 2);
+    const uint32_t nv = (vA ? 1u : 0u) + (vB ? 1u : 0u);
+    if (vA) {
+        const uint32_t oa = a.sidx[sA];
+        a.out_rgb[oa] = o0.x;
+        a.out_rgb[(size_t)a.n + oa] = o1.x;
+        a.out_rgb[2 * (size_t)a.n + oa] = o2.x;
+        if (a.out_hits) a.out_hits[oa] = (uint16_t)min(hA, 65535u);
+    }
+    if (vB) {
+        const uint32_t ob = a.sidx[sB];
+        a.out_rgb[ob] = o0.y;
+        a.out_rgb[(size_t)a.n + ob] = o1.y;
+        a.out_rgb[2 * (size_t)a.n + ob] = o2.y;
+        if (a.out_hits) a.out_hits[ob] = (uint16_t)min(hB, 65535u);
+    }
+    *n_nodes += (unsigned long long)nv * (outer ? mi.outer_nodes : mi.full_nodes);
+    *n_flops += (unsigned long long)nv * (outer ? mi.outer_flops : mi.full_flops);
+}
+
+// EVAL_OUTER and EVAL_PLAIN with two points per lane: a warp takes pairs of consecutive
+// items; a pair that straddles two materials runs as two single items.  BLOCK: the block
+// claims a tile of EVAL_WARPS consecutive pairs at a time (block-per-material work: the
+// warps of a block run one material's program together and share its instruction and
+// parameter lines in L1); else every warp claims its own pair.
+template <int MODE, bool BLOCK>
+__global__ void __launch_bounds__(EVAL_WARPS * 32, 7) k_eval2(BatchArgs a, uint32_t* item_ctr) {
+    extern __shared__ float s_val[];
+    __shared__ float2 s_grad[8];
+    __shared__ uint32_t s_tile;
+    init_gradients(s_grad);
+    __syncthreads();
+    const uint32_t warp = threadIdx.x >> 5, lane = lane_id();
+    const uint32_t slots = MODE == EVAL_OUTER ? a.max_slots_outer : a.max_slots;
+    char* Vw = reinterpret_cast<char*>(s_val + (size_t)warp * slots * 192u);
+    char* Vb2 = Vw + lane * 8u;
+    char* Vb1 = Vw + lane * 4u;
+    const uint32_t n_items = a.ctl->n_items;
+    unsigned long long n_nodes = 0, n_flops = 0;
+    for (;;) {
+        uint32_t pr = 0;
+        if (BLOCK) {
+            if (threadIdx.x == 0) s_tile = atomicAdd(item_ctr, 1u);
+            __syncthreads();
+            const uint32_t tile = s_tile;
+            __syncthreads();   // read by every warp before the next claim overwrites it
+            if (2u * tile * EVAL_WARPS >= n_items) break;   // uniform over the block
+            pr = tile * EVAL_WARPS + warp;
+        } else {
+            if (lane == 0) pr = atomicAdd(item_ctr, 1u);
+            pr = __shfl_sync(FULL_MASK, pr, 0);
+        }
+        const uint32_t it = 2u * pr;
+        if (it >= n_items) {
+            if (BLOCK) continue;   // this warp's pair is past the end; the block's tile is not
+            break;
+        }
+        const uint32_t m = find_material(a.item_base, a.n_mats, it);
+        if (it + 1u < __ldg(&a.item_base[m + 1])) {
+            eval_item2<MODE>(a, it, m, Vb2, s_grad, &n_nodes, &n_flops);
+        } else {
+            eval_item1<MODE>(a, it, m, Vb1, s_grad, &n_nodes, &n_flops);
+            if (it + 1u < n_items)
+                eval_item1<MODE>(a, it + 1u, find_material(a.item_base, a.n_mats, it + 1u), Vb1, s_grad, &n_nodes,
+                                 &n_flops);
+        }
+    }
+    warp_add_u64(&a.stats[ST_NODES], n_nodes);
+    warp_add_u64(&a.stats[ST_FLOPS], n_flops);
 }
 
 // Scans cell `cell` for h2 (Alg. 1's entry loop read as a lookup): the first slot that
@@ -778,7 +976,7 @@ __global__ void __launch_bounds__(EVAL_WARPS * 32) k_eval_fused(BatchArgs a, uin
     init_gradients(s_grad);
     __syncthreads();
     const uint32_t warp = threadIdx.x >> 5, lane = lane_id();
-    float* V = s_val + (size_t)warp * a.max_slots * 96u + lane;
+    char* Vb = reinterpret_cast<char*>(s_val + (size_t)warp * a.max_slots * 96u + lane);
     const uint32_t n_chunks = GROUPED ? a.ctl->n_items : (a.n + 31u) >> 5;
     const uint32_t ne = a.n_entries;
     unsigned long long n_nodes = 0, n_flops = 0, n_cand = 0, n_full = 0;
@@ -853,11 +1051,8 @@ __global__ void __launch_bounds__(EVAL_WARPS * 32) k_eval_fused(BatchArgs a, uin
                     if (GROUPED && surr == (int32_t)(ins.y >> 16)) {
                         // the learned surrogate wrote this node's value
                         if (mine) {
-                            const uint32_t slot = ins.y & 0xFFFFu;
                             const float4 rec = a.probes[(size_t)__ldg(&a.probe_base[mg]) + (size_t)(ins.y >> 16) * cnt + jj];
-                            V[(slot * 3 + 0) * 32] = rec.x;
-                            V[(slot * 3 + 1) * 32] = rec.y;
-                            V[(slot * 3 + 2) * 32] = rec.z;
+                            slot_store(Vb, ins.y & 0xFFFFu, rec.x, rec.y, rec.z);
                         }
                         need = false;
                     } else if (a.use_cache && mine && a.alg1) {
@@ -870,12 +1065,9 @@ __global__ void __launch_bounds__(EVAL_WARPS * 32) k_eval_fused(BatchArgs a, uin
                         n_look++;
                         n_slots += first >= 0 ? (uint32_t)first + 1u : ne;
                         if (first >= 0 && w != 0ull) {
-                            const uint32_t slot = ins.y & 0xFFFFu;
                             float r, g, b;
                             rgb9e5_decode((uint32_t)(w >> 32), &r, &g, &b);
-                            V[(slot * 3 + 0) * 32] = r;
-                            V[(slot * 3 + 1) * 32] = g;
-                            V[(slot * 3 + 2) * 32] = b;
+                            slot_store(Vb, ins.y & 0xFFFFu, r, g, b);
                             hits++;
                             n_hit++;
                             need = false;
@@ -892,11 +1084,8 @@ __global__ void __launch_bounds__(EVAL_WARPS * 32) k_eval_fused(BatchArgs a, uin
                         n_look++;
                         n_slots += first >= 0 ? (uint32_t)first + 1u : ne;
                         if (hit) {
-                            const uint32_t slot = ins.y & 0xFFFFu;
                             const float* val = cell_val(a, cand_cell, (uint32_t)first);
-                            V[(slot * 3 + 0) * 32] = __ldg(val);
-                            V[(slot * 3 + 1) * 32] = __ldg(val + 1);
-                            V[(slot * 3 + 2) * 32] = __ldg(val + 2);
+                            slot_store(Vb, ins.y & 0xFFFFu, __ldg(val), __ldg(val + 1), __ldg(val + 2));
                             hits++;
                             n_hit++;
                             need = false;
@@ -917,7 +1106,7 @@ __global__ void __launch_bounds__(EVAL_WARPS * 32) k_eval_fused(BatchArgs a, uin
                 }
                 const bool act = mine && pc > skip_end;
                 if (act) {
-                    exec_node(op, ins, V, pt, a.params, s_grad);
+                    exec_node(op, ins, Vb, pt, a.params, s_grad);
                     n_nodes++;
                     n_flops += ins.x >> 16;
                 }
@@ -927,18 +1116,19 @@ __global__ void __launch_bounds__(EVAL_WARPS * 32) k_eval_fused(BatchArgs a, uin
                         n_cand += act ? 1u : 0u;
                         n_full += (act && cand_full) ? 1u : 0u;   // a full cell stays full
                         if (act && !cand_full)
-                            alg1_insert(a, cand_cell, cand_h2, V[(out * 3) * 32], V[(out * 3 + 1) * 32],
-                                        V[(out * 3 + 2) * 32], &n_ins, &n_dup, &n_full, &n_race);
+                            alg1_insert(a, cand_cell, cand_h2, slot_ch(Vb, out, 0), slot_ch(Vb, out, 1),
+                                        slot_ch(Vb, out, 2), &n_ins, &n_dup, &n_full, &n_race);
                     } else {
-                        offer(a, act, i, cand_node, cand_cell, cand_h2, cand_start, cand_full, V[(out * 3) * 32],
-                              V[(out * 3 + 1) * 32], V[(out * 3 + 2) * 32], &n_cand, &n_full);
+                        offer(a, act, i, cand_node, cand_cell, cand_h2, cand_start, cand_full, slot_ch(Vb, out, 0),
+                              slot_ch(Vb, out, 1), slot_ch(Vb, out, 2), &n_cand, &n_full);
                     }
                 }
             }
             if (mine) {
-                a.out_rgb[i] = V[(mi.out_slot * 3) * 32];
-                a.out_rgb[(size_t)a.n + i] = V[(mi.out_slot * 3 + 1) * 32];
-                a.out_rgb[2 * (size_t)a.n + i] = V[(mi.out_slot * 3 + 2) * 32];
+                const uint32_t oo = mi.out_slot * SLOT_BYTES;
+                a.out_rgb[i] = slot_ch(Vb, oo, 0);
+                a.out_rgb[(size_t)a.n + i] = slot_ch(Vb, oo, 1);
+                a.out_rgb[2 * (size_t)a.n + i] = slot_ch(Vb, oo, 2);
                 if (a.out_hits) a.out_hits[i] = (uint16_t)min(hits, 65535u);
             }
         }
@@ -964,29 +1154,35 @@ __global__ void __launch_bounds__(EVAL_WARPS * 32) k_eval_fused(BatchArgs a, uin
     }
 }
 
-// Work items of the batched evaluation: ceil(misses / 32) per cacheable node.
+// Work items of the batched evaluation: ceil(misses / 32) per cacheable node, laid out in
+// ascending nesting level (root_order), with the first item of each level after them.
 __global__ void k_scan_roots(BatchArgs a) {
     __shared__ uint32_t s_tmp[33];
     const uint32_t T = blockDim.x, t = threadIdx.x, N = a.n_roots_total;
     const uint32_t per = (N + T - 1) / T;
     const uint32_t lo = min(t * per, N), hi = min(lo + per, N);
     uint32_t c = 0;
-    for (uint32_t g = lo; g < hi; ++g) c += (a.miss_cnt[g] + 31u) >> 5;
+    for (uint32_t q = lo; q < hi; ++q) c += (a.miss_cnt[a.root_order[q]] + 31u) >> 5;
     uint32_t tot;
     uint32_t b = block_incl_scan(c, s_tmp, &tot) - c;
-    for (uint32_t g = lo; g < hi; ++g) {
-        a.root_item_base[g] = b;
-        b += (a.miss_cnt[g] + 31u) >> 5;
+    for (uint32_t q = lo; q < hi; ++q) {
+        a.root_item_base[q] = b;
+        b += (a.miss_cnt[a.root_order[q]] + 31u) >> 5;
     }
+    __syncthreads();
     if (t == T - 1) {
         a.root_item_base[N] = tot;
         a.ctl->n_root_items = tot;
     }
+    __syncthreads();
+    uint32_t* level_items = a.root_item_base + N + 1;
+    for (uint32_t l = t; l <= MAX_LEVELS; l += T) level_items[l] = a.root_item_base[a.level_start[l]];
 }
 
 // Batched evaluation of the missed cacheable nodes (the "missed sub-graphs" of Sec. 3):
 // a warp runs one cacheable node's standalone program for 32 of its misses, writes the
-// values into their probe records and offers them to the table.
+// values into their probe records and offers them to the table.  Every lane runs every
+// instruction: a lane past the node's last miss shadows that miss and stores nothing.
 template <bool POS>
 __global__ void __launch_bounds__(EVAL_WARPS * 32) k_eval_roots(BatchArgs a, uint32_t level, uint32_t* item_ctr) {
     extern __shared__ float s_val[];
@@ -994,60 +1190,58 @@ __global__ void __launch_bounds__(EVAL_WARPS * 32) k_eval_roots(BatchArgs a, uin
     init_gradients(s_grad);
     __syncthreads();
     const uint32_t warp = threadIdx.x >> 5, lane = lane_id();
-    float* V = s_val + (size_t)warp * a.max_slots_roots * 96u + lane;
-    const uint32_t n_items = a.ctl->n_root_items;
+    char* Vb = reinterpret_cast<char*>(s_val + (size_t)warp * a.max_slots_roots * 96u + lane);
+    // this level's items only: they are contiguous in the level-ordered item layout
+    const uint32_t* level_items = a.root_item_base + a.n_roots_total + 1;
+    const uint32_t first = level_items[level], end = level_items[level + 1];
     unsigned long long n_nodes = 0, n_flops = 0, n_cand = 0, n_full = 0;
     for (;;) {
         uint32_t item = 0;
-        if (lane == 0) item = atomicAdd(item_ctr, 1u);
+        if (lane == 0) item = first + atomicAdd(item_ctr, 1u);
         item = __shfl_sync(FULL_MASK, item, 0);
-        if (item >= n_items) break;
-        const uint32_t g = find_material(a.root_item_base, a.n_roots_total, item);
+        if (item >= end) break;
+        const uint32_t q = find_material(a.root_item_base, a.n_roots_total, item);
+        const uint32_t g = __ldg(&a.root_order[q]);
         const RootInfo ri = a.rinfo[g];
-        if (ri.level != level) continue;
         const uint32_t m = ri.mat, r = ri.ordinal;
         const uint32_t cnt = __ldg(&a.counts[m]);
-        const uint32_t idx = (item - a.root_item_base[g]) * 32u + lane;
-        const bool valid = idx < a.miss_cnt[g];
+        const uint32_t nm = a.miss_cnt[g];   // at least one: the item exists
+        const uint32_t idx = (item - a.root_item_base[q]) * 32u + lane;
+        const bool valid = idx < nm;
         const size_t pbase = __ldg(&a.probe_base[m]);
         const size_t base = pbase + (size_t)r * cnt;
-        const uint32_t j = valid ? a.misslist[base + idx] : 0u;
+        const uint32_t j = a.misslist[base + (valid ? idx : nm - 1u)];
         const uint32_t s = __ldg(&a.seg_start[m]) + j;
         PointIn pt{0, 0, 0, 0, 0, 0, 0, 0};
-        float4 rec = make_float4(0.f, 0.f, 0.f, 0.f);
-        uint32_t orig = 0;
-        if (valid) {
-            pt.u = a.su[s];
-            pt.v = a.sv[s];
-            if (POS) {   // a position-class node reads the position
-                pt.px = a.spx[s];
-                pt.py = a.spy[s];
-                pt.pz = a.spz[s];
-            }
-            orig = a.sidx[s];
-            rec = a.probes[base + j];
+        pt.u = a.su[s];
+        pt.v = a.sv[s];
+        if (POS) {   // a position-class node reads the position
+            pt.px = a.spx[s];
+            pt.py = a.spy[s];
+            pt.pz = a.spz[s];
         }
+        const uint32_t orig = a.sidx[s];
+        const float4 rec = a.probes[base + j];
         const uint4* prog = a.prog + ri.prog_start;
-        uint4 nxt = ri.prog_len > 0 ? __ldg(&prog[0]) : make_uint4(0, 0, 0, 0);
+        uint4 nxt = __ldg(&prog[0]);   // the pool ends with a padding instruction
         for (uint32_t pc = 0; pc < ri.prog_len; ++pc) {
             const uint4 ins = nxt;
-            if (pc + 1 < ri.prog_len) nxt = __ldg(&prog[pc + 1]);
+            nxt = __ldg(&prog[pc + 1]);
             const uint32_t op = ins.x & 0xFFu;
-            if (!valid) continue;
             if (op == OP_LOAD_ROOT) {
-                const uint32_t slot = ins.y & 0xFFFFu, rr = ins.y >> 16;
-                const float4 v = a.probes[pbase + (size_t)rr * cnt + j];
-                V[(slot * 3) * 32] = v.x;
-                V[(slot * 3 + 1) * 32] = v.y;
-                V[(slot * 3 + 2) * 32] = v.z;
+                const float4 v = a.probes[pbase + (size_t)(ins.y >> 16) * cnt + j];
+                slot_store(Vb, ins.y & 0xFFFFu, v.x, v.y, v.z);
                 continue;
             }
-            exec_node(op, ins, V, pt, a.params, s_grad);
-            n_nodes++;
-            n_flops += ins.x >> 16;
+            exec_node(op, ins, Vb, pt, a.params, s_grad);
         }
-        const float v0 = V[(ri.out_slot * 3) * 32], v1 = V[(ri.out_slot * 3 + 1) * 32], v2 = V[(ri.out_slot * 3 + 2) * 32];
-        if (valid) a.probes[base + j] = make_float4(v0, v1, v2, __uint_as_float(PROBE_COMPUTED));
+        const uint32_t out_off = ri.out_slot * SLOT_BYTES;
+        const float v0 = slot_ch(Vb, out_off, 0), v1 = slot_ch(Vb, out_off, 1), v2 = slot_ch(Vb, out_off, 2);
+        if (valid) {
+            a.probes[base + j] = make_float4(v0, v1, v2, __uint_as_float(PROBE_COMPUTED));
+            n_nodes += ri.nodes;
+            n_flops += ri.flops;
+        }
         offer(a, valid, orig, ri.node, __float_as_uint(rec.x), __float_as_uint(rec.y), __float_as_uint(rec.z),
               __float_as_uint(rec.w) == PROBE_FULL, v0, v1, v2, &n_cand, &n_full);
     }
@@ -2391,10 +2585,19 @@ cudaError_t launch_batch(const BatchArgs& a, cudaStream_t s, int num_sms, cudaEv
         nl++;
     } else if (a.n > 0) {
         const bool outer = a.use_cache && a.split && !a.keys_inline;
+        const bool plain = !a.use_cache && !a.surr_ord;
         const size_t smem = eval_smem_bytes(outer ? a.max_slots_outer : a.max_slots),
                      smem_roots = eval_smem_bytes(a.max_slots_roots);
-        if (smem > 48 * 1024 &&
-            (e = cudaFuncSetAttribute(k_eval, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
+        auto keval = outer ? k_eval<EVAL_OUTER> : plain ? k_eval<EVAL_PLAIN> : k_eval<EVAL_GENERIC>;
+        // two points per lane where every lane runs every instruction and the doubled slot
+        // file leaves room for several blocks per SM; the item counter then counts pairs
+        const bool two = (outer || plain) && !a.one_point && 2 * smem <= EVAL2_MAX_SMEM;
+        if (two && a.block_items) keval = outer ? k_eval2<EVAL_OUTER, true> : k_eval2<EVAL_PLAIN, true>;
+        else if (two) keval = outer ? k_eval2<EVAL_OUTER, false> : k_eval2<EVAL_PLAIN, false>;
+        const size_t smem_eval = two ? 2 * smem : smem;
+        if (smem_eval > 48 * 1024 &&
+            (e = cudaFuncSetAttribute(keval, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_eval)) !=
+                cudaSuccess)
             return e;
         if (smem_roots > 48 * 1024 &&
             ((e = cudaFuncSetAttribute(k_eval_roots<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -2417,7 +2620,7 @@ cudaError_t launch_batch(const BatchArgs& a, cudaStream_t s, int num_sms, cudaEv
             }
         }
         if ((e = mark(3)) != cudaSuccess) return e;
-        k_eval<<<num_sms * 16, EVAL_WARPS * 32, smem, s>>>(a, item_ctr);
+        keval<<<num_sms * 16, EVAL_WARPS * 32, smem_eval, s>>>(a, item_ctr);
         nl++;
     } else if ((e = mark(3)) != cudaSuccess) {
         return e;

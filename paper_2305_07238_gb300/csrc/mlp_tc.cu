@@ -1,6 +1,7 @@
-// mlp_tc.cu -- inference of the learned surrogate on the 5th-generation tensor cores:
-// tcgen05.mma (kind::f16, BF16 operands from shared memory, FP32 accumulators in tensor
-// memory), completion tracked by an mbarrier, accumulators read back with tcgen05.ld.
+// mlp_tc.cu -- the learned surrogate on the 5th-generation tensor cores: inference and
+// training with tcgen05.mma (kind::f16, BF16 operands from shared memory, FP32 accumulators
+// in tensor memory), completion tracked by an mbarrier, accumulators read back with
+// tcgen05.ld.
 //
 // A CTA of 128 threads evaluates tiles of 128 points: thread t owns row t of every
 // activation matrix and lane t of tensor memory (warp w reads lanes 32w..32w+31).
@@ -45,12 +46,23 @@ __device__ __forceinline__ uint32_t cm_off(uint32_t r, uint32_t c) {
     return (r >> 3) * 1024u + (c >> 3) * 128u + (r & 7u) * 16u + (c & 7u) * 2u;
 }
 
+// The same for an operand of K columns: 8-row groups K * 16 bytes apart.
+__device__ __forceinline__ uint32_t cm_off_k(uint32_t r, uint32_t c, uint32_t k) {
+    return (r >> 3) * (k * 16u) + (c >> 3) * 128u + (r & 7u) * 16u + (c & 7u) * 2u;
+}
+
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
 // Shared-memory matrix descriptor: start address, leading byte offset 128, stride byte
 // offset 1024, the fixed 0b001 at bits 46-48, no swizzle.
 __device__ __forceinline__ uint64_t sdesc(uint32_t saddr) {
     return (uint64_t)((saddr >> 4) & 0x3FFFu) | ((uint64_t)(128u >> 4) << 16) | ((uint64_t)(1024u >> 4) << 32) |
+           ((uint64_t)1 << 46);
+}
+
+// The same for an operand of K columns (stride byte offset K * 16).
+__device__ __forceinline__ uint64_t sdesc_k(uint32_t saddr, uint32_t k) {
+    return (uint64_t)((saddr >> 4) & 0x3FFFu) | ((uint64_t)(128u >> 4) << 16) | ((uint64_t)((k * 16u) >> 4) << 32) |
            ((uint64_t)1 << 46);
 }
 
@@ -137,14 +149,37 @@ __device__ void tc_load_weights(unsigned char* sm, const float* __restrict__ th)
         bias[i] = i < 64 ? th[P_B1 + i] : (i < 128 ? th[P_B2 + i - 64] : (i < 131 ? th[P_B3 + i - 128] : 0.0f));
 }
 
+// sin and cos of pi k x for k = 1..16: sincospif at the anchor frequencies k = 1, 5, 9, 13,
+// and from each anchor three steps of the angle-addition formulas
+//   sin(a + b) = sin a cos b + cos a sin b,  cos(a + b) = cos a cos b - sin a sin b
+// with b = pi x.  A step adds about an ulp of error, so every feature is within a few ulps of
+// sincospif's, far below the BF16 rounding the features then take.
+__device__ __forceinline__ void tc_sincos16(float x, float (&s)[16], float (&c)[16]) {
+    float s1, c1;
+    sincospif(x, &s1, &c1);
+#pragma unroll
+    for (int a = 0; a < 16; a += 4) {
+        if (a == 0) {
+            s[0] = s1;
+            c[0] = c1;
+        } else {
+            sincospif((float)(a + 1) * x, &s[a], &c[a]);
+        }
+#pragma unroll
+        for (int j = 1; j < 4; ++j) {
+            s[a + j] = fmaf(s[a + j - 1], c1, c[a + j - 1] * s1);
+            c[a + j] = fmaf(c[a + j - 1], c1, -(s[a + j - 1] * s1));
+        }
+    }
+}
+
 // Row t of the feature matrix: [sin pi k u, cos pi k u, sin pi k v, cos pi k v], k = 1..16.
 __device__ __forceinline__ void tc_features(unsigned char* sm, uint32_t t, float u, float v) {
 #pragma unroll
     for (int half = 0; half < 2; ++half) {
         const float x = half ? v : u;
         float s[16], c[16];
-#pragma unroll
-        for (int k = 0; k < 16; ++k) sincospif((float)(k + 1) * x, &s[k], &c[k]);
+        tc_sincos16(x, s, c);
 #pragma unroll
         for (int q = 0; q < 2; ++q) {
             const uint4 ws = make_uint4(pack2(s[8 * q], s[8 * q + 1]), pack2(s[8 * q + 2], s[8 * q + 3]),
@@ -322,7 +357,395 @@ __global__ void __launch_bounds__(TC_ROWS) k_surrogate_tc(BatchArgs a) {
     tc_teardown(tmem);
 }
 
+
+// =======================================================================================
+// Training on the tensor cores.  A CTA of 128 threads takes minibatches of 128 rows of one
+// network; thread t owns row t of every activation and lane t of tensor memory.
+//   forward:   Z1 = G W1, H1 = relu(Z1 + b1); Z2 = H1 W2, H2 = relu(Z2 + b2); Y = H2 W3 + b3
+//   backward:  dY = s (Y - T); dZ2 = (dY W3^T) . [H2 > 0]; dZ1 = (dZ2 W2^T) . [H1 > 0]
+//   gradients: dW1 = G^T dZ1 and dW2 = H1^T dZ2 as one M = 128, N = 128 product
+//              [G^T; H1^T] [dZ1^T; dZ2^T]^T (its two diagonal blocks), dW3 = H2^T dY from
+//              [H1^T; H2^T] dY (its lower half); biases: column sums of dZ1, dZ2, dY
+// Every product takes BF16 operands from shared memory and accumulates in FP32 in tensor
+// memory; the batch-dimension products read transposed copies the epilogues write.  Then
+// FP32 Adam on the master weights.
+// =======================================================================================
+constexpr uint32_t TR_COLS = 256;               // tensor-memory columns of the training kernel
+
+struct St {                                     // byte offsets into dynamic shared memory
+    static constexpr uint32_t a0 = 0;           // [128][64] features, then H2 (A of layers 1, 3)
+    static constexpr uint32_t a1 = 16384;       // [128][64] H1 (A of layer 2)
+    static constexpr uint32_t dz2 = 32768;      // [128][64] dZ2 (A of dH1 = dZ2 W2^T)
+    static constexpr uint32_t dy = 49152;       // [128][16] dY, columns >= 3 zero (A of dH2)
+    static constexpr uint32_t gT = 53248;       // [64][128] G^T   \ gT, h1T: one 128-row operand
+    static constexpr uint32_t h1T = 69632;      // [64][128] H1^T  / h1T, h2T: another
+    static constexpr uint32_t h2T = 86016;      // [64][128] H2^T
+    static constexpr uint32_t dz1T = 102400;    // [64][128] dZ1^T \ one 128-row operand
+    static constexpr uint32_t dz2T = 118784;    // [64][128] dZ2^T /
+    static constexpr uint32_t dyT = 135168;     // [16][128] dY^T, rows >= 3 zero
+    static constexpr uint32_t w1t = 139264;     // [64][64] W1^T (B of layer 1)
+    static constexpr uint32_t w2t = 147456;     // [64][64] W2^T (B of layer 2)
+    static constexpr uint32_t w3t = 155648;     // [16][64] W3^T, rows >= 3 zero (B of layer 3)
+    static constexpr uint32_t w2n = 157696;     // [64][64] W2 (B of dH1)
+    static constexpr uint32_t w3n = 165888;     // [64][16] W3, columns >= 3 zero (B of dH2)
+    static constexpr uint32_t bias = 167936;    // b1[64], b2[64], b3[4] FP32
+    static constexpr uint32_t mbar = 168464;    // 8-byte mbarrier
+    static constexpr uint32_t tmem = 168472;    // tensor-memory base written by tcgen05.alloc
+    // one step's gradient, FP32: rows of W1 and of W2 at a stride of GROW floats (a padded
+    // stride spreads the rows written by the 32 lanes of a warp over the banks), then W3, b1,
+    // b2, b3 in parameter order
+    static constexpr uint32_t GROW = 68;
+    static constexpr uint32_t gw1 = 168960;
+    static constexpr uint32_t gw2 = gw1 + 64 * GROW * 4;
+    static constexpr uint32_t grest = gw2 + 64 * GROW * 4;   // W3 (192), b1 (64), b2 (64), b3 (3)
+    static constexpr uint32_t end = grest + 324 * 4;
+};
+static_assert(St::end <= 227 * 1024, "shared memory of the training kernel");
+
+struct TcTrainArgs {
+    float* theta;            // n_mats x MLP_PARAMS FP32 masters
+    float* adam_m;
+    float* adam_v;
+    float* grad;             // gradient mode: accumulated gradient
+    const float* data;       // per material: n_data rows of (u, v, r, g, b)
+    float* loss;             // per material: summed squared error of the steps run
+    uint32_t* err;           // ERR_TIMEOUT if a wait for the tensor cores ran out (may be null)
+    uint32_t n_data;
+    uint32_t steps;
+    uint64_t sample0;
+    uint32_t step0;
+    uint32_t total_steps;
+    float lr;
+    float grad_scale;        // dL/dy = grad_scale (y - t)
+    int mode;                // 0: Adam steps, 1: accumulate the gradient only
+};
+
+__device__ __forceinline__ void put_bf16(unsigned char* sm, uint32_t off, float x) {
+    *reinterpret_cast<__nv_bfloat16*>(sm + off) = __float2bfloat16_rn(x);
+}
+
+// The network's parameters as BF16 operands (both orientations where the backward pass
+// needs them) and FP32 biases.
+__device__ void tr_load_weights(unsigned char* sm, const float* __restrict__ th) {
+    for (uint32_t i = threadIdx.x; i < 64u * 64u; i += blockDim.x) {
+        const uint32_t in = i >> 6, out = i & 63u;
+        put_bf16(sm, St::w1t + cm_off(out, in), th[P_W1 + i]);
+        const float w2 = th[P_W2 + i];
+        put_bf16(sm, St::w2t + cm_off(out, in), w2);
+        put_bf16(sm, St::w2n + cm_off(in, out), w2);
+    }
+    for (uint32_t i = threadIdx.x; i < 16u * 64u; i += blockDim.x) {
+        const uint32_t out = i >> 6, in = i & 63u;
+        const float w = out < 3 ? th[P_W3 + in * 3 + out] : 0.0f;
+        put_bf16(sm, St::w3t + cm_off_k(out, in, 64), w);
+        put_bf16(sm, St::w3n + cm_off_k(in, out, 16), w);
+    }
+    float* bias = reinterpret_cast<float*>(sm + St::bias);
+    for (uint32_t i = threadIdx.x; i < 132u; i += blockDim.x)
+        bias[i] = i < 64 ? th[P_B1 + i] : (i < 128 ? th[P_B2 + i - 64] : (i < 131 ? th[P_B3 + i - 128] : 0.0f));
+}
+
+// Makes the operand rows written by every thread visible to the tensor cores, issues
+// `k16` K = 16 steps of one product from thread 0 and waits for it.  False if the wait
+// ran out (every thread gets the same answer).
+__device__ __forceinline__ bool tr_mma(uint32_t mbar, uint32_t* phase, uint32_t d, uint32_t a, uint32_t ka,
+                                       uint32_t b, uint32_t kb, uint32_t id, uint32_t k16) {
+    fence_async_smem();
+    fence_before();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        fence_after();
+        for (uint32_t s = 0; s < k16; ++s) mma_bf16(d, sdesc_k(a + 256u * s, ka), sdesc_k(b + 256u * s, kb), id, s > 0);
+        mma_commit(mbar);
+    }
+    const bool done = mbar_wait(mbar, *phase);
+    *phase ^= 1u;
+    const bool ok = !__syncthreads_or(!done);
+    fence_after();
+    return ok;
+}
+
+// relu(acc + bias) of 64 accumulator columns: row t of a [128][64] operand, column t of a
+// [64][128] transposed one, and the relu'(h) > 0 mask of the BF16 values.
+__device__ __forceinline__ uint64_t tr_hidden(unsigned char* sm, uint32_t dst, uint32_t dstT, uint32_t taddr,
+                                              const float* bias, uint32_t t) {
+    uint64_t mask = 0;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        float v[16];
+        tmem_ld16(taddr + 16u * q, v);
+        uint32_t p[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            p[k] = pack2(fmaxf(v[2 * k] + bias[16 * q + 2 * k], 0.0f), fmaxf(v[2 * k + 1] + bias[16 * q + 2 * k + 1], 0.0f));
+            const uint32_t c = 16 * q + 2 * k;
+            *reinterpret_cast<uint16_t*>(sm + dstT + cm_off_k(c, t, 128)) = (uint16_t)(p[k] & 0xFFFFu);
+            *reinterpret_cast<uint16_t*>(sm + dstT + cm_off_k(c + 1, t, 128)) = (uint16_t)(p[k] >> 16);
+            mask |= (uint64_t)((p[k] & 0x7FFFu) != 0 && !(p[k] & 0x8000u)) << c;
+            mask |= (uint64_t)(((p[k] >> 16) & 0x7FFFu) != 0 && !(p[k] & 0x80000000u)) << (c + 1);
+        }
+        *reinterpret_cast<uint4*>(sm + dst + cm_off(t, 16 * q)) = make_uint4(p[0], p[1], p[2], p[3]);
+        *reinterpret_cast<uint4*>(sm + dst + cm_off(t, 16 * q + 8)) = make_uint4(p[4], p[5], p[6], p[7]);
+    }
+    return mask;
+}
+
+// acc . mask of 64 accumulator columns as BF16: row t of a [128][64] operand (dst != ~0u)
+// and column t of a [64][128] transposed one.
+__device__ __forceinline__ void tr_masked(unsigned char* sm, uint32_t dst, uint32_t dstT, uint32_t taddr, uint64_t mask,
+                                          uint32_t t) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        float v[16];
+        tmem_ld16(taddr + 16u * q, v);
+        uint32_t p[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            const uint32_t c = 16 * q + 2 * k;
+            p[k] = pack2(((mask >> c) & 1u) ? v[2 * k] : 0.0f, ((mask >> (c + 1)) & 1u) ? v[2 * k + 1] : 0.0f);
+            *reinterpret_cast<uint16_t*>(sm + dstT + cm_off_k(c, t, 128)) = (uint16_t)(p[k] & 0xFFFFu);
+            *reinterpret_cast<uint16_t*>(sm + dstT + cm_off_k(c + 1, t, 128)) = (uint16_t)(p[k] >> 16);
+        }
+        if (dst != ~0u) {
+            *reinterpret_cast<uint4*>(sm + dst + cm_off(t, 16 * q)) = make_uint4(p[0], p[1], p[2], p[3]);
+            *reinterpret_cast<uint4*>(sm + dst + cm_off(t, 16 * q + 8)) = make_uint4(p[4], p[5], p[6], p[7]);
+        }
+    }
+}
+
+// Sum of row r of a [rows][128] BF16 operand (a bias gradient: a column sum over the batch).
+__device__ __forceinline__ float tr_row_sum(const unsigned char* sm, uint32_t base, uint32_t r) {
+    float s = 0.0f;
+#pragma unroll 4
+    for (uint32_t c = 0; c < 128; c += 8) {
+        const uint4 w = *reinterpret_cast<const uint4*>(sm + base + cm_off_k(r, c, 128));
+        const uint32_t x[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+        for (int k = 0; k < 4; ++k) s += __uint_as_float(x[k] << 16) + __uint_as_float(x[k] & 0xFFFF0000u);
+    }
+    return s;
+}
+
+// One CTA per (split, material) runs `steps` minibatch steps of 128 rows.
+__global__ void __launch_bounds__(TC_ROWS) k_mlp_train_tc(TcTrainArgs A) {
+    extern __shared__ __align__(1024) unsigned char sm[];
+    const uint32_t t = threadIdx.x;
+    const uint32_t base = smem_u32(sm), mbar = base + St::mbar;
+    const uint32_t mat = blockIdx.y;
+    const size_t pbase = (size_t)mat * MLP_PARAMS;
+    const float* data = A.data + (size_t)mat * A.n_data * 5;
+    if (t == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mbar));
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (t < 32) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(base + St::tmem),
+                     "r"(TR_COLS));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    // the zero columns of dY and zero rows of dY^T stay zero: only outputs 0..2 are written
+    for (uint32_t i = t; i < 128u * 16u; i += TC_ROWS) {
+        *reinterpret_cast<uint16_t*>(sm + St::dy + cm_off_k(i >> 4, i & 15u, 16)) = 0;
+        *reinterpret_cast<uint16_t*>(sm + St::dyT + cm_off_k(i & 15u, i >> 4, 128)) = 0;
+    }
+    fence_before();
+    __syncthreads();
+    fence_after();
+    const uint32_t tmem = *reinterpret_cast<volatile uint32_t*>(sm + St::tmem);
+    const uint32_t lane_addr = tmem + (((t >> 5) * 32u) << 16);
+    const float* bias = reinterpret_cast<const float*>(sm + St::bias);
+    const uint32_t log2n = 31 - __clz(A.n_data);
+    uint32_t phase = 0;
+    float loss = 0.0f;
+    bool ok = true;
+    tr_load_weights(sm, A.theta + pbase);   // later steps update the operands in place
+    __syncthreads();
+    for (uint32_t s = 0; s < A.steps && ok; ++s) {
+        const uint32_t step = s * gridDim.x + blockIdx.x;
+        // ---- row t of the minibatch: in order (gradient mode) or a fixed per-epoch shuffle
+        const uint64_t k = A.sample0 + (uint64_t)step * TC_ROWS + t;
+        uint32_t row;
+        if (A.mode == 1) {
+            row = (uint32_t)k;
+        } else {
+            const uint32_t epoch = (uint32_t)(k >> log2n);
+            row = (uint32_t)(k * 2654435761ull + (uint64_t)epoch * 0x9E3779B9ull) & (A.n_data - 1);
+        }
+        const float* d = data + (size_t)row * 5;
+        const float u = d[0], v = d[1], tg0 = d[2], tg1 = d[3], tg2 = d[4];
+        // ---- features: row t of G, column t of G^T
+        tc_features(sm, t, u, v);
+        for (uint32_t c = 0; c < 64; c += 8) {
+            const uint4 w = *reinterpret_cast<const uint4*>(sm + St::a0 + cm_off(t, c));
+            const uint32_t x[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                *reinterpret_cast<uint16_t*>(sm + St::gT + cm_off_k(c + 2 * q, t, 128)) = (uint16_t)(x[q] & 0xFFFFu);
+                *reinterpret_cast<uint16_t*>(sm + St::gT + cm_off_k(c + 2 * q + 1, t, 128)) = (uint16_t)(x[q] >> 16);
+            }
+        }
+        // ---- forward
+        ok = tr_mma(mbar, &phase, tmem + 0u, base + St::a0, 64, base + St::w1t, 64, idesc(128, 64), 4);
+        if (!ok) break;
+        const uint64_t mask1 = tr_hidden(sm, St::a1, St::h1T, lane_addr + 0u, bias, t);
+        fence_before();
+        ok = tr_mma(mbar, &phase, tmem + 64u, base + St::a1, 64, base + St::w2t, 64, idesc(128, 64), 4);
+        if (!ok) break;
+        const uint64_t mask2 = tr_hidden(sm, St::a0, St::h2T, lane_addr + 64u, bias + 64, t);
+        fence_before();
+        ok = tr_mma(mbar, &phase, tmem + 128u, base + St::a0, 64, base + St::w3t, 64, idesc(128, 16), 4);
+        if (!ok) break;
+        // ---- dL/dy and the loss
+        {
+            float o[4];
+            tmem_ld4(lane_addr + 128u, o);
+            const float e[3] = {o[0] + bias[128] - tg0, o[1] + bias[129] - tg1, o[2] + bias[130] - tg2};
+#pragma unroll
+            for (int q = 0; q < 3; ++q) {
+                loss += e[q] * e[q];
+                const float g = A.grad_scale * e[q];
+                put_bf16(sm, St::dy + cm_off_k(t, q, 16), g);
+                put_bf16(sm, St::dyT + cm_off_k(q, t, 128), g);
+            }
+        }
+        fence_before();
+        // ---- dH2 = dY W3^T, masked
+        ok = tr_mma(mbar, &phase, tmem + 0u, base + St::dy, 16, base + St::w3n, 16, idesc(128, 64), 1);
+        if (!ok) break;
+        tr_masked(sm, St::dz2, St::dz2T, lane_addr + 0u, mask2, t);
+        fence_before();
+        // ---- dH1 = dZ2 W2^T, masked
+        ok = tr_mma(mbar, &phase, tmem + 64u, base + St::dz2, 64, base + St::w2n, 64, idesc(128, 64), 4);
+        if (!ok) break;
+        tr_masked(sm, ~0u, St::dz1T, lane_addr + 64u, mask1, t);
+        fence_before();
+        // ---- weight gradients: [G^T; H1^T] x [dZ1^T; dZ2^T]^T and [H1^T; H2^T] x dY
+        fence_async_smem();
+        fence_before();
+        __syncthreads();
+        if (t == 0) {
+            fence_after();
+            for (uint32_t q = 0; q < 8; ++q)
+                mma_bf16(tmem + 0u, sdesc_k(base + St::gT + 256u * q, 128), sdesc_k(base + St::dz1T + 256u * q, 128),
+                         idesc(128, 128), q > 0);
+            for (uint32_t q = 0; q < 8; ++q)
+                mma_bf16(tmem + 128u, sdesc_k(base + St::h1T + 256u * q, 128), sdesc_k(base + St::dyT + 256u * q, 128),
+                         idesc(128, 16), q > 0);
+            mma_commit(mbar);
+        }
+        // bias gradients while the tensor cores run: column sums of dZ1, dZ2 and dY
+        const float gb = t < 64 ? tr_row_sum(sm, St::dz1T, t) : tr_row_sum(sm, St::dz2T, t - 64);
+        const float gb3 = t < 3 ? tr_row_sum(sm, St::dyT, t) : 0.0f;
+        const bool done = mbar_wait(mbar, phase);
+        phase ^= 1u;
+        if (__syncthreads_or(!done)) {
+            ok = false;
+            break;
+        }
+        fence_after();
+        // ---- the step's gradient into shared memory: thread t < 64 holds row t of dW1 (tensor-
+        // memory lane t, columns 0..63), thread t >= 64 row t - 64 of dW2 (columns 64..127)
+        // and of dW3 (columns 128..130)
+        float* gw1 = reinterpret_cast<float*>(sm + St::gw1);
+        float* gw2 = reinterpret_cast<float*>(sm + St::gw2);
+        float* grest = reinterpret_cast<float*>(sm + St::grest);
+        {
+            float* row = t < 64 ? gw1 + t * St::GROW : gw2 + (t - 64) * St::GROW;
+            const uint32_t col0 = t < 64 ? 0u : 64u;
+#pragma unroll
+            for (uint32_t q = 0; q < 4; ++q) {
+                float g[16];
+                tmem_ld16(lane_addr + col0 + 16u * q, g);
+#pragma unroll
+                for (int k = 0; k < 16; k += 4)
+                    *reinterpret_cast<float4*>(row + 16 * q + k) = make_float4(g[k], g[k + 1], g[k + 2], g[k + 3]);
+            }
+            if (t >= 64) {
+                float g3[4];
+                tmem_ld4(lane_addr + 128u, g3);
+                for (uint32_t o = 0; o < 3; ++o) grest[(t - 64) * 3 + o] = g3[o];
+            }
+            grest[192 + t] = gb;                  // b1 (t < 64), then b2
+            if (t < 3) grest[320 + t] = gb3;
+        }
+        fence_before();
+        __syncthreads();
+        // ---- Adam (or gradient accumulation) over the parameters in order, coalesced; the
+        // updated weights go straight into the BF16 operands of the next step
+        const uint32_t adam_t = A.step0 + step + 1;
+        const float frac = A.total_steps > 1 ? (float)(A.step0 + step) / (float)(A.total_steps - 1) : 0.0f;
+        const float lr_t = A.lr * (0.05f + 0.95f * 0.5f * (1.0f + cospif(fminf(frac, 1.0f))));
+        const float bc1 = 1.0f - powf(0.9f, (float)adam_t), bc2 = 1.0f - powf(0.999f, (float)adam_t);
+        float* bias_w = reinterpret_cast<float*>(sm + St::bias);
+#pragma unroll 4
+        for (uint32_t i = t; i < MLP_PARAMS; i += TC_ROWS) {
+            float g;
+            if (i < (uint32_t)P_B1) g = gw1[(i >> 6) * St::GROW + (i & 63u)];
+            else if (i < (uint32_t)P_W2) g = grest[192 + (i - P_B1)];
+            else if (i < (uint32_t)P_B2) g = gw2[((i - P_W2) >> 6) * St::GROW + ((i - P_W2) & 63u)];
+            else if (i < (uint32_t)P_W3) g = grest[256 + (i - P_B2)];
+            else if (i < (uint32_t)P_B3) g = grest[i - P_W3];
+            else g = grest[320 + (i - P_B3)];
+            const size_t k = pbase + i;
+            if (A.mode == 1) {
+                atomicAdd(&A.grad[k], g);
+                continue;
+            }
+            const float m1 = 0.9f * A.adam_m[k] + 0.1f * g;
+            const float m2 = 0.999f * A.adam_v[k] + 0.001f * g * g;
+            A.adam_m[k] = m1;
+            A.adam_v[k] = m2;
+            const float w = A.theta[k] - lr_t * (m1 / bc1) / (sqrtf(m2 / bc2) + 1e-8f);
+            A.theta[k] = w;
+            if (i < (uint32_t)P_B1) {
+                put_bf16(sm, St::w1t + cm_off(i & 63u, i >> 6), w);
+            } else if (i < (uint32_t)P_W2) {
+                bias_w[i - P_B1] = w;
+            } else if (i < (uint32_t)P_B2) {
+                const uint32_t j = i - P_W2, in = j >> 6, out = j & 63u;
+                put_bf16(sm, St::w2t + cm_off(out, in), w);
+                put_bf16(sm, St::w2n + cm_off(in, out), w);
+            } else if (i < (uint32_t)P_W3) {
+                bias_w[64 + (i - P_B2)] = w;
+            } else if (i < (uint32_t)P_B3) {
+                const uint32_t j = i - P_W3, in = j / 3u, out = j % 3u;
+                put_bf16(sm, St::w3t + cm_off_k(out, in, 64), w);
+                put_bf16(sm, St::w3n + cm_off_k(in, out, 16), w);
+            } else {
+                bias_w[128 + (i - P_B3)] = w;
+            }
+        }
+        fence_before();
+        __syncthreads();   // the next step reads the updated operands
+    }
+    if (!ok) {
+        if (t == 0) {
+            if (A.err) atomicOr(A.err, ERR_TIMEOUT);
+            atomicExch(&A.loss[mat], __int_as_float(0x7FC00000));
+        }
+    } else {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) loss += __shfl_xor_sync(0xFFFFFFFFu, loss, o);
+        if ((t & 31u) == 0) atomicAdd(&A.loss[mat], loss);
+    }
+    fence_before();
+    __syncthreads();
+    if (t < 32) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TR_COLS));
+}
+
 }  // namespace
+
+cudaError_t launch_mlp_train(float* theta, float* adam_m, float* adam_v, float* grad, const float* data, float* loss,
+                             uint32_t* err, uint32_t n_mats, uint32_t n_data, uint32_t steps, uint64_t sample0,
+                             uint32_t step0, uint32_t total_steps, float lr, float grad_scale, int mode, uint32_t splits,
+                             cudaStream_t s) {
+    TcTrainArgs A{theta, adam_m, adam_v, grad, data, loss, err, n_data, steps, sample0, step0, total_steps, lr,
+                  grad_scale, mode};
+    cudaError_t e = cudaFuncSetAttribute(k_mlp_train_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)St::end);
+    if (e != cudaSuccess) return e;
+    k_mlp_train_tc<<<dim3(splits, n_mats), TC_ROWS, St::end, s>>>(A);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_surrogate(const BatchArgs& a, int num_sms, cudaStream_t s) {
     cudaError_t e = cudaFuncSetAttribute(k_surrogate_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Sm::end);

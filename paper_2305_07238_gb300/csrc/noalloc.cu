@@ -157,10 +157,13 @@ extern "C" pmc_status pmc_eval_batch_noalloc(pmc_cache* c, const pmc_points* pts
     }
     a.rinfo = c->d_rinfo; a.n_roots_total = (uint32_t)c->root_info.size(); a.max_level = c->max_level;
     a.miss_cnt = c->d_miss_cnt; a.root_item_base = c->d_root_items;
+    a.root_order = c->d_root_order; a.level_start = c->d_root_order + c->root_info.size();
     a.misslist = reinterpret_cast<uint32_t*>(base + OFF_MISS);
     a.unsorted = c->unsorted;
     a.probe_inline = c->probe_inline;
     a.lookup_rb = c->lookup_rb;
+    a.block_items = c->block_items;
+    a.one_point = c->one_point;
     if (c->use_cache && (c->desc.flags & PMC_REPLACE_VISIBILITY)) {
         a.slot_cls = c->d_cls;
         a.vis = pts->vis;

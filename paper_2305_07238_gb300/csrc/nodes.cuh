@@ -118,73 +118,125 @@ __device__ __forceinline__ void init_gradients(float2* g) {
     }
 }
 
+// Pairs of independent FP32 operations issue as one instruction (Blackwell's packed FP32);
+// each lane of a pair rounds exactly as the scalar operation would.
+__device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+
+// quintic fade 6t^5 - 15t^4 + 10t^3 of both coordinates at once
+__device__ __forceinline__ float2 d_fade2(float2 t) {
+    const float2 t3 = mul2(mul2(t, t), t);
+    return mul2(t3, fma2(t, fma2(t, f2(6.0f, 6.0f), f2(-15.0f, -15.0f)), f2(10.0f, 10.0f)));
+}
+
 __device__ __forceinline__ float d_fade(float t) {
     return t * t * t * fmaf(t, fmaf(t, 6.0f, -15.0f), 10.0f);
 }
 
 __device__ __forceinline__ float d_perlin(float x, float y, uint32_t seed, const float2* grad) {
-    float fx0 = floorf(x), fy0 = floorf(y);
-    int ix = (int)fx0, iy = (int)fy0;
-    float fx = x - fx0, fy = y - fy0;
-    float fx1 = fx - 1.0f, fy1 = fy - 1.0f;
-    const float2 g00 = grad[d_lattice(ix, iy, seed) & 7u];
-    const float2 g10 = grad[d_lattice(ix + 1, iy, seed) & 7u];
-    const float2 g01 = grad[d_lattice(ix, iy + 1, seed) & 7u];
-    const float2 g11 = grad[d_lattice(ix + 1, iy + 1, seed) & 7u];
-    float d00 = fmaf(g00.x, fx, g00.y * fy);
-    float d10 = fmaf(g10.x, fx1, g10.y * fy);
-    float d01 = fmaf(g01.x, fx, g01.y * fy1);
-    float d11 = fmaf(g11.x, fx1, g11.y * fy1);
-    float su = d_fade(fx), sv = d_fade(fy);
-    float a = fmaf(su, d10 - d00, d00);
-    float b = fmaf(su, d11 - d01, d01);
-    return fmaf(sv, b - a, a);
+    const float2 p = f2(x, y);
+    const float2 f0 = f2(floorf(x), floorf(y));
+    const int ix = (int)f0.x, iy = (int)f0.y;
+    const float2 fr = fma2(f0, f2(-1.0f, -1.0f), p);          // (fx, fy) = p - floor(p)
+    const float2 fr1 = add2(fr, f2(-1.0f, -1.0f));            // (fx - 1, fy - 1)
+    // lattice hashes of the four corners: the prime products of x + 1 and y + 1 are those
+    // of x and y plus the prime
+    const uint32_t ax = (uint32_t)ix * 73856093u, by = (uint32_t)iy * 19349663u, sz = seed * 83492791u;
+    const uint32_t ax1 = ax + 73856093u, by1 = by + 19349663u;
+    const float2 g00 = grad[d_fmix32(ax ^ by ^ sz) & 7u];
+    const float2 g10 = grad[d_fmix32(ax1 ^ by ^ sz) & 7u];
+    const float2 g01 = grad[d_fmix32(ax ^ by1 ^ sz) & 7u];
+    const float2 g11 = grad[d_fmix32(ax1 ^ by1 ^ sz) & 7u];
+    // corner dot products, paired as (d00, d01) and (d10, d11)
+    const float2 dA = fma2(f2(g00.x, g01.x), f2(fr.x, fr.x), mul2(f2(g00.y, g01.y), f2(fr.y, fr1.y)));
+    const float2 dB = fma2(f2(g10.x, g11.x), f2(fr1.x, fr1.x), mul2(f2(g10.y, g11.y), f2(fr.y, fr1.y)));
+    const float2 s = d_fade2(fr);
+    // (a, b) = dA + s.x (dB - dA); result = a + s.y (b - a)
+    const float2 ab = fma2(f2(s.x, s.x), fma2(dA, f2(-1.0f, -1.0f), dB), dA);
+    return fmaf(s.y, ab.y - ab.x, ab.x);
 }
 
 // clamp to [0, 1] (NaN to 0) as a saturating modifier of the producing instruction
 __device__ __forceinline__ float d_clamp01(float x) { return __saturatef(x); }
 
-__device__ __forceinline__ float d_fbm(float x, float y, const float* p, const float2* grad) {
-    float scale = p[0], lac = p[1], gain = p[2], inv_norm = p[3];
-    int oct = __float_as_int(p[4]);
-    uint32_t seed = (uint32_t)__float_as_int(p[5]);
+// q = {scale, lacunarity, gain, 1 / sum of gains}, t = {octaves, seed} (integers in floats)
+__device__ __forceinline__ float d_fbm(float x, float y, const float4 q, const float4 t, const float2* grad) {
+    const float scale = q.x, lac = q.y, gain = q.z, inv_norm = q.w;
+    const int oct = __float_as_int(t.x);
+    const uint32_t seed = (uint32_t)__float_as_int(t.y);
     float sum = 0.0f, amp = 1.0f, freq = scale;
     for (int k = 0; k < oct; ++k) {
-        sum = fmaf(amp, d_perlin(x * freq, y * freq, seed + (uint32_t)k, grad), sum);
-        amp *= gain;
-        freq *= lac;
+        const float2 q = mul2(f2(x, y), f2(freq, freq));
+        sum = fmaf(amp, d_perlin(q.x, q.y, seed + (uint32_t)k, grad), sum);
+        const float2 af = mul2(f2(amp, freq), f2(gain, lac));
+        amp = af.x;
+        freq = af.y;
     }
     return d_clamp01(fmaf(sum, inv_norm, 0.5f));
 }
 
-__device__ __forceinline__ float d_voronoi(float x, float y, const float* p) {
-    float sx = x * p[0], sy = y * p[0];
-    uint32_t seed = (uint32_t)__float_as_int(p[1]);
-    float fx0 = floorf(sx), fy0 = floorf(sy);
-    int ix = (int)fx0, iy = (int)fy0;
-    float fx = sx - fx0, fy = sy - fy0;
+// The two 16-bit halves of a hash h as m = 1 + h16 2^-16, exactly: an FP32 number whose
+// fraction holds h16 in its top 16 bits.  One shift and one masked or per half, no
+// integer-to-float conversion.
+__device__ __forceinline__ float2 d_halves(uint32_t h) {
+    return f2(__uint_as_float(((h << 7) & 0x7FFF80u) | 0x3F800000u),
+              __uint_as_float(((h >> 9) & 0x7FFF80u) | 0x3F800000u));
+}
+
+__device__ __forceinline__ float d_voronoi(float x, float y, float scale, uint32_t seed) {
+    const float2 sc = mul2(f2(x, y), f2(scale, scale));
+    const float2 f0 = f2(floorf(sc.x), floorf(sc.y));
+    const int ix = (int)f0.x, iy = (int)f0.y;
+    const float2 fr = fma2(f0, f2(-1.0f, -1.0f), sc);
+    const uint32_t sz = seed * 83492791u;
+    const uint32_t ax = (uint32_t)ix * 73856093u;
+    const uint32_t axs[3] = {ax - 73856093u, ax, ax + 73856093u};
     float best = 3.0e38f;
 #pragma unroll
     for (int b = -1; b <= 1; ++b) {
+        const uint32_t by = ((uint32_t)iy * 19349663u + (uint32_t)b * 19349663u) ^ sz;
 #pragma unroll
         for (int a = -1; a <= 1; ++a) {
-            uint32_t h = d_lattice(ix + a, iy + b, seed);
-            float ox = fmaf((float)(h & 0xFFFFu), 0.5f / 65536.0f, (float)a + 0.25f);
-            float oy = fmaf((float)(h >> 16), 0.5f / 65536.0f, (float)b + 0.25f);
-            float dx = ox - fx, dy = oy - fy;
-            best = fminf(best, fmaf(dx, dx, dy * dy));
+            // feature point at cell + 0.25 + 0.5 h16 2^-16 per axis: with m = 1 + h16 2^-16,
+            // fmaf(m, 0.5, a - 0.25) is that same real number under one rounding, the value
+            // fmaf(h16, 0.5 / 65536, a + 0.25) gives
+            const float2 m = d_halves(d_fmix32(axs[a + 1] ^ by));
+            const float2 o = fma2(m, f2(0.5f, 0.5f), f2((float)a - 0.25f, (float)b - 0.25f));
+            const float2 d = fma2(fr, f2(-1.0f, -1.0f), o);
+            best = fminf(best, fmaf(d.x, d.x, d.y * d.y));
         }
     }
     return d_clamp01(sqrtf(best));
 }
 
+// Parity of an integer-valued FP32 number f as 0 or 1: f - 2 floor(f / 2), exact for every
+// finite f (integers beyond 2^24 are even, and the formula gives 0 there).
+__device__ __forceinline__ float d_parity(float f) { return fmaf(-2.0f, floorf(f * 0.5f), f); }
+
 struct PointIn {
     float u, v, px, py, pz, nx, ny, nz;
 };
 
-// One node instruction for one lane.  V points at the lane's slot file, laid out
-// [slot][channel][lane] so that the 32 lanes of a warp touch 32 consecutive words.
-__device__ __forceinline__ void exec_node(uint32_t op, const uint4& ins, float* V, const PointIn& pt,
+// A node's value slots, laid out [slot][channel][lane] per warp: the 32 lanes of a warp
+// touch 32 consecutive words.  Programs name slots by byte offsets from the lane's base
+// (slot x SLOT_BYTES), so an operand is one add away from its address.
+constexpr uint32_t CH_BYTES = 32u * 4u;
+
+__device__ __forceinline__ float slot_ch(const char* Vb, uint32_t off, int ch) {
+    return *reinterpret_cast<const float*>(Vb + off + ch * CH_BYTES);
+}
+__device__ __forceinline__ void slot_store(char* Vb, uint32_t off, float r0, float r1, float r2) {
+    float* o = reinterpret_cast<float*>(Vb + off);
+    o[0] = r0;
+    o[32] = r1;
+    o[64] = r2;
+}
+
+// One node instruction for one lane.  Vb is the lane's base in the slot file; the
+// instruction's y = out | in0 << 16, z = in1 | in2 << 16 are byte offsets from it.
+__device__ __forceinline__ void exec_node(uint32_t op, const uint4& ins, char* Vb, const PointIn& pt,
                                           const float* __restrict__ params, const float2* grad) {
     const uint32_t out = ins.y & 0xFFFFu;
     const uint32_t i0 = ins.y >> 16, i1 = ins.z & 0xFFFFu, i2 = ins.z >> 16;
@@ -204,7 +256,7 @@ __device__ __forceinline__ void exec_node(uint32_t op, const uint4& ins, float* 
     case PMC_OP_UV_AFFINE: {
         const float4 q = __ldg(p4);
         const float4 t = __ldg(p4 + 1);
-        float x = V[(i0 * 3) * 32], y = V[(i0 * 3 + 1) * 32];
+        const float x = slot_ch(Vb, i0, 0), y = slot_ch(Vb, i0, 1);
         r0 = fmaf(q.x, x, fmaf(q.y, y, t.x));
         r1 = fmaf(q.z, x, fmaf(q.w, y, t.y));
         break;
@@ -212,85 +264,222 @@ __device__ __forceinline__ void exec_node(uint32_t op, const uint4& ins, float* 
     case PMC_OP_FBM: {
         const float4 q = __ldg(p4);
         const float4 t = __ldg(p4 + 1);
-        const float pp[6] = {q.x, q.y, q.z, q.w, t.x, t.y};
-        r0 = r1 = r2 = d_fbm(V[(i0 * 3) * 32], V[(i0 * 3 + 1) * 32], pp, grad);
+        r0 = r1 = r2 = d_fbm(slot_ch(Vb, i0, 0), slot_ch(Vb, i0, 1), q, t, grad);
         break;
     }
     case PMC_OP_VORONOI: {
         const float4 q = __ldg(p4);
-        const float pp[2] = {q.x, q.y};
-        r0 = r1 = r2 = d_voronoi(V[(i0 * 3) * 32], V[(i0 * 3 + 1) * 32], pp);
+        r0 = r1 = r2 = d_voronoi(slot_ch(Vb, i0, 0), slot_ch(Vb, i0, 1), q.x, (uint32_t)__float_as_int(q.y));
         break;
     }
     case PMC_OP_CHECKER: {
+        // colour B iff floor(x s) + floor(y s) is odd, i.e. the two parities differ
         const float4 q = __ldg(p4);
         const float4 t = __ldg(p4 + 1);
-        const float sc = q.x;
-        long long k = (long long)floorf(V[(i0 * 3) * 32] * sc) + (long long)floorf(V[(i0 * 3 + 1) * 32] * sc);
-        const bool odd = (k & 1) != 0;
+        const float2 f = mul2(f2(slot_ch(Vb, i0, 0), slot_ch(Vb, i0, 1)), f2(q.x, q.x));
+        const bool odd = d_parity(floorf(f.x)) != d_parity(floorf(f.y));
         r0 = d_clamp01(odd ? t.x : q.y); r1 = d_clamp01(odd ? t.y : q.z); r2 = d_clamp01(odd ? t.z : q.w);
         break;
     }
     case PMC_OP_RAMP: {
-        int ns = __float_as_int(__ldg(&p[0]));
-        const float* pos = p + 1;
-        const float* col = p + 5;
-        float t = d_clamp01(V[(i0 * 3) * 32]);
-        if (t <= __ldg(&pos[0])) {
-            r0 = __ldg(&col[0]); r1 = __ldg(&col[1]); r2 = __ldg(&col[2]);
-        } else if (t >= __ldg(&pos[ns - 1])) {
-            r0 = __ldg(&col[3 * (ns - 1)]); r1 = __ldg(&col[3 * (ns - 1) + 1]); r2 = __ldg(&col[3 * (ns - 1) + 2]);
-        } else {
-            int k = 0;
-            while (k + 2 < ns && t >= __ldg(&pos[k + 1])) ++k;
-            float p0 = __ldg(&pos[k]), p1 = __ldg(&pos[k + 1]);
-            float w = (t - p0) / (p1 - p0);
-            float a0 = __ldg(&col[3 * k]), a1 = __ldg(&col[3 * k + 1]), a2 = __ldg(&col[3 * k + 2]);
-            r0 = fmaf(w, __ldg(&col[3 * k + 3]) - a0, a0);
-            r1 = fmaf(w, __ldg(&col[3 * k + 4]) - a1, a1);
-            r2 = fmaf(w, __ldg(&col[3 * k + 5]) - a2, a2);
+        // parameters: {first stop, last stop, second, third (2 if absent)}, (stop, 1 / segment
+        // length) of segments 0..2, padding, colours of stops 0..3 and of the last stop, four
+        // floats each
+        const float4 q = __ldg(p4);
+        const float t = d_clamp01(slot_ch(Vb, i0, 0));
+        const int k = (t >= q.z ? 1 : 0) + (t >= q.w ? 1 : 0);   // interior stops at or below t
+        const float2 seg = __ldg(reinterpret_cast<const float2*>(p + 4) + k);
+        const float4 ca = __ldg(p4 + 3 + k);
+        const float4 cb = __ldg(p4 + 4 + k);
+        const float w = (t - seg.x) * seg.y;
+        r0 = fmaf(w, cb.x - ca.x, ca.x);
+        r1 = fmaf(w, cb.y - ca.y, ca.y);
+        r2 = fmaf(w, cb.z - ca.z, ca.z);
+        if (t <= q.x) {
+            const float4 c0 = __ldg(p4 + 3);
+            r0 = c0.x; r1 = c0.y; r2 = c0.z;
+        } else if (t >= q.y) {
+            const float4 cl = __ldg(p4 + 7);
+            r0 = cl.x; r1 = cl.y; r2 = cl.z;
         }
         r0 = d_clamp01(r0); r1 = d_clamp01(r1); r2 = d_clamp01(r2);
         break;
     }
     case PMC_OP_MIX: {
-        float f = d_clamp01(i2 != 0xFFFFu ? V[(i2 * 3) * 32] : __ldg(&p[0]));
-        float a0 = V[(i0 * 3) * 32], a1 = V[(i0 * 3 + 1) * 32], a2 = V[(i0 * 3 + 2) * 32];
-        r0 = d_clamp01(fmaf(f, V[(i1 * 3) * 32] - a0, a0));
-        r1 = d_clamp01(fmaf(f, V[(i1 * 3 + 1) * 32] - a1, a1));
-        r2 = d_clamp01(fmaf(f, V[(i1 * 3 + 2) * 32] - a2, a2));
+        const float f = d_clamp01(((ins.x >> 8) & FLAG_IN2) ? slot_ch(Vb, i2, 0) : __ldg(&p[0]));
+        const float a0 = slot_ch(Vb, i0, 0), a1 = slot_ch(Vb, i0, 1), a2 = slot_ch(Vb, i0, 2);
+        r0 = d_clamp01(fmaf(f, slot_ch(Vb, i1, 0) - a0, a0));
+        r1 = d_clamp01(fmaf(f, slot_ch(Vb, i1, 1) - a1, a1));
+        r2 = d_clamp01(fmaf(f, slot_ch(Vb, i1, 2) - a2, a2));
         break;
     }
     case PMC_OP_ADD:
-        r0 = d_clamp01(V[(i0 * 3) * 32] + V[(i1 * 3) * 32]);
-        r1 = d_clamp01(V[(i0 * 3 + 1) * 32] + V[(i1 * 3 + 1) * 32]);
-        r2 = d_clamp01(V[(i0 * 3 + 2) * 32] + V[(i1 * 3 + 2) * 32]);
+        r0 = d_clamp01(slot_ch(Vb, i0, 0) + slot_ch(Vb, i1, 0));
+        r1 = d_clamp01(slot_ch(Vb, i0, 1) + slot_ch(Vb, i1, 1));
+        r2 = d_clamp01(slot_ch(Vb, i0, 2) + slot_ch(Vb, i1, 2));
         break;
     case PMC_OP_MUL:
-        r0 = d_clamp01(V[(i0 * 3) * 32] * V[(i1 * 3) * 32]);
-        r1 = d_clamp01(V[(i0 * 3 + 1) * 32] * V[(i1 * 3 + 1) * 32]);
-        r2 = d_clamp01(V[(i0 * 3 + 2) * 32] * V[(i1 * 3 + 2) * 32]);
+        r0 = d_clamp01(slot_ch(Vb, i0, 0) * slot_ch(Vb, i1, 0));
+        r1 = d_clamp01(slot_ch(Vb, i0, 1) * slot_ch(Vb, i1, 1));
+        r2 = d_clamp01(slot_ch(Vb, i0, 2) * slot_ch(Vb, i1, 2));
         break;
     case PMC_OP_POW: {
-        float e = __ldg(&p[0]);
-        r0 = d_clamp01(powf(fmaxf(V[(i0 * 3) * 32], 0.0f), e));
-        r1 = d_clamp01(powf(fmaxf(V[(i0 * 3 + 1) * 32], 0.0f), e));
-        r2 = d_clamp01(powf(fmaxf(V[(i0 * 3 + 2) * 32], 0.0f), e));
+        // x^e for x >= 0 through the hardware base-2 logarithm and exponential (__powf);
+        // x = 0 gives 0 for every e > 0
+        const float e = __ldg(&p[0]);
+        r0 = d_clamp01(__powf(fmaxf(slot_ch(Vb, i0, 0), 0.0f), e));
+        r1 = d_clamp01(__powf(fmaxf(slot_ch(Vb, i0, 1), 0.0f), e));
+        r2 = d_clamp01(__powf(fmaxf(slot_ch(Vb, i0, 2), 0.0f), e));
         break;
     }
     case PMC_OP_FACING: {
         const float4 q = __ldg(p4);
-        float d = fmaf(V[(i0 * 3) * 32], q.x, fmaf(V[(i0 * 3 + 1) * 32], q.y, V[(i0 * 3 + 2) * 32] * q.z));
+        float d = fmaf(slot_ch(Vb, i0, 0), q.x, fmaf(slot_ch(Vb, i0, 1), q.y, slot_ch(Vb, i0, 2) * q.z));
         r0 = r1 = r2 = d_clamp01(fabsf(d));
         break;
     }
     default:
         break;
     }
-    V[(out * 3) * 32] = r0;
-    V[(out * 3 + 1) * 32] = r1;
-    V[(out * 3 + 2) * 32] = r2;
+    slot_store(Vb, out, r0, r1, r2);
 }
 
+
+// Two points per lane: the slot file is [slot][channel][lane][2], so a slot is 2 x SLOT_BYTES
+// and a channel row 2 x CH_BYTES; an operand's byte offset in a program doubles.  One
+// decode, dispatch and parameter load serve both points, and their two independent
+// computations overlap.
+__device__ __forceinline__ float2 slot2(const char* Vb, uint32_t off, int ch) {
+    return *reinterpret_cast<const float2*>(Vb + 2u * off + ch * (2u * CH_BYTES));
+}
+__device__ __forceinline__ void slot2_store(char* Vb, uint32_t off, float2 r0, float2 r1, float2 r2) {
+    float2* o = reinterpret_cast<float2*>(Vb + 2u * off);
+    o[0] = r0;
+    o[32] = r1;
+    o[64] = r2;
+}
+__device__ __forceinline__ float2 sat2(float2 x) { return f2(d_clamp01(x.x), d_clamp01(x.y)); }
+
+// exec_node for points A (.x of every pair) and B (.y).
+__device__ __forceinline__ void exec_node2(uint32_t op, const uint4& ins, char* Vb, const PointIn& A, const PointIn& B,
+                                           const float* __restrict__ params, const float2* grad) {
+    const uint32_t out = ins.y & 0xFFFFu;
+    const uint32_t i0 = ins.y >> 16, i1 = ins.z & 0xFFFFu, i2 = ins.z >> 16;
+    const float* p = params + ins.w;
+    const float4* p4 = reinterpret_cast<const float4*>(p);
+    float2 r0 = f2(0.f, 0.f), r1 = f2(0.f, 0.f), r2 = f2(0.f, 0.f);
+    switch (op) {
+    case PMC_OP_UV: r0 = f2(A.u, B.u); r1 = f2(A.v, B.v); break;
+    case PMC_OP_POSITION: r0 = f2(A.px, B.px); r1 = f2(A.py, B.py); r2 = f2(A.pz, B.pz); break;
+    case PMC_OP_NORMAL: r0 = f2(A.nx, B.nx); r1 = f2(A.ny, B.ny); r2 = f2(A.nz, B.nz); break;
+    case PMC_OP_CONST: {
+        const float4 q = __ldg(p4);
+        r0 = f2(q.x, q.x); r1 = f2(q.y, q.y); r2 = f2(q.z, q.z);
+        break;
+    }
+    case PMC_OP_UV_AFFINE: {
+        const float4 q = __ldg(p4);
+        const float4 t = __ldg(p4 + 1);
+        const float2 x = slot2(Vb, i0, 0), y = slot2(Vb, i0, 1);
+        r0 = fma2(f2(q.x, q.x), x, fma2(f2(q.y, q.y), y, f2(t.x, t.x)));
+        r1 = fma2(f2(q.z, q.z), x, fma2(f2(q.w, q.w), y, f2(t.y, t.y)));
+        break;
+    }
+    case PMC_OP_FBM: {
+        const float4 q = __ldg(p4);
+        const float4 t = __ldg(p4 + 1);
+        const float2 x = slot2(Vb, i0, 0), y = slot2(Vb, i0, 1);
+        r0 = f2(d_fbm(x.x, y.x, q, t, grad), d_fbm(x.y, y.y, q, t, grad));
+        r1 = r2 = r0;
+        break;
+    }
+    case PMC_OP_VORONOI: {
+        const float4 q = __ldg(p4);
+        const float2 x = slot2(Vb, i0, 0), y = slot2(Vb, i0, 1);
+        const uint32_t seed = (uint32_t)__float_as_int(q.y);
+        r0 = f2(d_voronoi(x.x, y.x, q.x, seed), d_voronoi(x.y, y.y, q.x, seed));
+        r1 = r2 = r0;
+        break;
+    }
+    case PMC_OP_CHECKER: {
+        const float4 q = __ldg(p4);
+        const float4 t = __ldg(p4 + 1);
+        const float2 fx = mul2(slot2(Vb, i0, 0), f2(q.x, q.x)), fy = mul2(slot2(Vb, i0, 1), f2(q.x, q.x));
+        const bool oa = d_parity(floorf(fx.x)) != d_parity(floorf(fy.x));
+        const bool ob = d_parity(floorf(fx.y)) != d_parity(floorf(fy.y));
+        r0 = sat2(f2(oa ? t.x : q.y, ob ? t.x : q.y));
+        r1 = sat2(f2(oa ? t.y : q.z, ob ? t.y : q.z));
+        r2 = sat2(f2(oa ? t.z : q.w, ob ? t.z : q.w));
+        break;
+    }
+    case PMC_OP_RAMP: {
+        const float4 q = __ldg(p4);
+        const float2 tt = sat2(slot2(Vb, i0, 0));
+        const float ts[2] = {tt.x, tt.y};
+        float o[2][3];
+#pragma unroll
+        for (int s = 0; s < 2; ++s) {
+            const float t = ts[s];
+            const int k = (t >= q.z ? 1 : 0) + (t >= q.w ? 1 : 0);
+            const float2 seg = __ldg(reinterpret_cast<const float2*>(p + 4) + k);
+            const float4 ca = __ldg(p4 + 3 + k);
+            const float4 cb = __ldg(p4 + 4 + k);
+            const float w = (t - seg.x) * seg.y;
+            o[s][0] = fmaf(w, cb.x - ca.x, ca.x);
+            o[s][1] = fmaf(w, cb.y - ca.y, ca.y);
+            o[s][2] = fmaf(w, cb.z - ca.z, ca.z);
+            if (t <= q.x) {
+                const float4 c0 = __ldg(p4 + 3);
+                o[s][0] = c0.x; o[s][1] = c0.y; o[s][2] = c0.z;
+            } else if (t >= q.y) {
+                const float4 cl = __ldg(p4 + 7);
+                o[s][0] = cl.x; o[s][1] = cl.y; o[s][2] = cl.z;
+            }
+        }
+        r0 = sat2(f2(o[0][0], o[1][0]));
+        r1 = sat2(f2(o[0][1], o[1][1]));
+        r2 = sat2(f2(o[0][2], o[1][2]));
+        break;
+    }
+    case PMC_OP_MIX: {
+        const float2 f = sat2(((ins.x >> 8) & FLAG_IN2) ? slot2(Vb, i2, 0) : f2(__ldg(&p[0]), __ldg(&p[0])));
+        const float2 a0 = slot2(Vb, i0, 0), a1 = slot2(Vb, i0, 1), a2 = slot2(Vb, i0, 2);
+        // a + f (b - a), each product and sum rounded as fmaf(f, b - a, a) rounds them
+        r0 = sat2(fma2(f, fma2(a0, f2(-1.0f, -1.0f), slot2(Vb, i1, 0)), a0));
+        r1 = sat2(fma2(f, fma2(a1, f2(-1.0f, -1.0f), slot2(Vb, i1, 1)), a1));
+        r2 = sat2(fma2(f, fma2(a2, f2(-1.0f, -1.0f), slot2(Vb, i1, 2)), a2));
+        break;
+    }
+    case PMC_OP_ADD:
+        r0 = sat2(add2(slot2(Vb, i0, 0), slot2(Vb, i1, 0)));
+        r1 = sat2(add2(slot2(Vb, i0, 1), slot2(Vb, i1, 1)));
+        r2 = sat2(add2(slot2(Vb, i0, 2), slot2(Vb, i1, 2)));
+        break;
+    case PMC_OP_MUL:
+        r0 = sat2(mul2(slot2(Vb, i0, 0), slot2(Vb, i1, 0)));
+        r1 = sat2(mul2(slot2(Vb, i0, 1), slot2(Vb, i1, 1)));
+        r2 = sat2(mul2(slot2(Vb, i0, 2), slot2(Vb, i1, 2)));
+        break;
+    case PMC_OP_POW: {
+        const float e = __ldg(&p[0]);
+        const float2 x0 = slot2(Vb, i0, 0), x1 = slot2(Vb, i0, 1), x2 = slot2(Vb, i0, 2);
+        r0 = sat2(f2(__powf(fmaxf(x0.x, 0.0f), e), __powf(fmaxf(x0.y, 0.0f), e)));
+        r1 = sat2(f2(__powf(fmaxf(x1.x, 0.0f), e), __powf(fmaxf(x1.y, 0.0f), e)));
+        r2 = sat2(f2(__powf(fmaxf(x2.x, 0.0f), e), __powf(fmaxf(x2.y, 0.0f), e)));
+        break;
+    }
+    case PMC_OP_FACING: {
+        const float4 q = __ldg(p4);
+        const float2 d = fma2(slot2(Vb, i0, 0), f2(q.x, q.x),
+                              fma2(slot2(Vb, i0, 1), f2(q.y, q.y), mul2(slot2(Vb, i0, 2), f2(q.z, q.z))));
+        r0 = sat2(f2(fabsf(d.x), fabsf(d.y)));
+        r1 = r2 = r0;
+        break;
+    }
+    default:
+        break;
+    }
+    slot2_store(Vb, out, r0, r1, r2);
+}
 
 }  // namespace pmc

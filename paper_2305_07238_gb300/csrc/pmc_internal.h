@@ -29,6 +29,13 @@ constexpr uint32_t OP_ROOT_BEGIN = 32;
 constexpr uint32_t OP_LOAD_ROOT = 33;   // y: out slot | root ordinal; reads that node's probe record
 constexpr uint32_t FLAG_ROOT = 1;
 constexpr uint32_t FLAG_POSROOT = 2;    // ROOT_BEGIN of a node looked up under a position voxel
+constexpr uint32_t FLAG_IN2 = 4;        // MIX: the factor comes from in2 (else from fp0)
+
+// On the device, y and z of a node instruction hold byte offsets into the lane's slot
+// file (slot x SLOT_BYTES: the file is [slot][channel][lane] per warp), so an operand is one
+// add away from its address; 16-bit offsets allow MAX_DEVICE_SLOTS slots.
+constexpr uint32_t SLOT_BYTES = 3u * 32u * 4u;
+constexpr uint32_t MAX_DEVICE_SLOTS = 0xFFFFu / SLOT_BYTES;
 constexpr uint32_t ROOT_POS_BIT = 1u << 31;   // device root table: node ID | this bit for such nodes
 
 // Each cacheable node also gets a standalone program (its sub-graph, with any cacheable
@@ -43,6 +50,8 @@ struct RootInfo {
     uint32_t n_slots;
     uint32_t node;
     uint32_t out_slot;
+    uint32_t nodes;       // nodes and FP32 operations one run of the program evaluates
+    uint32_t flops;
 };
 
 struct MatInfo {
@@ -58,6 +67,9 @@ struct MatInfo {
     uint32_t outer_out_slot;
     uint32_t outer_slots;
     uint32_t pad;
+    // nodes and FP32 operations one point evaluates with the whole program run (every
+    // block evaluated) and with the outer program
+    uint32_t full_nodes, full_flops, outer_nodes, outer_flops;
 };
 
 struct CompiledMaterial {
@@ -185,7 +197,12 @@ struct BatchArgs {
     int split;
     const RootInfo* rinfo; uint32_t n_roots_total; uint32_t max_level;
     uint32_t* miss_cnt;        // n_roots_total counters, then MAX_LEVELS item counters
-    uint32_t* root_item_base;  // n_roots_total + 1
+    // cacheable nodes in ascending nesting level (a permutation of the global root index),
+    // and where each level starts in it (MAX_LEVELS + 1 entries): the batched evaluation of
+    // one level visits only that level's work items
+    const uint32_t* root_order; const uint32_t* level_start;
+    uint32_t* root_item_base;  // n_roots_total + 1 item offsets in root_order's order, then
+                               // MAX_LEVELS + 1 first items of each level
     uint32_t* misslist;        // probe_cap
     int insert_rounds;         // 1: atomicMin rounds (claims hold epoch words); 0: cell-grouped
     // learned surrogates: per material the surrogate's slot (-1 = none) and cacheable-node
@@ -202,6 +219,8 @@ struct BatchArgs {
     int unsorted;              // 1: no grouping; k_eval_fused probes inline in batch order
     int probe_inline;          // 1: grouped; k_eval_fused probes inline (no lookup kernel)
     uint32_t lookup_rb;        // k_lookup: probes in flight per lane (1, 2 or 4)
+    int block_items;           // 1: the per-point evaluator claims block-wide tiles of items
+    int one_point;             // 1: one point per lane in the per-point evaluator (else two)
     int alg1;                  // the paper's concurrent update: 8-byte slots {hash2, RGB9E5},
                                // looked up and inserted inside the evaluator (one 64-bit CAS)
     // replacement by visibility class (Sec. 5): per point its class (caller-owned, optional,
@@ -229,12 +248,13 @@ cudaError_t launch_keys(const uint32_t* mat, const uint32_t* node, const float* 
                         uint64_t* key, uint64_t* cell, uint32_t* h2, cudaStream_t s);
 size_t eval_smem_bytes(uint32_t max_slots);
 
-// Learned surrogate kernels (mlp.cu).
-size_t mlp_train_smem();
-size_t mlp_infer_smem();
+// Training of the learned surrogates on the tcgen05 tensor cores (mlp_tc.cu): `steps`
+// minibatches of 128 rows per (split, material); mode 0 takes Adam steps, mode 1 adds the
+// gradient into `grad`.  err (may be null) receives ERR_TIMEOUT if a bounded wait for the
+// tensor cores ran out (that material's loss then reads NaN).
 cudaError_t launch_mlp_train(float* theta, float* adam_m, float* adam_v, float* grad, const float* data, float* loss,
-                             uint32_t n_mats, uint32_t n_data, uint32_t steps, uint64_t sample0, uint32_t step0,
-                             uint32_t total_steps, float lr, float grad_scale, int mode, uint32_t splits,
+                             uint32_t* err, uint32_t n_mats, uint32_t n_data, uint32_t steps, uint64_t sample0,
+                             uint32_t step0, uint32_t total_steps, float lr, float grad_scale, int mode, uint32_t splits,
                              cudaStream_t s);
 // Tensor-core (tcgen05) inference (mlp_tc.cu); err may be null.
 cudaError_t launch_mlp_forward_tc(const float* theta, const float* u, const float* v, uint32_t n, float* out, int clamp,

@@ -27,6 +27,8 @@ PMC_PROBE_INLINE = 0x40
 PMC_ALG1 = 0x80
 PMC_REPLACE_VISIBILITY = 0x100
 PMC_POSITION_DESCRIPTOR = 0x200
+PMC_BLOCK_ITEMS = 0x400
+PMC_ONE_POINT = 0x800
 PMC_GRAPH_RESET = 0x1
 TUNE_MAX = 16
 
@@ -38,7 +40,7 @@ EXPORTED = (
     "pmc_get_surrogate", "pmc_use_surrogates", "pmc_mlp_forward", "pmc_mlp_gradient", "pmc_mlp_train",
     "pmc_get_schedule", "pmc_set_schedule", "pmc_graph_create", "pmc_graph_launch", "pmc_graph_destroy",
     "pmc_autotune", "pmc_status_str", "pmc_slot_classes", "pmc_analyze_material_ext", "pmc_cast_rays",
-    "pmc_node_cost",
+    "pmc_node_cost", "pmc_eval_passes_host",
 )
 NOALLOC_MAX_POINTS, NOALLOC_MAX_PROBES, NOALLOC_MAX_MATERIALS = 8192, 32768, 4096
 PHASES = ("sort", "lookup", "missed", "eval", "insert", "finish")
@@ -133,6 +135,8 @@ def load():
     L.pmc_analyze_material.argtypes = [vp, u32, vp, vp, u32, vp, vp]
     L.pmc_analyze_material.restype = st
     L.pmc_analyze_material_ext.argtypes = [vp, u32, u32, u32, vp, vp, vp, u32, vp, vp]
+    L.pmc_eval_passes_host.argtypes = [vp, vp, u32, vp, vp, vp]
+    L.pmc_eval_passes_host.restype = st
     L.pmc_node_cost.argtypes = [vp]
     L.pmc_node_cost.restype = u32
     L.pmc_analyze_material_ext.restype = st
@@ -295,6 +299,25 @@ class Cache:
         _check(load().pmc_eval_batch_host(self._h, C.byref(p), out_rgb.ctypes.data,
                                           None if out_hits is None else out_hits.ctypes.data,
                                           _stream_handle(stream)), "pmc_eval_batch_host")
+
+    def eval_passes_host(self, passes, out_rgb, out_hits=None, stream=None):
+        """Consecutive passes from host buffers (dicts of numpy arrays) into out_rgb[k] (and
+        out_hits[k]), copies overlapped with the evaluation; returns when all are done."""
+        keep = []
+        for pts in passes:
+            d = {k: np.ascontiguousarray(pts[k]) for k in POINT_FIELDS + (CONE_FIELDS if _has_cones(pts) else ())}
+            if pts.get("vis") is not None:
+                d["vis"] = np.ascontiguousarray(pts["vis"], dtype=np.uint8)
+            keep.append(d)
+        arr = (_Points * max(1, len(keep)))()
+        for i, d in enumerate(keep):
+            arr[i] = _points(d, len(d["u"]), lambda a: a.ctypes.data)
+        rgb_p = (C.c_void_p * max(1, len(keep)))(*[o.ctypes.data for o in out_rgb])
+        hits_p = None
+        if out_hits is not None:
+            hits_p = (C.c_void_p * max(1, len(keep)))(*[None if h is None else h.ctypes.data for h in out_hits])
+        _check(load().pmc_eval_passes_host(self._h, arr, len(keep), rgb_p, hits_p, _stream_handle(stream)),
+               "pmc_eval_passes_host")
 
     def sync(self):
         _check(load().pmc_sync(self._h), "pmc_sync")

@@ -315,3 +315,33 @@ def test_reset_empties_table(P, mode):
     assert gpu.stats()["inserted"] == 0 and not gpu.table()[0].any()
     _, hits = _run_gpu(gpu, P, pts)
     assert not hits.any()
+
+
+def test_pipelined_host_passes_equal_device_passes(P):
+    """pmc_eval_passes_host (copies overlapped with evaluation, two staging sets) gives the
+    device entry point's outputs, hits, counters and table, pass by pass, with a ragged last
+    pass and a pass without hit output."""
+    frame = W.Frame(W.FrameSpec(width=1920, height=1080, n_mats=16, seed=4))
+    mats = W.random_materials(16, 20, 120, 0.2, seed=4)
+    passes = [frame.points(p, rows=(100, 130)) for p in range(5)]
+    passes[-1] = W.slice_points(passes[-1], 0, 40000 - 17)
+    dev = P.Cache(mats, 1 << 14, 8)
+    host = P.Cache(mats, 1 << 14, 8)
+    want = []
+    for pts in passes:
+        n = len(pts["u"])
+        rgb = torch.empty((3, n), device="cuda")
+        hits = torch.empty(n, dtype=torch.int16, device="cuda")
+        dev.eval_batch(P.points_to_device(pts), rgb, hits)
+        want.append((rgb.cpu().numpy(), hits.cpu().numpy().astype(np.uint16)))
+    out_rgb = [np.full(3 * len(p["u"]), -1.0, dtype=np.float32) for p in passes]
+    out_hits = [np.zeros(len(p["u"]), dtype=np.uint16) for p in passes]
+    out_hits[2] = None
+    host.eval_passes_host(passes, out_rgb, out_hits)
+    for k, (rgb, hits) in enumerate(want):
+        assert np.array_equal(out_rgb[k].reshape(3, -1), rgb), k
+        if out_hits[k] is not None:
+            assert np.array_equal(out_hits[k], hits), k
+    assert dev.stats() == host.stats()
+    assert np.array_equal(dev.table()[0], host.table()[0])
+    assert np.array_equal(dev.table()[1], host.table()[1])

@@ -55,7 +55,10 @@ def _host(ts):
     return [t.cpu().numpy() for t in ts]
 
 
-SCHEDULES = [(0, 4), (0, 2), (0, 1), (0x8, 4), (0x28, 4), (0x10, 4), (0x30, 2), (0x40, 4), (0x50, 4)]
+# ... plus the evaluator's work distribution: block-wide tiles of one material (0x400) and one
+# point per lane (0x800)
+SCHEDULES = [(0, 4), (0, 2), (0, 1), (0x8, 4), (0x28, 4), (0x10, 4), (0x30, 2), (0x40, 4), (0x50, 4),
+             (0x400, 2), (0x800, 2), (0x410, 4), (0x840, 4)]
 
 
 def test_every_schedule_same_results(P, band):
@@ -215,3 +218,25 @@ def test_unsorted_refused_with_surrogates(P):
     assert ei.value.status == P.PMC_ERR_UNSUPPORTED
     c.use_surrogates(False)
     c.set_schedule(0x20, 4)
+
+
+@pytest.mark.parametrize("flags", [0, 0x400, 0x800])
+def test_uncached_work_distributions_same_results(P, band, flags):
+    """With the cache off every point runs its whole program: two points per lane in warp
+    pairs or block tiles, and one point per lane, give the same outputs bit for bit (and
+    match the FP64 oracle)."""
+    mats, parts = band
+    ref = O.Cache(mats, 1 << 12, 8, cache_off=True)
+    c = P.Cache(mats, 1 << 12, 8, flags=P.PMC_CACHE_OFF)
+    c.set_schedule(flags, 4)
+    base = P.Cache(mats, 1 << 12, 8, flags=P.PMC_CACHE_OFF)
+    for p in parts[:2]:
+        d = P.points_to_device(p)
+        rgb, hits = _outputs(P, [p])
+        _eager(P, c, [d], rgb, hits)
+        rgb0, hits0 = _outputs(P, [p])
+        _eager(P, base, [d], rgb0, hits0)
+        assert np.array_equal(rgb[0].cpu().numpy(), rgb0[0].cpu().numpy())
+        assert float(np.abs(rgb[0].cpu().numpy() - ref.run_batch(p)["rgb"]).max()) <= TOL
+    for k in ("flops", "nodes_evaluated", "points"):
+        assert c.stats()[k] == base.stats()[k], k

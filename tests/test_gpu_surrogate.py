@@ -256,3 +256,33 @@ def test_surrogate_pass_beats_exact_evaluation_with_the_cache(P, trained):
             hit_rate = (st["hits"] - before["hits"]) / max(1, st["lookups"] - before["lookups"])
     assert hit_rate > 0.5, hit_rate                # the cache is doing its job ...
     assert times["surrogate"] * 1.3 <= times["cached"], (times, hit_rate)   # ... and loses
+
+
+def test_features_within_one_bf16_step_of_sin_cos(P):
+    """The kernels form the 64 Fourier features from sincospif at k = 1, 5, 9, 13 and the
+    angle-addition formulas in between.  With identity hidden layers and W3 picking three
+    features, the network returns max(BF16(feature), 0) exactly; every returned feature is
+    within one BF16 step of BF16(sin or cos of pi k x) evaluated in FP64, and almost all equal
+    it (a flip needs the FP32 value within a few ulps of a BF16 rounding boundary)."""
+    rng = np.random.default_rng(41)
+    n = 4096
+    u = rng.random(n).astype(np.float32)
+    v = rng.random(n).astype(np.float32)
+    u[:4] = [0.0, 1.0, 0.5, 0.25]
+    ref = M.bf16_round(M.features(u.astype(np.float64), v.astype(np.float64)))   # (n, 64)
+    mism = 0
+    for f0 in range(0, 64, 3):
+        sel = [min(f0 + k, 63) for k in range(3)]
+        th = np.zeros(M.N_PARAMS)
+        th[0:4096] = np.eye(64).ravel()            # W1 [in][out]
+        th[4160:8256] = np.eye(64).ravel()         # W2
+        for o, f in enumerate(sel):
+            th[8320 + f * 3 + o] = 1.0             # W3 [in][out]
+        out = P.mlp_forward(_dev(th), _dev(u), _dev(v), clamp=False).cpu().numpy()
+        for o, f in enumerate(sel):
+            want = np.maximum(ref[:, f], 0.0)
+            got = out[o].astype(np.float64)
+            step = np.abs(want) * 2.0 ** -7 + 1e-30   # one BF16 step (8 significant bits)
+            assert np.all(np.abs(got - want) <= step), (f, float(np.abs(got - want).max()))
+            mism += int(np.sum(got != want))
+    assert mism <= 0.005 * n * 66, mism

@@ -295,3 +295,27 @@ def test_bad_material_id_reported():
     r = c.run_batch(pts)
     assert r["status"] == 2
     assert r["hits"][2] == 0 and np.all(r["rgb"][:, 2] == 0)
+
+
+@pytest.mark.parametrize("kw", [{}, {"replacement": True}, {"pos_level": 4}, {"cones": True},
+                                {"cache_off": True}, {"alg1": True}])
+def test_all_core_form_equals_one_thread(kw):
+    """The all-core form of a pass (ranges of points in parallel against the same snapshot,
+    then one sequential insert) gives the one-thread results bit for bit."""
+    kw = dict(kw)
+    cones = kw.pop("cones", False)
+    mats = W.random_materials(12, 10, 80, 0.3, seed=31)
+    frame = W.Frame(W.FrameSpec(width=640, height=48, n_mats=12, seed=31))
+    caches = [O.Cache(mats, 512, 4, threads=t, **kw) for t in (1, 4)]
+    for p in range(3):
+        pts = frame.points(p, cones=cones) if cones else frame.points(p)
+        if kw.get("replacement"):
+            pts["vis"] = (np.arange(len(pts["u"])) % 3).astype(np.uint8)
+        pts["mat"][::997] = 99                    # a few bad material indices
+        r = [c.run_batch(pts, probes=True) for c in caches]
+        for k in ("rgb", "hits", "evaluated", "key", "cell", "h2", "hit"):
+            assert np.array_equal(r[0][k], r[1][k]), k
+        assert r[0]["status"] == r[1]["status"] != 0
+        assert caches[0].stats() == caches[1].stats()
+        for a, b in zip(caches[0].table(), caches[1].table()):
+            assert np.array_equal(a, b)
