@@ -42,7 +42,7 @@ SAMPLE_ROWS = (0, 40)            # CPU-oracle sample: 40 full-width rows, all 16
 REF_ROWS = (0, 16)               # reference arm: 16 full-width rows per step, all 16 passes
 # ncu capture of k_eval / k_lookup on the same workload (profiles/): DRAM bytes per launch
 # (profiles/launches_frame1080p.md: mean over the launches of one frame of each kernel)
-NCU_TRAFFIC = {"eval": 313.0e6, "eval_roots": 182.1e6, "lookup": 1050.1e6}
+NCU_TRAFFIC = {"eval": 150.7e6, "eval_roots": 77.6e6, "lookup": 329.4e6}
 
 FP32_LANES_PER_SM = 128          # Blackwell SM: 4 partitions x 32 FP32 lanes
 
@@ -257,9 +257,9 @@ def ours(args, rank, world, local_rank, dist):
         # break-even cost of a cacheable node: a probe (its lookup and insert, from the
         # all-roots run's phase times) against the evaluation a hit saves at the measured hit
         # rate
-        ms, st = m_all["timing"]["ms"], m_all["frame_stats"]
-        t_probe = (ms["lookup"] + ms["insert"]) / args.steps / max(1, st["lookups"])
-        hit = st["hits"] / max(1, st["lookups"])
+        ms_all, st_all = m_all["timing"]["ms"], m_all["frame_stats"]
+        t_probe = (ms_all["lookup"] + ms_all["insert"]) / args.steps / max(1, st_all["lookups"])
+        hit = st_all["hits"] / max(1, st_all["lookups"])
         min_root_cost = int(round(t_probe / max(1e-30, hit * t_flop) / 50.0) * 50)
         cached = P.Cache(mats, N_CELLS, N_ENTRIES, uv_level=LEVEL, min_root_cost=min_root_cost, device=local_rank)
         m = measure(cached)
@@ -285,7 +285,7 @@ def ours(args, rank, world, local_rank, dist):
     # ---- end to end through the host-buffer entry point --------------------------------
     e2e = None
     if "e2e" in legs:
-        e2e = e2e_run(torch, P, mats, passes_host, args, local_rank, barrier, dist, dev)
+        e2e = e2e_run(torch, P, mats, passes_host, args, local_rank, barrier, dist, dev, min_root_cost)
 
     # ---- roofline of the dominant kernel ------------------------------------------------
     hbm_peak, sm_mhz_max, peak_kind = peaks()
@@ -348,8 +348,8 @@ def ours(args, rank, world, local_rank, dist):
         "cached_all_roots": {"value": round(whole_job_rate(pts_total, world, m_all["secs"]), 1), "unit": UNIT,
                              "ms_per_step": round(m_all["secs"] / args.steps * 1e3, 3),
                              "hit_rate": round(hit, 4),
-                             "lookups_per_point": round(st["lookups"] / (n * SPP), 3),
-                             "phase_ms_per_step": {k: round(v / args.steps, 3) for k, v in ms.items()}},
+                             "lookups_per_point": round(st_all["lookups"] / (n * SPP), 3),
+                             "phase_ms_per_step": {k: round(v / args.steps, 3) for k, v in ms_all.items()}},
         "uncached": {"value": round(u_value, 1), "unit": UNIT,
                      "ms_per_step": round(usecs / args.steps * 1e3, 3),
                      "speedup_cached_over_uncached": round(value / u_value, 3),
@@ -399,6 +399,9 @@ def ours(args, rank, world, local_rank, dist):
         guarded("replacement", lambda: replace_leg(torch, P, dev, local_rank, seed=rank))
     if "sweep" in legs:
         guarded("scale_sweep", lambda: sweep_leg(torch, P, dev, local_rank, seed=rank))
+    if "scale" in legs:
+        guarded("scale", lambda: sweep_leg(torch, P, dev, local_rank, seed=rank, full=False,
+                                           min_root_cost=min_root_cost))
     if "threshold" in legs:
         guarded("cost_threshold", lambda: threshold_leg(torch, P, mats, dev_passes, outs, hits, local_rank))
         if u_value == u_value and "runs" in line["cost_threshold"]:
@@ -788,13 +791,14 @@ def cones_leg(torch, P, dev, local_rank, seed=0):
 SCALE_MATS, SCALE_LO, SCALE_HI, SCALE_SP, SCALE_ZIPF, SCALE_SIDE, SCALE_BATCHES = 4096, 10, 2000, 0.4, 0.9, 2048, 64
 
 
-def sweep_leg(torch, P, dev, local_rank, seed=0):
+def sweep_leg(torch, P, dev, local_rank, seed=0, full=True, min_root_cost=0):
     """The scale configuration: 4096 networks of 10-2000 nodes (40 % SP), materials
-    Zipf(0.9) per 8x8 tile of a 2048x2048 stream, 2^28 points in 64 batches of 2^22; the
-    table swept from 2^20 to 2^29 slots (16 MB - 8 GB).  Per size: points/s of the whole
-    stream replayed as one CUDA graph, hit rate, inserted and dropped counts.  Then the
-    surrogate mix at 2^26 slots: networks trained for every material's candidate node,
-    the ones within RMSE 2e-3 enabled."""
+    Zipf(0.9) per 8x8 tile of a 2048x2048 stream, 2^28 points in 64 batches of 2^22.  With
+    `full`, the table swept from 2^20 to 2^29 slots (16 MB - 8 GB); else 2^26 slots (1 GB)
+    under the rule of Sec. 3 and under the cost threshold `min_root_cost`.  Per run: points/s
+    of the whole stream replayed as one CUDA graph, hit rate, inserted and dropped counts.
+    Then the surrogate mix at 2^26 slots (with the cost threshold): networks trained for
+    every material's candidate node, those validated within 1.6e-3 enabled."""
     from paper_2305_07238_gb300 import pmc as Pm
     t0 = time.perf_counter()
     mats = W.random_materials(SCALE_MATS, SCALE_LO, SCALE_HI, SCALE_SP, seed=seed + 500)
@@ -829,26 +833,32 @@ def sweep_leg(torch, P, dev, local_rank, seed=0):
     res["uncached"] = round(rate(u), 1)
     u.close()
     rows = []
-    for log_slots in range(20, 30):
-        c = P.Cache(mats, 1 << (log_slots - 3), N_ENTRIES, uv_level=LEVEL, device=local_rank, probe_capacity=need)
+    runs = [(ls, 0) for ls in range(20, 30)] if full else [(26, 0), (26, min_root_cost)]
+    for log_slots, thr in runs:
+        c = P.Cache(mats, 1 << (log_slots - 3), N_ENTRIES, uv_level=LEVEL, device=local_rank, probe_capacity=need,
+                    min_root_cost=thr)
         r = rate(c)
         s = c.stats()
-        rows.append({"slots": 1 << log_slots, "table_mb": (16 << log_slots) >> 20, "value": round(r, 1),
-                     "hit_rate": round(s["hits"] / max(1, s["lookups"]), 4), "inserted": s["inserted"],
+        rows.append({"slots": 1 << log_slots, "table_mb": (16 << log_slots) >> 20, "min_root_cost": thr,
+                     "value": round(r, 1), "hit_rate": round(s["hits"] / max(1, s["lookups"]), 4),
+                     "lookups_per_point": round(s["lookups"] / total, 3), "inserted": s["inserted"],
                      "dropped_full": s["dropped_full"], "speedup_over_uncached": round(r / res["uncached"], 3)})
         c.close()
-    res["sweep"] = rows
-    c = P.Cache(mats, 1 << 23, N_ENTRIES, uv_level=LEVEL, device=local_rank, probe_capacity=need)
+    res["sweep" if full else "runs"] = rows
+    c = P.Cache(mats, 1 << 23, N_ENTRIES, uv_level=LEVEL, device=local_rank, probe_capacity=need,
+                min_root_cost=min_root_cost)
     t = time.perf_counter()
     rmse = c.train_surrogates(n_train=1 << 16, n_valid=1 << 13, epochs=16, lr=1e-2, seed=2)
     torch.cuda.synchronize()
-    res["surrogate_mix"] = {"slots": 1 << 26, "train_s": round(time.perf_counter() - t, 2),
+    res["surrogate_mix"] = {"slots": 1 << 26, "min_root_cost": min_root_cost,
+                            "train_s": round(time.perf_counter() - t, 2),
                             "candidates": int(np.sum(rmse >= 0)),
                             "enabled": int(np.sum((rmse >= 0) & (rmse <= 1.6e-3))),
                             "value": round(rate(c), 1)}
     s = c.stats()
     res["surrogate_mix"]["hit_rate"] = round(s["hits"] / max(1, s["lookups"]), 4)
     res["surrogate_mix"]["surrogate_evals"] = s["surrogate_evals"]
+    res["surrogate_mix"]["speedup_over_uncached"] = round(res["surrogate_mix"]["value"] / res["uncached"], 3)
     c.close()
     del passes
     torch.cuda.empty_cache()
@@ -953,7 +963,7 @@ def surrogate_leg(torch, P, dev, local_rank, seed=0):
     return res
 
 
-def e2e_run(torch, P, mats, passes_host, args, local_rank, barrier, dist, dev):
+def e2e_run(torch, P, mats, passes_host, args, local_rank, barrier, dist, dev, min_root_cost=0):
     """Same frame through pmc_eval_passes_host from pinned host buffers: every pass's points
     go in and its colours and hit counts come out inside the timed region, the copies of a
     pass overlapping the evaluation of its neighbours."""
@@ -967,7 +977,7 @@ def e2e_run(torch, P, mats, passes_host, args, local_rank, barrier, dist, dev):
         pinned.append(d)
     rgb = [torch.empty(3 * n, dtype=torch.float32).pin_memory().numpy() for _ in range(SPP)]
     hits = [torch.empty(n, dtype=torch.int16).pin_memory().numpy().view(np.uint16) for _ in range(SPP)]
-    cache = P.Cache(mats, N_CELLS, N_ENTRIES, uv_level=LEVEL, device=local_rank)
+    cache = P.Cache(mats, N_CELLS, N_ENTRIES, uv_level=LEVEL, min_root_cost=min_root_cost, device=local_rank)
 
     def frame_host():
         cache.reset()
@@ -1106,6 +1116,36 @@ def profile_primitives():
     return {"profile": "primitives", "points": PRIM_POINTS, "launch_order": rows}
 
 
+TRAIN_FLOPS_PER_STEP = 2 * 128 * (2 * (64 * 64 + 64 * 64 + 64 * 3) + (3 * 64 + 64 * 64))
+
+
+def profile_train(args):
+    """One network trained on 2^16 random (u, v, target) rows for `steps` minibatches of 128
+    in one launch of the tensor-core training kernel (one CTA): per-step time and the
+    useful tensor work per step (forward, backward to the hidden activations, weight
+    gradients)."""
+    import torch
+    from paper_2305_07238_gb300 import build as B
+    from paper_2305_07238_gb300 import pmc as P
+    B.build()
+    rng = np.random.default_rng(0)
+    n = 1 << 16
+    data = torch.tensor(rng.random((n, 5)), dtype=torch.float32, device="cuda")
+    theta = torch.tensor(rng.normal(0, 0.1, 8515), dtype=torch.float32, device="cuda")
+    m1, m2 = torch.zeros(8515, device="cuda"), torch.zeros(8515, device="cuda")
+    steps = max(1, args.steps) * 128
+    P.mlp_train(theta, m1, m2, data, steps, 0, steps, 1e-3)      # warm-up launch
+    torch.cuda.synchronize()
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t0.record()
+    P.mlp_train(theta, m1, m2, data, steps, steps, 2 * steps, 1e-3)
+    t1.record()
+    torch.cuda.synchronize()
+    us = t0.elapsed_time(t1) * 1e3 / steps
+    return {"profile": "surrogate training, one network", "steps": steps, "us_per_step": round(us, 3),
+            "useful_tflops_per_cta": round(TRAIN_FLOPS_PER_STEP / (us * 1e-6) / 1e12, 3)}
+
+
 def profile_run(args):
     """Eager frames only (default schedule, no autotuning, no graph, no other legs), so
     that an ncu launch list can select whole frames: W warm-up frames, then K frames.
@@ -1137,7 +1177,7 @@ def profile_run(args):
     outs = torch.empty((3, n), dtype=torch.float32, device="cuda")
     hits = torch.empty(n, dtype=torch.int16, device="cuda")
     flags = P.PMC_CACHE_OFF if args.profile_uncached else 0
-    cache = P.Cache(mats, N_CELLS, N_ENTRIES, uv_level=LEVEL, flags=flags)
+    cache = P.Cache(mats, N_CELLS, N_ENTRIES, uv_level=LEVEL, flags=flags, min_root_cost=args.profile_min_root_cost)
 
     def frame_():
         cache.reset()
@@ -1158,6 +1198,7 @@ def profile_run(args):
     secs = t0.elapsed_time(t1) / 1e3
     launches = cache.read_timing()["launches"]
     return {"profile": "eager frames" + (" (cache off)" if args.profile_uncached else ""),
+            "min_root_cost": args.profile_min_root_cost,
             "passes_per_frame": n_pass, "value": round(n * n_pass * args.steps / secs, 1), "unit": UNIT,
             "steps": args.steps, "warmup": args.warmup, "launches_per_frame": launches // max(1, args.steps)}
 
@@ -1206,11 +1247,11 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--legs", default="cached,uncached,e2e,surr,f128,alg1,cones,raycast,position,replace,cpu",
-                    help="comma list of cached, uncached, e2e, surr, f128, alg1, cones, raycast, position, replace, "
-                         "sweep, cpu "
-                         "(sweep is not in the "
-                         "default: about a minute more; profiling runs take 'cached')")
+    ap.add_argument("--legs",
+                    default="cached,uncached,e2e,surr,f128,scale,threshold,alg1,cones,raycast,position,replace,cpu",
+                    help="comma list of cached, uncached, e2e, surr, f128, scale, threshold, alg1, cones, raycast, "
+                         "position, replace, sweep, cpu (sweep, the full table-size sweep of the scale "
+                         "configuration, is not in the default: a few minutes more)")
     ap.add_argument("--profile", action="store_true",
                     help="eager frames only, for ncu launch lists (prints launches per frame)")
     ap.add_argument("--profile-surrogate", action="store_true",
@@ -1221,9 +1262,16 @@ def main():
                     help="with --profile: the same frames with the cache off")
     ap.add_argument("--profile-primitives", action="store_true",
                     help="one cache-off pass per single-primitive network (per-node device costs)")
+    ap.add_argument("--profile-min-root-cost", type=int, default=0,
+                    help="with --profile: the cost threshold of cacheable nodes")
+    ap.add_argument("--profile-train", action="store_true",
+                    help="one launch of the surrogate training kernel on one network (steps x 128 minibatches)")
     args = ap.parse_args()
     if args.profile_primitives:
         print(json.dumps(profile_primitives()), flush=True)
+        return 0
+    if args.profile_train:
+        print(json.dumps(profile_train(args)), flush=True)
         return 0
     if args.profile:
         print(json.dumps(profile_run(args)), flush=True)
