@@ -40,9 +40,10 @@ N_MATS, NODES_LO, NODES_HI, SP_FRAC = 64, 20, 200, 0.2
 N_CELLS, N_ENTRIES, LEVEL = 1 << 21, 8, 10
 SAMPLE_ROWS = (0, 40)            # CPU-oracle sample: 40 full-width rows, all 16 passes
 REF_ROWS = (0, 16)               # reference arm: 16 full-width rows per step, all 16 passes
-# ncu capture of k_eval / k_lookup on the same workload (profiles/): DRAM bytes per launch
-# (profiles/launches_frame1080p.md: mean over the launches of one frame of each kernel)
-NCU_TRAFFIC = {"eval": 150.7e6, "eval_roots": 77.6e6, "lookup": 329.4e6}
+# DRAM bytes (read + written) per launch of each kernel, the mean of the two launches one
+# ncu capture of that kernel takes from a four-pass frame of this workload at the bench's
+# cost threshold; None while the kernel has changed since its capture
+NCU_TRAFFIC = {"eval": None, "eval_roots": None, "lookup": 329.4e6}
 
 FP32_LANES_PER_SM = 128          # Blackwell SM: 4 partitions x 32 FP32 lanes
 
@@ -1094,11 +1095,11 @@ def primitive_materials():
     return out
 
 
-def profile_primitives():
-    """One cache-off pass of PRIM_POINTS uniform points per single-primitive network, in the
-    order printed, so that an ncu capture of k_eval gets one launch per (primitive, chain
-    length): the per-node instruction and FP32 operation counts follow from the difference
-    between the 9-copy and 1-copy chains."""
+def profile_primitives(only=""):
+    """One cache-off pass of PRIM_POINTS uniform points per single-primitive network (of
+    `only` alone if given), in the order printed after one warm-up pass, so that an ncu
+    capture of k_eval that skips one launch gets one launch per (primitive, chain length): the per-node instruction and FP32 operation counts
+    follow from the difference between the 9-copy and 1-copy chains."""
     import torch
     from paper_2305_07238_gb300 import build as B
     from paper_2305_07238_gb300 import pmc as P
@@ -1106,7 +1107,11 @@ def profile_primitives():
     pts = P.points_to_device(W.points_uniform(PRIM_POINTS, seed=0))
     rgb = torch.empty((3, PRIM_POINTS), dtype=torch.float32, device="cuda")
     rows = []
-    for name, L, mat in primitive_materials():
+    chains = [(name, L, mat) for name, L, mat in primitive_materials() if not only or name == only]
+    w = P.Cache([chains[0][2]], 1, 1, flags=P.PMC_CACHE_OFF)     # one warm-up launch (ncu -s 1)
+    w.eval_batch(pts, rgb)
+    w.close()
+    for name, L, mat in chains:
         c = P.Cache([mat], 1, 1, flags=P.PMC_CACHE_OFF)
         c.eval_batch(pts, rgb)
         st = c.stats()
@@ -1262,13 +1267,15 @@ def main():
                     help="with --profile: the same frames with the cache off")
     ap.add_argument("--profile-primitives", action="store_true",
                     help="one cache-off pass per single-primitive network (per-node device costs)")
+    ap.add_argument("--primitive", default="",
+                    help="with --profile-primitives: only this primitive's two chains (two launches)")
     ap.add_argument("--profile-min-root-cost", type=int, default=0,
                     help="with --profile: the cost threshold of cacheable nodes")
     ap.add_argument("--profile-train", action="store_true",
                     help="one launch of the surrogate training kernel on one network (steps x 128 minibatches)")
     args = ap.parse_args()
     if args.profile_primitives:
-        print(json.dumps(profile_primitives()), flush=True)
+        print(json.dumps(profile_primitives(args.primitive)), flush=True)
         return 0
     if args.profile_train:
         print(json.dumps(profile_train(args)), flush=True)

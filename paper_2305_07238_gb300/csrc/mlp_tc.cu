@@ -26,20 +26,26 @@ namespace {
 
 constexpr int P_W1 = 0, P_B1 = 4096, P_W2 = 4160, P_B2 = 8256, P_W3 = 8320, P_B3 = 8512;
 constexpr uint32_t TC_ROWS = 128;
-constexpr uint32_t TC_COLS = 128;               // tensor-memory columns: D1 at 0, D2 at 64, D3 at 0
+constexpr uint32_t TC_COLS = 64;                // tensor-memory columns: D1, D2 and D3 all at column 0
+constexpr uint32_t TC_CTAS_PER_SM = 6;          // resident inference CTAs (shared memory and TMEM allow 6)
 constexpr uint32_t WAIT_POLLS = 1u << 22;       // bound of every mbarrier wait
 
+// One activation operand serves the three layers: a layer's epilogue overwrites it only after
+// the product that read it has completed (the mbarrier wait), and likewise one 64-column
+// accumulator, read out completely before the next product is issued.  35 KB of shared
+// memory and 64 TMEM columns per CTA let six CTAs share an SM.
 struct Sm {                                     // byte offsets into dynamic shared memory
-    static constexpr uint32_t a0 = 0;           // 128 x 64 BF16: features, then layer-2 output
-    static constexpr uint32_t a1 = 16384;       // 128 x 64 BF16: layer-1 output
-    static constexpr uint32_t w1 = 32768;       // 64 x 64 BF16: W1 transposed (n rows, k columns)
-    static constexpr uint32_t w2 = 40960;       // 64 x 64 BF16: W2 transposed
-    static constexpr uint32_t w3 = 49152;       // 16 x 64 BF16: W3 transposed, rows 3..15 zero
-    static constexpr uint32_t bias = 51200;     // b1[64], b2[64], b3[4] FP32
-    static constexpr uint32_t mbar = 51744;     // 8-byte mbarrier
-    static constexpr uint32_t tmem = 51752;     // tensor-memory base written by tcgen05.alloc
-    static constexpr uint32_t end = 51760;
+    static constexpr uint32_t a0 = 0;           // 128 x 64 BF16: features, then layer-1, then layer-2 output
+    static constexpr uint32_t w1 = 16384;       // 64 x 64 BF16: W1 transposed (n rows, k columns)
+    static constexpr uint32_t w2 = 24576;       // 64 x 64 BF16: W2 transposed
+    static constexpr uint32_t w3 = 32768;       // 16 x 64 BF16: W3 transposed, rows 3..15 zero
+    static constexpr uint32_t bias = 34816;     // b1[64], b2[64], b3[4] FP32
+    static constexpr uint32_t mbar = 35344;     // 8-byte mbarrier
+    static constexpr uint32_t tmem = 35352;     // tensor-memory base written by tcgen05.alloc
+    static constexpr uint32_t end = 35360;
 };
+static_assert(TC_CTAS_PER_SM * (Sm::end + 1024) <= 228 * 1024, "inference CTAs per SM by shared memory");
+static_assert(TC_CTAS_PER_SM * TC_COLS <= 512, "inference CTAs per SM by tensor memory");
 
 // Byte offset of element (r, c) of a 64-column operand in the core-matrix layout.
 __device__ __forceinline__ uint32_t cm_off(uint32_t r, uint32_t c) {
@@ -133,11 +139,23 @@ __device__ __forceinline__ uint32_t pack2(float lo, float hi) {
 
 // FP32 parameters -> BF16 transposed operands and FP32 biases in shared memory (all 128
 // threads); the async-proxy fence is issued by the caller before the next MMA.
+// The loads of W1 and W2 are issued eight per matrix at a time, so that a thread has 16 in
+// flight instead of one (the parameters are FP32 and 4-byte aligned only).
 __device__ void tc_load_weights(unsigned char* sm, const float* __restrict__ th) {
-    for (uint32_t i = threadIdx.x; i < 64u * 64u; i += blockDim.x) {
-        const uint32_t in = i >> 6, out = i & 63u;
-        *reinterpret_cast<__nv_bfloat16*>(sm + Sm::w1 + cm_off(out, in)) = __float2bfloat16_rn(th[P_W1 + i]);
-        *reinterpret_cast<__nv_bfloat16*>(sm + Sm::w2 + cm_off(out, in)) = __float2bfloat16_rn(th[P_W2 + i]);
+    static_assert(64u * 64u % (TC_ROWS * 8u) == 0, "W1/W2 batches");
+    for (uint32_t i0 = threadIdx.x; i0 < 64u * 64u; i0 += 8u * TC_ROWS) {
+        float w1[8], w2[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            w1[k] = __ldg(th + P_W1 + i0 + k * TC_ROWS);
+            w2[k] = __ldg(th + P_W2 + i0 + k * TC_ROWS);
+        }
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            const uint32_t i = i0 + k * TC_ROWS, in = i >> 6, out = i & 63u;
+            *reinterpret_cast<__nv_bfloat16*>(sm + Sm::w1 + cm_off(out, in)) = __float2bfloat16_rn(w1[k]);
+            *reinterpret_cast<__nv_bfloat16*>(sm + Sm::w2 + cm_off(out, in)) = __float2bfloat16_rn(w2[k]);
+        }
     }
     for (uint32_t i = threadIdx.x; i < 16u * 64u; i += blockDim.x) {
         const uint32_t out = i >> 6, in = i & 63u;
@@ -222,10 +240,8 @@ __device__ bool tc_forward(unsigned char* sm, uint32_t tmem, uint32_t t, float u
     const uint32_t lane_addr = tmem + (((t >> 5) * 32u) << 16);
     const float* bias = reinterpret_cast<const float*>(sm + Sm::bias);
     tc_features(sm, t, u, v);
-    const uint32_t a0 = base + Sm::a0, a1 = base + Sm::a1;
-    const uint32_t srcA[3] = {a0, a1, a0};
+    const uint32_t a0 = base + Sm::a0;
     const uint32_t srcB[3] = {base + Sm::w1, base + Sm::w2, base + Sm::w3};
-    const uint32_t dcol[3] = {0u, 64u, 0u};
     const uint32_t ids[3] = {idesc(128, 64), idesc(128, 64), idesc(128, 16)};
 #pragma unroll
     for (int layer = 0; layer < 3; ++layer) {
@@ -235,15 +251,15 @@ __device__ bool tc_forward(unsigned char* sm, uint32_t tmem, uint32_t t, float u
         __syncthreads();
         if (t == 0) {
             fence_after();
-            tc_layer(tmem + dcol[layer], srcA[layer], srcB[layer], ids[layer]);
+            tc_layer(tmem, a0, srcB[layer], ids[layer]);
             mma_commit(mbar);
         }
         const bool done = mbar_wait(mbar, *phase);
         *phase ^= 1u;
         if (__syncthreads_or(!done)) return false;
         fence_after();
-        if (layer == 0) tc_hidden(sm, Sm::a1, lane_addr + 0u, bias, t);
-        else if (layer == 1) tc_hidden(sm, Sm::a0, lane_addr + 64u, bias + 64, t);
+        if (layer == 0) tc_hidden(sm, Sm::a0, lane_addr, bias, t);
+        else if (layer == 1) tc_hidden(sm, Sm::a0, lane_addr, bias + 64, t);
         else {
             float o[4];
             tmem_ld4(lane_addr + 0u, o);
@@ -750,15 +766,16 @@ cudaError_t launch_mlp_train(float* theta, float* adam_m, float* adam_v, float* 
 cudaError_t launch_surrogate(const BatchArgs& a, int num_sms, cudaStream_t s) {
     cudaError_t e = cudaFuncSetAttribute(k_surrogate_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Sm::end);
     if (e != cudaSuccess) return e;
-    // four CTAs per SM: their tensor-memory allocations (4 x 128 columns) fit the SM's 512
-    k_surrogate_tc<<<num_sms * 4, TC_ROWS, Sm::end, s>>>(a);
+    // six CTAs per SM: their tensor-memory allocations (6 x 64 columns) fit the SM's 512
+    k_surrogate_tc<<<num_sms * TC_CTAS_PER_SM, TC_ROWS, Sm::end, s>>>(a);
     return cudaGetLastError();
 }
 
 cudaError_t launch_mlp_forward_tc(const float* theta, const float* u, const float* v, uint32_t n, float* out, int clamp,
                                   uint32_t* err, int num_sms, cudaStream_t s) {
     const uint32_t tiles = (n + TC_ROWS - 1) / TC_ROWS;
-    uint32_t blocks = tiles < (uint32_t)num_sms * 4u ? tiles : (uint32_t)num_sms * 4u;
+    const uint32_t full = (uint32_t)num_sms * TC_CTAS_PER_SM;
+    uint32_t blocks = tiles < full ? tiles : full;
     if (blocks == 0) return cudaSuccess;
     cudaError_t e = cudaFuncSetAttribute(k_mlp_forward_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Sm::end);
     if (e != cudaSuccess) return e;

@@ -149,13 +149,40 @@ __device__ __forceinline__ float d_perlin(float x, float y, uint32_t seed, const
     const float2 g10 = grad[d_fmix32(ax1 ^ by ^ sz) & 7u];
     const float2 g01 = grad[d_fmix32(ax ^ by1 ^ sz) & 7u];
     const float2 g11 = grad[d_fmix32(ax1 ^ by1 ^ sz) & 7u];
-    // corner dot products, paired as (d00, d01) and (d10, d11)
-    const float2 dA = fma2(f2(g00.x, g01.x), f2(fr.x, fr.x), mul2(f2(g00.y, g01.y), f2(fr.y, fr1.y)));
-    const float2 dB = fma2(f2(g10.x, g11.x), f2(fr1.x, fr1.x), mul2(f2(g10.y, g11.y), f2(fr.y, fr1.y)));
+    // corner dot products g . (p - corner), each as fmaf(gx, dx, gy dy); scalar, since the
+    // corners' gradients arrive in separate registers
+    const float2 dA = f2(fmaf(g00.x, fr.x, g00.y * fr.y), fmaf(g01.x, fr.x, g01.y * fr1.y));    // (d00, d01)
+    const float2 dB = f2(fmaf(g10.x, fr1.x, g10.y * fr.y), fmaf(g11.x, fr1.x, g11.y * fr1.y));  // (d10, d11)
     const float2 s = d_fade2(fr);
     // (a, b) = dA + s.x (dB - dA); result = a + s.y (b - a)
     const float2 ab = fma2(f2(s.x, s.x), fma2(dA, f2(-1.0f, -1.0f), dB), dA);
     return fmaf(s.y, ab.y - ab.x, ab.x);
+}
+
+// The same noise at two points A and B, every FP32 quantity held as an (A, B) pair so that
+// each packed instruction serves both points; the result is (noise(A), noise(B)) with the
+// roundings of d_perlin.
+__device__ __forceinline__ float2 d_perlin2(float2 X, float2 Y, uint32_t seed, const float2* grad) {
+    const float2 fX = f2(floorf(X.x), floorf(X.y)), fY = f2(floorf(Y.x), floorf(Y.y));
+    const float2 rX = fma2(fX, f2(-1.0f, -1.0f), X), rY = fma2(fY, f2(-1.0f, -1.0f), Y);   // fx, fy
+    const float2 rX1 = add2(rX, f2(-1.0f, -1.0f)), rY1 = add2(rY, f2(-1.0f, -1.0f));       // fx - 1, fy - 1
+    const uint32_t sz = seed * 83492791u;
+    const uint32_t axA = (uint32_t)(int)fX.x * 73856093u, byA = (uint32_t)(int)fY.x * 19349663u;
+    const uint32_t axB = (uint32_t)(int)fX.y * 73856093u, byB = (uint32_t)(int)fY.y * 19349663u;
+    const uint32_t axA1 = axA + 73856093u, byA1 = byA + 19349663u;
+    const uint32_t axB1 = axB + 73856093u, byB1 = byB + 19349663u;
+    const float2 a00 = grad[d_fmix32(axA ^ byA ^ sz) & 7u], b00 = grad[d_fmix32(axB ^ byB ^ sz) & 7u];
+    const float2 a10 = grad[d_fmix32(axA1 ^ byA ^ sz) & 7u], b10 = grad[d_fmix32(axB1 ^ byB ^ sz) & 7u];
+    const float2 a01 = grad[d_fmix32(axA ^ byA1 ^ sz) & 7u], b01 = grad[d_fmix32(axB ^ byB1 ^ sz) & 7u];
+    const float2 a11 = grad[d_fmix32(axA1 ^ byA1 ^ sz) & 7u], b11 = grad[d_fmix32(axB1 ^ byB1 ^ sz) & 7u];
+    const float2 d00 = f2(fmaf(a00.x, rX.x, a00.y * rY.x), fmaf(b00.x, rX.y, b00.y * rY.y));
+    const float2 d10 = f2(fmaf(a10.x, rX1.x, a10.y * rY.x), fmaf(b10.x, rX1.y, b10.y * rY.y));
+    const float2 d01 = f2(fmaf(a01.x, rX.x, a01.y * rY1.x), fmaf(b01.x, rX.y, b01.y * rY1.y));
+    const float2 d11 = f2(fmaf(a11.x, rX1.x, a11.y * rY1.x), fmaf(b11.x, rX1.y, b11.y * rY1.y));
+    const float2 sX = d_fade2(rX), sY = d_fade2(rY);
+    const float2 a = fma2(sX, fma2(d00, f2(-1.0f, -1.0f), d10), d00);
+    const float2 b = fma2(sX, fma2(d01, f2(-1.0f, -1.0f), d11), d01);
+    return fma2(sY, fma2(a, f2(-1.0f, -1.0f), b), a);
 }
 
 // clamp to [0, 1] (NaN to 0) as a saturating modifier of the producing instruction
@@ -175,6 +202,24 @@ __device__ __forceinline__ float d_fbm(float x, float y, const float4 q, const f
         freq = af.y;
     }
     return d_clamp01(fmaf(sum, inv_norm, 0.5f));
+}
+
+// d_fbm at two points in one octave loop (the amplitude and frequency updates are shared)
+__device__ __forceinline__ float2 d_fbm2(float2 X, float2 Y, const float4 q, const float4 t, const float2* grad) {
+    const float scale = q.x, lac = q.y, gain = q.z, inv_norm = q.w;
+    const int oct = __float_as_int(t.x);
+    const uint32_t seed = (uint32_t)__float_as_int(t.y);
+    float2 sum = f2(0.0f, 0.0f);
+    float amp = 1.0f, freq = scale;
+    for (int k = 0; k < oct; ++k) {
+        const float2 n = d_perlin2(mul2(X, f2(freq, freq)), mul2(Y, f2(freq, freq)), seed + (uint32_t)k, grad);
+        sum = fma2(f2(amp, amp), n, sum);
+        const float2 af = mul2(f2(amp, freq), f2(gain, lac));
+        amp = af.x;
+        freq = af.y;
+    }
+    const float2 r = fma2(sum, f2(inv_norm, inv_norm), f2(0.5f, 0.5f));
+    return f2(d_clamp01(r.x), d_clamp01(r.y));
 }
 
 // The two 16-bit halves of a hash h as m = 1 + h16 2^-16, exactly: an FP32 number whose
@@ -208,7 +253,9 @@ __device__ __forceinline__ float d_voronoi(float x, float y, float scale, uint32
             best = fminf(best, fmaf(d.x, d.x, d.y * d.y));
         }
     }
-    return d_clamp01(sqrtf(best));
+    // sqrt(best) as best / sqrt(best) through the reciprocal square root (within a few ulp);
+    // best = 0 gives 0 x inf = NaN, which the clamp maps to 0 = sqrt(0)
+    return d_clamp01(best * rsqrtf(best));
 }
 
 // Parity of an integer-valued FP32 number f as 0 or 1: f - 2 floor(f / 2), exact for every
@@ -367,38 +414,37 @@ __device__ __forceinline__ void exec_node2(uint32_t op, const uint4& ins, char* 
     const uint32_t i0 = ins.y >> 16, i1 = ins.z & 0xFFFFu, i2 = ins.z >> 16;
     const float* p = params + ins.w;
     const float4* p4 = reinterpret_cast<const float4*>(p);
-    float2 r0 = f2(0.f, 0.f), r1 = f2(0.f, 0.f), r2 = f2(0.f, 0.f);
+    // every case stores its own result: no values merge after the switch
     switch (op) {
-    case PMC_OP_UV: r0 = f2(A.u, B.u); r1 = f2(A.v, B.v); break;
-    case PMC_OP_POSITION: r0 = f2(A.px, B.px); r1 = f2(A.py, B.py); r2 = f2(A.pz, B.pz); break;
-    case PMC_OP_NORMAL: r0 = f2(A.nx, B.nx); r1 = f2(A.ny, B.ny); r2 = f2(A.nz, B.nz); break;
+    case PMC_OP_UV: slot2_store(Vb, out, f2(A.u, B.u), f2(A.v, B.v), f2(0.f, 0.f)); break;
+    case PMC_OP_POSITION: slot2_store(Vb, out, f2(A.px, B.px), f2(A.py, B.py), f2(A.pz, B.pz)); break;
+    case PMC_OP_NORMAL: slot2_store(Vb, out, f2(A.nx, B.nx), f2(A.ny, B.ny), f2(A.nz, B.nz)); break;
     case PMC_OP_CONST: {
         const float4 q = __ldg(p4);
-        r0 = f2(q.x, q.x); r1 = f2(q.y, q.y); r2 = f2(q.z, q.z);
+        slot2_store(Vb, out, f2(q.x, q.x), f2(q.y, q.y), f2(q.z, q.z));
         break;
     }
     case PMC_OP_UV_AFFINE: {
         const float4 q = __ldg(p4);
         const float4 t = __ldg(p4 + 1);
         const float2 x = slot2(Vb, i0, 0), y = slot2(Vb, i0, 1);
-        r0 = fma2(f2(q.x, q.x), x, fma2(f2(q.y, q.y), y, f2(t.x, t.x)));
-        r1 = fma2(f2(q.z, q.z), x, fma2(f2(q.w, q.w), y, f2(t.y, t.y)));
+        slot2_store(Vb, out, fma2(f2(q.x, q.x), x, fma2(f2(q.y, q.y), y, f2(t.x, t.x))),
+                    fma2(f2(q.z, q.z), x, fma2(f2(q.w, q.w), y, f2(t.y, t.y))), f2(0.f, 0.f));
         break;
     }
     case PMC_OP_FBM: {
         const float4 q = __ldg(p4);
         const float4 t = __ldg(p4 + 1);
-        const float2 x = slot2(Vb, i0, 0), y = slot2(Vb, i0, 1);
-        r0 = f2(d_fbm(x.x, y.x, q, t, grad), d_fbm(x.y, y.y, q, t, grad));
-        r1 = r2 = r0;
+        const float2 r = d_fbm2(slot2(Vb, i0, 0), slot2(Vb, i0, 1), q, t, grad);
+        slot2_store(Vb, out, r, r, r);
         break;
     }
     case PMC_OP_VORONOI: {
         const float4 q = __ldg(p4);
         const float2 x = slot2(Vb, i0, 0), y = slot2(Vb, i0, 1);
         const uint32_t seed = (uint32_t)__float_as_int(q.y);
-        r0 = f2(d_voronoi(x.x, y.x, q.x, seed), d_voronoi(x.y, y.y, q.x, seed));
-        r1 = r2 = r0;
+        const float2 r = f2(d_voronoi(x.x, y.x, q.x, seed), d_voronoi(x.y, y.y, q.x, seed));
+        slot2_store(Vb, out, r, r, r);
         break;
     }
     case PMC_OP_CHECKER: {
@@ -407,9 +453,8 @@ __device__ __forceinline__ void exec_node2(uint32_t op, const uint4& ins, char* 
         const float2 fx = mul2(slot2(Vb, i0, 0), f2(q.x, q.x)), fy = mul2(slot2(Vb, i0, 1), f2(q.x, q.x));
         const bool oa = d_parity(floorf(fx.x)) != d_parity(floorf(fy.x));
         const bool ob = d_parity(floorf(fx.y)) != d_parity(floorf(fy.y));
-        r0 = sat2(f2(oa ? t.x : q.y, ob ? t.x : q.y));
-        r1 = sat2(f2(oa ? t.y : q.z, ob ? t.y : q.z));
-        r2 = sat2(f2(oa ? t.z : q.w, ob ? t.z : q.w));
+        slot2_store(Vb, out, sat2(f2(oa ? t.x : q.y, ob ? t.x : q.y)), sat2(f2(oa ? t.y : q.z, ob ? t.y : q.z)),
+                    sat2(f2(oa ? t.z : q.w, ob ? t.z : q.w)));
         break;
     }
     case PMC_OP_RAMP: {
@@ -436,50 +481,46 @@ __device__ __forceinline__ void exec_node2(uint32_t op, const uint4& ins, char* 
                 o[s][0] = cl.x; o[s][1] = cl.y; o[s][2] = cl.z;
             }
         }
-        r0 = sat2(f2(o[0][0], o[1][0]));
-        r1 = sat2(f2(o[0][1], o[1][1]));
-        r2 = sat2(f2(o[0][2], o[1][2]));
+        slot2_store(Vb, out, sat2(f2(o[0][0], o[1][0])), sat2(f2(o[0][1], o[1][1])), sat2(f2(o[0][2], o[1][2])));
         break;
     }
     case PMC_OP_MIX: {
         const float2 f = sat2(((ins.x >> 8) & FLAG_IN2) ? slot2(Vb, i2, 0) : f2(__ldg(&p[0]), __ldg(&p[0])));
         const float2 a0 = slot2(Vb, i0, 0), a1 = slot2(Vb, i0, 1), a2 = slot2(Vb, i0, 2);
         // a + f (b - a), each product and sum rounded as fmaf(f, b - a, a) rounds them
-        r0 = sat2(fma2(f, fma2(a0, f2(-1.0f, -1.0f), slot2(Vb, i1, 0)), a0));
-        r1 = sat2(fma2(f, fma2(a1, f2(-1.0f, -1.0f), slot2(Vb, i1, 1)), a1));
-        r2 = sat2(fma2(f, fma2(a2, f2(-1.0f, -1.0f), slot2(Vb, i1, 2)), a2));
+        slot2_store(Vb, out, sat2(fma2(f, fma2(a0, f2(-1.0f, -1.0f), slot2(Vb, i1, 0)), a0)),
+                    sat2(fma2(f, fma2(a1, f2(-1.0f, -1.0f), slot2(Vb, i1, 1)), a1)),
+                    sat2(fma2(f, fma2(a2, f2(-1.0f, -1.0f), slot2(Vb, i1, 2)), a2)));
         break;
     }
     case PMC_OP_ADD:
-        r0 = sat2(add2(slot2(Vb, i0, 0), slot2(Vb, i1, 0)));
-        r1 = sat2(add2(slot2(Vb, i0, 1), slot2(Vb, i1, 1)));
-        r2 = sat2(add2(slot2(Vb, i0, 2), slot2(Vb, i1, 2)));
+        slot2_store(Vb, out, sat2(add2(slot2(Vb, i0, 0), slot2(Vb, i1, 0))), sat2(add2(slot2(Vb, i0, 1), slot2(Vb, i1, 1))),
+                    sat2(add2(slot2(Vb, i0, 2), slot2(Vb, i1, 2))));
         break;
     case PMC_OP_MUL:
-        r0 = sat2(mul2(slot2(Vb, i0, 0), slot2(Vb, i1, 0)));
-        r1 = sat2(mul2(slot2(Vb, i0, 1), slot2(Vb, i1, 1)));
-        r2 = sat2(mul2(slot2(Vb, i0, 2), slot2(Vb, i1, 2)));
+        slot2_store(Vb, out, sat2(mul2(slot2(Vb, i0, 0), slot2(Vb, i1, 0))), sat2(mul2(slot2(Vb, i0, 1), slot2(Vb, i1, 1))),
+                    sat2(mul2(slot2(Vb, i0, 2), slot2(Vb, i1, 2))));
         break;
     case PMC_OP_POW: {
         const float e = __ldg(&p[0]);
         const float2 x0 = slot2(Vb, i0, 0), x1 = slot2(Vb, i0, 1), x2 = slot2(Vb, i0, 2);
-        r0 = sat2(f2(__powf(fmaxf(x0.x, 0.0f), e), __powf(fmaxf(x0.y, 0.0f), e)));
-        r1 = sat2(f2(__powf(fmaxf(x1.x, 0.0f), e), __powf(fmaxf(x1.y, 0.0f), e)));
-        r2 = sat2(f2(__powf(fmaxf(x2.x, 0.0f), e), __powf(fmaxf(x2.y, 0.0f), e)));
+        slot2_store(Vb, out, sat2(f2(__powf(fmaxf(x0.x, 0.0f), e), __powf(fmaxf(x0.y, 0.0f), e))),
+                    sat2(f2(__powf(fmaxf(x1.x, 0.0f), e), __powf(fmaxf(x1.y, 0.0f), e))),
+                    sat2(f2(__powf(fmaxf(x2.x, 0.0f), e), __powf(fmaxf(x2.y, 0.0f), e))));
         break;
     }
     case PMC_OP_FACING: {
         const float4 q = __ldg(p4);
         const float2 d = fma2(slot2(Vb, i0, 0), f2(q.x, q.x),
                               fma2(slot2(Vb, i0, 1), f2(q.y, q.y), mul2(slot2(Vb, i0, 2), f2(q.z, q.z))));
-        r0 = sat2(f2(fabsf(d.x), fabsf(d.y)));
-        r1 = r2 = r0;
+        const float2 r = sat2(f2(fabsf(d.x), fabsf(d.y)));
+        slot2_store(Vb, out, r, r, r);
         break;
     }
     default:
+        slot2_store(Vb, out, f2(0.f, 0.f), f2(0.f, 0.f), f2(0.f, 0.f));
         break;
     }
-    slot2_store(Vb, out, r0, r1, r2);
 }
 
 }  // namespace pmc
