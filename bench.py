@@ -796,7 +796,7 @@ def sweep_leg(torch, P, dev, local_rank, seed=0, full=True, min_root_cost=0):
     """The scale configuration: 4096 networks of 10-2000 nodes (40 % SP), materials
     Zipf(0.9) per 8x8 tile of a 2048x2048 stream, 2^28 points in 64 batches of 2^22.  With
     `full`, the table swept from 2^20 to 2^29 slots (16 MB - 8 GB); else 2^26 slots (1 GB)
-    under the rule of Sec. 3 and under the cost threshold `min_root_cost`.  Per run: points/s
+    under the rule of Sec. 3 and under cost thresholds 300, 450, `min_root_cost` and 800.  Per run: points/s
     of the whole stream replayed as one CUDA graph, hit rate, inserted and dropped counts.
     Then the surrogate mix at 2^26 slots (with the cost threshold): networks trained for
     every material's candidate node, those validated within 1.6e-3 enabled."""
@@ -834,7 +834,8 @@ def sweep_leg(torch, P, dev, local_rank, seed=0, full=True, min_root_cost=0):
     res["uncached"] = round(rate(u), 1)
     u.close()
     rows = []
-    runs = [(ls, 0) for ls in range(20, 30)] if full else [(26, 0), (26, min_root_cost)]
+    thresholds = sorted({0, 300, 450, min_root_cost, 800})
+    runs = [(ls, 0) for ls in range(20, 30)] if full else [(26, thr) for thr in thresholds]
     for log_slots, thr in runs:
         c = P.Cache(mats, 1 << (log_slots - 3), N_ENTRIES, uv_level=LEVEL, device=local_rank, probe_capacity=need,
                     min_root_cost=thr)

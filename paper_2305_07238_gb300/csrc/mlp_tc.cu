@@ -167,46 +167,59 @@ __device__ void tc_load_weights(unsigned char* sm, const float* __restrict__ th)
         bias[i] = i < 64 ? th[P_B1 + i] : (i < 128 ? th[P_B2 + i - 64] : (i < 131 ? th[P_B3 + i - 128] : 0.0f));
 }
 
-// sin and cos of pi k x for k = 1..16: sincospif at the anchor frequencies k = 1, 5, 9, 13,
-// and from each anchor three steps of the angle-addition formulas
-//   sin(a + b) = sin a cos b + cos a sin b,  cos(a + b) = cos a cos b - sin a sin b
-// with b = pi x.  A step adds about an ulp of error, so every feature is within a few ulps of
-// sincospif's, far below the BF16 rounding the features then take.
-__device__ __forceinline__ void tc_sincos16(float x, float (&s)[16], float (&c)[16]) {
-    float s1, c1;
-    sincospif(x, &s1, &c1);
-#pragma unroll
-    for (int a = 0; a < 16; a += 4) {
-        if (a == 0) {
-            s[0] = s1;
-            c[0] = c1;
-        } else {
-            sincospif((float)(a + 1) * x, &s[a], &c[a]);
-        }
-#pragma unroll
-        for (int j = 1; j < 4; ++j) {
-            s[a + j] = fmaf(s[a + j - 1], c1, c[a + j - 1] * s1);
-            c[a + j] = fmaf(c[a + j - 1], c1, -(s[a + j - 1] * s1));
-        }
-    }
+// BF16 pair {relu(lo), relu(hi)} (lo in the low half) in one conversion: each value is
+// clamped below at 0, then rounded to nearest even, as pack2(fmaxf(lo, 0), fmaxf(hi, 0)).
+__device__ __forceinline__ uint32_t pack2_relu(float lo, float hi) {
+    uint32_t r;
+    asm("cvt.rn.relu.bf16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(hi), "f"(lo));
+    return r;
 }
 
 // Row t of the feature matrix: [sin pi k u, cos pi k u, sin pi k v, cos pi k v], k = 1..16.
+// sincospif gives the anchors k = 1 and k = 9 of both coordinates; from each anchor, seven
+// steps of the angle-addition formulas
+//   sin(a + b) = sin a cos b + cos a sin b,  cos(a + b) = cos a cos b - sin a sin b
+// with b = pi x give the next seven frequencies.  Every quantity is a (u, v) pair, so one
+// packed instruction steps both coordinates.  A step adds about an ulp of error, so every
+// feature is within a few ulps of sincospif's, far below the BF16 rounding the features
+// then take.  The features are packed to BF16 as soon as two neighbours exist.
 __device__ __forceinline__ void tc_features(unsigned char* sm, uint32_t t, float u, float v) {
+    float s1u, c1u, s1v, c1v;
+    sincospif(u, &s1u, &c1u);
+    sincospif(v, &s1v, &c1v);
+    const float2 S1 = f2(s1u, s1v), C1 = f2(c1u, c1v), nS1 = f2(-s1u, -s1v);
 #pragma unroll
     for (int half = 0; half < 2; ++half) {
-        const float x = half ? v : u;
-        float s[16], c[16];
-        tc_sincos16(x, s, c);
-#pragma unroll
-        for (int q = 0; q < 2; ++q) {
-            const uint4 ws = make_uint4(pack2(s[8 * q], s[8 * q + 1]), pack2(s[8 * q + 2], s[8 * q + 3]),
-                                        pack2(s[8 * q + 4], s[8 * q + 5]), pack2(s[8 * q + 6], s[8 * q + 7]));
-            const uint4 wc = make_uint4(pack2(c[8 * q], c[8 * q + 1]), pack2(c[8 * q + 2], c[8 * q + 3]),
-                                        pack2(c[8 * q + 4], c[8 * q + 5]), pack2(c[8 * q + 6], c[8 * q + 7]));
-            *reinterpret_cast<uint4*>(sm + Sm::a0 + cm_off(t, 32 * half + 8 * q)) = ws;
-            *reinterpret_cast<uint4*>(sm + Sm::a0 + cm_off(t, 32 * half + 16 + 8 * q)) = wc;
+        float2 sk, ck;
+        if (half == 0) {
+            sk = S1;
+            ck = C1;
+        } else {
+            float su, cu, sv, cv;
+            sincospif(9.0f * u, &su, &cu);
+            sincospif(9.0f * v, &sv, &cv);
+            sk = f2(su, sv);
+            ck = f2(cu, cv);
         }
+        uint32_t wsu[4], wcu[4], wsv[4], wcv[4];
+#pragma unroll
+        for (int j = 0; j < 8; j += 2) {
+            const float2 sn = fma2(sk, C1, mul2(ck, S1));
+            const float2 cn = fma2(ck, C1, mul2(sk, nS1));
+            wsu[j / 2] = pack2(sk.x, sn.x);
+            wcu[j / 2] = pack2(ck.x, cn.x);
+            wsv[j / 2] = pack2(sk.y, sn.y);
+            wcv[j / 2] = pack2(ck.y, cn.y);
+            if (j < 6) {
+                sk = fma2(sn, C1, mul2(cn, S1));
+                ck = fma2(cn, C1, mul2(sn, nS1));
+            }
+        }
+        const uint32_t k0 = 8u * half;   // first frequency of this anchor, minus one
+        *reinterpret_cast<uint4*>(sm + Sm::a0 + cm_off(t, k0)) = make_uint4(wsu[0], wsu[1], wsu[2], wsu[3]);
+        *reinterpret_cast<uint4*>(sm + Sm::a0 + cm_off(t, 16 + k0)) = make_uint4(wcu[0], wcu[1], wcu[2], wcu[3]);
+        *reinterpret_cast<uint4*>(sm + Sm::a0 + cm_off(t, 32 + k0)) = make_uint4(wsv[0], wsv[1], wsv[2], wsv[3]);
+        *reinterpret_cast<uint4*>(sm + Sm::a0 + cm_off(t, 48 + k0)) = make_uint4(wcv[0], wcv[1], wcv[2], wcv[3]);
     }
 }
 
@@ -219,8 +232,13 @@ __device__ __forceinline__ void tc_hidden(unsigned char* sm, uint32_t dst, uint3
         tmem_ld16(taddr + 16u * q, v);
         uint32_t p[8];
 #pragma unroll
-        for (int k = 0; k < 8; ++k)
-            p[k] = pack2(fmaxf(v[2 * k] + bias[16 * q + 2 * k], 0.0f), fmaxf(v[2 * k + 1] + bias[16 * q + 2 * k + 1], 0.0f));
+        for (int k = 0; k < 8; k += 2) {
+            const float4 b = *reinterpret_cast<const float4*>(bias + 16 * q + 2 * k);
+            const float2 x0 = add2(f2(v[2 * k], v[2 * k + 1]), f2(b.x, b.y));
+            const float2 x1 = add2(f2(v[2 * k + 2], v[2 * k + 3]), f2(b.z, b.w));
+            p[k] = pack2_relu(x0.x, x0.y);
+            p[k + 1] = pack2_relu(x1.x, x1.y);
+        }
         *reinterpret_cast<uint4*>(sm + dst + cm_off(t, 16 * q)) = make_uint4(p[0], p[1], p[2], p[3]);
         *reinterpret_cast<uint4*>(sm + dst + cm_off(t, 16 * q + 8)) = make_uint4(p[4], p[5], p[6], p[7]);
     }
@@ -341,27 +359,36 @@ __global__ void __launch_bounds__(TC_ROWS) k_surrogate_tc(BatchArgs a) {
     uint32_t loaded = 0xFFFFFFFFu, phase = 0;
     unsigned long long n_eval = 0;
     bool ok = true;
+    // an item's material is the largest m with surr_item_base[m] <= item; the CTA's items are
+    // consecutive, so the bisection runs only when an item passes the current material's end
+    uint32_t m = 0, next_base = 0, ibase = 0, cnt = 0, s0 = 0;
+    size_t rbase = 0;   // the first probe record of the node's column in material m
     for (uint32_t item = blockIdx.x * per; item < i_end && ok; ++item) {
-        uint32_t lo = 0, hi = a.n_mats;   // largest m with surr_item_base[m] <= item
-        while (hi - lo > 1) {
-            const uint32_t mid = (lo + hi) >> 1;
-            if (a.surr_item_base[mid] <= item) lo = mid;
-            else hi = mid;
+        if (item >= next_base) {
+            uint32_t lo = 0, hi = a.n_mats;
+            while (hi - lo > 1) {
+                const uint32_t mid = (lo + hi) >> 1;
+                if (a.surr_item_base[mid] <= item) lo = mid;
+                else hi = mid;
+            }
+            m = lo;
+            ibase = a.surr_item_base[m];
+            next_base = a.surr_item_base[m + 1];
+            cnt = a.counts[m];
+            s0 = a.seg_start[m];
+            rbase = (size_t)a.probe_base[m] + (size_t)(uint32_t)a.surr_ord[m] * cnt;
         }
-        const uint32_t m = lo;
         if (m != loaded) {
             __syncthreads();   // the previous network's tile is finished everywhere
             tc_load_weights(sm, a.surr_theta + (size_t)a.surr_slot[m] * MLP_PARAMS);
             loaded = m;
         }
-        const uint32_t cnt = a.counts[m], r = (uint32_t)a.surr_ord[m];
-        const uint32_t j = (item - a.surr_item_base[m]) * TC_ROWS + t;
-        const uint32_t s0 = a.seg_start[m];
+        const uint32_t j = (item - ibase) * TC_ROWS + t;
         const float uu = j < cnt ? a.su[s0 + j] : 0.0f, vv = j < cnt ? a.sv[s0 + j] : 0.0f;
         float y[3];
         ok = tc_forward(sm, tmem, t, uu, vv, y, &phase);
         if (ok && j < cnt) {
-            const size_t rec = (size_t)a.probe_base[m] + (size_t)r * cnt + j;
+            const size_t rec = rbase + j;
             a.probes[rec] = make_float4(__saturatef(y[0]), __saturatef(y[1]), __saturatef(y[2]), __uint_as_float(3u));
             n_eval++;
         }

@@ -259,8 +259,8 @@ def test_surrogate_pass_beats_exact_evaluation_with_the_cache(P, trained):
 
 
 def test_features_within_one_bf16_step_of_sin_cos(P):
-    """The kernels form the 64 Fourier features from sincospif at k = 1, 5, 9, 13 and the
-    angle-addition formulas in between.  With identity hidden layers and W3 picking three
+    """The kernels form the 64 Fourier features from sincospif at k = 1 and 9 and the
+    angle-addition formulas in between (seven steps from each).  With identity hidden layers and W3 picking three
     features, the network returns max(BF16(feature), 0) exactly; every returned feature is
     within one BF16 step of BF16(sin or cos of pi k x) evaluated in FP64, and almost all equal
     it (a flip needs the FP32 value within a few ulps of a BF16 rounding boundary)."""
