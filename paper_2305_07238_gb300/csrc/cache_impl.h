@@ -61,6 +61,7 @@ struct pmc_cache {
     int32_t* d_surr_ord = nullptr;        // n_mats: ordinal if enabled, else -1
     uint32_t* d_surr_items = nullptr;     // n_mats + 1
     bool any_surr_on = false;
+    bool all_roots_surr = false;   // every material's cacheable nodes are all surrogates' (>= one)
     uint32_t* d_bins = nullptr;           // counts (n_bins) | bases (n_bins + 1)
     // per-batch scratch, grown on demand
     uint64_t cap_points = 0;

@@ -484,6 +484,7 @@ pmc_status enqueue_batch(pmc_cache* c, const pmc_points* pts, float* out_rgb, ui
     if (surrogates_active(c)) {
         a.surr_slot = c->d_surr_slot; a.surr_ord = c->d_surr_ord; a.surr_theta = c->d_surr_theta;
         a.surr_item_base = c->d_surr_items;
+        a.all_surr = c->all_roots_surr ? 1 : 0;
     }
     a.rinfo = c->d_rinfo; a.n_roots_total = (uint32_t)c->root_info.size(); a.max_level = c->max_level;
     a.miss_cnt = c->d_miss_cnt; a.root_item_base = c->d_root_items; a.misslist = c->d_misslist;
@@ -921,13 +922,20 @@ cudaError_t upload_surrogate_maps(pmc_cache* c) {
     std::vector<int32_t> slot(c->n_mats, -1), ord(c->n_mats, -1);
     c->any_surr_on = false;
     c->layout_gen++;
+    bool all = true;
     for (uint32_t m = 0; m < c->n_mats; ++m) {
-        if (c->surr_on[m] && c->surr_slot[m] >= 0 && c->surr_cand[m] >= 0) {
+        const bool on = c->surr_on[m] && c->surr_slot[m] >= 0 && c->surr_cand[m] >= 0;
+        if (on) {
             slot[m] = c->surr_slot[m];
             ord[m] = c->surr_cand[m];
             c->any_surr_on = true;
         }
+        // a surrogate stands for one cacheable node: the material needs no probe iff that
+        // is its only one
+        const uint32_t nr = c->mat_info[m].n_roots;
+        if (nr > 1 || (nr == 1 && !on)) all = false;
     }
+    c->all_roots_surr = all && c->any_surr_on;
     cudaError_t e = cudaMemcpy(c->d_surr_slot, slot.data(), c->n_mats * sizeof(int32_t), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(c->d_surr_ord, ord.data(), c->n_mats * sizeof(int32_t), cudaMemcpyHostToDevice);
     return e;

@@ -2560,7 +2560,7 @@ cudaError_t launch_batch(const BatchArgs& a, cudaStream_t s, int num_sms, cudaEv
     if ((e = mark(1)) != cudaSuccess) return e;
     // grouped schedule with the probes in the evaluator: no lookup kernel, no records
     const bool fused = a.probe_inline && a.use_cache;
-    if (a.n > 0 && a.use_cache && !a.keys_inline && !fused) {
+    if (a.n > 0 && a.use_cache && !a.keys_inline && !fused && !a.all_surr) {
         const uint32_t ne = a.n_entries, rb = a.lookup_rb;
         const unsigned lb = (unsigned)num_sms * 8u;
         if (a.pos_level >= 0)
@@ -2605,7 +2605,7 @@ cudaError_t launch_batch(const BatchArgs& a, cudaStream_t s, int num_sms, cudaEv
              (e = cudaFuncSetAttribute(k_eval_roots<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)smem_roots)) != cudaSuccess))
             return e;
-        if (a.use_cache && a.split && !a.keys_inline) {
+        if (a.use_cache && a.split && !a.keys_inline && !a.all_surr) {
             k_scan_roots<<<1, 1024, 0, s>>>(a);
             nl++;
             // the level counters live after the per-root miss counters
@@ -2626,7 +2626,8 @@ cudaError_t launch_batch(const BatchArgs& a, cudaStream_t s, int num_sms, cudaEv
         return e;
     }
     if ((e = mark(4)) != cudaSuccess) return e;
-    if ((e = launch_insert(a, s, num_sms, &nl)) != cudaSuccess) return e;
+    // with every cacheable node a surrogate's there is nothing to insert
+    if (!a.all_surr && (e = launch_insert(a, s, num_sms, &nl)) != cudaSuccess) return e;
     if ((e = mark(5)) != cudaSuccess) return e;
     k_finish<<<1, 32, 0, s>>>(a);
     nl++;

@@ -209,6 +209,8 @@ struct BatchArgs {
     // ordinal; FP32 parameters per slot; work items of 128 points per material
     const int32_t* surr_slot; const int32_t* surr_ord; const float* surr_theta;
     uint32_t* surr_item_base;  // n_mats + 1 (computed by k_scan)
+    int all_surr;              // 1: every cacheable node of every material is a surrogate's:
+                               // no lookup, no batched misses, no insert
     uint32_t n_bins;           // cell-grouped insert: ceil(n_cells / INSERT_BIN_CELLS) bins
     uint32_t* bin_cnt;         // n_bins
     uint32_t* bin_base;        // n_bins + 1

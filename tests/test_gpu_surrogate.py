@@ -288,3 +288,45 @@ def test_features_within_one_bf16_step_of_sin_cos(P):
             assert np.all(np.abs(got - want) <= step), (f, float(np.abs(got - want).max()))
             mism += int(np.sum(got != want))
     assert mism <= 0.005 * n * 66, mism
+
+
+def test_pass_with_every_node_a_surrogate_skips_lookup_and_insert(P):
+    """Every material's only cacheable node has a network: the pass needs no lookup, no
+    batched misses and no insert, so the library launches none of them.  Outputs equal the
+    oracle's pass with the same networks (BF16 rounding points), and both count zero
+    lookups and inserts."""
+    mats = W.surrogate_materials(5, 200, 600, seed=12)
+    cache = P.Cache(mats, 1 << 10, 8)
+    ref = O.Cache(mats, 1 << 10, 8)
+    rng = np.random.default_rng(12)
+    for m in range(len(mats)):
+        assert cache.material_info(m)["roots"].size == 1
+        th = np.zeros(M.N_PARAMS)
+        th[0:4096] = rng.uniform(-1, 1, 4096) * np.sqrt(6 / 64)
+        th[4160:8256] = rng.uniform(-1, 1, 4096) * np.sqrt(6 / 64)
+        th[8320:8512] = rng.uniform(-1, 1, 192) * np.sqrt(6 / 64) * 0.5
+        th[8512:] = 0.5
+        cache.set_surrogate(m, th.astype(np.float32))
+        info = cache.get_surrogate(m)
+        assert info["enabled"]
+        ref.set_surrogate(m, info["node"], info["theta"].astype(np.float64), bf16=True)
+    pts = W.points_uniform(3000, seed=13, n_mats=len(mats))
+    launches = []
+    for p in range(2):
+        part = W.slice_points(pts, 1500 * p, 1500 * (p + 1))
+        d = P.points_to_device(part)
+        rgb = torch.empty((3, 1500), device="cuda")
+        cache.read_timing()                 # restarts the launch count
+        cache.eval_batch(d, rgb)
+        cache.sync()
+        launches.append(cache.read_timing()["launches"])
+        r = ref.run_batch(part)
+        g = rgb.cpu().numpy()
+        assert np.abs(g - r["rgb"]).max() <= FWD_TOL
+        assert np.quantile(np.abs(g - r["rgb"]), 0.99) <= FWD_Q99
+    gs, rs = cache.stats(), ref.stats()
+    for k in ("lookups", "hits", "misses", "candidates", "inserted"):
+        assert gs[k] == rs[k] == 0, (k, gs[k], rs[k])
+    assert gs["surrogate_evals"] == 3000
+    # grouping (3) + surrogate + evaluation + bookkeeping, on the pass after the first
+    assert launches[1] <= 6, launches
