@@ -324,15 +324,21 @@ __global__ void __launch_bounds__(TC_ROWS) k_mlp_forward_tc(const float* __restr
     uint32_t phase = 0;
     bool ok = true;
     const uint32_t tiles = (n + TC_ROWS - 1) / TC_ROWS;
+    // each tile's (u, v) is loaded while the previous tile runs through the network
+    uint32_t r = blockIdx.x * TC_ROWS + t;
+    float uu = r < n ? u[r] : 0.0f, vv = r < n ? v[r] : 0.0f;
     for (uint32_t tile = blockIdx.x; tile < tiles && ok; tile += gridDim.x) {
-        const uint32_t r = tile * TC_ROWS + t;
-        const float uu = r < n ? u[r] : 0.0f, vv = r < n ? v[r] : 0.0f;
+        const uint32_t rn = r + gridDim.x * TC_ROWS;
+        const float un = rn < n ? u[rn] : 0.0f, vn = rn < n ? v[rn] : 0.0f;
         float y[3];
         ok = tc_forward(sm, tmem, t, uu, vv, y, &phase);
         if (ok && r < n) {
 #pragma unroll
             for (int k = 0; k < 3; ++k) out[(size_t)k * n + r] = clamp ? __saturatef(y[k]) : y[k];
         }
+        r = rn;
+        uu = un;
+        vv = vn;
     }
     if (!ok) {
         // a wait for the tensor cores ran out: this CTA's remaining rows read NaN
@@ -361,7 +367,8 @@ __global__ void __launch_bounds__(TC_ROWS) k_surrogate_tc(BatchArgs a) {
     bool ok = true;
     // an item's material is the largest m with surr_item_base[m] <= item; the CTA's items are
     // consecutive, so the bisection runs only when an item passes the current material's end
-    uint32_t m = 0, next_base = 0, ibase = 0, cnt = 0, s0 = 0;
+    uint32_t m = 0, next_base = 0, ibase = 0, cnt = 0, s0 = 0, pre_item = 0xFFFFFFFFu;
+    float uu = 0.0f, vv = 0.0f;
     size_t rbase = 0;   // the first probe record of the node's column in material m
     for (uint32_t item = blockIdx.x * per; item < i_end && ok; ++item) {
         if (item >= next_base) {
@@ -384,7 +391,15 @@ __global__ void __launch_bounds__(TC_ROWS) k_surrogate_tc(BatchArgs a) {
             loaded = m;
         }
         const uint32_t j = (item - ibase) * TC_ROWS + t;
-        const float uu = j < cnt ? a.su[s0 + j] : 0.0f, vv = j < cnt ? a.sv[s0 + j] : 0.0f;
+        // this item's (u, v) were loaded during the previous item if it had the same material
+        if (item != pre_item) {
+            uu = j < cnt ? a.su[s0 + j] : 0.0f;
+            vv = j < cnt ? a.sv[s0 + j] : 0.0f;
+        }
+        const uint32_t jn = j + TC_ROWS;
+        const bool pre = item + 1 < i_end && item + 1 < next_base;
+        const float un = (pre && jn < cnt) ? a.su[s0 + jn] : 0.0f, vn = (pre && jn < cnt) ? a.sv[s0 + jn] : 0.0f;
+        pre_item = pre ? item + 1 : 0xFFFFFFFFu;
         float y[3];
         ok = tc_forward(sm, tmem, t, uu, vv, y, &phase);
         if (ok && j < cnt) {
@@ -392,6 +407,8 @@ __global__ void __launch_bounds__(TC_ROWS) k_surrogate_tc(BatchArgs a) {
             a.probes[rec] = make_float4(__saturatef(y[0]), __saturatef(y[1]), __saturatef(y[2]), __uint_as_float(3u));
             n_eval++;
         }
+        uu = un;
+        vv = vn;
     }
     if (!ok && t == 0) atomicOr(&a.ctl->err, ERR_TIMEOUT);
 #pragma unroll
