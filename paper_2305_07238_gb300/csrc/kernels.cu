@@ -486,18 +486,48 @@ __device__ __forceinline__ void offer(const BatchArgs& a, bool act, uint32_t ori
     }
 }
 
+// EVAL_FILL: the pass on an empty table without surrogates.  Every probe would miss at slot
+// 0, so every lane runs the whole program (as EVAL_PLAIN) and offers each cacheable node's
+// value under its descriptor as it is computed; the counters of the skipped lookups are
+// those of EVAL_GENERIC's inline descriptors (one lookup, one miss, one empty slot).
+struct FillStats {
+    unsigned long long n_cand = 0, n_full = 0, n_look = 0;
+};
+
+// Offers the value (r, g, b) of cacheable node `node` at grouped point s (act: a valid
+// point); the point's level, texel and batch index are read here, where they are needed.
+__device__ __forceinline__ void fill_offer(const BatchArgs& a, bool act, uint32_t s, uint32_t m, uint32_t node, bool pos,
+                                           const PointIn& p, float r, float g, float b, FillStats* fs) {
+    uint32_t cell = 0, h2 = 0, orig = 0;
+    if (act) {
+        uint64_t key;
+        if (pos) {
+            key = d_key_pos(m, node, (uint32_t)a.pos_level, p.px, p.py, p.pz);
+        } else {
+            const uint32_t lev = a.g1u ? (uint32_t)a.slev[s] : a.level;
+            key = d_key(m, node, lev, d_texel(p.u, lev), d_texel(p.v, lev));
+        }
+        d_address(key, a.n_cells, a.cells_pow2_mask, &cell, &h2);
+        orig = a.sidx[s];
+        fs->n_look++;
+    }
+    offer(a, act, orig, node, cell, h2, 0u, false, r, g, b, &fs->n_cand, &fs->n_full);
+}
+
 // Per-point interpreter: one warp runs one material's program for 32 grouped points.
 // EVAL_OUTER: every cacheable node already has its value in its probe record (a hit, a
 //   value computed by k_eval_roots or a learned surrogate), so the outer program runs:
 //   each block replaced by a load of its node's record.
 // EVAL_PLAIN: the cache is off; the whole program runs for every point.
+// EVAL_FILL: the first pass on an empty table without surrogates (two points per lane only;
+//   see fill_offer).
 // EVAL_GENERIC: the whole program with per-lane skipping: the first pass on an empty table
 //   (descriptors formed here, every cacheable node offered), the inline evaluation of
 //   misses (a lane whose lookup hit skips the block), learned surrogates on that pass.
 // In the first two modes every lane runs every instruction: a lane past the end of its
 // material's points shadows the segment's last point and stores nothing, and the node and
 // operation counts come from the program's totals.
-enum { EVAL_OUTER = 0, EVAL_PLAIN = 1, EVAL_GENERIC = 2 };
+enum { EVAL_OUTER = 0, EVAL_PLAIN = 1, EVAL_GENERIC = 2, EVAL_FILL = 3 };
 
 template <int MODE>
 __global__ void __launch_bounds__(EVAL_WARPS * 32) k_eval(BatchArgs a, uint32_t* item_ctr) {
@@ -660,10 +690,11 @@ __global__ void __launch_bounds__(EVAL_WARPS * 32) k_eval(BatchArgs a, uint32_t*
 }
 
 // One 32-point item of the modes in which every lane runs every instruction (EVAL_OUTER,
-// EVAL_PLAIN), one point per lane (Vb: the lane's base in a [slot][channel][lane] file).
+// EVAL_PLAIN, EVAL_FILL), one point per lane (Vb: the lane's base in a [slot][channel][lane]
+// file).
 template <int MODE>
 __device__ __forceinline__ void eval_item1(const BatchArgs& a, uint32_t item, uint32_t m, char* Vb, const float2* grad,
-                                           unsigned long long* n_nodes, unsigned long long* n_flops) {
+                                           unsigned long long* n_nodes, unsigned long long* n_flops, FillStats* fs) {
     constexpr bool outer = MODE == EVAL_OUTER;
     const uint32_t lane = lane_id();
     const uint32_t cnt = __ldg(&a.counts[m]);
@@ -687,6 +718,8 @@ __device__ __forceinline__ void eval_item1(const BatchArgs& a, uint32_t item, ui
         const uint32_t nr = min(mi.n_roots, 16u);
         for (uint32_t r = 0; r < nr; ++r) asm volatile("prefetch.global.L1 [%0];" ::"l"(rec0 + (size_t)r * cnt));
     }
+    uint32_t cnode = 0;
+    bool cpos = false;
     uint4 nxt = __ldg(&prog[0]);   // the pool ends with a padding instruction
     for (int pc = 0; pc < len; ++pc) {
         const uint4 ins = nxt;
@@ -700,8 +733,18 @@ __device__ __forceinline__ void eval_item1(const BatchArgs& a, uint32_t item, ui
             if (valid && state != PROBE_HIT && state != PROBE_COMPUTED) atomicOr(&a.ctl->err, ERR_BOUNDS);
             continue;
         }
-        if (!outer && op == OP_ROOT_BEGIN) continue;
+        if (!outer && op == OP_ROOT_BEGIN) {
+            if (MODE == EVAL_FILL) {
+                cnode = ins.z;
+                cpos = ((ins.x >> 8) & FLAG_POSROOT) != 0;
+            }
+            continue;
+        }
         exec_node(op, ins, Vb, pt, a.params, grad);
+        if (MODE == EVAL_FILL && ((ins.x >> 8) & FLAG_ROOT)) {
+            const uint32_t o = ins.y & 0xFFFFu;
+            fill_offer(a, valid, s, m, cnode, cpos, pt, slot_ch(Vb, o, 0), slot_ch(Vb, o, 1), slot_ch(Vb, o, 2), fs);
+        }
     }
     if (valid) {
         a.out_rgb[orig] = slot_ch(Vb, out_off, 0);
@@ -717,7 +760,7 @@ __device__ __forceinline__ void eval_item1(const BatchArgs& a, uint32_t item, ui
 // item, B from the second; Vb: the lane's base in a [slot][channel][lane][2] file).
 template <int MODE>
 __device__ __forceinline__ void eval_item2(const BatchArgs& a, uint32_t item, uint32_t m, char* Vb, const float2* grad,
-                                           unsigned long long* n_nodes, unsigned long long* n_flops) {
+                                           unsigned long long* n_nodes, unsigned long long* n_flops, FillStats* fs) {
     constexpr bool outer = MODE == EVAL_OUTER;
     const uint32_t lane = lane_id();
     const uint32_t cnt = __ldg(&a.counts[m]);
@@ -746,6 +789,8 @@ __device__ __forceinline__ void eval_item2(const BatchArgs& a, uint32_t item, ui
             asm volatile("prefetch.global.L1 [%0];" ::"l"(rb + (size_t)r * cnt));
         }
     }
+    uint32_t cnode = 0;
+    bool cpos = false;
     uint4 nxt = __ldg(&prog[0]);
     for (int pc = 0; pc < len; ++pc) {
         const uint4 ins = nxt;
@@ -762,8 +807,20 @@ __device__ __forceinline__ void eval_item2(const BatchArgs& a, uint32_t item, ui
                 atomicOr(&a.ctl->err, ERR_BOUNDS);
             continue;
         }
-        if (!outer && op == OP_ROOT_BEGIN) continue;
+        if (!outer && op == OP_ROOT_BEGIN) {
+            if (MODE == EVAL_FILL) {
+                cnode = ins.z;
+                cpos = ((ins.x >> 8) & FLAG_POSROOT) != 0;
+            }
+            continue;
+        }
         exec_node2(op, ins, Vb, A, B, a.params, grad);
+        if (MODE == EVAL_FILL && ((ins.x >> 8) & FLAG_ROOT)) {
+            const uint32_t o = ins.y & 0xFFFFu;
+            const float2 c0 = slot2(Vb, o, 0), c1 = slot2(Vb, o, 1), c2 = slot2(Vb, o, 2);
+            fill_offer(a, vA, sA, m, cnode, cpos, A, c0.x, c1.x, c2.x, fs);
+            fill_offer(a, vB, sB, m, cnode, cpos, B, c0.y, c1.y, c2.y, fs);
+        }
     }
     const float2 o0 = slot2(Vb, out_off, 0), o1 = slot2(Vb, out_off, 1), o2 = slot2(Vb, out_off, 2);
     const uint32_t nv = (vA ? 1u : 0u) + (vB ? 1u : 0u);
@@ -791,7 +848,7 @@ __device__ __forceinline__ void eval_item2(const BatchArgs& a, uint32_t item, ui
 // warps of a block run one material's program together and share its instruction and
 // parameter lines in L1); else every warp claims its own pair.
 template <int MODE, bool BLOCK>
-__global__ void __launch_bounds__(EVAL_WARPS * 32, 7) k_eval2(BatchArgs a, uint32_t* item_ctr) {
+__global__ void __launch_bounds__(EVAL_WARPS * 32, MODE == EVAL_FILL ? 6 : 7) k_eval2(BatchArgs a, uint32_t* item_ctr) {
     extern __shared__ float s_val[];
     __shared__ float2 s_grad[8];
     __shared__ uint32_t s_tile;
@@ -799,6 +856,7 @@ __global__ void __launch_bounds__(EVAL_WARPS * 32, 7) k_eval2(BatchArgs a, uint3
     __syncthreads();
     const uint32_t warp = threadIdx.x >> 5, lane = lane_id();
     const uint32_t slots = MODE == EVAL_OUTER ? a.max_slots_outer : a.max_slots;
+    FillStats fs;
     char* Vw = reinterpret_cast<char*>(s_val + (size_t)warp * slots * 192u);
     char* Vb2 = Vw + lane * 8u;
     char* Vb1 = Vw + lane * 4u;
@@ -824,16 +882,23 @@ __global__ void __launch_bounds__(EVAL_WARPS * 32, 7) k_eval2(BatchArgs a, uint3
         }
         const uint32_t m = find_material(a.item_base, a.n_mats, it);
         if (it + 1u < __ldg(&a.item_base[m + 1])) {
-            eval_item2<MODE>(a, it, m, Vb2, s_grad, &n_nodes, &n_flops);
+            eval_item2<MODE>(a, it, m, Vb2, s_grad, &n_nodes, &n_flops, &fs);
         } else {
-            eval_item1<MODE>(a, it, m, Vb1, s_grad, &n_nodes, &n_flops);
+            eval_item1<MODE>(a, it, m, Vb1, s_grad, &n_nodes, &n_flops, &fs);
             if (it + 1u < n_items)
                 eval_item1<MODE>(a, it + 1u, find_material(a.item_base, a.n_mats, it + 1u), Vb1, s_grad, &n_nodes,
-                                 &n_flops);
+                                 &n_flops, &fs);
         }
     }
     warp_add_u64(&a.stats[ST_NODES], n_nodes);
     warp_add_u64(&a.stats[ST_FLOPS], n_flops);
+    if (MODE == EVAL_FILL) {
+        warp_add_u64(&a.stats[ST_CANDIDATES], fs.n_cand);
+        warp_add_u64(&a.stats[ST_FULL], fs.n_full);
+        warp_add_u64(&a.stats[ST_LOOKUPS], fs.n_look);
+        warp_add_u64(&a.stats[ST_MISSES], fs.n_look);
+        warp_add_u64(&a.stats[ST_SLOTS], fs.n_look);   // one (empty) slot examined per probe
+    }
 }
 
 // Scans cell `cell` for h2 (Alg. 1's entry loop read as a lookup): the first slot that
@@ -2588,12 +2653,16 @@ cudaError_t launch_batch(const BatchArgs& a, cudaStream_t s, int num_sms, cudaEv
         const bool plain = !a.use_cache && !a.surr_ord;
         const size_t smem = eval_smem_bytes(outer ? a.max_slots_outer : a.max_slots),
                      smem_roots = eval_smem_bytes(a.max_slots_roots);
+        // the first pass on an empty table without surrogates: every lane runs every node
+        const bool fill = a.use_cache && a.keys_inline && !a.surr_ord;
         auto keval = outer ? k_eval<EVAL_OUTER> : plain ? k_eval<EVAL_PLAIN> : k_eval<EVAL_GENERIC>;
         // two points per lane where every lane runs every instruction and the doubled slot
         // file leaves room for several blocks per SM; the item counter then counts pairs
-        const bool two = (outer || plain) && !a.one_point && 2 * smem <= EVAL2_MAX_SMEM;
-        if (two && a.block_items) keval = outer ? k_eval2<EVAL_OUTER, true> : k_eval2<EVAL_PLAIN, true>;
-        else if (two) keval = outer ? k_eval2<EVAL_OUTER, false> : k_eval2<EVAL_PLAIN, false>;
+        const bool two = (outer || plain || fill) && !a.one_point && 2 * smem <= EVAL2_MAX_SMEM;
+        if (two && a.block_items)
+            keval = outer ? k_eval2<EVAL_OUTER, true> : plain ? k_eval2<EVAL_PLAIN, true> : k_eval2<EVAL_FILL, true>;
+        else if (two)
+            keval = outer ? k_eval2<EVAL_OUTER, false> : plain ? k_eval2<EVAL_PLAIN, false> : k_eval2<EVAL_FILL, false>;
         const size_t smem_eval = two ? 2 * smem : smem;
         if (smem_eval > 48 * 1024 &&
             (e = cudaFuncSetAttribute(keval, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_eval)) !=
