@@ -67,6 +67,10 @@ __device__ __forceinline__ uint32_t find_material(const uint32_t* item_base, uin
 // =======================================================================================
 // Materials counted in shared memory per block; beyond this the counters are global.
 constexpr uint32_t GROUP_SMEM_MATS = 4096;
+// grouping kernels (k_hist, k_scatter): eight blocks of 256 threads per SM, the SM's full
+// thread capacity, so that each block's range is short and the memory latency of its
+// dependent count / reserve / scatter steps is hidden by the other blocks
+constexpr int GROUP_BLOCKS_PER_SM = 8;
 
 // Points of block b: the contiguous range [b * chunk, min(n, (b + 1) * chunk)).
 __device__ __forceinline__ void block_range(uint32_t n, uint32_t* lo, uint32_t* hi) {
@@ -2541,12 +2545,11 @@ cudaError_t launch_batch(const BatchArgs& a, cudaStream_t s, int num_sms, cudaEv
     if (a.split && (e = cudaMemsetAsync(a.miss_cnt, 0, (a.n_roots_total + MAX_LEVELS) * sizeof(uint32_t), s)) != cudaSuccess)
         return e;
     uint32_t* item_ctr = a.counts + a.n_mats;
-    const int gs_blocks = num_sms * 4;
     if (a.alg1 && a.use_cache) {
         // the paper's concurrent update: lookups and inserts inside the evaluator, no
         // lookup kernel, no insert phase; grouped by material unless unsorted
         if (!a.unsorted && a.n > 0) {
-            k_hist<<<gs_blocks, 256, 0, s>>>(a);
+            k_hist<<<num_sms * GROUP_BLOCKS_PER_SM, 256, 0, s>>>(a);
             nl++;
         }
         if (!a.unsorted) {
@@ -2554,7 +2557,7 @@ cudaError_t launch_batch(const BatchArgs& a, cudaStream_t s, int num_sms, cudaEv
             nl++;
         }
         if (!a.unsorted && a.n > 0) {
-            k_scatter<<<gs_blocks, 256, 0, s>>>(a);
+            k_scatter<<<num_sms * GROUP_BLOCKS_PER_SM, 256, 0, s>>>(a);
             nl++;
         }
         if ((e = mark(1)) != cudaSuccess) return e;
@@ -2613,13 +2616,13 @@ cudaError_t launch_batch(const BatchArgs& a, cudaStream_t s, int num_sms, cudaEv
         return cudaGetLastError();
     }
     if (a.n > 0) {
-        k_hist<<<gs_blocks, 256, 0, s>>>(a);
+        k_hist<<<num_sms * GROUP_BLOCKS_PER_SM, 256, 0, s>>>(a);
         nl++;
     }
     k_scan<<<1, 1024, 0, s>>>(a);
     nl++;
     if (a.n > 0) {
-        k_scatter<<<gs_blocks, 256, 0, s>>>(a);
+        k_scatter<<<num_sms * GROUP_BLOCKS_PER_SM, 256, 0, s>>>(a);
         nl++;
     }
     if ((e = mark(1)) != cudaSuccess) return e;
