@@ -121,16 +121,30 @@ __global__ void __launch_bounds__(256) k_hist(BatchArgs a) {
     uint32_t lo, hi;
     block_range(a.n, &lo, &hi);
     unsigned long long bad = 0;
-    for (uint32_t i = lo + threadIdx.x; i < ((hi + 31u) & ~31u) && lo < hi; i += blockDim.x) {
-        bool act = i < hi;
-        uint32_t m = act ? a.mat[i] : 0u;
-        bool ok = act && m < a.n_mats;
-        if (act && !ok) bad++;
-        unsigned vmask = __ballot_sync(FULL_MASK, ok);
-        if (ok) {
-            unsigned peers = __match_any_sync(vmask, m);
-            int leader = __ffs(peers) - 1;
-            if ((int)lane_id() == leader) atomicAdd(local ? &s_cnt[m] : &a.counts[m], (uint32_t)__popc(peers));
+    const uint32_t hi32 = (hi + 31u) & ~31u;
+    // four material ids in flight per thread (a warp's indices are consecutive and 32-aligned,
+    // so the bound checks are uniform over the warp)
+    for (uint32_t i0 = lo + threadIdx.x; i0 < hi32 && lo < hi; i0 += 4u * blockDim.x) {
+        uint32_t mm[4];
+#pragma unroll
+        for (uint32_t k = 0; k < 4; ++k) {
+            const uint32_t i = i0 + k * blockDim.x;
+            mm[k] = i < hi ? a.mat[i] : 0u;
+        }
+#pragma unroll
+        for (uint32_t k = 0; k < 4; ++k) {
+            const uint32_t i = i0 + k * blockDim.x;
+            if (i >= hi32) break;
+            const bool act = i < hi;
+            const uint32_t m = mm[k];
+            const bool ok = act && m < a.n_mats;
+            if (act && !ok) bad++;
+            const unsigned vmask = __ballot_sync(FULL_MASK, ok);
+            if (ok) {
+                const unsigned peers = __match_any_sync(vmask, m);
+                const int leader = __ffs(peers) - 1;
+                if ((int)lane_id() == leader) atomicAdd(local ? &s_cnt[m] : &a.counts[m], (uint32_t)__popc(peers));
+            }
         }
     }
     if (local) {
@@ -202,19 +216,6 @@ __global__ void k_scan(BatchArgs a) {
     }
 }
 
-__device__ __forceinline__ void scatter_point(const BatchArgs& a, uint32_t i, uint32_t pos) {
-    a.su[pos] = a.u[i];
-    a.sv[pos] = a.v[i];
-    a.spx[pos] = a.px[i];
-    a.spy[pos] = a.py[i];
-    a.spz[pos] = a.pz[i];
-    a.snx[pos] = a.nx[i];
-    a.sny[pos] = a.ny[i];
-    a.snz[pos] = a.nz[i];
-    a.sidx[pos] = i;
-    if (a.g1u) a.slev[pos] = d_level(a.g1u[i], a.g1v[i], a.g2u[i], a.g2v[i], a.level_offset);
-}
-
 __device__ __forceinline__ void zero_output(const BatchArgs& a, uint32_t i) {
     // out-of-range material: zero output, no probes
     a.out_rgb[i] = 0.0f;
@@ -235,14 +236,24 @@ __global__ void __launch_bounds__(256) k_scatter(BatchArgs a) {
     if (local) {
         for (uint32_t m = threadIdx.x; m < a.n_mats; m += blockDim.x) s_cnt[m] = 0;
         __syncthreads();
-        for (uint32_t i = lo + threadIdx.x; i < hi32 && lo < hi; i += blockDim.x) {
-            const bool act = i < hi;
-            const uint32_t m = act ? a.mat[i] : 0u;
-            const bool ok = act && m < a.n_mats;
-            const unsigned vmask = __ballot_sync(FULL_MASK, ok);
-            if (ok) {
-                const unsigned peers = __match_any_sync(vmask, m);
-                if ((int)lane_id() == __ffs(peers) - 1) atomicAdd(&s_cnt[m], (uint32_t)__popc(peers));
+        // four material ids in flight per thread; a warp's 32 indices are consecutive and
+        // 32-aligned, so the bound checks are uniform over the warp
+        for (uint32_t i0 = lo + threadIdx.x; i0 < hi32 && lo < hi; i0 += 4u * blockDim.x) {
+            uint32_t mm[4];
+#pragma unroll
+            for (uint32_t k = 0; k < 4; ++k) {
+                const uint32_t i = i0 + k * blockDim.x;
+                mm[k] = i < hi ? a.mat[i] : 0xFFFFFFFFu;
+            }
+#pragma unroll
+            for (uint32_t k = 0; k < 4; ++k) {
+                if (i0 + k * blockDim.x >= hi32) break;
+                const bool ok = mm[k] < a.n_mats;
+                const unsigned vmask = __ballot_sync(FULL_MASK, ok);
+                if (ok) {
+                    const unsigned peers = __match_any_sync(vmask, mm[k]);
+                    if ((int)lane_id() == __ffs(peers) - 1) atomicAdd(&s_cnt[mm[k]], (uint32_t)__popc(peers));
+                }
             }
         }
         __syncthreads();
@@ -255,6 +266,16 @@ __global__ void __launch_bounds__(256) k_scatter(BatchArgs a) {
         const bool act = i < hi;
         const uint32_t m = act ? a.mat[i] : 0u;
         const bool ok = act && m < a.n_mats;
+        // the point's fields are loaded before its position is known, so that the loads
+        // overlap the match and the reservation
+        PointIn p{0, 0, 0, 0, 0, 0, 0, 0};
+        uint32_t lev = 0;
+        if (ok) {
+            p.u = a.u[i]; p.v = a.v[i];
+            p.px = a.px[i]; p.py = a.py[i]; p.pz = a.pz[i];
+            p.nx = a.nx[i]; p.ny = a.ny[i]; p.nz = a.nz[i];
+            if (a.g1u) lev = d_level(a.g1u[i], a.g1v[i], a.g2u[i], a.g2v[i], a.level_offset);
+        }
         const unsigned vmask = __ballot_sync(FULL_MASK, ok);
         if (ok) {
             const unsigned peers = __match_any_sync(vmask, m);
@@ -263,7 +284,12 @@ __global__ void __launch_bounds__(256) k_scatter(BatchArgs a) {
             if ((int)lane_id() == leader)
                 base = atomicAdd(local ? &s_cnt[m] : &a.cursor[m], (uint32_t)__popc(peers));
             base = __shfl_sync(peers, base, leader);
-            scatter_point(a, i, base + __popc(peers & ((1u << lane_id()) - 1u)));
+            const uint32_t pos = base + __popc(peers & ((1u << lane_id()) - 1u));
+            a.su[pos] = p.u; a.sv[pos] = p.v;
+            a.spx[pos] = p.px; a.spy[pos] = p.py; a.spz[pos] = p.pz;
+            a.snx[pos] = p.nx; a.sny[pos] = p.ny; a.snz[pos] = p.nz;
+            a.sidx[pos] = i;
+            if (a.g1u) a.slev[pos] = lev;
         } else if (act) {
             zero_output(a, i);
         }
