@@ -1278,6 +1278,129 @@ __global__ void k_scan_roots(BatchArgs a) {
 // a warp runs one cacheable node's standalone program for 32 of its misses, writes the
 // values into their probe records and offers them to the table.  Every lane runs every
 // instruction: a lane past the node's last miss shadows that miss and stores nothing.
+struct RootStats {
+    unsigned long long n_nodes = 0, n_flops = 0, n_cand = 0, n_full = 0;
+};
+
+// One item (32 misses of one cacheable node), one miss per lane (Vb: the lane's base in a
+// [slot][channel][lane] file).
+template <bool POS>
+__device__ __forceinline__ void roots_item1(const BatchArgs& a, uint32_t item, uint32_t q, char* Vb, const float2* grad,
+                                            RootStats* st) {
+    const uint32_t lane = lane_id();
+    const uint32_t g = __ldg(&a.root_order[q]);
+    const RootInfo ri = a.rinfo[g];
+    const uint32_t m = ri.mat, r = ri.ordinal;
+    const uint32_t cnt = __ldg(&a.counts[m]);
+    const uint32_t nm = a.miss_cnt[g];   // at least one: the item exists
+    const uint32_t idx = (item - a.root_item_base[q]) * 32u + lane;
+    const bool valid = idx < nm;
+    const size_t pbase = __ldg(&a.probe_base[m]);
+    const size_t base = pbase + (size_t)r * cnt;
+    const uint32_t j = a.misslist[base + (valid ? idx : nm - 1u)];
+    const uint32_t s = __ldg(&a.seg_start[m]) + j;
+    PointIn pt{0, 0, 0, 0, 0, 0, 0, 0};
+    pt.u = a.su[s];
+    pt.v = a.sv[s];
+    if (POS) {   // a position-class node reads the position
+        pt.px = a.spx[s];
+        pt.py = a.spy[s];
+        pt.pz = a.spz[s];
+    }
+    const uint32_t orig = a.sidx[s];
+    const float4 rec = a.probes[base + j];
+    const uint4* prog = a.prog + ri.prog_start;
+    uint4 nxt = __ldg(&prog[0]);   // the pool ends with a padding instruction
+    for (uint32_t pc = 0; pc < ri.prog_len; ++pc) {
+        const uint4 ins = nxt;
+        nxt = __ldg(&prog[pc + 1]);
+        const uint32_t op = ins.x & 0xFFu;
+        if (op == OP_LOAD_ROOT) {
+            const float4 v = a.probes[pbase + (size_t)(ins.y >> 16) * cnt + j];
+            slot_store(Vb, ins.y & 0xFFFFu, v.x, v.y, v.z);
+            continue;
+        }
+        exec_node(op, ins, Vb, pt, a.params, grad);
+    }
+    const uint32_t out_off = ri.out_slot * SLOT_BYTES;
+    const float v0 = slot_ch(Vb, out_off, 0), v1 = slot_ch(Vb, out_off, 1), v2 = slot_ch(Vb, out_off, 2);
+    if (valid) {
+        a.probes[base + j] = make_float4(v0, v1, v2, __uint_as_float(PROBE_COMPUTED));
+        st->n_nodes += ri.nodes;
+        st->n_flops += ri.flops;
+    }
+    offer(a, valid, orig, ri.node, __float_as_uint(rec.x), __float_as_uint(rec.y), __float_as_uint(rec.z),
+          __float_as_uint(rec.w) == PROBE_FULL, v0, v1, v2, &st->n_cand, &st->n_full);
+}
+
+// Two consecutive items of one cacheable node, two misses per lane (A from the first item,
+// B from the second; Vb: the lane's base in a [slot][channel][lane][2] file).
+template <bool POS>
+__device__ __forceinline__ void roots_item2(const BatchArgs& a, uint32_t item, uint32_t q, char* Vb, const float2* grad,
+                                            RootStats* st) {
+    const uint32_t lane = lane_id();
+    const uint32_t g = __ldg(&a.root_order[q]);
+    const RootInfo ri = a.rinfo[g];
+    const uint32_t m = ri.mat, r = ri.ordinal;
+    const uint32_t cnt = __ldg(&a.counts[m]);
+    const uint32_t nm = a.miss_cnt[g];
+    const uint32_t iA = (item - a.root_item_base[q]) * 32u + lane, iB = iA + 32u;
+    const bool vA = iA < nm, vB = iB < nm;
+    const size_t pbase = __ldg(&a.probe_base[m]);
+    const size_t base = pbase + (size_t)r * cnt;
+    const uint32_t jA = a.misslist[base + (vA ? iA : nm - 1u)], jB = a.misslist[base + (vB ? iB : nm - 1u)];
+    const uint32_t s0 = __ldg(&a.seg_start[m]);
+    const uint32_t sA = s0 + jA, sB = s0 + jB;
+    PointIn A{0, 0, 0, 0, 0, 0, 0, 0}, B{0, 0, 0, 0, 0, 0, 0, 0};
+    A.u = a.su[sA]; A.v = a.sv[sA];
+    B.u = a.su[sB]; B.v = a.sv[sB];
+    if (POS) {
+        A.px = a.spx[sA]; A.py = a.spy[sA]; A.pz = a.spz[sA];
+        B.px = a.spx[sB]; B.py = a.spy[sB]; B.pz = a.spz[sB];
+    }
+    // the miss records and batch indices the offers need, loaded while the program runs
+    const float4 recA = a.probes[base + jA], recB = a.probes[base + jB];
+    const uint32_t oA = a.sidx[sA], oB = a.sidx[sB];
+    const uint4* prog = a.prog + ri.prog_start;
+    uint4 nxt = __ldg(&prog[0]);
+    for (uint32_t pc = 0; pc < ri.prog_len; ++pc) {
+        const uint4 ins = nxt;
+        nxt = __ldg(&prog[pc + 1]);
+        const uint32_t op = ins.x & 0xFFu;
+        if (op == OP_LOAD_ROOT) {
+            const size_t rb = pbase + (size_t)(ins.y >> 16) * cnt;
+            const float4 ra = a.probes[rb + jA], rc = a.probes[rb + jB];
+            slot2_store(Vb, ins.y & 0xFFFFu, f2(ra.x, rc.x), f2(ra.y, rc.y), f2(ra.z, rc.z));
+            continue;
+        }
+        exec_node2(op, ins, Vb, A, B, a.params, grad);
+    }
+    const uint32_t out_off = ri.out_slot * SLOT_BYTES;
+    const float2 o0 = slot2(Vb, out_off, 0), o1 = slot2(Vb, out_off, 1), o2 = slot2(Vb, out_off, 2);
+    if (vA) {
+        a.probes[base + jA] = make_float4(o0.x, o1.x, o2.x, __uint_as_float(PROBE_COMPUTED));
+        st->n_nodes += ri.nodes;
+        st->n_flops += ri.flops;
+    }
+    if (vB) {
+        a.probes[base + jB] = make_float4(o0.y, o1.y, o2.y, __uint_as_float(PROBE_COMPUTED));
+        st->n_nodes += ri.nodes;
+        st->n_flops += ri.flops;
+    }
+    offer(a, vA, oA, ri.node, __float_as_uint(recA.x), __float_as_uint(recA.y), __float_as_uint(recA.z),
+          __float_as_uint(recA.w) == PROBE_FULL, o0.x, o1.x, o2.x, &st->n_cand, &st->n_full);
+    offer(a, vB, oB, ri.node, __float_as_uint(recB.x), __float_as_uint(recB.y), __float_as_uint(recB.z),
+          __float_as_uint(recB.w) == PROBE_FULL, o0.y, o1.y, o2.y, &st->n_cand, &st->n_full);
+}
+
+__device__ __forceinline__ void roots_stats(const BatchArgs& a, const RootStats& st) {
+    warp_add_u64(&a.stats[ST_NODES], st.n_nodes);
+    warp_add_u64(&a.stats[ST_FLOPS], st.n_flops);
+    warp_add_u64(&a.stats[ST_FLOPS_MISSED], st.n_flops);
+    warp_add_u64(&a.stats[ST_CANDIDATES], st.n_cand);
+    warp_add_u64(&a.stats[ST_FULL], st.n_full);
+}
+
 template <bool POS>
 __global__ void __launch_bounds__(EVAL_WARPS * 32) k_eval_roots(BatchArgs a, uint32_t level, uint32_t* item_ctr) {
     extern __shared__ float s_val[];
@@ -1289,62 +1412,50 @@ __global__ void __launch_bounds__(EVAL_WARPS * 32) k_eval_roots(BatchArgs a, uin
     // this level's items only: they are contiguous in the level-ordered item layout
     const uint32_t* level_items = a.root_item_base + a.n_roots_total + 1;
     const uint32_t first = level_items[level], end = level_items[level + 1];
-    unsigned long long n_nodes = 0, n_flops = 0, n_cand = 0, n_full = 0;
+    RootStats st;
     for (;;) {
         uint32_t item = 0;
         if (lane == 0) item = first + atomicAdd(item_ctr, 1u);
         item = __shfl_sync(FULL_MASK, item, 0);
         if (item >= end) break;
-        const uint32_t q = find_material(a.root_item_base, a.n_roots_total, item);
-        const uint32_t g = __ldg(&a.root_order[q]);
-        const RootInfo ri = a.rinfo[g];
-        const uint32_t m = ri.mat, r = ri.ordinal;
-        const uint32_t cnt = __ldg(&a.counts[m]);
-        const uint32_t nm = a.miss_cnt[g];   // at least one: the item exists
-        const uint32_t idx = (item - a.root_item_base[q]) * 32u + lane;
-        const bool valid = idx < nm;
-        const size_t pbase = __ldg(&a.probe_base[m]);
-        const size_t base = pbase + (size_t)r * cnt;
-        const uint32_t j = a.misslist[base + (valid ? idx : nm - 1u)];
-        const uint32_t s = __ldg(&a.seg_start[m]) + j;
-        PointIn pt{0, 0, 0, 0, 0, 0, 0, 0};
-        pt.u = a.su[s];
-        pt.v = a.sv[s];
-        if (POS) {   // a position-class node reads the position
-            pt.px = a.spx[s];
-            pt.py = a.spy[s];
-            pt.pz = a.spz[s];
-        }
-        const uint32_t orig = a.sidx[s];
-        const float4 rec = a.probes[base + j];
-        const uint4* prog = a.prog + ri.prog_start;
-        uint4 nxt = __ldg(&prog[0]);   // the pool ends with a padding instruction
-        for (uint32_t pc = 0; pc < ri.prog_len; ++pc) {
-            const uint4 ins = nxt;
-            nxt = __ldg(&prog[pc + 1]);
-            const uint32_t op = ins.x & 0xFFu;
-            if (op == OP_LOAD_ROOT) {
-                const float4 v = a.probes[pbase + (size_t)(ins.y >> 16) * cnt + j];
-                slot_store(Vb, ins.y & 0xFFFFu, v.x, v.y, v.z);
-                continue;
-            }
-            exec_node(op, ins, Vb, pt, a.params, s_grad);
-        }
-        const uint32_t out_off = ri.out_slot * SLOT_BYTES;
-        const float v0 = slot_ch(Vb, out_off, 0), v1 = slot_ch(Vb, out_off, 1), v2 = slot_ch(Vb, out_off, 2);
-        if (valid) {
-            a.probes[base + j] = make_float4(v0, v1, v2, __uint_as_float(PROBE_COMPUTED));
-            n_nodes += ri.nodes;
-            n_flops += ri.flops;
-        }
-        offer(a, valid, orig, ri.node, __float_as_uint(rec.x), __float_as_uint(rec.y), __float_as_uint(rec.z),
-              __float_as_uint(rec.w) == PROBE_FULL, v0, v1, v2, &n_cand, &n_full);
+        roots_item1<POS>(a, item, find_material(a.root_item_base, a.n_roots_total, item), Vb, s_grad, &st);
     }
-    warp_add_u64(&a.stats[ST_NODES], n_nodes);
-    warp_add_u64(&a.stats[ST_FLOPS], n_flops);
-    warp_add_u64(&a.stats[ST_FLOPS_MISSED], n_flops);
-    warp_add_u64(&a.stats[ST_CANDIDATES], n_cand);
-    warp_add_u64(&a.stats[ST_FULL], n_full);
+    roots_stats(a, st);
+}
+
+// The same with two misses per lane: a warp takes pairs of consecutive items (the item
+// counter counts pairs); a pair whose items belong to two cacheable nodes runs as two
+// single items.
+template <bool POS>
+__global__ void __launch_bounds__(EVAL_WARPS * 32, 6) k_eval_roots2(BatchArgs a, uint32_t level, uint32_t* item_ctr) {
+    extern __shared__ float s_val[];
+    __shared__ float2 s_grad[8];
+    init_gradients(s_grad);
+    __syncthreads();
+    const uint32_t warp = threadIdx.x >> 5, lane = lane_id();
+    char* Vw = reinterpret_cast<char*>(s_val + (size_t)warp * a.max_slots_roots * 192u);
+    char* Vb2 = Vw + lane * 8u;
+    char* Vb1 = Vw + lane * 4u;
+    const uint32_t* level_items = a.root_item_base + a.n_roots_total + 1;
+    const uint32_t first = level_items[level], end = level_items[level + 1];
+    RootStats st;
+    for (;;) {
+        uint32_t pr = 0;
+        if (lane == 0) pr = atomicAdd(item_ctr, 1u);
+        pr = __shfl_sync(FULL_MASK, pr, 0);
+        const uint32_t it = first + 2u * pr;
+        if (it >= end) break;
+        const uint32_t q = find_material(a.root_item_base, a.n_roots_total, it);
+        if (it + 1u < end && it + 1u < a.root_item_base[q + 1]) {
+            roots_item2<POS>(a, it, q, Vb2, s_grad, &st);
+        } else {
+            roots_item1<POS>(a, it, q, Vb1, s_grad, &st);
+            if (it + 1u < end)
+                roots_item1<POS>(a, it + 1u, find_material(a.root_item_base, a.n_roots_total, it + 1u), Vb1, s_grad,
+                                 &st);
+        }
+    }
+    roots_stats(a, st);
 }
 
 // =======================================================================================
@@ -2697,23 +2808,22 @@ cudaError_t launch_batch(const BatchArgs& a, cudaStream_t s, int num_sms, cudaEv
             (e = cudaFuncSetAttribute(keval, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_eval)) !=
                 cudaSuccess)
             return e;
-        if (smem_roots > 48 * 1024 &&
-            ((e = cudaFuncSetAttribute(k_eval_roots<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)smem_roots)) != cudaSuccess ||
-             (e = cudaFuncSetAttribute(k_eval_roots<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)smem_roots)) != cudaSuccess))
+        // the batched misses: two misses per lane under the same conditions as the per-point
+        // evaluator (the item counter then counts pairs)
+        const bool two_roots = !a.one_point && 2 * smem_roots <= EVAL2_MAX_SMEM;
+        auto kroots = a.pos_level >= 0 ? (two_roots ? k_eval_roots2<true> : k_eval_roots<true>)
+                                       : (two_roots ? k_eval_roots2<false> : k_eval_roots<false>);
+        const size_t smem_kroots = two_roots ? 2 * smem_roots : smem_roots;
+        if (smem_kroots > 48 * 1024 &&
+            (e = cudaFuncSetAttribute(kroots, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_kroots)) !=
+                cudaSuccess)
             return e;
         if (a.use_cache && a.split && !a.keys_inline && !a.all_surr) {
             k_scan_roots<<<1, 1024, 0, s>>>(a);
             nl++;
             // the level counters live after the per-root miss counters
             for (uint32_t lv = 0; lv <= a.max_level; ++lv) {
-                if (a.pos_level >= 0)
-                    k_eval_roots<true><<<num_sms * 16, EVAL_WARPS * 32, smem_roots, s>>>(a, lv,
-                                                                                      a.miss_cnt + a.n_roots_total + lv);
-                else
-                    k_eval_roots<false><<<num_sms * 16, EVAL_WARPS * 32, smem_roots, s>>>(a, lv,
-                                                                                       a.miss_cnt + a.n_roots_total + lv);
+                kroots<<<num_sms * 16, EVAL_WARPS * 32, smem_kroots, s>>>(a, lv, a.miss_cnt + a.n_roots_total + lv);
                 nl++;
             }
         }
