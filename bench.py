@@ -43,7 +43,7 @@ REF_ROWS = (0, 16)               # reference arm: 16 full-width rows per step, a
 # DRAM bytes (read + written) per launch of each kernel, the mean of the two launches one
 # ncu capture of that kernel takes from a four-pass frame of this workload at the bench's
 # cost threshold; None while the kernel has changed since its capture
-NCU_TRAFFIC = {"eval": 150.6e6, "eval_roots": 77.6e6, "lookup": 329.2e6}
+NCU_TRAFFIC = {"eval": 150.6e6, "eval_roots": None, "lookup": 329.2e6}
 
 FP32_LANES_PER_SM = 128          # Blackwell SM: 4 partitions x 32 FP32 lanes
 
@@ -332,7 +332,13 @@ def ours(args, rank, world, local_rank, dist):
     phase_of = {"eval": "eval", "eval_roots": "missed", "lookup": "lookup"}
     dominant = max(phase_of, key=lambda k: ms[phase_of[k]])
     roof = dict(kernels[dominant])
-    roof["kernel"] = {"eval": "k_eval", "eval_roots": "k_eval_roots", "lookup": "k_lookup"}[dominant]
+    # the evaluators of the tuned schedule: two points per lane unless it is PMC_ONE_POINT
+    one_point = bool(tune["schedule"]["flags"] & P.PMC_ONE_POINT)
+    names = {"eval": "k_eval" if one_point else "k_eval2", "eval_roots": "k_eval_roots" if one_point else "k_eval_roots2",
+             "lookup": "k_lookup"}
+    for k in kernels:
+        kernels[k]["kernel"] = names[k]
+    roof["kernel"] = names[dominant]
     roof["peak_kind"] = "FP32 lanes x 2 x max SM clock" if dominant != "lookup" else peak_kind + " HBM copy"
 
     line = {

@@ -2525,6 +2525,24 @@ __global__ void __launch_bounds__(256, 6) k_bin_insert(BatchArgs a) {
                     }
                     if (t == 0 && s_best[0] != ~0ull) insert_one(a, cb[s_bidx[0]], ne, &n_ins, &n_dup, &n_full, &n_rep);
                     last = s_best[0];
+                    // keep-first: once the cell is full (its slots fill as a prefix) nothing
+                    // changes it, so each remaining candidate is a duplicate or dropped as full
+                    // whatever the order: they resolve in parallel
+                    if (t == 0) s_misc[1] = (!a.slot_cls && __ldcg(&cell_h2(a, cell)[ne - 1]) != 0u) ? 1u : 0u;
+                    __syncthreads();
+                    if (s_misc[1]) {
+                        const uint32_t* cw = cell_h2(a, cell);
+                        for (uint32_t i = lo + t; i < hi; i += T) {
+                            if (__ldcg(&cb[i].cell) != cell || cb[i].prio <= last) continue;
+                            const uint32_t tg = __ldcg(&cb[i].target), hc = __ldcg(&cb[i].h2);
+                            bool dup = false;
+                            for (uint32_t e2 = tg & 0xFFu; e2 < ne; ++e2) dup |= __ldcg(&cw[e2]) == hc;
+                            if (dup) n_dup += 1u + (tg >> 16);
+                            else n_full += 1u + (tg >> 16);
+                        }
+                        __syncthreads();
+                        break;
+                    }
                     __syncthreads();
                 }
             }

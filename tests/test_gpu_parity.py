@@ -272,6 +272,22 @@ def test_bad_material_index_reported(P, mode):
     assert float(np.abs(out[:, ok] - r["rgb"][:, ok]).max()) <= TOL
 
 
+@pytest.mark.parametrize("n_cells", [2, 16])
+def test_cells_with_more_candidates_than_a_stage(P, n_cells):
+    """A table of a few cells takes thousands of candidates per cell in the first pass.  The
+    large-bin insert selects a crowded cell's candidates in order until the cell is full,
+    then settles the rest (duplicates or dropped) at once; the table and every counter equal
+    the oracle's sequential insert."""
+    mats = W.random_materials(4, 20, 80, 0.2, seed=31)
+    frame = W.Frame(W.FrameSpec(width=1920, height=1080, n_mats=4, seed=31))
+    gpu = P.Cache(mats, n_cells, 8)
+    ref = O.Cache(mats, n_cells, 8)
+    for p in range(2):
+        _compare_pass(gpu, ref, P, frame.points(p, rows=(0, 8)), check_masks=False)   # 15,360 points
+    assert gpu.stats()["dropped_full"] > 1024 * n_cells
+    _compare_tables(gpu, ref)
+
+
 def test_two_runs_identical(P):
     frame = W.Frame(W.FrameSpec(seed=2))
     mats = W.random_materials(64, 20, 200, 0.2, seed=2)
