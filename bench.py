@@ -43,7 +43,7 @@ REF_ROWS = (0, 16)               # reference arm: 16 full-width rows per step, a
 # DRAM bytes (read + written) per launch of each kernel, the mean of the two launches one
 # ncu capture of that kernel takes from a four-pass frame of this workload at the bench's
 # cost threshold; None while the kernel has changed since its capture
-NCU_TRAFFIC = {"eval": 150.6e6, "eval_roots": None, "lookup": 329.2e6}
+NCU_TRAFFIC = {"eval": 150.6e6, "eval_roots": 80.6e6, "lookup": 329.2e6}
 
 FP32_LANES_PER_SM = 128          # Blackwell SM: 4 partitions x 32 FP32 lanes
 
