@@ -187,8 +187,8 @@ typedef struct {
                                      block, 256 grouped points) per claim instead of one warp's
                                      64 points, so the warps of a block share the material's
                                      instruction and parameter lines (same results)          */
-#define PMC_ONE_POINT 0x800u    /* schedule only: one point per lane in the per-point evaluator
-                                     instead of two (same results)                           */
+#define PMC_ONE_POINT 0x800u    /* schedule only: one point per lane in the per-point and
+                                     batched-miss evaluators instead of two (same results)   */
 #define PMC_MAX_POS_LEVEL 20u
 
 typedef struct {
