@@ -407,7 +407,9 @@ pmc_status pmc_read_timing(pmc_cache* cache, double* ms, uint64_t* kernel_launch
  * tcgen05 tensor cores (tensor-memory accumulators), in inference and in training (forward,
  * backward and the weight gradients); FP32 master weights take Adam steps.  Per material the candidate node is its
  * most expensive cacheable node with no cacheable node below it.  A node with an enabled
- * surrogate is not probed: every pass evaluates the network for it. */
+ * surrogate is not probed: every pass evaluates the network for it.  When every cacheable
+ * node of every material has an enabled surrogate, a pass launches no lookup, no batched
+ * evaluation of misses and no insert (nothing is probed, so nothing is missed or inserted). */
 #define PMC_MLP_PARAMS 8515u
 
 typedef struct {
