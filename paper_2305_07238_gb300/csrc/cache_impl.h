@@ -57,6 +57,7 @@ struct pmc_cache {
     std::vector<uint8_t> surr_on;         // per material: enabled
     uint32_t n_surr_slots = 0, cap_surr_slots = 0;
     float* d_surr_theta = nullptr;        // cap_surr_slots x MLP_PARAMS
+    unsigned char* d_surr_img = nullptr;  // cap_surr_slots x SURR_IMG_BYTES (operand images)
     int32_t* d_surr_slot = nullptr;       // n_mats: slot if enabled, else -1
     int32_t* d_surr_ord = nullptr;        // n_mats: ordinal if enabled, else -1
     uint32_t* d_surr_items = nullptr;     // n_mats + 1

@@ -202,6 +202,7 @@ void pmc_destroy_cache(pmc_cache* c) {
         dfree(&c->d_root_order);
         dfree(&c->d_bins);
         dfree(&c->d_surr_theta);
+        dfree(&c->d_surr_img);
         dfree(&c->d_surr_slot);
         dfree(&c->d_surr_ord);
         dfree(&c->d_surr_items);
@@ -484,6 +485,7 @@ pmc_status enqueue_batch(pmc_cache* c, const pmc_points* pts, float* out_rgb, ui
     if (surrogates_active(c)) {
         a.surr_slot = c->d_surr_slot; a.surr_ord = c->d_surr_ord; a.surr_theta = c->d_surr_theta;
         a.surr_item_base = c->d_surr_items;
+        a.surr_img = c->d_surr_img;
         a.all_surr = c->all_roots_surr ? 1 : 0;
     }
     a.rinfo = c->d_rinfo; a.n_roots_total = (uint32_t)c->root_info.size(); a.max_level = c->max_level;
@@ -909,6 +911,12 @@ pmc_status grow_surrogate_slots(pmc_cache* c, uint32_t need) {
     pmc_status st = dalloc(&nt, (size_t)cap * MLP_PARAMS);
     if (st != PMC_OK) return st;
     cudaDeviceSynchronize();
+    // the images are rebuilt from the parameters whenever the maps are uploaded
+    dfree(&c->d_surr_img);
+    if ((st = dalloc(&c->d_surr_img, (size_t)cap * SURR_IMG_BYTES)) != PMC_OK) {
+        dfree(&nt);
+        return st;
+    }
     if (c->d_surr_theta && c->n_surr_slots)
         cudaMemcpy(nt, c->d_surr_theta, (size_t)c->n_surr_slots * MLP_PARAMS * sizeof(float), cudaMemcpyDeviceToDevice);
     dfree(&c->d_surr_theta);
@@ -938,6 +946,10 @@ cudaError_t upload_surrogate_maps(pmc_cache* c) {
     c->all_roots_surr = all && c->any_surr_on;
     cudaError_t e = cudaMemcpy(c->d_surr_slot, slot.data(), c->n_mats * sizeof(int32_t), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(c->d_surr_ord, ord.data(), c->n_mats * sizeof(int32_t), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && c->n_surr_slots && c->d_surr_img) {
+        e = launch_surrogate_images(c->d_surr_theta, c->n_surr_slots, c->d_surr_img, 0);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(0);
+    }
     return e;
 }
 

@@ -40,10 +40,14 @@ struct Sm {                                     // byte offsets into dynamic sha
     static constexpr uint32_t w2 = 24576;       // 64 x 64 BF16: W2 transposed
     static constexpr uint32_t w3 = 32768;       // 16 x 64 BF16: W3 transposed, rows 3..15 zero
     static constexpr uint32_t bias = 34816;     // b1[64], b2[64], b3[4] FP32
-    static constexpr uint32_t mbar = 35344;     // 8-byte mbarrier
-    static constexpr uint32_t tmem = 35352;     // tensor-memory base written by tcgen05.alloc
-    static constexpr uint32_t end = 35360;
+    static constexpr uint32_t mbar = 35344;     // 8-byte mbarrier of the products
+    static constexpr uint32_t mbar_w = 35352;   // 8-byte mbarrier of the operand-image copy
+    static constexpr uint32_t tmem = 35360;     // tensor-memory base written by tcgen05.alloc
+    static constexpr uint32_t end = 35368;
 };
+// the operand image of a network is shared memory [w1, bias end), in that layout
+static_assert(Sm::bias + 132 * 4 - Sm::w1 == SURR_IMG_BYTES, "operand image = weights and biases of Sm");
+static_assert(Sm::w1 % 16 == 0, "bulk copies land on 16-byte boundaries");
 static_assert(TC_CTAS_PER_SM * (Sm::end + 1024) <= 228 * 1024, "inference CTAs per SM by shared memory");
 static_assert(TC_CTAS_PER_SM * TC_COLS <= 512, "inference CTAs per SM by tensor memory");
 
@@ -139,9 +143,12 @@ __device__ __forceinline__ uint32_t pack2(float lo, float hi) {
 
 // FP32 parameters -> BF16 transposed operands and FP32 biases in shared memory (all 128
 // threads); the async-proxy fence is issued by the caller before the next MMA.
-// The loads of W1 and W2 are issued eight per matrix at a time, so that a thread has 16 in
-// flight instead of one (the parameters are FP32 and 4-byte aligned only).
-__device__ void tc_load_weights(unsigned char* sm, const float* __restrict__ th) {
+// The network's operands from its FP32 parameters, written at dst in the layout of Sm from
+// w1 on (shared memory, or a network's operand image in global memory).  The loads of W1
+// and W2 are issued eight per matrix at a time, so that a thread has 16 in flight instead
+// of one (the parameters are FP32 and 4-byte aligned only).
+__device__ void tc_write_weights(unsigned char* dst, const float* __restrict__ th) {
+    unsigned char* sm = dst - Sm::w1;   // offsets below are Sm's
     static_assert(64u * 64u % (TC_ROWS * 8u) == 0, "W1/W2 batches");
     for (uint32_t i0 = threadIdx.x; i0 < 64u * 64u; i0 += 8u * TC_ROWS) {
         float w1[8], w2[8];
@@ -165,6 +172,36 @@ __device__ void tc_load_weights(unsigned char* sm, const float* __restrict__ th)
     float* bias = reinterpret_cast<float*>(sm + Sm::bias);
     for (uint32_t i = threadIdx.x; i < 132u; i += blockDim.x)
         bias[i] = i < 64 ? th[P_B1 + i] : (i < 128 ? th[P_B2 + i - 64] : (i < 131 ? th[P_B3 + i - 128] : 0.0f));
+}
+
+__device__ __forceinline__ void tc_load_weights(unsigned char* sm, const float* __restrict__ th) {
+    tc_write_weights(sm + Sm::w1, th);
+}
+
+// The operand image of one network: block b writes slot b's.
+__global__ void __launch_bounds__(TC_ROWS) k_surr_images(const float* __restrict__ theta, unsigned char* img) {
+    tc_write_weights(img + (size_t)blockIdx.x * SURR_IMG_BYTES, theta + (size_t)blockIdx.x * MLP_PARAMS);
+}
+
+// One bulk copy (the tensor memory accelerator's linear form) of a network's operand image
+// into shared memory [w1, bias end), completing on mbar_w with its byte count: issued by
+// thread 0 after every thread is done with the previous network's operands (the caller's
+// barrier); every thread then waits (bounded).  False if the wait ran out.
+__device__ __forceinline__ bool tc_copy_image(unsigned char* sm, const unsigned char* src, uint32_t* phase_w) {
+    const uint32_t base = smem_u32(sm), mbar = base + Sm::mbar_w;
+    if (threadIdx.x == 0) {
+        fence_async_smem();
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mbar), "r"(SURR_IMG_BYTES)
+                     : "memory");
+        asm volatile(
+            "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(base +
+                                                                                                           Sm::w1),
+            "l"(src), "r"(SURR_IMG_BYTES), "r"(mbar)
+            : "memory");
+    }
+    const bool done = mbar_wait(mbar, *phase_w);
+    *phase_w ^= 1u;
+    return !__syncthreads_or(!done);
 }
 
 // BF16 pair {relu(lo), relu(hi)} (lo in the low half) in one conversion: each value is
@@ -294,6 +331,7 @@ __device__ __forceinline__ uint32_t tc_setup(unsigned char* sm) {
     const uint32_t base = smem_u32(sm);
     if (threadIdx.x == 0) {
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(base + Sm::mbar));
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(base + Sm::mbar_w));
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (threadIdx.x < 32) {
@@ -362,7 +400,7 @@ __global__ void __launch_bounds__(TC_ROWS) k_surrogate_tc(BatchArgs a) {
     const uint32_t n_items = a.ctl->n_surr_items;
     const uint32_t per = (n_items + gridDim.x - 1) / gridDim.x;
     const uint32_t i_end = min(n_items, (blockIdx.x + 1) * per);
-    uint32_t loaded = 0xFFFFFFFFu, phase = 0;
+    uint32_t loaded = 0xFFFFFFFFu, phase = 0, phase_w = 0;
     unsigned long long n_eval = 0;
     bool ok = true;
     // an item's material is the largest m with surr_item_base[m] <= item; the CTA's items are
@@ -387,7 +425,14 @@ __global__ void __launch_bounds__(TC_ROWS) k_surrogate_tc(BatchArgs a) {
         }
         if (m != loaded) {
             __syncthreads();   // the previous network's tile is finished everywhere
-            tc_load_weights(sm, a.surr_theta + (size_t)a.surr_slot[m] * MLP_PARAMS);
+            if (a.surr_img) {
+                if (!tc_copy_image(sm, a.surr_img + (size_t)a.surr_slot[m] * SURR_IMG_BYTES, &phase_w)) {
+                    ok = false;
+                    break;
+                }
+            } else {
+                tc_load_weights(sm, a.surr_theta + (size_t)a.surr_slot[m] * MLP_PARAMS);
+            }
             loaded = m;
         }
         const uint32_t j = (item - ibase) * TC_ROWS + t;
@@ -812,6 +857,12 @@ cudaError_t launch_surrogate(const BatchArgs& a, int num_sms, cudaStream_t s) {
     if (e != cudaSuccess) return e;
     // six CTAs per SM: their tensor-memory allocations (6 x 64 columns) fit the SM's 512
     k_surrogate_tc<<<num_sms * TC_CTAS_PER_SM, TC_ROWS, Sm::end, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_surrogate_images(const float* theta, uint32_t n_slots, unsigned char* img, cudaStream_t s) {
+    if (n_slots == 0) return cudaSuccess;
+    k_surr_images<<<n_slots, TC_ROWS, 0, s>>>(theta, img);
     return cudaGetLastError();
 }
 

@@ -154,6 +154,7 @@ extern "C" pmc_status pmc_eval_batch_noalloc(pmc_cache* c, const pmc_points* pts
     if (c->use_surrogates && c->any_surr_on) {
         a.surr_slot = c->d_surr_slot; a.surr_ord = c->d_surr_ord; a.surr_theta = c->d_surr_theta;
         a.surr_item_base = c->d_surr_items;
+        a.surr_img = c->d_surr_img;
         a.all_surr = c->all_roots_surr ? 1 : 0;
     }
     a.rinfo = c->d_rinfo; a.n_roots_total = (uint32_t)c->root_info.size(); a.max_level = c->max_level;

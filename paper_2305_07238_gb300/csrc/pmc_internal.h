@@ -119,6 +119,11 @@ constexpr uint64_t MAX_POINTS = 1ull << 28;
 
 constexpr uint32_t MAX_LEVELS = 16;    // nesting depth of cacheable nodes handled in batches
 constexpr uint32_t MLP_PARAMS = 8515;  // learned surrogate: 64 -> 64 -> 64 -> 3
+// A network's operand image: W1, W2 (64 x 64) and W3 (16 x 64, rows 3..15 zero) as BF16 in the
+// inference kernel's shared-memory layout, then b1, b2, b3 and one zero as FP32 -- the bytes
+// one bulk copy puts in place at a material boundary (a multiple of 16)
+constexpr uint32_t SURR_IMG_BYTES = 8192 + 8192 + 2048 + 132 * 4;
+static_assert(SURR_IMG_BYTES % 16 == 0, "bulk copies move multiples of 16 bytes");
 
 // Device-side control block of one cache object.
 struct Control {
@@ -208,6 +213,7 @@ struct BatchArgs {
     // learned surrogates: per material the surrogate's slot (-1 = none) and cacheable-node
     // ordinal; FP32 parameters per slot; work items of 128 points per material
     const int32_t* surr_slot; const int32_t* surr_ord; const float* surr_theta;
+    const unsigned char* surr_img;   // per slot SURR_IMG_BYTES (16-byte aligned), or null
     uint32_t* surr_item_base;  // n_mats + 1 (computed by k_scan)
     int all_surr;              // 1: every cacheable node of every material is a surrogate's:
                                // no lookup, no batched misses, no insert
@@ -265,5 +271,7 @@ cudaError_t launch_root_samples(const uint4* prog, const float* params, const Ro
                                 uint32_t n_train_mats, uint32_t n_rows, uint64_t seed, float* data, uint32_t max_slots,
                                 int num_sms, cudaStream_t s);
 cudaError_t launch_surrogate(const BatchArgs& a, int num_sms, cudaStream_t s);
+// Writes the operand images of slots 0 .. n_slots - 1 from their FP32 parameters.
+cudaError_t launch_surrogate_images(const float* theta, uint32_t n_slots, unsigned char* img, cudaStream_t s);
 
 }  // namespace pmc
