@@ -420,7 +420,7 @@ def ours(args, rank, world, local_rank, dist):
     if "surr" in legs:
         guarded("surrogate", lambda: surrogate_leg(torch, P, dev, local_rank, seed=rank))
     if "f128" in legs:
-        guarded("frame128", lambda: frame128_leg(torch, P, dev, local_rank, seed=rank))
+        guarded("frame128", lambda: frame128_leg(torch, P, dev, local_rank, seed=rank, min_root_cost=min_root_cost))
     if "alg1" in legs:
         guarded("alg1", lambda: alg1_leg(torch, P, mats, dev_passes, outs, hits, local_rank))
         if u_value == u_value and "cached" in line["alg1"]:
@@ -455,9 +455,10 @@ def ours(args, rank, world, local_rank, dist):
 F128_MATS, F128_LO, F128_HI, F128_PASSES, F128_CELLS = 1024, 5, 2000, 128, 1 << 23
 
 
-def frame128_leg(torch, P, dev, local_rank, seed=0):
+def frame128_leg(torch, P, dev, local_rank, seed=0, min_root_cost=0):
     """1024 networks of 5-2000 nodes (20 % SP); one 1920x1080 frame rendered as 128 passes
-    of one sample per pixel against a 1 GB table (2^23 cells x 8).  Frame throughput with
+    of one sample per pixel against a 1 GB table (2^23 cells x 8), cacheable nodes above the
+    cost threshold `min_root_cost`.  Frame throughput with
     stream launches and as one CUDA graph; grouped by material vs unsorted; the autotuned
     schedule; the uncached frame.  Points come from the torch form of the frame generator
     (9.6 GB resident)."""
@@ -467,19 +468,19 @@ def frame128_leg(torch, P, dev, local_rank, seed=0):
     passes = [frame.points_torch(p, dev) for p in range(F128_PASSES)]
     n = WIDTH * HEIGHT
     # materials are fixed per tile, so every pass needs the same number of probe records
-    roots = np.array([len(P.analyze_material(m)["roots"]) for m in mats])
-    need = int(roots[frame.tile_mat[frame.pix_tile]].sum())
+    roots = np.array([len(P.analyze_material(m, min_root_cost=min_root_cost)["roots"]) for m in mats])
+    need = max(1, int(roots[frame.tile_mat[frame.pix_tile]].sum()))
     outs = torch.empty((3, n), dtype=torch.float32, device=dev)
     hits = torch.empty(n, dtype=torch.int16, device=dev)
     pts_frame = n * F128_PASSES
     res = {"config": f"frame {WIDTH}x{HEIGHT}, {F128_PASSES} passes of 1 spp ({pts_frame} points), "
                      f"{F128_MATS} materials {F128_LO}-{F128_HI} nodes ({int(SP_FRAC * 100)}% SP), Zipf 1.1, "
                      f"table {F128_CELLS}x{N_ENTRIES} slots (1 GB), lambda {LEVEL}",
-           "unit": UNIT, "probes_per_pass": need}
+           "unit": UNIT, "probes_per_pass": need, "min_root_cost": min_root_cost}
 
     def make(flags=0):
         return P.Cache(mats, F128_CELLS, N_ENTRIES, uv_level=LEVEL, flags=flags, device=local_rank,
-                       probe_capacity=need)
+                       probe_capacity=need, min_root_cost=min_root_cost)
 
     def graph_rate(c, reps=2):
         g = c.graph(passes, [outs] * F128_PASSES, [hits] * F128_PASSES, reset=True)
