@@ -426,13 +426,15 @@ def ours(args, rank, world, local_rank, dist):
         if u_value == u_value and "cached" in line["alg1"]:
             line["alg1"]["speedup_cached_over_uncached"] = round(line["alg1"]["cached"] / u_value, 3)
     if "cones" in legs:
-        guarded("ray_cones", lambda: cones_leg(torch, P, dev, local_rank, seed=rank))
+        guarded("ray_cones", lambda: cones_leg(torch, P, dev, local_rank, seed=rank, min_root_cost=min_root_cost))
         if u_value == u_value and "offset0" in line["ray_cones"]:
-            for off in (0, -1):
-                r = line["ray_cones"][f"offset{off}"]
+            for key in [k for k in ("offset0", "offset-1", "offset0_threshold", "offset-1_threshold")
+                        if k in line["ray_cones"]]:
+                r = line["ray_cones"][key]
                 r["speedup_cached_over_uncached"] = round(r["cached"] / u_value, 3)
     if "raycast" in legs:
-        guarded("ray_caster", lambda: raycast_leg(torch, P, mats, dev, local_rank, seed=rank))
+        guarded("ray_caster", lambda: raycast_leg(torch, P, mats, dev, local_rank, seed=rank,
+                                                  min_root_cost=min_root_cost))
     if "position" in legs:
         guarded("position_descriptor", lambda: position_leg(torch, P, mats, dev_passes, outs, hits, local_rank))
     if "replace" in legs:
@@ -579,12 +581,13 @@ def alg1_leg(torch, P, mats, dev_passes, outs, hits, local_rank):
             "table": {k: st[k] for k in ("inserted", "dropped_dup", "dropped_full", "dropped_race")}}
 
 
-def raycast_leg(torch, P, mats, dev, local_rank, seed=0):
+def raycast_leg(torch, P, mats, dev, local_rank, seed=0, min_root_cost=0):
     """Shading points from the library's ray caster instead of the synthetic stream: a
     closed room with 24 spheres, 64 materials (Zipf 1.1 over the objects), a 1920x1080
     pinhole camera, one primary ray per pixel per pass, 16 passes.  The caster alone
     (points/s and the HBM roofline of its 56 B of output per point), then cast + pass with
-    per-point levels from the ray cones (Eq. 1), cached and uncached, eager launches."""
+    per-point levels from the ray cones (Eq. 1), cached (every cacheable node, and above the
+    cost threshold `min_root_cost`) and uncached, eager launches."""
     sc = W.Scene(W.SceneSpec(seed=seed))
     n = WIDTH * HEIGHT
     bufs = P.cast_rays(sc.objects, sc.camera, seed=seed + 1, pass_index=0)
@@ -616,8 +619,11 @@ def raycast_leg(torch, P, mats, dev, local_rank, seed=0):
                              "bytes_per_point": 56}}
     outs = torch.empty((3, n), dtype=torch.float32, device=dev)
     hits = torch.empty(n, dtype=torch.int16, device=dev)
-    for name, flags in (("cached", 0), ("uncached", P.PMC_CACHE_OFF)):
-        c = P.Cache(mats, N_CELLS, N_ENTRIES, uv_level=LEVEL, flags=flags, device=local_rank)
+    runs = [("cached", 0, 0), ("uncached", P.PMC_CACHE_OFF, 0)]
+    if min_root_cost:
+        runs.insert(1, ("cached_threshold", 0, min_root_cost))
+    for name, flags, thr in runs:
+        c = P.Cache(mats, N_CELLS, N_ENTRIES, uv_level=LEVEL, flags=flags, device=local_rank, min_root_cost=thr)
         for p in range(2):
             P.cast_rays(sc.objects, sc.camera, seed=seed + 1, pass_index=p, out=bufs)
             c.eval_batch(bufs, outs, hits)
@@ -632,12 +638,15 @@ def raycast_leg(torch, P, mats, dev, local_rank, seed=0):
         torch.cuda.synchronize()
         st = c.stats()
         r = {"points_per_s": round(n * SPP / (t0.elapsed_time(t1) / 1e3), 1)}
-        if name == "cached":
-            r.update(hit_rate=round(st["hits"] / max(1, st["lookups"]), 4), inserted=st["inserted"],
-                     dropped_full=st["dropped_full"])
+        if name != "uncached":
+            r.update(min_root_cost=thr, hit_rate=round(st["hits"] / max(1, st["lookups"]), 4),
+                     inserted=st["inserted"], dropped_full=st["dropped_full"])
         c.close()
         res[name] = r
     res["speedup_cached_over_uncached"] = round(res["cached"]["points_per_s"] / res["uncached"]["points_per_s"], 3)
+    if "cached_threshold" in res:
+        res["speedup_threshold_over_uncached"] = round(res["cached_threshold"]["points_per_s"] /
+                                                       res["uncached"]["points_per_s"], 3)
     return res
 
 
@@ -785,10 +794,11 @@ def replace_leg(torch, P, dev, local_rank, seed=0):
     return res
 
 
-def cones_leg(torch, P, dev, local_rank, seed=0):
+def cones_leg(torch, P, dev, local_rank, seed=0, min_root_cost=0):
     """The benchmark frame with every shading point at its own mip level, from the
     texture-coordinate gradients of its ray-cone footprint (Eq. 1; footprint minor axis
-    delta * 2^U(-1/2, 1/2), axis ratio log-uniform on [1, 4]), for level offsets 0 and -1:
+    delta * 2^U(-1/2, 1/2), axis ratio log-uniform on [1, 4]), for level offsets 0 and -1,
+    every cacheable node cached and with the cost threshold `min_root_cost` ("_threshold"):
     cached points/s (whole frame as one CUDA graph, autotuned schedule), hit rate and the
     levels the first pass uses.  Uncached evaluation does not depend on the level."""
     mats, frame = workload(seed)
@@ -801,8 +811,9 @@ def cones_leg(torch, P, dev, local_rank, seed=0):
     res = {"config": "frame 1920x1080x16spp, per-point mip level from ray-cone gradients, "
                      f"table {N_CELLS}x{N_ENTRIES} slots", "unit": UNIT,
            "levels_pass0": {int(k): int(v) for k, v in enumerate(hist) if v}}
-    for off in (0, -1):
-        c = P.Cache(mats, N_CELLS, N_ENTRIES, uv_level=LEVEL, level_offset=off, device=local_rank)
+    for off, thr in ((0, 0), (-1, 0), (0, min_root_cost), (-1, min_root_cost)):
+        c = P.Cache(mats, N_CELLS, N_ENTRIES, uv_level=LEVEL, level_offset=off, device=local_rank,
+                    min_root_cost=thr)
         for p in range(2):
             c.eval_batch(passes[p], outs, hits)
         c.autotune(passes[2], reps=2)
@@ -821,9 +832,10 @@ def cones_leg(torch, P, dev, local_rank, seed=0):
         torch.cuda.synchronize()
         g.close()
         c.close()
-        res[f"offset{off}"] = {"cached": round(3 * n * SPP / (t0.elapsed_time(t1) / 1e3), 1),
-                               "hit_rate": round(st["hits"] / max(1, st["lookups"]), 4),
-                               "inserted": st["inserted"], "dropped_full": st["dropped_full"]}
+        res[f"offset{off}" + ("_threshold" if thr else "")] = {
+            "cached": round(3 * n * SPP / (t0.elapsed_time(t1) / 1e3), 1), "min_root_cost": thr,
+            "hit_rate": round(st["hits"] / max(1, st["lookups"]), 4),
+            "inserted": st["inserted"], "dropped_full": st["dropped_full"]}
     del passes
     torch.cuda.empty_cache()
     return res
