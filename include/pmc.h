@@ -17,7 +17,8 @@
  *     or 0.  This library resolves concurrent inserts deterministically: a batch
  *     looks up against the table as it was when the batch started, then inserts
  *     its misses in ascending (point index, node ID) order, which it realises by
- *     grouping the candidates by cell (default) or with rounds of atomicMin on a
+ *     grouping the candidates by cell (default: a list per cell for N_e <= 8
+ *     keep-first tables, else bins of cells) or with rounds of atomicMin on a
  *     per-cell claim word (PMC_INSERT_ROUNDS).
  *
  * Conventions for every entry point:
@@ -189,6 +190,12 @@ typedef struct {
                                      instruction and parameter lines (same results)          */
 #define PMC_ONE_POINT 0x800u    /* schedule only: one point per lane in the per-point and
                                      batched-miss evaluators instead of two (same results)   */
+#define PMC_INSERT_BINNED 0x1000u /* schedule only: group the candidates by bins of 256 cells
+                                     (count, scan, scatter, then a warp or a block per bin)
+                                     where the default would chain each cell's candidates in
+                                     a list resolved by its first arrival (keep-first tables
+                                     of N_e <= 8 without PMC_INSERT_ROUNDS); same table and
+                                     counters either way                                     */
 #define PMC_MAX_POS_LEVEL 20u
 
 typedef struct {
@@ -510,7 +517,8 @@ pmc_status pmc_eval_batch_noalloc(pmc_cache* cache, const pmc_points* pts, float
  * counters and table, bit for bit. */
 typedef struct {
     uint32_t flags;     /* subset of PMC_EVAL_INLINE | PMC_INSERT_ROUNDS | PMC_UNSORTED |
-                           PMC_PROBE_INLINE | PMC_BLOCK_ITEMS | PMC_ONE_POINT           */
+                           PMC_PROBE_INLINE | PMC_BLOCK_ITEMS | PMC_ONE_POINT |
+                           PMC_INSERT_BINNED                                          */
     uint32_t lookup_rb; /* probes in flight per lane in the lookup kernel: 1, 2 or 4    */
 } pmc_schedule;
 

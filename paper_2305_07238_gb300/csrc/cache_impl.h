@@ -29,6 +29,7 @@ struct pmc_cache {
     uint32_t lookup_rb = 4;               // probes in flight per lane in k_lookup
     int block_items = 0;                  // PMC_BLOCK_ITEMS schedule
     int one_point = 0;                    // PMC_ONE_POINT schedule
+    int insert_binned = 0;                // PMC_INSERT_BINNED schedule
     uint64_t layout_gen = 1;              // bumped whenever a recorded graph would go stale
     uint32_t prog_len = 0;
     // device-resident, owned
@@ -39,6 +40,7 @@ struct pmc_cache {
     uint4* d_table = nullptr;
     uint8_t* d_cls = nullptr;             // PMC_REPLACE_VISIBILITY: class of every slot's entry
     unsigned long long* d_claims = nullptr;
+    uint32_t* d_chain_head = nullptr;     // n_cells list heads of the per-cell-list insert
     Control* d_ctl = nullptr;
     unsigned long long* d_stats = nullptr;
     pmc::RootInfo* d_rinfo = nullptr;
@@ -100,3 +102,11 @@ struct pmc_cache {
     uint64_t launches = 0;
     uint64_t timed_batches = 0;
 };
+
+// The insert through per-cell lists applies to keep-first tables of N_e <= 8 resolved after
+// the evaluation (not the claim rounds, the paper's concurrent update or replacement by
+// visibility class), unless the PMC_INSERT_BINNED schedule asks for the binned insert.
+inline bool insert_lists(const pmc_cache* c) {
+    return c->use_cache && c->desc.n_entries <= 8 &&
+           !(c->desc.flags & (PMC_INSERT_ROUNDS | PMC_ALG1 | PMC_REPLACE_VISIBILITY)) && !c->insert_binned;
+}

@@ -194,6 +194,7 @@ void pmc_destroy_cache(pmc_cache* c) {
         dfree(&c->d_table);
         dfree(&c->d_cls);
         dfree(&c->d_claims);
+        dfree(&c->d_chain_head);
         dfree(&c->d_ctl);
         dfree(&c->d_stats);
         dfree(&c->d_rinfo);
@@ -253,6 +254,7 @@ pmc_status pmc_create_cache(const pmc_cache_desc* desc, const pmc_material* mats
     c->probe_inline = (desc->flags & PMC_PROBE_INLINE) ? 1 : 0;
     c->block_items = (desc->flags & PMC_BLOCK_ITEMS) ? 1 : 0;
     c->one_point = (desc->flags & PMC_ONE_POINT) ? 1 : 0;
+    c->insert_binned = (desc->flags & PMC_INSERT_BINNED) ? 1 : 0;
     c->n_mats = n_mats;
 
     std::vector<uint4> prog;
@@ -354,6 +356,7 @@ pmc_status pmc_create_cache(const pmc_cache_desc* desc, const pmc_material* mats
         (s = dalloc(&c->d_table, slots ? table_units(c) + 16 : 0)) != PMC_OK ||
         (s = dalloc(&c->d_cls, replacing(c) ? slots : 0)) != PMC_OK ||
         (s = dalloc(&c->d_claims, cells)) != PMC_OK ||
+        (s = dalloc(&c->d_chain_head, cells)) != PMC_OK ||
         (s = dalloc(&c->d_ctl, 1)) != PMC_OK ||
         (s = dalloc(&c->d_stats, ST_COUNT)) != PMC_OK ||
         (s = dalloc(&c->d_rinfo, c->root_info.size())) != PMC_OK ||
@@ -397,7 +400,7 @@ pmc_status pmc_create_cache(const pmc_cache_desc* desc, const pmc_material* mats
     c->surr_on.assign(n_mats, 0);
     if (e == cudaSuccess) e = cudaMemset(c->d_surr_slot, 0xFF, n_mats * sizeof(int32_t));
     if (e == cudaSuccess) e = cudaMemset(c->d_surr_ord, 0xFF, n_mats * sizeof(int32_t));
-    if (e == cudaSuccess) e = launch_reset(c->d_table, table_units(c), c->d_claims, cells, c->d_ctl, c->d_stats, 0,
+    if (e == cudaSuccess) e = launch_reset(c->d_table, table_units(c), c->d_claims, c->d_chain_head, cells, c->d_ctl, c->d_stats, 0,
                                            (desc->flags & PMC_INSERT_ROUNDS) != 0);
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
     if (e != cudaSuccess) {
@@ -482,6 +485,9 @@ pmc_status enqueue_batch(pmc_cache* c, const pmc_points* pts, float* out_rgb, ui
     a.n_bins = c->n_bins; a.bin_cnt = c->d_bins; a.bin_base = c->d_bins + c->n_bins;
     a.bin_list = c->d_bins + 2 * (size_t)c->n_bins + 1;
     a.cands_binned = c->d_cands_binned;
+    a.insert_lists = insert_lists(c) ? 1 : 0;
+    a.chain_head = c->d_chain_head;
+    a.chain_next = reinterpret_cast<uint32_t*>(c->d_cands_binned);   // probe_cap words of its space
     if (surrogates_active(c)) {
         a.surr_slot = c->d_surr_slot; a.surr_ord = c->d_surr_ord; a.surr_theta = c->d_surr_theta;
         a.surr_item_base = c->d_surr_items;
@@ -824,7 +830,7 @@ pmc_status pmc_reset(pmc_cache* c, void* stream) {
     if (c->sticky != PMC_OK) return c->sticky;
     DeviceGuard g(c->desc.device);
     const uint64_t cells = c->use_cache ? c->desc.n_cells : 0;
-    cudaError_t e = launch_reset(c->d_table, table_units(c), c->d_claims, cells, c->d_ctl, c->d_stats,
+    cudaError_t e = launch_reset(c->d_table, table_units(c), c->d_claims, c->d_chain_head, cells, c->d_ctl, c->d_stats,
                                  (cudaStream_t)stream, (c->desc.flags & PMC_INSERT_ROUNDS) != 0);
     if (e != cudaSuccess) return cuda_fail(c, e);
     c->epoch_host = 0;
@@ -1190,7 +1196,8 @@ pmc_status pmc_get_schedule(const pmc_cache* c, pmc_schedule* out) {
     if (!c || !out) return PMC_ERR_INVALID_ARG;
     out->flags = (c->split ? 0u : PMC_EVAL_INLINE) | ((c->desc.flags & PMC_INSERT_ROUNDS) ? PMC_INSERT_ROUNDS : 0u) |
                  (c->unsorted ? PMC_UNSORTED : 0u) | (c->probe_inline ? PMC_PROBE_INLINE : 0u) |
-                 (c->block_items ? PMC_BLOCK_ITEMS : 0u) | (c->one_point ? PMC_ONE_POINT : 0u);
+                 (c->block_items ? PMC_BLOCK_ITEMS : 0u) | (c->one_point ? PMC_ONE_POINT : 0u) |
+                 (c->insert_binned ? PMC_INSERT_BINNED : 0u);
     out->lookup_rb = c->lookup_rb;
     return PMC_OK;
 }
@@ -1198,7 +1205,8 @@ pmc_status pmc_get_schedule(const pmc_cache* c, pmc_schedule* out) {
 pmc_status pmc_set_schedule(pmc_cache* c, const pmc_schedule* sc) {
     if (!c || !sc) return PMC_ERR_INVALID_ARG;
     const uint32_t known =
-        PMC_EVAL_INLINE | PMC_INSERT_ROUNDS | PMC_UNSORTED | PMC_PROBE_INLINE | PMC_BLOCK_ITEMS | PMC_ONE_POINT;
+        PMC_EVAL_INLINE | PMC_INSERT_ROUNDS | PMC_UNSORTED | PMC_PROBE_INLINE | PMC_BLOCK_ITEMS | PMC_ONE_POINT |
+        PMC_INSERT_BINNED;
     if (sc->flags & ~known) return PMC_ERR_INVALID_ARG;
     if (sc->lookup_rb != 1 && sc->lookup_rb != 2 && sc->lookup_rb != 4) return PMC_ERR_INVALID_ARG;
     if ((sc->flags & PMC_UNSORTED) && surrogates_active(c)) return PMC_ERR_UNSUPPORTED;
@@ -1209,6 +1217,7 @@ pmc_status pmc_set_schedule(pmc_cache* c, const pmc_schedule* sc) {
     c->probe_inline = (sc->flags & PMC_PROBE_INLINE) ? 1 : 0;
     c->block_items = (sc->flags & PMC_BLOCK_ITEMS) ? 1 : 0;
     c->one_point = (sc->flags & PMC_ONE_POINT) ? 1 : 0;
+    c->insert_binned = (sc->flags & PMC_INSERT_BINNED) ? 1 : 0;
     c->lookup_rb = sc->lookup_rb;
     c->desc.flags = (c->desc.flags & ~PMC_INSERT_ROUNDS) | (sc->flags & PMC_INSERT_ROUNDS);
     c->layout_gen++;
@@ -1267,7 +1276,7 @@ pmc_status pmc_graph_create(pmc_cache* c, const pmc_points* passes, uint32_t n_p
         const uint64_t slots = c->use_cache ? c->desc.n_cells * ne : 0;
         const uint64_t cells = c->use_cache ? c->desc.n_cells : 0;
         if (flags & PMC_GRAPH_RESET) {
-            e = launch_reset(c->d_table, table_units(c), c->d_claims, cells, c->d_ctl, c->d_stats, s, rounds);
+            e = launch_reset(c->d_table, table_units(c), c->d_claims, c->d_chain_head, cells, c->d_ctl, c->d_stats, s, rounds);
             c->table_empty = true;
         } else {
             c->table_empty = false;   // the table's contents at replay time are unknown
@@ -1414,14 +1423,16 @@ pmc_status pmc_autotune(pmc_cache* c, const pmc_points* sample, uint32_t reps, p
         if (table_bytes) r = cudaMemcpyAsync(c->d_table, saved, table_bytes, cudaMemcpyDeviceToDevice, s);
         if (r == cudaSuccess && cls_bytes) r = cudaMemcpyAsync(c->d_cls, saved_cls, cls_bytes, cudaMemcpyDeviceToDevice, s);
         if (r == cudaSuccess && cells) r = cudaMemsetAsync(c->d_claims, 0xFF, cells * sizeof(unsigned long long), s);
+        if (r == cudaSuccess && cells) r = cudaMemsetAsync(c->d_chain_head, 0xFF, cells * sizeof(uint32_t), s);
         if (r == cudaSuccess) r = cudaMemsetAsync(&c->d_ctl->epoch, 0, sizeof(uint32_t), s);
         c->epoch_host = 0;
         c->table_empty = s_empty;
         return r;
     };
-    std::vector<float> best_ms(cand.size(), 0.0f);
-    for (size_t k = 0; k < cand.size() && e == cudaSuccess && st == PMC_OK; ++k) {
-        if ((st = pmc_set_schedule(c, &cand[k])) != PMC_OK) break;
+    std::vector<float> best_ms;
+    auto time_cand = [&](size_t k) {
+        best_ms.resize(k + 1, 0.0f);
+        if ((st = pmc_set_schedule(c, &cand[k])) != PMC_OK) return;
         float bm = 0.0f;
         for (uint32_t r = 0; r < reps && e == cudaSuccess && st == PMC_OK; ++r) {
             if ((e = restore()) != cudaSuccess) break;
@@ -1434,12 +1445,29 @@ pmc_status pmc_autotune(pmc_cache* c, const pmc_points* sample, uint32_t reps, p
             if (r == 0 || ms < bm) bm = ms;
         }
         best_ms[k] = bm;
+    };
+    auto fastest = [&]() {
+        size_t b = 0;
+        for (size_t k = 1; k < best_ms.size(); ++k)
+            if (best_ms[k] < best_ms[b]) b = k;
+        return b;
+    };
+    for (size_t k = 0; k < cand.size() && e == cudaSuccess && st == PMC_OK; ++k) time_cand(k);
+    // the insert is independent of the evaluator's schedule: the fastest schedule again
+    // with the binned insert, where the per-cell lists would apply
+    if (e == cudaSuccess && st == PMC_OK && cand.size() < PMC_TUNE_MAX) {
+        const pmc_schedule b = cand[fastest()];
+        pmc_schedule x = b;
+        x.flags |= PMC_INSERT_BINNED;
+        if ((st = pmc_set_schedule(c, &b)) == PMC_OK && insert_lists(c)) {
+            cand.push_back(x);
+            time_cand(cand.size() - 1);
+        }
     }
     if (e == cudaSuccess && st == PMC_OK) st = fold_device_errors(c);
     // put the table, counters and history back, keep the fastest schedule
-    size_t best = 0;
-    for (size_t k = 1; k < cand.size(); ++k)
-        if (best_ms[k] < best_ms[best]) best = k;
+    const size_t best = best_ms.empty() ? 0 : fastest();
+    best_ms.resize(cand.size(), 0.0f);
     if (e == cudaSuccess) e = restore();
     if (e == cudaSuccess) e = cudaMemcpyAsync(c->d_stats, stats, sizeof(stats), cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);

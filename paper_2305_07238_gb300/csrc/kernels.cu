@@ -38,6 +38,12 @@ __device__ __forceinline__ void warp_add_u64(unsigned long long* dst, unsigned l
     if (lane_id() == 0 && v) atomicAdd(dst, v);
 }
 
+__device__ __forceinline__ void warp_add_u32(uint32_t* dst, uint32_t v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULL_MASK, v, o);
+    if (lane_id() == 0 && v) atomicAdd(dst, v);
+}
+
 // Appends the lanes with `pred` to a list; returns each lane's index (undefined for others).
 __device__ __forceinline__ uint32_t warp_append(uint32_t* counter, bool pred) {
     unsigned m = __ballot_sync(FULL_MASK, pred);
@@ -711,6 +717,7 @@ __global__ void __launch_bounds__(EVAL_WARPS * 32) k_eval(BatchArgs a, uint32_t*
     if (MODE == EVAL_GENERIC) {
         warp_add_u64(&a.stats[ST_CANDIDATES], n_cand);
         warp_add_u64(&a.stats[ST_FULL], n_full);
+        warp_add_u32(&a.ctl->w_cand, (uint32_t)(n_cand - n_full));
         if (a.keys_inline) {
             warp_add_u64(&a.stats[ST_LOOKUPS], n_look);
             warp_add_u64(&a.stats[ST_MISSES], n_look);
@@ -925,6 +932,7 @@ __global__ void __launch_bounds__(EVAL_WARPS * 32, MODE == EVAL_FILL ? 6 : 7) k_
     if (MODE == EVAL_FILL) {
         warp_add_u64(&a.stats[ST_CANDIDATES], fs.n_cand);
         warp_add_u64(&a.stats[ST_FULL], fs.n_full);
+        warp_add_u32(&a.ctl->w_cand, (uint32_t)(fs.n_cand - fs.n_full));
         warp_add_u64(&a.stats[ST_LOOKUPS], fs.n_look);
         warp_add_u64(&a.stats[ST_MISSES], fs.n_look);
         warp_add_u64(&a.stats[ST_SLOTS], fs.n_look);   // one (empty) slot examined per probe
@@ -1234,6 +1242,7 @@ __global__ void __launch_bounds__(EVAL_WARPS * 32) k_eval_fused(BatchArgs a, uin
     warp_add_u64(&a.stats[ST_FLOPS], n_flops);
     warp_add_u64(&a.stats[ST_CANDIDATES], n_cand);
     warp_add_u64(&a.stats[ST_FULL], n_full);
+    warp_add_u32(&a.ctl->w_cand, (uint32_t)(n_cand - n_full));
     warp_add_u64(&a.stats[ST_LOOKUPS], n_look);
     warp_add_u64(&a.stats[ST_HITS], n_hit);
     warp_add_u64(&a.stats[ST_MISSES], n_look - n_hit);
@@ -1399,6 +1408,7 @@ __device__ __forceinline__ void roots_stats(const BatchArgs& a, const RootStats&
     warp_add_u64(&a.stats[ST_FLOPS_MISSED], st.n_flops);
     warp_add_u64(&a.stats[ST_CANDIDATES], st.n_cand);
     warp_add_u64(&a.stats[ST_FULL], st.n_full);
+    warp_add_u32(&a.ctl->w_cand, (uint32_t)(st.n_cand - st.n_full));
 }
 
 template <bool POS>
@@ -2555,6 +2565,197 @@ __global__ void __launch_bounds__(256, 6) k_bin_insert(BatchArgs a) {
     warp_add_u64(&a.stats[ST_REPLACED], n_rep);
 }
 
+// ---- insert through per-cell lists (keep-first, N_e <= 8): two launches and no staging.
+// k_chain_link chains each candidate to the one that reached its cell before it
+// (chain_head[cell] = the last arrival, chain_next[i] = the one before i, CHAIN_END after
+// the first) and lists each cell once, when its first candidate arrives; k_chain_resolve
+// then resolves each listed cell with one thread.
+//
+// The chain's order is arbitrary, but sequential resolution in ascending priority depends
+// only on the set of the cell's candidates:
+//   * they all saw the same snapshot of the cell, whose slots from the first empty one on
+//     were empty, so only keys inserted by this resolution can make a duplicate;
+//   * with F empty slots, the keys inserted are the F distinct hash2 values whose smallest
+//     priority is smallest, in that order, each with the value of that candidate;
+//   * a candidate with an inserted hash2 that is not its smallest is a duplicate; the
+//     candidates of every other hash2 find the cell full.
+// A first walk keeps the best F distinct keys seen so far in a buffer, each with the smallest
+// priority seen for it; a new key pushes out the entry of largest priority when the buffer
+// is full and its own priority is smaller.  A key that belongs to the final F is never pushed
+// out (F better keys would have to exist) and enters at its smallest priority at the latest,
+// so the buffer ends as the inserted keys.  A second walk (lists of two or more) writes each
+// inserted key's candidate of smallest priority into the slot of its rank and sums the
+// weights (1 + shadows) of the inserted keys' candidates.  The rest are dropped full: the
+// evaluation counted the batch's emitted weight, which the resolution starts from, so a
+// cell without an empty slot is not walked at all.
+constexpr uint32_t CHAIN_END = 0xFFFFFFFFu;
+
+__global__ void __launch_bounds__(256) k_chain_link(BatchArgs a) {
+    const uint32_t n_in = min(a.ctl->n_cand, a.probe_cap);
+    const uint32_t* cc = a.lists[0];
+    const uint32_t lane = lane_id();
+    const uint32_t warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, n_warps = (gridDim.x * blockDim.x) >> 5;
+    // a warp takes 128 consecutive candidates per step: four independent atomics per lane
+    for (uint32_t b = warp * 128u; b < n_in; b += n_warps * 128u) {
+        uint32_t c[4];
+        bool first[4];
+#pragma unroll
+        for (uint32_t k = 0; k < 4; ++k) {
+            const uint32_t i = b + 32u * k + lane;
+            c[k] = i < n_in ? __ldcg(&cc[i]) : 0u;
+        }
+#pragma unroll
+        for (uint32_t k = 0; k < 4; ++k) {
+            const uint32_t i = b + 32u * k + lane;
+            first[k] = false;
+            if (i < n_in) {
+                const uint32_t prev = atomicExch(&a.chain_head[c[k]], i);
+                a.chain_next[i] = prev;
+                first[k] = prev == CHAIN_END;
+            }
+        }
+#pragma unroll
+        for (uint32_t k = 0; k < 4; ++k) {
+            const uint32_t x = warp_append(&a.ctl->n_lists, first[k]);
+            if (first[k]) a.lists[1][x] = c[k];
+        }
+    }
+}
+
+__global__ void __launch_bounds__(256, 4) k_chain_resolve(BatchArgs a) {
+    const uint32_t n_in = min(a.ctl->n_cand, a.probe_cap);
+    const uint32_t n_cells = min(a.ctl->n_lists, n_in);
+    const uint32_t ne = a.n_entries;
+    const uint4* cb = reinterpret_cast<const uint4*>(a.cands);   // two 16-byte halves per candidate
+    // every candidate counts as dropped full until its cell's resolution says otherwise
+    // (modular arithmetic: the sum of the counter's updates is the non-negative count)
+    unsigned long long n_dup = 0, n_ins = 0;
+    unsigned long long n_full = (blockIdx.x == 0 && threadIdx.x == 0) ? (unsigned long long)a.ctl->w_cand : 0ull;
+    bool bad = false;
+    const uint32_t stride = gridDim.x * blockDim.x;
+    for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < n_cells && !bad; t += stride) {
+        const uint32_t cell = __ldcg(&a.lists[1][t]);
+        const uint32_t head = atomicExch(&a.chain_head[cell], CHAIN_END);   // takes the list, leaves it empty
+        uint4 w0, w1;
+        load_cell_words(a, cell, &w0, &w1);
+        uint32_t used = ne;
+        {
+            const uint32_t h[8] = {w0.x, w0.y, w0.z, w0.w, w1.x, w1.y, w1.z, w1.w};
+#pragma unroll
+            for (int e = 7; e >= 0; --e)
+                if ((uint32_t)e < ne && h[e] == 0u) used = (uint32_t)e;   // the first empty slot
+        }
+        const uint32_t F = ne - used;
+        if (F == 0) continue;   // a full cell: every candidate is dropped, as counted
+        // walk 1: the buffer (hash2 and the smallest priority seen for it, unordered)
+        uint32_t hb[8];
+        unsigned long long pb[8];
+#pragma unroll
+        for (uint32_t e = 0; e < 8; ++e) {
+            hb[e] = 0u;
+            pb[e] = 0ull;
+        }
+        uint32_t nb = 0, steps = 0;
+        uint4 v = make_uint4(0, 0, 0, 0);   // r, g, b, target of the last candidate walked
+        for (uint32_t j = head; j != CHAIN_END;) {
+            if (j >= n_in || ++steps > n_in) {   // not a list of this batch's candidates
+                bad = true;
+                break;
+            }
+            const uint4 q = __ldcg(cb + 2 * (size_t)j);   // prio, cell, hash2
+            v = __ldcg(cb + 2 * (size_t)j + 1);
+            const uint32_t nj = __ldcg(&a.chain_next[j]);
+            const unsigned long long pr = ((unsigned long long)q.y << 32) | q.x;
+            const uint32_t hc = q.w;
+            bool found = false;
+#pragma unroll
+            for (uint32_t e = 0; e < 8; ++e)
+                if (e < nb && hb[e] == hc) {
+                    found = true;
+                    if (pr < pb[e]) pb[e] = pr;
+                }
+            if (!found) {
+                uint32_t at = nb;   // the buffer entry it takes (8: none)
+                if (nb < F) {
+                    nb++;
+                } else {
+                    // a new key with the buffer full: it pushes out the entry of largest
+                    // priority if its own is smaller
+                    unsigned long long mx = 0ull;
+#pragma unroll
+                    for (uint32_t e = 0; e < 8; ++e)
+                        if (e < nb && pb[e] > mx) {
+                            mx = pb[e];
+                            at = e;
+                        }
+                    if (pr >= mx) at = 8;
+                }
+#pragma unroll
+                for (uint32_t e = 0; e < 8; ++e)
+                    if (e == at) {
+                        hb[e] = hc;
+                        pb[e] = pr;
+                    }
+            }
+            j = nj;
+        }
+        if (bad) break;
+        uint32_t* cw = cell_h2(a, cell);
+        if (steps == 1) {
+            // one candidate: it takes the first empty slot; its shadows find it
+            const uint32_t w = 1u + (v.w >> 16);
+            cw[used] = hb[0];
+            float* val = cell_val(a, cell, used);
+            val[0] = __uint_as_float(v.x);
+            val[1] = __uint_as_float(v.y);
+            val[2] = __uint_as_float(v.z);
+            n_ins += 1;
+            n_dup += w - 1u;
+            n_full -= w;
+            continue;
+        }
+        // walk 2: the weight of the inserted keys' candidates; each key's candidate of
+        // smallest priority writes the key and its value into the slot of its rank
+        unsigned long long WI = 0;
+        for (uint32_t j = head, k = 0; j != CHAIN_END && k < steps; ++k) {   // the list checked above
+            const uint4 q = __ldcg(cb + 2 * (size_t)j);
+            const uint4 x = __ldcg(cb + 2 * (size_t)j + 1);
+            const uint32_t nj = __ldcg(&a.chain_next[j]);
+            const unsigned long long pr = ((unsigned long long)q.y << 32) | q.x;
+            const uint32_t hc = q.w;
+            bool in = false;
+            unsigned long long best = 0ull;
+#pragma unroll
+            for (uint32_t e = 0; e < 8; ++e)
+                if (e < nb && hb[e] == hc) {
+                    in = true;
+                    best = pb[e];
+                }
+            if (in) {
+                WI += 1u + (x.w >> 16);
+                if (pr == best) {
+                    uint32_t slot = used;
+#pragma unroll
+                    for (uint32_t f = 0; f < 8; ++f) slot += (f < nb && pb[f] < best) ? 1u : 0u;
+                    cw[slot] = hc;
+                    float* val = cell_val(a, cell, slot);
+                    val[0] = __uint_as_float(x.x);
+                    val[1] = __uint_as_float(x.y);
+                    val[2] = __uint_as_float(x.z);
+                }
+            }
+            j = nj;
+        }
+        n_ins += nb;
+        n_dup += WI - nb;
+        n_full -= WI;
+    }
+    if (bad) atomicOr(&a.ctl->err, ERR_INSERT);
+    warp_add_u64(&a.stats[ST_DUP], n_dup);
+    warp_add_u64(&a.stats[ST_FULL], n_full);
+    warp_add_u64(&a.stats[ST_INSERTED], n_ins);
+}
+
 __global__ void k_finish(BatchArgs a) {
     if (threadIdx.x == 0 && blockIdx.x == 0) {
         if (a.use_cache) a.ctl->epoch += a.n_entries + 1u;
@@ -2612,14 +2813,17 @@ cudaError_t launch_keys(const uint32_t* mat, const uint32_t* node, const float* 
     return cudaGetLastError();
 }
 
-cudaError_t launch_reset(uint4* table, size_t units, unsigned long long* claims, size_t cells,
+cudaError_t launch_reset(uint4* table, size_t units, unsigned long long* claims, uint32_t* chain_head, size_t cells,
                          Control* ctl, unsigned long long* stats, cudaStream_t s, bool claim_words) {
     cudaError_t e;
     if (units && (e = cudaMemsetAsync(table, 0, (units + 16) * sizeof(uint4), s)) != cudaSuccess) return e;
-    // all-ones: the largest claim word of the atomicMin rounds, an empty list per cell
-    // for the grouped insert
+    // all-ones: the largest claim word of the atomicMin rounds, and an empty list per cell
+    // for the per-cell-list insert (which leaves every list empty after a batch; this only
+    // repairs lists left by a batch that failed)
     (void)claim_words;
     if (cells && (e = cudaMemsetAsync(claims, 0xFF, cells * sizeof(unsigned long long), s)) != cudaSuccess) return e;
+    if (cells && chain_head && (e = cudaMemsetAsync(chain_head, 0xFF, cells * sizeof(uint32_t), s)) != cudaSuccess)
+        return e;
     if ((e = cudaMemsetAsync(ctl, 0, sizeof(Control), s)) != cudaSuccess) return e;
     return cudaMemsetAsync(stats, 0, ST_COUNT * sizeof(unsigned long long), s);
 }
@@ -2645,6 +2849,16 @@ static cudaError_t launch_insert(const BatchArgs& a, cudaStream_t s, int num_sms
             cudaSuccess)
             return e;
         *nl += 1;
+    } else if (a.n > 0 && a.use_cache && a.insert_lists) {
+        static int per_sm = 0;
+        if (per_sm == 0) {
+            int v = 0;
+            if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, k_chain_resolve, 256, 0) != cudaSuccess || v <= 0) v = 1;
+            per_sm = v;
+        }
+        k_chain_link<<<num_sms * 8, 256, 0, s>>>(a);
+        k_chain_resolve<<<num_sms * per_sm, 256, 0, s>>>(a);
+        *nl += 2;
     } else if (a.n > 0 && a.use_cache) {
         if ((e = cudaMemsetAsync(a.bin_cnt, 0, (size_t)a.n_bins * sizeof(uint32_t), s)) != cudaSuccess) return e;
         k_bin_count<<<gs_blocks, 256, 0, s>>>(a);

@@ -136,6 +136,8 @@ struct Control {
     uint32_t bins_warp;         // insert bins resolved by a warp, by a block, by ranges
     uint32_t bins_mid;
     uint32_t bins_big;
+    uint32_t n_lists;           // cells with candidates (per-cell-list insert)
+    uint32_t w_cand;            // candidates emitted for the insert, shadows included
     uint32_t pad1;
     // persistent
     uint32_t epoch;             // claim epoch of round 0 of the current batch
@@ -195,7 +197,8 @@ struct BatchArgs {
     float4* probes; uint32_t probe_cap;
     Candidate* cands;
     // index lists of the claim-round insert; the cell-grouped insert uses lists[0] for
-    // the cells of the candidates in emission order
+    // the cells of the candidates in emission order, and the per-cell-list insert lists[1]
+    // for the cells that received candidates
     uint32_t* lists[3];
     Control* ctl; unsigned long long* stats;
     // batched evaluation of misses
@@ -223,6 +226,12 @@ struct BatchArgs {
     uint32_t* bin_list;        // n_bins: the non-empty bins by resolving kernel (warp, block,
                                // ranges), each class in ascending bin order
     Candidate* cands_binned;   // probe_cap
+    // insert through per-cell lists (keep-first, N_e <= 8): the last candidate to reach
+    // each cell (n_cells entries, CHAIN_END when none; every list is empty between
+    // batches) and each candidate's predecessor in its cell (probe_cap entries)
+    int insert_lists;
+    uint32_t* chain_head;
+    uint32_t* chain_next;
     // schedule (chosen by the caller's flags or by the autotuner)
     int unsorted;              // 1: no grouping; k_eval_fused probes inline in batch order
     int probe_inline;          // 1: grouped; k_eval_fused probes inline (no lookup kernel)
@@ -247,7 +256,7 @@ enum { PH_SORT = 0, PH_LOOKUP, PH_MISSED, PH_EVAL, PH_INSERT, PH_FINISH, PH_COUN
 // events recorded on `s` at the phase boundaries; `*launches` counts kernel launches.
 cudaError_t launch_batch(const BatchArgs& a, cudaStream_t s, int num_sms, cudaEvent_t* ev,
                          uint64_t* launches);
-cudaError_t launch_reset(uint4* table, size_t units, unsigned long long* claims, size_t cells,
+cudaError_t launch_reset(uint4* table, size_t units, unsigned long long* claims, uint32_t* chain_head, size_t cells,
                          Control* ctl, unsigned long long* stats, cudaStream_t s, bool claim_words);
 cudaError_t launch_levels(const float* g1u, const float* g1v, const float* g2u, const float* g2v, uint64_t n,
                           int32_t offset, uint32_t* level, cudaStream_t s);

@@ -29,6 +29,7 @@ PMC_REPLACE_VISIBILITY = 0x100
 PMC_POSITION_DESCRIPTOR = 0x200
 PMC_BLOCK_ITEMS = 0x400
 PMC_ONE_POINT = 0x800
+PMC_INSERT_BINNED = 0x1000
 PMC_GRAPH_RESET = 0x1
 TUNE_MAX = 16
 

@@ -145,9 +145,11 @@ def test_tiny_config_cache_off(P):
 
 
 # ---- frame-shaped streams: a band of the 1920-wide frame, several table geometries ----------
-# PMC_EVAL_INLINE, PMC_INSERT_ROUNDS, PMC_UNSORTED, PMC_PROBE_INLINE
+# PMC_EVAL_INLINE, PMC_INSERT_ROUNDS, PMC_UNSORTED, PMC_PROBE_INLINE, PMC_INSERT_BINNED (the
+# default insert of N_e <= 8 tables chains each cell's candidates; "binned" groups them by
+# bins of cells, as the default does for N_e > 8)
 MODES = {"grouped": 0, "inline": 0x8, "rounds": 0x10, "unsorted": 0x20, "unsorted_rounds": 0x30,
-         "probe_inline": 0x40, "probe_inline_rounds": 0x50}
+         "probe_inline": 0x40, "probe_inline_rounds": 0x50, "binned": 0x1000, "unsorted_binned": 0x1020}
 
 
 @pytest.mark.parametrize("mode", sorted(MODES))
@@ -272,15 +274,17 @@ def test_bad_material_index_reported(P, mode):
     assert float(np.abs(out[:, ok] - r["rgb"][:, ok]).max()) <= TOL
 
 
+@pytest.mark.parametrize("insert", ["lists", "binned"])
 @pytest.mark.parametrize("n_cells", [2, 16])
-def test_cells_with_more_candidates_than_a_stage(P, n_cells):
+def test_cells_with_more_candidates_than_a_stage(P, n_cells, insert):
     """A table of a few cells takes thousands of candidates per cell in the first pass.  The
     large-bin insert selects a crowded cell's candidates in order until the cell is full,
-    then settles the rest (duplicates or dropped) at once; the table and every counter equal
-    the oracle's sequential insert."""
+    then settles the rest (duplicates or dropped) at once; the per-cell lists are walked
+    thousands of steps, with keys pushed out of the walk's buffer.  The table and every
+    counter equal the oracle's sequential insert."""
     mats = W.random_materials(4, 20, 80, 0.2, seed=31)
     frame = W.Frame(W.FrameSpec(width=1920, height=1080, n_mats=4, seed=31))
-    gpu = P.Cache(mats, n_cells, 8)
+    gpu = P.Cache(mats, n_cells, 8, flags=P.PMC_INSERT_BINNED if insert == "binned" else 0)
     ref = O.Cache(mats, n_cells, 8)
     for p in range(2):
         _compare_pass(gpu, ref, P, frame.points(p, rows=(0, 8)), check_masks=False)   # 15,360 points

@@ -56,9 +56,10 @@ def _host(ts):
 
 
 # ... plus the evaluator's work distribution: block-wide tiles of one material (0x400) and one
-# point per lane (0x800)
+# point per lane (0x800), and the binned insert instead of per-cell lists (0x1000)
 SCHEDULES = [(0, 4), (0, 2), (0, 1), (0x8, 4), (0x28, 4), (0x10, 4), (0x30, 2), (0x40, 4), (0x50, 4),
-             (0x400, 2), (0x800, 2), (0x410, 4), (0x840, 4)]
+             (0x400, 2), (0x800, 2), (0x410, 4), (0x840, 4), (0x1000, 4), (0x1028, 4), (0x1040, 1),
+             (0x1800, 2)]
 
 
 def test_every_schedule_same_results(P, band):
@@ -84,7 +85,7 @@ def test_every_schedule_same_results(P, band):
         assert got[3] == base[3], (flags, rb)
 
 
-@pytest.mark.parametrize("flags", [0, 0x20, 0x10, 0x40])
+@pytest.mark.parametrize("flags", [0, 0x20, 0x10, 0x40, 0x1000])
 def test_graph_with_reset_replays_the_frame(P, band, flags):
     mats, parts = band
     dparts = [P.points_to_device(p) for p in parts]
@@ -178,6 +179,8 @@ def test_autotune_leaves_cache_unchanged(P, band):
     assert len(res["tried"]) >= 5 and 0 <= res["best"] < len(res["tried"])
     assert all(t["ms"] > 0 for t in res["tried"])
     assert res["schedule"] == {k: res["tried"][res["best"]][k] for k in ("flags", "lookup_rb")}
+    # the fastest schedule is tried again with the binned insert
+    assert res["tried"][-1]["flags"] & P.PMC_INSERT_BINNED
     assert a.stats() == b.stats()
     assert np.array_equal(a.table()[0], b.table()[0]) and np.array_equal(a.table()[1], b.table()[1])
     ra, ha = _outputs(P, parts[2:])
