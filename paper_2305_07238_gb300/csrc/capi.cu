@@ -487,7 +487,6 @@ pmc_status enqueue_batch(pmc_cache* c, const pmc_points* pts, float* out_rgb, ui
     a.cands_binned = c->d_cands_binned;
     a.insert_lists = insert_lists(c) ? 1 : 0;
     a.chain_head = c->d_chain_head;
-    a.chain_next = reinterpret_cast<uint32_t*>(c->d_cands_binned);   // probe_cap words of its space
     if (surrogates_active(c)) {
         a.surr_slot = c->d_surr_slot; a.surr_ord = c->d_surr_ord; a.surr_theta = c->d_surr_theta;
         a.surr_item_base = c->d_surr_items;

@@ -2567,9 +2567,10 @@ __global__ void __launch_bounds__(256, 6) k_bin_insert(BatchArgs a) {
 
 // ---- insert through per-cell lists (keep-first, N_e <= 8): two launches and no staging.
 // k_chain_link chains each candidate to the one that reached its cell before it
-// (chain_head[cell] = the last arrival, chain_next[i] = the one before i, CHAIN_END after
-// the first) and lists each cell once, when its first candidate arrives; k_chain_resolve
-// then resolves each listed cell with one thread.
+// (chain_head[cell] = the last arrival; candidate i's cell field becomes the one before i,
+// CHAIN_END after the first, so that a step of a walk reads one 32-byte sector) and lists
+// each cell once, when its first candidate arrives; k_chain_resolve then resolves each
+// listed cell with one thread.
 //
 // The chain's order is arbitrary, but sequential resolution in ascending priority depends
 // only on the set of the cell's candidates:
@@ -2610,7 +2611,7 @@ __global__ void __launch_bounds__(256) k_chain_link(BatchArgs a) {
             first[k] = false;
             if (i < n_in) {
                 const uint32_t prev = atomicExch(&a.chain_head[c[k]], i);
-                a.chain_next[i] = prev;
+                a.cands[i].cell = prev;   // the successor replaces the cell, known from the list
                 first[k] = prev == CHAIN_END;
             }
         }
@@ -2662,9 +2663,11 @@ __global__ void __launch_bounds__(256, 4) k_chain_resolve(BatchArgs a) {
                 bad = true;
                 break;
             }
-            const uint4 q = __ldcg(cb + 2 * (size_t)j);   // prio, cell, hash2
-            v = __ldcg(cb + 2 * (size_t)j + 1);
-            const uint32_t nj = __ldcg(&a.chain_next[j]);
+            // prio, successor (in place of the cell), hash2; the candidates are read-only here,
+            // so the loads go through L1, where the second walk finds them
+            const uint4 q = __ldg(cb + 2 * (size_t)j);
+            v = __ldg(cb + 2 * (size_t)j + 1);
+            const uint32_t nj = q.z;
             const unsigned long long pr = ((unsigned long long)q.y << 32) | q.x;
             const uint32_t hc = q.w;
             bool found = false;
@@ -2718,9 +2721,9 @@ __global__ void __launch_bounds__(256, 4) k_chain_resolve(BatchArgs a) {
         // smallest priority writes the key and its value into the slot of its rank
         unsigned long long WI = 0;
         for (uint32_t j = head, k = 0; j != CHAIN_END && k < steps; ++k) {   // the list checked above
-            const uint4 q = __ldcg(cb + 2 * (size_t)j);
-            const uint4 x = __ldcg(cb + 2 * (size_t)j + 1);
-            const uint32_t nj = __ldcg(&a.chain_next[j]);
+            const uint4 q = __ldg(cb + 2 * (size_t)j);
+            const uint4 x = __ldg(cb + 2 * (size_t)j + 1);
+            const uint32_t nj = q.z;
             const unsigned long long pr = ((unsigned long long)q.y << 32) | q.x;
             const uint32_t hc = q.w;
             bool in = false;

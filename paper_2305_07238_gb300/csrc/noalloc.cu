@@ -153,7 +153,6 @@ extern "C" pmc_status pmc_eval_batch_noalloc(pmc_cache* c, const pmc_points* pts
     a.cands_binned = reinterpret_cast<Candidate*>(base + OFF_BINNED);
     a.insert_lists = insert_lists(c) ? 1 : 0;
     a.chain_head = c->d_chain_head;
-    a.chain_next = reinterpret_cast<uint32_t*>(base + OFF_BINNED);   // NA_PROBES words of its space
     if (c->use_surrogates && c->any_surr_on) {
         a.surr_slot = c->d_surr_slot; a.surr_ord = c->d_surr_ord; a.surr_theta = c->d_surr_theta;
         a.surr_item_base = c->d_surr_items;

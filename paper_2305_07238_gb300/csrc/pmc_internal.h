@@ -228,10 +228,9 @@ struct BatchArgs {
     Candidate* cands_binned;   // probe_cap
     // insert through per-cell lists (keep-first, N_e <= 8): the last candidate to reach
     // each cell (n_cells entries, CHAIN_END when none; every list is empty between
-    // batches) and each candidate's predecessor in its cell (probe_cap entries)
+    // batches); a candidate's cell field then holds its predecessor in its cell's list
     int insert_lists;
     uint32_t* chain_head;
-    uint32_t* chain_next;
     // schedule (chosen by the caller's flags or by the autotuner)
     int unsorted;              // 1: no grouping; k_eval_fused probes inline in batch order
     int probe_inline;          // 1: grouped; k_eval_fused probes inline (no lookup kernel)
