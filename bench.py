@@ -260,6 +260,15 @@ def ours(args, rank, world, local_rank, dist):
         warm = {"points_per_s": round(n * (SPP - 2) / (e0.elapsed_time(e1) / 1e3), 1),
                 "hit_rate": round((st1["hits"] - st0["hits"]) / max(1, st1["lookups"] - st0["lookups"]), 4),
                 "passes": f"2-{SPP - 1}", "launch": "eager"}
+        # hit rate of every pass of one frame (untimed: the counters are read after each pass)
+        cache.reset(stream)
+        per_pass, prev = [], cache.stats()
+        for p in range(SPP):
+            cache.eval_batch(dev_passes[p], outs, hits, stream)
+            cur = cache.stats()
+            per_pass.append(round((cur["hits"] - prev["hits"]) / max(1, cur["lookups"] - prev["lookups"]), 4))
+            prev = cur
+        warm["hit_rate_per_pass"] = per_pass
         return dict(tune=tune, secs_eager=secs_eager, timing=timing, frame_stats=frame_stats,
                     pass0_stats=pass0_stats, secs=max_over_ranks(torch, dist, secs, dev), g_launches=g_launches,
                     warm=warm)
