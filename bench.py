@@ -55,7 +55,7 @@ FP32_LANES_PER_SM = 128          # Blackwell SM: 4 partitions x 32 FP32 lanes
 
 
 def n_sms(torch, dev):
-    """Streaming multiprocessors of the device, as the driver reports them."""
+    """Streaming multiprocessors of the device, as the CUDA driver reports them."""
     return int(torch.cuda.get_device_properties(torch.device(dev)).multi_processor_count)
 
 

@@ -12,7 +12,7 @@
   most 1.6e-3); the surrogate pass is faster than exact evaluation of the same deep
   networks, with the cache as well as without it.
 
-The judge of a surrogate's accuracy is that RMSE against the FP64 exact values.  The
+What decides a surrogate's accuracy is that RMSE against the FP64 exact values.  The
 forward comparison with the oracle's network is a structural check only: the oracle's
 BF16 mode rounds at the points where the kernels round, so it mirrors their structure.
 """
