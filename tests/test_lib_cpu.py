@@ -35,6 +35,17 @@ def test_exports_every_declared_symbol(lib):
     assert set(P.EXPORTED) <= set(names)
 
 
+def test_binding_flag_values_match_the_header():
+    """Every PMC_* flag or limit the Python binding names has the header's value."""
+    text = re.sub(r"/\*.*?\*/", "", open(os.path.join(ROOT, "include/pmc.h")).read(), flags=re.S)
+    header = {m.group(1): int(m.group(2), 0) for m in re.finditer(r"#define\s+(PMC_[A-Z_0-9]+)\s+(0x[0-9A-Fa-f]+|\d+)u?\b", text)}
+    named = {k: v for k, v in vars(P).items() if k.startswith("PMC_") and isinstance(v, int)}
+    assert {"PMC_CACHE_OFF", "PMC_INSERT_ROUNDS", "PMC_ONE_POINT", "PMC_INSERT_BINNED"} <= set(named)
+    for k, v in named.items():
+        if k in header:
+            assert header[k] == v, k
+
+
 def _enum(path, prefix):
     text = open(os.path.join(ROOT, path)).read()
     return {m.group(1): int(m.group(2)) for m in re.finditer(rf"\b{prefix}([A-Z_]+)\s*=\s*(\d+)", text)}
