@@ -157,6 +157,11 @@ pmc_status fold_device_errors(pmc_cache* c) {
     }
     if (err & (ERR_INSERT | ERR_BOUNDS)) {
         fprintf(stderr, "pmc: internal device check failed (flags %u)\n", err);
+        // a walk of the per-cell-list insert that gave up left lists behind: empty them all,
+        // so that later batches start from empty lists
+        if ((err & ERR_INSERT) && c->d_chain_head && c->use_cache &&
+            cudaMemset(c->d_chain_head, 0xFF, c->desc.n_cells * sizeof(uint32_t)) == cudaSuccess)
+            cudaDeviceSynchronize();
         return PMC_ERR_CUDA;
     }
     if (err & ERR_BAD_MAT) return PMC_ERR_INVALID_ARG;
