@@ -373,13 +373,23 @@ def ours(args, rank, world, local_rank, dist):
                    "achieved_layout_bytes": round(layout_gbs, 1),
                    "frac_layout_bytes": round(layout_gbs / hbm_peak, 4)},
     }
+    # algorithmic bytes of the insert per frame: 24 B per candidate offered (its key, cell and
+    # value) and 16 B per slot filled.  No ncu traffic figure: the captures of its resolve
+    # cover the first two passes of a frame only, not a frame's mean launch.
+    ins_bytes_frame = 24 * frame_stats["candidates"] + 16 * frame_stats["inserted"]
+    ins_gbs = ins_bytes_frame * args.steps / (ms["insert"] / 1e3) / 1e9 if ms["insert"] else 0.0
+    kernels["insert"] = {"bound": "hbm", "achieved": round(ins_gbs, 1), "peak": hbm_peak, "unit": "GB/s",
+                         "frac": round(ins_gbs / hbm_peak, 4), "ms_per_pass": round(per_launch_ms["insert"], 4),
+                         "traffic": None, "bytes_per_pass": round(ins_bytes_frame / SPP)}
     phase_of = {"eval": "eval", "eval_roots": "missed", "lookup": "lookup"}
     dominant = max(phase_of, key=lambda k: ms[phase_of[k]])
     roof = dict(kernels[dominant])
     # the evaluators of the tuned schedule: two points per lane unless it is PMC_ONE_POINT
     one_point = bool(tune["schedule"]["flags"] & P.PMC_ONE_POINT)
+    binned = bool(tune["schedule"]["flags"] & P.PMC_INSERT_BINNED)
     names = {"eval": "k_eval" if one_point else "k_eval2", "eval_roots": "k_eval_roots" if one_point else "k_eval_roots2",
-             "lookup": "k_lookup"}
+             "lookup": "k_lookup",
+             "insert": "k_bin_count .. k_bin_insert (binned)" if binned else "k_chain_link + k_chain_resolve"}
     for k in kernels:
         kernels[k]["kernel"] = names[k]
     roof["kernel"] = names[dominant]
